@@ -1,0 +1,327 @@
+#!/usr/bin/env python3
+"""Benchmark of the coupled pressure-temperature multigrid on GB300.
+
+Workload (one "step"): for each of two bubble problems, coefficient set-up
+(mg_set_coeffs: elimination, coarsening, exact coarsest inverse) and a full
+FP64 solve (mg_solve: V(2,2) cycles, red-black block Gauss-Seidel, stop at
+1e-10 reduction of both per-field residual norms):
+  - 2D 1024 x 1024, 16 seeded bubbles (radii 0.02-0.08), walls;
+  - axisymmetric 512 x 1024 (r, z), one bubble of radius 0.2 on the axis.
+Metric: Mcell * V-cycles per second (finest cells times cycles, summed over the
+step, per second of device time), plus solves per second.
+
+Arms:
+  default            the CUDA library through its C ABI (inputs resident in HBM);
+                     `e2e` repeats the step from host buffers (copies timed).
+  --impl reference   the FP64 CPU oracle on the host cores, a bounded sample
+                     of the same workload per step (one V-cycle per problem).
+
+Multi-GPU (torchrun): replicas only.  Each rank solves its own copy of the
+workload; value = units of all ranks / max-over-ranks time (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "coupled p-T MG Mcell-Vcycles/s & solves/s at 1e-10 resid; HBM %peak; p50/p99"
+UNIT = "Mcell-Vcycles/s"
+FALLBACK_HBM_GBS = 6800.0
+L2_FLUSH_BYTES = 256 << 20
+# algorithmic bytes per finest cell of one colour half-sweep (FP64, 2D):
+# x 16 + b 16 + Dinv 32 + faces 32 read, x 16 written per full sweep = 112 B
+SMOOTH_BYTES_PER_CELL_HALF = {("fp64", 2): 56.0, ("fp64", 3): 64.0, ("mixed", 2): 28.0, ("mixed", 3): 32.0}
+
+
+def env_int(k, d):
+    try:
+        return int(os.environ.get(k, d))
+    except ValueError:
+        return d
+
+
+def workload_problems():
+    from paper_2206_11294_gb300 import inputs as I
+    return [I.bubbles_1024(), I.bubble_axi()]
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        for k in ("hbm_gbs", "hbm_GBs", "hbm"):
+            if k in d:
+                v = d[k]
+                return float(v["value"] if isinstance(v, dict) else v), "measured"
+    except Exception:
+        pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_id: str | None):
+        self.proc = None
+        self.path = None
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+            if device_id:
+                cmd += ["-i", device_id]
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(cmd, stdout=self.out, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict | None:
+        if self.proc is None:
+            return None
+        try:
+            self.proc.terminate()
+            self.proc.wait(timeout=5)
+        except Exception:
+            pass
+        self.out.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 8:
+                try:
+                    rows.append(parts)
+                except Exception:
+                    pass
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = sorted(float(r[0]) for r in rows if r[0].replace(".", "").isdigit())
+        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[q] for r in rows for q in range(4) if r[4 + q].lower() == "active"})
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def gpu_identity(torch, dev):
+    try:
+        u = torch.cuda.get_device_properties(dev).uuid
+        s = str(u)
+        return s if s.startswith("GPU-") else "GPU-" + s
+    except Exception:
+        return None
+
+
+def face_bytes(p):
+    return sum(8 * (a.size + b.size) for a, b in zip(p.fa, p.fk))
+
+
+# ----------------------------------------------------------------- our arm
+def run_ours(args, rank, world):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from paper_2206_11294_gb300.binding import Solver
+
+    dev = env_int("LOCAL_RANK", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    probs = workload_problems()
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda(dev)
+    dev_in = []
+    solvers = []
+    for p in probs:
+        s = Solver(p.grid, precision=args.precision, rtol=1e-10, max_cycles=50, device=dev, stream=stream)
+        dev_in.append(dict(lam=T(p.lam), fa=[T(f) for f in p.fa], fk=[T(f) for f in p.fk], b=T(p.b),
+                           x0=T(p.x0), x=T(p.x0)))
+        solvers.append(s)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=f"cuda:{dev}")
+
+    def step(collect):
+        for s, d in zip(solvers, dev_in):
+            s.set_coeffs(d["lam"], d["fa"], d["fk"])
+            st = s.solve(d["b"], d["x"])
+            collect.append(st)
+
+    # timing hooks of the dominant kernel (finest-level smoothing of problem 0)
+    for s in solvers:
+        s.set_timing(True)
+    for _ in range(args.warmup):
+        for d in dev_in:
+            d["x"].copy_(d["x0"])
+        step([])
+    torch.cuda.synchronize()
+    for s in solvers:
+        s.set_timing(True)           # reset counters after warm-up
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    stats = []
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(gpu_identity(torch, dev)) if rank == 0 else None
+    wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()                           # L2 flushed between timed steps
+        for d in dev_in:
+            d["x"].copy_(d["x0"])
+        starts[k].record(stream)
+        step(stats)
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop() if clocks else None
+    dev_ms = sum(a.elapsed_time(b) for a, b in zip(starts, ends))
+    counters = [s.counters() for s in solvers]
+    units = sum(p.grid.N * st["cycles"] for p, st in zip(probs * args.steps, stats)) / 1e6
+    solves = len(stats)
+    t = torch.tensor([dev_ms / 1e3], dtype=torch.float64, device=f"cuda:{dev}")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    tmax = float(t.item())
+    value = units * world / tmax
+    # roofline of the dominant kernel, from its live event timings
+    c0 = counters[0]
+    peak, peak_kind = measured_peak()
+    half_bytes = SMOOTH_BYTES_PER_CELL_HALF[(args.precision, probs[0].grid.dim)] * c0["smooth_cells"]
+    avg_s = c0["smooth_ms"] / 1e3 / max(1, c0["smooth_launches"])
+    achieved = half_bytes / avg_s / 1e9 if avg_s > 0 else None
+    cycles = [st["cycles"] for st in stats[: len(probs)]]
+
+    # end to end through the C ABI from host buffers (copies inside the timed region)
+    e2e = None
+    if not args.no_e2e:
+        host_x = [p.x0.copy() for p in probs]
+        for s in solvers:
+            s.set_timing(False)
+        torch.cuda.synchronize()
+        e_units = 0.0
+        w0 = time.perf_counter()
+        for k in range(args.steps):
+            for p, s, hx in zip(probs, solvers, host_x):
+                hx[:] = p.x0
+                s.set_coeffs(p.lam, p.fa, p.fk)
+                st = s.solve(p.b, hx)
+                e_units += p.grid.N * st["cycles"] / 1e6
+        torch.cuda.synchronize()
+        e_wall = time.perf_counter() - w0
+        tt = torch.tensor([e_wall], dtype=torch.float64, device=f"cuda:{dev}")
+        if world > 1:
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        h2d = sum(32 * p.grid.N + face_bytes(p) + 32 * p.grid.N for p in probs)
+        d2h = sum(16 * p.grid.N for p in probs)
+        e2e = {"value": e_units * world / float(tt.item()), "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "seconds": float(tt.item())}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(probs)
+
+    if rank != 0:
+        return None
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": tmax * 1e3 / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+        "data": "synthetic (seeded bubble fields; Eqs. 29-34 coefficients)",
+        "config": {"workload": "bubbles16_1024x1024 + axi_512x1024, set-up + FP64 solve to 1e-10 per step",
+                   "cells_per_step": sum(p.grid.N for p in probs), "cycles_per_solve": cycles,
+                   "solves_per_s": solves * world / tmax, "precision": args.precision,
+                   "cycle": "V(2,2) red-black block GS, exact coarsest solve", "l2": "flushed between steps",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "hbm", "kernel": "k_rbgs_colour finest level (one colour per launch)",
+                     "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": (achieved / peak) if achieved else None, "peak_source": peak_kind,
+                     "algorithmic_bytes_per_launch": half_bytes, "avg_launch_us": avg_s * 1e6,
+                     "traffic": None},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": int(sum(c["launches"] for c in counters)),
+        "clocks": clk,
+        "wall_s": wall,
+    }
+    return out
+
+
+def cpu_baseline(probs):
+    """The oracle as it stands (one thread), one V-cycle per problem with its
+    hierarchy set-up: a bounded sample of the workload."""
+    import oracle
+    oracle.build()
+    units = 0.0
+    t0 = time.perf_counter()
+    for p in probs:
+        x, cyc, _ = oracle.mg_solve(p.grid.as_dict(), p.lam, p.fa, p.fk, p.b, p.x0, max_cycles=1, rtol=0.0)
+        units += p.grid.N * cyc / 1e6
+    dt = time.perf_counter() - t0
+    return {"value": units / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "1 V-cycle (with hierarchy set-up and residuals) on each of the 2 problems",
+            "seconds": dt}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    probs = workload_problems()
+    import oracle
+    oracle.build()
+    for _ in range(args.warmup):
+        pass   # the oracle has no warm-up state; its build is outside the timing
+    units = 0.0
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for p in probs:
+            x, cyc, _ = oracle.mg_solve(p.grid.as_dict(), p.lam, p.fa, p.fk, p.b, p.x0, max_cycles=1, rtol=0.0)
+            units += p.grid.N * cyc / 1e6
+    dt = time.perf_counter() - t0
+    v = units / dt
+    return {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded bubble fields)", "impl": "reference",
+            "config": {"workload": "bubbles16_1024x1024 + axi_512x1024, one oracle V-cycle each per step"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "1 V-cycle (with set-up) on each of the 2 problems per step"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    world = env_int("WORLD_SIZE", 1)
+    rank = env_int("RANK", 0)
+    if args.impl == "ours" and world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(env_int("LOCAL_RANK", 0))
+        dist.init_process_group("nccl")
+    out = run_reference(args, rank, world) if args.impl == "reference" else run_ours(args, rank, world)
+    if out is not None:
+        print(json.dumps(out), flush=True)
+    if args.impl == "ours" and world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

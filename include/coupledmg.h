@@ -1,0 +1,172 @@
+/*
+ * coupledmg.h - C ABI of the GB300 multigrid solver for the coupled
+ * pressure-temperature Poisson-Helmholtz system of Saade, Lohse & Fuster
+ * (arXiv 2206.11294), Sec. 3, Eqs. 27-34.
+ *
+ * The system (unknown per cell a = (T, p), the paper's order):
+ *
+ *   div(k grad T)     + l1 T + l2 p                    = lambda_T   (Eq. 27)
+ *   div((1/rho) grad p) + l3 p + l4 div(k grad T)      = lambda_p   (Eq. 28)
+ *
+ * with per-cell l1..l4 (Eqs. 29-32) and right-hand side lambda_T, lambda_p
+ * (Eqs. 33-34), discretised with cell-centred finite volumes on a uniform grid
+ * (2D Cartesian, 2D axisymmetric (r, z), 3D Cartesian).  It is solved by the
+ * paper's defect-correction loop (Sec. 3, the four steps after Eq. 34) with
+ * one multigrid V-cycle as the correction solve, entirely on one GPU.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Cells are numbered x-fastest: id = i + n0*(j + n1*k).
+ * - Faces normal to axis a carry n_a + 1 entries along a and n_b along the
+ *   other axes, numbered x-fastest in that shape: boundary faces included.
+ * - Cell arrays of pairs are [N][2] doubles, (T, p) or (lambda_T, lambda_p);
+ *   lambda is [N][4] doubles, l1..l4.
+ * - Pointers are host pointers when on_device == 0 and device pointers of the
+ *   handle's device when on_device == 1.  Device pointers must be 16-byte
+ *   aligned.  The caller owns every buffer it passes; the library copies what
+ *   it keeps.
+ * - Every call runs on the CUDA stream given to mg_create and returns after
+ *   that work has completed (the *_async calls excepted).
+ * - Errors are returned as mg_status; no exception or signal crosses the ABI.
+ *   mg_last_error() gives a thread-local message for the last failure.
+ *   Arguments are validated before any output is written.
+ */
+#ifndef COUPLEDMG_H
+#define COUPLEDMG_H
+
+#include <stddef.h>
+
+#if defined(__GNUC__)
+#define MG_API __attribute__((visibility("default")))
+#else
+#define MG_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MG_OK = 0,
+    MG_ERR_INVALID_ARG = 1,     /* bad sizes, kinds, pointers, or a grid whose coarsest level is too large */
+    MG_ERR_OOM = 2,             /* device allocation failed */
+    MG_ERR_BUDGET = 3,          /* workspace given to mg_create too small */
+    MG_ERR_INVALID_COEFF = 4,   /* a local 2x2 block is singular or not finite */
+    MG_ERR_NOT_CONVERGED = 5,   /* max_cycles reached; x and stats still written */
+    MG_ERR_TIMEOUT = 6,         /* a bounded device-side wait gave up */
+    MG_ERR_CUDA = 7,            /* a CUDA runtime call failed (message in mg_last_error) */
+    MG_ERR_STATE = 8            /* call out of order (e.g. mg_solve before mg_set_coeffs) */
+} mg_status;
+
+/* Boundary kinds per axis and side (Appendix B uses Dirichlet p; Sec. 5.2 a
+ * rigid no-flux wall; the axisymmetric runs a symmetry axis at r = 0). */
+enum { MG_BC_WALL = 0, MG_BC_DIRICHLET = 1, MG_BC_AXIS = 2 };
+
+/* Precision of the multigrid cycles. */
+enum { MG_FP64 = 0, MG_MIXED = 1 };
+
+typedef struct {
+    int dim;             /* 2 or 3 */
+    int axisym;          /* 1: dim == 2 and axis 0 is the radius r, axis 1 is z */
+    int n[3];            /* cells per axis, n[2] = 1 when dim == 2 */
+    double h;            /* uniform cell size */
+    double r0;           /* axisymmetric: radius of the low-r face (0: the symmetry axis) */
+    int bc[3][2];        /* MG_BC_* per axis, low and high side */
+    double bc_T[3][2];   /* Dirichlet values of T (used where bc == MG_BC_DIRICHLET) */
+    double bc_p[3][2];   /* Dirichlet values of p */
+} mg_grid;
+
+typedef struct {
+    int nu1, nu2;        /* pre- and post-smoothing sweeps per level (default 2, 2) */
+    int precision;       /* MG_FP64 or MG_MIXED (FP32 cycles inside FP64 refinement) */
+    double rtol;         /* stop when both per-field norms fell by rtol; <= 0: run max_cycles */
+    int max_cycles;      /* FP64: V-cycles; MIXED: outer refinement steps */
+    int coarse_min;      /* coarsen while every n_a is even and n_a/2 >= coarse_min (default 4) */
+    int inner_cycles;    /* MIXED: FP32 V-cycles per outer step (default 1) */
+} mg_options;
+
+typedef struct {
+    int cycles;          /* V-cycles run (MIXED: total FP32 cycles) */
+    int outer;           /* MIXED: outer FP64 steps; FP64: equals cycles */
+    double r0[2];        /* initial per-field stopping norms ||D^-1 r||_2 (T, p) */
+    double rfinal[2];    /* final per-field stopping norms */
+    double seconds;      /* wall time of the call */
+    int status;          /* mg_status of the solve */
+    int levels;          /* multigrid levels of the hierarchy */
+} mg_stats;
+
+typedef struct mg_handle mg_handle;
+
+/* Fills defaults: V(2,2), FP64, rtol 1e-10, 50 cycles, coarse_min 4, 1 inner cycle. */
+MG_API mg_status mg_default_options(mg_options *opt);
+
+/* Device bytes a handle of this grid and these options needs (hierarchy,
+ * coarse inverse, staging).  No device work. */
+MG_API mg_status mg_workspace_size(const mg_grid *grid, const mg_options *opt, size_t *bytes);
+
+/* Creates a solver for one grid on the current CUDA device.
+ *   workspace, workspace_bytes: device memory of at least mg_workspace_size
+ *     bytes, owned by the caller and kept alive until mg_destroy; NULL lets the
+ *     library allocate (and free) its own.
+ *   stream: a cudaStream_t (NULL = legacy default stream) for all later work.
+ * The handle is not thread-safe; distinct handles may be used concurrently. */
+MG_API mg_status mg_create(const mg_grid *grid, const mg_options *opt, void *workspace,
+                    size_t workspace_bytes, void *stream, mg_handle **out);
+
+/* Coefficient intake and set-up (Eqs. 27-32): per-cell lambda [N][4] = l1..l4
+ * and per-axis face arrays of 1/rho (face_alpha[a]) and k (face_k[a]) for
+ * a < dim.  Builds the whole hierarchy on the device: row elimination
+ * (p-row minus l4 times T-row), coarse coefficients and the exact coarsest
+ * solve.  MG_ERR_INVALID_COEFF if a local block is singular or not finite. */
+MG_API mg_status mg_set_coeffs(mg_handle *h, const double *lambda, const double *const face_alpha[3],
+                        const double *const face_k[3], int on_device);
+
+/* Solves L(x) = rhs: rhs [N][2] = (lambda_T, lambda_p) (Eqs. 33-34); x [N][2]
+ * = (T, p), in: initial guess (the paper's a~), out: result.  stats may be
+ * NULL.  Returns MG_OK on convergence, MG_ERR_NOT_CONVERGED (x written)
+ * after max_cycles. */
+MG_API mg_status mg_solve(mg_handle *h, const double *rhs, double *x, int on_device, mg_stats *stats);
+
+/* y = L(x) (Eqs. 27-28 with the grid's Dirichlet values), all pointers on the
+ * given side.  A building block for residual checks: res = b - L(x). */
+MG_API mg_status mg_apply(mg_handle *h, const double *x, double *y, int on_device);
+
+/* In place: `sweeps` red-black block Gauss-Seidel sweeps on the finest level
+ * (red = even i+j+k first; each cell's 2x2 block solved exactly) of the
+ * row-eliminated system with right-hand side rhs. */
+MG_API mg_status mg_smooth(mg_handle *h, const double *rhs, double *x, int sweeps, int on_device);
+
+/* Per-field stopping norms ||D^-1 r||_2 (out[2], host) of x for rhs, where r
+ * is the residual of the row-eliminated system and D its 2x2 diagonal block. */
+MG_API mg_status mg_residual_norms(mg_handle *h, const double *rhs, const double *x, int on_device,
+                            double out[2]);
+
+/* Instrumentation.  mg_set_timing(h, 1) resets the counters and, from then
+ * on, brackets the finest level's smoothing in every cycle with CUDA events
+ * on the handle's stream (the cycle graphs are re-captured with event
+ * nodes); 0 turns that off.  mg_counters reports, since the last reset:
+ *   launches          kernels this handle launched (graph nodes counted per replay)
+ *   smooth_ms         device time of the finest-level smoothing kernels (timing on)
+ *   smooth_launches   how many such kernel launches that time covers
+ *   smooth_cells      finest-level cells per smoothing launch */
+MG_API mg_status mg_set_timing(mg_handle *h, int enable);
+MG_API mg_status mg_counters(const mg_handle *h, long long *launches, double *smooth_ms,
+                             long long *smooth_launches, long long *smooth_cells);
+
+/* Makes `device` the CUDA device this thread's later mg_create calls use
+ * (the library's own runtime keeps a current device per thread). */
+MG_API mg_status mg_set_device(int device);
+
+/* Number of multigrid levels and the finest-to-coarsest sizes (n_out: levels x 3 ints, may be NULL). */
+MG_API mg_status mg_levels(const mg_handle *h, int *levels, int *n_out);
+
+MG_API mg_status mg_destroy(mg_handle *h);
+
+/* Message of the calling thread's last failure ("" if none). */
+MG_API const char *mg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* COUPLEDMG_H */

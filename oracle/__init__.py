@@ -15,6 +15,7 @@ defect-correction loop after them; see the C file for the exact statements):
 - ``rbgs_sweeps``     in-place red-black block Gauss-Seidel sweeps
 - ``residual_norms``  the per-field stopping norm ||D^-1 r'||_2
 - ``level_coeffs``    coarse-level blocks and faces of the hierarchy
+- ``apply_rows``      L(x) at selected cells (residual checks of large solutions)
 """
 from __future__ import annotations
 
@@ -82,6 +83,8 @@ def _load():
             lib.orc_num_levels.restype = C.c_int
             lib.orc_level_coeffs.argtypes = [gp, dp, pa3, pa3, C.c_int, C.c_int, dp, pa3, pa3]
             lib.orc_level_coeffs.restype = C.c_int
+            lib.orc_apply_rows.argtypes = [gp, dp, pa3, pa3, dp, C.POINTER(C.c_long), C.c_long, dp]
+            lib.orc_apply_rows.restype = None
             _lib = lib
     return _lib
 
@@ -223,3 +226,17 @@ def level_coeffs(g, lam, fa, fk, level, coarse_min=4):
     if rc:
         raise RuntimeError(f"oracle level_coeffs failed ({rc})")
     return B.reshape(N, 4), fa_o[:dim], fk_o[:dim]
+
+
+def apply_rows(g, lam, fa, fk, x, ids) -> np.ndarray:
+    """L(x) (Eqs. 27-28, with the Dirichlet values) at cells ``ids``: [len(ids), 2]."""
+    lib = _load()
+    gs = _grid(g)
+    lam, x = _c64(lam), _c64(x)
+    ids = np.ascontiguousarray(ids, dtype=np.int64)
+    pa, ka = _faces(fa)
+    pk, kk = _faces(fk)
+    out = np.empty((ids.size, 2))
+    lib.orc_apply_rows(C.byref(gs), _dp(lam), pa, pk, _dp(x), ids.ctypes.data_as(C.POINTER(C.c_long)),
+                       int(ids.size), _dp(out))
+    return out

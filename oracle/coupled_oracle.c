@@ -723,3 +723,24 @@ done:
     free(Ls);
     return rc;
 }
+
+/* y at selected cells only: out[2*q..] = L(x) of Eqs. 27-28 at cell ids[q]
+ * (with the grid's Dirichlet values).  For checking residuals of large
+ * solutions at sampled cells. */
+void orc_apply_rows(const orc_grid *g, const double *lam, double *const fa[3], double *const fk[3],
+                    const double *x, const long *ids, long nids, double *out)
+{
+    double (*vT)[2] = (double (*)[2])g->bcT;
+    double (*vp)[2] = (double (*)[2])g->bcp;
+    for (long q = 0; q < nids; q++) {
+        long i = ids[q];
+        int c[3];
+        cell_of(g, i, c);
+        double lapT = div_flux(g, fk, x + 0, vT, c);
+        double lapp = div_flux(g, fa, x + 1, vp, c);
+        const double *l = lam + 4 * i;
+        double T = x[2 * i], p = x[2 * i + 1];
+        out[2 * q]     = lapT + l[0] * T + l[1] * p;            /* Eq. 27 */
+        out[2 * q + 1] = lapp + l[2] * p + l[3] * lapT;         /* Eq. 28 */
+    }
+}

@@ -1,0 +1,310 @@
+"""ctypes binding of libcoupledmg.so (include/coupledmg.h): argument marshalling only.
+
+Every step of the solve runs in the library's CUDA kernels.  PyTorch supplies
+device memory (the handle's workspace) and the CUDA stream.  If the library is
+missing this module raises: there is no CPU or Python fallback.
+
+Arrays may be numpy arrays (host; the library copies them to the device
+inside the call) or CUDA torch tensors (device; used in place).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+from typing import Optional, Sequence
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_build", "libcoupledmg.so")
+
+MG_OK, MG_ERR_INVALID_ARG, MG_ERR_OOM, MG_ERR_BUDGET, MG_ERR_INVALID_COEFF = 0, 1, 2, 3, 4
+MG_ERR_NOT_CONVERGED, MG_ERR_TIMEOUT, MG_ERR_CUDA, MG_ERR_STATE = 5, 6, 7, 8
+MG_FP64, MG_MIXED = 0, 1
+STATUS_NAMES = {0: "MG_OK", 1: "MG_ERR_INVALID_ARG", 2: "MG_ERR_OOM", 3: "MG_ERR_BUDGET",
+                4: "MG_ERR_INVALID_COEFF", 5: "MG_ERR_NOT_CONVERGED", 6: "MG_ERR_TIMEOUT",
+                7: "MG_ERR_CUDA", 8: "MG_ERR_STATE"}
+
+# every entry point the header declares (checked by the CPU tests)
+EXPORTS = ["mg_default_options", "mg_workspace_size", "mg_create", "mg_set_coeffs", "mg_solve",
+           "mg_apply", "mg_smooth", "mg_residual_norms", "mg_set_device", "mg_levels", "mg_destroy",
+           "mg_last_error", "mg_set_timing", "mg_counters"]
+
+
+class MgError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class MgGrid(C.Structure):
+    _fields_ = [("dim", C.c_int), ("axisym", C.c_int), ("n", C.c_int * 3), ("h", C.c_double),
+                ("r0", C.c_double), ("bc", (C.c_int * 2) * 3), ("bc_T", (C.c_double * 2) * 3),
+                ("bc_p", (C.c_double * 2) * 3)]
+
+
+class MgOptions(C.Structure):
+    _fields_ = [("nu1", C.c_int), ("nu2", C.c_int), ("precision", C.c_int), ("rtol", C.c_double),
+                ("max_cycles", C.c_int), ("coarse_min", C.c_int), ("inner_cycles", C.c_int)]
+
+
+class MgStats(C.Structure):
+    _fields_ = [("cycles", C.c_int), ("outer", C.c_int), ("r0", C.c_double * 2),
+                ("rfinal", C.c_double * 2), ("seconds", C.c_double), ("status", C.c_int),
+                ("levels", C.c_int)]
+
+    def as_dict(self) -> dict:
+        return dict(cycles=self.cycles, outer=self.outer, r0=list(self.r0), rfinal=list(self.rfinal),
+                    seconds=self.seconds, status=STATUS_NAMES.get(self.status, self.status),
+                    levels=self.levels)
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load(path: str = LIB_PATH):
+    """Loads the library (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise RuntimeError(f"libcoupledmg.so not built ({path}); run __graft_entry__.build()")
+        lib = C.CDLL(path)
+        P = C.c_void_p
+        dp = C.POINTER(C.c_double)
+        pa3 = C.c_void_p * 3
+        sig = {
+            "mg_default_options": ([C.POINTER(MgOptions)], C.c_int),
+            "mg_workspace_size": ([C.POINTER(MgGrid), C.POINTER(MgOptions), C.POINTER(C.c_size_t)], C.c_int),
+            "mg_create": ([C.POINTER(MgGrid), C.POINTER(MgOptions), P, C.c_size_t, P, C.POINTER(P)], C.c_int),
+            "mg_set_coeffs": ([P, P, pa3, pa3, C.c_int], C.c_int),
+            "mg_solve": ([P, P, P, C.c_int, C.POINTER(MgStats)], C.c_int),
+            "mg_apply": ([P, P, P, C.c_int], C.c_int),
+            "mg_smooth": ([P, P, P, C.c_int, C.c_int], C.c_int),
+            "mg_residual_norms": ([P, P, P, C.c_int, dp], C.c_int),
+            "mg_set_device": ([C.c_int], C.c_int),
+            "mg_levels": ([P, C.POINTER(C.c_int), C.POINTER(C.c_int)], C.c_int),
+            "mg_destroy": ([P], C.c_int),
+            "mg_last_error": ([], C.c_char_p),
+            "mg_set_timing": ([P, C.c_int], C.c_int),
+            "mg_counters": ([P, C.POINTER(C.c_longlong), C.POINTER(C.c_double), C.POINTER(C.c_longlong),
+                             C.POINTER(C.c_longlong)], C.c_int),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = lib
+    return _lib
+
+
+def last_error() -> str:
+    return load().mg_last_error().decode()
+
+
+def check(status: int, allow=(MG_OK,)) -> int:
+    if status not in allow:
+        raise MgError(status, last_error())
+    return status
+
+
+def make_grid(g) -> MgGrid:
+    """From an inputs.Grid, a dict with the same keys, or an MgGrid."""
+    if isinstance(g, MgGrid):
+        return g
+    get = (lambda k: g[k]) if isinstance(g, dict) else (lambda k: getattr(g, k))
+    s = MgGrid()
+    s.dim, s.axisym = int(get("dim")), int(get("axisym"))
+    n = list(get("n")) + [1] * (3 - len(get("n")))
+    for a in range(3):
+        s.n[a] = int(n[a])
+    s.h, s.r0 = float(get("h")), float(get("r0"))
+    bc, bT, bp = get("bc"), get("bcT"), get("bcp")
+    for a in range(3):
+        for side in range(2):
+            s.bc[a][side] = int(bc[a][side])
+            s.bc_T[a][side] = float(bT[a][side])
+            s.bc_p[a][side] = float(bp[a][side])
+    return s
+
+
+def make_options(precision="fp64", rtol=1e-10, max_cycles=50, nu1=2, nu2=2, coarse_min=4,
+                 inner_cycles=1) -> MgOptions:
+    o = MgOptions()
+    check(load().mg_default_options(C.byref(o)))
+    o.precision = MG_MIXED if precision in ("mixed", MG_MIXED) else MG_FP64
+    o.rtol, o.max_cycles, o.nu1, o.nu2 = float(rtol), int(max_cycles), int(nu1), int(nu2)
+    o.coarse_min, o.inner_cycles = int(coarse_min), int(inner_cycles)
+    return o
+
+
+def _is_torch(a) -> bool:
+    return type(a).__module__.startswith("torch")
+
+
+def _ptr(a, on_device: bool, dtype=np.float64):
+    """(pointer, keepalive) for a numpy array (host) or a CUDA tensor (device)."""
+    if on_device:
+        import torch
+        if not (_is_torch(a) and a.is_cuda and a.dtype == torch.float64 and a.is_contiguous()):
+            raise TypeError("device arrays must be contiguous float64 CUDA tensors")
+        return C.c_void_p(a.data_ptr()), a
+    arr = np.ascontiguousarray(a, dtype=dtype)
+    return C.c_void_p(arr.ctypes.data), arr
+
+
+def _side(*arrays) -> bool:
+    flags = {_is_torch(a) and a.is_cuda for a in arrays if a is not None}
+    if len(flags) > 1:
+        raise TypeError("mix of host and device arrays in one call")
+    return flags.pop() if flags else False
+
+
+class Solver:
+    """One mg_handle: a grid, its device hierarchy and a stream."""
+
+    def __init__(self, grid, precision="fp64", rtol=1e-10, max_cycles=50, nu1=2, nu2=2, coarse_min=4,
+                 inner_cycles=1, device: Optional[int] = None, stream=None, torch_workspace: bool = True):
+        import torch
+        lib = load()
+        self._lib = lib
+        self.grid = make_grid(grid)
+        self.options = make_options(precision, rtol, max_cycles, nu1, nu2, coarse_min, inner_cycles)
+        dev = torch.cuda.current_device() if device is None else int(device)
+        self.device = dev
+        check(lib.mg_set_device(dev))
+        nbytes = C.c_size_t()
+        check(lib.mg_workspace_size(C.byref(self.grid), C.byref(self.options), C.byref(nbytes)))
+        self.workspace_bytes = int(nbytes.value)
+        self._ws = None
+        ws_ptr = None
+        if torch_workspace:
+            self._ws = torch.empty(self.workspace_bytes, dtype=torch.uint8, device=f"cuda:{dev}")
+            ws_ptr = C.c_void_p(self._ws.data_ptr())
+        if stream is None:
+            stream = torch.cuda.current_stream(dev)
+        self.stream = stream
+        handle = C.c_void_p()
+        check(lib.mg_create(C.byref(self.grid), C.byref(self.options), ws_ptr, self.workspace_bytes,
+                            C.c_void_p(stream.cuda_stream), C.byref(handle)))
+        self._h = handle
+        self.N = self.grid.n[0] * self.grid.n[1] * self.grid.n[2]
+
+    # -------------------------------------------------------------- sizes
+    def nfaces(self, a: int) -> int:
+        n = [self.grid.n[0], self.grid.n[1], self.grid.n[2]]
+        n[a] += 1
+        return n[0] * n[1] * n[2]
+
+    @staticmethod
+    def _numel(a) -> int:
+        return int(a.numel()) if _is_torch(a) else int(np.asarray(a).size)
+
+    def _need(self, a, count: int, what: str):
+        if self._numel(a) != count:
+            raise ValueError(f"{what}: expected {count} values, got {self._numel(a)}")
+
+    # -------------------------------------------------------------- calls
+    def set_coeffs(self, lam, fa: Sequence, fk: Sequence):
+        self._need(lam, 4 * self.N, "lambda")
+        if len(fa) < self.grid.dim or len(fk) < self.grid.dim:
+            raise ValueError("one face array per axis is required")
+        for a in range(self.grid.dim):
+            self._need(fa[a], self.nfaces(a), f"face_alpha[{a}]")
+            self._need(fk[a], self.nfaces(a), f"face_k[{a}]")
+        dev = _side(lam, *fa[: self.grid.dim], *fk[: self.grid.dim])
+        lp, keep = _ptr(lam, dev)
+        pa = (C.c_void_p * 3)()
+        pk = (C.c_void_p * 3)()
+        keeps = [keep]
+        for a in range(self.grid.dim):
+            p1, k1 = _ptr(fa[a], dev)
+            p2, k2 = _ptr(fk[a], dev)
+            pa[a], pk[a] = p1, p2
+            keeps += [k1, k2]
+        check(self._lib.mg_set_coeffs(self._h, lp, pa, pk, int(dev)))
+
+    def solve(self, b, x, allow_not_converged: bool = False) -> dict:
+        """Solves in place: x (numpy float64 [N,2] or CUDA tensor) holds the
+        initial guess and receives the result.  Returns the stats."""
+        self._need(b, 2 * self.N, "rhs")
+        self._need(x, 2 * self.N, "x")
+        dev = _side(b, x)
+        bp, bk = _ptr(b, dev)
+        if not dev:
+            if not (isinstance(x, np.ndarray) and x.dtype == np.float64 and x.flags.c_contiguous):
+                raise TypeError("host x must be a C-contiguous float64 numpy array (solved in place)")
+        xp, xk = _ptr(x, dev)
+        st = MgStats()
+        allow = (MG_OK, MG_ERR_NOT_CONVERGED) if allow_not_converged else (MG_OK,)
+        check(self._lib.mg_solve(self._h, bp, xp, int(dev), C.byref(st)), allow)
+        return st.as_dict()
+
+    def apply(self, x):
+        self._need(x, 2 * self.N, "x")
+        dev = _side(x)
+        xp, xk = _ptr(x, dev)
+        if dev:
+            import torch
+            y = torch.empty_like(x)
+        else:
+            y = np.empty_like(xk)
+        yp, yk = _ptr(y, dev)
+        check(self._lib.mg_apply(self._h, xp, yp, int(dev)))
+        return y
+
+    def smooth(self, b, x, sweeps: int = 1):
+        self._need(b, 2 * self.N, "rhs")
+        self._need(x, 2 * self.N, "x")
+        if not _is_torch(x) and not (isinstance(x, np.ndarray) and x.dtype == np.float64 and x.flags.c_contiguous):
+            raise TypeError("host x must be a C-contiguous float64 numpy array (smoothed in place)")
+        dev = _side(b, x)
+        bp, bk = _ptr(b, dev)
+        xp, xk = _ptr(x, dev)
+        check(self._lib.mg_smooth(self._h, bp, xp, int(sweeps), int(dev)))
+        return x
+
+    def residual_norms(self, b, x) -> np.ndarray:
+        self._need(b, 2 * self.N, "rhs")
+        self._need(x, 2 * self.N, "x")
+        dev = _side(b, x)
+        bp, bk = _ptr(b, dev)
+        xp, xk = _ptr(x, dev)
+        out = (C.c_double * 2)()
+        check(self._lib.mg_residual_norms(self._h, bp, xp, int(dev), out))
+        return np.array(list(out))
+
+    def set_timing(self, enable: bool = True):
+        check(self._lib.mg_set_timing(self._h, int(enable)))
+
+    def counters(self) -> dict:
+        n, ms, sl, sc = C.c_longlong(), C.c_double(), C.c_longlong(), C.c_longlong()
+        check(self._lib.mg_counters(self._h, C.byref(n), C.byref(ms), C.byref(sl), C.byref(sc)))
+        return dict(launches=n.value, smooth_ms=ms.value, smooth_launches=sl.value, smooth_cells=sc.value)
+
+    def levels(self):
+        n = C.c_int()
+        sizes = (C.c_int * (3 * 32))()
+        check(self._lib.mg_levels(self._h, C.byref(n), sizes))
+        return [tuple(sizes[3 * l: 3 * l + 3]) for l in range(n.value)]
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.mg_destroy(self._h)
+            self._h = None
+        self._ws = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

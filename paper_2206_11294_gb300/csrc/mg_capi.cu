@@ -1,0 +1,812 @@
+// Host side of the C ABI declared in include/coupledmg.h: argument checks,
+// the device hierarchy (one arena), coefficient set-up, the V-cycle launch
+// sequence (captured once per handle as a CUDA graph and replayed), the FP64
+// defect-correction loop and the mixed-precision refinement loop.
+//
+// The outer loop is the paper's (Sec. 3, after Eq. 34): residual, stop test,
+// correction solve by one multigrid V-cycle, update.  The FP64 path runs the
+// V-cycle in place on x, which equals "correction from zero, then add" for a
+// linear cycle.  The mixed path solves the correction in FP32 from zero and
+// adds it in FP64.
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "coupledmg.h"
+#include "mg_kernels.cuh"
+
+using namespace cmg;
+
+namespace {
+
+constexpr int kMaxLevels = 32;
+constexpr int kMaxCoarseUnknowns = 1024;
+constexpr size_t kAlign = 256;
+
+thread_local std::string g_err;
+
+mg_status fail(mg_status s, const std::string &msg) {
+    g_err = msg;
+    return s;
+}
+
+#define CK(call)                                                                                  \
+    do {                                                                                          \
+        cudaError_t e_ = (call);                                                                  \
+        if (e_ != cudaSuccess)                                                                    \
+            return fail(MG_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));         \
+    } while (0)
+
+struct LevelBuf {
+    int n[3];
+    long long N;
+    long long nf[3];
+    double2 *x, *b;
+    double2 *G[3];
+    dq *D, *Dinv;
+    float2 *x32, *b32;
+    float2 *G32[3];
+    fq *D32, *Dinv32;
+};
+
+}  // namespace
+
+struct mg_handle {
+    mg_grid grid;
+    mg_options opt;
+    int device;
+    cudaStream_t stream;   // caller's stream: all work runs here
+    cudaStream_t cap;      // private stream used only to capture graphs
+    int nlev;
+    LevelBuf L[kMaxLevels];
+    char *arena;
+    size_t arena_bytes;
+    bool owns_arena;
+    double *lam4;
+    char *stage;
+    size_t stage_bytes;
+    int nc;                // unknowns of the coarsest level
+    double *Minv, *Mtmp;
+    float *Minv32;
+    double2 *partial;
+    int npartial;
+    double *norms_d;       // device: [2] latest norms
+    int *err_d;
+    double *norms_h;       // pinned host: [2]
+    bool coeffs_set;
+    cudaGraphExec_t g64, g32;   // FP64 cycle+norm; mixed inner cycles+update+residual
+    // instrumentation
+    long long enq;              // kernels launched since the last reset (graph nodes per replay)
+    long long graph_kernels64, graph_kernels32;
+    int timing;
+    cudaEvent_t ev[4];          // finest-level smoothing: pre start/end, post start/end
+    double smooth_ms;
+    long long smooth_launches;
+};
+
+namespace {
+
+// ---------------------------------------------------------------- validation
+bool can_coarsen(const int n[3], int dim, int coarse_min) {
+    for (int a = 0; a < dim; a++)
+        if (n[a] % 2 != 0 || n[a] / 2 < coarse_min) return false;
+    return true;
+}
+
+mg_status check_grid(const mg_grid *g, const mg_options *o) {
+    if (!g || !o) return fail(MG_ERR_INVALID_ARG, "grid and options must not be NULL");
+    if (g->dim != 2 && g->dim != 3) return fail(MG_ERR_INVALID_ARG, "dim must be 2 or 3");
+    if (g->axisym && g->dim != 2) return fail(MG_ERR_INVALID_ARG, "axisymmetric grids are 2D (r, z)");
+    for (int a = 0; a < 3; a++) {
+        if (g->n[a] < 1) return fail(MG_ERR_INVALID_ARG, "every n[a] must be >= 1");
+        if (a >= g->dim && g->n[a] != 1) return fail(MG_ERR_INVALID_ARG, "n[2] must be 1 for a 2D grid");
+    }
+    if (g->n[0] > (1 << 28) || g->n[1] > 8 * 65535 || g->n[2] > 65535)
+        return fail(MG_ERR_INVALID_ARG, "grid too large for the launch geometry (n1 <= 524280, n2 <= 65535)");
+    if (!(g->h > 0.0) || !std::isfinite(g->h)) return fail(MG_ERR_INVALID_ARG, "h must be positive and finite");
+    if (g->axisym && (!(g->r0 >= 0.0) || !std::isfinite(g->r0)))
+        return fail(MG_ERR_INVALID_ARG, "r0 must be >= 0 and finite");
+    for (int a = 0; a < g->dim; a++)
+        for (int s = 0; s < 2; s++) {
+            const int k = g->bc[a][s];
+            if (k != MG_BC_WALL && k != MG_BC_DIRICHLET && k != MG_BC_AXIS)
+                return fail(MG_ERR_INVALID_ARG, "unknown boundary kind");
+            if (k == MG_BC_AXIS && !(g->axisym && a == 0 && s == 0 && g->r0 == 0.0))
+                return fail(MG_ERR_INVALID_ARG, "MG_BC_AXIS only on the low-r side of an axisymmetric grid with r0 = 0");
+            if (k == MG_BC_DIRICHLET && (!std::isfinite(g->bc_T[a][s]) || !std::isfinite(g->bc_p[a][s])))
+                return fail(MG_ERR_INVALID_ARG, "Dirichlet values must be finite");
+        }
+    if (g->axisym && g->r0 == 0.0 && g->bc[0][0] == MG_BC_DIRICHLET)
+        return fail(MG_ERR_INVALID_ARG, "the symmetry axis (r0 = 0) cannot carry a Dirichlet condition");
+    if (o->nu1 < 0 || o->nu2 < 0 || o->nu1 > 16 || o->nu2 > 16 || o->nu1 + o->nu2 == 0)
+        return fail(MG_ERR_INVALID_ARG, "nu1, nu2 must be in 0..16 and not both zero");
+    if (o->precision != MG_FP64 && o->precision != MG_MIXED) return fail(MG_ERR_INVALID_ARG, "unknown precision");
+    if (o->max_cycles < 0 || o->coarse_min < 1 || o->inner_cycles < 1 || o->inner_cycles > 64)
+        return fail(MG_ERR_INVALID_ARG, "max_cycles >= 0, coarse_min >= 1, inner_cycles in 1..64");
+    if (!std::isfinite(o->rtol)) return fail(MG_ERR_INVALID_ARG, "rtol must be finite");
+    int n[3] = {g->n[0], g->n[1], g->n[2]}, lev = 1;
+    while (can_coarsen(n, g->dim, o->coarse_min) && lev < kMaxLevels) {
+        for (int a = 0; a < g->dim; a++) n[a] /= 2;
+        lev++;
+    }
+    const long long nc = 2LL * n[0] * n[1] * n[2];
+    if (nc > kMaxCoarseUnknowns)
+        return fail(MG_ERR_INVALID_ARG, "coarsest level has " + std::to_string(nc) + " unknowns (limit " +
+                                             std::to_string(kMaxCoarseUnknowns) +
+                                             "): choose sizes with more factors of two");
+    return MG_OK;
+}
+
+// ---------------------------------------------------------------- arena plan
+struct Planner {
+    char *base;       // NULL while sizing
+    size_t off = 0;
+    template <typename T> T *take(long long count) {
+        off = (off + kAlign - 1) / kAlign * kAlign;
+        T *p = base ? reinterpret_cast<T *>(base + off) : nullptr;
+        off += sizeof(T) * (size_t)count;
+        return p;
+    }
+};
+
+dim3 cell_grid(const LevelBuf &l, int dim, int xthreads) {
+    return dim3((unsigned)((xthreads + kBX - 1) / kBX), (unsigned)((l.n[1] + kBY - 1) / kBY),
+                (unsigned)(dim == 3 ? l.n[2] : 1));
+}
+
+// Lays out every buffer; with base == NULL only computes the size.
+void plan(mg_handle *h, char *base, size_t *bytes) {
+    Planner P{base};
+    const mg_grid &g = h->grid;
+    const bool mixed = h->opt.precision == MG_MIXED;
+    int n[3] = {g.n[0], g.n[1], g.n[2]};
+    h->nlev = 0;
+    for (;;) {
+        LevelBuf &l = h->L[h->nlev];
+        std::memset(&l, 0, sizeof(l));
+        for (int a = 0; a < 3; a++) l.n[a] = n[a];
+        l.N = (long long)n[0] * n[1] * n[2];
+        for (int a = 0; a < 3; a++) {
+            l.nf[a] = 1;
+            for (int b = 0; b < 3; b++) l.nf[a] *= (b == a) ? n[b] + 1 : n[b];
+        }
+        l.x = P.take<double2>(l.N);
+        l.b = P.take<double2>(l.N);
+        for (int a = 0; a < g.dim; a++) l.G[a] = P.take<double2>(l.nf[a]);
+        l.D = P.take<dq>(l.N);
+        l.Dinv = P.take<dq>(l.N);
+        if (mixed) {
+            l.x32 = P.take<float2>(l.N);
+            l.b32 = P.take<float2>(l.N);
+            for (int a = 0; a < g.dim; a++) l.G32[a] = P.take<float2>(l.nf[a]);
+            l.D32 = P.take<fq>(l.N);
+            l.Dinv32 = P.take<fq>(l.N);
+        }
+        h->nlev++;
+        if (!can_coarsen(n, g.dim, h->opt.coarse_min) || h->nlev == kMaxLevels) break;
+        for (int a = 0; a < g.dim; a++) n[a] /= 2;
+    }
+    const LevelBuf &f = h->L[0];
+    const LevelBuf &c = h->L[h->nlev - 1];
+    h->nc = (int)(2 * c.N);
+    h->lam4 = P.take<double>(f.N);
+    long long maxnf = 0;
+    for (int a = 0; a < g.dim; a++) maxnf = f.nf[a] > maxnf ? f.nf[a] : maxnf;
+    h->stage_bytes = (size_t)std::max<long long>(32 * f.N, 16 * maxnf);
+    h->stage = P.take<char>((long long)h->stage_bytes);
+    h->Minv = P.take<double>((long long)h->nc * h->nc);
+    h->Mtmp = P.take<double>((long long)h->nc * h->nc);
+    h->Minv32 = mixed ? P.take<float>((long long)h->nc * h->nc) : nullptr;
+    const dim3 gg = cell_grid(f, g.dim, f.n[0]);
+    h->npartial = (int)(gg.x * gg.y * gg.z);
+    h->partial = P.take<double2>(h->npartial);
+    h->norms_d = P.take<double>(8);
+    h->err_d = P.take<int>(1);
+    *bytes = P.off + kAlign;
+}
+
+template <typename R> Level<R> view(const LevelBuf &l);
+template <> Level<double> view<double>(const LevelBuf &l) {
+    return Level<double>{l.n[0], l.n[1], l.n[2], l.N, l.x, l.b, l.G[0], l.G[1], l.G[2], l.D, l.Dinv};
+}
+template <> Level<float> view<float>(const LevelBuf &l) {
+    return Level<float>{l.n[0], l.n[1], l.n[2], l.N, l.x32, l.b32, l.G32[0], l.G32[1], l.G32[2], l.D32, l.Dinv32};
+}
+
+BcFlags bc_flags(const mg_grid &g) {
+    BcFlags f;
+    for (int a = 0; a < 3; a++)
+        for (int s = 0; s < 2; s++) f.dir[a][s] = (a < g.dim && g.bc[a][s] == MG_BC_DIRICHLET) ? 1 : 0;
+    return f;
+}
+
+BcVals bc_vals(const mg_grid &g) {
+    BcVals v;
+    for (int a = 0; a < 3; a++)
+        for (int s = 0; s < 2; s++) {
+            v.dir[a][s] = (a < g.dim && g.bc[a][s] == MG_BC_DIRICHLET) ? 1 : 0;
+            v.T[a][s] = g.bc_T[a][s];
+            v.p[a][s] = g.bc_p[a][s];
+        }
+    return v;
+}
+
+dim3 kBlock(kBX, kBY, 1);
+
+unsigned lin_blocks(long long n) {
+    long long b = (n + 255) / 256;
+    return (unsigned)(b < 1 ? 1 : (b > 152 * 16 ? 152 * 16 : b));
+}
+
+// ---------------------------------------------------------------- V-cycle
+inline void counted(const mg_handle *h, long long n = 1) { const_cast<mg_handle *>(h)->enq += n; }
+
+template <typename R, int DIM>
+void enqueue_smooth(const mg_handle *h, cudaStream_t s, int l, int sweeps) {
+    const LevelBuf &lb = h->L[l];
+    const dim3 gr = cell_grid(lb, DIM, (lb.n[0] + 1) / 2);
+    const Level<R> v = view<R>(lb);
+    for (int q = 0; q < sweeps; q++) {
+        k_rbgs_colour<R, DIM><<<gr, kBlock, 0, s>>>(v, 0);
+        k_rbgs_colour<R, DIM><<<gr, kBlock, 0, s>>>(v, 1);
+        counted(h, 2);
+    }
+}
+
+template <typename R> const R *coarse_inverse(const mg_handle *h);
+template <> const double *coarse_inverse<double>(const mg_handle *h) { return h->Minv; }
+template <> const float *coarse_inverse<float>(const mg_handle *h) { return h->Minv32; }
+
+template <typename R, int DIM>
+void enqueue_vcycle(const mg_handle *h, cudaStream_t s, int l) {
+    const LevelBuf &lb = h->L[l];
+    if (l == h->nlev - 1) {
+        const Level<R> v = view<R>(lb);
+        const int threads = 256;
+        const unsigned blocks = (unsigned)((h->nc * 32LL + threads - 1) / threads);
+        k_coarse_matvec<R><<<blocks, threads, 0, s>>>(coarse_inverse<R>(h), reinterpret_cast<const R *>(v.b),
+                                                      reinterpret_cast<R *>(v.x), h->nc);
+        counted(h);
+        return;
+    }
+    const LevelBuf &cb = h->L[l + 1];
+    const bool tm = h->timing && l == 0;
+    if (tm) cudaEventRecord(h->ev[0], s);
+    enqueue_smooth<R, DIM>(h, s, l, h->opt.nu1);
+    if (tm) cudaEventRecord(h->ev[1], s);
+    k_residual_restrict<R, DIM><<<cell_grid(cb, DIM, cb.n[0]), kBlock, 0, s>>>(view<R>(lb), view<R>(cb));
+    counted(h);
+    enqueue_vcycle<R, DIM>(h, s, l + 1);
+    k_prolong_add<R, DIM><<<cell_grid(lb, DIM, lb.n[0]), kBlock, 0, s>>>(view<R>(cb), view<R>(lb), bc_flags(h->grid));
+    counted(h);
+    if (tm) cudaEventRecord(h->ev[2], s);
+    enqueue_smooth<R, DIM>(h, s, l, h->opt.nu2);
+    if (tm) cudaEventRecord(h->ev[3], s);
+}
+
+template <int DIM>
+void enqueue_norm(const mg_handle *h, cudaStream_t s) {
+    const LevelBuf &f = h->L[0];
+    k_norm_partials<DIM><<<cell_grid(f, DIM, f.n[0]), kBlock, 0, s>>>(view<double>(f), h->partial);
+    k_reduce_norms<<<1, kReduceThreads, 0, s>>>(h->partial, h->npartial, h->norms_d);
+    counted(h, 2);
+}
+
+template <int DIM>
+void enqueue_residual_to32(const mg_handle *h, cudaStream_t s) {
+    const LevelBuf &f = h->L[0];
+    k_residual64_to32<DIM><<<cell_grid(f, DIM, f.n[0]), kBlock, 0, s>>>(view<double>(f), f.b32, f.x32, h->partial);
+    k_reduce_norms<<<1, kReduceThreads, 0, s>>>(h->partial, h->npartial, h->norms_d);
+    counted(h, 2);
+}
+
+// FP64: one V-cycle, then the stopping norm, copied to pinned host memory.
+template <int DIM>
+void enqueue_cycle64(const mg_handle *h, cudaStream_t s) {
+    enqueue_vcycle<double, DIM>(h, s, 0);
+    enqueue_norm<DIM>(h, s);
+    cudaMemcpyAsync(h->norms_h, h->norms_d, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
+}
+
+// Mixed: FP32 V-cycles on the correction, FP64 update, FP64 residual + norm.
+template <int DIM>
+void enqueue_step32(const mg_handle *h, cudaStream_t s) {
+    for (int q = 0; q < h->opt.inner_cycles; q++) enqueue_vcycle<float, DIM>(h, s, 0);
+    const LevelBuf &f = h->L[0];
+    k_add_correction<<<lin_blocks(f.N), 256, 0, s>>>(f.x, f.x32, f.N);
+    counted(h);
+    enqueue_residual_to32<DIM>(h, s);
+    cudaMemcpyAsync(h->norms_h, h->norms_d, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
+}
+
+template <typename F>
+mg_status capture(mg_handle *h, cudaGraphExec_t *out, long long *kernels, F &&body) {
+    cudaGraph_t graph = nullptr;
+    CK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
+    const long long before = h->enq;
+    body(h->cap);
+    *kernels = h->enq - before;
+    h->enq = before;
+    cudaError_t e = cudaStreamEndCapture(h->cap, &graph);
+    if (e != cudaSuccess) return fail(MG_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(out, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return fail(MG_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    return MG_OK;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+// Brings a [N][2] pair array to the device: the caller's pointer itself when
+// on_device, else a copy in the staging area.
+mg_status pair_in(mg_handle *h, const double *src, int on_device, const double2 **dev) {
+    const long long N = h->L[0].N;
+    if (on_device) {
+        if (!aligned16(src)) return fail(MG_ERR_INVALID_ARG, "device pair arrays must be 16-byte aligned");
+        *dev = reinterpret_cast<const double2 *>(src);
+        return MG_OK;
+    }
+    CK(cudaMemcpyAsync(h->stage, src, sizeof(double2) * N, cudaMemcpyHostToDevice, h->stream));
+    *dev = reinterpret_cast<const double2 *>(h->stage);
+    return MG_OK;
+}
+
+mg_status x_in(mg_handle *h, const double *x, int on_device) {
+    const long long N = h->L[0].N;
+    if (on_device && !aligned16(x)) return fail(MG_ERR_INVALID_ARG, "device pair arrays must be 16-byte aligned");
+    CK(cudaMemcpyAsync(h->L[0].x, x, sizeof(double2) * N, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                       h->stream));
+    return MG_OK;
+}
+
+mg_status x_out(mg_handle *h, double *x, int on_device) {
+    const long long N = h->L[0].N;
+    CK(cudaMemcpyAsync(x, h->L[0].x, sizeof(double2) * N, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                       h->stream));
+    return MG_OK;
+}
+
+template <int DIM>
+void enqueue_prep(mg_handle *h, const double2 *rhs) {
+    const LevelBuf &f = h->L[0];
+    k_prep_rhs<DIM><<<cell_grid(f, DIM, f.n[0]), kBlock, 0, h->stream>>>(view<double>(f), rhs, h->lam4, bc_vals(h->grid),
+                                                                          h->grid.axisym, h->grid.r0, h->grid.h);
+    counted(h);
+}
+
+mg_status prep(mg_handle *h, const double *rhs, const double *x, int on_device) {
+    const double2 *r = nullptr;
+    mg_status st = pair_in(h, rhs, on_device, &r);
+    if (st) return st;
+    if ((st = x_in(h, x, on_device))) return st;
+    if (h->grid.dim == 2) enqueue_prep<2>(h, r);
+    else enqueue_prep<3>(h, r);
+    CK(cudaGetLastError());
+    return MG_OK;
+}
+
+mg_status sync_norms(mg_handle *h, double out[2]) {
+    CK(cudaStreamSynchronize(h->stream));
+    out[0] = h->norms_h[0];
+    out[1] = h->norms_h[1];
+    return MG_OK;
+}
+
+// After a synchronised cycle: add the finest-level smoothing time it recorded.
+mg_status accumulate_timing(mg_handle *h) {
+    if (!h->timing || h->L[0].N == 0 || h->nlev < 2) return MG_OK;
+    float a = 0.f, b = 0.f;
+    CK(cudaEventElapsedTime(&a, h->ev[0], h->ev[1]));
+    CK(cudaEventElapsedTime(&b, h->ev[2], h->ev[3]));
+    h->smooth_ms += (double)a + (double)b;
+    h->smooth_launches += 2LL * (h->opt.nu1 + h->opt.nu2);
+    return MG_OK;
+}
+
+bool converged(const double n0[2], const double nk[2], double rtol) {
+    if (!(rtol > 0.0)) return false;
+    for (int f = 0; f < 2; f++) {
+        const double q = n0[f] > 0.0 ? nk[f] / n0[f] : 0.0;
+        if (!(q <= rtol)) return false;
+    }
+    return true;
+}
+
+// ---------------------------------------------------------------- set-up
+template <int DIM>
+mg_status setup_hierarchy(mg_handle *h, const double *lam, const double *const fa[3], const double *const fk[3],
+                          int on_device) {
+    const mg_grid &g = h->grid;
+    cudaStream_t s = h->stream;
+    LevelBuf &f = h->L[0];
+    CK(cudaMemsetAsync(h->err_d, 0, sizeof(int), s));
+    const double *lam_d = lam;
+    if (!on_device) {
+        CK(cudaMemcpyAsync(h->stage, lam, sizeof(double) * 4 * f.N, cudaMemcpyHostToDevice, s));
+        lam_d = reinterpret_cast<const double *>(h->stage);
+    }
+    k_block0<<<lin_blocks(f.N), 256, 0, s>>>(lam_d, f.n[0], f.N, g.axisym, g.r0, g.h, f.D, h->lam4, h->err_d);
+    CK(cudaGetLastError());
+    for (int a = 0; a < DIM; a++) {
+        const double *al = fa[a], *kk = fk[a];
+        if (!on_device) {
+            // the lambda copy above is consumed in stream order before this overwrite
+            double *st = reinterpret_cast<double *>(h->stage);
+            CK(cudaMemcpyAsync(st, fa[a], sizeof(double) * f.nf[a], cudaMemcpyHostToDevice, s));
+            CK(cudaMemcpyAsync(st + f.nf[a], fk[a], sizeof(double) * f.nf[a], cudaMemcpyHostToDevice, s));
+            al = st;
+            kk = st + f.nf[a];
+        }
+        FaceGeom fg;
+        for (int q = 0; q < 3; q++) fg.n[q] = f.n[q];
+        fg.axis = a;
+        fg.axisym = g.axisym;
+        fg.r0 = g.r0;
+        fg.h = g.h;
+        for (int sd = 0; sd < 2; sd++) fg.fac[sd] = g.bc[a][sd] == MG_BC_DIRICHLET ? 2.0 : 0.0;
+        k_faces0<<<lin_blocks(f.nf[a]), 256, 0, s>>>(fg, al, kk, f.G[a], f.nf[a], h->err_d);
+        CK(cudaGetLastError());
+    }
+    for (int l = 1; l < h->nlev; l++) {
+        const LevelBuf &F = h->L[l - 1];
+        LevelBuf &C = h->L[l];
+        k_coarsen_blocks<DIM><<<lin_blocks(C.N), 256, 0, s>>>(F.D, F.n[0], F.n[1], C.D, C.n[0], C.n[1], C.n[2]);
+        for (int a = 0; a < DIM; a++)
+            k_coarsen_faces<DIM><<<lin_blocks(C.nf[a]), 256, 0, s>>>(a, F.G[a], F.n[0], F.n[1], C.G[a], C.n[0],
+                                                                      C.n[1], C.n[2]);
+        CK(cudaGetLastError());
+    }
+    for (int l = 0; l < h->nlev; l++) {
+        LevelBuf &lb = h->L[l];
+        k_diag<DIM><<<lin_blocks(lb.N), 256, 0, s>>>(lb.n[0], lb.n[1], lb.n[2], lb.G[0], lb.G[1],
+                                                     DIM == 3 ? lb.G[2] : nullptr, lb.D, lb.Dinv, h->err_d);
+        CK(cudaGetLastError());
+    }
+    const LevelBuf &c = h->L[h->nlev - 1];
+    CK(cudaMemsetAsync(h->Mtmp, 0, sizeof(double) * h->nc * h->nc, s));
+    k_coarse_assemble<DIM><<<lin_blocks(c.N), 256, 0, s>>>(c.n[0], c.n[1], c.n[2], c.G[0], c.G[1],
+                                                           DIM == 3 ? c.G[2] : nullptr, c.D, h->Mtmp);
+    k_gauss_jordan<<<1, 1024, 0, s>>>(h->Mtmp, h->Minv, h->nc, h->err_d);
+    CK(cudaGetLastError());
+    if (h->opt.precision == MG_MIXED) {
+        for (int l = 0; l < h->nlev; l++) {
+            LevelBuf &lb = h->L[l];
+            for (int a = 0; a < DIM; a++)
+                k_to_f32_v2<<<lin_blocks(lb.nf[a]), 256, 0, s>>>(lb.G[a], lb.G32[a], lb.nf[a]);
+            k_to_f32_q<<<lin_blocks(lb.N), 256, 0, s>>>(lb.D, lb.D32, lb.N);
+            k_to_f32_q<<<lin_blocks(lb.N), 256, 0, s>>>(lb.Dinv, lb.Dinv32, lb.N);
+        }
+        k_to_f32<<<lin_blocks((long long)h->nc * h->nc), 256, 0, s>>>(h->Minv, h->Minv32, (long long)h->nc * h->nc);
+        CK(cudaGetLastError());
+    }
+    counted(h, 1 + DIM + (h->nlev - 1) * (1 + DIM) + h->nlev + 2 +
+                   (h->opt.precision == MG_MIXED ? h->nlev * (DIM + 2) + 1 : 0));
+    int err = 0;
+    CK(cudaMemcpyAsync(&err, h->err_d, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (err & 1) return fail(MG_ERR_INVALID_COEFF, "non-finite coefficient in lambda or the face arrays");
+    if (err & 2) return fail(MG_ERR_INVALID_COEFF, "a local 2x2 block is singular or not finite");
+    if (err & 4) return fail(MG_ERR_INVALID_COEFF, "the coarsest-level matrix is singular");
+    return MG_OK;
+}
+
+// ---------------------------------------------------------------- solves
+template <int DIM>
+mg_status solve64(mg_handle *h, mg_stats *st) {
+    double n0[2], nk[2];
+    enqueue_norm<DIM>(h, h->stream);
+    CK(cudaMemcpyAsync(h->norms_h, h->norms_d, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    mg_status e = sync_norms(h, n0);
+    if (e) return e;
+    nk[0] = n0[0];
+    nk[1] = n0[1];
+    if (!h->g64) {
+        e = capture(h, &h->g64, &h->graph_kernels64, [&](cudaStream_t s) { enqueue_cycle64<DIM>(h, s); });
+        if (e) return e;
+    }
+    int cyc = 0;
+    bool ok = converged(n0, nk, h->opt.rtol) || (n0[0] == 0.0 && n0[1] == 0.0);
+    while (!ok && cyc < h->opt.max_cycles) {
+        CK(cudaGraphLaunch(h->g64, h->stream));
+        h->enq += h->graph_kernels64;
+        if ((e = sync_norms(h, nk))) return e;
+        if ((e = accumulate_timing(h))) return e;
+        cyc++;
+        ok = converged(n0, nk, h->opt.rtol);
+    }
+    st->cycles = cyc;
+    st->outer = cyc;
+    st->r0[0] = n0[0];
+    st->r0[1] = n0[1];
+    st->rfinal[0] = nk[0];
+    st->rfinal[1] = nk[1];
+    st->status = (ok || !(h->opt.rtol > 0.0)) ? MG_OK : MG_ERR_NOT_CONVERGED;
+    return MG_OK;
+}
+
+template <int DIM>
+mg_status solve_mixed(mg_handle *h, mg_stats *st) {
+    double n0[2], nk[2];
+    enqueue_residual_to32<DIM>(h, h->stream);
+    CK(cudaMemcpyAsync(h->norms_h, h->norms_d, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    mg_status e = sync_norms(h, n0);
+    if (e) return e;
+    nk[0] = n0[0];
+    nk[1] = n0[1];
+    if (!h->g32) {
+        e = capture(h, &h->g32, &h->graph_kernels32, [&](cudaStream_t s) { enqueue_step32<DIM>(h, s); });
+        if (e) return e;
+    }
+    int outer = 0;
+    bool ok = converged(n0, nk, h->opt.rtol) || (n0[0] == 0.0 && n0[1] == 0.0);
+    while (!ok && outer < h->opt.max_cycles) {
+        CK(cudaGraphLaunch(h->g32, h->stream));
+        h->enq += h->graph_kernels32;
+        if ((e = sync_norms(h, nk))) return e;
+        if ((e = accumulate_timing(h))) return e;
+        outer++;
+        ok = converged(n0, nk, h->opt.rtol);
+    }
+    st->cycles = outer * h->opt.inner_cycles;
+    st->outer = outer;
+    st->r0[0] = n0[0];
+    st->r0[1] = n0[1];
+    st->rfinal[0] = nk[0];
+    st->rfinal[1] = nk[1];
+    st->status = (ok || !(h->opt.rtol > 0.0)) ? MG_OK : MG_ERR_NOT_CONVERGED;
+    return MG_OK;
+}
+
+mg_status check_handle(const mg_handle *h, bool need_coeffs) {
+    if (!h) return fail(MG_ERR_INVALID_ARG, "handle is NULL");
+    if (need_coeffs && !h->coeffs_set) return fail(MG_ERR_STATE, "mg_set_coeffs has not succeeded on this handle");
+    return MG_OK;
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+extern "C" {
+
+mg_status mg_default_options(mg_options *o) {
+    if (!o) return fail(MG_ERR_INVALID_ARG, "options is NULL");
+    o->nu1 = 2;
+    o->nu2 = 2;
+    o->precision = MG_FP64;
+    o->rtol = 1e-10;
+    o->max_cycles = 50;
+    o->coarse_min = 4;
+    o->inner_cycles = 1;
+    return MG_OK;
+}
+
+mg_status mg_workspace_size(const mg_grid *grid, const mg_options *opt, size_t *bytes) {
+    mg_status st = check_grid(grid, opt);
+    if (st) return st;
+    if (!bytes) return fail(MG_ERR_INVALID_ARG, "bytes is NULL");
+    mg_handle tmp;
+    std::memset(&tmp, 0, sizeof(tmp));
+    tmp.grid = *grid;
+    tmp.opt = *opt;
+    plan(&tmp, nullptr, bytes);
+    return MG_OK;
+}
+
+mg_status mg_create(const mg_grid *grid, const mg_options *opt, void *workspace, size_t workspace_bytes, void *stream,
+                    mg_handle **out) {
+    mg_status st = check_grid(grid, opt);
+    if (st) return st;
+    if (!out) return fail(MG_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    mg_handle *h = new (std::nothrow) mg_handle;
+    if (!h) return fail(MG_ERR_OOM, "host allocation failed");
+    std::memset(h, 0, sizeof(*h));
+    h->grid = *grid;
+    h->opt = *opt;
+    h->stream = reinterpret_cast<cudaStream_t>(stream);
+    cudaGetDevice(&h->device);
+    size_t need = 0;
+    plan(h, nullptr, &need);
+    char *base = nullptr;
+    if (workspace) {
+        if (workspace_bytes < need) {
+            delete h;
+            return fail(MG_ERR_BUDGET, "workspace of " + std::to_string(workspace_bytes) + " bytes, need " +
+                                           std::to_string(need));
+        }
+        base = static_cast<char *>(workspace);
+    } else {
+        cudaError_t e = cudaMalloc(&base, need);
+        if (e != cudaSuccess) {
+            delete h;
+            cudaGetLastError();
+            return fail(MG_ERR_OOM, std::string("cudaMalloc of the hierarchy failed: ") + cudaGetErrorString(e));
+        }
+        h->owns_arena = true;
+    }
+    char *aligned = reinterpret_cast<char *>((reinterpret_cast<uintptr_t>(base) + kAlign - 1) / kAlign * kAlign);
+    h->arena = base;
+    h->arena_bytes = need;
+    size_t dummy;
+    plan(h, aligned, &dummy);
+    if (cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaMallocHost(&h->norms_h, 8 * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        mg_destroy(h);
+        return fail(MG_ERR_CUDA, "stream or pinned buffer creation failed");
+    }
+    *out = h;
+    return MG_OK;
+}
+
+mg_status mg_set_coeffs(mg_handle *h, const double *lambda, const double *const face_alpha[3],
+                        const double *const face_k[3], int on_device) {
+    mg_status st = check_handle(h, false);
+    if (st) return st;
+    if (!lambda || !face_alpha || !face_k) return fail(MG_ERR_INVALID_ARG, "NULL coefficient pointer");
+    for (int a = 0; a < h->grid.dim; a++)
+        if (!face_alpha[a] || !face_k[a]) return fail(MG_ERR_INVALID_ARG, "NULL face array");
+    if (on_device) {
+        if ((reinterpret_cast<uintptr_t>(lambda) & 7u) != 0) return fail(MG_ERR_INVALID_ARG, "lambda misaligned");
+        for (int a = 0; a < h->grid.dim; a++)
+            if ((reinterpret_cast<uintptr_t>(face_alpha[a]) & 7u) || (reinterpret_cast<uintptr_t>(face_k[a]) & 7u))
+                return fail(MG_ERR_INVALID_ARG, "face array misaligned");
+    }
+    DeviceGuard dg(h->device);
+    h->coeffs_set = false;
+    st = h->grid.dim == 2 ? setup_hierarchy<2>(h, lambda, face_alpha, face_k, on_device)
+                          : setup_hierarchy<3>(h, lambda, face_alpha, face_k, on_device);
+    if (st == MG_OK) h->coeffs_set = true;
+    return st;
+}
+
+mg_status mg_solve(mg_handle *h, const double *rhs, double *x, int on_device, mg_stats *stats) {
+    const auto t0 = std::chrono::steady_clock::now();
+    mg_status st = check_handle(h, true);
+    if (st) return st;
+    if (!rhs || !x) return fail(MG_ERR_INVALID_ARG, "rhs and x must not be NULL");
+    DeviceGuard dg(h->device);
+    if ((st = prep(h, rhs, x, on_device))) return st;
+    mg_stats s;
+    std::memset(&s, 0, sizeof(s));
+    s.levels = h->nlev;
+    const int dim = h->grid.dim;
+    if (h->opt.precision == MG_FP64) st = dim == 2 ? solve64<2>(h, &s) : solve64<3>(h, &s);
+    else st = dim == 2 ? solve_mixed<2>(h, &s) : solve_mixed<3>(h, &s);
+    if (st) return st;
+    if ((st = x_out(h, x, on_device))) return st;
+    CK(cudaStreamSynchronize(h->stream));
+    s.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (stats) *stats = s;
+    if (s.status != MG_OK) {
+        g_err = "not converged after " + std::to_string(h->opt.max_cycles) + " cycles";
+        return (mg_status)s.status;
+    }
+    return MG_OK;
+}
+
+mg_status mg_apply(mg_handle *h, const double *x, double *y, int on_device) {
+    mg_status st = check_handle(h, true);
+    if (st) return st;
+    if (!x || !y) return fail(MG_ERR_INVALID_ARG, "x and y must not be NULL");
+    if (on_device && !aligned16(y)) return fail(MG_ERR_INVALID_ARG, "device pair arrays must be 16-byte aligned");
+    DeviceGuard dg(h->device);
+    if ((st = x_in(h, x, on_device))) return st;
+    const LevelBuf &f = h->L[0];
+    double2 *yd = on_device ? reinterpret_cast<double2 *>(y) : reinterpret_cast<double2 *>(h->stage);
+    if (h->grid.dim == 2)
+        k_apply_paper<2><<<cell_grid(f, 2, f.n[0]), kBlock, 0, h->stream>>>(view<double>(f), h->lam4, bc_vals(h->grid),
+                                                                            h->grid.axisym, h->grid.r0, h->grid.h, yd);
+    else
+        k_apply_paper<3><<<cell_grid(f, 3, f.n[0]), kBlock, 0, h->stream>>>(view<double>(f), h->lam4, bc_vals(h->grid),
+                                                                            h->grid.axisym, h->grid.r0, h->grid.h, yd);
+    counted(h);
+    CK(cudaGetLastError());
+    if (!on_device) CK(cudaMemcpyAsync(y, yd, sizeof(double2) * f.N, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return MG_OK;
+}
+
+mg_status mg_smooth(mg_handle *h, const double *rhs, double *x, int sweeps, int on_device) {
+    mg_status st = check_handle(h, true);
+    if (st) return st;
+    if (!rhs || !x || sweeps < 0) return fail(MG_ERR_INVALID_ARG, "bad arguments to mg_smooth");
+    DeviceGuard dg(h->device);
+    if ((st = prep(h, rhs, x, on_device))) return st;
+    if (h->grid.dim == 2) enqueue_smooth<double, 2>(h, h->stream, 0, sweeps);
+    else enqueue_smooth<double, 3>(h, h->stream, 0, sweeps);
+    CK(cudaGetLastError());
+    if ((st = x_out(h, x, on_device))) return st;
+    CK(cudaStreamSynchronize(h->stream));
+    return MG_OK;
+}
+
+mg_status mg_residual_norms(mg_handle *h, const double *rhs, const double *x, int on_device, double out[2]) {
+    mg_status st = check_handle(h, true);
+    if (st) return st;
+    if (!rhs || !x || !out) return fail(MG_ERR_INVALID_ARG, "bad arguments to mg_residual_norms");
+    DeviceGuard dg(h->device);
+    if ((st = prep(h, rhs, x, on_device))) return st;
+    if (h->grid.dim == 2) enqueue_norm<2>(h, h->stream);
+    else enqueue_norm<3>(h, h->stream);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(h->norms_h, h->norms_d, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    return sync_norms(h, out);
+}
+
+mg_status mg_set_timing(mg_handle *h, int enable) {
+    mg_status st = check_handle(h, false);
+    if (st) return st;
+    DeviceGuard dg(h->device);
+    CK(cudaStreamSynchronize(h->stream));
+    if (enable && !h->ev[0])
+        for (int q = 0; q < 4; q++) CK(cudaEventCreate(&h->ev[q]));
+    // re-capture the cycle graphs with (or without) the event nodes
+    if (h->g64) { cudaGraphExecDestroy(h->g64); h->g64 = nullptr; }
+    if (h->g32) { cudaGraphExecDestroy(h->g32); h->g32 = nullptr; }
+    h->timing = enable ? 1 : 0;
+    h->enq = 0;
+    h->smooth_ms = 0.0;
+    h->smooth_launches = 0;
+    return MG_OK;
+}
+
+mg_status mg_counters(const mg_handle *h, long long *launches, double *smooth_ms, long long *smooth_launches,
+                      long long *smooth_cells) {
+    mg_status st = check_handle(h, false);
+    if (st) return st;
+    if (launches) *launches = h->enq;
+    if (smooth_ms) *smooth_ms = h->smooth_ms;
+    if (smooth_launches) *smooth_launches = h->smooth_launches;
+    if (smooth_cells) *smooth_cells = h->L[0].N;
+    return MG_OK;
+}
+
+mg_status mg_set_device(int device) {
+    CK(cudaSetDevice(device));
+    return MG_OK;
+}
+
+mg_status mg_levels(const mg_handle *h, int *levels, int *n_out) {
+    mg_status st = check_handle(h, false);
+    if (st) return st;
+    if (levels) *levels = h->nlev;
+    if (n_out)
+        for (int l = 0; l < h->nlev; l++)
+            for (int a = 0; a < 3; a++) n_out[3 * l + a] = h->L[l].n[a];
+    return MG_OK;
+}
+
+mg_status mg_destroy(mg_handle *h) {
+    if (!h) return MG_OK;
+    DeviceGuard dg(h->device);
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    if (h->g64) cudaGraphExecDestroy(h->g64);
+    if (h->g32) cudaGraphExecDestroy(h->g32);
+    if (h->cap) cudaStreamDestroy(h->cap);
+    for (int q = 0; q < 4; q++)
+        if (h->ev[q]) cudaEventDestroy(h->ev[q]);
+    if (h->norms_h) cudaFreeHost(h->norms_h);
+    if (h->owns_arena && h->arena) cudaFree(h->arena);
+    delete h;
+    return MG_OK;
+}
+
+const char *mg_last_error(void) { return g_err.c_str(); }
+
+}  // extern "C"

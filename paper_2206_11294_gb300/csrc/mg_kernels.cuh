@@ -1,0 +1,590 @@
+// CUDA kernels of the coupled p-T multigrid: set-up, smoothing, residual,
+// restriction, prolongation, coarsest solve, norms.  Templated on the real
+// type R (double: FP64 path and the FP64 side of mixed precision; float: the
+// inner cycles of mixed precision) and on the dimension.
+//
+// The system each level holds is described in mg_types.cuh.
+#pragma once
+#include "mg_types.cuh"
+
+namespace cmg {
+
+constexpr int kBX = 32;   // block shape of the 2D/3D cell kernels
+constexpr int kBY = 8;
+constexpr int kReduceThreads = 256;
+
+template <typename R> __device__ __forceinline__ typename Vec<R>::v2 mk2(R a, R b);
+template <> __device__ __forceinline__ double2 mk2<double>(double a, double b) { return make_double2(a, b); }
+template <> __device__ __forceinline__ float2 mk2<float>(float a, float b) { return make_float2(a, b); }
+
+template <typename V> __device__ __forceinline__ V ldg2(const V *p) { return __ldg(p); }
+__device__ __forceinline__ dq ldgq(const dq *p) {
+    const double2 *q = reinterpret_cast<const double2 *>(p);
+    double2 u = __ldg(q), v = __ldg(q + 1);
+    return dq{u.x, u.y, v.x, v.y};
+}
+__device__ __forceinline__ fq ldgq(const fq *p) {
+    float4 u = __ldg(reinterpret_cast<const float4 *>(p));
+    return fq{u.x, u.y, u.z, u.w};
+}
+
+// Off-diagonal part of a row: sum over interior faces of G_f * u_nb (per field).
+// Neighbours beyond the grid contribute nothing (homogeneous boundary values;
+// inhomogeneous Dirichlet data are folded into the right-hand side).
+template <typename R, int DIM>
+__device__ __forceinline__ void offdiag(const Level<R> &L, const typename Vec<R>::v2 *__restrict__ x,
+                                        int i, int j, int k, long long c, R &sT, R &sp) {
+    using V2 = typename Vec<R>::v2;
+    const int n0 = L.n0, n1 = L.n1;
+    sT = R(0);
+    sp = R(0);
+    const long long f0 = (long long)i + (long long)(n0 + 1) * ((long long)j + (long long)n1 * k);
+    if (i > 0)      { V2 g = ldg2(L.G0 + f0);     V2 u = ldg2(x + c - 1);  sT += g.x * u.x; sp += g.y * u.y; }
+    if (i < n0 - 1) { V2 g = ldg2(L.G0 + f0 + 1); V2 u = ldg2(x + c + 1);  sT += g.x * u.x; sp += g.y * u.y; }
+    const long long f1 = (long long)i + (long long)n0 * ((long long)j + (long long)(n1 + 1) * k);
+    if (j > 0)      { V2 g = ldg2(L.G1 + f1);      V2 u = ldg2(x + c - n0); sT += g.x * u.x; sp += g.y * u.y; }
+    if (j < n1 - 1) { V2 g = ldg2(L.G1 + f1 + n0); V2 u = ldg2(x + c + n0); sT += g.x * u.x; sp += g.y * u.y; }
+    if (DIM == 3) {
+        const long long pl = (long long)n0 * n1;
+        if (k > 0)        { V2 g = ldg2(L.G2 + c);      V2 u = ldg2(x + c - pl); sT += g.x * u.x; sp += g.y * u.y; }
+        if (k < L.n2 - 1) { V2 g = ldg2(L.G2 + c + pl); V2 u = ldg2(x + c + pl); sT += g.x * u.x; sp += g.y * u.y; }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Smoothing: one colour of a red-black block Gauss-Seidel sweep.  Each thread
+// owns one cell of the colour (red: i+j+k even) and solves its 2x2 block:
+//   x_i = Dinv_i (b_i - sum_f G_f x_nb).
+// Neighbours are of the other colour and are not written by this launch.
+// ---------------------------------------------------------------------------
+template <typename R, int DIM>
+__global__ void __launch_bounds__(kBX * kBY) k_rbgs_colour(Level<R> L, int colour) {
+    using V2 = typename Vec<R>::v2;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = DIM == 3 ? (int)blockIdx.z : 0;
+    if (j >= L.n1) return;
+    const int par = (j + k + colour) & 1;
+    const int i = 2 * (int)(blockIdx.x * blockDim.x + threadIdx.x) + par;
+    if (i >= L.n0) return;
+    const long long c = cell_id(i, j, k, L.n0, L.n1);
+    R sT, sp;
+    offdiag<R, DIM>(L, L.x, i, j, k, c, sT, sp);
+    const V2 bb = ldg2(L.b + c);
+    const auto Di = ldgq(L.Dinv + c);
+    const R rT = bb.x - sT, rp = bb.y - sp;
+    L.x[c] = mk2<R>(Di.a * rT + Di.b * rp, Di.c * rT + Di.d * rp);
+}
+
+// ---------------------------------------------------------------------------
+// Residual of the children, restricted: coarse b = mean of the 2^DIM
+// children's residuals (plain mean in the row-scaled form = volume-weighted
+// mean of the physical residuals).  Also zeroes the coarse initial guess.
+// ---------------------------------------------------------------------------
+template <typename R, int DIM>
+__global__ void __launch_bounds__(kBX * kBY) k_residual_restrict(Level<R> F, Level<R> C) {
+    using V2 = typename Vec<R>::v2;
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    const int J = blockIdx.y * blockDim.y + threadIdx.y;
+    const int K = DIM == 3 ? (int)blockIdx.z : 0;
+    if (I >= C.n0 || J >= C.n1) return;
+    R aT = R(0), ap = R(0);
+#pragma unroll
+    for (int q = 0; q < (1 << DIM); q++) {
+        const int i = 2 * I + (q & 1), j = 2 * J + ((q >> 1) & 1), k = DIM == 3 ? 2 * K + (q >> 2) : 0;
+        const long long c = cell_id(i, j, k, F.n0, F.n1);
+        R sT, sp;
+        offdiag<R, DIM>(F, F.x, i, j, k, c, sT, sp);
+        const V2 bb = ldg2(F.b + c), xx = ldg2(F.x + c);
+        const auto Dd = ldgq(F.D + c);
+        aT += bb.x - sT - (Dd.a * xx.x + Dd.b * xx.y);
+        ap += bb.y - sp - (Dd.c * xx.x + Dd.d * xx.y);
+    }
+    const R w = R(1) / R(1 << DIM);
+    const long long cc = cell_id(I, J, K, C.n0, C.n1);
+    C.b[cc] = mk2<R>(aT * w, ap * w);
+    C.x[cc] = mk2<R>(R(0), R(0));
+}
+
+// ---------------------------------------------------------------------------
+// Prolongation and correction: fine x += cell-centred bi/tri-linear
+// interpolation of the coarse correction (weight 3/4 towards the parent and
+// 1/4 towards the next coarse cell per axis).  Beyond the grid the ghost
+// reflects the parent: same value at walls and the axis, opposite sign at
+// Dirichlet faces (the correction vanishes there).
+// ---------------------------------------------------------------------------
+template <typename R, int DIM>
+__global__ void __launch_bounds__(kBX * kBY) k_prolong_add(Level<R> C, Level<R> F, BcFlags bc) {
+    using V2 = typename Vec<R>::v2;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = DIM == 3 ? (int)blockIdx.z : 0;
+    if (i >= F.n0 || j >= F.n1) return;
+    const int P[3] = {i >> 1, j >> 1, k >> 1};
+    const int s[3] = {(i & 1) ? 1 : -1, (j & 1) ? 1 : -1, (k & 1) ? 1 : -1};
+    const int nC[3] = {C.n0, C.n1, C.n2};
+    // neighbour index and sign per axis
+    int Qn[3];
+    R sg[3];
+#pragma unroll
+    for (int a = 0; a < DIM; a++) {
+        const int t = P[a] + s[a];
+        if (t < 0)             { Qn[a] = P[a]; sg[a] = bc.dir[a][0] ? R(-1) : R(1); }
+        else if (t >= nC[a])   { Qn[a] = P[a]; sg[a] = bc.dir[a][1] ? R(-1) : R(1); }
+        else                   { Qn[a] = t;    sg[a] = R(1); }
+    }
+    R aT = R(0), ap = R(0);
+#pragma unroll
+    for (int q = 0; q < (1 << DIM); q++) {
+        int Q[3] = {P[0], P[1], DIM == 3 ? P[2] : 0};
+        R w = R(1);
+#pragma unroll
+        for (int a = 0; a < DIM; a++) {
+            if ((q >> a) & 1) { Q[a] = Qn[a]; w *= R(0.25) * sg[a]; }
+            else              { w *= R(0.75); }
+        }
+        const V2 e = ldg2(C.x + cell_id(Q[0], Q[1], Q[2], C.n0, C.n1));
+        aT += w * e.x;
+        ap += w * e.y;
+    }
+    const long long c = cell_id(i, j, k, F.n0, F.n1);
+    V2 xv = F.x[c];
+    xv.x += aT;
+    xv.y += ap;
+    F.x[c] = xv;
+}
+
+// ---------------------------------------------------------------------------
+// Coarsest level: x = Minv b with the dense inverse of the level's matrix
+// (unknown order: (T, p) per cell).  One warp per row, fixed summation order.
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void k_coarse_matvec(const R *__restrict__ Minv, const R *__restrict__ b, R *__restrict__ x, int n) {
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (warp >= n) return;
+    const R *row = Minv + (long long)warp * n;
+    R acc = R(0);
+    for (int c = lane; c < n; c += 32) acc += row[c] * b[c];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (lane == 0) x[warp] = acc;
+}
+
+// ---------------------------------------------------------------------------
+// Norms.  Per cell z = Dinv (b - offdiag(x)) - x = Dinv r: the block-Jacobi
+// scaled residual, invariant under the row scaling.  Each block writes its
+// partial sums of z_T^2 and z_p^2; k_reduce_norms sums them in a fixed order.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void block_sum2(double &a, double &b) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        b += __shfl_down_sync(0xffffffffu, b, o);
+    }
+    __shared__ double sa[32], sb[32];
+    const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+    const int nthr = blockDim.x * blockDim.y * blockDim.z;
+    const int lane = tid & 31, w = tid >> 5;
+    if (lane == 0) { sa[w] = a; sb[w] = b; }
+    __syncthreads();
+    if (w == 0) {
+        const int nw = (nthr + 31) >> 5;
+        a = lane < nw ? sa[lane] : 0.0;
+        b = lane < nw ? sb[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_down_sync(0xffffffffu, a, o);
+            b += __shfl_down_sync(0xffffffffu, b, o);
+        }
+    }
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(kBX * kBY) k_norm_partials(Level<double> L, double2 *__restrict__ partial) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = DIM == 3 ? (int)blockIdx.z : 0;
+    double zT2 = 0.0, zp2 = 0.0;
+    if (i < L.n0 && j < L.n1) {
+        const long long c = cell_id(i, j, k, L.n0, L.n1);
+        double sT, sp;
+        offdiag<double, DIM>(L, L.x, i, j, k, c, sT, sp);
+        const double2 bb = ldg2(L.b + c), xx = ldg2(L.x + c);
+        const dq Di = ldgq(L.Dinv + c);
+        const double rT = bb.x - sT, rp = bb.y - sp;
+        const double zT = Di.a * rT + Di.b * rp - xx.x;
+        const double zp = Di.c * rT + Di.d * rp - xx.y;
+        zT2 = zT * zT;
+        zp2 = zp * zp;
+    }
+    block_sum2(zT2, zp2);
+    if (threadIdx.x == 0 && threadIdx.y == 0)
+        partial[blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)] = make_double2(zT2, zp2);
+}
+
+// FP64 residual of the finest level for mixed precision: r = b - A x is
+// written (rounded) as the FP32 right-hand side of the correction problem,
+// the FP32 correction is zeroed, and the norm partials of Dinv r are formed.
+template <int DIM>
+__global__ void __launch_bounds__(kBX * kBY) k_residual64_to32(Level<double> L, float2 *__restrict__ b32,
+                                                             float2 *__restrict__ e32, double2 *__restrict__ partial) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = DIM == 3 ? (int)blockIdx.z : 0;
+    double zT2 = 0.0, zp2 = 0.0;
+    if (i < L.n0 && j < L.n1) {
+        const long long c = cell_id(i, j, k, L.n0, L.n1);
+        double sT, sp;
+        offdiag<double, DIM>(L, L.x, i, j, k, c, sT, sp);
+        const double2 bb = ldg2(L.b + c), xx = ldg2(L.x + c);
+        const dq Dd = ldgq(L.D + c);
+        const dq Di = ldgq(L.Dinv + c);
+        const double rT = bb.x - sT - (Dd.a * xx.x + Dd.b * xx.y);
+        const double rp = bb.y - sp - (Dd.c * xx.x + Dd.d * xx.y);
+        const double zT = Di.a * rT + Di.b * rp;
+        const double zp = Di.c * rT + Di.d * rp;
+        zT2 = zT * zT;
+        zp2 = zp * zp;
+        b32[c] = make_float2((float)rT, (float)rp);
+        e32[c] = make_float2(0.f, 0.f);
+    }
+    block_sum2(zT2, zp2);
+    if (threadIdx.x == 0 && threadIdx.y == 0)
+        partial[blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)] = make_double2(zT2, zp2);
+}
+
+// x64 += e32 (the refinement update)
+__global__ void k_add_correction(double2 *__restrict__ x, const float2 *__restrict__ e, long long N) {
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
+        const float2 d = e[c];
+        double2 v = x[c];
+        v.x += (double)d.x;
+        v.y += (double)d.y;
+        x[c] = v;
+    }
+}
+
+// Sums the partials in a fixed order; out[0..1] = sqrt of the sums.
+__global__ void __launch_bounds__(kReduceThreads) k_reduce_norms(const double2 *__restrict__ partial, int n,
+                                                                 double *__restrict__ out) {
+    double a = 0.0, b = 0.0;
+    for (int q = threadIdx.x; q < n; q += blockDim.x) {
+        a += partial[q].x;
+        b += partial[q].y;
+    }
+    block_sum2(a, b);
+    if (threadIdx.x == 0) {
+        out[0] = sqrt(a);
+        out[1] = sqrt(b);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Finest-level right-hand side: b0 = s_i (lambda_T, lambda_p - l4 lambda_T)
+// minus the Dirichlet boundary data of the row (G_f g for each boundary face).
+// ---------------------------------------------------------------------------
+struct BcVals {
+    int dir[3][2];
+    double T[3][2], p[3][2];
+};
+
+template <int DIM>
+__device__ __forceinline__ void boundary_data(const Level<double> &L, const BcVals &bv, int i, int j, int k,
+                                              double &gT, double &gp) {
+    const int n0 = L.n0, n1 = L.n1;
+    gT = 0.0;
+    gp = 0.0;
+    const long long f0 = (long long)i + (long long)(n0 + 1) * ((long long)j + (long long)n1 * k);
+    if (i == 0 && bv.dir[0][0])      { double2 g = L.G0[f0];     gT += g.x * bv.T[0][0]; gp += g.y * bv.p[0][0]; }
+    if (i == n0 - 1 && bv.dir[0][1]) { double2 g = L.G0[f0 + 1]; gT += g.x * bv.T[0][1]; gp += g.y * bv.p[0][1]; }
+    const long long f1 = (long long)i + (long long)n0 * ((long long)j + (long long)(n1 + 1) * k);
+    if (j == 0 && bv.dir[1][0])      { double2 g = L.G1[f1];      gT += g.x * bv.T[1][0]; gp += g.y * bv.p[1][0]; }
+    if (j == n1 - 1 && bv.dir[1][1]) { double2 g = L.G1[f1 + n0]; gT += g.x * bv.T[1][1]; gp += g.y * bv.p[1][1]; }
+    if (DIM == 3) {
+        const long long c = cell_id(i, j, k, n0, n1), pl = (long long)n0 * n1;
+        if (k == 0 && bv.dir[2][0])        { double2 g = L.G2[c];      gT += g.x * bv.T[2][0]; gp += g.y * bv.p[2][0]; }
+        if (k == L.n2 - 1 && bv.dir[2][1]) { double2 g = L.G2[c + pl]; gT += g.x * bv.T[2][1]; gp += g.y * bv.p[2][1]; }
+    }
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(kBX * kBY) k_prep_rhs(Level<double> L, const double2 *__restrict__ rhs,
+                                                      const double *__restrict__ lam4, BcVals bv, int axisym,
+                                                      double r0, double h) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = DIM == 3 ? (int)blockIdx.z : 0;
+    if (i >= L.n0 || j >= L.n1) return;
+    const long long c = cell_id(i, j, k, L.n0, L.n1);
+    const double s = axisym ? r0 + (i + 0.5) * h : 1.0;
+    const double2 q = rhs[c];
+    double gT, gp;
+    boundary_data<DIM>(L, bv, i, j, k, gT, gp);
+    L.b[c] = make_double2(s * q.x - gT, s * (q.y - lam4[c] * q.x) - gp);
+}
+
+// y = L(x) in the paper's form (Eqs. 27-28) from the row-scaled eliminated
+// data: E = offdiag + boundary data + D x is s_i times the eliminated rows, so
+// L_T = E_T / s_i and L_p = E_p / s_i + l4 L_T.
+template <int DIM>
+__global__ void __launch_bounds__(kBX * kBY) k_apply_paper(Level<double> L, const double *__restrict__ lam4,
+                                                         BcVals bv, int axisym, double r0, double h,
+                                                         double2 *__restrict__ y) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = DIM == 3 ? (int)blockIdx.z : 0;
+    if (i >= L.n0 || j >= L.n1) return;
+    const long long c = cell_id(i, j, k, L.n0, L.n1);
+    double sT, sp, gT, gp;
+    offdiag<double, DIM>(L, L.x, i, j, k, c, sT, sp);
+    boundary_data<DIM>(L, bv, i, j, k, gT, gp);
+    const double2 xx = L.x[c];
+    const dq Dd = L.D[c];
+    const double s = axisym ? r0 + (i + 0.5) * h : 1.0;
+    const double LT = (sT + gT + Dd.a * xx.x + Dd.b * xx.y) / s;
+    const double Ep = (sp + gp + Dd.c * xx.x + Dd.d * xx.y) / s;
+    y[c] = make_double2(LT, Ep + lam4[c] * LT);
+}
+
+// ---------------------------------------------------------------------------
+// Set-up kernels (FP64)
+// ---------------------------------------------------------------------------
+struct FaceGeom {
+    int n[3];          // level cells per axis
+    int axis;          // faces normal to this axis
+    int axisym;
+    double r0, h;
+    double fac[2];     // boundary factor low/high side: 2 Dirichlet, 0 wall/axis
+};
+
+// G = (k, 1/rho) * rho_f / h^2 * (1 interior | boundary factor)
+__global__ void k_faces0(FaceGeom fg, const double *__restrict__ alpha, const double *__restrict__ kap,
+                         double2 *__restrict__ G, long long M, int *__restrict__ err) {
+    const int a = fg.axis;
+    const int m0 = fg.n[0] + (a == 0), m1 = fg.n[1] + (a == 1);
+    for (long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x; f < M; f += (long long)gridDim.x * blockDim.x) {
+        const int fi = (int)(f % m0);
+        const long long rest = f / m0;
+        const int fj = (int)(rest % m1);
+        const int fk = (int)(rest / m1);
+        const int pos = a == 0 ? fi : (a == 1 ? fj : fk);
+        double fac = 1.0;
+        if (pos == 0) fac = fg.fac[0];
+        else if (pos == fg.n[a]) fac = fg.fac[1];
+        double rho_f = 1.0;
+        if (fg.axisym) rho_f = a == 0 ? fg.r0 + fi * fg.h : fg.r0 + (fi + 0.5) * fg.h;
+        const double w = rho_f / (fg.h * fg.h) * fac;
+        const double al = alpha[f], kk = kap[f];
+        if (!isfinite(al) || !isfinite(kk)) atomicOr(err, 1);
+        G[f] = make_double2(kk * w, al * w);
+    }
+}
+
+// Scaled eliminated block S = s_i [[l1, l2], [-l4 l1, l3 - l4 l2]]; keeps l4.
+__global__ void k_block0(const double *__restrict__ lam, int n0, long long N, int axisym, double r0, double h,
+                         dq *__restrict__ S, double *__restrict__ lam4, int *__restrict__ err) {
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
+        const double l1 = lam[4 * c], l2 = lam[4 * c + 1], l3 = lam[4 * c + 2], l4 = lam[4 * c + 3];
+        if (!isfinite(l1) || !isfinite(l2) || !isfinite(l3) || !isfinite(l4)) atomicOr(err, 1);
+        const int i = (int)(c % n0);
+        const double s = axisym ? r0 + (i + 0.5) * h : 1.0;
+        S[c] = dq{s * l1, s * l2, s * (-l4 * l1), s * (l3 - l4 * l2)};
+        lam4[c] = l4;
+    }
+}
+
+// Coarse block = mean of the 2^DIM children's scaled blocks.
+template <int DIM>
+__global__ void k_coarsen_blocks(const dq *__restrict__ Sf, int f0, int f1, dq *__restrict__ Sc, int c0, int c1,
+                                 int c2) {
+    const long long Nc = (long long)c0 * c1 * c2;
+    for (long long cc = blockIdx.x * (long long)blockDim.x + threadIdx.x; cc < Nc; cc += (long long)gridDim.x * blockDim.x) {
+        const int I = (int)(cc % c0), J = (int)((cc / c0) % c1), K = (int)(cc / ((long long)c0 * c1));
+        double a = 0, b = 0, c = 0, d = 0;
+        for (int q = 0; q < (1 << DIM); q++) {
+            const dq s = Sf[cell_id(2 * I + (q & 1), 2 * J + ((q >> 1) & 1), DIM == 3 ? 2 * K + (q >> 2) : 0, f0, f1)];
+            a += s.a; b += s.b; c += s.c; d += s.d;
+        }
+        const double w = 1.0 / (1 << DIM);
+        Sc[cc] = dq{a * w, b * w, c * w, d * w};
+    }
+}
+
+// Coarse face = sum of its 2^(DIM-1) fine faces / 2^(DIM+1): the area-weighted
+// mean coefficient re-discretised at spacing 2h.
+template <int DIM>
+__global__ void k_coarsen_faces(int axis, const double2 *__restrict__ Gf, int fn0, int fn1,
+                                double2 *__restrict__ Gc, int cn0, int cn1, int cn2) {
+    const int cm0 = cn0 + (axis == 0), cm1 = cn1 + (axis == 1), cm2 = cn2 + (axis == 2);
+    const int fm0 = fn0 + (axis == 0), fm1 = fn1 + (axis == 1);
+    const long long M = (long long)cm0 * cm1 * cm2;
+    for (long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x; f < M; f += (long long)gridDim.x * blockDim.x) {
+        const int FI = (int)(f % cm0), FJ = (int)((f / cm0) % cm1), FK = (int)(f / ((long long)cm0 * cm1));
+        double sT = 0, sp = 0;
+        for (int q = 0; q < (1 << (DIM - 1)); q++) {
+            int o[3] = {0, 0, 0}, bit = 0;
+            for (int b = 0; b < DIM; b++) {
+                if (b == axis) continue;
+                o[b] = (q >> bit) & 1;
+                bit++;
+            }
+            const int fi = 2 * FI + o[0], fj = 2 * FJ + o[1], fk = DIM == 3 ? 2 * FK + o[2] : 0;
+            const double2 g = Gf[(long long)fi + (long long)fm0 * ((long long)fj + (long long)fm1 * fk)];
+            sT += g.x;
+            sp += g.y;
+        }
+        const double w = 1.0 / (1 << (DIM + 1));
+        Gc[f] = make_double2(sT * w, sp * w);
+    }
+}
+
+// D = S - diag(sum of G^T, sum of G^p over all faces of the cell), in place,
+// and Dinv.  err |= 2 for a singular or non-finite block.
+template <int DIM>
+__global__ void k_diag(int n0, int n1, int n2, const double2 *__restrict__ G0, const double2 *__restrict__ G1,
+                       const double2 *__restrict__ G2, dq *__restrict__ D, dq *__restrict__ Dinv,
+                       int *__restrict__ err) {
+    const long long N = (long long)n0 * n1 * n2;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(c % n0), j = (int)((c / n0) % n1), k = (int)(c / ((long long)n0 * n1));
+        const long long f0 = (long long)i + (long long)(n0 + 1) * ((long long)j + (long long)n1 * k);
+        const long long f1 = (long long)i + (long long)n0 * ((long long)j + (long long)(n1 + 1) * k);
+        double2 g = G0[f0], h2 = G0[f0 + 1], u = G1[f1], v = G1[f1 + n0];
+        double sT = g.x + h2.x + u.x + v.x, sp = g.y + h2.y + u.y + v.y;
+        if (DIM == 3) {
+            const double2 w0 = G2[c], w1 = G2[c + (long long)n0 * n1];
+            sT += w0.x + w1.x;
+            sp += w0.y + w1.y;
+        }
+        dq s = D[c];
+        s.a -= sT;
+        s.d -= sp;
+        const double det = s.a * s.d - s.b * s.c;
+        if (!(det != 0.0) || !isfinite(det)) atomicOr(err, 2);
+        const double id = 1.0 / det;
+        D[c] = s;
+        Dinv[c] = dq{s.d * id, -s.b * id, -s.c * id, s.a * id};
+    }
+}
+
+__global__ void k_to_f32_v2(const double2 *__restrict__ in, float2 *__restrict__ out, long long n) {
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+        const double2 v = in[q];
+        out[q] = make_float2((float)v.x, (float)v.y);
+    }
+}
+__global__ void k_to_f32_q(const dq *__restrict__ in, fq *__restrict__ out, long long n) {
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+        const dq v = in[q];
+        out[q] = fq{(float)v.a, (float)v.b, (float)v.c, (float)v.d};
+    }
+}
+__global__ void k_to_f32(const double *__restrict__ in, float *__restrict__ out, long long n) {
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x)
+        out[q] = (float)in[q];
+}
+
+// Dense matrix of the coarsest level (M zeroed beforehand): row 2c+f holds
+// D_c on the diagonal block and G_f on the neighbours of the same field.
+template <int DIM>
+__global__ void k_coarse_assemble(int n0, int n1, int n2, const double2 *__restrict__ G0,
+                                  const double2 *__restrict__ G1, const double2 *__restrict__ G2,
+                                  const dq *__restrict__ D, double *__restrict__ M) {
+    const long long N = (long long)n0 * n1 * n2;
+    const long long n = 2 * N;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(c % n0), j = (int)((c / n0) % n1), k = (int)(c / ((long long)n0 * n1));
+        const dq d = D[c];
+        M[(2 * c) * n + 2 * c] = d.a;
+        M[(2 * c) * n + 2 * c + 1] = d.b;
+        M[(2 * c + 1) * n + 2 * c] = d.c;
+        M[(2 * c + 1) * n + 2 * c + 1] = d.d;
+        const long long f0 = (long long)i + (long long)(n0 + 1) * ((long long)j + (long long)n1 * k);
+        const long long f1 = (long long)i + (long long)n0 * ((long long)j + (long long)(n1 + 1) * k);
+        auto put = [&](long long nb, double2 g) {
+            M[(2 * c) * n + 2 * nb] = g.x;
+            M[(2 * c + 1) * n + 2 * nb + 1] = g.y;
+        };
+        if (i > 0) put(c - 1, G0[f0]);
+        if (i < n0 - 1) put(c + 1, G0[f0 + 1]);
+        if (j > 0) put(c - n0, G1[f1]);
+        if (j < n1 - 1) put(c + n0, G1[f1 + n0]);
+        if (DIM == 3) {
+            const long long pl = (long long)n0 * n1;
+            if (k > 0) put(c - pl, G2[c]);
+            if (k < n2 - 1) put(c + pl, G2[c + pl]);
+        }
+    }
+}
+
+// Gauss-Jordan inversion with partial pivoting in one block (n <= 1024):
+// M (destroyed) -> Minv.  err |= 4 on a zero pivot.
+__global__ void __launch_bounds__(1024) k_gauss_jordan(double *__restrict__ M, double *__restrict__ Minv, int n,
+                                                       int *__restrict__ err) {
+    __shared__ double fac[1024];
+    __shared__ double pv[32];
+    __shared__ int pi[32];
+    __shared__ int piv_row;
+    __shared__ double piv_val;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (long long q = tid; q < (long long)n * n; q += nt) Minv[q] = (q / n == q % n) ? 1.0 : 0.0;
+    __syncthreads();
+    for (int col = 0; col < n; col++) {
+        // pivot: largest |M[r][col]|, r >= col, lowest index on ties
+        double best = -1.0;
+        int br = col;
+        for (int r = col + tid; r < n; r += nt) {
+            const double v = fabs(M[(long long)r * n + col]);
+            if (v > best) { best = v; br = r; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const double ov = __shfl_down_sync(0xffffffffu, best, o);
+            const int orr = __shfl_down_sync(0xffffffffu, br, o);
+            if (ov > best || (ov == best && orr < br)) { best = ov; br = orr; }
+        }
+        if ((tid & 31) == 0) { pv[tid >> 5] = best; pi[tid >> 5] = br; }
+        __syncthreads();
+        if (tid == 0) {
+            double b = -1.0;
+            int r = col;
+            for (int w = 0; w < (nt + 31) / 32; w++)
+                if (pv[w] > b || (pv[w] == b && pi[w] < r)) { b = pv[w]; r = pi[w]; }
+            piv_row = r;
+            piv_val = M[(long long)r * n + col];
+            if (!(b > 0.0)) atomicOr(err, 4);
+        }
+        __syncthreads();
+        if (!(piv_val != 0.0)) return;
+        const int pr = piv_row;
+        if (pr != col) {
+            for (int c = tid; c < n; c += nt) {
+                double t = M[(long long)col * n + c];
+                M[(long long)col * n + c] = M[(long long)pr * n + c];
+                M[(long long)pr * n + c] = t;
+                t = Minv[(long long)col * n + c];
+                Minv[(long long)col * n + c] = Minv[(long long)pr * n + c];
+                Minv[(long long)pr * n + c] = t;
+            }
+        }
+        __syncthreads();
+        const double ip = 1.0 / piv_val;
+        for (int c = tid; c < n; c += nt) {
+            M[(long long)col * n + c] *= ip;
+            Minv[(long long)col * n + c] *= ip;
+        }
+        __syncthreads();
+        for (int r = tid; r < n; r += nt) fac[r] = (r == col) ? 0.0 : M[(long long)r * n + col];
+        __syncthreads();
+        for (long long q = tid; q < (long long)n * n; q += nt) {
+            const int r = (int)(q / n), c = (int)(q % n);
+            const double f = fac[r];
+            if (f != 0.0) {
+                M[q] -= f * M[(long long)col * n + c];
+                Minv[q] -= f * Minv[(long long)col * n + c];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace cmg

@@ -1,0 +1,55 @@
+// Device-side types of the coupled p-T multigrid (sm_103a).
+//
+// Every level stores the row-scaled, row-eliminated system
+//
+//     sum_f G_f (u_nb - u_i) + S_i u_i = s_i * b'_i          (per cell i)
+//
+// obtained from Eqs. 27-28 by (1) subtracting l4 times the T-row from the
+// p-row, which removes div(k grad T) from the p-row, and (2) multiplying row
+// i by s_i = V_i / h^dim (1 on Cartesian grids, r_i on axisymmetric ones).
+// The scaling makes every face coefficient G_f = c_f * rho_f / h^2 the same
+// for both cells of the face (rho_f = r_f on r-faces, r_i on z-faces, 1 on
+// Cartesian grids), so restriction becomes a plain average of children and
+// face coefficients coarsen by a plain sum.  Boundary faces carry G = 0
+// (wall, axis) or twice the interior value (Dirichlet: the boundary value
+// sits h/2 away); their Dirichlet data move to the right-hand side once.
+//
+// Per level and cell:
+//   x, b      pair (T, p)                      R2  (double2 / float2)
+//   D         2x2 diagonal block S_i - diag(sum_f G^T_f, sum_f G^p_f)
+//   Dinv      its inverse                      R4  (row-major 2x2)
+// Per face, one array per axis:
+//   G         (G^T, G^p) = (k, 1/rho) times rho_f / h^2 times the boundary factor
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace cmg {
+
+struct __align__(32) dq { double a, b, c, d; };   // 2x2 block, row-major
+struct __align__(16) fq { float a, b, c, d; };
+
+template <typename R> struct Vec;
+template <> struct Vec<double> { using v2 = double2; using q4 = dq; };
+template <> struct Vec<float>  { using v2 = float2;  using q4 = fq; };
+
+template <typename R>
+struct Level {
+    int n0, n1, n2;                 // cells per axis (n2 = 1 in 2D)
+    long long N;                    // cells
+    typename Vec<R>::v2 *x;         // unknowns (T, p)
+    typename Vec<R>::v2 *b;         // right-hand side of this level
+    const typename Vec<R>::v2 *G0, *G1, *G2;   // face coefficients, axes 0..2
+    const typename Vec<R>::q4 *D, *Dinv;
+};
+
+// Dirichlet flags per axis and side (prolongation ghost signs).
+struct BcFlags {
+    int dir[3][2];
+};
+
+__host__ __device__ inline long long cell_id(int i, int j, int k, int n0, int n1) {
+    return (long long)i + (long long)n0 * ((long long)j + (long long)n1 * k);
+}
+
+}  // namespace cmg

@@ -1,0 +1,99 @@
+"""C-ABI checks that need no GPU: the library builds, loads and exports every
+symbol include/*.h declares; host-side argument validation and workspace
+sizing (no device work)."""
+import ctypes as C
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        names |= set(re.findall(r"^MG_API\s+[\w\s\*]+?\b(mg_\w+)\s*\(", src, flags=re.M))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2206_11294_gb300 import build, binding
+    build.build()
+    return binding.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_2206_11294_gb300 import binding
+    names = _declared()
+    assert len(names) >= 12
+    for n in names:
+        assert hasattr(lib, n), n
+    assert names == set(binding.EXPORTS), names ^ set(binding.EXPORTS)
+
+
+def test_default_options(lib):
+    from paper_2206_11294_gb300 import binding as B
+    o = B.MgOptions()
+    assert lib.mg_default_options(C.byref(o)) == 0
+    assert (o.nu1, o.nu2, o.precision, o.max_cycles, o.coarse_min, o.inner_cycles) == (2, 2, 0, 50, 4, 1)
+    assert o.rtol == 1e-10
+
+
+def _grid(**kw):
+    from paper_2206_11294_gb300 import binding as B, inputs as I
+    g = I.Grid(dim=kw.get("dim", 2), axisym=kw.get("axisym", 0), n=kw.get("n", (64, 64, 1)), h=kw.get("h", 1 / 64),
+               r0=kw.get("r0", 0.0), bc=kw.get("bc", ((0, 0), (0, 0), (0, 0))))
+    return B.make_grid(g)
+
+
+def _size(lib, g, **okw):
+    from paper_2206_11294_gb300 import binding as B
+    o = B.make_options(**okw)
+    n = C.c_size_t()
+    st = lib.mg_workspace_size(C.byref(g), C.byref(o), C.byref(n))
+    return st, n.value
+
+
+def test_workspace_size_scales_with_levels(lib):
+    st, a = _size(lib, _grid(n=(64, 64, 1)))
+    st2, b = _size(lib, _grid(n=(128, 128, 1)))
+    st3, c = _size(lib, _grid(n=(128, 128, 1)), precision="mixed")
+    assert st == st2 == st3 == 0
+    # hierarchy ~ 4/3 of the finest level; 4x the cells -> about 4x the bytes
+    assert 3.5 < b / a < 4.5
+    assert c > b
+
+
+@pytest.mark.parametrize("kw,okw", [
+    (dict(dim=4), {}),
+    (dict(dim=2, n=(64, 64, 2)), {}),
+    (dict(axisym=1, dim=3, n=(8, 8, 8)), {}),
+    (dict(h=-1.0), {}),
+    (dict(bc=((2, 0), (0, 0), (0, 0))), {}),                      # axis on a Cartesian grid
+    (dict(axisym=1, r0=0.0, bc=((1, 0), (0, 0), (0, 0))), {}),   # Dirichlet on the axis
+    (dict(n=(96, 160, 1)), {}),                                   # 6 x 10 x 2 coarse unknowns fine
+    (dict(n=(1000, 1000, 1)), {}),                                # coarsest 125 x 125: too large
+    ({}, dict(nu1=0, nu2=0)),
+    ({}, dict(max_cycles=-1)),
+])
+def test_argument_validation(lib, kw, okw):
+    st, _ = _size(lib, _grid(**kw), **okw)
+    ok_cases = [dict(n=(96, 160, 1))]
+    if kw in ok_cases and not okw:
+        assert st == 0
+    else:
+        assert st == 1, lib.mg_last_error()
+        assert len(lib.mg_last_error()) > 0
+
+
+def test_product_path_has_no_oracle_dependency():
+    """The package and the library never import, load or link the oracle."""
+    pkg = os.path.join(ROOT, "paper_2206_11294_gb300")
+    for path in glob.glob(os.path.join(pkg, "**", "*.*"), recursive=True):
+        if path.endswith((".py", ".cu", ".cuh", ".h")):
+            src = open(path).read()
+            assert "import oracle" not in src and "coupled_oracle" not in src, path

@@ -1,0 +1,244 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 CPU oracle.
+
+Element-by-element comparisons on the same seeded inputs, at sizes that span
+several thread blocks and leave ragged tails, for every geometry and boundary
+mix.  Tolerances:
+  - operator application, one sweep, norms: 1e-13 .. 1e-12 relative (FP64
+    rounding only; the GPU contracts to FMA, the oracle does not);
+  - FP64 solves after the same number of cycles: <= 1e-12 relative L2 of the
+    deviation from the initial guess, per field;
+  - mixed precision (FP32 cycles in FP64 refinement) at 1e-10 residual
+    reduction: <= 1e-8 relative L2 against the converged oracle.
+"""
+import numpy as np
+import pytest
+
+from paper_2206_11294_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+W, D, A = I.BC_WALL, I.BC_DIRICHLET, I.BC_AXIS
+
+
+def rel_dev(x, ref, x0):
+    out = 0.0
+    for f in range(2):
+        d = ref[:, f] - x0[:, f]
+        out = max(out, np.linalg.norm(x[:, f] - ref[:, f]) / max(np.linalg.norm(d), 1e-300))
+    return out
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2206_11294_gb300 import binding
+    binding.load()
+    return torch
+
+
+def _solver(p, **kw):
+    from paper_2206_11294_gb300.binding import Solver
+    s = Solver(p.grid, **kw)
+    s.set_coeffs(p.lam, p.fa, p.fk)
+    return s
+
+
+# grids: several blocks of 32 x 8 threads, ragged tails, every boundary mix
+def _cases():
+    out = {}
+    out["2d_ragged_walls"] = I.random_coeff_problem(
+        I.Grid(dim=2, axisym=0, n=(200, 72, 1), h=1e-4, bc=((W, W), (W, W), (0, 0))), seed=21, dt=1e-5)
+    out["2d_dirichlet_mix"] = I.random_coeff_problem(
+        I.Grid(dim=2, axisym=0, n=(96, 40, 1), h=1e-4, bc=((D, W), (W, D), (0, 0)),
+               bcT=((310, 0), (0, 290), (0, 0)), bcp=((1.1e5, 0), (0, 0.9e5), (0, 0))), seed=22, dt=1e-5)
+    out["axi_axis"] = I.random_coeff_problem(
+        I.Grid(dim=2, axisym=1, n=(48, 104, 1), h=1e-4, bc=((A, D), (W, W), (0, 0)),
+               bcT=((0, 300), (0, 0), (0, 0)), bcp=((0, 1e5), (0, 0), (0, 0))), seed=23, dt=1e-5)
+    out["axi_annulus"] = I.random_coeff_problem(
+        I.Grid(dim=2, axisym=1, n=(40, 64, 1), h=1e-4, r0=2e-4, bc=((W, D), (D, W), (0, 0)),
+               bcT=((0, 300), (305, 0), (0, 0)), bcp=((0, 1e5), (1.2e5, 0), (0, 0))), seed=24, dt=1e-5)
+    out["3d_wall_dirichlet"] = I.random_coeff_problem(
+        I.Grid(dim=3, axisym=0, n=(40, 24, 16), h=1e-4, bc=((D, D), (D, D), (W, D)),
+               bcT=((300, 300), (300, 300), (0, 300)), bcp=((1e5, 1e5), (1e5, 1e5), (0, 1e5))), seed=25, dt=1e-5)
+    out["3d_walls_odd"] = I.random_coeff_problem(
+        I.Grid(dim=3, axisym=0, n=(36, 20, 12), h=1e-4, bc=((W, W), (W, W), (W, W))), seed=26, dt=1e-5)
+    return out
+
+
+CASES = _cases()
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_apply(torch_cuda, orc, name):
+    p = CASES[name]
+    s = _solver(p)
+    rng = np.random.default_rng(1)
+    x = p.x0 * (1 + 1e-2 * rng.standard_normal(p.x0.shape))
+    y = s.apply(x)
+    ref = orc.apply_paper(p.grid.as_dict(), p.lam, p.fa, p.fk, x)
+    for f in range(2):
+        assert np.abs(y[:, f] - ref[:, f]).max() <= 1e-12 * np.abs(ref[:, f]).max()
+    s.close()
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("sweeps", [1, 3])
+def test_smooth(torch_cuda, orc, name, sweeps):
+    p = CASES[name]
+    s = _solver(p)
+    x = p.x0.copy()
+    s.smooth(p.b, x, sweeps)
+    ref = orc.rbgs_sweeps(p.grid.as_dict(), p.lam, p.fa, p.fk, p.b, p.x0, sweeps)
+    assert rel_dev(x, ref, p.x0) <= 1e-12
+    s.close()
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_residual_norms(torch_cuda, orc, name):
+    p = CASES[name]
+    s = _solver(p)
+    got = s.residual_norms(p.b, p.x0)
+    ref = orc.residual_norms(p.grid.as_dict(), p.lam, p.fa, p.fk, p.b, p.x0)
+    assert np.allclose(got, ref, rtol=1e-12, atol=0)
+    s.close()
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("cycles", [1, 4])
+def test_fixed_cycles_fp64(torch_cuda, orc, name, cycles):
+    p = CASES[name]
+    s = _solver(p, rtol=0.0, max_cycles=cycles)
+    x = p.x0.copy()
+    st = s.solve(p.b, x)
+    ref, cyc, _ = orc.mg_solve(p.grid.as_dict(), p.lam, p.fa, p.fk, p.b, p.x0, max_cycles=cycles, rtol=0.0)
+    assert st["cycles"] == cycles == cyc
+    assert rel_dev(x, ref, p.x0) <= 1e-12
+    assert st["levels"] == orc.num_levels(p.grid.as_dict())
+    s.close()
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_converged_fp64_same_cycles_as_oracle(torch_cuda, orc, name):
+    p = CASES[name]
+    s = _solver(p, rtol=1e-10, max_cycles=60)
+    x = p.x0.copy()
+    st = s.solve(p.b, x)
+    ref, cyc, hist = orc.mg_solve(p.grid.as_dict(), p.lam, p.fa, p.fk, p.b, p.x0, max_cycles=60, rtol=1e-10)
+    assert st["cycles"] == cyc
+    assert np.allclose(st["r0"], hist[0], rtol=1e-12)
+    assert rel_dev(x, ref, p.x0) <= 1e-12
+    s.close()
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_mixed_precision(torch_cuda, orc, name):
+    p = CASES[name]
+    s = _solver(p, precision="mixed", rtol=1e-10, max_cycles=40)
+    x = p.x0.copy()
+    st = s.solve(p.b, x)
+    ref, cyc, hist = orc.mg_solve(p.grid.as_dict(), p.lam, p.fa, p.fk, p.b, p.x0, max_cycles=80, rtol=1e-13)
+    assert max(st["rfinal"][f] / st["r0"][f] for f in range(2)) <= 1e-10
+    assert rel_dev(x, ref, p.x0) <= 1e-8
+    s.close()
+
+
+def test_device_pointers_and_workspace(torch_cuda, orc):
+    """Device-side inputs (torch tensors) give the same result as host inputs."""
+    torch = torch_cuda
+    p = CASES["2d_dirichlet_mix"]
+    s = _solver(p, rtol=0.0, max_cycles=2)
+    x_h = p.x0.copy()
+    s.solve(p.b, x_h)
+    s2 = _solver(p, rtol=0.0, max_cycles=2)
+    s2.set_coeffs(torch.from_numpy(p.lam).cuda(), [torch.from_numpy(f).cuda() for f in p.fa],
+                  [torch.from_numpy(f).cuda() for f in p.fk])
+    x_d = torch.from_numpy(p.x0.copy()).cuda()
+    s2.solve(torch.from_numpy(p.b).cuda(), x_d)
+    assert np.array_equal(x_d.cpu().numpy(), x_h)
+    s.close()
+    s2.close()
+
+
+def test_repeat_solves_are_bitwise_identical(torch_cuda):
+    p = CASES["3d_walls_odd"]
+    s = _solver(p, rtol=1e-10, max_cycles=60)
+    xs = []
+    for _ in range(3):
+        x = p.x0.copy()
+        s.solve(p.b, x)
+        xs.append(x)
+    assert np.array_equal(xs[0], xs[1]) and np.array_equal(xs[1], xs[2])
+    s.close()
+
+
+def test_invalid_coefficients_rejected(torch_cuda):
+    from paper_2206_11294_gb300.binding import MgError, Solver, MG_ERR_INVALID_COEFF, MG_ERR_STATE
+    p = CASES["2d_ragged_walls"]
+    s = Solver(p.grid)
+    with pytest.raises(MgError) as e:
+        s.solve(p.b, p.x0.copy())
+    assert e.value.status == MG_ERR_STATE
+    lam = p.lam.copy()
+    lam[5, 0] = np.nan
+    with pytest.raises(MgError) as e:
+        s.set_coeffs(lam, p.fa, p.fk)
+    assert e.value.status == MG_ERR_INVALID_COEFF
+    s.close()
+
+
+def test_not_converged_status(torch_cuda):
+    from paper_2206_11294_gb300.binding import MgError, MG_ERR_NOT_CONVERGED
+    p = I.stiff(I.bubble_2d, 64)
+    s = _solver(p, rtol=1e-14, max_cycles=2)
+    x = p.x0.copy()
+    with pytest.raises(MgError) as e:
+        s.solve(p.b, x)
+    assert e.value.status == MG_ERR_NOT_CONVERGED
+    st = s.solve(p.b, p.x0.copy(), allow_not_converged=True)
+    assert st["cycles"] == 2 and st["status"] == "MG_ERR_NOT_CONVERGED"
+    s.close()
+
+
+# ------------------------------------------------------------- full sizes
+def _full_case(name):
+    if name == "bubbles_1024":
+        return I.bubbles_1024()
+    if name == "axi_512x1024":
+        return I.bubble_axi()
+    return I.bubble_wall_3d(256)
+
+
+@pytest.mark.parametrize("name", ["bubbles_1024", "axi_512x1024"])
+def test_full_size_2d_vs_oracle(torch_cuda, orc, name):
+    """The benchmark's 2D workloads at full size, in the launch configuration
+    the benchmark times: whole-field comparison with the oracle's solve."""
+    p = _full_case(name)
+    s = _solver(p, rtol=1e-10, max_cycles=50)
+    x = p.x0.copy()
+    st = s.solve(p.b, x)
+    ref, cyc, hist = orc.mg_solve(p.grid.as_dict(), p.lam, p.fa, p.fk, p.b, p.x0, max_cycles=50, rtol=1e-10)
+    assert st["cycles"] == cyc
+    assert rel_dev(x, ref, p.x0) <= 1e-12
+    s.close()
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-9), ("mixed", 1e-9)])
+def test_full_size_3d_sampled_residual(torch_cuda, orc, precision, tol):
+    """256^3 bubble near a wall: the oracle evaluates the residual of the GPU
+    solution at sampled cells (too large for a full oracle solve); the
+    residual must be tiny against the right-hand side's scale there."""
+    p = _full_case("wall3d")
+    s = _solver(p, precision=precision, rtol=1e-10, max_cycles=50)
+    x = p.x0.copy()
+    st = s.solve(p.b, x)
+    rng = np.random.default_rng(0)
+    ids = rng.choice(p.grid.N, 4000, replace=False)
+    Lx = orc.apply_rows(p.grid.as_dict(), p.lam, p.fa, p.fk, x, ids)
+    Lx0 = orc.apply_rows(p.grid.as_dict(), p.lam, p.fa, p.fk, p.x0, ids)
+    r = p.b[ids] - Lx
+    r0 = p.b[ids] - Lx0
+    for f in range(2):
+        assert np.linalg.norm(r[:, f]) <= tol * np.linalg.norm(r0[:, f]) * 10, (f, st)
+    s.close()

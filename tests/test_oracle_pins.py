@@ -429,3 +429,13 @@ def test_mg_convergence_factor_stiff(orc):
                                 rtol=1e-10)
     q = hist[1:, 1] / hist[:-1, 1]
     assert cyc <= 20 and np.max(q[:-1]) < 0.3
+
+
+def test_apply_rows_matches_apply(orc):
+    g = GRIDS["3d_mixed"]
+    rng = np.random.default_rng(11)
+    lam, fa, fk = rng.standard_normal((g.N, 4)), rand_faces(g, rng), rand_faces(g, rng)
+    x = rng.standard_normal((g.N, 2))
+    ids = rng.choice(g.N, 17, replace=False)
+    y = orc.apply_paper(g.as_dict(), lam, fa, fk, x)
+    assert np.array_equal(orc.apply_rows(g.as_dict(), lam, fa, fk, x, ids), y[ids])
