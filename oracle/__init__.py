@@ -13,7 +13,7 @@ defect-correction loop after them; see the C file for the exact statements):
 - ``dense_solve``     exact solution of L(x) = b by Gaussian elimination
 - ``mg_solve``        defect-correction loop with V(nu1, nu2) cycles
 - ``rbgs_sweeps``     in-place red-black block Gauss-Seidel sweeps
-- ``residual_norms``  the per-field stopping norm ||D^-1 r'||_2
+- ``residual_norms``  the per-field stopping norm ||D^-1 r||_2
 - ``level_coeffs``    coarse-level blocks and faces of the hierarchy
 - ``apply_rows``      L(x) at selected cells (residual checks of large solutions)
 """
@@ -198,7 +198,7 @@ def num_levels(g, coarse_min=4) -> int:
 
 
 def level_coeffs(g, lam, fa, fk, level, coarse_min=4):
-    """(B (N_l x 4), fa_l, fk_l) of hierarchy level ``level`` (physical form)."""
+    """(lambda (N_l x 4), fa_l, fk_l) of hierarchy level ``level`` (physical form)."""
     lib = _load()
     gs = _grid(g)
     dim = gs.dim

@@ -37,23 +37,24 @@
  *
  * The multigrid (the paper names the solver type but not its parts) is this
  * library's reading, written out plainly:
- *   - exact row elimination p-row <- p-row - l4 * T-row, which removes the
- *     div(k grad T) term from the p-row (Eq. 28 minus l4 times Eq. 27);
+ *   - the system is solved in its printed form (Eqs. 27-28), the p-row
+ *     keeping its l4 div(k grad T) term;
  *   - V(nu1, nu2) cycle, red-black block Gauss-Seidel (red = even i+j+k,
- *     red first), each cell's 2x2 block solved exactly;
+ *     red first), each cell's two equations solved exactly for (T_i, p_i);
  *   - restriction: volume-weighted mean of the 2^dim children;
  *   - prolongation: cell-centred bi/tri-linear (weights 3/4 and 1/4 per axis),
  *     reflecting ghosts (same value at walls and the axis, opposite sign at
  *     Dirichlet faces);
- *   - coarse operator re-discretised at 2h with area-weighted mean face
- *     coefficients and volume-weighted mean local blocks; coarsen while every
- *     dimension is even and halves to at least coarse_min;
+ *   - coarse operator: Eqs. 27-28 re-discretised at 2h with area-weighted
+ *     mean face coefficients and volume-weighted mean l1..l4; coarsen while
+ *     every dimension is even and halves to at least coarse_min;
  *   - coarsest level solved exactly by Gaussian elimination;
  *   - outer loop = the paper's defect correction: res = b - L(a); stop when
  *     small; else solve L(da) ~= res by one V-cycle from da = 0; a += da.
  *   - stopping norm, per field: || D^{-1} r ||_2 over cells, where r is the
- *     eliminated-system residual and D its 2x2 diagonal block; stop when both
- *     fields' norms fell by rtol relative to the initial ones.
+ *     residual and D the 2x2 block of each cell's own unknowns in its two
+ *     equations; stop when both fields' norms fell by rtol relative to the
+ *     initial ones.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -72,11 +73,11 @@ typedef struct {
     double bcp[3][2]; /* Dirichlet values of p */
 } orc_grid;
 
-/* One multigrid level of the eliminated system, physical form. */
+/* One multigrid level, physical form. */
 typedef struct {
     orc_grid g;
     long N;
-    double *B;        /* N x 4, eliminated local block, row-major 2x2 */
+    double *lam;      /* N x 4: l1..l4 of Eqs. 29-32 (coarse levels: volume-weighted means) */
     double *fa[3];    /* 1/rho on faces, per axis */
     double *fk[3];    /* k on faces, per axis */
     double *rhs;      /* N x 2 */
@@ -268,31 +269,35 @@ int orc_dense_solve(const orc_grid *g, const double *lam, double *const fa[3],
 }
 
 /* ------------------------------------------------------------------ */
-/* Eliminated system on one level (homogeneous boundary values)        */
+/* Eqs. 27-28 on one level                                              */
 /* ------------------------------------------------------------------ */
 
-/* E(u)_i for the eliminated system:
- *   T-row: div(k grad T) + B00 T + B01 p
- *   p-row: div((1/rho) grad p) + B10 T + B11 p                       */
-static void elim_row(const level *L, const double *u, double *const bcT2, double *const bcp2,
-                     const int c[3], double out[2])
+/* The two rows of Eqs. 27-28 at cell c of a level:
+ *   T-row: div(k grad T) + l1 T + l2 p
+ *   p-row: div((1/rho) grad p) + l3 p + l4 div(k grad T)              */
+static void paper_row(const level *L, const double *u, double *const bcT2, double *const bcp2,
+                      const int c[3], double out[2])
 {
     long i = cell_id(&L->g, c);
-    const double *B = L->B + 4 * i;
+    const double *l = L->lam + 4 * i;
     double lapT = div_flux(&L->g, L->fk, u + 0, (double (*)[2])bcT2, c);
     double lapp = div_flux(&L->g, L->fa, u + 1, (double (*)[2])bcp2, c);
-    out[0] = lapT + B[0] * u[2 * i] + B[1] * u[2 * i + 1];
-    out[1] = lapp + B[2] * u[2 * i] + B[3] * u[2 * i + 1];
+    out[0] = lapT + l[0] * u[2 * i] + l[1] * u[2 * i + 1];
+    out[1] = lapp + l[2] * u[2 * i + 1] + l[3] * lapT;
 }
 
+/* Coefficients of (T_i, p_i) in cell i's two rows:
+ *   [[l1 - sigma_k, l2], [-l4 sigma_k, l3 - sigma_a]]                  */
 static void diag_block(const level *L, const int c[3], double D[4])
 {
     long i = cell_id(&L->g, c);
-    const double *B = L->B + 4 * i;
-    D[0] = B[0] - div_flux_diag(&L->g, L->fk, c);
-    D[1] = B[1];
-    D[2] = B[2];
-    D[3] = B[3] - div_flux_diag(&L->g, L->fa, c);
+    const double *l = L->lam + 4 * i;
+    double sk = div_flux_diag(&L->g, L->fk, c);
+    double sa = div_flux_diag(&L->g, L->fa, c);
+    D[0] = l[0] - sk;
+    D[1] = l[1];
+    D[2] = -l[3] * sk;
+    D[3] = l[2] - sa;
 }
 
 static void solve2(const double D[4], const double s[2], double z[2])
@@ -302,14 +307,14 @@ static void solve2(const double D[4], const double s[2], double z[2])
     z[1] = (D[0] * s[1] - D[2] * s[0]) / det;
 }
 
-/* r = rhs - E(u) on a level (homogeneous boundary values). */
-static void elim_residual(level *L)
+/* r = rhs - L(u) on a level (homogeneous boundary values). */
+static void level_residual(level *L)
 {
     for (long i = 0; i < L->N; i++) {
         int c[3];
         cell_of(&L->g, i, c);
         double e[2];
-        elim_row(L, L->u, NULL, NULL, c, e);
+        paper_row(L, L->u, NULL, NULL, c, e);
         L->r[2 * i] = L->rhs[2 * i] - e[0];
         L->r[2 * i + 1] = L->rhs[2 * i + 1] - e[1];
     }
@@ -326,9 +331,9 @@ static void rbgs_sweep(level *L, double *const bcT2, double *const bcp2)
             cell_of(&L->g, i, c);
             if (((c[0] + c[1] + c[2]) & 1) != colour) continue;
             double e[2], D[4], s[2], z[2];
-            elim_row(L, L->u, bcT2, bcp2, c, e);
+            paper_row(L, L->u, bcT2, bcp2, c, e);
             diag_block(L, c, D);
-            /* rhs minus the off-diagonal part of the row: rhs - (E(u) - D u_i) */
+            /* rhs minus the off-diagonal part of the rows: rhs - (L(u) - D u_i) */
             s[0] = L->rhs[2 * i] - (e[0] - (D[0] * L->u[2 * i] + D[1] * L->u[2 * i + 1]));
             s[1] = L->rhs[2 * i + 1] - (e[1] - (D[2] * L->u[2 * i] + D[3] * L->u[2 * i + 1]));
             solve2(D, s, z);
@@ -347,11 +352,11 @@ static int alloc_level(level *L, const orc_grid *g)
     memset(L, 0, sizeof(*L));
     L->g = *g;
     L->N = ncells(g);
-    L->B = calloc(4 * L->N, sizeof(double));
+    L->lam = calloc(4 * L->N, sizeof(double));
     L->rhs = calloc(2 * L->N, sizeof(double));
     L->u = calloc(2 * L->N, sizeof(double));
     L->r = calloc(2 * L->N, sizeof(double));
-    int ok = L->B && L->rhs && L->u && L->r;
+    int ok = L->lam && L->rhs && L->u && L->r;
     for (int a = 0; a < 3; a++) {
         long m = a < g->dim ? nfaces(g, a) : 1;
         L->fa[a] = calloc(m, sizeof(double));
@@ -363,7 +368,7 @@ static int alloc_level(level *L, const orc_grid *g)
 
 static void free_level(level *L)
 {
-    free(L->B); free(L->rhs); free(L->u); free(L->r);
+    free(L->lam); free(L->rhs); free(L->u); free(L->r);
     for (int a = 0; a < 3; a++) { free(L->fa[a]); free(L->fk[a]); }
 }
 
@@ -375,7 +380,7 @@ static int can_coarsen(const orc_grid *g, int coarse_min)
 }
 
 /* Coarse level at spacing 2h: area-weighted mean face coefficients and
- * volume-weighted mean local blocks of the children. */
+ * volume-weighted mean l1..l4 of the children. */
 static int coarsen(const level *F, level *C)
 {
     orc_grid g = F->g;
@@ -394,11 +399,11 @@ static int coarsen(const level *F, level *C)
             int fc[3] = {2 * cc[0] + (q & 1), 2 * cc[1] + ((q >> 1) & 1),
                          g.dim == 3 ? 2 * cc[2] + ((q >> 2) & 1) : 0};
             double V = volume(&F->g, fc);
-            const double *B = F->B + 4 * cell_id(&F->g, fc);
-            for (int t = 0; t < 4; t++) acc[t] += V * B[t];
+            const double *l = F->lam + 4 * cell_id(&F->g, fc);
+            for (int t = 0; t < 4; t++) acc[t] += V * l[t];
             vsum += V;
         }
-        for (int t = 0; t < 4; t++) C->B[4 * I + t] = acc[t] / vsum;
+        for (int t = 0; t < 4; t++) C->lam[4 * I + t] = acc[t] / vsum;
     }
 
     for (int a = 0; a < g.dim; a++) {
@@ -499,7 +504,7 @@ static void prolong_add(const level *C, level *F)
     }
 }
 
-/* Exact solve of the coarsest level's eliminated system (homogeneous). */
+/* Exact solve of the coarsest level's Eqs. 27-28 (homogeneous). */
 static int coarse_solve(level *L)
 {
     long n = 2 * L->N;
@@ -515,7 +520,7 @@ static int coarse_solve(level *L)
             int c[3];
             double out[2];
             cell_of(&L->g, i, c);
-            elim_row(L, e, NULL, NULL, c, out);
+            paper_row(L, e, NULL, NULL, c, out);
             M[(2 * i) * n + j] = out[0];
             M[(2 * i + 1) * n + j] = out[1];
         }
@@ -534,7 +539,7 @@ static int vcycle(level *Ls, int l, int nlev, int nu1, int nu2)
     level *L = &Ls[l];
     if (l == nlev - 1) return coarse_solve(L);
     for (int s = 0; s < nu1; s++) rbgs_sweep(L, NULL, NULL);
-    elim_residual(L);
+    level_residual(L);
     restrict_residual(L, &Ls[l + 1]);
     int rc = vcycle(Ls, l + 1, nlev, nu1, nu2);
     if (rc) return rc;
@@ -543,17 +548,10 @@ static int vcycle(level *Ls, int l, int nlev, int nu1, int nu2)
     return 0;
 }
 
-/* Fill level 0 of the eliminated system from the paper's inputs:
- * B = [[l1, l2], [-l4 l1, l3 - l4 l2]]  (Eq. 28 minus l4 times Eq. 27). */
+/* Fill level 0 from the paper's inputs. */
 static void fill_level0(level *L, const double *lam, double *const fa[3], double *const fk[3])
 {
-    for (long i = 0; i < L->N; i++) {
-        const double *l = lam + 4 * i;
-        L->B[4 * i + 0] = l[0];
-        L->B[4 * i + 1] = l[1];
-        L->B[4 * i + 2] = -l[3] * l[0];
-        L->B[4 * i + 3] = l[2] - l[3] * l[1];
-    }
+    memcpy(L->lam, lam, sizeof(double) * 4 * L->N);
     for (int a = 0; a < L->g.dim; a++) {
         long m = nfaces(&L->g, a);
         memcpy(L->fa[a], fa[a], sizeof(double) * m);
@@ -561,19 +559,16 @@ static void fill_level0(level *L, const double *lam, double *const fa[3], double
     }
 }
 
-/* Per-field || D^{-1} r' ||_2 of the eliminated residual r' = (res_T,
- * res_p - l4 res_T) of the paper's residual res. */
-static void scaled_norms(const level *L0, const double *lam, const double *res, double out[2])
+/* Per-field || D^{-1} res ||_2 with D the cell's 2x2 diagonal block. */
+static void scaled_norms(const level *L0, const double *res, double out[2])
 {
     double s0 = 0.0, s1 = 0.0;
     for (long i = 0; i < L0->N; i++) {
         int c[3];
         cell_of(&L0->g, i, c);
-        double D[4], rr[2], z[2];
+        double D[4], z[2];
         diag_block(L0, c, D);
-        rr[0] = res[2 * i];
-        rr[1] = res[2 * i + 1] - lam[4 * i + 3] * res[2 * i];
-        solve2(D, rr, z);
+        solve2(D, res + 2 * i, z);
         s0 += z[0] * z[0];
         s1 += z[1] * z[1];
     }
@@ -630,7 +625,7 @@ int orc_mg_solve(const orc_grid *g, const double *lam, double *const fa[3], doub
         orc_apply_paper(g, lam, fa, fk, x, res, 0);
         for (long i = 0; i < 2 * N; i++) res[i] = b[i] - res[i];
         double nk[2];
-        scaled_norms(&Ls[0], lam, res, nk);
+        scaled_norms(&Ls[0], res, nk);
         if (hist) { hist[2 * k] = nk[0]; hist[2 * k + 1] = nk[1]; }
         if (k == 0) { n0[0] = nk[0]; n0[1] = nk[1]; }
         /* step 2: stop when small enough */
@@ -640,13 +635,9 @@ int orc_mg_solve(const orc_grid *g, const double *lam, double *const fa[3], doub
             double q1 = n0[1] > 0.0 ? nk[1] / n0[1] : 0.0;
             if (q0 <= rtol && q1 <= rtol) break;
         }
-        /* step 3: L(da) ~= res by one V-cycle on the eliminated system from da = 0 */
-        for (long i = 0; i < N; i++) {
-            Ls[0].rhs[2 * i] = res[2 * i];
-            Ls[0].rhs[2 * i + 1] = res[2 * i + 1] - lam[4 * i + 3] * res[2 * i];
-            Ls[0].u[2 * i] = 0.0;
-            Ls[0].u[2 * i + 1] = 0.0;
-        }
+        /* step 3: L(da) ~= res by one V-cycle from da = 0 */
+        memcpy(Ls[0].rhs, res, sizeof(double) * 2 * N);
+        memset(Ls[0].u, 0, sizeof(double) * 2 * N);
         rc = vcycle(Ls, 0, nlev, nu1, nu2);
         if (rc) goto done;
         /* step 4: a += da */
@@ -661,18 +652,15 @@ done:
     return rc;
 }
 
-/* In-place red-black block Gauss-Seidel sweeps on the eliminated system of
- * level 0 with the grid's Dirichlet values (used to check single sweeps). */
+/* In-place red-black block Gauss-Seidel sweeps on level 0 with the grid's
+ * Dirichlet values (used to check single sweeps). */
 int orc_rbgs_sweeps(const orc_grid *g, const double *lam, double *const fa[3],
                     double *const fk[3], const double *b, double *x, int sweeps)
 {
     level L;
     if (alloc_level(&L, g)) { free_level(&L); return -2; }
     fill_level0(&L, lam, fa, fk);
-    for (long i = 0; i < L.N; i++) {
-        L.rhs[2 * i] = b[2 * i];
-        L.rhs[2 * i + 1] = b[2 * i + 1] - lam[4 * i + 3] * b[2 * i];
-    }
+    memcpy(L.rhs, b, sizeof(double) * 2 * L.N);
     memcpy(L.u, x, sizeof(double) * 2 * L.N);
     for (int s = 0; s < sweeps; s++) rbgs_sweep(&L, &L.g.bcT[0][0], &L.g.bcp[0][0]);
     memcpy(x, L.u, sizeof(double) * 2 * L.N);
@@ -680,7 +668,7 @@ int orc_rbgs_sweeps(const orc_grid *g, const double *lam, double *const fa[3],
     return 0;
 }
 
-/* Per-field || D^{-1} r' ||_2 of the current x (the stopping norm). */
+/* Per-field || D^{-1} res ||_2 of the current x (the stopping norm). */
 int orc_residual_norms(const orc_grid *g, const double *lam, double *const fa[3],
                        double *const fk[3], const double *b, const double *x, double out[2])
 {
@@ -691,14 +679,14 @@ int orc_residual_norms(const orc_grid *g, const double *lam, double *const fa[3]
     fill_level0(&L, lam, fa, fk);
     orc_apply_paper(g, lam, fa, fk, x, res, 0);
     for (long i = 0; i < 2 * N; i++) res[i] = b[i] - res[i];
-    scaled_norms(&L, lam, res, out);
+    scaled_norms(&L, res, out);
     free(res);
     free_level(&L);
     return 0;
 }
 
 /* Coarse-level data of the hierarchy, for comparing set-up steps:
- * writes level l's eliminated blocks (N_l x 4) and face coefficients. */
+ * writes level l's l1..l4 (N_l x 4) and face coefficients. */
 int orc_level_coeffs(const orc_grid *g, const double *lam, double *const fa[3],
                      double *const fk[3], int coarse_min, int l, double *B_out,
                      double *const fa_out[3], double *const fk_out[3])
@@ -712,7 +700,7 @@ int orc_level_coeffs(const orc_grid *g, const double *lam, double *const fa[3],
     fill_level0(&Ls[0], lam, fa, fk);
     for (int q = 1; q <= l; q++)
         if (coarsen(&Ls[q - 1], &Ls[q])) { rc = -2; goto done; }
-    memcpy(B_out, Ls[l].B, sizeof(double) * 4 * Ls[l].N);
+    memcpy(B_out, Ls[l].lam, sizeof(double) * 4 * Ls[l].N);
     for (int a = 0; a < g->dim; a++) {
         long m = nfaces(&Ls[l].g, a);
         memcpy(fa_out[a], Ls[l].fa[a], sizeof(double) * m);

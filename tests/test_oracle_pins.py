@@ -272,8 +272,8 @@ def test_adiabatic_limit_k_zero(orc):
 
 
 def test_rbgs_sweep_is_block_gauss_seidel(orc):
-    """One sweep equals the block Gauss-Seidel step of the assembled matrix
-    with red cells ordered before black ones, on the eliminated system."""
+    """One sweep equals the block Gauss-Seidel step of the assembled matrix of
+    Eqs. 27-28 (2x2 blocks per cell) with red cells ordered before black ones."""
     g = GRIDS["2d_mixed"]
     rng = np.random.default_rng(10)
     lam, fa, fk = rand_lam(g.N, rng), rand_faces(g, rng), rand_faces(g, rng)
@@ -283,17 +283,12 @@ def test_rbgs_sweep_is_block_gauss_seidel(orc):
     M, aff = fv.paper_operator(g, lam, fa, fk)
     M = M.toarray()
     rhs = b.reshape(-1) - aff
-    # eliminate: p-row -= l4 * T-row
-    E = np.eye(2 * g.N)
-    for i in range(g.N):
-        E[2 * i + 1, 2 * i] = -lam[i, 3]
-    Me, re = E @ M, E @ rhs
     idx = np.arange(g.N)
     ii, jj = idx % g.n[0], idx // g.n[0]
     red = ((ii + jj) % 2 == 0)
     order = np.concatenate([np.flatnonzero(red), np.flatnonzero(~red)])
     perm = np.stack([2 * order, 2 * order + 1], axis=1).reshape(-1)
-    Mp, rp, xp = Me[perm][:, perm], re[perm], x0.reshape(-1)[perm]
+    Mp, rp, xp = M[perm][:, perm], rhs[perm], x0.reshape(-1)[perm]
     # block lower triangle (2x2 diagonal blocks included) and strict upper part
     Lo = np.zeros_like(Mp)
     for r in range(2 * g.N):
@@ -307,23 +302,22 @@ def test_rbgs_sweep_is_block_gauss_seidel(orc):
 
 
 def test_stopping_norm_single_cell(orc):
-    """On one cell with walls there are no fluxes, D = B and D^-1 r' =
-    B^-1 b' - x with b' the eliminated right-hand side."""
+    """On one cell with walls there are no fluxes: D = [[l1, l2], [0, l3]]
+    and D^-1 r = D^-1 b - x."""
     g = I.Grid(dim=2, axisym=0, n=(1, 1, 1), h=1.0)
     lam = np.array([[-2.0, 0.5, -3.0, 0.25]])
     b = np.array([[1.0, -4.0]])
     x = np.array([[0.3, 0.7]])
     out = orc.residual_norms(g.as_dict(), lam, [np.ones(2)] * 2, [np.ones(2)] * 2, b, x)
-    B = np.array([[-2.0, 0.5], [0.5, -3.0 - 0.125]])
-    bp = np.array([1.0, -4.0 - 0.25 * 1.0])
-    z = np.linalg.solve(B, bp) - x[0]
+    B = np.array([[-2.0, 0.5], [0.0, -3.0]])
+    z = np.linalg.solve(B, b[0]) - x[0]
     assert out == pytest.approx(np.abs(z), rel=1e-14)
 
 
 def test_coarse_coefficients_weighting(orc):
     """Axisymmetric coarsening on a hand-computed case: a coarse z-face is the
-    radius-weighted mean of its fine faces; a coarse block the volume-weighted
-    mean of its children; constants are preserved."""
+    radius-weighted mean of its fine faces; coarse l1..l4 the volume-weighted
+    means of the children's; constants are preserved."""
     g = I.Grid(dim=2, axisym=1, n=(2, 2, 1), h=1.0, bc=((A, W), (W, W), (0, 0)))
     # children radii 0.5 and 1.5; z-faces (shape (n1+1, n0)) get k = 1 at r=0.5, 3 at r=1.5
     fk = [np.ones(3 * 2), np.array([1.0, 3.0] * 3)]
