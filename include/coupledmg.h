@@ -115,9 +115,10 @@ MG_API mg_status mg_create(const mg_grid *grid, const mg_options *opt, void *wor
 
 /* Coefficient intake and set-up (Eqs. 27-32): per-cell lambda [N][4] = l1..l4
  * and per-axis face arrays of 1/rho (face_alpha[a]) and k (face_k[a]) for
- * a < dim.  Builds the whole hierarchy on the device: row elimination
- * (p-row minus l4 times T-row), coarse coefficients and the exact coarsest
- * solve.  MG_ERR_INVALID_COEFF if a local block is singular or not finite. */
+ * a < dim.  Builds the whole hierarchy on the device: the per-cell 2x2 blocks
+ * of Eqs. 27-28, coarse coefficients (area-weighted faces, volume-weighted
+ * l1..l4) and the exact coarsest solve.  MG_ERR_INVALID_COEFF if an input is
+ * not finite or a local block is singular. */
 MG_API mg_status mg_set_coeffs(mg_handle *h, const double *lambda, const double *const face_alpha[3],
                         const double *const face_k[3], int on_device);
 
@@ -132,12 +133,12 @@ MG_API mg_status mg_solve(mg_handle *h, const double *rhs, double *x, int on_dev
 MG_API mg_status mg_apply(mg_handle *h, const double *x, double *y, int on_device);
 
 /* In place: `sweeps` red-black block Gauss-Seidel sweeps on the finest level
- * (red = even i+j+k first; each cell's 2x2 block solved exactly) of the
- * row-eliminated system with right-hand side rhs. */
+ * (red = even i+j+k first; each cell's two equations solved exactly for
+ * (T_i, p_i)) of L(x) = rhs. */
 MG_API mg_status mg_smooth(mg_handle *h, const double *rhs, double *x, int sweeps, int on_device);
 
-/* Per-field stopping norms ||D^-1 r||_2 (out[2], host) of x for rhs, where r
- * is the residual of the row-eliminated system and D its 2x2 diagonal block. */
+/* Per-field stopping norms ||D^-1 r||_2 (out[2], host) of x for rhs, where
+ * r = rhs - L(x) and D is each cell's 2x2 block of its own (T_i, p_i). */
 MG_API mg_status mg_residual_norms(mg_handle *h, const double *rhs, const double *x, int on_device,
                             double out[2]);
 

@@ -46,9 +46,11 @@ struct LevelBuf {
     double2 *x, *b;
     double2 *G[3];
     dq *D, *Dinv;
+    double *l4;
     float2 *x32, *b32;
     float2 *G32[3];
     fq *D32, *Dinv32;
+    float *l4_32;
 };
 
 }  // namespace
@@ -64,7 +66,6 @@ struct mg_handle {
     char *arena;
     size_t arena_bytes;
     bool owns_arena;
-    double *lam4;
     char *stage;
     size_t stage_bytes;
     int nc;                // unknowns of the coarsest level
@@ -177,12 +178,14 @@ void plan(mg_handle *h, char *base, size_t *bytes) {
         for (int a = 0; a < g.dim; a++) l.G[a] = P.take<double2>(l.nf[a]);
         l.D = P.take<dq>(l.N);
         l.Dinv = P.take<dq>(l.N);
+        l.l4 = P.take<double>(l.N);
         if (mixed) {
             l.x32 = P.take<float2>(l.N);
             l.b32 = P.take<float2>(l.N);
             for (int a = 0; a < g.dim; a++) l.G32[a] = P.take<float2>(l.nf[a]);
             l.D32 = P.take<fq>(l.N);
             l.Dinv32 = P.take<fq>(l.N);
+            l.l4_32 = P.take<float>(l.N);
         }
         h->nlev++;
         if (!can_coarsen(n, g.dim, h->opt.coarse_min) || h->nlev == kMaxLevels) break;
@@ -191,7 +194,6 @@ void plan(mg_handle *h, char *base, size_t *bytes) {
     const LevelBuf &f = h->L[0];
     const LevelBuf &c = h->L[h->nlev - 1];
     h->nc = (int)(2 * c.N);
-    h->lam4 = P.take<double>(f.N);
     long long maxnf = 0;
     for (int a = 0; a < g.dim; a++) maxnf = f.nf[a] > maxnf ? f.nf[a] : maxnf;
     h->stage_bytes = (size_t)std::max<long long>(32 * f.N, 16 * maxnf);
@@ -209,10 +211,11 @@ void plan(mg_handle *h, char *base, size_t *bytes) {
 
 template <typename R> Level<R> view(const LevelBuf &l);
 template <> Level<double> view<double>(const LevelBuf &l) {
-    return Level<double>{l.n[0], l.n[1], l.n[2], l.N, l.x, l.b, l.G[0], l.G[1], l.G[2], l.D, l.Dinv};
+    return Level<double>{l.n[0], l.n[1], l.n[2], l.N, l.x, l.b, l.G[0], l.G[1], l.G[2], l.D, l.Dinv, l.l4};
 }
 template <> Level<float> view<float>(const LevelBuf &l) {
-    return Level<float>{l.n[0], l.n[1], l.n[2], l.N, l.x32, l.b32, l.G32[0], l.G32[1], l.G32[2], l.D32, l.Dinv32};
+    return Level<float>{l.n[0], l.n[1], l.n[2], l.N, l.x32, l.b32, l.G32[0], l.G32[1], l.G32[2], l.D32, l.Dinv32,
+                        l.l4_32};
 }
 
 BcFlags bc_flags(const mg_grid &g) {
@@ -273,17 +276,17 @@ void enqueue_vcycle(const mg_handle *h, cudaStream_t s, int l) {
     }
     const LevelBuf &cb = h->L[l + 1];
     const bool tm = h->timing && l == 0;
-    if (tm) cudaEventRecord(h->ev[0], s);
+    if (tm) cudaEventRecordWithFlags(h->ev[0], s, cudaEventRecordExternal);
     enqueue_smooth<R, DIM>(h, s, l, h->opt.nu1);
-    if (tm) cudaEventRecord(h->ev[1], s);
+    if (tm) cudaEventRecordWithFlags(h->ev[1], s, cudaEventRecordExternal);
     k_residual_restrict<R, DIM><<<cell_grid(cb, DIM, cb.n[0]), kBlock, 0, s>>>(view<R>(lb), view<R>(cb));
     counted(h);
     enqueue_vcycle<R, DIM>(h, s, l + 1);
     k_prolong_add<R, DIM><<<cell_grid(lb, DIM, lb.n[0]), kBlock, 0, s>>>(view<R>(cb), view<R>(lb), bc_flags(h->grid));
     counted(h);
-    if (tm) cudaEventRecord(h->ev[2], s);
+    if (tm) cudaEventRecordWithFlags(h->ev[2], s, cudaEventRecordExternal);
     enqueue_smooth<R, DIM>(h, s, l, h->opt.nu2);
-    if (tm) cudaEventRecord(h->ev[3], s);
+    if (tm) cudaEventRecordWithFlags(h->ev[3], s, cudaEventRecordExternal);
 }
 
 template <int DIM>
@@ -384,7 +387,7 @@ mg_status x_out(mg_handle *h, double *x, int on_device) {
 template <int DIM>
 void enqueue_prep(mg_handle *h, const double2 *rhs) {
     const LevelBuf &f = h->L[0];
-    k_prep_rhs<DIM><<<cell_grid(f, DIM, f.n[0]), kBlock, 0, h->stream>>>(view<double>(f), rhs, h->lam4, bc_vals(h->grid),
+    k_prep_rhs<DIM><<<cell_grid(f, DIM, f.n[0]), kBlock, 0, h->stream>>>(view<double>(f), rhs, bc_vals(h->grid),
                                                                           h->grid.axisym, h->grid.r0, h->grid.h);
     counted(h);
 }
@@ -440,7 +443,7 @@ mg_status setup_hierarchy(mg_handle *h, const double *lam, const double *const f
         CK(cudaMemcpyAsync(h->stage, lam, sizeof(double) * 4 * f.N, cudaMemcpyHostToDevice, s));
         lam_d = reinterpret_cast<const double *>(h->stage);
     }
-    k_block0<<<lin_blocks(f.N), 256, 0, s>>>(lam_d, f.n[0], f.N, g.axisym, g.r0, g.h, f.D, h->lam4, h->err_d);
+    k_block0<<<lin_blocks(f.N), 256, 0, s>>>(lam_d, f.n[0], f.N, g.axisym, g.r0, g.h, f.D, f.l4, h->err_d);
     CK(cudaGetLastError());
     for (int a = 0; a < DIM; a++) {
         const double *al = fa[a], *kk = fk[a];
@@ -462,10 +465,13 @@ mg_status setup_hierarchy(mg_handle *h, const double *lam, const double *const f
         k_faces0<<<lin_blocks(f.nf[a]), 256, 0, s>>>(fg, al, kk, f.G[a], f.nf[a], h->err_d);
         CK(cudaGetLastError());
     }
+    double hl = g.h;
     for (int l = 1; l < h->nlev; l++) {
         const LevelBuf &F = h->L[l - 1];
         LevelBuf &C = h->L[l];
-        k_coarsen_blocks<DIM><<<lin_blocks(C.N), 256, 0, s>>>(F.D, F.n[0], F.n[1], C.D, C.n[0], C.n[1], C.n[2]);
+        k_coarsen_blocks<DIM><<<lin_blocks(C.N), 256, 0, s>>>(F.D, F.l4, F.n[0], F.n[1], C.D, C.l4, C.n[0], C.n[1],
+                                                              C.n[2], g.axisym, g.r0, hl);
+        hl *= 2.0;
         for (int a = 0; a < DIM; a++)
             k_coarsen_faces<DIM><<<lin_blocks(C.nf[a]), 256, 0, s>>>(a, F.G[a], F.n[0], F.n[1], C.G[a], C.n[0],
                                                                       C.n[1], C.n[2]);
@@ -474,13 +480,13 @@ mg_status setup_hierarchy(mg_handle *h, const double *lam, const double *const f
     for (int l = 0; l < h->nlev; l++) {
         LevelBuf &lb = h->L[l];
         k_diag<DIM><<<lin_blocks(lb.N), 256, 0, s>>>(lb.n[0], lb.n[1], lb.n[2], lb.G[0], lb.G[1],
-                                                     DIM == 3 ? lb.G[2] : nullptr, lb.D, lb.Dinv, h->err_d);
+                                                     DIM == 3 ? lb.G[2] : nullptr, lb.l4, lb.D, lb.Dinv, h->err_d);
         CK(cudaGetLastError());
     }
     const LevelBuf &c = h->L[h->nlev - 1];
     CK(cudaMemsetAsync(h->Mtmp, 0, sizeof(double) * h->nc * h->nc, s));
     k_coarse_assemble<DIM><<<lin_blocks(c.N), 256, 0, s>>>(c.n[0], c.n[1], c.n[2], c.G[0], c.G[1],
-                                                           DIM == 3 ? c.G[2] : nullptr, c.D, h->Mtmp);
+                                                           DIM == 3 ? c.G[2] : nullptr, c.D, c.l4, h->Mtmp);
     k_gauss_jordan<<<1, 1024, 0, s>>>(h->Mtmp, h->Minv, h->nc, h->err_d);
     CK(cudaGetLastError());
     if (h->opt.precision == MG_MIXED) {
@@ -490,12 +496,13 @@ mg_status setup_hierarchy(mg_handle *h, const double *lam, const double *const f
                 k_to_f32_v2<<<lin_blocks(lb.nf[a]), 256, 0, s>>>(lb.G[a], lb.G32[a], lb.nf[a]);
             k_to_f32_q<<<lin_blocks(lb.N), 256, 0, s>>>(lb.D, lb.D32, lb.N);
             k_to_f32_q<<<lin_blocks(lb.N), 256, 0, s>>>(lb.Dinv, lb.Dinv32, lb.N);
+            k_to_f32<<<lin_blocks(lb.N), 256, 0, s>>>(lb.l4, lb.l4_32, lb.N);
         }
         k_to_f32<<<lin_blocks((long long)h->nc * h->nc), 256, 0, s>>>(h->Minv, h->Minv32, (long long)h->nc * h->nc);
         CK(cudaGetLastError());
     }
     counted(h, 1 + DIM + (h->nlev - 1) * (1 + DIM) + h->nlev + 2 +
-                   (h->opt.precision == MG_MIXED ? h->nlev * (DIM + 2) + 1 : 0));
+                   (h->opt.precision == MG_MIXED ? h->nlev * (DIM + 3) + 1 : 0));
     int err = 0;
     CK(cudaMemcpyAsync(&err, h->err_d, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -710,10 +717,10 @@ mg_status mg_apply(mg_handle *h, const double *x, double *y, int on_device) {
     const LevelBuf &f = h->L[0];
     double2 *yd = on_device ? reinterpret_cast<double2 *>(y) : reinterpret_cast<double2 *>(h->stage);
     if (h->grid.dim == 2)
-        k_apply_paper<2><<<cell_grid(f, 2, f.n[0]), kBlock, 0, h->stream>>>(view<double>(f), h->lam4, bc_vals(h->grid),
+        k_apply_paper<2><<<cell_grid(f, 2, f.n[0]), kBlock, 0, h->stream>>>(view<double>(f), bc_vals(h->grid),
                                                                             h->grid.axisym, h->grid.r0, h->grid.h, yd);
     else
-        k_apply_paper<3><<<cell_grid(f, 3, f.n[0]), kBlock, 0, h->stream>>>(view<double>(f), h->lam4, bc_vals(h->grid),
+        k_apply_paper<3><<<cell_grid(f, 3, f.n[0]), kBlock, 0, h->stream>>>(view<double>(f), bc_vals(h->grid),
                                                                             h->grid.axisym, h->grid.r0, h->grid.h, yd);
     counted(h);
     CK(cudaGetLastError());

@@ -28,7 +28,8 @@ __device__ __forceinline__ fq ldgq(const fq *p) {
     return fq{u.x, u.y, u.z, u.w};
 }
 
-// Off-diagonal part of a row: sum over interior faces of G_f * u_nb (per field).
+// Off-diagonal part of the two rows: sT = sum over interior faces of G^T_f T_nb,
+// sp = sum of G^p_f p_nb + l4 * sT (the p-row's T-Laplacian term, Eq. 28).
 // Neighbours beyond the grid contribute nothing (homogeneous boundary values;
 // inhomogeneous Dirichlet data are folded into the right-hand side).
 template <typename R, int DIM>
@@ -49,12 +50,13 @@ __device__ __forceinline__ void offdiag(const Level<R> &L, const typename Vec<R>
         if (k > 0)        { V2 g = ldg2(L.G2 + c);      V2 u = ldg2(x + c - pl); sT += g.x * u.x; sp += g.y * u.y; }
         if (k < L.n2 - 1) { V2 g = ldg2(L.G2 + c + pl); V2 u = ldg2(x + c + pl); sT += g.x * u.x; sp += g.y * u.y; }
     }
+    sp += __ldg(L.l4 + c) * sT;
 }
 
 // ---------------------------------------------------------------------------
 // Smoothing: one colour of a red-black block Gauss-Seidel sweep.  Each thread
-// owns one cell of the colour (red: i+j+k even) and solves its 2x2 block:
-//   x_i = Dinv_i (b_i - sum_f G_f x_nb).
+// owns one cell of the colour (red: i+j+k even) and solves its two rows for
+// (T_i, p_i):  x_i = Dinv_i (b_i - offdiag_i).
 // Neighbours are of the other colour and are not written by this launch.
 // ---------------------------------------------------------------------------
 template <typename R, int DIM>
@@ -280,14 +282,15 @@ __global__ void __launch_bounds__(kReduceThreads) k_reduce_norms(const double2 *
 }
 
 // ---------------------------------------------------------------------------
-// Finest-level right-hand side: b0 = s_i (lambda_T, lambda_p - l4 lambda_T)
-// minus the Dirichlet boundary data of the row (G_f g for each boundary face).
+// Finest-level right-hand side: b0 = s_i (lambda_T, lambda_p) minus the
+// Dirichlet boundary data of the rows.
 // ---------------------------------------------------------------------------
 struct BcVals {
     int dir[3][2];
     double T[3][2], p[3][2];
 };
 
+// Dirichlet data of a boundary cell's rows: G^T g_T and G^p g_p + l4 G^T g_T.
 template <int DIM>
 __device__ __forceinline__ void boundary_data(const Level<double> &L, const BcVals &bv, int i, int j, int k,
                                               double &gT, double &gp) {
@@ -305,12 +308,12 @@ __device__ __forceinline__ void boundary_data(const Level<double> &L, const BcVa
         if (k == 0 && bv.dir[2][0])        { double2 g = L.G2[c];      gT += g.x * bv.T[2][0]; gp += g.y * bv.p[2][0]; }
         if (k == L.n2 - 1 && bv.dir[2][1]) { double2 g = L.G2[c + pl]; gT += g.x * bv.T[2][1]; gp += g.y * bv.p[2][1]; }
     }
+    gp += L.l4[cell_id(i, j, k, n0, n1)] * gT;
 }
 
 template <int DIM>
 __global__ void __launch_bounds__(kBX * kBY) k_prep_rhs(Level<double> L, const double2 *__restrict__ rhs,
-                                                      const double *__restrict__ lam4, BcVals bv, int axisym,
-                                                      double r0, double h) {
+                                                      BcVals bv, int axisym, double r0, double h) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     const int k = DIM == 3 ? (int)blockIdx.z : 0;
@@ -320,16 +323,13 @@ __global__ void __launch_bounds__(kBX * kBY) k_prep_rhs(Level<double> L, const d
     const double2 q = rhs[c];
     double gT, gp;
     boundary_data<DIM>(L, bv, i, j, k, gT, gp);
-    L.b[c] = make_double2(s * q.x - gT, s * (q.y - lam4[c] * q.x) - gp);
+    L.b[c] = make_double2(s * q.x - gT, s * q.y - gp);
 }
 
-// y = L(x) in the paper's form (Eqs. 27-28) from the row-scaled eliminated
-// data: E = offdiag + boundary data + D x is s_i times the eliminated rows, so
-// L_T = E_T / s_i and L_p = E_p / s_i + l4 L_T.
+// y = L(x) (Eqs. 27-28): offdiag + boundary data + D x is s_i times the rows.
 template <int DIM>
-__global__ void __launch_bounds__(kBX * kBY) k_apply_paper(Level<double> L, const double *__restrict__ lam4,
-                                                         BcVals bv, int axisym, double r0, double h,
-                                                         double2 *__restrict__ y) {
+__global__ void __launch_bounds__(kBX * kBY) k_apply_paper(Level<double> L, BcVals bv, int axisym, double r0,
+                                                         double h, double2 *__restrict__ y) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     const int k = DIM == 3 ? (int)blockIdx.z : 0;
@@ -341,9 +341,7 @@ __global__ void __launch_bounds__(kBX * kBY) k_apply_paper(Level<double> L, cons
     const double2 xx = L.x[c];
     const dq Dd = L.D[c];
     const double s = axisym ? r0 + (i + 0.5) * h : 1.0;
-    const double LT = (sT + gT + Dd.a * xx.x + Dd.b * xx.y) / s;
-    const double Ep = (sp + gp + Dd.c * xx.x + Dd.d * xx.y) / s;
-    y[c] = make_double2(LT, Ep + lam4[c] * LT);
+    y[c] = make_double2((sT + gT + Dd.a * xx.x + Dd.b * xx.y) / s, (sp + gp + Dd.c * xx.x + Dd.d * xx.y) / s);
 }
 
 // ---------------------------------------------------------------------------
@@ -380,7 +378,7 @@ __global__ void k_faces0(FaceGeom fg, const double *__restrict__ alpha, const do
     }
 }
 
-// Scaled eliminated block S = s_i [[l1, l2], [-l4 l1, l3 - l4 l2]]; keeps l4.
+// Scaled local terms S = s_i [[l1, l2], [0, l3]] (in the D array) and l4.
 __global__ void k_block0(const double *__restrict__ lam, int n0, long long N, int axisym, double r0, double h,
                          dq *__restrict__ S, double *__restrict__ lam4, int *__restrict__ err) {
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
@@ -388,25 +386,33 @@ __global__ void k_block0(const double *__restrict__ lam, int n0, long long N, in
         if (!isfinite(l1) || !isfinite(l2) || !isfinite(l3) || !isfinite(l4)) atomicOr(err, 1);
         const int i = (int)(c % n0);
         const double s = axisym ? r0 + (i + 0.5) * h : 1.0;
-        S[c] = dq{s * l1, s * l2, s * (-l4 * l1), s * (l3 - l4 * l2)};
+        S[c] = dq{s * l1, s * l2, 0.0, s * l3};
         lam4[c] = l4;
     }
 }
 
-// Coarse block = mean of the 2^DIM children's scaled blocks.
+// Coarse local terms: mean of the 2^DIM children's scaled terms (= s_C times
+// the volume-weighted mean l1..l3); coarse l4 = volume-weighted mean of l4.
 template <int DIM>
-__global__ void k_coarsen_blocks(const dq *__restrict__ Sf, int f0, int f1, dq *__restrict__ Sc, int c0, int c1,
-                                 int c2) {
+__global__ void k_coarsen_blocks(const dq *__restrict__ Sf, const double *__restrict__ l4f, int f0, int f1,
+                                 dq *__restrict__ Sc, double *__restrict__ l4c, int c0, int c1, int c2, int axisym,
+                                 double r0, double hf) {
     const long long Nc = (long long)c0 * c1 * c2;
     for (long long cc = blockIdx.x * (long long)blockDim.x + threadIdx.x; cc < Nc; cc += (long long)gridDim.x * blockDim.x) {
         const int I = (int)(cc % c0), J = (int)((cc / c0) % c1), K = (int)(cc / ((long long)c0 * c1));
-        double a = 0, b = 0, c = 0, d = 0;
+        double a = 0, b = 0, c = 0, d = 0, v4 = 0, vs = 0;
         for (int q = 0; q < (1 << DIM); q++) {
-            const dq s = Sf[cell_id(2 * I + (q & 1), 2 * J + ((q >> 1) & 1), DIM == 3 ? 2 * K + (q >> 2) : 0, f0, f1)];
+            const int i = 2 * I + (q & 1);
+            const long long f = cell_id(i, 2 * J + ((q >> 1) & 1), DIM == 3 ? 2 * K + (q >> 2) : 0, f0, f1);
+            const dq s = Sf[f];
+            const double sc = axisym ? r0 + (i + 0.5) * hf : 1.0;
             a += s.a; b += s.b; c += s.c; d += s.d;
+            v4 += sc * l4f[f];
+            vs += sc;
         }
         const double w = 1.0 / (1 << DIM);
         Sc[cc] = dq{a * w, b * w, c * w, d * w};
+        l4c[cc] = v4 / vs;
     }
 }
 
@@ -438,12 +444,12 @@ __global__ void k_coarsen_faces(int axis, const double2 *__restrict__ Gf, int fn
     }
 }
 
-// D = S - diag(sum of G^T, sum of G^p over all faces of the cell), in place,
-// and Dinv.  err |= 2 for a singular or non-finite block.
+// D = [[S.a - sum G^T, S.b], [-l4 sum G^T, S.d - sum G^p]] over all faces of
+// the cell, in place, and Dinv.  err |= 2 for a singular or non-finite block.
 template <int DIM>
 __global__ void k_diag(int n0, int n1, int n2, const double2 *__restrict__ G0, const double2 *__restrict__ G1,
-                       const double2 *__restrict__ G2, dq *__restrict__ D, dq *__restrict__ Dinv,
-                       int *__restrict__ err) {
+                       const double2 *__restrict__ G2, const double *__restrict__ l4, dq *__restrict__ D,
+                       dq *__restrict__ Dinv, int *__restrict__ err) {
     const long long N = (long long)n0 * n1 * n2;
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
         const int i = (int)(c % n0), j = (int)((c / n0) % n1), k = (int)(c / ((long long)n0 * n1));
@@ -458,6 +464,7 @@ __global__ void k_diag(int n0, int n1, int n2, const double2 *__restrict__ G0, c
         }
         dq s = D[c];
         s.a -= sT;
+        s.c -= l4[c] * sT;
         s.d -= sp;
         const double det = s.a * s.d - s.b * s.c;
         if (!(det != 0.0) || !isfinite(det)) atomicOr(err, 2);
@@ -484,12 +491,13 @@ __global__ void k_to_f32(const double *__restrict__ in, float *__restrict__ out,
         out[q] = (float)in[q];
 }
 
-// Dense matrix of the coarsest level (M zeroed beforehand): row 2c+f holds
-// D_c on the diagonal block and G_f on the neighbours of the same field.
+// Dense matrix of the coarsest level (M zeroed beforehand): rows 2c, 2c+1
+// hold D_c on the diagonal block; on a neighbour, G^T in the T-row, G^p and
+// l4 G^T in the p-row.
 template <int DIM>
 __global__ void k_coarse_assemble(int n0, int n1, int n2, const double2 *__restrict__ G0,
                                   const double2 *__restrict__ G1, const double2 *__restrict__ G2,
-                                  const dq *__restrict__ D, double *__restrict__ M) {
+                                  const dq *__restrict__ D, const double *__restrict__ l4, double *__restrict__ M) {
     const long long N = (long long)n0 * n1 * n2;
     const long long n = 2 * N;
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
@@ -501,8 +509,10 @@ __global__ void k_coarse_assemble(int n0, int n1, int n2, const double2 *__restr
         M[(2 * c + 1) * n + 2 * c + 1] = d.d;
         const long long f0 = (long long)i + (long long)(n0 + 1) * ((long long)j + (long long)n1 * k);
         const long long f1 = (long long)i + (long long)n0 * ((long long)j + (long long)(n1 + 1) * k);
+        const double w4 = l4[c];
         auto put = [&](long long nb, double2 g) {
             M[(2 * c) * n + 2 * nb] = g.x;
+            M[(2 * c + 1) * n + 2 * nb] = w4 * g.x;
             M[(2 * c + 1) * n + 2 * nb + 1] = g.y;
         };
         if (i > 0) put(c - 1, G0[f0]);

@@ -1,12 +1,11 @@
 // Device-side types of the coupled p-T multigrid (sm_103a).
 //
-// Every level stores the row-scaled, row-eliminated system
+// Every level stores Eqs. 27-28 with each cell's two rows multiplied by
+// s_i = V_i / h^dim (1 on Cartesian grids, r_i on axisymmetric ones):
 //
-//     sum_f G_f (u_nb - u_i) + S_i u_i = s_i * b'_i          (per cell i)
+//   T-row:  sum_f G^T_f (T_nb - T_i) + s l1 T_i + s l2 p_i              = s lambda_T
+//   p-row:  sum_f G^p_f (p_nb - p_i) + s l3 p_i + l4 sum_f G^T_f (T_nb - T_i) = s lambda_p
 //
-// obtained from Eqs. 27-28 by (1) subtracting l4 times the T-row from the
-// p-row, which removes div(k grad T) from the p-row, and (2) multiplying row
-// i by s_i = V_i / h^dim (1 on Cartesian grids, r_i on axisymmetric ones).
 // The scaling makes every face coefficient G_f = c_f * rho_f / h^2 the same
 // for both cells of the face (rho_f = r_f on r-faces, r_i on z-faces, 1 on
 // Cartesian grids), so restriction becomes a plain average of children and
@@ -16,8 +15,10 @@
 //
 // Per level and cell:
 //   x, b      pair (T, p)                      R2  (double2 / float2)
-//   D         2x2 diagonal block S_i - diag(sum_f G^T_f, sum_f G^p_f)
+//   D         the 2x2 block of (T_i, p_i) in the cell's two rows:
+//             [[s l1 - sum G^T, s l2], [-l4 sum G^T, s l3 - sum G^p]]
 //   Dinv      its inverse                      R4  (row-major 2x2)
+//   l4        the p-row's weight of the T-Laplacian (Eq. 32)
 // Per face, one array per axis:
 //   G         (G^T, G^p) = (k, 1/rho) times rho_f / h^2 times the boundary factor
 #pragma once
@@ -41,6 +42,7 @@ struct Level {
     typename Vec<R>::v2 *b;         // right-hand side of this level
     const typename Vec<R>::v2 *G0, *G1, *G2;   // face coefficients, axes 0..2
     const typename Vec<R>::q4 *D, *Dinv;
+    const R *l4;
 };
 
 // Dirichlet flags per axis and side (prolongation ghost signs).
