@@ -147,12 +147,18 @@ def test_converged_fp64_same_cycles_as_oracle(torch_cuda, orc, name):
 
 @pytest.mark.parametrize("name", list(CASES))
 def test_mixed_precision(torch_cuda, orc, name):
+    """FP32 cycles inside FP64 refinement against the converged FP64 oracle.
+    Literal regime: the workloads' stopping rule (1e-10 reduction) must give
+    1e-8.  Stiff regime: at 1e-10 the algebraic error of ANY solver is up to
+    cond(D^-1 A) * 1e-10 (~1e-7 here), so the solve runs to 1e-12 and must then
+    reach the same 1e-8, i.e. FP32 cycles lose nothing the FP64 loop needs."""
     p, _ = CASES[name]
-    s = _solver(p, precision="mixed", rtol=1e-10, max_cycles=40)
+    rtol = 1e-10 if name.startswith("literal") else 1e-12
+    s = _solver(p, precision="mixed", rtol=rtol, max_cycles=60)
     x = p.x0.copy()
     st = s.solve(p.b, x)
     ref, cyc, hist = orc.mg_solve(p.grid.as_dict(), p.lam, p.fa, p.fk, p.b, p.x0, max_cycles=80, rtol=1e-13)
-    assert max(st["rfinal"][f] / st["r0"][f] for f in range(2)) <= 1e-10
+    assert max(st["rfinal"][f] / st["r0"][f] for f in range(2)) <= rtol
     assert rel_dev(x, ref, p.x0) <= 1e-8
     s.close()
 
