@@ -154,6 +154,30 @@ MG_API mg_status mg_set_timing(mg_handle *h, int enable);
 MG_API mg_status mg_counters(const mg_handle *h, long long *launches, double *smooth_ms,
                              long long *smooth_launches, long long *smooth_cells);
 
+/* Allocation-free stopping norms (the paper has no counterpart: this is a
+ * library service).  For callers that cannot allocate device memory - their
+ * device memory is owned by another allocator, or their time loop must not
+ * call cudaMalloc/cudaFree, which can synchronise the whole device - and so
+ * cannot create an mg_handle: computes the same per-field norms
+ * ||D^-1 r||_2 as mg_residual_norms, r = rhs - L(x) of Eqs. 27-28, straight
+ * from the caller's arrays.
+ *   lambda [N][4], face_alpha[a] / face_k[a] (a < dim), rhs [N][2], x [N][2]:
+ *     device pointers in the layouts described at the top of this file.
+ *   out: device pointer to 2 doubles, receives (norm_T, norm_p).
+ *   stream: cudaStream_t for the work; the call returns after it completed.
+ * Allocates nothing: partial sums go to a static device array of 65536
+ * entries (1 MiB per GPU that loads the library, kept until exit), so grids
+ * of more than 65536 blocks of 32 x 8 cells (beyond 16,777,216 cells, e.g.
+ * 256^3 or 4096^2) are rejected with MG_ERR_INVALID_ARG.  Its device address
+ * is looked up the first time this is called on each device; make that first
+ * call before any stream capture.  Each call rewrites every partial it later
+ * reads, so no state carries over from the previous call, but all calls share
+ * the array: calls that overlap on the GPU (other streams, other threads)
+ * race and must be serialised by the caller. */
+MG_API mg_status mg_residual_norms_noalloc(const mg_grid *grid, const double *lambda,
+                                           const double *const face_alpha[3], const double *const face_k[3],
+                                           const double *rhs, const double *x, double *out, void *stream);
+
 /* Makes `device` the CUDA device this thread's later mg_create calls use
  * (the library's own runtime keeps a current device per thread). */
 MG_API mg_status mg_set_device(int device);

@@ -29,7 +29,7 @@ STATUS_NAMES = {0: "MG_OK", 1: "MG_ERR_INVALID_ARG", 2: "MG_ERR_OOM", 3: "MG_ERR
 # every entry point the header declares (checked by the CPU tests)
 EXPORTS = ["mg_default_options", "mg_workspace_size", "mg_create", "mg_set_coeffs", "mg_solve",
            "mg_apply", "mg_smooth", "mg_residual_norms", "mg_set_device", "mg_levels", "mg_destroy",
-           "mg_last_error", "mg_set_timing", "mg_counters"]
+           "mg_last_error", "mg_set_timing", "mg_counters", "mg_residual_norms_noalloc"]
 
 
 class MgError(RuntimeError):
@@ -90,6 +90,7 @@ def load(path: str = LIB_PATH):
             "mg_destroy": ([P], C.c_int),
             "mg_last_error": ([], C.c_char_p),
             "mg_set_timing": ([P, C.c_int], C.c_int),
+            "mg_residual_norms_noalloc": ([C.POINTER(MgGrid), P, pa3, pa3, P, P, P, P], C.c_int),
             "mg_counters": ([P, C.POINTER(C.c_longlong), C.POINTER(C.c_double), C.POINTER(C.c_longlong),
                              C.POINTER(C.c_longlong)], C.c_int),
         }
@@ -161,6 +162,22 @@ def _side(*arrays) -> bool:
     if len(flags) > 1:
         raise TypeError("mix of host and device arrays in one call")
     return flags.pop() if flags else False
+
+
+def residual_norms_noalloc(grid, lam, fa, fk, b, x, out, stream=None) -> None:
+    """mg_residual_norms_noalloc: every array a contiguous float64 CUDA tensor;
+    out (2 values) receives the per-field norms.  No device allocation."""
+    import torch
+    g = make_grid(grid)
+    pa = (C.c_void_p * 3)()
+    pk = (C.c_void_p * 3)()
+    for a in range(g.dim):
+        pa[a] = _ptr(fa[a], True)[0]
+        pk[a] = _ptr(fk[a], True)[0]
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    check(load().mg_residual_norms_noalloc(C.byref(g), _ptr(lam, True)[0], pa, pk, _ptr(b, True)[0],
+                                           _ptr(x, True)[0], _ptr(out, True)[0], C.c_void_p(stream.cuda_stream)))
 
 
 class Solver:

@@ -15,6 +15,7 @@
 #include <string>
 
 #include "coupledmg.h"
+#include "mg_host.h"
 #include "mg_kernels.cuh"
 
 using namespace cmg;
@@ -54,6 +55,11 @@ struct LevelBuf {
 };
 
 }  // namespace
+
+mg_status cmg::set_error(mg_status s, const char *msg) {
+    g_err = msg ? msg : "";
+    return s;
+}
 
 struct mg_handle {
     mg_grid grid;
