@@ -36,9 +36,10 @@ METRIC = "coupled p-T MG Mcell-Vcycles/s & solves/s at 1e-10 resid; HBM %peak; p
 UNIT = "Mcell-Vcycles/s"
 FALLBACK_HBM_GBS = 6800.0
 L2_FLUSH_BYTES = 256 << 20
-# algorithmic bytes per finest cell of one colour half-sweep (FP64, 2D):
-# x 16 + b 16 + Dinv 32 + faces 32 read, x 16 written per full sweep = 112 B
-SMOOTH_BYTES_PER_CELL_HALF = {("fp64", 2): 56.0, ("fp64", 3): 64.0, ("mixed", 2): 28.0, ("mixed", 3): 32.0}
+# algorithmic bytes per finest cell of one full red-black sweep:
+# read x 16 + b 16 + Dinv 32 + faces (2D 32, 3D 48) + l4 8, write x 16 (FP64);
+# half of that for the FP32 cycles of mixed precision
+SWEEP_BYTES_PER_CELL = {("fp64", 2): 120.0, ("fp64", 3): 136.0, ("mixed", 2): 60.0, ("mixed", 3): 68.0}
 
 
 def env_int(k, d):
@@ -197,9 +198,10 @@ def run_ours(args, rank, world):
     # roofline of the dominant kernel, from its live event timings
     c0 = counters[0]
     peak, peak_kind = measured_peak()
-    half_bytes = SMOOTH_BYTES_PER_CELL_HALF[(args.precision, probs[0].grid.dim)] * c0["smooth_cells"]
+    per_launch = (SWEEP_BYTES_PER_CELL[(args.precision, probs[0].grid.dim)] * c0["smooth_cells"]
+                  * c0["smooth_sweeps"] / max(1, c0["smooth_launches"]))
     avg_s = c0["smooth_ms"] / 1e3 / max(1, c0["smooth_launches"])
-    achieved = half_bytes / avg_s / 1e9 if avg_s > 0 else None
+    achieved = per_launch / avg_s / 1e9 if avg_s > 0 else None
     cycles = [st["cycles"] for st in stats[: len(probs)]]
 
     # end to end through the C ABI from host buffers (copies inside the timed region)
@@ -243,11 +245,13 @@ def run_ours(args, rank, world):
                    "solves_per_s": solves * world / tmax, "precision": args.precision,
                    "cycle": "V(2,2) red-black block GS, exact coarsest solve", "l2": "flushed between steps",
                    "parallelism": f"replicas x{world}"},
-        "roofline": {"bound": "hbm", "kernel": "k_rbgs_colour finest level (one colour per launch)",
+        "roofline": {"bound": "hbm",
+                     "kernel": ("k_rbgs_fused2d" if probs[0].grid.dim == 2 else "k_rbgs_colour")
+                     + " on the finest level of " + probs[0].name,
                      "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None, "peak_source": peak_kind,
-                     "algorithmic_bytes_per_launch": half_bytes, "avg_launch_us": avg_s * 1e6,
-                     "traffic": None},
+                     "algorithmic_bytes_per_launch": per_launch, "avg_launch_us": avg_s * 1e6,
+                     "launches_timed": c0["smooth_launches"], "traffic": args.traffic},
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": int(sum(c["launches"] for c in counters)),
@@ -307,6 +311,8 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--traffic", type=float, default=None,
+                    help="DRAM bytes per launch of the dominant kernel from an ncu capture (profiles/)")
     args = ap.parse_args()
     world = env_int("WORLD_SIZE", 1)
     rank = env_int("RANK", 0)

@@ -149,10 +149,11 @@ MG_API mg_status mg_residual_norms(mg_handle *h, const double *rhs, const double
  *   launches          kernels this handle launched (graph nodes counted per replay)
  *   smooth_ms         device time of the finest-level smoothing kernels (timing on)
  *   smooth_launches   how many such kernel launches that time covers
- *   smooth_cells      finest-level cells per smoothing launch */
+ *   smooth_sweeps     how many red-black sweeps those launches performed
+ *   smooth_cells      finest-level cells per sweep */
 MG_API mg_status mg_set_timing(mg_handle *h, int enable);
 MG_API mg_status mg_counters(const mg_handle *h, long long *launches, double *smooth_ms,
-                             long long *smooth_launches, long long *smooth_cells);
+                             long long *smooth_launches, long long *smooth_sweeps, long long *smooth_cells);
 
 /* Allocation-free stopping norms (the paper has no counterpart: this is a
  * library service).  For callers that cannot allocate device memory - their

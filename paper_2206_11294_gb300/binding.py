@@ -92,7 +92,7 @@ def load(path: str = LIB_PATH):
             "mg_set_timing": ([P, C.c_int], C.c_int),
             "mg_residual_norms_noalloc": ([C.POINTER(MgGrid), P, pa3, pa3, P, P, P, P], C.c_int),
             "mg_counters": ([P, C.POINTER(C.c_longlong), C.POINTER(C.c_double), C.POINTER(C.c_longlong),
-                             C.POINTER(C.c_longlong)], C.c_int),
+                             C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)], C.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -298,9 +298,10 @@ class Solver:
         check(self._lib.mg_set_timing(self._h, int(enable)))
 
     def counters(self) -> dict:
-        n, ms, sl, sc = C.c_longlong(), C.c_double(), C.c_longlong(), C.c_longlong()
-        check(self._lib.mg_counters(self._h, C.byref(n), C.byref(ms), C.byref(sl), C.byref(sc)))
-        return dict(launches=n.value, smooth_ms=ms.value, smooth_launches=sl.value, smooth_cells=sc.value)
+        n, ms, sl, sw, sc = C.c_longlong(), C.c_double(), C.c_longlong(), C.c_longlong(), C.c_longlong()
+        check(self._lib.mg_counters(self._h, C.byref(n), C.byref(ms), C.byref(sl), C.byref(sw), C.byref(sc)))
+        return dict(launches=n.value, smooth_ms=ms.value, smooth_launches=sl.value, smooth_sweeps=sw.value,
+                    smooth_cells=sc.value)
 
     def levels(self):
         n = C.c_int()

@@ -45,10 +45,12 @@ struct LevelBuf {
     long long N;
     long long nf[3];
     double2 *x, *b;
+    double2 *xalt;          // ping-pong partner of x for fused sweeps (2D)
     double2 *G[3];
     dq *D, *Dinv;
     double *l4;
     float2 *x32, *b32;
+    float2 *xalt32;
     float2 *G32[3];
     fq *D32, *Dinv32;
     float *l4_32;
@@ -91,6 +93,7 @@ struct mg_handle {
     cudaEvent_t ev[4];          // finest-level smoothing: pre start/end, post start/end
     double smooth_ms;
     long long smooth_launches;
+    long long smooth_sweeps;
 };
 
 namespace {
@@ -181,6 +184,7 @@ void plan(mg_handle *h, char *base, size_t *bytes) {
         }
         l.x = P.take<double2>(l.N);
         l.b = P.take<double2>(l.N);
+        if (g.dim == 2) l.xalt = P.take<double2>(l.N);
         for (int a = 0; a < g.dim; a++) l.G[a] = P.take<double2>(l.nf[a]);
         l.D = P.take<dq>(l.N);
         l.Dinv = P.take<dq>(l.N);
@@ -188,6 +192,7 @@ void plan(mg_handle *h, char *base, size_t *bytes) {
         if (mixed) {
             l.x32 = P.take<float2>(l.N);
             l.b32 = P.take<float2>(l.N);
+            if (g.dim == 2) l.xalt32 = P.take<float2>(l.N);
             for (int a = 0; a < g.dim; a++) l.G32[a] = P.take<float2>(l.nf[a]);
             l.D32 = P.take<fq>(l.N);
             l.Dinv32 = P.take<fq>(l.N);
@@ -252,16 +257,40 @@ unsigned lin_blocks(long long n) {
 // ---------------------------------------------------------------- V-cycle
 inline void counted(const mg_handle *h, long long n = 1) { const_cast<mg_handle *>(h)->enq += n; }
 
+template <typename R> typename Vec<R>::v2 *xalt_of(const LevelBuf &l);
+template <> double2 *xalt_of<double>(const LevelBuf &l) { return l.xalt; }
+template <> float2 *xalt_of<float>(const LevelBuf &l) { return l.xalt32; }
+
+// `sweeps` red-black sweeps on level l.  2D: pairs of sweeps run as fused
+// launches x -> xalt -> x; a leftover odd sweep (and every 3D sweep) runs as
+// two colour launches in place.  The result always ends in x.
 template <typename R, int DIM>
 void enqueue_smooth(const mg_handle *h, cudaStream_t s, int l, int sweeps) {
     const LevelBuf &lb = h->L[l];
+    Level<R> v = view<R>(lb);
+    int q = 0;
+    if (DIM == 2) {
+        const dim3 gf((unsigned)((lb.n[0] + kFTX - 1) / kFTX), (unsigned)((lb.n[1] + kFTY - 1) / kFTY), 1);
+        typename Vec<R>::v2 *xa = xalt_of<R>(lb);
+        for (; q + 1 < sweeps; q += 2) {
+            k_rbgs_fused2d<R><<<gf, kBlock, 0, s>>>(v, v.x, xa);
+            k_rbgs_fused2d<R><<<gf, kBlock, 0, s>>>(v, xa, v.x);
+            counted(h, 2);
+        }
+    }
     const dim3 gr = cell_grid(lb, DIM, (lb.n[0] + 1) / 2);
-    const Level<R> v = view<R>(lb);
-    for (int q = 0; q < sweeps; q++) {
+    for (; q < sweeps; q++) {
         k_rbgs_colour<R, DIM><<<gr, kBlock, 0, s>>>(v, 0);
         k_rbgs_colour<R, DIM><<<gr, kBlock, 0, s>>>(v, 1);
         counted(h, 2);
     }
+}
+
+// Kernel launches and sweeps of one call of enqueue_smooth.
+void smooth_launches(int dim, int sweeps, long long *launches, long long *sweeps_out) {
+    const int fused_pairs = dim == 2 ? sweeps / 2 : 0;
+    *launches = 2LL * fused_pairs + 2LL * (sweeps - 2 * fused_pairs);
+    *sweeps_out = sweeps;
 }
 
 template <typename R> const R *coarse_inverse(const mg_handle *h);
@@ -423,7 +452,11 @@ mg_status accumulate_timing(mg_handle *h) {
     CK(cudaEventElapsedTime(&a, h->ev[0], h->ev[1]));
     CK(cudaEventElapsedTime(&b, h->ev[2], h->ev[3]));
     h->smooth_ms += (double)a + (double)b;
-    h->smooth_launches += 2LL * (h->opt.nu1 + h->opt.nu2);
+    long long l1, s1, l2, s2;
+    smooth_launches(h->grid.dim, h->opt.nu1, &l1, &s1);
+    smooth_launches(h->grid.dim, h->opt.nu2, &l2, &s2);
+    h->smooth_launches += l1 + l2;
+    h->smooth_sweeps += s1 + s2;
     return MG_OK;
 }
 
@@ -493,7 +526,13 @@ mg_status setup_hierarchy(mg_handle *h, const double *lam, const double *const f
     CK(cudaMemsetAsync(h->Mtmp, 0, sizeof(double) * h->nc * h->nc, s));
     k_coarse_assemble<DIM><<<lin_blocks(c.N), 256, 0, s>>>(c.n[0], c.n[1], c.n[2], c.G[0], c.G[1],
                                                            DIM == 3 ? c.G[2] : nullptr, c.D, c.l4, h->Mtmp);
-    k_gauss_jordan<<<1, 1024, 0, s>>>(h->Mtmp, h->Minv, h->nc, h->err_d);
+    if (h->nc <= kGJSmemMax) {
+        const size_t smem = sizeof(double) * h->nc * h->nc;
+        CK(cudaFuncSetAttribute(k_gauss_jordan_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_gauss_jordan_smem<<<1, dim3(32, 32, 1), smem, s>>>(h->Mtmp, h->Minv, h->nc, h->err_d);
+    } else {
+        k_gauss_jordan<<<1, 1024, 0, s>>>(h->Mtmp, h->Minv, h->nc, h->err_d);
+    }
     CK(cudaGetLastError());
     if (h->opt.precision == MG_MIXED) {
         for (int l = 0; l < h->nlev; l++) {
@@ -776,16 +815,18 @@ mg_status mg_set_timing(mg_handle *h, int enable) {
     h->enq = 0;
     h->smooth_ms = 0.0;
     h->smooth_launches = 0;
+    h->smooth_sweeps = 0;
     return MG_OK;
 }
 
 mg_status mg_counters(const mg_handle *h, long long *launches, double *smooth_ms, long long *smooth_launches,
-                      long long *smooth_cells) {
+                      long long *smooth_sweeps, long long *smooth_cells) {
     mg_status st = check_handle(h, false);
     if (st) return st;
     if (launches) *launches = h->enq;
     if (smooth_ms) *smooth_ms = h->smooth_ms;
     if (smooth_launches) *smooth_launches = h->smooth_launches;
+    if (smooth_sweeps) *smooth_sweeps = h->smooth_sweeps;
     if (smooth_cells) *smooth_cells = h->L[0].N;
     return MG_OK;
 }

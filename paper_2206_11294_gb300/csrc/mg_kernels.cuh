@@ -78,6 +78,92 @@ __global__ void __launch_bounds__(kBX * kBY) k_rbgs_colour(Level<R> L, int colou
 }
 
 // ---------------------------------------------------------------------------
+// Fused 2D sweep: one launch does a whole red-black sweep (red, then black)
+// from xin to xout.  A CTA owns a kFTX x kFTY tile.  It stages xin with a
+// halo of 2 in shared memory, updates the red cells of the tile and of a
+// one-cell ring around it (the ring's red values are what the tile's black
+// cells see; neighbouring CTAs compute the same values), then the tile's
+// black cells, and writes the tile.  Reading xin and writing xout (distinct
+// buffers) keeps CTAs from seeing each other's updates.  Same arithmetic as
+// two k_rbgs_colour launches.
+// ---------------------------------------------------------------------------
+constexpr int kFTX = 64, kFTY = 16;
+
+template <typename R>
+__device__ __forceinline__ void offdiag_tile2d(const Level<R> &L, const typename Vec<R>::v2 (*xs)[kFTX + 4], int lx,
+                                               int ly, int i, int j, long long c, R &sT, R &sp) {
+    using V2 = typename Vec<R>::v2;
+    const int n0 = L.n0, n1 = L.n1;
+    sT = R(0);
+    sp = R(0);
+    const long long f0 = (long long)i + (long long)(n0 + 1) * j;
+    if (i > 0)      { V2 g = ldg2(L.G0 + f0);     V2 u = xs[ly][lx - 1]; sT += g.x * u.x; sp += g.y * u.y; }
+    if (i < n0 - 1) { V2 g = ldg2(L.G0 + f0 + 1); V2 u = xs[ly][lx + 1]; sT += g.x * u.x; sp += g.y * u.y; }
+    const long long f1 = (long long)i + (long long)n0 * j;
+    if (j > 0)      { V2 g = ldg2(L.G1 + f1);      V2 u = xs[ly - 1][lx]; sT += g.x * u.x; sp += g.y * u.y; }
+    if (j < n1 - 1) { V2 g = ldg2(L.G1 + f1 + n0); V2 u = xs[ly + 1][lx]; sT += g.x * u.x; sp += g.y * u.y; }
+    sp += __ldg(L.l4 + c) * sT;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_rbgs_fused2d(Level<R> L, const typename Vec<R>::v2 *__restrict__ xin,
+                                                      typename Vec<R>::v2 *__restrict__ xout) {
+    using V2 = typename Vec<R>::v2;
+    __shared__ V2 xs[kFTY + 4][kFTX + 4];
+    const int n0 = L.n0, n1 = L.n1;
+    const int i0 = blockIdx.x * kFTX, j0 = blockIdx.y * kFTY;
+    const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+    // stage xin, halo 2 (cells beyond the grid are never read)
+    for (int q = tid; q < (kFTY + 4) * (kFTX + 4); q += 256) {
+        const int ly = q / (kFTX + 4), lx = q - ly * (kFTX + 4);
+        const int gi = i0 + lx - 2, gj = j0 + ly - 2;
+        if (gi >= 0 && gi < n0 && gj >= 0 && gj < n1) xs[ly][lx] = ldg2(xin + (long long)gj * n0 + gi);
+    }
+    __syncthreads();
+    // red cells ((i + j) even) of the tile and its one-cell ring
+    constexpr int kRedPerRow = (kFTX + 2) / 2;
+    for (int q = tid; q < (kFTY + 2) * kRedPerRow; q += 256) {
+        const int ry = q / kRedPerRow, rx = q - ry * kRedPerRow;
+        const int gj = j0 - 1 + ry;
+        const int gi = i0 - 1 + 2 * rx + ((i0 - 1 + gj) & 1);
+        if (gi < 0 || gi >= n0 || gj < 0 || gj >= n1) continue;
+        const int lx = gi - i0 + 2, ly = gj - j0 + 2;
+        const long long c = (long long)gj * n0 + gi;
+        R sT, sp;
+        offdiag_tile2d<R>(L, xs, lx, ly, gi, gj, c, sT, sp);
+        const V2 bb = ldg2(L.b + c);
+        const auto Di = ldgq(L.Dinv + c);
+        const R rT = bb.x - sT, rp = bb.y - sp;
+        xs[ly][lx] = mk2<R>(Di.a * rT + Di.b * rp, Di.c * rT + Di.d * rp);
+    }
+    __syncthreads();
+    // black cells of the tile; each thread writes a pair of adjacent cells
+    constexpr int kPairs = kFTX / 2;
+    for (int q = tid; q < kFTY * kPairs; q += 256) {
+        const int ty = q / kPairs, px = q - ty * kPairs;
+        const int gj = j0 + ty;
+        if (gj >= n1) continue;
+#pragma unroll
+        for (int e = 0; e < 2; e++) {
+            const int gi = i0 + 2 * px + e;
+            if (gi >= n0) continue;
+            const int lx = gi - i0 + 2, ly = ty + 2;
+            const long long c = (long long)gj * n0 + gi;
+            V2 v = xs[ly][lx];
+            if ((gi + gj) & 1) {
+                R sT, sp;
+                offdiag_tile2d<R>(L, xs, lx, ly, gi, gj, c, sT, sp);
+                const V2 bb = ldg2(L.b + c);
+                const auto Di = ldgq(L.Dinv + c);
+                const R rT = bb.x - sT, rp = bb.y - sp;
+                v = mk2<R>(Di.a * rT + Di.b * rp, Di.c * rT + Di.d * rp);
+            }
+            xout[c] = v;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Residual of the children, restricted: coarse b = mean of the 2^DIM
 // children's residuals (plain mean in the row-scaled form = volume-weighted
 // mean of the physical residuals).  Also zeroes the coarse initial guess.
@@ -525,6 +611,85 @@ __global__ void k_coarse_assemble(int n0, int n1, int n2, const double2 *__restr
             if (k < n2 - 1) put(c + pl, G2[c + pl]);
         }
     }
+}
+
+// In-place Gauss-Jordan inversion with row pivoting, the whole matrix in
+// shared memory (n <= kGJSmemMax): for each column k the pivot row is swapped
+// in, the pivot row scaled and every other row eliminated, the eliminated
+// column k then holding column k of the inverse; the row swaps are undone as
+// column swaps at the end (inv(P A) P = inv(A)).  One block of 32 x 32 threads.
+// err |= 4 on a zero pivot.
+constexpr int kGJSmemMax = 160;
+
+__global__ void __launch_bounds__(1024) k_gauss_jordan_smem(const double *__restrict__ M, double *__restrict__ Minv,
+                                                            int n, int *__restrict__ err) {
+    extern __shared__ double a[];          // n x n, row-major
+    __shared__ double rowk[kGJSmemMax], colf[kGJSmemMax];
+    __shared__ int perm[kGJSmemMax];
+    __shared__ int piv_row;
+    __shared__ int bad;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int tid = tx + 32 * ty;
+    for (int q = tid; q < n * n; q += 1024) a[q] = M[q];
+    if (tid == 0) bad = 0;
+    __syncthreads();
+    for (int k = 0; k < n; k++) {
+        if (ty == 0) {                     // warp 0: pivot = largest |a[r][k]|, r >= k, lowest index on ties
+            double best = -1.0;
+            int br = k;
+            for (int r = k + tx; r < n; r += 32) {
+                const double v = fabs(a[r * n + k]);
+                if (v > best) { best = v; br = r; }
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                const double ov = __shfl_down_sync(0xffffffffu, best, o);
+                const int orr = __shfl_down_sync(0xffffffffu, br, o);
+                if (ov > best || (ov == best && orr < br)) { best = ov; br = orr; }
+            }
+            if (tx == 0) {
+                piv_row = br;
+                perm[k] = br;
+                if (!(best > 0.0)) bad = 1;
+            }
+        }
+        __syncthreads();
+        if (bad) break;
+        const int pr = piv_row;
+        if (pr != k)
+            for (int c = tid; c < n; c += 1024) {
+                const double t = a[k * n + c];
+                a[k * n + c] = a[pr * n + c];
+                a[pr * n + c] = t;
+            }
+        __syncthreads();
+        const double ip = 1.0 / a[k * n + k];
+        for (int c = tid; c < n; c += 1024) rowk[c] = (c == k) ? ip : a[k * n + c] * ip;
+        for (int r = tid; r < n; r += 1024) colf[r] = (r == k) ? 0.0 : a[r * n + k];
+        __syncthreads();
+        for (int r = ty; r < n; r += 32) {
+            const double f = colf[r];
+            for (int c = tx; c < n; c += 32) {
+                if (r == k) a[r * n + c] = rowk[c];
+                else a[r * n + c] = (c == k ? 0.0 : a[r * n + c]) - f * rowk[c];
+            }
+        }
+        __syncthreads();
+    }
+    if (bad) {
+        if (tid == 0) atomicOr(err, 4);
+        return;
+    }
+    for (int k = n - 1; k >= 0; k--) {     // undo the row swaps as column swaps
+        const int pk = perm[k];
+        if (pk != k)
+            for (int r = tid; r < n; r += 1024) {
+                const double t = a[r * n + k];
+                a[r * n + k] = a[r * n + pk];
+                a[r * n + pk] = t;
+            }
+        __syncthreads();
+    }
+    for (int q = tid; q < n * n; q += 1024) Minv[q] = a[q];
 }
 
 // Gauss-Jordan inversion with partial pivoting in one block (n <= 1024):
