@@ -155,6 +155,29 @@ MG_API mg_status mg_set_timing(mg_handle *h, int enable);
 MG_API mg_status mg_counters(const mg_handle *h, long long *launches, double *smooth_ms,
                              long long *smooth_launches, long long *smooth_sweeps, long long *smooth_cells);
 
+/* Batched solve of many independent problems in one set of launches
+ * (uneven sizes; SURVEY-level workload: many bubble grids per time step).
+ * The problems are handles created and given coefficients as usual; they
+ * must share dim, options (nu1, nu2, precision, rtol, max_cycles,
+ * inner_cycles), stream and device.  Each V-cycle stage runs as one
+ * persistent kernel over every problem's tiles, a whole cycle is one CUDA
+ * graph replay, and each problem stops on its own with mg_solve's rule, so
+ * its result is the one mg_solve gives.  The batch keeps pointers to the
+ * handles: destroy the batch before them. */
+typedef struct mg_batch mg_batch;
+MG_API mg_status mg_batch_create(int count, mg_handle *const *handles, mg_batch **out);
+
+/* rhs[p], x[p]: per problem, as in mg_solve (x in: initial guess, out:
+ * result); stats: NULL or count entries.  MG_ERR_NOT_CONVERGED if any
+ * problem reached max_cycles (all x and stats still written). */
+MG_API mg_status mg_batch_solve(mg_batch *b, const double *const *rhs, double *const *x, int on_device,
+                                mg_stats *stats);
+
+/* Kernels launched by this batch since creation (graph nodes per replay). */
+MG_API mg_status mg_batch_counters(const mg_batch *b, long long *launches);
+
+MG_API mg_status mg_batch_destroy(mg_batch *b);
+
 /* Allocation-free stopping norms (the paper has no counterpart: this is a
  * library service).  For callers that cannot allocate device memory - their
  * device memory is owned by another allocator, or their time loop must not

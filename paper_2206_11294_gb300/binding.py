@@ -29,7 +29,8 @@ STATUS_NAMES = {0: "MG_OK", 1: "MG_ERR_INVALID_ARG", 2: "MG_ERR_OOM", 3: "MG_ERR
 # every entry point the header declares (checked by the CPU tests)
 EXPORTS = ["mg_default_options", "mg_workspace_size", "mg_create", "mg_set_coeffs", "mg_solve",
            "mg_apply", "mg_smooth", "mg_residual_norms", "mg_set_device", "mg_levels", "mg_destroy",
-           "mg_last_error", "mg_set_timing", "mg_counters", "mg_residual_norms_noalloc"]
+           "mg_last_error", "mg_set_timing", "mg_counters", "mg_residual_norms_noalloc",
+           "mg_batch_create", "mg_batch_solve", "mg_batch_counters", "mg_batch_destroy"]
 
 
 class MgError(RuntimeError):
@@ -91,6 +92,10 @@ def load(path: str = LIB_PATH):
             "mg_last_error": ([], C.c_char_p),
             "mg_set_timing": ([P, C.c_int], C.c_int),
             "mg_residual_norms_noalloc": ([C.POINTER(MgGrid), P, pa3, pa3, P, P, P, P], C.c_int),
+            "mg_batch_create": ([C.c_int, C.POINTER(P), C.POINTER(P)], C.c_int),
+            "mg_batch_solve": ([P, C.POINTER(P), C.POINTER(P), C.c_int, C.POINTER(MgStats)], C.c_int),
+            "mg_batch_counters": ([P, C.POINTER(C.c_longlong)], C.c_int),
+            "mg_batch_destroy": ([P], C.c_int),
             "mg_counters": ([P, C.POINTER(C.c_longlong), C.POINTER(C.c_double), C.POINTER(C.c_longlong),
                              C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)], C.c_int),
         }
@@ -326,3 +331,54 @@ class Solver:
 
     def __exit__(self, *a):
         self.close()
+
+
+class Batch:
+    """mg_batch over existing Solvers (same dim, options, stream): one set of
+    launches per V-cycle stage for all of them."""
+
+    def __init__(self, solvers: Sequence["Solver"]):
+        self._lib = load()
+        self.solvers = list(solvers)
+        hs = (C.c_void_p * len(self.solvers))(*[s._h for s in self.solvers])
+        out = C.c_void_p()
+        check(self._lib.mg_batch_create(len(self.solvers), hs, C.byref(out)))
+        self._b = out
+
+    def solve(self, bs: Sequence, xs: Sequence, allow_not_converged: bool = False) -> list:
+        n = len(self.solvers)
+        if len(bs) != n or len(xs) != n:
+            raise ValueError("one rhs and one x per problem")
+        dev = _side(*bs, *xs)
+        keep = []
+        pb = (C.c_void_p * n)()
+        px = (C.c_void_p * n)()
+        for q, (s, b, x) in enumerate(zip(self.solvers, bs, xs)):
+            s._need(b, 2 * s.N, "rhs")
+            s._need(x, 2 * s.N, "x")
+            if not dev and not (isinstance(x, np.ndarray) and x.dtype == np.float64 and x.flags.c_contiguous):
+                raise TypeError("host x must be C-contiguous float64 numpy arrays (solved in place)")
+            p1, k1 = _ptr(b, dev)
+            p2, k2 = _ptr(x, dev)
+            pb[q], px[q] = p1, p2
+            keep += [k1, k2]
+        st = (MgStats * n)()
+        allow = (MG_OK, MG_ERR_NOT_CONVERGED) if allow_not_converged else (MG_OK,)
+        check(self._lib.mg_batch_solve(self._b, pb, px, int(dev), st), allow)
+        return [st[q].as_dict() for q in range(n)]
+
+    def launches(self) -> int:
+        n = C.c_longlong()
+        check(self._lib.mg_batch_counters(self._b, C.byref(n)))
+        return n.value
+
+    def close(self):
+        if getattr(self, "_b", None):
+            self._lib.mg_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

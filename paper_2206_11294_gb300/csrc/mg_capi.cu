@@ -8,11 +8,13 @@
 // V-cycle in place on x, which equals "correction from zero, then add" for a
 // linear cycle.  The mixed path solves the correction in FP32 from zero and
 // adds it in FP64.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <vector>
 
 #include "coupledmg.h"
 #include "mg_host.h"
@@ -82,6 +84,7 @@ struct mg_handle {
     double2 *partial;
     int npartial;
     double *norms_d;       // device: [2] latest norms
+    unsigned int *ticket;  // device: last-block counter of the norm kernels (re-armed by them)
     int *err_d;
     double *norms_h;       // pinned host: [2]
     bool coeffs_set;
@@ -216,6 +219,7 @@ void plan(mg_handle *h, char *base, size_t *bytes) {
     h->npartial = (int)(gg.x * gg.y * gg.z);
     h->partial = P.take<double2>(h->npartial);
     h->norms_d = P.take<double>(8);
+    h->ticket = P.take<unsigned int>(1);
     h->err_d = P.take<int>(1);
     *bytes = P.off + kAlign;
 }
@@ -327,17 +331,17 @@ void enqueue_vcycle(const mg_handle *h, cudaStream_t s, int l) {
 template <int DIM>
 void enqueue_norm(const mg_handle *h, cudaStream_t s) {
     const LevelBuf &f = h->L[0];
-    k_norm_partials<DIM><<<cell_grid(f, DIM, f.n[0]), kBlock, 0, s>>>(view<double>(f), h->partial);
-    k_reduce_norms<<<1, kReduceThreads, 0, s>>>(h->partial, h->npartial, h->norms_d);
-    counted(h, 2);
+    k_norm_partials<DIM><<<cell_grid(f, DIM, f.n[0]), kBlock, 0, s>>>(view<double>(f), h->partial, h->ticket,
+                                                                       h->norms_d);
+    counted(h);
 }
 
 template <int DIM>
 void enqueue_residual_to32(const mg_handle *h, cudaStream_t s) {
     const LevelBuf &f = h->L[0];
-    k_residual64_to32<DIM><<<cell_grid(f, DIM, f.n[0]), kBlock, 0, s>>>(view<double>(f), f.b32, f.x32, h->partial);
-    k_reduce_norms<<<1, kReduceThreads, 0, s>>>(h->partial, h->npartial, h->norms_d);
-    counted(h, 2);
+    k_residual64_to32<DIM><<<cell_grid(f, DIM, f.n[0]), kBlock, 0, s>>>(view<double>(f), f.b32, f.x32, h->partial,
+                                                                         h->ticket, h->norms_d);
+    counted(h);
 }
 
 // FP64: one V-cycle, then the stopping norm, copied to pinned host memory.
@@ -697,7 +701,9 @@ mg_status mg_create(const mg_grid *grid, const mg_options *opt, void *workspace,
     size_t dummy;
     plan(h, aligned, &dummy);
     if (cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaMallocHost(&h->norms_h, 8 * sizeof(double)) != cudaSuccess) {
+        cudaMallocHost(&h->norms_h, 8 * sizeof(double)) != cudaSuccess ||
+        cudaMemsetAsync(h->ticket, 0, sizeof(unsigned int), h->stream) != cudaSuccess ||
+        cudaStreamSynchronize(h->stream) != cudaSuccess) {
         cudaGetLastError();
         mg_destroy(h);
         return fail(MG_ERR_CUDA, "stream or pinned buffer creation failed");
@@ -864,3 +870,5 @@ mg_status mg_destroy(mg_handle *h) {
 const char *mg_last_error(void) { return g_err.c_str(); }
 
 }  // extern "C"
+
+#include "mg_batch.cuh"

@@ -59,14 +59,16 @@ __device__ __forceinline__ void offdiag(const Level<R> &L, const typename Vec<R>
 // (T_i, p_i):  x_i = Dinv_i (b_i - offdiag_i).
 // Neighbours are of the other colour and are not written by this launch.
 // ---------------------------------------------------------------------------
+// The work of thread block (bx, by, bz) of the launch geometry
+// (ceil(ceil(n0/2)/32), ceil(n1/8), n2); shared with the batched kernels.
 template <typename R, int DIM>
-__global__ void __launch_bounds__(kBX * kBY) k_rbgs_colour(Level<R> L, int colour) {
+__device__ __forceinline__ void rbgs_colour_block(const Level<R> &L, int colour, int bx, int by, int bz) {
     using V2 = typename Vec<R>::v2;
-    const int j = blockIdx.y * blockDim.y + threadIdx.y;
-    const int k = DIM == 3 ? (int)blockIdx.z : 0;
+    const int j = by * kBY + threadIdx.y;
+    const int k = DIM == 3 ? bz : 0;
     if (j >= L.n1) return;
     const int par = (j + k + colour) & 1;
-    const int i = 2 * (int)(blockIdx.x * blockDim.x + threadIdx.x) + par;
+    const int i = 2 * (bx * kBX + (int)threadIdx.x) + par;
     if (i >= L.n0) return;
     const long long c = cell_id(i, j, k, L.n0, L.n1);
     R sT, sp;
@@ -75,6 +77,11 @@ __global__ void __launch_bounds__(kBX * kBY) k_rbgs_colour(Level<R> L, int colou
     const auto Di = ldgq(L.Dinv + c);
     const R rT = bb.x - sT, rp = bb.y - sp;
     L.x[c] = mk2<R>(Di.a * rT + Di.b * rp, Di.c * rT + Di.d * rp);
+}
+
+template <typename R, int DIM>
+__global__ void __launch_bounds__(kBX * kBY) k_rbgs_colour(Level<R> L, int colour) {
+    rbgs_colour_block<R, DIM>(L, colour, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 // ---------------------------------------------------------------------------
@@ -105,14 +112,18 @@ __device__ __forceinline__ void offdiag_tile2d(const Level<R> &L, const typename
     sp += __ldg(L.l4 + c) * sT;
 }
 
+// Tile (bx, by) of the launch geometry (ceil(n0/64), ceil(n1/16)); shared with
+// the batched kernels (which call it repeatedly: it starts with a barrier so
+// the previous tile's readers are done with the shared stage).
 template <typename R>
-__global__ void __launch_bounds__(256) k_rbgs_fused2d(Level<R> L, const typename Vec<R>::v2 *__restrict__ xin,
-                                                      typename Vec<R>::v2 *__restrict__ xout) {
+__device__ __forceinline__ void rbgs_fused2d_block(const Level<R> &L, const typename Vec<R>::v2 *__restrict__ xin,
+                                                   typename Vec<R>::v2 *__restrict__ xout, int bx, int by) {
     using V2 = typename Vec<R>::v2;
     __shared__ V2 xs[kFTY + 4][kFTX + 4];
     const int n0 = L.n0, n1 = L.n1;
-    const int i0 = blockIdx.x * kFTX, j0 = blockIdx.y * kFTY;
+    const int i0 = bx * kFTX, j0 = by * kFTY;
     const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+    __syncthreads();
     // stage xin, halo 2 (cells beyond the grid are never read)
     for (int q = tid; q < (kFTY + 4) * (kFTX + 4); q += 256) {
         const int ly = q / (kFTX + 4), lx = q - ly * (kFTX + 4);
@@ -163,17 +174,23 @@ __global__ void __launch_bounds__(256) k_rbgs_fused2d(Level<R> L, const typename
     }
 }
 
+template <typename R>
+__global__ void __launch_bounds__(256) k_rbgs_fused2d(Level<R> L, const typename Vec<R>::v2 *__restrict__ xin,
+                                                      typename Vec<R>::v2 *__restrict__ xout) {
+    rbgs_fused2d_block<R>(L, xin, xout, blockIdx.x, blockIdx.y);
+}
+
 // ---------------------------------------------------------------------------
 // Residual of the children, restricted: coarse b = mean of the 2^DIM
 // children's residuals (plain mean in the row-scaled form = volume-weighted
 // mean of the physical residuals).  Also zeroes the coarse initial guess.
 // ---------------------------------------------------------------------------
 template <typename R, int DIM>
-__global__ void __launch_bounds__(kBX * kBY) k_residual_restrict(Level<R> F, Level<R> C) {
+__device__ __forceinline__ void residual_restrict_block(const Level<R> &F, const Level<R> &C, int bx, int by, int bz) {
     using V2 = typename Vec<R>::v2;
-    const int I = blockIdx.x * blockDim.x + threadIdx.x;
-    const int J = blockIdx.y * blockDim.y + threadIdx.y;
-    const int K = DIM == 3 ? (int)blockIdx.z : 0;
+    const int I = bx * kBX + threadIdx.x;
+    const int J = by * kBY + threadIdx.y;
+    const int K = DIM == 3 ? bz : 0;
     if (I >= C.n0 || J >= C.n1) return;
     R aT = R(0), ap = R(0);
 #pragma unroll
@@ -193,6 +210,11 @@ __global__ void __launch_bounds__(kBX * kBY) k_residual_restrict(Level<R> F, Lev
     C.x[cc] = mk2<R>(R(0), R(0));
 }
 
+template <typename R, int DIM>
+__global__ void __launch_bounds__(kBX * kBY) k_residual_restrict(Level<R> F, Level<R> C) {
+    residual_restrict_block<R, DIM>(F, C, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
 // ---------------------------------------------------------------------------
 // Prolongation and correction: fine x += cell-centred bi/tri-linear
 // interpolation of the coarse correction (weight 3/4 towards the parent and
@@ -201,36 +223,41 @@ __global__ void __launch_bounds__(kBX * kBY) k_residual_restrict(Level<R> F, Lev
 // Dirichlet faces (the correction vanishes there).
 // ---------------------------------------------------------------------------
 template <typename R, int DIM>
-__global__ void __launch_bounds__(kBX * kBY) k_prolong_add(Level<R> C, Level<R> F, BcFlags bc) {
+__device__ __forceinline__ void prolong_add_block(const Level<R> &C, const Level<R> &F, const BcFlags &bc, int bx,
+                                                  int by, int bz) {
     using V2 = typename Vec<R>::v2;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y * blockDim.y + threadIdx.y;
-    const int k = DIM == 3 ? (int)blockIdx.z : 0;
+    const int i = bx * kBX + threadIdx.x;
+    const int j = by * kBY + threadIdx.y;
+    const int k = DIM == 3 ? bz : 0;
     if (i >= F.n0 || j >= F.n1) return;
     const int P[3] = {i >> 1, j >> 1, k >> 1};
     const int s[3] = {(i & 1) ? 1 : -1, (j & 1) ? 1 : -1, (k & 1) ? 1 : -1};
     const int nC[3] = {C.n0, C.n1, C.n2};
-    // neighbour index and sign per axis
+    // neighbour index per axis; `neg` marks a ghost beyond a Dirichlet face
     int Qn[3];
-    R sg[3];
+    bool neg[3];
 #pragma unroll
     for (int a = 0; a < DIM; a++) {
         const int t = P[a] + s[a];
-        if (t < 0)             { Qn[a] = P[a]; sg[a] = bc.dir[a][0] ? R(-1) : R(1); }
-        else if (t >= nC[a])   { Qn[a] = P[a]; sg[a] = bc.dir[a][1] ? R(-1) : R(1); }
-        else                   { Qn[a] = t;    sg[a] = R(1); }
+        if (t < 0)           { Qn[a] = P[a]; neg[a] = bc.dir[a][0] != 0; }
+        else if (t >= nC[a]) { Qn[a] = P[a]; neg[a] = bc.dir[a][1] != 0; }
+        else                 { Qn[a] = t;    neg[a] = false; }
     }
+    // per-axis weights 3/4 (parent) and 1/4 (neighbour); products are exact
+    // constants, signs are applied by selection, not arithmetic
     R aT = R(0), ap = R(0);
 #pragma unroll
     for (int q = 0; q < (1 << DIM); q++) {
         int Q[3] = {P[0], P[1], DIM == 3 ? P[2] : 0};
-        R w = R(1);
+        bool flip = false;
+        int nq = 0;
 #pragma unroll
-        for (int a = 0; a < DIM; a++) {
-            if ((q >> a) & 1) { Q[a] = Qn[a]; w *= R(0.25) * sg[a]; }
-            else              { w *= R(0.75); }
-        }
-        const V2 e = ldg2(C.x + cell_id(Q[0], Q[1], Q[2], C.n0, C.n1));
+        for (int a = 0; a < DIM; a++)
+            if ((q >> a) & 1) { Q[a] = Qn[a]; flip ^= neg[a]; nq++; }
+        const R w = DIM == 2 ? (nq == 0 ? R(9.0 / 16) : nq == 1 ? R(3.0 / 16) : R(1.0 / 16))
+                             : (nq == 0 ? R(27.0 / 64) : nq == 1 ? R(9.0 / 64) : nq == 2 ? R(3.0 / 64) : R(1.0 / 64));
+        V2 e = ldg2(C.x + cell_id(Q[0], Q[1], Q[2], C.n0, C.n1));
+        if (flip) { e.x = -e.x; e.y = -e.y; }
         aT += w * e.x;
         ap += w * e.y;
     }
@@ -239,6 +266,11 @@ __global__ void __launch_bounds__(kBX * kBY) k_prolong_add(Level<R> C, Level<R> 
     xv.x += aT;
     xv.y += ap;
     F.x[c] = xv;
+}
+
+template <typename R, int DIM>
+__global__ void __launch_bounds__(kBX * kBY) k_prolong_add(Level<R> C, Level<R> F, BcFlags bc) {
+    prolong_add_block<R, DIM>(C, F, bc, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 // ---------------------------------------------------------------------------
@@ -287,11 +319,41 @@ __device__ __forceinline__ void block_sum2(double &a, double &b) {
     }
 }
 
+// Last-block completion: after a block stored its partial, the block that
+// draws the final ticket sums all partials in index order (deterministic),
+// writes sqrt of the two sums to out and re-arms the ticket counter.
+__device__ __forceinline__ void finish_norms(double2 *partial, int nblocks, unsigned int *ticket, double *out) {
+    __shared__ bool last;
+    const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+    const int nthr = blockDim.x * blockDim.y * blockDim.z;
+    if (tid == 0) {
+        __threadfence();
+        last = atomicAdd(ticket, 1u) == (unsigned)nblocks - 1u;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double a = 0.0, b = 0.0;
+    for (int q = tid; q < nblocks; q += nthr) {
+        const double2 v = __ldcg(partial + q);
+        a += v.x;
+        b += v.y;
+    }
+    block_sum2(a, b);
+    if (tid == 0) {
+        out[0] = sqrt(a);
+        out[1] = sqrt(b);
+        *ticket = 0u;
+    }
+}
+
+// Sums of (Dinv r)_T^2 and (Dinv r)_p^2 over block (bx, by, bz) of the cell
+// grid (ceil(n0/32), ceil(n1/8), n2); valid in thread 0.
 template <int DIM>
-__global__ void __launch_bounds__(kBX * kBY) k_norm_partials(Level<double> L, double2 *__restrict__ partial) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y * blockDim.y + threadIdx.y;
-    const int k = DIM == 3 ? (int)blockIdx.z : 0;
+__device__ __forceinline__ double2 norm_block(const Level<double> &L, int bx, int by, int bz) {
+    const int i = bx * kBX + threadIdx.x;
+    const int j = by * kBY + threadIdx.y;
+    const int k = DIM == 3 ? bz : 0;
     double zT2 = 0.0, zp2 = 0.0;
     if (i < L.n0 && j < L.n1) {
         const long long c = cell_id(i, j, k, L.n0, L.n1);
@@ -306,19 +368,27 @@ __global__ void __launch_bounds__(kBX * kBY) k_norm_partials(Level<double> L, do
         zp2 = zp * zp;
     }
     block_sum2(zT2, zp2);
+    return make_double2(zT2, zp2);
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(kBX * kBY) k_norm_partials(Level<double> L, double2 *__restrict__ partial,
+                                                           unsigned int *__restrict__ ticket, double *__restrict__ out) {
+    const double2 s = norm_block<DIM>(L, blockIdx.x, blockIdx.y, blockIdx.z);
     if (threadIdx.x == 0 && threadIdx.y == 0)
-        partial[blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)] = make_double2(zT2, zp2);
+        partial[blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)] = s;
+    finish_norms(partial, gridDim.x * gridDim.y * gridDim.z, ticket, out);
 }
 
 // FP64 residual of the finest level for mixed precision: r = b - A x is
 // written (rounded) as the FP32 right-hand side of the correction problem,
 // the FP32 correction is zeroed, and the norm partials of Dinv r are formed.
 template <int DIM>
-__global__ void __launch_bounds__(kBX * kBY) k_residual64_to32(Level<double> L, float2 *__restrict__ b32,
-                                                             float2 *__restrict__ e32, double2 *__restrict__ partial) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y * blockDim.y + threadIdx.y;
-    const int k = DIM == 3 ? (int)blockIdx.z : 0;
+__device__ __forceinline__ double2 residual64_to32_block(const Level<double> &L, float2 *__restrict__ b32,
+                                                         float2 *__restrict__ e32, int bx, int by, int bz) {
+    const int i = bx * kBX + threadIdx.x;
+    const int j = by * kBY + threadIdx.y;
+    const int k = DIM == 3 ? bz : 0;
     double zT2 = 0.0, zp2 = 0.0;
     if (i < L.n0 && j < L.n1) {
         const long long c = cell_id(i, j, k, L.n0, L.n1);
@@ -337,8 +407,18 @@ __global__ void __launch_bounds__(kBX * kBY) k_residual64_to32(Level<double> L, 
         e32[c] = make_float2(0.f, 0.f);
     }
     block_sum2(zT2, zp2);
+    return make_double2(zT2, zp2);
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(kBX * kBY) k_residual64_to32(Level<double> L, float2 *__restrict__ b32,
+                                                             float2 *__restrict__ e32, double2 *__restrict__ partial,
+                                                             unsigned int *__restrict__ ticket,
+                                                             double *__restrict__ out) {
+    const double2 s = residual64_to32_block<DIM>(L, b32, e32, blockIdx.x, blockIdx.y, blockIdx.z);
     if (threadIdx.x == 0 && threadIdx.y == 0)
-        partial[blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)] = make_double2(zT2, zp2);
+        partial[blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)] = s;
+    finish_norms(partial, gridDim.x * gridDim.y * gridDim.z, ticket, out);
 }
 
 // x64 += e32 (the refinement update)
@@ -628,6 +708,7 @@ __global__ void __launch_bounds__(1024) k_gauss_jordan_smem(const double *__rest
     __shared__ int perm[kGJSmemMax];
     __shared__ int piv_row;
     __shared__ int bad;
+    __shared__ double piv_inv;
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int tid = tx + 32 * ty;
     for (int q = tid; q < n * n; q += 1024) a[q] = M[q];
@@ -650,6 +731,7 @@ __global__ void __launch_bounds__(1024) k_gauss_jordan_smem(const double *__rest
                 piv_row = br;
                 perm[k] = br;
                 if (!(best > 0.0)) bad = 1;
+                else piv_inv = 1.0 / a[br * n + k];   // one FP64 division per column
             }
         }
         __syncthreads();
@@ -662,7 +744,7 @@ __global__ void __launch_bounds__(1024) k_gauss_jordan_smem(const double *__rest
                 a[pr * n + c] = t;
             }
         __syncthreads();
-        const double ip = 1.0 / a[k * n + k];
+        const double ip = piv_inv;
         for (int c = tid; c < n; c += 1024) rowk[c] = (c == k) ? ip : a[k * n + c] * ip;
         for (int r = tid; r < n; r += 1024) colf[r] = (r == k) ? 0.0 : a[r * n + k];
         __syncthreads();
@@ -700,7 +782,7 @@ __global__ void __launch_bounds__(1024) k_gauss_jordan(double *__restrict__ M, d
     __shared__ double pv[32];
     __shared__ int pi[32];
     __shared__ int piv_row;
-    __shared__ double piv_val;
+    __shared__ double piv_val, piv_inv;
     const int tid = threadIdx.x, nt = blockDim.x;
     for (long long q = tid; q < (long long)n * n; q += nt) Minv[q] = (q / n == q % n) ? 1.0 : 0.0;
     __syncthreads();
@@ -726,6 +808,7 @@ __global__ void __launch_bounds__(1024) k_gauss_jordan(double *__restrict__ M, d
                 if (pv[w] > b || (pv[w] == b && pi[w] < r)) { b = pv[w]; r = pi[w]; }
             piv_row = r;
             piv_val = M[(long long)r * n + col];
+            piv_inv = 1.0 / piv_val;
             if (!(b > 0.0)) atomicOr(err, 4);
         }
         __syncthreads();
@@ -742,7 +825,7 @@ __global__ void __launch_bounds__(1024) k_gauss_jordan(double *__restrict__ M, d
             }
         }
         __syncthreads();
-        const double ip = 1.0 / piv_val;
+        const double ip = piv_inv;
         for (int c = tid; c < n; c += nt) {
             M[(long long)col * n + c] *= ip;
             Minv[(long long)col * n + c] *= ip;

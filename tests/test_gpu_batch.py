@@ -1,0 +1,156 @@
+"""Batched solves (mg_batch_*): many independent problems of uneven sizes in
+one set of launches per V-cycle stage, each graph replay one cycle of all.
+
+Each problem's result must be the one mg_solve gives it alone (same cycles,
+same values: the batch runs the same per-block device code on the same data
+and stops each problem with the same rule), and the batch must agree with the
+oracle like the single path does.
+"""
+import numpy as np
+import pytest
+
+from paper_2206_11294_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+def rel_dev(x, ref, x0):
+    out = 0.0
+    for f in range(2):
+        d = ref[:, f] - x0[:, f]
+        out = max(out, np.linalg.norm(x[:, f] - ref[:, f]) / max(np.linalg.norm(d), 1e-300))
+    return out
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+def _problems_2d():
+    sizes = [64, 96, 128, 160, 224, 256, 96, 64, 320, 192]
+    out = []
+    for q, n in enumerate(sizes):
+        p = I.bubble_2d(n=n, seed=100 + q, n_bubbles=1 + q % 4, rmin=0.05, rmax=0.15, centred=False,
+                        gas_rho=1.0, name=f"b{q}")
+        if q % 3 == 2:          # some stiff members: more cycles, uneven stopping
+            p = I.bubble_2d(n=n, seed=100 + q, n_bubbles=2, rmin=0.05, rmax=0.15, centred=False, gas_rho=1.0,
+                            length=6.4e-3, dt=1e-5, name=f"s{q}")
+        out.append(p)
+    return out
+
+
+def _problems_3d():
+    return [I.random_coeff_problem(I.Grid(dim=3, axisym=0, n=n, h=1e-4, bc=((1, 1), (0, 1), (0, 1)),
+                                          bcT=((300, 300), (0, 300), (0, 300)),
+                                          bcp=((1e5, 1e5), (0, 1e5), (0, 1e5))), seed=200 + q, dt=1e-5)
+            for q, n in enumerate([(32, 32, 32), (64, 32, 16), (40, 24, 16), (16, 16, 16)])]
+
+
+def _solvers(probs, **kw):
+    from paper_2206_11294_gb300.binding import Solver
+    out = []
+    for p in probs:
+        s = Solver(p.grid, **kw)
+        s.set_coeffs(p.lam, p.fa, p.fk)
+        out.append(s)
+    return out
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("which", ["2d", "3d"])
+def test_batch_equals_solo(torch_cuda, precision, which):
+    from paper_2206_11294_gb300.binding import Batch
+    probs = _problems_2d() if which == "2d" else _problems_3d()
+    kw = dict(precision=precision, rtol=1e-10, max_cycles=60)
+    solo = _solvers(probs, **kw)
+    xs_solo, st_solo = [], []
+    for s, p in zip(solo, probs):
+        x = p.x0.copy()
+        st_solo.append(s.solve(p.b, x))
+        xs_solo.append(x)
+    batch = Batch(solo)
+    xs = [p.x0.copy() for p in probs]
+    st = batch.solve([p.b for p in probs], xs)
+    for q, p in enumerate(probs):
+        assert st[q]["cycles"] == st_solo[q]["cycles"], q
+        assert st[q]["status"] == "MG_OK"
+        assert rel_dev(xs[q], xs_solo[q], p.x0) <= 1e-13, q
+    # members stop at different cycle counts in the stiff/literal mix
+    if which == "2d":
+        assert len({s["cycles"] for s in st}) > 1
+    assert batch.launches() > 0
+    batch.close()
+    for s in solo:
+        s.close()
+
+
+def test_batch_membership_does_not_change_results(torch_cuda):
+    """A problem solved in a batch of one and in the full mix: bitwise equal."""
+    from paper_2206_11294_gb300.binding import Batch
+    probs = _problems_2d()
+    solvers = _solvers(probs, rtol=1e-10, max_cycles=60)
+    mix = Batch(solvers)
+    xs = [p.x0.copy() for p in probs]
+    mix.solve([p.b for p in probs], xs)
+    for q in (0, 4, 8):
+        one = Batch([solvers[q]])
+        x1 = probs[q].x0.copy()
+        one.solve([probs[q].b], [x1])
+        assert np.array_equal(x1, xs[q]), q
+        one.close()
+    mix.close()
+    for s in solvers:
+        s.close()
+
+
+def test_batch_vs_oracle(torch_cuda, orc):
+    from paper_2206_11294_gb300.binding import Batch
+    probs = _problems_2d()[:4]
+    solvers = _solvers(probs, rtol=0.0, max_cycles=3)
+    b = Batch(solvers)
+    xs = [p.x0.copy() for p in probs]
+    st = b.solve([p.b for p in probs], xs)
+    for q, p in enumerate(probs):
+        ref, cyc, _ = orc.mg_solve(p.grid.as_dict(), p.lam, p.fa, p.fk, p.b, p.x0, max_cycles=3, rtol=0.0)
+        assert st[q]["cycles"] == 3 == cyc
+        tol = 1e-12 if p.name.startswith("b") else 1e-9
+        assert rel_dev(xs[q], ref, p.x0) <= tol, q
+    b.close()
+    for s in solvers:
+        s.close()
+
+
+def test_batch_device_arrays_and_repeat(torch_cuda):
+    """Device-side per-problem arrays; two solves in a row give identical results."""
+    torch = torch_cuda
+    from paper_2206_11294_gb300.binding import Batch
+    probs = _problems_2d()[:5]
+    solvers = _solvers(probs, precision="mixed", rtol=1e-10, max_cycles=60)
+    b = Batch(solvers)
+    bs = [torch.from_numpy(p.b).cuda() for p in probs]
+    outs = []
+    for _ in range(2):
+        xs = [torch.from_numpy(p.x0.copy()).cuda() for p in probs]
+        b.solve(bs, xs)
+        outs.append([x.cpu().numpy() for x in xs])
+    for a, c in zip(*outs):
+        assert np.array_equal(a, c)
+    b.close()
+    for s in solvers:
+        s.close()
+
+
+def test_batch_rejects_mismatched_options(torch_cuda):
+    from paper_2206_11294_gb300.binding import Batch, MgError, MG_ERR_INVALID_ARG
+    probs = _problems_2d()[:2]
+    s1 = _solvers(probs[:1], rtol=1e-10)[0]
+    s2 = _solvers(probs[1:], rtol=1e-8)[0]
+    with pytest.raises(MgError) as e:
+        Batch([s1, s2])
+    assert e.value.status == MG_ERR_INVALID_ARG
+    s1.close()
+    s2.close()
