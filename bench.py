@@ -40,6 +40,13 @@ L2_FLUSH_BYTES = 256 << 20
 # read x 16 + b 16 + Dinv 32 + faces (2D 32, 3D 48) + l4 8, write x 16 (FP64);
 # half of that for the FP32 cycles of mixed precision
 SWEEP_BYTES_PER_CELL = {("fp64", 2): 120.0, ("fp64", 3): 136.0, ("mixed", 2): 60.0, ("mixed", 3): 68.0}
+# FP64 instructions per cell update of a sweep (each cell once per sweep):
+# neighbour products 2*2*dim (first a multiply, the rest FMAs), l4 * sT (1),
+# b - offdiag (2), the 2x2 Dinv product (4)
+SWEEP_FP64_INST_PER_CELL = {2: 15.0, 3: 19.0}
+# GB300 FP64 pipe: 1.25 TFLOP/s nominal = 2 FP64 FMA per clock per SM
+# (1.25e12 / (2 * 152 * 2.07e9) = 1.99); 152 SMs at 2.07 GHz
+FP64_INST_PEAK_G = 152 * 2 * 2.07
 
 
 def env_int(k, d):
@@ -198,10 +205,29 @@ def run_ours(args, rank, world):
     # roofline of the dominant kernel, from its live event timings
     c0 = counters[0]
     peak, peak_kind = measured_peak()
-    per_launch = (SWEEP_BYTES_PER_CELL[(args.precision, probs[0].grid.dim)] * c0["smooth_cells"]
-                  * c0["smooth_sweeps"] / max(1, c0["smooth_launches"]))
+    dim0 = probs[0].grid.dim
+    sweeps_per_launch = c0["smooth_sweeps"] / max(1, c0["smooth_launches"])
+    per_launch = SWEEP_BYTES_PER_CELL[(args.precision, dim0)] * c0["smooth_cells"] * sweeps_per_launch
     avg_s = c0["smooth_ms"] / 1e3 / max(1, c0["smooth_launches"])
     achieved = per_launch / avg_s / 1e9 if avg_s > 0 else None
+    fused = args.precision == "mixed" and dim0 == 2
+    kernel = ("k_rbgs_fused2d<float>" if fused else
+              f"k_rbgs_colour<{'double' if args.precision == 'fp64' else 'float'},{dim0}>") \
+        + " on the finest level of " + probs[0].name
+    hbm = {"bound": "hbm", "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "GB/s",
+           "frac": (achieved / peak) if achieved else None, "peak_source": peak_kind,
+           "algorithmic_bytes_per_launch": per_launch, "avg_launch_us": avg_s * 1e6,
+           "launches_timed": c0["smooth_launches"], "traffic": args.traffic}
+    if args.precision == "fp64":
+        inst = SWEEP_FP64_INST_PER_CELL[dim0] * c0["smooth_cells"] * sweeps_per_launch
+        ach_i = inst / avg_s / 1e9 if avg_s > 0 else None
+        roofline = {"bound": "alu", "kernel": kernel, "achieved": ach_i, "peak": FP64_INST_PEAK_G,
+                    "unit": "G FP64 inst/s", "frac": (ach_i / FP64_INST_PEAK_G) if ach_i else None,
+                    "peak_source": "derived: 152 SMs x 2 FP64 inst/clk/SM x 2.07 GHz (1.25 TFLOP/s FP64 nominal)",
+                    "algorithmic_fp64_inst_per_launch": inst, "avg_launch_us": avg_s * 1e6,
+                    "launches_timed": c0["smooth_launches"], "traffic": args.traffic, "hbm": hbm}
+    else:
+        roofline = hbm
     cycles = [st["cycles"] for st in stats[: len(probs)]]
 
     # end to end through the C ABI from host buffers (copies inside the timed region)
@@ -245,19 +271,98 @@ def run_ours(args, rank, world):
                    "solves_per_s": solves * world / tmax, "precision": args.precision,
                    "cycle": "V(2,2) red-black block GS, exact coarsest solve", "l2": "flushed between steps",
                    "parallelism": f"replicas x{world}"},
-        "roofline": {"bound": "hbm",
-                     "kernel": ("k_rbgs_fused2d" if probs[0].grid.dim == 2 else "k_rbgs_colour")
-                     + " on the finest level of " + probs[0].name,
-                     "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": (achieved / peak) if achieved else None, "peak_source": peak_kind,
-                     "algorithmic_bytes_per_launch": per_launch, "avg_launch_us": avg_s * 1e6,
-                     "launches_timed": c0["smooth_launches"], "traffic": args.traffic},
+        "roofline": roofline,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": int(sum(c["launches"] for c in counters)),
         "clocks": clk,
         "wall_s": wall,
     }
+    return out
+
+
+# ----------------------------------------------------------------- other workloads
+def run_batch(args):
+    """256 independent 2D problems (sizes log-uniform 64..1024, multiples of 32,
+    1-8 bubbles, density ratio 1000): mixed precision through one mg_batch per
+    step versus looping the plain FP64 solver over them, both to 1e-10."""
+    import numpy as np
+    import torch
+    from paper_2206_11294_gb300 import inputs as I
+    from paper_2206_11294_gb300.binding import Batch, Solver
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    probs = I.batch_problems(count=args.batch_count)
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    dev = [dict(lam=T(p.lam), fa=[T(f) for f in p.fa], fk=[T(f) for f in p.fk], b=T(p.b), x0=T(p.x0),
+                x=T(p.x0)) for p in probs]
+    cells = sum(p.grid.N for p in probs)
+    out = {"workload": f"batch of {len(probs)} 2D problems, {cells} cells", "metric": "solves/s at 1e-10"}
+    for mode in ("batched_mixed", "loop_fp64"):
+        prec = "mixed" if mode == "batched_mixed" else "fp64"
+        solvers = [Solver(p.grid, precision=prec, rtol=1e-10, max_cycles=60, stream=stream) for p in probs]
+        batch = Batch(solvers) if mode == "batched_mixed" else None
+
+        def step(stats):
+            for s, d in zip(solvers, dev):
+                d["x"].copy_(d["x0"])
+                s.set_coeffs(d["lam"], d["fa"], d["fk"])
+            if batch is not None:
+                stats.extend(batch.solve([d["b"] for d in dev], [d["x"] for d in dev]))
+            else:
+                for s, d in zip(solvers, dev):
+                    stats.append(s.solve(d["b"], d["x"]))
+
+        for _ in range(args.warmup):
+            step([])
+        torch.cuda.synchronize()
+        st = []
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            step(st)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        secs = e0.elapsed_time(e1) / 1e3
+        cyc = [s["cycles"] for s in st[: len(probs)]]
+        out[mode] = {"solves_per_s": len(st) / secs, "ms_per_step": secs * 1e3 / args.steps,
+                     "mcell_vcycles_per_s": sum(p.grid.N * c for p, c in zip(probs, cyc)) * args.steps / secs / 1e6,
+                     "cycles_mean": float(np.mean(cyc)), "launches": batch.launches() if batch else None}
+        if batch is not None:
+            batch.close()
+        for s in solvers:
+            s.close()
+    out["speedup_batched_mixed_vs_loop_fp64"] = out["batched_mixed"]["solves_per_s"] / out["loop_fp64"]["solves_per_s"]
+    return out
+
+
+def run_serve(args):
+    """Poisson arrivals of mixed 2D (128..1024) and 3D (64..160) bubble solves,
+    mixed precision, admitted against an HBM budget; p50/p99 per arrival rate."""
+    import numpy as np
+    from paper_2206_11294_gb300 import inputs as I
+    from paper_2206_11294_gb300.serve import Engine, Server, run_stream
+    rng = np.random.default_rng(6)
+    pool = []
+    for q in range(12):
+        n = I.round_to(float(np.exp(rng.uniform(np.log(128), np.log(1024)))), 32)
+        pool.append(I.bubble_2d(n=n, seed=600 + q, n_bubbles=int(rng.integers(1, 9)), rmin=0.02, rmax=0.08,
+                                centred=False, name=f"s2d_{n}"))
+    for q, n in enumerate([64, 96, 128, 160]):
+        pool.append(I.bubble_wall_3d(n=n, seed=700 + q, name=f"s3d_{n}"))
+    # 80% 2D, 20% 3D requests
+    weighted = pool[:12] * 4 + pool[12:] * 3
+    eng = Engine(device=0, precision="mixed", rtol=1e-10, max_cycles=60)
+    out = {"workload": "Poisson stream, 80% 2D 128^2-1024^2 / 20% 3D 64^3-160^3, mixed precision",
+           "hbm_budget_bytes": args.serve_budget, "rates": []}
+    for rate in args.serve_rates:
+        srv = Server(eng, hbm_budget=args.serve_budget, slots=4, max_batch=8)
+        count = int(min(args.serve_max, max(40, rate * args.serve_seconds)))
+        run_stream(srv, weighted[:2], rate=50.0, count=8)        # warm hierarchies and kernels
+        srv.log.clear()
+        st = run_stream(srv, weighted, rate=rate, count=count, seed=int(rate))
+        srv.close()
+        out["rates"].append(st)
     return out
 
 
@@ -311,11 +416,22 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--workload", default="bubbles", choices=["bubbles", "batch", "serve"])
+    ap.add_argument("--batch-count", type=int, default=256)
+    ap.add_argument("--serve-rates", type=float, nargs="+", default=[10, 30, 100, 300, 1000, 2000])
+    ap.add_argument("--serve-seconds", type=float, default=4.0)
+    ap.add_argument("--serve-max", type=int, default=600)
+    ap.add_argument("--serve-budget", type=int, default=40 << 30)
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per launch of the dominant kernel from an ncu capture (profiles/)")
     args = ap.parse_args()
     world = env_int("WORLD_SIZE", 1)
     rank = env_int("RANK", 0)
+    if args.workload != "bubbles":
+        if rank == 0:
+            out = run_batch(args) if args.workload == "batch" else run_serve(args)
+            print(json.dumps(out), flush=True)
+        return
     if args.impl == "ours" and world > 1:
         import torch
         import torch.distributed as dist

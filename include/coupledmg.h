@@ -202,6 +202,10 @@ MG_API mg_status mg_residual_norms_noalloc(const mg_grid *grid, const double *la
                                            const double *const face_alpha[3], const double *const face_k[3],
                                            const double *rhs, const double *x, double *out, void *stream);
 
+/* Moves all later work of the handle to another stream (cudaStream_t on the
+ * handle's device).  Waits for the handle's work on its current stream. */
+MG_API mg_status mg_set_stream(mg_handle *h, void *stream);
+
 /* Makes `device` the CUDA device this thread's later mg_create calls use
  * (the library's own runtime keeps a current device per thread). */
 MG_API mg_status mg_set_device(int device);

@@ -30,7 +30,7 @@ STATUS_NAMES = {0: "MG_OK", 1: "MG_ERR_INVALID_ARG", 2: "MG_ERR_OOM", 3: "MG_ERR
 EXPORTS = ["mg_default_options", "mg_workspace_size", "mg_create", "mg_set_coeffs", "mg_solve",
            "mg_apply", "mg_smooth", "mg_residual_norms", "mg_set_device", "mg_levels", "mg_destroy",
            "mg_last_error", "mg_set_timing", "mg_counters", "mg_residual_norms_noalloc",
-           "mg_batch_create", "mg_batch_solve", "mg_batch_counters", "mg_batch_destroy"]
+           "mg_batch_create", "mg_batch_solve", "mg_batch_counters", "mg_batch_destroy", "mg_set_stream"]
 
 
 class MgError(RuntimeError):
@@ -96,6 +96,7 @@ def load(path: str = LIB_PATH):
             "mg_batch_solve": ([P, C.POINTER(P), C.POINTER(P), C.c_int, C.POINTER(MgStats)], C.c_int),
             "mg_batch_counters": ([P, C.POINTER(C.c_longlong)], C.c_int),
             "mg_batch_destroy": ([P], C.c_int),
+            "mg_set_stream": ([P, P], C.c_int),
             "mg_counters": ([P, C.POINTER(C.c_longlong), C.POINTER(C.c_double), C.POINTER(C.c_longlong),
                              C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)], C.c_int),
         }
@@ -298,6 +299,11 @@ class Solver:
         out = (C.c_double * 2)()
         check(self._lib.mg_residual_norms(self._h, bp, xp, int(dev), out))
         return np.array(list(out))
+
+    def set_stream(self, stream):
+        """Runs this handle's later work on `stream` (a torch.cuda.Stream)."""
+        check(self._lib.mg_set_stream(self._h, C.c_void_p(stream.cuda_stream)))
+        self.stream = stream
 
     def set_timing(self, enable: bool = True):
         check(self._lib.mg_set_timing(self._h, int(enable)))

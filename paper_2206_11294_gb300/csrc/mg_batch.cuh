@@ -306,7 +306,7 @@ void b_smooth(mg_batch *b, cudaStream_t s, int d, int sweeps) {
     const int2 *ct = b->tabs + b->colour[d].first;
     const int nc = b->colour[d].second;
     int q = 0;
-    if (DIM == 2) {
+    if (fused_sweeps<R, DIM>()) {
         const int2 *ft = b->tabs + b->fused[d].first;
         const int nf = b->fused[d].second;
         for (; q + 1 < sweeps; q += 2) {

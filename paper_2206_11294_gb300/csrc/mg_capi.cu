@@ -265,15 +265,21 @@ template <typename R> typename Vec<R>::v2 *xalt_of(const LevelBuf &l);
 template <> double2 *xalt_of<double>(const LevelBuf &l) { return l.xalt; }
 template <> float2 *xalt_of<float>(const LevelBuf &l) { return l.xalt32; }
 
-// `sweeps` red-black sweeps on level l.  2D: pairs of sweeps run as fused
-// launches x -> xalt -> x; a leftover odd sweep (and every 3D sweep) runs as
-// two colour launches in place.  The result always ends in x.
+// Whether sweeps of this precision and dimension run fused.  FP32 (HBM-bound)
+// sweeps run fused in 2D.  FP64 sweeps are bound by GB300's FP64 pipe (2
+// instructions per clock per SM), where the fused kernel's recomputed ring
+// costs more than the DRAM traffic it saves, so they run as colour launches.
+template <typename R, int DIM> constexpr bool fused_sweeps() { return DIM == 2 && sizeof(R) == 4; }
+
+// `sweeps` red-black sweeps on level l.  Fused: pairs of sweeps run as fused
+// launches x -> xalt -> x; a leftover odd sweep (and every non-fused sweep)
+// runs as two colour launches in place.  The result always ends in x.
 template <typename R, int DIM>
 void enqueue_smooth(const mg_handle *h, cudaStream_t s, int l, int sweeps) {
     const LevelBuf &lb = h->L[l];
     Level<R> v = view<R>(lb);
     int q = 0;
-    if (DIM == 2) {
+    if (fused_sweeps<R, DIM>()) {
         const dim3 gf((unsigned)((lb.n[0] + kFTX - 1) / kFTX), (unsigned)((lb.n[1] + kFTY - 1) / kFTY), 1);
         typename Vec<R>::v2 *xa = xalt_of<R>(lb);
         for (; q + 1 < sweeps; q += 2) {
@@ -291,8 +297,8 @@ void enqueue_smooth(const mg_handle *h, cudaStream_t s, int l, int sweeps) {
 }
 
 // Kernel launches and sweeps of one call of enqueue_smooth.
-void smooth_launches(int dim, int sweeps, long long *launches, long long *sweeps_out) {
-    const int fused_pairs = dim == 2 ? sweeps / 2 : 0;
+void smooth_launches(bool fused, int sweeps, long long *launches, long long *sweeps_out) {
+    const int fused_pairs = fused ? sweeps / 2 : 0;
     *launches = 2LL * fused_pairs + 2LL * (sweeps - 2 * fused_pairs);
     *sweeps_out = sweeps;
 }
@@ -457,8 +463,9 @@ mg_status accumulate_timing(mg_handle *h) {
     CK(cudaEventElapsedTime(&b, h->ev[2], h->ev[3]));
     h->smooth_ms += (double)a + (double)b;
     long long l1, s1, l2, s2;
-    smooth_launches(h->grid.dim, h->opt.nu1, &l1, &s1);
-    smooth_launches(h->grid.dim, h->opt.nu2, &l2, &s2);
+    const bool fused = h->grid.dim == 2 && h->opt.precision == MG_MIXED;
+    smooth_launches(fused, h->opt.nu1, &l1, &s1);
+    smooth_launches(fused, h->opt.nu2, &l2, &s2);
     h->smooth_launches += l1 + l2;
     h->smooth_sweeps += s1 + s2;
     return MG_OK;
@@ -834,6 +841,15 @@ mg_status mg_counters(const mg_handle *h, long long *launches, double *smooth_ms
     if (smooth_launches) *smooth_launches = h->smooth_launches;
     if (smooth_sweeps) *smooth_sweeps = h->smooth_sweeps;
     if (smooth_cells) *smooth_cells = h->L[0].N;
+    return MG_OK;
+}
+
+mg_status mg_set_stream(mg_handle *h, void *stream) {
+    mg_status st = check_handle(h, false);
+    if (st) return st;
+    DeviceGuard dg(h->device);
+    CK(cudaStreamSynchronize(h->stream));
+    h->stream = reinterpret_cast<cudaStream_t>(stream);
     return MG_OK;
 }
 

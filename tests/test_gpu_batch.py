@@ -117,7 +117,10 @@ def test_batch_vs_oracle(torch_cuda, orc):
     for q, p in enumerate(probs):
         ref, cyc, _ = orc.mg_solve(p.grid.as_dict(), p.lam, p.fa, p.fk, p.b, p.x0, max_cycles=3, rtol=0.0)
         assert st[q]["cycles"] == 3 == cyc
-        tol = 1e-12 if p.name.startswith("b") else 1e-9
+        # literal members 1e-12; stiff members (h = 5e-5 m) carry FP64 rounding of
+        # the 1e5 Pa background through rows where sum_f G_f ~ 1.6e6 meets l3 ~ 5.4:
+        # eps * sum G * |p| / (|l3| * dev) ~ 6.5e-9, so 1e-8
+        tol = 1e-12 if p.name.startswith("b") else 1e-8
         assert rel_dev(xs[q], ref, p.x0) <= tol, q
     b.close()
     for s in solvers:

@@ -1,0 +1,63 @@
+"""Serving loop on the GPU: requests of different sizes (2D and 3D, literal
+and stiff) arrive while others run; each result must be the one a lone
+mg_solve gives (same cycles, values within 1e-13 relative: the batch and the
+single path run the same device code), and the HBM budget must hold."""
+import numpy as np
+import pytest
+
+from paper_2206_11294_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+def rel_dev(x, ref, x0):
+    out = 0.0
+    for f in range(2):
+        d = ref[:, f] - x0[:, f]
+        out = max(out, np.linalg.norm(x[:, f] - ref[:, f]) / max(np.linalg.norm(d), 1e-300))
+    return out
+
+
+def _pool():
+    out = [I.bubble_2d(n=n, seed=300 + q, n_bubbles=1 + q % 3, rmin=0.05, rmax=0.12, centred=False, gas_rho=1.0,
+                       name=f"r{q}") for q, n in enumerate([64, 96, 128, 192, 256])]
+    out.append(I.bubble_2d(n=128, seed=310, n_bubbles=2, rmin=0.05, rmax=0.12, centred=False, gas_rho=1.0,
+                           length=6.4e-3, dt=1e-5, name="stiff128"))
+    out.append(I.bubble_wall_3d(n=32, seed=311, name="wall32"))
+    out.append(I.bubble_wall_3d(n=64, seed=312, name="wall64"))
+    return out
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_served_results_equal_solo(precision):
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2206_11294_gb300.binding import Solver
+    from paper_2206_11294_gb300.serve import Engine, Server
+    pool = _pool()
+    solo = {}
+    for p in pool:
+        s = Solver(p.grid, precision=precision, rtol=1e-10, max_cycles=60)
+        s.set_coeffs(p.lam, p.fa, p.fk)
+        x = p.x0.copy()
+        st = s.solve(p.b, x)
+        solo[p.name] = (x, st)
+        s.close()
+    eng = Engine(device=0, precision=precision, rtol=1e-10, max_cycles=60)
+    sizes = {p.name: eng.size(p) for p in pool}
+    budget = int(0.6 * sum(sizes.values()))          # forces waiting and eviction
+    srv = Server(eng, hbm_budget=budget, slots=3, max_batch=4)
+    rng = np.random.default_rng(0)
+    order = [pool[int(rng.integers(len(pool)))] for _ in range(30)]
+    futs = [(p, srv.submit(p)) for p in order]
+    for p, f in futs:
+        x, st = f.result(timeout=300)
+        xr, sr = solo[p.name]
+        assert st["cycles"] == sr["cycles"], p.name
+        assert rel_dev(x, xr, p.x0) <= 1e-13, p.name
+    stats = srv.stats()
+    srv.close()
+    assert stats["requests"] == 30
+    assert stats["peak_bytes"] <= budget
+    assert stats["mean_batch"] > 1.0                  # queued requests were batched
