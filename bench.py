@@ -345,7 +345,7 @@ def run_serve(args):
     rng = np.random.default_rng(6)
     pool = []
     for q in range(12):
-        n = I.round_to(float(np.exp(rng.uniform(np.log(128), np.log(1024)))), 32)
+        n = I.round_to(float(np.exp(rng.uniform(np.log(128), np.log(1024)))), 64)
         pool.append(I.bubble_2d(n=n, seed=600 + q, n_bubbles=int(rng.integers(1, 9)), rmin=0.02, rmax=0.08,
                                 centred=False, name=f"s2d_{n}"))
     for q, n in enumerate([64, 96, 128, 160]):

@@ -80,6 +80,9 @@ struct mg_handle {
     size_t stage_bytes;
     int nc;                // unknowns of the coarsest level
     double *Minv, *Mtmp;
+    double *Mwork;         // coarse inverse: columns before the transpose (banded path)
+    int *piv;              // coarse inverse: pivot rows (banded path)
+    double *dinv;          // coarse inverse: reciprocal pivots (banded path)
     float *Minv32;
     double2 *partial;
     int npartial;
@@ -214,6 +217,10 @@ void plan(mg_handle *h, char *base, size_t *bytes) {
     h->stage = P.take<char>((long long)h->stage_bytes);
     h->Minv = P.take<double>((long long)h->nc * h->nc);
     h->Mtmp = P.take<double>((long long)h->nc * h->nc);
+    const bool banded = h->nc > kGJBandedAbove;
+    h->Mwork = banded ? P.take<double>((long long)h->nc * h->nc) : nullptr;
+    h->piv = banded ? P.take<int>(h->nc) : nullptr;
+    h->dinv = banded ? P.take<double>(h->nc) : nullptr;
     h->Minv32 = mixed ? P.take<float>((long long)h->nc * h->nc) : nullptr;
     const dim3 gg = cell_grid(f, g.dim, f.n[0]);
     h->npartial = (int)(gg.x * gg.y * gg.z);
@@ -537,12 +544,18 @@ mg_status setup_hierarchy(mg_handle *h, const double *lam, const double *const f
     CK(cudaMemsetAsync(h->Mtmp, 0, sizeof(double) * h->nc * h->nc, s));
     k_coarse_assemble<DIM><<<lin_blocks(c.N), 256, 0, s>>>(c.n[0], c.n[1], c.n[2], c.G[0], c.G[1],
                                                            DIM == 3 ? c.G[2] : nullptr, c.D, c.l4, h->Mtmp);
-    if (h->nc <= kGJSmemMax) {
+    if (h->nc <= kGJBandedAbove) {
         const size_t smem = sizeof(double) * h->nc * h->nc;
         CK(cudaFuncSetAttribute(k_gauss_jordan_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         k_gauss_jordan_smem<<<1, dim3(32, 32, 1), smem, s>>>(h->Mtmp, h->Minv, h->nc, h->err_d);
     } else {
-        k_gauss_jordan<<<1, 1024, 0, s>>>(h->Mtmp, h->Minv, h->nc, h->err_d);
+        // band of the coarsest matrix: the farthest neighbour cell is n0 (2D)
+        // or n0*n1 (3D) cells away, two unknowns per cell
+        const int off = DIM == 3 ? c.n[0] * c.n[1] : c.n[0];
+        const int kl = std::min(h->nc - 1, 2 * off + 1);
+        k_band_lu<<<1, dim3(32, 32, 1), 0, s>>>(h->Mtmp, h->nc, kl, kl, h->piv, h->dinv, h->err_d);
+        k_band_inv_cols<<<(h->nc + 127) / 128, 128, 0, s>>>(h->Mtmp, h->piv, h->dinv, h->nc, kl, kl, h->Mwork);
+        k_transpose<<<lin_blocks((long long)h->nc * h->nc), 256, 0, s>>>(h->Mwork, h->Minv, h->nc);
     }
     CK(cudaGetLastError());
     if (h->opt.precision == MG_MIXED) {

@@ -527,10 +527,11 @@ __global__ void k_faces0(FaceGeom fg, const double *__restrict__ alpha, const do
     const int a = fg.axis;
     const int m0 = fg.n[0] + (a == 0), m1 = fg.n[1] + (a == 1);
     for (long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x; f < M; f += (long long)gridDim.x * blockDim.x) {
-        const int fi = (int)(f % m0);
-        const long long rest = f / m0;
-        const int fj = (int)(rest % m1);
-        const int fk = (int)(rest / m1);
+        const unsigned uf = (unsigned)f, um0 = (unsigned)m0, um1 = (unsigned)m1;   // grids stay below 2^32 faces
+        const unsigned rest = uf / um0;
+        const int fi = (int)(uf - rest * um0);
+        const int fj = (int)(rest % um1);
+        const int fk = (int)(rest / um1);
         const int pos = a == 0 ? fi : (a == 1 ? fj : fk);
         double fac = 1.0;
         if (pos == 0) fac = fg.fac[0];
@@ -550,7 +551,7 @@ __global__ void k_block0(const double *__restrict__ lam, int n0, long long N, in
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
         const double l1 = lam[4 * c], l2 = lam[4 * c + 1], l3 = lam[4 * c + 2], l4 = lam[4 * c + 3];
         if (!isfinite(l1) || !isfinite(l2) || !isfinite(l3) || !isfinite(l4)) atomicOr(err, 1);
-        const int i = (int)(c % n0);
+        const int i = (int)((unsigned)c % (unsigned)n0);
         const double s = axisym ? r0 + (i + 0.5) * h : 1.0;
         S[c] = dq{s * l1, s * l2, 0.0, s * l3};
         lam4[c] = l4;
@@ -565,7 +566,8 @@ __global__ void k_coarsen_blocks(const dq *__restrict__ Sf, const double *__rest
                                  double r0, double hf) {
     const long long Nc = (long long)c0 * c1 * c2;
     for (long long cc = blockIdx.x * (long long)blockDim.x + threadIdx.x; cc < Nc; cc += (long long)gridDim.x * blockDim.x) {
-        const int I = (int)(cc % c0), J = (int)((cc / c0) % c1), K = (int)(cc / ((long long)c0 * c1));
+        const unsigned u = (unsigned)cc, r = u / (unsigned)c0;
+        const int I = (int)(u - r * (unsigned)c0), J = (int)(r % (unsigned)c1), K = (int)(r / (unsigned)c1);
         double a = 0, b = 0, c = 0, d = 0, v4 = 0, vs = 0;
         for (int q = 0; q < (1 << DIM); q++) {
             const int i = 2 * I + (q & 1);
@@ -591,7 +593,8 @@ __global__ void k_coarsen_faces(int axis, const double2 *__restrict__ Gf, int fn
     const int fm0 = fn0 + (axis == 0), fm1 = fn1 + (axis == 1);
     const long long M = (long long)cm0 * cm1 * cm2;
     for (long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x; f < M; f += (long long)gridDim.x * blockDim.x) {
-        const int FI = (int)(f % cm0), FJ = (int)((f / cm0) % cm1), FK = (int)(f / ((long long)cm0 * cm1));
+        const unsigned u = (unsigned)f, r = u / (unsigned)cm0;
+        const int FI = (int)(u - r * (unsigned)cm0), FJ = (int)(r % (unsigned)cm1), FK = (int)(r / (unsigned)cm1);
         double sT = 0, sp = 0;
         for (int q = 0; q < (1 << (DIM - 1)); q++) {
             int o[3] = {0, 0, 0}, bit = 0;
@@ -618,7 +621,8 @@ __global__ void k_diag(int n0, int n1, int n2, const double2 *__restrict__ G0, c
                        dq *__restrict__ Dinv, int *__restrict__ err) {
     const long long N = (long long)n0 * n1 * n2;
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
-        const int i = (int)(c % n0), j = (int)((c / n0) % n1), k = (int)(c / ((long long)n0 * n1));
+        const unsigned uc = (unsigned)c, r = uc / (unsigned)n0;
+        const int i = (int)(uc - r * (unsigned)n0), j = (int)(r % (unsigned)n1), k = (int)(r / (unsigned)n1);
         const long long f0 = (long long)i + (long long)(n0 + 1) * ((long long)j + (long long)n1 * k);
         const long long f1 = (long long)i + (long long)n0 * ((long long)j + (long long)(n1 + 1) * k);
         double2 g = G0[f0], h2 = G0[f0 + 1], u = G1[f1], v = G1[f1 + n0];
@@ -700,6 +704,9 @@ __global__ void k_coarse_assemble(int n0, int n1, int n2, const double2 *__restr
 // column swaps at the end (inv(P A) P = inv(A)).  One block of 32 x 32 threads.
 // err |= 4 on a zero pivot.
 constexpr int kGJSmemMax = 160;
+// Above this many unknowns the banded LU path is cheaper than Gauss-Jordan:
+// GJ does n^2 FP64 FMAs per column on one SM, the band kl * (kl + ku).
+constexpr int kGJBandedAbove = 24;
 
 __global__ void __launch_bounds__(1024) k_gauss_jordan_smem(const double *__restrict__ M, double *__restrict__ Minv,
                                                             int n, int *__restrict__ err) {
@@ -772,6 +779,115 @@ __global__ void __launch_bounds__(1024) k_gauss_jordan_smem(const double *__rest
         __syncthreads();
     }
     for (int q = tid; q < n * n; q += 1024) Minv[q] = a[q];
+}
+
+// Coarsest inverse for kGJSmemMax < n <= 1024 in three kernels that exploit
+// the band of the coarsest matrix (cells in lexicographic order, two unknowns
+// each: entries lie within kl = 2 * (largest neighbour cell offset) + 1 of the
+// diagonal).
+//
+// 1. k_band_lu: LU with partial pivoting restricted to the band, one block:
+//    per column k the pivot is the largest |a_rk| for k <= r <= k + kl, rows
+//    k and pivot are swapped over the columns the band can reach (k .. k + kl
+//    + ku, U's band after pivoting), multipliers l_rk = a_rk / a_kk are stored
+//    below the diagonal and the window rows k+1..k+kl, columns k+1..k+kl+ku
+//    is updated.  piv[k] = pivot row; dinv[k] = 1 / u_kk.  err |= 4 on a zero
+//    pivot.
+// 2. k_band_inv_cols: thread j solves L U x = P e_j (row swaps and the unit
+//    lower factor forward, U backward) into W[j][*].
+// 3. k_transpose: Minv[i][j] = W[j][i].
+__global__ void __launch_bounds__(1024) k_band_lu(double *__restrict__ M, int n, int kl, int ku,
+                                                  int *__restrict__ piv, double *__restrict__ dinv,
+                                                  int *__restrict__ err) {
+    __shared__ int prow;
+    __shared__ double pinv;
+    __shared__ int bad;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int tid = tx + 32 * ty;
+    const int ur = kl + ku;                      // reach of U after pivoting
+    if (tid == 0) bad = 0;
+    __syncthreads();
+    for (int k = 0; k < n; k++) {
+        const int rlast = min(n - 1, k + kl), clast = min(n - 1, k + ur);
+        if (ty == 0) {
+            double best = -1.0;
+            int br = k;
+            for (int r = k + tx; r <= rlast; r += 32) {
+                const double v = fabs(M[(long long)r * n + k]);
+                if (v > best) { best = v; br = r; }
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                const double ov = __shfl_down_sync(0xffffffffu, best, o);
+                const int orr = __shfl_down_sync(0xffffffffu, br, o);
+                if (ov > best || (ov == best && orr < br)) { best = ov; br = orr; }
+            }
+            if (tx == 0) {
+                prow = br;
+                piv[k] = br;
+                if (!(best > 0.0)) bad = 1;
+                else {
+                    pinv = 1.0 / M[(long long)br * n + k];
+                    dinv[k] = pinv;
+                }
+            }
+        }
+        __syncthreads();
+        if (bad) break;
+        const int p = prow;
+        if (p != k)
+            for (int c = k + tid; c <= clast; c += 1024) {
+                const double t = M[(long long)k * n + c];
+                M[(long long)k * n + c] = M[(long long)p * n + c];
+                M[(long long)p * n + c] = t;
+            }
+        __syncthreads();
+        const double ip = pinv;
+        for (int r = k + 1 + tid; r <= rlast; r += 1024) M[(long long)r * n + k] *= ip;
+        __syncthreads();
+        for (int r = k + 1 + ty; r <= rlast; r += 32) {
+            const double l = M[(long long)r * n + k];
+            if (l != 0.0)
+                for (int c = k + 1 + tx; c <= clast; c += 32) M[(long long)r * n + c] -= l * M[(long long)k * n + c];
+        }
+        __syncthreads();
+    }
+    if (bad && tid == 0) atomicOr(err, 4);
+}
+
+__global__ void k_band_inv_cols(const double *__restrict__ M, const int *__restrict__ piv,
+                                const double *__restrict__ dinv, int n, int kl, int ku, double *__restrict__ W) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    double *y = W + (long long)j * n;
+    for (int i = 0; i < n; i++) y[i] = (i == j) ? 1.0 : 0.0;
+    for (int k = 0; k < n; k++) {              // P and L, in the order the factorisation applied them
+        const int p = piv[k];
+        if (p != k) {
+            const double t = y[k];
+            y[k] = y[p];
+            y[p] = t;
+        }
+        const double yk = y[k];
+        if (yk != 0.0) {
+            const int rlast = min(n - 1, k + kl);
+            for (int r = k + 1; r <= rlast; r++) y[r] -= M[(long long)r * n + k] * yk;
+        }
+    }
+    const int ur = kl + ku;
+    for (int i = n - 1; i >= 0; i--) {         // U
+        double s = y[i];
+        const int clast = min(n - 1, i + ur);
+        for (int c = i + 1; c <= clast; c++) s -= M[(long long)i * n + c] * y[c];
+        y[i] = s * dinv[i];
+    }
+}
+
+__global__ void k_transpose(const double *__restrict__ W, double *__restrict__ Minv, int n) {
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < (long long)n * n;
+         q += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(q / n), j = (int)(q - (long long)i * n);
+        Minv[q] = W[(long long)j * n + i];
+    }
 }
 
 // Gauss-Jordan inversion with partial pivoting in one block (n <= 1024):
