@@ -49,6 +49,7 @@ struct LevelBuf {
     double2 *x, *b;
     double2 *xalt;          // ping-pong partner of x for fused sweeps (2D)
     double2 *G[3];
+    dq *S;                  // scaled local terms s [[l1, l2], [0, l3]] (set-up)
     dq *D, *Dinv;
     double *l4;
     float2 *x32, *b32;
@@ -192,6 +193,7 @@ void plan(mg_handle *h, char *base, size_t *bytes) {
         l.b = P.take<double2>(l.N);
         if (g.dim == 2) l.xalt = P.take<double2>(l.N);
         for (int a = 0; a < g.dim; a++) l.G[a] = P.take<double2>(l.nf[a]);
+        l.S = P.take<dq>(l.N);
         l.D = P.take<dq>(l.N);
         l.Dinv = P.take<dq>(l.N);
         l.l4 = P.take<double>(l.N);
@@ -211,13 +213,14 @@ void plan(mg_handle *h, char *base, size_t *bytes) {
     const LevelBuf &f = h->L[0];
     const LevelBuf &c = h->L[h->nlev - 1];
     h->nc = (int)(2 * c.N);
-    long long maxnf = 0;
-    for (int a = 0; a < g.dim; a++) maxnf = f.nf[a] > maxnf ? f.nf[a] : maxnf;
-    h->stage_bytes = (size_t)std::max<long long>(32 * f.N, 16 * maxnf);
+    long long sumnf = 0;
+    for (int a = 0; a < g.dim; a++) sumnf += f.nf[a];
+    // lambda, then 1/rho and k of every axis (host-side coefficient intake)
+    h->stage_bytes = (size_t)(32 * f.N + 16 * sumnf);
     h->stage = P.take<char>((long long)h->stage_bytes);
     h->Minv = P.take<double>((long long)h->nc * h->nc);
     h->Mtmp = P.take<double>((long long)h->nc * h->nc);
-    const bool banded = h->nc > kGJBandedAbove;
+    const bool banded = h->nc > kBandSmemMax;
     h->Mwork = banded ? P.take<double>((long long)h->nc * h->nc) : nullptr;
     h->piv = banded ? P.take<int>(h->nc) : nullptr;
     h->dinv = banded ? P.take<double>(h->nc) : nullptr;
@@ -488,90 +491,104 @@ bool converged(const double n0[2], const double nk[2], double rtol) {
 }
 
 // ---------------------------------------------------------------- set-up
+SetupOut setup_out(const LevelBuf &l, bool mixed) {
+    SetupOut o;
+    std::memset(&o, 0, sizeof(o));
+    for (int a = 0; a < 3; a++) {
+        o.G[a] = l.G[a];
+        o.G32[a] = mixed ? l.G32[a] : nullptr;
+    }
+    o.S = l.S;
+    o.D = l.D;
+    o.Dinv = l.Dinv;
+    o.l4 = l.l4;
+    if (mixed) {
+        o.D32 = l.D32;
+        o.Dinv32 = l.Dinv32;
+        o.l432 = l.l4_32;
+    }
+    return o;
+}
+
 template <int DIM>
 mg_status setup_hierarchy(mg_handle *h, const double *lam, const double *const fa[3], const double *const fk[3],
                           int on_device) {
     const mg_grid &g = h->grid;
     cudaStream_t s = h->stream;
+    const bool mixed = h->opt.precision == MG_MIXED;
     LevelBuf &f = h->L[0];
     CK(cudaMemsetAsync(h->err_d, 0, sizeof(int), s));
     const double *lam_d = lam;
+    const double *fad[3] = {nullptr, nullptr, nullptr}, *fkd[3] = {nullptr, nullptr, nullptr};
     if (!on_device) {
-        CK(cudaMemcpyAsync(h->stage, lam, sizeof(double) * 4 * f.N, cudaMemcpyHostToDevice, s));
-        lam_d = reinterpret_cast<const double *>(h->stage);
-    }
-    k_block0<<<lin_blocks(f.N), 256, 0, s>>>(lam_d, f.n[0], f.N, g.axisym, g.r0, g.h, f.D, f.l4, h->err_d);
-    CK(cudaGetLastError());
-    for (int a = 0; a < DIM; a++) {
-        const double *al = fa[a], *kk = fk[a];
-        if (!on_device) {
-            // the lambda copy above is consumed in stream order before this overwrite
-            double *st = reinterpret_cast<double *>(h->stage);
-            CK(cudaMemcpyAsync(st, fa[a], sizeof(double) * f.nf[a], cudaMemcpyHostToDevice, s));
-            CK(cudaMemcpyAsync(st + f.nf[a], fk[a], sizeof(double) * f.nf[a], cudaMemcpyHostToDevice, s));
-            al = st;
-            kk = st + f.nf[a];
+        double *st = reinterpret_cast<double *>(h->stage);
+        CK(cudaMemcpyAsync(st, lam, sizeof(double) * 4 * f.N, cudaMemcpyHostToDevice, s));
+        lam_d = st;
+        double *p = st + 4 * f.N;
+        for (int a = 0; a < DIM; a++) {
+            CK(cudaMemcpyAsync(p, fa[a], sizeof(double) * f.nf[a], cudaMemcpyHostToDevice, s));
+            fad[a] = p;
+            p += f.nf[a];
+            CK(cudaMemcpyAsync(p, fk[a], sizeof(double) * f.nf[a], cudaMemcpyHostToDevice, s));
+            fkd[a] = p;
+            p += f.nf[a];
         }
-        FaceGeom fg;
-        for (int q = 0; q < 3; q++) fg.n[q] = f.n[q];
-        fg.axis = a;
-        fg.axisym = g.axisym;
-        fg.r0 = g.r0;
-        fg.h = g.h;
-        for (int sd = 0; sd < 2; sd++) fg.fac[sd] = g.bc[a][sd] == MG_BC_DIRICHLET ? 2.0 : 0.0;
-        k_faces0<<<lin_blocks(f.nf[a]), 256, 0, s>>>(fg, al, kk, f.G[a], f.nf[a], h->err_d);
-        CK(cudaGetLastError());
+    } else {
+        for (int a = 0; a < DIM; a++) {
+            fad[a] = fa[a];
+            fkd[a] = fk[a];
+        }
     }
+    SetupGeom gm;
+    std::memset(&gm, 0, sizeof(gm));
+    for (int a = 0; a < 3; a++) {
+        gm.n[a] = f.n[a];
+        for (int sd = 0; sd < 2; sd++)
+            gm.fac[a][sd] = (a < DIM && g.bc[a][sd] == MG_BC_DIRICHLET) ? 2.0 : 0.0;
+    }
+    gm.axisym = g.axisym;
+    gm.r0 = g.r0;
+    gm.h = g.h;
+    const double *f2a = DIM == 3 ? fad[2] : fad[0], *f2k = DIM == 3 ? fkd[2] : fkd[0];
+    k_setup_fine<DIM><<<cell_grid(f, DIM, f.n[0]), kBlock, 0, s>>>(gm, lam_d, fad[0], fad[1], f2a, fkd[0], fkd[1],
+                                                                   f2k, setup_out(f, mixed), h->err_d);
+    CK(cudaGetLastError());
     double hl = g.h;
     for (int l = 1; l < h->nlev; l++) {
         const LevelBuf &F = h->L[l - 1];
         LevelBuf &C = h->L[l];
-        k_coarsen_blocks<DIM><<<lin_blocks(C.N), 256, 0, s>>>(F.D, F.l4, F.n[0], F.n[1], C.D, C.l4, C.n[0], C.n[1],
-                                                              C.n[2], g.axisym, g.r0, hl);
+        SetupGeom cg = gm;
+        for (int a = 0; a < 3; a++) cg.n[a] = C.n[a];
+        cg.h = 2.0 * hl;
+        k_setup_coarse<DIM><<<cell_grid(C, DIM, C.n[0]), kBlock, 0, s>>>(cg, F.n[0], F.n[1], F.S, F.l4, F.G[0],
+                                                                         F.G[1], DIM == 3 ? F.G[2] : F.G[0], hl,
+                                                                         setup_out(C, mixed), h->err_d);
+        CK(cudaGetLastError());
         hl *= 2.0;
-        for (int a = 0; a < DIM; a++)
-            k_coarsen_faces<DIM><<<lin_blocks(C.nf[a]), 256, 0, s>>>(a, F.G[a], F.n[0], F.n[1], C.G[a], C.n[0],
-                                                                      C.n[1], C.n[2]);
-        CK(cudaGetLastError());
-    }
-    for (int l = 0; l < h->nlev; l++) {
-        LevelBuf &lb = h->L[l];
-        k_diag<DIM><<<lin_blocks(lb.N), 256, 0, s>>>(lb.n[0], lb.n[1], lb.n[2], lb.G[0], lb.G[1],
-                                                     DIM == 3 ? lb.G[2] : nullptr, lb.l4, lb.D, lb.Dinv, h->err_d);
-        CK(cudaGetLastError());
     }
     const LevelBuf &c = h->L[h->nlev - 1];
     CK(cudaMemsetAsync(h->Mtmp, 0, sizeof(double) * h->nc * h->nc, s));
     k_coarse_assemble<DIM><<<lin_blocks(c.N), 256, 0, s>>>(c.n[0], c.n[1], c.n[2], c.G[0], c.G[1],
                                                            DIM == 3 ? c.G[2] : nullptr, c.D, c.l4, h->Mtmp);
-    if (h->nc <= kGJBandedAbove) {
-        const size_t smem = sizeof(double) * h->nc * h->nc;
-        CK(cudaFuncSetAttribute(k_gauss_jordan_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_gauss_jordan_smem<<<1, dim3(32, 32, 1), smem, s>>>(h->Mtmp, h->Minv, h->nc, h->err_d);
+    // band of the coarsest matrix: the farthest neighbour cell is n0 (2D)
+    // or n0*n1 (3D) cells away, two unknowns per cell
+    const int off = DIM == 3 ? c.n[0] * c.n[1] : c.n[0];
+    const int kl = std::min(h->nc - 1, 2 * off + 1);
+    if (h->nc <= kBandSmemMax) {
+        const size_t smem = sizeof(double) * ((size_t)h->nc * h->nc + 32 * (size_t)h->nc);
+        CK(cudaFuncSetAttribute(k_band_inverse_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_band_inverse_smem<<<1, 1024, smem, s>>>(h->Mtmp, h->Minv, h->nc, kl, kl, h->err_d);
     } else {
-        // band of the coarsest matrix: the farthest neighbour cell is n0 (2D)
-        // or n0*n1 (3D) cells away, two unknowns per cell
-        const int off = DIM == 3 ? c.n[0] * c.n[1] : c.n[0];
-        const int kl = std::min(h->nc - 1, 2 * off + 1);
         k_band_lu<<<1, dim3(32, 32, 1), 0, s>>>(h->Mtmp, h->nc, kl, kl, h->piv, h->dinv, h->err_d);
         k_band_inv_cols<<<(h->nc + 127) / 128, 128, 0, s>>>(h->Mtmp, h->piv, h->dinv, h->nc, kl, kl, h->Mwork);
         k_transpose<<<lin_blocks((long long)h->nc * h->nc), 256, 0, s>>>(h->Mwork, h->Minv, h->nc);
     }
     CK(cudaGetLastError());
-    if (h->opt.precision == MG_MIXED) {
-        for (int l = 0; l < h->nlev; l++) {
-            LevelBuf &lb = h->L[l];
-            for (int a = 0; a < DIM; a++)
-                k_to_f32_v2<<<lin_blocks(lb.nf[a]), 256, 0, s>>>(lb.G[a], lb.G32[a], lb.nf[a]);
-            k_to_f32_q<<<lin_blocks(lb.N), 256, 0, s>>>(lb.D, lb.D32, lb.N);
-            k_to_f32_q<<<lin_blocks(lb.N), 256, 0, s>>>(lb.Dinv, lb.Dinv32, lb.N);
-            k_to_f32<<<lin_blocks(lb.N), 256, 0, s>>>(lb.l4, lb.l4_32, lb.N);
-        }
+    if (mixed) {
         k_to_f32<<<lin_blocks((long long)h->nc * h->nc), 256, 0, s>>>(h->Minv, h->Minv32, (long long)h->nc * h->nc);
         CK(cudaGetLastError());
     }
-    counted(h, 1 + DIM + (h->nlev - 1) * (1 + DIM) + h->nlev + 2 +
-                   (h->opt.precision == MG_MIXED ? h->nlev * (DIM + 3) + 1 : 0));
+    counted(h, h->nlev + 1 + (h->nc <= kBandSmemMax ? 1 : 3) + (mixed ? 1 : 0));
     int err = 0;
     CK(cudaMemcpyAsync(&err, h->err_d, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));

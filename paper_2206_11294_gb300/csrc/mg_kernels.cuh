@@ -511,151 +511,179 @@ __global__ void __launch_bounds__(kBX * kBY) k_apply_paper(Level<double> L, BcVa
 }
 
 // ---------------------------------------------------------------------------
-// Set-up kernels (FP64)
+// Set-up kernels (FP64).  One launch per level: the finest level from the
+// caller's arrays, every coarser level from the level below.  Each cell
+// computes all 2*DIM of its face coefficients (a face shared by two cells is
+// computed identically by both) and stores the faces it owns: its low faces,
+// and its high faces on the high boundary.  It then forms its 2x2 block D and
+// the inverse.  The scaled local terms S = s [[l1, l2], [0, l3]] are kept per
+// level for the next coarsening.
 // ---------------------------------------------------------------------------
-struct FaceGeom {
-    int n[3];          // level cells per axis
-    int axis;          // faces normal to this axis
-    int axisym;
-    double r0, h;
-    double fac[2];     // boundary factor low/high side: 2 Dirichlet, 0 wall/axis
+struct SetupOut {                 // one level's outputs
+    double2 *G[3];
+    dq *S, *D, *Dinv;
+    double *l4;
+    float2 *G32[3];               // FP32 copies (mixed precision), or NULL
+    fq *D32, *Dinv32;
+    float *l432;
 };
 
-// G = (k, 1/rho) * rho_f / h^2 * (1 interior | boundary factor)
-__global__ void k_faces0(FaceGeom fg, const double *__restrict__ alpha, const double *__restrict__ kap,
-                         double2 *__restrict__ G, long long M, int *__restrict__ err) {
-    const int a = fg.axis;
-    const int m0 = fg.n[0] + (a == 0), m1 = fg.n[1] + (a == 1);
-    for (long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x; f < M; f += (long long)gridDim.x * blockDim.x) {
-        const unsigned uf = (unsigned)f, um0 = (unsigned)m0, um1 = (unsigned)m1;   // grids stay below 2^32 faces
-        const unsigned rest = uf / um0;
-        const int fi = (int)(uf - rest * um0);
-        const int fj = (int)(rest % um1);
-        const int fk = (int)(rest / um1);
-        const int pos = a == 0 ? fi : (a == 1 ? fj : fk);
-        double fac = 1.0;
-        if (pos == 0) fac = fg.fac[0];
-        else if (pos == fg.n[a]) fac = fg.fac[1];
-        double rho_f = 1.0;
-        if (fg.axisym) rho_f = a == 0 ? fg.r0 + fi * fg.h : fg.r0 + (fi + 0.5) * fg.h;
-        const double w = rho_f / (fg.h * fg.h) * fac;
-        const double al = alpha[f], kk = kap[f];
-        if (!isfinite(al) || !isfinite(kk)) atomicOr(err, 1);
-        G[f] = make_double2(kk * w, al * w);
-    }
-}
+struct SetupGeom {
+    int n[3];
+    int axisym;
+    double r0, h;                 // this level's spacing
+    double fac[3][2];             // boundary factor per axis / side: 2 Dirichlet, 0 wall/axis
+};
 
-// Scaled local terms S = s_i [[l1, l2], [0, l3]] (in the D array) and l4.
-__global__ void k_block0(const double *__restrict__ lam, int n0, long long N, int axisym, double r0, double h,
-                         dq *__restrict__ S, double *__restrict__ lam4, int *__restrict__ err) {
-    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
-        const double l1 = lam[4 * c], l2 = lam[4 * c + 1], l3 = lam[4 * c + 2], l4 = lam[4 * c + 3];
-        if (!isfinite(l1) || !isfinite(l2) || !isfinite(l3) || !isfinite(l4)) atomicOr(err, 1);
-        const int i = (int)((unsigned)c % (unsigned)n0);
-        const double s = axisym ? r0 + (i + 0.5) * h : 1.0;
-        S[c] = dq{s * l1, s * l2, 0.0, s * l3};
-        lam4[c] = l4;
-    }
-}
-
-// Coarse local terms: mean of the 2^DIM children's scaled terms (= s_C times
-// the volume-weighted mean l1..l3); coarse l4 = volume-weighted mean of l4.
 template <int DIM>
-__global__ void k_coarsen_blocks(const dq *__restrict__ Sf, const double *__restrict__ l4f, int f0, int f1,
-                                 dq *__restrict__ Sc, double *__restrict__ l4c, int c0, int c1, int c2, int axisym,
-                                 double r0, double hf) {
-    const long long Nc = (long long)c0 * c1 * c2;
-    for (long long cc = blockIdx.x * (long long)blockDim.x + threadIdx.x; cc < Nc; cc += (long long)gridDim.x * blockDim.x) {
-        const unsigned u = (unsigned)cc, r = u / (unsigned)c0;
-        const int I = (int)(u - r * (unsigned)c0), J = (int)(r % (unsigned)c1), K = (int)(r / (unsigned)c1);
-        double a = 0, b = 0, c = 0, d = 0, v4 = 0, vs = 0;
-        for (int q = 0; q < (1 << DIM); q++) {
-            const int i = 2 * I + (q & 1);
-            const long long f = cell_id(i, 2 * J + ((q >> 1) & 1), DIM == 3 ? 2 * K + (q >> 2) : 0, f0, f1);
-            const dq s = Sf[f];
-            const double sc = axisym ? r0 + (i + 0.5) * hf : 1.0;
-            a += s.a; b += s.b; c += s.c; d += s.d;
-            v4 += sc * l4f[f];
-            vs += sc;
-        }
-        const double w = 1.0 / (1 << DIM);
-        Sc[cc] = dq{a * w, b * w, c * w, d * w};
-        l4c[cc] = v4 / vs;
-    }
-}
-
-// Coarse face = sum of its 2^(DIM-1) fine faces / 2^(DIM+1): the area-weighted
-// mean coefficient re-discretised at spacing 2h.
-template <int DIM>
-__global__ void k_coarsen_faces(int axis, const double2 *__restrict__ Gf, int fn0, int fn1,
-                                double2 *__restrict__ Gc, int cn0, int cn1, int cn2) {
-    const int cm0 = cn0 + (axis == 0), cm1 = cn1 + (axis == 1), cm2 = cn2 + (axis == 2);
-    const int fm0 = fn0 + (axis == 0), fm1 = fn1 + (axis == 1);
-    const long long M = (long long)cm0 * cm1 * cm2;
-    for (long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x; f < M; f += (long long)gridDim.x * blockDim.x) {
-        const unsigned u = (unsigned)f, r = u / (unsigned)cm0;
-        const int FI = (int)(u - r * (unsigned)cm0), FJ = (int)(r % (unsigned)cm1), FK = (int)(r / (unsigned)cm1);
-        double sT = 0, sp = 0;
-        for (int q = 0; q < (1 << (DIM - 1)); q++) {
-            int o[3] = {0, 0, 0}, bit = 0;
-            for (int b = 0; b < DIM; b++) {
-                if (b == axis) continue;
-                o[b] = (q >> bit) & 1;
-                bit++;
+__device__ __forceinline__ void finish_cell(const SetupOut &o, long long c, const long long fid[3][2], int own[3][2],
+                                            const double2 g[3][2], dq S, double l4, int *err) {
+    double sT = 0.0, sp = 0.0;
+#pragma unroll
+    for (int a = 0; a < DIM; a++)
+#pragma unroll
+        for (int sd = 0; sd < 2; sd++) {
+            sT += g[a][sd].x;
+            sp += g[a][sd].y;
+            if (own[a][sd]) {
+                o.G[a][fid[a][sd]] = g[a][sd];
+                if (o.G32[a]) o.G32[a][fid[a][sd]] = make_float2((float)g[a][sd].x, (float)g[a][sd].y);
             }
-            const int fi = 2 * FI + o[0], fj = 2 * FJ + o[1], fk = DIM == 3 ? 2 * FK + o[2] : 0;
-            const double2 g = Gf[(long long)fi + (long long)fm0 * ((long long)fj + (long long)fm1 * fk)];
-            sT += g.x;
-            sp += g.y;
         }
-        const double w = 1.0 / (1 << (DIM + 1));
-        Gc[f] = make_double2(sT * w, sp * w);
+    o.S[c] = S;
+    o.l4[c] = l4;
+    dq D{S.a - sT, S.b, S.c - l4 * sT, S.d - sp};
+    const double det = D.a * D.d - D.b * D.c;
+    if (!(det != 0.0) || !isfinite(det)) atomicOr(err, 2);
+    const double id = 1.0 / det;
+    const dq Di{D.d * id, -D.b * id, -D.c * id, D.a * id};
+    o.D[c] = D;
+    o.Dinv[c] = Di;
+    if (o.D32) {
+        o.D32[c] = fq{(float)D.a, (float)D.b, (float)D.c, (float)D.d};
+        o.Dinv32[c] = fq{(float)Di.a, (float)Di.b, (float)Di.c, (float)Di.d};
+        o.l432[c] = (float)l4;
     }
 }
 
-// D = [[S.a - sum G^T, S.b], [-l4 sum G^T, S.d - sum G^p]] over all faces of
-// the cell, in place, and Dinv.  err |= 2 for a singular or non-finite block.
+__device__ __forceinline__ void face_ids(const int n[3], int i, int j, int k, long long fid[3][2]) {
+    const long long f0 = (long long)i + (long long)(n[0] + 1) * ((long long)j + (long long)n[1] * k);
+    const long long f1 = (long long)i + (long long)n[0] * ((long long)j + (long long)(n[1] + 1) * k);
+    const long long f2 = (long long)i + (long long)n[0] * ((long long)j + (long long)n[1] * k);
+    fid[0][0] = f0; fid[0][1] = f0 + 1;
+    fid[1][0] = f1; fid[1][1] = f1 + n[0];
+    fid[2][0] = f2; fid[2][1] = f2 + (long long)n[0] * n[1];
+}
+
+// Finest level from lambda [N][4] and the per-axis arrays of 1/rho and k.
 template <int DIM>
-__global__ void k_diag(int n0, int n1, int n2, const double2 *__restrict__ G0, const double2 *__restrict__ G1,
-                       const double2 *__restrict__ G2, const double *__restrict__ l4, dq *__restrict__ D,
-                       dq *__restrict__ Dinv, int *__restrict__ err) {
-    const long long N = (long long)n0 * n1 * n2;
-    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
-        const unsigned uc = (unsigned)c, r = uc / (unsigned)n0;
-        const int i = (int)(uc - r * (unsigned)n0), j = (int)(r % (unsigned)n1), k = (int)(r / (unsigned)n1);
-        const long long f0 = (long long)i + (long long)(n0 + 1) * ((long long)j + (long long)n1 * k);
-        const long long f1 = (long long)i + (long long)n0 * ((long long)j + (long long)(n1 + 1) * k);
-        double2 g = G0[f0], h2 = G0[f0 + 1], u = G1[f1], v = G1[f1 + n0];
-        double sT = g.x + h2.x + u.x + v.x, sp = g.y + h2.y + u.y + v.y;
-        if (DIM == 3) {
-            const double2 w0 = G2[c], w1 = G2[c + (long long)n0 * n1];
-            sT += w0.x + w1.x;
-            sp += w0.y + w1.y;
+__global__ void __launch_bounds__(kBX * kBY) k_setup_fine(SetupGeom gm, const double *__restrict__ lam,
+                                                        const double *__restrict__ fa0, const double *__restrict__ fa1,
+                                                        const double *__restrict__ fa2, const double *__restrict__ fk0,
+                                                        const double *__restrict__ fk1, const double *__restrict__ fk2,
+                                                        SetupOut o, int *__restrict__ err) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = DIM == 3 ? (int)blockIdx.z : 0;
+    if (i >= gm.n[0] || j >= gm.n[1]) return;
+    const long long c = cell_id(i, j, k, gm.n[0], gm.n[1]);
+    const double l1 = lam[4 * c], l2 = lam[4 * c + 1], l3 = lam[4 * c + 2], l4 = lam[4 * c + 3];
+    bool bad = !isfinite(l1) || !isfinite(l2) || !isfinite(l3) || !isfinite(l4);
+    const double s = gm.axisym ? gm.r0 + (i + 0.5) * gm.h : 1.0;
+    const double ih2 = 1.0 / (gm.h * gm.h);
+    const double *fa[3] = {fa0, fa1, fa2}, *fk[3] = {fk0, fk1, fk2};
+    const int pos[3] = {i, j, k};
+    long long fid[3][2];
+    face_ids(gm.n, i, j, k, fid);
+    int own[3][2];
+    double2 g[3][2];
+#pragma unroll
+    for (int a = 0; a < DIM; a++)
+#pragma unroll
+        for (int sd = 0; sd < 2; sd++) {
+            const int fpos = pos[a] + sd;
+            double fac = 1.0;
+            if (fpos == 0) fac = gm.fac[a][0];
+            else if (fpos == gm.n[a]) fac = gm.fac[a][1];
+            double rho_f = 1.0;
+            if (gm.axisym) rho_f = a == 0 ? gm.r0 + (i + sd) * gm.h : s;
+            const double w = rho_f * ih2 * fac;
+            const double al = fa[a][fid[a][sd]], kk = fk[a][fid[a][sd]];
+            bad = bad || !isfinite(al) || !isfinite(kk);
+            g[a][sd] = make_double2(kk * w, al * w);
+            own[a][sd] = sd == 0 || fpos == gm.n[a];
         }
-        dq s = D[c];
-        s.a -= sT;
-        s.c -= l4[c] * sT;
-        s.d -= sp;
-        const double det = s.a * s.d - s.b * s.c;
-        if (!(det != 0.0) || !isfinite(det)) atomicOr(err, 2);
-        const double id = 1.0 / det;
-        D[c] = s;
-        Dinv[c] = dq{s.d * id, -s.b * id, -s.c * id, s.a * id};
-    }
+    if (bad) atomicOr(err, 1);
+    finish_cell<DIM>(o, c, fid, own, g, dq{s * l1, s * l2, 0.0, s * l3}, l4, err);
 }
 
-__global__ void k_to_f32_v2(const double2 *__restrict__ in, float2 *__restrict__ out, long long n) {
-    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
-        const double2 v = in[q];
-        out[q] = make_float2((float)v.x, (float)v.y);
+// Coarse level from the level below: S = mean of the children's S, l4 the
+// volume-weighted mean of theirs, each face the sum of its 2^(DIM-1) fine
+// faces / 2^(DIM+1) (area-weighted mean coefficient re-discretised at 2h).
+template <int DIM>
+__global__ void __launch_bounds__(kBX * kBY) k_setup_coarse(SetupGeom cg, int fn0, int fn1, const dq *__restrict__ Sf,
+                                                          const double *__restrict__ l4f,
+                                                          const double2 *__restrict__ Gf0,
+                                                          const double2 *__restrict__ Gf1,
+                                                          const double2 *__restrict__ Gf2, double hf, SetupOut o,
+                                                          int *__restrict__ err) {
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    const int J = blockIdx.y * blockDim.y + threadIdx.y;
+    const int K = DIM == 3 ? (int)blockIdx.z : 0;
+    if (I >= cg.n[0] || J >= cg.n[1]) return;
+    const long long cc = cell_id(I, J, K, cg.n[0], cg.n[1]);
+    double a0 = 0, a1 = 0, a2 = 0, a3 = 0, v4 = 0, vs = 0;
+#pragma unroll
+    for (int q = 0; q < (1 << DIM); q++) {
+        const int i = 2 * I + (q & 1);
+        const long long f = cell_id(i, 2 * J + ((q >> 1) & 1), DIM == 3 ? 2 * K + (q >> 2) : 0, fn0, fn1);
+        const dq sf = Sf[f];
+        const double sc = cg.axisym ? cg.r0 + (i + 0.5) * hf : 1.0;
+        a0 += sf.a; a1 += sf.b; a2 += sf.c; a3 += sf.d;
+        v4 += sc * l4f[f];
+        vs += sc;
     }
+    const double wb = 1.0 / (1 << DIM);
+    const dq S{a0 * wb, a1 * wb, a2 * wb, a3 * wb};
+    const double l4 = v4 / vs;
+    const int P[3] = {I, J, K};
+    const int fm[3][2] = {{fn0 + 1, fn1}, {fn0, fn1 + 1}, {fn0, fn1}};   // fine face array dims (x, y) per axis
+    const double2 *Gf[3] = {Gf0, Gf1, Gf2};
+    long long fid[3][2];
+    face_ids(cg.n, I, J, K, fid);
+    int own[3][2];
+    double2 g[3][2];
+    const double wf = 1.0 / (1 << (DIM + 1));
+#pragma unroll
+    for (int a = 0; a < DIM; a++)
+#pragma unroll
+        for (int sd = 0; sd < 2; sd++) {
+            double sT = 0.0, sp = 0.0;
+#pragma unroll
+            for (int q = 0; q < (1 << (DIM - 1)); q++) {
+                int off[3] = {0, 0, 0}, bit = 0;
+#pragma unroll
+                for (int b = 0; b < DIM; b++) {
+                    if (b == a) continue;
+                    off[b] = (q >> bit) & 1;
+                    bit++;
+                }
+                int fpos[3];
+#pragma unroll
+                for (int b = 0; b < 3; b++) fpos[b] = (b == a) ? 2 * (P[b] + sd) : 2 * P[b] + off[b];
+                if (DIM == 2) fpos[2] = 0;
+                const double2 v = Gf[a][(long long)fpos[0] + (long long)fm[a][0] * ((long long)fpos[1] +
+                                                                                  (long long)fm[a][1] * fpos[2])];
+                sT += v.x;
+                sp += v.y;
+            }
+            g[a][sd] = make_double2(sT * wf, sp * wf);
+            own[a][sd] = sd == 0 || P[a] + sd == cg.n[a];
+        }
+    finish_cell<DIM>(o, cc, fid, own, g, S, l4, err);
 }
-__global__ void k_to_f32_q(const dq *__restrict__ in, fq *__restrict__ out, long long n) {
-    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
-        const dq v = in[q];
-        out[q] = fq{(float)v.a, (float)v.b, (float)v.c, (float)v.d};
-    }
-}
+
+// FP32 copy of an FP64 array (the coarsest inverse of mixed precision).
 __global__ void k_to_f32(const double *__restrict__ in, float *__restrict__ out, long long n) {
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x)
         out[q] = (float)in[q];
@@ -697,91 +725,107 @@ __global__ void k_coarse_assemble(int n0, int n1, int n2, const double2 *__restr
     }
 }
 
-// In-place Gauss-Jordan inversion with row pivoting, the whole matrix in
-// shared memory (n <= kGJSmemMax): for each column k the pivot row is swapped
-// in, the pivot row scaled and every other row eliminated, the eliminated
-// column k then holding column k of the inverse; the row swaps are undone as
-// column swaps at the end (inv(P A) P = inv(A)).  One block of 32 x 32 threads.
-// err |= 4 on a zero pivot.
-constexpr int kGJSmemMax = 160;
-// Above this many unknowns the banded LU path is cheaper than Gauss-Jordan:
-// GJ does n^2 FP64 FMAs per column on one SM, the band kl * (kl + ku).
-constexpr int kGJBandedAbove = 24;
+// Coarsest inverse for n <= kBandSmemMax in one block, everything in shared
+// memory: the banded LU of k_band_lu below done by warp 0 alone (no block
+// barriers inside the column loop), then each warp solves L U x = P e_j for
+// columns j = warp, warp + 32, ... with its vector in shared memory and writes
+// column j of the inverse.  Same arithmetic as the three-kernel path.
+constexpr int kBandSmemMax = 128;
 
-__global__ void __launch_bounds__(1024) k_gauss_jordan_smem(const double *__restrict__ M, double *__restrict__ Minv,
-                                                            int n, int *__restrict__ err) {
-    extern __shared__ double a[];          // n x n, row-major
-    __shared__ double rowk[kGJSmemMax], colf[kGJSmemMax];
-    __shared__ int perm[kGJSmemMax];
-    __shared__ int piv_row;
+__global__ void __launch_bounds__(1024) k_band_inverse_smem(const double *__restrict__ M, double *__restrict__ Minv,
+                                                            int n, int kl, int ku, int *__restrict__ err) {
+    extern __shared__ double sm[];
+    double *a = sm;                         // n x n
+    double *ys = sm + n * n;                // 32 vectors of n
+    __shared__ int piv[kBandSmemMax];
+    __shared__ double dinv[kBandSmemMax];
     __shared__ int bad;
-    __shared__ double piv_inv;
-    const int tx = threadIdx.x, ty = threadIdx.y;
-    const int tid = tx + 32 * ty;
-    for (int q = tid; q < n * n; q += 1024) a[q] = M[q];
-    if (tid == 0) bad = 0;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int q = threadIdx.x; q < n * n; q += blockDim.x) a[q] = M[q];
+    if (threadIdx.x == 0) bad = 0;
     __syncthreads();
-    for (int k = 0; k < n; k++) {
-        if (ty == 0) {                     // warp 0: pivot = largest |a[r][k]|, r >= k, lowest index on ties
+    const int ur = kl + ku;
+    if (warp == 0) {
+        for (int k = 0; k < n; k++) {
+            const int rlast = min(n - 1, k + kl), clast = min(n - 1, k + ur);
             double best = -1.0;
             int br = k;
-            for (int r = k + tx; r < n; r += 32) {
+            for (int r = k + lane; r <= rlast; r += 32) {
                 const double v = fabs(a[r * n + k]);
                 if (v > best) { best = v; br = r; }
             }
             for (int o = 16; o > 0; o >>= 1) {
-                const double ov = __shfl_down_sync(0xffffffffu, best, o);
-                const int orr = __shfl_down_sync(0xffffffffu, br, o);
+                const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+                const int orr = __shfl_xor_sync(0xffffffffu, br, o);
                 if (ov > best || (ov == best && orr < br)) { best = ov; br = orr; }
             }
-            if (tx == 0) {
-                piv_row = br;
-                perm[k] = br;
-                if (!(best > 0.0)) bad = 1;
-                else piv_inv = 1.0 / a[br * n + k];   // one FP64 division per column
+            if (!(best > 0.0)) {
+                if (lane == 0) bad = 1;
+                break;
             }
+            if (br != k)
+                for (int c = k + lane; c <= clast; c += 32) {
+                    const double t = a[k * n + c];
+                    a[k * n + c] = a[br * n + c];
+                    a[br * n + c] = t;
+                }
+            __syncwarp();
+            double ip = 0.0;
+            if (lane == 0) {
+                ip = 1.0 / a[k * n + k];
+                piv[k] = br;
+                dinv[k] = ip;
+            }
+            ip = __shfl_sync(0xffffffffu, ip, 0);
+            for (int r = k + 1 + lane; r <= rlast; r += 32) a[r * n + k] *= ip;
+            __syncwarp();
+            const int w = clast - k;                       // window columns k+1..clast
+            const int rows = rlast - k;
+            for (int q = lane; q < rows * w; q += 32) {
+                const int r = k + 1 + q / w, c = k + 1 + q % w;
+                const double l = a[r * n + k];
+                if (l != 0.0) a[r * n + c] -= l * a[k * n + c];
+            }
+            __syncwarp();
         }
-        __syncthreads();
-        if (bad) break;
-        const int pr = piv_row;
-        if (pr != k)
-            for (int c = tid; c < n; c += 1024) {
-                const double t = a[k * n + c];
-                a[k * n + c] = a[pr * n + c];
-                a[pr * n + c] = t;
-            }
-        __syncthreads();
-        const double ip = piv_inv;
-        for (int c = tid; c < n; c += 1024) rowk[c] = (c == k) ? ip : a[k * n + c] * ip;
-        for (int r = tid; r < n; r += 1024) colf[r] = (r == k) ? 0.0 : a[r * n + k];
-        __syncthreads();
-        for (int r = ty; r < n; r += 32) {
-            const double f = colf[r];
-            for (int c = tx; c < n; c += 32) {
-                if (r == k) a[r * n + c] = rowk[c];
-                else a[r * n + c] = (c == k ? 0.0 : a[r * n + c]) - f * rowk[c];
-            }
-        }
-        __syncthreads();
     }
+    __syncthreads();
     if (bad) {
-        if (tid == 0) atomicOr(err, 4);
+        if (threadIdx.x == 0) atomicOr(err, 4);
         return;
     }
-    for (int k = n - 1; k >= 0; k--) {     // undo the row swaps as column swaps
-        const int pk = perm[k];
-        if (pk != k)
-            for (int r = tid; r < n; r += 1024) {
-                const double t = a[r * n + k];
-                a[r * n + k] = a[r * n + pk];
-                a[r * n + pk] = t;
+    double *y = ys + warp * n;
+    for (int j = warp; j < n; j += (int)(blockDim.x >> 5)) {
+        for (int i = lane; i < n; i += 32) y[i] = (i == j) ? 1.0 : 0.0;
+        __syncwarp();
+        for (int k = 0; k < n; k++) {
+            const int p = piv[k];
+            if (p != k && lane == 0) {
+                const double t = y[k];
+                y[k] = y[p];
+                y[p] = t;
             }
-        __syncthreads();
+            __syncwarp();
+            const double yk = y[k];
+            const int rlast = min(n - 1, k + kl);
+            if (yk != 0.0)
+                for (int r = k + 1 + lane; r <= rlast; r += 32) y[r] -= a[r * n + k] * yk;
+            __syncwarp();
+        }
+        for (int i = n - 1; i >= 0; i--) {
+            const int clast = min(n - 1, i + ur);
+            double s = 0.0;
+            for (int c = i + 1 + lane; c <= clast; c += 32) s += a[i * n + c] * y[c];
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (lane == 0) y[i] = (y[i] - s) * dinv[i];
+            __syncwarp();
+        }
+        for (int i = lane; i < n; i += 32) Minv[(long long)i * n + j] = y[i];
+        __syncwarp();
     }
-    for (int q = tid; q < n * n; q += 1024) Minv[q] = a[q];
 }
 
-// Coarsest inverse for kGJSmemMax < n <= 1024 in three kernels that exploit
+// Coarsest inverse for kBandSmemMax < n <= 1024 in three kernels that exploit
 // the band of the coarsest matrix (cells in lexicographic order, two unknowns
 // each: entries lie within kl = 2 * (largest neighbour cell offset) + 1 of the
 // diagonal).
@@ -887,77 +931,6 @@ __global__ void k_transpose(const double *__restrict__ W, double *__restrict__ M
          q += (long long)gridDim.x * blockDim.x) {
         const int i = (int)(q / n), j = (int)(q - (long long)i * n);
         Minv[q] = W[(long long)j * n + i];
-    }
-}
-
-// Gauss-Jordan inversion with partial pivoting in one block (n <= 1024):
-// M (destroyed) -> Minv.  err |= 4 on a zero pivot.
-__global__ void __launch_bounds__(1024) k_gauss_jordan(double *__restrict__ M, double *__restrict__ Minv, int n,
-                                                       int *__restrict__ err) {
-    __shared__ double fac[1024];
-    __shared__ double pv[32];
-    __shared__ int pi[32];
-    __shared__ int piv_row;
-    __shared__ double piv_val, piv_inv;
-    const int tid = threadIdx.x, nt = blockDim.x;
-    for (long long q = tid; q < (long long)n * n; q += nt) Minv[q] = (q / n == q % n) ? 1.0 : 0.0;
-    __syncthreads();
-    for (int col = 0; col < n; col++) {
-        // pivot: largest |M[r][col]|, r >= col, lowest index on ties
-        double best = -1.0;
-        int br = col;
-        for (int r = col + tid; r < n; r += nt) {
-            const double v = fabs(M[(long long)r * n + col]);
-            if (v > best) { best = v; br = r; }
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-            const double ov = __shfl_down_sync(0xffffffffu, best, o);
-            const int orr = __shfl_down_sync(0xffffffffu, br, o);
-            if (ov > best || (ov == best && orr < br)) { best = ov; br = orr; }
-        }
-        if ((tid & 31) == 0) { pv[tid >> 5] = best; pi[tid >> 5] = br; }
-        __syncthreads();
-        if (tid == 0) {
-            double b = -1.0;
-            int r = col;
-            for (int w = 0; w < (nt + 31) / 32; w++)
-                if (pv[w] > b || (pv[w] == b && pi[w] < r)) { b = pv[w]; r = pi[w]; }
-            piv_row = r;
-            piv_val = M[(long long)r * n + col];
-            piv_inv = 1.0 / piv_val;
-            if (!(b > 0.0)) atomicOr(err, 4);
-        }
-        __syncthreads();
-        if (!(piv_val != 0.0)) return;
-        const int pr = piv_row;
-        if (pr != col) {
-            for (int c = tid; c < n; c += nt) {
-                double t = M[(long long)col * n + c];
-                M[(long long)col * n + c] = M[(long long)pr * n + c];
-                M[(long long)pr * n + c] = t;
-                t = Minv[(long long)col * n + c];
-                Minv[(long long)col * n + c] = Minv[(long long)pr * n + c];
-                Minv[(long long)pr * n + c] = t;
-            }
-        }
-        __syncthreads();
-        const double ip = piv_inv;
-        for (int c = tid; c < n; c += nt) {
-            M[(long long)col * n + c] *= ip;
-            Minv[(long long)col * n + c] *= ip;
-        }
-        __syncthreads();
-        for (int r = tid; r < n; r += nt) fac[r] = (r == col) ? 0.0 : M[(long long)r * n + col];
-        __syncthreads();
-        for (long long q = tid; q < (long long)n * n; q += nt) {
-            const int r = (int)(q / n), c = (int)(q % n);
-            const double f = fac[r];
-            if (f != 0.0) {
-                M[q] -= f * M[(long long)col * n + c];
-                Minv[q] -= f * Minv[(long long)col * n + c];
-            }
-        }
-        __syncthreads();
     }
 }
 
