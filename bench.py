@@ -304,13 +304,14 @@ def run_batch(args):
         batch = Batch(solvers) if mode == "batched_mixed" else None
 
         def step(stats):
-            for s, d in zip(solvers, dev):
+            for d in dev:
                 d["x"].copy_(d["x0"])
-                s.set_coeffs(d["lam"], d["fa"], d["fk"])
             if batch is not None:
+                batch.set_coeffs([d["lam"] for d in dev], [d["fa"] for d in dev], [d["fk"] for d in dev])
                 stats.extend(batch.solve([d["b"] for d in dev], [d["x"] for d in dev]))
             else:
                 for s, d in zip(solvers, dev):
+                    s.set_coeffs(d["lam"], d["fa"], d["fk"])
                     stats.append(s.solve(d["b"], d["x"]))
 
         for _ in range(args.warmup):

@@ -173,6 +173,13 @@ MG_API mg_status mg_batch_create(int count, mg_handle *const *handles, mg_batch 
 MG_API mg_status mg_batch_solve(mg_batch *b, const double *const *rhs, double *const *x, int on_device,
                                 mg_stats *stats);
 
+/* Coefficient intake and set-up of every problem of the batch in one set of
+ * launches (as mg_set_coeffs, per problem): lambda[p] [N_p][4];
+ * face_alpha[3*p + a], face_k[3*p + a] the face arrays of problem p, axis a
+ * (a < dim).  MG_ERR_INVALID_COEFF names the first failing problem. */
+MG_API mg_status mg_batch_set_coeffs(mg_batch *b, const double *const *lambda, const double *const *face_alpha,
+                                     const double *const *face_k, int on_device);
+
 /* Kernels launched by this batch since creation (graph nodes per replay). */
 MG_API mg_status mg_batch_counters(const mg_batch *b, long long *launches);
 

@@ -30,7 +30,8 @@ STATUS_NAMES = {0: "MG_OK", 1: "MG_ERR_INVALID_ARG", 2: "MG_ERR_OOM", 3: "MG_ERR
 EXPORTS = ["mg_default_options", "mg_workspace_size", "mg_create", "mg_set_coeffs", "mg_solve",
            "mg_apply", "mg_smooth", "mg_residual_norms", "mg_set_device", "mg_levels", "mg_destroy",
            "mg_last_error", "mg_set_timing", "mg_counters", "mg_residual_norms_noalloc",
-           "mg_batch_create", "mg_batch_solve", "mg_batch_counters", "mg_batch_destroy", "mg_set_stream"]
+           "mg_batch_create", "mg_batch_solve", "mg_batch_counters", "mg_batch_destroy", "mg_set_stream",
+           "mg_batch_set_coeffs"]
 
 
 class MgError(RuntimeError):
@@ -97,6 +98,7 @@ def load(path: str = LIB_PATH):
             "mg_batch_counters": ([P, C.POINTER(C.c_longlong)], C.c_int),
             "mg_batch_destroy": ([P], C.c_int),
             "mg_set_stream": ([P, P], C.c_int),
+            "mg_batch_set_coeffs": ([P, C.POINTER(P), C.POINTER(P), C.POINTER(P), C.c_int], C.c_int),
             "mg_counters": ([P, C.POINTER(C.c_longlong), C.POINTER(C.c_double), C.POINTER(C.c_longlong),
                              C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)], C.c_int),
         }
@@ -350,6 +352,30 @@ class Batch:
         out = C.c_void_p()
         check(self._lib.mg_batch_create(len(self.solvers), hs, C.byref(out)))
         self._b = out
+
+    def set_coeffs(self, lams: Sequence, fas: Sequence, fks: Sequence):
+        """Coefficients of every problem in one set of launches."""
+        n = len(self.solvers)
+        if not (len(lams) == len(fas) == len(fks) == n):
+            raise ValueError("one coefficient set per problem")
+        dev = _side(*lams, *[f for fa in fas for f in fa[:3]], *[f for fk in fks for f in fk[:3]])
+        keep = []
+        pl = (C.c_void_p * n)()
+        pa = (C.c_void_p * (3 * n))()
+        pk = (C.c_void_p * (3 * n))()
+        for q, (s, lam, fa, fk) in enumerate(zip(self.solvers, lams, fas, fks)):
+            s._need(lam, 4 * s.N, "lambda")
+            p, k = _ptr(lam, dev)
+            pl[q] = p
+            keep.append(k)
+            for a in range(s.grid.dim):
+                s._need(fa[a], s.nfaces(a), f"face_alpha[{a}]")
+                s._need(fk[a], s.nfaces(a), f"face_k[{a}]")
+                p1, k1 = _ptr(fa[a], dev)
+                p2, k2 = _ptr(fk[a], dev)
+                pa[3 * q + a], pk[3 * q + a] = p1, p2
+                keep += [k1, k2]
+        check(self._lib.mg_batch_set_coeffs(self._b, pl, pa, pk, int(dev)))
 
     def solve(self, bs: Sequence, xs: Sequence, allow_not_converged: bool = False) -> list:
         n = len(self.solvers)

@@ -37,6 +37,23 @@ struct BProb {                  // one problem, device side
     float2 *x32_0;              // finest-level FP32 correction (mixed)
 };
 
+struct BSetupLevel {            // one (problem, level) of the batched set-up
+    SetupGeom gm;
+    SetupOut out;
+    SetupFine fine;             // the level below (coarse levels only)
+    int problem;
+    int *err;                   // the problem's set-up error flags
+};
+
+struct BIo {                    // one problem's solve inputs, device side
+    const double2 *rhs;
+    const double2 *xin;         // initial guess (device), or NULL when already in place
+    double2 *xout;              // result destination (device), or NULL
+    BcVals bv;
+    int axisym;
+    double r0, h;
+};
+
 struct BState {                 // per-problem solve state, device side
     double n0[2];
     double nk[2];
@@ -150,6 +167,141 @@ __global__ void __launch_bounds__(kBatchThreads) kb_coarse(const BLevel *__restr
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
         if (lane == 0) reinterpret_cast<R *>(C.x)[row] = acc;
+    }
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(kBatchThreads) kb_setup_fine(const BSetupLevel *__restrict__ sl,
+                                                               const SetupIn *__restrict__ in,
+                                                               const int2 *__restrict__ tab, int n) {
+    for (int v = blockIdx.x; v < n; v += gridDim.x) {
+        const int2 e = tab[v];
+        const BSetupLevel &L = sl[e.x];
+        const int gx = (L.gm.n[0] + kBX - 1) / kBX, gy = (L.gm.n[1] + kBY - 1) / kBY;
+        int bx, by, bz;
+        block_coords(e.y, gx, gy, bx, by, bz);
+        setup_fine_block<DIM>(L.gm, in[L.problem], L.out, L.err, bx, by, bz);
+    }
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(kBatchThreads) kb_setup_coarse(const BSetupLevel *__restrict__ sl,
+                                                                 const int2 *__restrict__ tab, int n) {
+    for (int v = blockIdx.x; v < n; v += gridDim.x) {
+        const int2 e = tab[v];
+        const BSetupLevel &L = sl[e.x];
+        const int gx = (L.gm.n[0] + kBX - 1) / kBX, gy = (L.gm.n[1] + kBY - 1) / kBY;
+        int bx, by, bz;
+        block_coords(e.y, gx, gy, bx, by, bz);
+        setup_coarse_block<DIM>(L.gm, L.fine, L.out, L.err, bx, by, bz);
+    }
+}
+
+// Dense coarsest matrices of all problems (zeroed first by kb_zero_coarse).
+struct BCoarse {
+    int n[3];
+    const double2 *G0, *G1, *G2;
+    const dq *D;
+    const double *l4;
+    double *M;
+    double *Minv;
+    float *Minv32;
+    int *piv;
+    double *dinv;
+    int nc, kl;
+    int *err;
+};
+
+__global__ void __launch_bounds__(kBatchThreads) kb_zero_coarse(const BCoarse *__restrict__ co, int count) {
+    for (int p = blockIdx.y; p < count; p += gridDim.y) {
+        const long long m = (long long)co[p].nc * co[p].nc;
+        for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < m; q += (long long)gridDim.x * blockDim.x)
+            co[p].M[q] = 0.0;
+    }
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(kBatchThreads) kb_coarse_assemble(const BCoarse *__restrict__ co, int count) {
+    for (int p = blockIdx.y; p < count; p += gridDim.y) {
+        const BCoarse &C = co[p];
+        const long long N = (long long)C.n[0] * C.n[1] * C.n[2];
+        const long long n = 2 * N;
+        for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
+            const int i = (int)(c % C.n[0]), j = (int)((c / C.n[0]) % C.n[1]), k = (int)(c / ((long long)C.n[0] * C.n[1]));
+            const dq d = C.D[c];
+            double *M = C.M;
+            M[(2 * c) * n + 2 * c] = d.a;
+            M[(2 * c) * n + 2 * c + 1] = d.b;
+            M[(2 * c + 1) * n + 2 * c] = d.c;
+            M[(2 * c + 1) * n + 2 * c + 1] = d.d;
+            const long long f0 = (long long)i + (long long)(C.n[0] + 1) * ((long long)j + (long long)C.n[1] * k);
+            const long long f1 = (long long)i + (long long)C.n[0] * ((long long)j + (long long)(C.n[1] + 1) * k);
+            const double w4 = C.l4[c];
+            auto put = [&](long long nb, double2 g) {
+                M[(2 * c) * n + 2 * nb] = g.x;
+                M[(2 * c + 1) * n + 2 * nb] = w4 * g.x;
+                M[(2 * c + 1) * n + 2 * nb + 1] = g.y;
+            };
+            if (i > 0) put(c - 1, C.G0[f0]);
+            if (i < C.n[0] - 1) put(c + 1, C.G0[f0 + 1]);
+            if (j > 0) put(c - C.n[0], C.G1[f1]);
+            if (j < C.n[1] - 1) put(c + C.n[0], C.G1[f1 + C.n[0]]);
+            if (DIM == 3) {
+                const long long pl = (long long)C.n[0] * C.n[1];
+                if (k > 0) put(c - pl, C.G2[c]);
+                if (k < C.n[2] - 1) put(c + pl, C.G2[c + pl]);
+            }
+        }
+    }
+}
+
+// Coarsest inverses of the problems listed in ids (nc <= kBandSmemMax): the
+// single-warp LU, one block per problem; then the columns, one warp per 32.
+__global__ void __launch_bounds__(32) kb_band_lu_warp(const BCoarse *__restrict__ co, const int *__restrict__ ids) {
+    const BCoarse &C = co[ids[blockIdx.x]];
+    band_lu_warp_block(C.M, C.nc, C.kl, C.kl, C.piv, C.dinv, C.err);
+}
+
+__global__ void __launch_bounds__(32) kb_band_inv_cols_warp(const BCoarse *__restrict__ co,
+                                                            const int *__restrict__ ids) {
+    const BCoarse &C = co[ids[blockIdx.y]];
+    if ((int)blockIdx.x * 32 >= C.nc) return;
+    band_inv_cols_warp_block(C.M, C.piv, C.dinv, C.nc, C.kl, C.kl, C.Minv, C.Minv32, blockIdx.x);
+}
+
+// Finest-level right-hand sides (and initial guesses) of all problems.
+template <int DIM>
+__global__ void __launch_bounds__(kBatchThreads) kb_prep(const BLevel *__restrict__ lv, const BIo *__restrict__ io,
+                                                         const int2 *__restrict__ tab, int n) {
+    for (int v = blockIdx.x; v < n; v += gridDim.x) {
+        const int2 e = tab[v];
+        const BLevel &B = lv[e.x];
+        const BIo &P = io[B.problem];
+        const Level<double> L = B.d;
+        const int gx = (L.n0 + kBX - 1) / kBX, gy = (L.n1 + kBY - 1) / kBY;
+        int bx, by, bz;
+        block_coords(e.y, gx, gy, bx, by, bz);
+        prep_rhs_block<DIM>(L, P.rhs, P.xin, P.bv, P.axisym, P.r0, P.h, bx, by, bz);
+    }
+}
+
+__global__ void kb_zero_err(const BCoarse *__restrict__ co, int count) {
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < count; p += gridDim.x * blockDim.x) *co[p].err = 0;
+}
+
+__global__ void kb_gather_err(const BCoarse *__restrict__ co, int count, int *__restrict__ out) {
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < count; p += gridDim.x * blockDim.x) out[p] = *co[p].err;
+}
+
+// Results of all problems to the callers' device arrays.
+__global__ void __launch_bounds__(kBatchThreads) kb_copy_out(const BLevel *__restrict__ lv, const BIo *__restrict__ io,
+                                                             const int2 *__restrict__ tab, int n) {
+    for (int v = blockIdx.x; v < n; v += gridDim.x) {
+        const int2 e = tab[v];
+        const BLevel &B = lv[e.x];
+        double2 *dst = io[B.problem].xout;
+        const long long c = (long long)e.y * kBatchThreads + threadIdx.x;
+        if (dst && c < B.d.N) dst[c] = B.d.x[c];
     }
 }
 
@@ -292,6 +444,20 @@ struct mg_batch {
     cudaGraphExec_t graph;
     long long graph_kernels;
     long long launches;
+    // batched set-up and I/O
+    BSetupLevel *sl;
+    SetupIn *sin;
+    BCoarse *co;
+    BIo *io;
+    int *inv_ids;
+    int n_inv_smem;
+    size_t inv_smem_bytes;
+    int max_nc_small;
+    std::vector<int> big_coarse;      // problems whose coarsest inverse takes the banded three-kernel path
+    std::pair<long long, int> setup_fine_tab;
+    std::vector<std::pair<long long, int>> setup_tab;   // depth 1.. (all levels at that depth)
+    char *host_io;                    // pinned staging for the per-call pointer tables
+    int *err_d, *err_h;               // per-problem set-up error flags (device, pinned host)
 };
 
 namespace {
@@ -473,6 +639,68 @@ mg_status mg_batch_create(int count, mg_handle *const *handles, mg_batch **out) 
     b->norm = slice(tn);
     b->coarse = slice(tco);
     b->cells0 = slice(tcell);
+    b->setup_fine_tab = b->norm;                  // level-0 cell grids, as the norm
+    for (int d = 1; d < b->dmax; d++) {
+        std::vector<int2> ts;
+        for (int p = 0; p < count; p++) {
+            const mg_handle *h = handles[p];
+            if (h->nlev <= d) continue;
+            const dim3 gl = cell_grid(h->L[d], dim, h->L[d].n[0]);
+            add_blocks(ts, base[p] + d, (long long)gl.x * gl.y * gl.z);
+        }
+        b->setup_tab.push_back(slice(ts));
+    }
+    // set-up descriptors, one per (problem, level), same indexing as lv
+    std::vector<BSetupLevel> sl(lv.size());
+    std::vector<BCoarse> co(count);
+    std::vector<int> inv_ids;
+    for (int p = 0; p < count; p++) {
+        const mg_handle *h = handles[p];
+        const bool mixed = h->opt.precision == MG_MIXED;
+        double hl = h->grid.h;
+        for (int l = 0; l < h->nlev; l++) {
+            BSetupLevel &S = sl[base[p] + l];
+            std::memset(&S, 0, sizeof(S));
+            for (int a = 0; a < 3; a++) {
+                S.gm.n[a] = h->L[l].n[a];
+                for (int sd = 0; sd < 2; sd++)
+                    S.gm.fac[a][sd] = (a < dim && h->grid.bc[a][sd] == MG_BC_DIRICHLET) ? 2.0 : 0.0;
+            }
+            S.gm.axisym = h->grid.axisym;
+            S.gm.r0 = h->grid.r0;
+            S.gm.h = hl;
+            S.out = setup_out(h->L[l], mixed);
+            if (l > 0) S.fine = setup_fine_of(h->L[l - 1], hl / 2.0);
+            S.problem = p;
+            S.err = h->err_d;
+            hl *= 2.0;
+        }
+        const LevelBuf &c = h->L[h->nlev - 1];
+        BCoarse &C = co[p];
+        for (int a = 0; a < 3; a++) C.n[a] = c.n[a];
+        C.G0 = c.G[0];
+        C.G1 = c.G[1];
+        C.G2 = dim == 3 ? c.G[2] : c.G[0];
+        C.D = c.D;
+        C.l4 = c.l4;
+        C.M = h->Mtmp;
+        C.Minv = h->Minv;
+        C.Minv32 = mixed ? h->Minv32 : nullptr;
+        C.piv = h->piv;
+        C.dinv = h->dinv;
+        C.nc = h->nc;
+        const int off = dim == 3 ? c.n[0] * c.n[1] : c.n[0];
+        C.kl = std::min(h->nc - 1, 2 * off + 1);
+        C.err = h->err_d;
+        if (h->nc <= kBandSmemMax) {
+            inv_ids.push_back(p);
+            b->inv_smem_bytes = std::max(b->inv_smem_bytes, sizeof(double) * (size_t)h->nc * h->nc);
+            b->max_nc_small = std::max(b->max_nc_small, h->nc);
+        } else {
+            b->big_coarse.push_back(p);
+        }
+    }
+    b->n_inv_smem = (int)inv_ids.size();
     // one device allocation for the tables
     size_t off = 0;
     auto take = [&](size_t bytes) {
@@ -483,7 +711,10 @@ mg_status mg_batch_create(int count, mg_handle *const *handles, mg_batch **out) 
     };
     const size_t o_lv = take(sizeof(BLevel) * lv.size()), o_pr = take(sizeof(BProb) * count),
                  o_st = take(sizeof(BState) * count), o_ac = take(sizeof(int)),
-                 o_tab = take(sizeof(int2) * std::max<size_t>(1, tabs.size()));
+                 o_tab = take(sizeof(int2) * std::max<size_t>(1, tabs.size())),
+                 o_sl = take(sizeof(BSetupLevel) * sl.size()), o_sin = take(sizeof(SetupIn) * count),
+                 o_co = take(sizeof(BCoarse) * count), o_io = take(sizeof(BIo) * count),
+                 o_ids = take(sizeof(int) * std::max<size_t>(1, inv_ids.size())), o_err = take(sizeof(int) * count);
     cudaError_t e = cudaMalloc(&b->mem, off);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -495,11 +726,23 @@ mg_status mg_batch_create(int count, mg_handle *const *handles, mg_batch **out) 
     b->st = reinterpret_cast<BState *>(b->mem + o_st);
     b->active_count = reinterpret_cast<int *>(b->mem + o_ac);
     b->tabs = reinterpret_cast<int2 *>(b->mem + o_tab);
+    b->sl = reinterpret_cast<BSetupLevel *>(b->mem + o_sl);
+    b->sin = reinterpret_cast<SetupIn *>(b->mem + o_sin);
+    b->co = reinterpret_cast<BCoarse *>(b->mem + o_co);
+    b->io = reinterpret_cast<BIo *>(b->mem + o_io);
+    b->inv_ids = reinterpret_cast<int *>(b->mem + o_ids);
+    b->err_d = reinterpret_cast<int *>(b->mem + o_err);
     if (cudaMemcpy(b->lv, lv.data(), sizeof(BLevel) * lv.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(b->pr, pr.data(), sizeof(BProb) * count, cudaMemcpyHostToDevice) != cudaSuccess ||
         (tabs.size() && cudaMemcpy(b->tabs, tabs.data(), sizeof(int2) * tabs.size(), cudaMemcpyHostToDevice) !=
                             cudaSuccess) ||
+        cudaMemcpy(b->sl, sl.data(), sizeof(BSetupLevel) * sl.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(b->co, co.data(), sizeof(BCoarse) * count, cudaMemcpyHostToDevice) != cudaSuccess ||
+        (inv_ids.size() && cudaMemcpy(b->inv_ids, inv_ids.data(), sizeof(int) * inv_ids.size(),
+                                      cudaMemcpyHostToDevice) != cudaSuccess) ||
         cudaMemset(b->st, 0, sizeof(BState) * count) != cudaSuccess ||
+        cudaMallocHost(&b->host_io, std::max(sizeof(SetupIn), sizeof(BIo)) * count) != cudaSuccess ||
+        cudaMallocHost(&b->err_h, sizeof(int) * count) != cudaSuccess ||
         cudaMallocHost(&b->active_h, sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
         mg_batch_destroy(b);
@@ -518,11 +761,36 @@ mg_status mg_batch_solve(mg_batch *b, const double *const *rhs, double *const *x
         if (!rhs[p] || !x[p]) return fail(MG_ERR_INVALID_ARG, "mg_batch_solve: NULL rhs or x");
     }
     DeviceGuard dg(b->device);
-    for (int p = 0; p < b->count; p++) {
-        mg_status st = prep(b->h[p], rhs[p], x[p], on_device);
-        if (st) return st;
-    }
     cudaStream_t s = b->stream;
+    {
+        BIo *io = reinterpret_cast<BIo *>(b->host_io);
+        for (int p = 0; p < b->count; p++) {
+            mg_handle *h = b->h[p];
+            BIo &o = io[p];
+            std::memset(&o, 0, sizeof(o));
+            o.bv = bc_vals(h->grid);
+            o.axisym = h->grid.axisym;
+            o.r0 = h->grid.r0;
+            o.h = h->grid.h;
+            if (on_device) {
+                if (!aligned16(rhs[p]) || !aligned16(x[p]))
+                    return fail(MG_ERR_INVALID_ARG, "device pair arrays must be 16-byte aligned");
+                o.rhs = reinterpret_cast<const double2 *>(rhs[p]);
+                o.xin = reinterpret_cast<const double2 *>(x[p]);
+                o.xout = reinterpret_cast<double2 *>(x[p]);
+            } else {
+                CK(cudaMemcpyAsync(h->stage, rhs[p], sizeof(double2) * h->L[0].N, cudaMemcpyHostToDevice, s));
+                CK(cudaMemcpyAsync(h->L[0].x, x[p], sizeof(double2) * h->L[0].N, cudaMemcpyHostToDevice, s));
+                o.rhs = reinterpret_cast<const double2 *>(h->stage);
+            }
+        }
+        CK(cudaMemcpyAsync(b->io, io, sizeof(BIo) * b->count, cudaMemcpyHostToDevice, s));
+        const int n = b->norm.second;
+        if (b->dim == 2) kb_prep<2><<<batch_grid(n), kBlock, 0, s>>>(b->lv, b->io, b->tabs + b->norm.first, n);
+        else kb_prep<3><<<batch_grid(n), kBlock, 0, s>>>(b->lv, b->io, b->tabs + b->norm.first, n);
+        b->launches++;
+        CK(cudaGetLastError());
+    }
     if (b->dim == 2) b_norm<2>(b, s, 1);
     else b_norm<3>(b, s, 1);
     CK(cudaGetLastError());
@@ -554,9 +822,16 @@ mg_status mg_batch_solve(mg_batch *b, const double *const *rhs, double *const *x
     }
     std::vector<BState> host(b->count);
     CK(cudaMemcpyAsync(host.data(), b->st, sizeof(BState) * b->count, cudaMemcpyDeviceToHost, s));
-    for (int p = 0; p < b->count; p++) {
-        mg_status st = x_out(b->h[p], x[p], on_device);
-        if (st) return st;
+    if (on_device) {
+        const int n = b->cells0.second;
+        kb_copy_out<<<batch_grid(n), kBatchThreads, 0, s>>>(b->lv, b->io, b->tabs + b->cells0.first, n);
+        b->launches++;
+        CK(cudaGetLastError());
+    } else {
+        for (int p = 0; p < b->count; p++) {
+            mg_status st = x_out(b->h[p], x[p], 0);
+            if (st) return st;
+        }
     }
     CK(cudaStreamSynchronize(s));
     const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -586,6 +861,101 @@ mg_status mg_batch_solve(mg_batch *b, const double *const *rhs, double *const *x
     return MG_OK;
 }
 
+mg_status mg_batch_set_coeffs(mg_batch *b, const double *const *lambda, const double *const *face_alpha,
+                              const double *const *face_k, int on_device) {
+    if (!b || !lambda || !face_alpha || !face_k) return fail(MG_ERR_INVALID_ARG, "mg_batch_set_coeffs: bad arguments");
+    const int dim = b->dim;
+    for (int p = 0; p < b->count; p++) {
+        if (!lambda[p]) return fail(MG_ERR_INVALID_ARG, "NULL lambda");
+        for (int a = 0; a < dim; a++)
+            if (!face_alpha[3 * p + a] || !face_k[3 * p + a]) return fail(MG_ERR_INVALID_ARG, "NULL face array");
+    }
+    DeviceGuard dg(b->device);
+    cudaStream_t s = b->stream;
+    SetupIn *in = reinterpret_cast<SetupIn *>(b->host_io);
+    for (int p = 0; p < b->count; p++) {
+        mg_handle *h = b->h[p];
+        h->coeffs_set = false;
+        const LevelBuf &f = h->L[0];
+        SetupIn &q = in[p];
+        std::memset(&q, 0, sizeof(q));
+        if (on_device) {
+            q.lam = lambda[p];
+            for (int a = 0; a < dim; a++) {
+                q.fa[a] = face_alpha[3 * p + a];
+                q.fk[a] = face_k[3 * p + a];
+            }
+        } else {
+            double *st = reinterpret_cast<double *>(h->stage);
+            CK(cudaMemcpyAsync(st, lambda[p], sizeof(double) * 4 * f.N, cudaMemcpyHostToDevice, s));
+            q.lam = st;
+            double *ptr = st + 4 * f.N;
+            for (int a = 0; a < dim; a++) {
+                CK(cudaMemcpyAsync(ptr, face_alpha[3 * p + a], sizeof(double) * f.nf[a], cudaMemcpyHostToDevice, s));
+                q.fa[a] = ptr;
+                ptr += f.nf[a];
+                CK(cudaMemcpyAsync(ptr, face_k[3 * p + a], sizeof(double) * f.nf[a], cudaMemcpyHostToDevice, s));
+                q.fk[a] = ptr;
+                ptr += f.nf[a];
+            }
+        }
+    }
+    CK(cudaMemcpyAsync(b->sin, in, sizeof(SetupIn) * b->count, cudaMemcpyHostToDevice, s));
+    kb_zero_err<<<(b->count + 255) / 256, 256, 0, s>>>(b->co, b->count);
+    const int nf = b->setup_fine_tab.second;
+    if (dim == 2) kb_setup_fine<2><<<batch_grid(nf), kBlock, 0, s>>>(b->sl, b->sin, b->tabs + b->setup_fine_tab.first, nf);
+    else kb_setup_fine<3><<<batch_grid(nf), kBlock, 0, s>>>(b->sl, b->sin, b->tabs + b->setup_fine_tab.first, nf);
+    b->launches += 2;
+    for (size_t d = 0; d < b->setup_tab.size(); d++) {
+        const int n = b->setup_tab[d].second;
+        if (n == 0) continue;
+        if (dim == 2) kb_setup_coarse<2><<<batch_grid(n), kBlock, 0, s>>>(b->sl, b->tabs + b->setup_tab[d].first, n);
+        else kb_setup_coarse<3><<<batch_grid(n), kBlock, 0, s>>>(b->sl, b->tabs + b->setup_tab[d].first, n);
+        b->launches++;
+    }
+    const unsigned gy = (unsigned)std::min(b->count, 65535);
+    kb_zero_coarse<<<dim3(16, gy), kBatchThreads, 0, s>>>(b->co, b->count);
+    if (dim == 2) kb_coarse_assemble<2><<<dim3(4, gy), kBatchThreads, 0, s>>>(b->co, b->count);
+    else kb_coarse_assemble<3><<<dim3(4, gy), kBatchThreads, 0, s>>>(b->co, b->count);
+    b->launches += 2;
+    if (b->n_inv_smem > 0) {
+        CK(cudaFuncSetAttribute(kb_band_lu_warp, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)b->inv_smem_bytes));
+        kb_band_lu_warp<<<b->n_inv_smem, 32, b->inv_smem_bytes, s>>>(b->co, b->inv_ids);
+        kb_band_inv_cols_warp<<<dim3((b->max_nc_small + 31) / 32, b->n_inv_smem), 32,
+                                sizeof(double) * 32 * (size_t)b->max_nc_small, s>>>(b->co, b->inv_ids);
+        b->launches += 2;
+    }
+    for (int p : b->big_coarse) {           // medium coarsest levels: the banded three-kernel path
+        mg_handle *h = b->h[p];
+        const LevelBuf &c = h->L[h->nlev - 1];
+        const int off = dim == 3 ? c.n[0] * c.n[1] : c.n[0];
+        const int kl = std::min(h->nc - 1, 2 * off + 1);
+        k_band_lu<<<1, dim3(32, 32, 1), 0, s>>>(h->Mtmp, h->nc, kl, kl, h->piv, h->dinv, h->err_d);
+        k_band_inv_cols<<<(h->nc + 127) / 128, 128, 0, s>>>(h->Mtmp, h->piv, h->dinv, h->nc, kl, kl, h->Mwork);
+        k_transpose<<<lin_blocks((long long)h->nc * h->nc), 256, 0, s>>>(h->Mwork, h->Minv, h->nc);
+        b->launches += 3;
+        if (h->opt.precision == MG_MIXED) {
+            k_to_f32<<<lin_blocks((long long)h->nc * h->nc), 256, 0, s>>>(h->Minv, h->Minv32,
+                                                                         (long long)h->nc * h->nc);
+            b->launches++;
+        }
+    }
+    kb_gather_err<<<(b->count + 255) / 256, 256, 0, s>>>(b->co, b->count, b->err_d);
+    b->launches++;
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(b->err_h, b->err_d, sizeof(int) * b->count, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    for (int p = 0; p < b->count; p++) {
+        const int e = b->err_h[p];
+        if (e & 1) return fail(MG_ERR_INVALID_COEFF, "problem " + std::to_string(p) + ": non-finite coefficient");
+        if (e & 2) return fail(MG_ERR_INVALID_COEFF, "problem " + std::to_string(p) + ": singular local block");
+        if (e & 4) return fail(MG_ERR_INVALID_COEFF, "problem " + std::to_string(p) + ": singular coarsest matrix");
+    }
+    for (int p = 0; p < b->count; p++) b->h[p]->coeffs_set = true;
+    return MG_OK;
+}
+
 mg_status mg_batch_counters(const mg_batch *b, long long *launches) {
     if (!b) return fail(MG_ERR_INVALID_ARG, "batch is NULL");
     if (launches) *launches = b->launches;
@@ -598,6 +968,8 @@ mg_status mg_batch_destroy(mg_batch *b) {
     if (b->stream) cudaStreamSynchronize(b->stream);
     if (b->graph) cudaGraphExecDestroy(b->graph);
     if (b->active_h) cudaFreeHost(b->active_h);
+    if (b->host_io) cudaFreeHost(b->host_io);
+    if (b->err_h) cudaFreeHost(b->err_h);
     if (b->mem) cudaFree(b->mem);
     delete b;
     return MG_OK;

@@ -220,10 +220,10 @@ void plan(mg_handle *h, char *base, size_t *bytes) {
     h->stage = P.take<char>((long long)h->stage_bytes);
     h->Minv = P.take<double>((long long)h->nc * h->nc);
     h->Mtmp = P.take<double>((long long)h->nc * h->nc);
-    const bool banded = h->nc > kBandSmemMax;
-    h->Mwork = banded ? P.take<double>((long long)h->nc * h->nc) : nullptr;
-    h->piv = banded ? P.take<int>(h->nc) : nullptr;
-    h->dinv = banded ? P.take<double>(h->nc) : nullptr;
+    const bool big = h->nc > kBandSmemMax;
+    h->Mwork = big ? P.take<double>((long long)h->nc * h->nc) : nullptr;
+    h->piv = P.take<int>(h->nc);
+    h->dinv = P.take<double>(h->nc);
     h->Minv32 = mixed ? P.take<float>((long long)h->nc * h->nc) : nullptr;
     const dim3 gg = cell_grid(f, g.dim, f.n[0]);
     h->npartial = (int)(gg.x * gg.y * gg.z);
@@ -510,6 +510,17 @@ SetupOut setup_out(const LevelBuf &l, bool mixed) {
     return o;
 }
 
+SetupFine setup_fine_of(const LevelBuf &F, double h) {
+    SetupFine s;
+    s.n0 = F.n[0];
+    s.n1 = F.n[1];
+    s.S = F.S;
+    s.l4 = F.l4;
+    for (int a = 0; a < 3; a++) s.G[a] = F.G[a] ? F.G[a] : F.G[0];
+    s.h = h;
+    return s;
+}
+
 template <int DIM>
 mg_status setup_hierarchy(mg_handle *h, const double *lam, const double *const fa[3], const double *const fk[3],
                           int on_device) {
@@ -549,9 +560,13 @@ mg_status setup_hierarchy(mg_handle *h, const double *lam, const double *const f
     gm.axisym = g.axisym;
     gm.r0 = g.r0;
     gm.h = g.h;
-    const double *f2a = DIM == 3 ? fad[2] : fad[0], *f2k = DIM == 3 ? fkd[2] : fkd[0];
-    k_setup_fine<DIM><<<cell_grid(f, DIM, f.n[0]), kBlock, 0, s>>>(gm, lam_d, fad[0], fad[1], f2a, fkd[0], fkd[1],
-                                                                   f2k, setup_out(f, mixed), h->err_d);
+    SetupIn in;
+    in.lam = lam_d;
+    for (int a = 0; a < 3; a++) {
+        in.fa[a] = a < DIM ? fad[a] : nullptr;
+        in.fk[a] = a < DIM ? fkd[a] : nullptr;
+    }
+    k_setup_fine<DIM><<<cell_grid(f, DIM, f.n[0]), kBlock, 0, s>>>(gm, in, setup_out(f, mixed), h->err_d);
     CK(cudaGetLastError());
     double hl = g.h;
     for (int l = 1; l < h->nlev; l++) {
@@ -560,9 +575,8 @@ mg_status setup_hierarchy(mg_handle *h, const double *lam, const double *const f
         SetupGeom cg = gm;
         for (int a = 0; a < 3; a++) cg.n[a] = C.n[a];
         cg.h = 2.0 * hl;
-        k_setup_coarse<DIM><<<cell_grid(C, DIM, C.n[0]), kBlock, 0, s>>>(cg, F.n[0], F.n[1], F.S, F.l4, F.G[0],
-                                                                         F.G[1], DIM == 3 ? F.G[2] : F.G[0], hl,
-                                                                         setup_out(C, mixed), h->err_d);
+        k_setup_coarse<DIM><<<cell_grid(C, DIM, C.n[0]), kBlock, 0, s>>>(cg, setup_fine_of(F, hl), setup_out(C, mixed),
+                                                                         h->err_d);
         CK(cudaGetLastError());
         hl *= 2.0;
     }
@@ -575,20 +589,22 @@ mg_status setup_hierarchy(mg_handle *h, const double *lam, const double *const f
     const int off = DIM == 3 ? c.n[0] * c.n[1] : c.n[0];
     const int kl = std::min(h->nc - 1, 2 * off + 1);
     if (h->nc <= kBandSmemMax) {
-        const size_t smem = sizeof(double) * ((size_t)h->nc * h->nc + 32 * (size_t)h->nc);
-        CK(cudaFuncSetAttribute(k_band_inverse_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_band_inverse_smem<<<1, 1024, smem, s>>>(h->Mtmp, h->Minv, h->nc, kl, kl, h->err_d);
+        const size_t smem_lu = sizeof(double) * (size_t)h->nc * h->nc;
+        CK(cudaFuncSetAttribute(k_band_lu_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_lu));
+        k_band_lu_warp<<<1, 32, smem_lu, s>>>(h->Mtmp, h->nc, kl, kl, h->piv, h->dinv, h->err_d);
+        k_band_inv_cols_warp<<<(h->nc + 31) / 32, 32, sizeof(double) * 32 * (size_t)h->nc, s>>>(
+            h->Mtmp, h->piv, h->dinv, h->nc, kl, kl, h->Minv, mixed ? h->Minv32 : nullptr);
     } else {
         k_band_lu<<<1, dim3(32, 32, 1), 0, s>>>(h->Mtmp, h->nc, kl, kl, h->piv, h->dinv, h->err_d);
         k_band_inv_cols<<<(h->nc + 127) / 128, 128, 0, s>>>(h->Mtmp, h->piv, h->dinv, h->nc, kl, kl, h->Mwork);
         k_transpose<<<lin_blocks((long long)h->nc * h->nc), 256, 0, s>>>(h->Mwork, h->Minv, h->nc);
     }
     CK(cudaGetLastError());
-    if (mixed) {
+    if (mixed && h->nc > kBandSmemMax) {
         k_to_f32<<<lin_blocks((long long)h->nc * h->nc), 256, 0, s>>>(h->Minv, h->Minv32, (long long)h->nc * h->nc);
         CK(cudaGetLastError());
     }
-    counted(h, h->nlev + 1 + (h->nc <= kBandSmemMax ? 1 : 3) + (mixed ? 1 : 0));
+    counted(h, h->nlev + 1 + (h->nc <= kBandSmemMax ? 2 : 4));
     int err = 0;
     CK(cudaMemcpyAsync(&err, h->err_d, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));

@@ -477,12 +477,14 @@ __device__ __forceinline__ void boundary_data(const Level<double> &L, const BcVa
     gp += L.l4[cell_id(i, j, k, n0, n1)] * gT;
 }
 
+// Block (bx, by, bz) of the cell grid; xin (may be NULL) is also copied into L.x.
 template <int DIM>
-__global__ void __launch_bounds__(kBX * kBY) k_prep_rhs(Level<double> L, const double2 *__restrict__ rhs,
-                                                      BcVals bv, int axisym, double r0, double h) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y * blockDim.y + threadIdx.y;
-    const int k = DIM == 3 ? (int)blockIdx.z : 0;
+__device__ __forceinline__ void prep_rhs_block(const Level<double> &L, const double2 *__restrict__ rhs,
+                                               const double2 *__restrict__ xin, const BcVals &bv, int axisym,
+                                               double r0, double h, int bx, int by, int bz) {
+    const int i = bx * kBX + threadIdx.x;
+    const int j = by * kBY + threadIdx.y;
+    const int k = DIM == 3 ? bz : 0;
     if (i >= L.n0 || j >= L.n1) return;
     const long long c = cell_id(i, j, k, L.n0, L.n1);
     const double s = axisym ? r0 + (i + 0.5) * h : 1.0;
@@ -490,6 +492,13 @@ __global__ void __launch_bounds__(kBX * kBY) k_prep_rhs(Level<double> L, const d
     double gT, gp;
     boundary_data<DIM>(L, bv, i, j, k, gT, gp);
     L.b[c] = make_double2(s * q.x - gT, s * q.y - gp);
+    if (xin) L.x[c] = xin[c];
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(kBX * kBY) k_prep_rhs(Level<double> L, const double2 *__restrict__ rhs,
+                                                      BcVals bv, int axisym, double r0, double h) {
+    prep_rhs_block<DIM>(L, rhs, nullptr, bv, axisym, r0, h, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 // y = L(x) (Eqs. 27-28): offdiag + boundary data + D x is s_i times the rows.
@@ -535,6 +544,11 @@ struct SetupGeom {
     double fac[3][2];             // boundary factor per axis / side: 2 Dirichlet, 0 wall/axis
 };
 
+// Finite test on the bit pattern (integer pipe, not the scarce FP64 pipe).
+__device__ __forceinline__ bool finite_bits(double v) {
+    return (__double_as_longlong(v) & 0x7ff0000000000000LL) != 0x7ff0000000000000LL;
+}
+
 template <int DIM>
 __device__ __forceinline__ void finish_cell(const SetupOut &o, long long c, const long long fid[3][2], int own[3][2],
                                             const double2 g[3][2], dq S, double l4, int *err) {
@@ -554,7 +568,7 @@ __device__ __forceinline__ void finish_cell(const SetupOut &o, long long c, cons
     o.l4[c] = l4;
     dq D{S.a - sT, S.b, S.c - l4 * sT, S.d - sp};
     const double det = D.a * D.d - D.b * D.c;
-    if (!(det != 0.0) || !isfinite(det)) atomicOr(err, 2);
+    if ((__double_as_longlong(det) & 0x7fffffffffffffffLL) == 0 || !finite_bits(det)) atomicOr(err, 2);
     const double id = 1.0 / det;
     const dq Di{D.d * id, -D.b * id, -D.c * id, D.a * id};
     o.D[c] = D;
@@ -575,23 +589,28 @@ __device__ __forceinline__ void face_ids(const int n[3], int i, int j, int k, lo
     fid[2][0] = f2; fid[2][1] = f2 + (long long)n[0] * n[1];
 }
 
-// Finest level from lambda [N][4] and the per-axis arrays of 1/rho and k.
+// The caller's coefficient arrays of one problem.
+struct SetupIn {
+    const double *lam;            // [N][4]
+    const double *fa[3], *fk[3];  // 1/rho and k on the faces of each axis
+};
+
+// Finest level from lambda [N][4] and the per-axis arrays of 1/rho and k:
+// block (bx, by, bz) of the cell grid (ceil(n0/32), ceil(n1/8), n2).
 template <int DIM>
-__global__ void __launch_bounds__(kBX * kBY) k_setup_fine(SetupGeom gm, const double *__restrict__ lam,
-                                                        const double *__restrict__ fa0, const double *__restrict__ fa1,
-                                                        const double *__restrict__ fa2, const double *__restrict__ fk0,
-                                                        const double *__restrict__ fk1, const double *__restrict__ fk2,
-                                                        SetupOut o, int *__restrict__ err) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y * blockDim.y + threadIdx.y;
-    const int k = DIM == 3 ? (int)blockIdx.z : 0;
+__device__ __forceinline__ void setup_fine_block(const SetupGeom &gm, const SetupIn &in, const SetupOut &o, int *err,
+                                                 int bx, int by, int bz) {
+    const int i = bx * kBX + threadIdx.x;
+    const int j = by * kBY + threadIdx.y;
+    const int k = DIM == 3 ? bz : 0;
     if (i >= gm.n[0] || j >= gm.n[1]) return;
+    const double *lam = in.lam;
     const long long c = cell_id(i, j, k, gm.n[0], gm.n[1]);
     const double l1 = lam[4 * c], l2 = lam[4 * c + 1], l3 = lam[4 * c + 2], l4 = lam[4 * c + 3];
-    bool bad = !isfinite(l1) || !isfinite(l2) || !isfinite(l3) || !isfinite(l4);
+    bool bad = !finite_bits(l1) || !finite_bits(l2) || !finite_bits(l3) || !finite_bits(l4);
     const double s = gm.axisym ? gm.r0 + (i + 0.5) * gm.h : 1.0;
     const double ih2 = 1.0 / (gm.h * gm.h);
-    const double *fa[3] = {fa0, fa1, fa2}, *fk[3] = {fk0, fk1, fk2};
+    const double *const *fa = in.fa, *const *fk = in.fk;
     const int pos[3] = {i, j, k};
     long long fid[3][2];
     face_ids(gm.n, i, j, k, fid);
@@ -602,14 +621,14 @@ __global__ void __launch_bounds__(kBX * kBY) k_setup_fine(SetupGeom gm, const do
 #pragma unroll
         for (int sd = 0; sd < 2; sd++) {
             const int fpos = pos[a] + sd;
-            double fac = 1.0;
-            if (fpos == 0) fac = gm.fac[a][0];
-            else if (fpos == gm.n[a]) fac = gm.fac[a][1];
-            double rho_f = 1.0;
-            if (gm.axisym) rho_f = a == 0 ? gm.r0 + (i + sd) * gm.h : s;
-            const double w = rho_f * ih2 * fac;
+            // w = rho_f / h^2 times the boundary factor; FP64 multiplies only
+            // where the geometry or a boundary needs them
+            double w = ih2;
+            if (gm.axisym) w *= (a == 0 ? gm.r0 + (i + sd) * gm.h : s);
+            if (fpos == 0) w *= gm.fac[a][0];
+            else if (fpos == gm.n[a]) w *= gm.fac[a][1];
             const double al = fa[a][fid[a][sd]], kk = fk[a][fid[a][sd]];
-            bad = bad || !isfinite(al) || !isfinite(kk);
+            bad = bad || !finite_bits(al) || !finite_bits(kk);
             g[a][sd] = make_double2(kk * w, al * w);
             own[a][sd] = sd == 0 || fpos == gm.n[a];
         }
@@ -617,20 +636,34 @@ __global__ void __launch_bounds__(kBX * kBY) k_setup_fine(SetupGeom gm, const do
     finish_cell<DIM>(o, c, fid, own, g, dq{s * l1, s * l2, 0.0, s * l3}, l4, err);
 }
 
+template <int DIM>
+__global__ void __launch_bounds__(kBX * kBY) k_setup_fine(SetupGeom gm, SetupIn in, SetupOut o, int *__restrict__ err) {
+    setup_fine_block<DIM>(gm, in, o, err, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
 // Coarse level from the level below: S = mean of the children's S, l4 the
 // volume-weighted mean of theirs, each face the sum of its 2^(DIM-1) fine
 // faces / 2^(DIM+1) (area-weighted mean coefficient re-discretised at 2h).
+// The level below, as the coarsening reads it.
+struct SetupFine {
+    int n0, n1;
+    const dq *S;
+    const double *l4;
+    const double2 *G[3];
+    double h;
+};
+
 template <int DIM>
-__global__ void __launch_bounds__(kBX * kBY) k_setup_coarse(SetupGeom cg, int fn0, int fn1, const dq *__restrict__ Sf,
-                                                          const double *__restrict__ l4f,
-                                                          const double2 *__restrict__ Gf0,
-                                                          const double2 *__restrict__ Gf1,
-                                                          const double2 *__restrict__ Gf2, double hf, SetupOut o,
-                                                          int *__restrict__ err) {
-    const int I = blockIdx.x * blockDim.x + threadIdx.x;
-    const int J = blockIdx.y * blockDim.y + threadIdx.y;
-    const int K = DIM == 3 ? (int)blockIdx.z : 0;
+__device__ __forceinline__ void setup_coarse_block(const SetupGeom &cg, const SetupFine &F, const SetupOut &o,
+                                                   int *err, int bx, int by, int bz) {
+    const int I = bx * kBX + threadIdx.x;
+    const int J = by * kBY + threadIdx.y;
+    const int K = DIM == 3 ? bz : 0;
     if (I >= cg.n[0] || J >= cg.n[1]) return;
+    const int fn0 = F.n0, fn1 = F.n1;
+    const dq *Sf = F.S;
+    const double *l4f = F.l4;
+    const double hf = F.h;
     const long long cc = cell_id(I, J, K, cg.n[0], cg.n[1]);
     double a0 = 0, a1 = 0, a2 = 0, a3 = 0, v4 = 0, vs = 0;
 #pragma unroll
@@ -648,7 +681,7 @@ __global__ void __launch_bounds__(kBX * kBY) k_setup_coarse(SetupGeom cg, int fn
     const double l4 = v4 / vs;
     const int P[3] = {I, J, K};
     const int fm[3][2] = {{fn0 + 1, fn1}, {fn0, fn1 + 1}, {fn0, fn1}};   // fine face array dims (x, y) per axis
-    const double2 *Gf[3] = {Gf0, Gf1, Gf2};
+    const double2 *const *Gf = F.G;
     long long fid[3][2];
     face_ids(cg.n, I, J, K, fid);
     int own[3][2];
@@ -681,6 +714,12 @@ __global__ void __launch_bounds__(kBX * kBY) k_setup_coarse(SetupGeom cg, int fn
             own[a][sd] = sd == 0 || P[a] + sd == cg.n[a];
         }
     finish_cell<DIM>(o, cc, fid, own, g, S, l4, err);
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(kBX * kBY) k_setup_coarse(SetupGeom cg, SetupFine F, SetupOut o,
+                                                          int *__restrict__ err) {
+    setup_coarse_block<DIM>(cg, F, o, err, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 // FP32 copy of an FP64 array (the coarsest inverse of mixed precision).
@@ -725,104 +764,126 @@ __global__ void k_coarse_assemble(int n0, int n1, int n2, const double2 *__restr
     }
 }
 
-// Coarsest inverse for n <= kBandSmemMax in one block, everything in shared
-// memory: the banded LU of k_band_lu below done by warp 0 alone (no block
-// barriers inside the column loop), then each warp solves L U x = P e_j for
-// columns j = warp, warp + 32, ... with its vector in shared memory and writes
-// column j of the inverse.  Same arithmetic as the three-kernel path.
+// Coarsest inverse for n <= kBandSmemMax in two kernels.  GB300's FP64 pipe
+// issues one warp instruction per 16 clocks per SM, so the work is arranged so
+// that every FP64 warp instruction does 32 useful operations where it can:
+//
+// k_band_lu_warp: one warp, the matrix in shared memory.  The banded LU with
+//   partial pivoting of k_band_lu below (the pivot chosen by comparing |a| as
+//   integers: the bit patterns of non-negative doubles order like the values,
+//   lowest row on ties), factors written back to M, piv[k], dinv[k] = 1/u_kk.
+// k_band_inv_cols_warp: one warp per block, one column j of the inverse per
+//   lane: L U x = P e_j with the vectors in shared memory (column-interleaved)
+//   and the factors read as warp-wide broadcasts; writes Minv (and Minv32).
 constexpr int kBandSmemMax = 128;
 
-__global__ void __launch_bounds__(1024) k_band_inverse_smem(const double *__restrict__ M, double *__restrict__ Minv,
-                                                            int n, int kl, int ku, int *__restrict__ err) {
-    extern __shared__ double sm[];
-    double *a = sm;                         // n x n
-    double *ys = sm + n * n;                // 32 vectors of n
-    __shared__ int piv[kBandSmemMax];
-    __shared__ double dinv[kBandSmemMax];
-    __shared__ int bad;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int q = threadIdx.x; q < n * n; q += blockDim.x) a[q] = M[q];
-    if (threadIdx.x == 0) bad = 0;
-    __syncthreads();
+__device__ __forceinline__ long long abs_bits(double v) {
+    return __double_as_longlong(v) & 0x7fffffffffffffffLL;
+}
+
+__device__ __forceinline__ void band_lu_warp_block(double *__restrict__ M, int n, int kl, int ku,
+                                                   int *__restrict__ piv, double *__restrict__ dinv,
+                                                   int *__restrict__ err) {
+    extern __shared__ double a[];
+    const int lane = threadIdx.x;
+    for (int q = lane; q < n * n; q += 32) a[q] = M[q];
+    __syncwarp();
     const int ur = kl + ku;
-    if (warp == 0) {
-        for (int k = 0; k < n; k++) {
-            const int rlast = min(n - 1, k + kl), clast = min(n - 1, k + ur);
-            double best = -1.0;
-            int br = k;
-            for (int r = k + lane; r <= rlast; r += 32) {
-                const double v = fabs(a[r * n + k]);
-                if (v > best) { best = v; br = r; }
-            }
-            for (int o = 16; o > 0; o >>= 1) {
-                const double ov = __shfl_xor_sync(0xffffffffu, best, o);
-                const int orr = __shfl_xor_sync(0xffffffffu, br, o);
-                if (ov > best || (ov == best && orr < br)) { best = ov; br = orr; }
-            }
-            if (!(best > 0.0)) {
-                if (lane == 0) bad = 1;
-                break;
-            }
-            if (br != k)
-                for (int c = k + lane; c <= clast; c += 32) {
-                    const double t = a[k * n + c];
-                    a[k * n + c] = a[br * n + c];
-                    a[br * n + c] = t;
-                }
-            __syncwarp();
-            double ip = 0.0;
-            if (lane == 0) {
-                ip = 1.0 / a[k * n + k];
-                piv[k] = br;
-                dinv[k] = ip;
-            }
-            ip = __shfl_sync(0xffffffffu, ip, 0);
-            for (int r = k + 1 + lane; r <= rlast; r += 32) a[r * n + k] *= ip;
-            __syncwarp();
-            const int w = clast - k;                       // window columns k+1..clast
-            const int rows = rlast - k;
-            for (int q = lane; q < rows * w; q += 32) {
-                const int r = k + 1 + q / w, c = k + 1 + q % w;
-                const double l = a[r * n + k];
-                if (l != 0.0) a[r * n + c] -= l * a[k * n + c];
-            }
-            __syncwarp();
+    const long long kInfBits = 0x7ff0000000000000LL;
+    for (int k = 0; k < n; k++) {
+        const int rlast = min(n - 1, k + kl), clast = min(n - 1, k + ur);
+        long long best = -1;
+        int br = k;
+        for (int r = k + lane; r <= rlast; r += 32) {
+            const long long v = abs_bits(a[r * n + k]);
+            if (v > best) { best = v; br = r; }
         }
-    }
-    __syncthreads();
-    if (bad) {
-        if (threadIdx.x == 0) atomicOr(err, 4);
-        return;
-    }
-    double *y = ys + warp * n;
-    for (int j = warp; j < n; j += (int)(blockDim.x >> 5)) {
-        for (int i = lane; i < n; i += 32) y[i] = (i == j) ? 1.0 : 0.0;
+        for (int o = 16; o > 0; o >>= 1) {
+            const long long ov = __shfl_xor_sync(0xffffffffu, best, o);
+            const int orr = __shfl_xor_sync(0xffffffffu, br, o);
+            if (ov > best || (ov == best && orr < br)) { best = ov; br = orr; }
+        }
+        if (best <= 0 || best >= kInfBits) {           // zero, infinite or NaN pivot
+            if (lane == 0) atomicOr(err, 4);
+            return;
+        }
+        if (br != k)
+            for (int c = k + lane; c <= clast; c += 32) {
+                const double t = a[k * n + c];
+                a[k * n + c] = a[br * n + c];
+                a[br * n + c] = t;
+            }
         __syncwarp();
-        for (int k = 0; k < n; k++) {
-            const int p = piv[k];
-            if (p != k && lane == 0) {
-                const double t = y[k];
-                y[k] = y[p];
-                y[p] = t;
-            }
-            __syncwarp();
-            const double yk = y[k];
-            const int rlast = min(n - 1, k + kl);
-            if (yk != 0.0)
-                for (int r = k + 1 + lane; r <= rlast; r += 32) y[r] -= a[r * n + k] * yk;
-            __syncwarp();
+        double ip = 0.0;
+        if (lane == 0) {
+            ip = 1.0 / a[k * n + k];
+            piv[k] = br;
+            dinv[k] = ip;
         }
-        for (int i = n - 1; i >= 0; i--) {
-            const int clast = min(n - 1, i + ur);
-            double s = 0.0;
-            for (int c = i + 1 + lane; c <= clast; c += 32) s += a[i * n + c] * y[c];
-            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-            if (lane == 0) y[i] = (y[i] - s) * dinv[i];
-            __syncwarp();
+        ip = __shfl_sync(0xffffffffu, ip, 0);
+        for (int r = k + 1 + lane; r <= rlast; r += 32) a[r * n + k] *= ip;
+        __syncwarp();
+        for (int r = k + 1; r <= rlast; r++) {
+            const double l = a[r * n + k];
+            if (abs_bits(l) == 0) continue;
+            for (int c = k + 1 + lane; c <= clast; c += 32) a[r * n + c] -= l * a[k * n + c];
         }
-        for (int i = lane; i < n; i += 32) Minv[(long long)i * n + j] = y[i];
         __syncwarp();
     }
+    for (int q = lane; q < n * n; q += 32) M[q] = a[q];
+}
+
+__global__ void __launch_bounds__(32) k_band_lu_warp(double *__restrict__ M, int n, int kl, int ku,
+                                                     int *__restrict__ piv, double *__restrict__ dinv,
+                                                     int *__restrict__ err) {
+    band_lu_warp_block(M, n, kl, ku, piv, dinv, err);
+}
+
+// Columns 32 * col_block + lane of the inverse from the factors of k_band_lu_warp.
+__device__ __forceinline__ void band_inv_cols_warp_block(const double *__restrict__ M, const int *__restrict__ piv,
+                                                         const double *__restrict__ dinv, int n, int kl, int ku,
+                                                         double *__restrict__ Minv, float *__restrict__ Minv32,
+                                                         int col_block) {
+    extern __shared__ double ysm[];                    // y[i][lane], n x 32
+    const int lane = threadIdx.x;
+    const int j = col_block * 32 + lane;
+    for (int i = 0; i < n; i++) ysm[i * 32 + lane] = (i == j) ? 1.0 : 0.0;
+    for (int k = 0; k < n; k++) {                      // P and L, in the factorisation's order
+        const int p = __ldg(piv + k);
+        if (p != k) {
+            const double t = ysm[k * 32 + lane];
+            ysm[k * 32 + lane] = ysm[p * 32 + lane];
+            ysm[p * 32 + lane] = t;
+        }
+        const double yk = ysm[k * 32 + lane];
+        const int rlast = min(n - 1, k + kl);
+        for (int r = k + 1; r <= rlast; r++) {
+            const double l = __ldg(M + (long long)r * n + k);
+            if (abs_bits(l) != 0) ysm[r * 32 + lane] -= l * yk;
+        }
+    }
+    const int ur = kl + ku;
+    for (int i = n - 1; i >= 0; i--) {                 // U
+        double s = ysm[i * 32 + lane];
+        const int clast = min(n - 1, i + ur);
+        for (int c = i + 1; c <= clast; c++) {
+            const double u = __ldg(M + (long long)i * n + c);
+            if (abs_bits(u) != 0) s -= u * ysm[c * 32 + lane];
+        }
+        ysm[i * 32 + lane] = s * __ldg(dinv + i);
+    }
+    if (j < n)
+        for (int i = 0; i < n; i++) {
+            const double v = ysm[i * 32 + lane];
+            Minv[(long long)i * n + j] = v;
+            if (Minv32) Minv32[(long long)i * n + j] = (float)v;
+        }
+}
+
+__global__ void __launch_bounds__(32) k_band_inv_cols_warp(const double *__restrict__ M, const int *__restrict__ piv,
+                                                           const double *__restrict__ dinv, int n, int kl, int ku,
+                                                           double *__restrict__ Minv, float *__restrict__ Minv32) {
+    band_inv_cols_warp_block(M, piv, dinv, n, kl, ku, Minv, Minv32, blockIdx.x);
 }
 
 // Coarsest inverse for kBandSmemMax < n <= 1024 in three kernels that exploit

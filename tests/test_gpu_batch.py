@@ -157,3 +157,52 @@ def test_batch_rejects_mismatched_options(torch_cuda):
     assert e.value.status == MG_ERR_INVALID_ARG
     s1.close()
     s2.close()
+
+
+@pytest.mark.parametrize("precision,which", [("fp64", "2d"), ("mixed", "2d"), ("mixed", "3d")])
+def test_batched_set_coeffs_equals_per_handle(torch_cuda, precision, which):
+    """Coefficient set-up of all problems in one set of launches gives the
+    hierarchy the per-handle set-up gives: same cycles, same results."""
+    torch = torch_cuda
+    from paper_2206_11294_gb300.binding import Batch, Solver
+    probs = _problems_2d() if which == "2d" else _problems_3d()
+    kw = dict(precision=precision, rtol=1e-10, max_cycles=60)
+    ref = _solvers(probs, **kw)
+    xs_ref = []
+    for s, p in zip(ref, probs):
+        x = p.x0.copy()
+        s.solve(p.b, x)
+        xs_ref.append(x)
+    fresh = [Solver(p.grid, **kw) for p in probs]
+    b = Batch(fresh)
+    T = lambda a: torch.from_numpy(a).cuda()
+    b.set_coeffs([T(p.lam) for p in probs], [[T(f) for f in p.fa] for p in probs],
+                 [[T(f) for f in p.fk] for p in probs])
+    xs = [p.x0.copy() for p in probs]
+    st = b.solve([p.b for p in probs], xs)
+    for q, p in enumerate(probs):
+        assert rel_dev(xs[q], xs_ref[q], p.x0) <= 1e-13, q
+    # host-array intake through the batch as well
+    b.set_coeffs([p.lam for p in probs], [p.fa for p in probs], [p.fk for p in probs])
+    xs2 = [p.x0.copy() for p in probs]
+    b.solve([p.b for p in probs], xs2)
+    for q in range(len(probs)):
+        assert np.array_equal(xs2[q], xs[q]), q
+    b.close()
+    for s in ref + fresh:
+        s.close()
+
+
+def test_batched_set_coeffs_names_bad_problem(torch_cuda):
+    from paper_2206_11294_gb300.binding import Batch, MgError, MG_ERR_INVALID_COEFF, Solver
+    probs = _problems_2d()[:4]
+    solvers = [Solver(p.grid) for p in probs]
+    b = Batch(solvers)
+    lams = [p.lam.copy() for p in probs]
+    lams[2][7, 1] = np.inf
+    with pytest.raises(MgError) as e:
+        b.set_coeffs(lams, [p.fa for p in probs], [p.fk for p in probs])
+    assert e.value.status == MG_ERR_INVALID_COEFF and "problem 2" in str(e.value)
+    b.close()
+    for s in solvers:
+        s.close()
