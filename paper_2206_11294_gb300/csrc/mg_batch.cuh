@@ -257,16 +257,17 @@ __global__ void __launch_bounds__(kBatchThreads) kb_coarse_assemble(const BCoars
 
 // Coarsest inverses of the problems listed in ids (nc <= kBandSmemMax): the
 // single-warp LU, one block per problem; then the columns, one warp per 32.
-__global__ void __launch_bounds__(32) kb_band_lu_warp(const BCoarse *__restrict__ co, const int *__restrict__ ids) {
+__global__ void __launch_bounds__(kLUThreads) kb_band_lu_warp(const BCoarse *__restrict__ co,
+                                                               const int *__restrict__ ids) {
     const BCoarse &C = co[ids[blockIdx.x]];
     band_lu_warp_block(C.M, C.nc, C.kl, C.kl, C.piv, C.dinv, C.err);
 }
 
-__global__ void __launch_bounds__(32) kb_band_inv_cols_warp(const BCoarse *__restrict__ co,
-                                                            const int *__restrict__ ids) {
+__global__ void __launch_bounds__(32 * kInvRows) kb_band_inv_cols_warp(const BCoarse *__restrict__ co,
+                                                                      const int *__restrict__ ids) {
     const BCoarse &C = co[ids[blockIdx.y]];
     if ((int)blockIdx.x * 32 >= C.nc) return;
-    band_inv_cols_warp_block(C.M, C.piv, C.dinv, C.nc, C.kl, C.kl, C.Minv, C.Minv32, blockIdx.x);
+    band_inv_cols_warp_block(C.M, C.piv, C.dinv, C.nc, C.kl, C.kl, C.Minv, C.Minv32, blockIdx.x, C.err);
 }
 
 // Finest-level right-hand sides (and initial guesses) of all problems.
@@ -921,9 +922,9 @@ mg_status mg_batch_set_coeffs(mg_batch *b, const double *const *lambda, const do
     if (b->n_inv_smem > 0) {
         CK(cudaFuncSetAttribute(kb_band_lu_warp, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)b->inv_smem_bytes));
-        kb_band_lu_warp<<<b->n_inv_smem, 32, b->inv_smem_bytes, s>>>(b->co, b->inv_ids);
-        kb_band_inv_cols_warp<<<dim3((b->max_nc_small + 31) / 32, b->n_inv_smem), 32,
-                                sizeof(double) * 32 * (size_t)b->max_nc_small, s>>>(b->co, b->inv_ids);
+        kb_band_lu_warp<<<b->n_inv_smem, kLUThreads, b->inv_smem_bytes, s>>>(b->co, b->inv_ids);
+        kb_band_inv_cols_warp<<<dim3((b->max_nc_small + 31) / 32, b->n_inv_smem), dim3(32, kInvRows),
+                                sizeof(double) * 32 * (size_t)(b->max_nc_small + kInvRows), s>>>(b->co, b->inv_ids);
         b->launches += 2;
     }
     for (int p : b->big_coarse) {           // medium coarsest levels: the banded three-kernel path
@@ -932,7 +933,8 @@ mg_status mg_batch_set_coeffs(mg_batch *b, const double *const *lambda, const do
         const int off = dim == 3 ? c.n[0] * c.n[1] : c.n[0];
         const int kl = std::min(h->nc - 1, 2 * off + 1);
         k_band_lu<<<1, dim3(32, 32, 1), 0, s>>>(h->Mtmp, h->nc, kl, kl, h->piv, h->dinv, h->err_d);
-        k_band_inv_cols<<<(h->nc + 127) / 128, 128, 0, s>>>(h->Mtmp, h->piv, h->dinv, h->nc, kl, kl, h->Mwork);
+        k_band_inv_cols<<<(h->nc + 127) / 128, 128, 0, s>>>(h->Mtmp, h->piv, h->dinv, h->nc, kl, kl, h->Mwork,
+                                                            h->err_d);
         k_transpose<<<lin_blocks((long long)h->nc * h->nc), 256, 0, s>>>(h->Mwork, h->Minv, h->nc);
         b->launches += 3;
         if (h->opt.precision == MG_MIXED) {

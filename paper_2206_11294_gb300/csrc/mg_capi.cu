@@ -591,12 +591,13 @@ mg_status setup_hierarchy(mg_handle *h, const double *lam, const double *const f
     if (h->nc <= kBandSmemMax) {
         const size_t smem_lu = sizeof(double) * (size_t)h->nc * h->nc;
         CK(cudaFuncSetAttribute(k_band_lu_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_lu));
-        k_band_lu_warp<<<1, 32, smem_lu, s>>>(h->Mtmp, h->nc, kl, kl, h->piv, h->dinv, h->err_d);
-        k_band_inv_cols_warp<<<(h->nc + 31) / 32, 32, sizeof(double) * 32 * (size_t)h->nc, s>>>(
-            h->Mtmp, h->piv, h->dinv, h->nc, kl, kl, h->Minv, mixed ? h->Minv32 : nullptr);
+        k_band_lu_warp<<<1, kLUThreads, smem_lu, s>>>(h->Mtmp, h->nc, kl, kl, h->piv, h->dinv, h->err_d);
+        k_band_inv_cols_warp<<<(h->nc + 31) / 32, dim3(32, kInvRows), sizeof(double) * 32 * (size_t)(h->nc + kInvRows), s>>>(
+            h->Mtmp, h->piv, h->dinv, h->nc, kl, kl, h->Minv, mixed ? h->Minv32 : nullptr, h->err_d);
     } else {
         k_band_lu<<<1, dim3(32, 32, 1), 0, s>>>(h->Mtmp, h->nc, kl, kl, h->piv, h->dinv, h->err_d);
-        k_band_inv_cols<<<(h->nc + 127) / 128, 128, 0, s>>>(h->Mtmp, h->piv, h->dinv, h->nc, kl, kl, h->Mwork);
+        k_band_inv_cols<<<(h->nc + 127) / 128, 128, 0, s>>>(h->Mtmp, h->piv, h->dinv, h->nc, kl, kl, h->Mwork,
+                                                            h->err_d);
         k_transpose<<<lin_blocks((long long)h->nc * h->nc), 256, 0, s>>>(h->Mwork, h->Minv, h->nc);
     }
     CK(cudaGetLastError());

@@ -765,125 +765,170 @@ __global__ void k_coarse_assemble(int n0, int n1, int n2, const double2 *__restr
 }
 
 // Coarsest inverse for n <= kBandSmemMax in two kernels.  GB300's FP64 pipe
-// issues one warp instruction per 16 clocks per SM, so the work is arranged so
-// that every FP64 warp instruction does 32 useful operations where it can:
+// issues one warp instruction per 16 clocks per SM and single chains of FP64
+// work are latency-bound, so both kernels spread each step over a block:
 //
-// k_band_lu_warp: one warp, the matrix in shared memory.  The banded LU with
+// k_band_lu_warp: one block, the matrix in shared memory.  The banded LU with
 //   partial pivoting of k_band_lu below (the pivot chosen by comparing |a| as
 //   integers: the bit patterns of non-negative doubles order like the values,
 //   lowest row on ties), factors written back to M, piv[k], dinv[k] = 1/u_kk.
-// k_band_inv_cols_warp: one warp per block, one column j of the inverse per
-//   lane: L U x = P e_j with the vectors in shared memory (column-interleaved)
-//   and the factors read as warp-wide broadcasts; writes Minv (and Minv32).
+// k_band_inv_cols_warp: one block per 32 columns, one column j of the inverse
+//   per lane and row groups on threadIdx.y: L U x = P e_j with the vectors in
+//   shared memory (column-interleaved) and the factors read as broadcasts;
+//   writes Minv (and Minv32).
 constexpr int kBandSmemMax = 128;
 
 __device__ __forceinline__ long long abs_bits(double v) {
     return __double_as_longlong(v) & 0x7fffffffffffffffLL;
 }
 
+// One block of kLUThreads threads, the matrix in shared memory.
+constexpr int kLUThreads = 256;
+
 __device__ __forceinline__ void band_lu_warp_block(double *__restrict__ M, int n, int kl, int ku,
                                                    int *__restrict__ piv, double *__restrict__ dinv,
                                                    int *__restrict__ err) {
     extern __shared__ double a[];
-    const int lane = threadIdx.x;
-    for (int q = lane; q < n * n; q += 32) a[q] = M[q];
-    __syncwarp();
+    __shared__ int prow, bad;
+    __shared__ double pinv;
+    const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+    const int nthr = blockDim.x * blockDim.y;
+    const int lane = tid & 31, warp = tid >> 5;
+    for (int q = tid; q < n * n; q += nthr) a[q] = M[q];
+    if (tid == 0) bad = 0;
+    __syncthreads();
     const int ur = kl + ku;
     const long long kInfBits = 0x7ff0000000000000LL;
-    for (int k = 0; k < n; k++) {
+    int k = 0;
+    for (; k < n; k++) {
         const int rlast = min(n - 1, k + kl), clast = min(n - 1, k + ur);
-        long long best = -1;
-        int br = k;
-        for (int r = k + lane; r <= rlast; r += 32) {
-            const long long v = abs_bits(a[r * n + k]);
-            if (v > best) { best = v; br = r; }
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-            const long long ov = __shfl_xor_sync(0xffffffffu, best, o);
-            const int orr = __shfl_xor_sync(0xffffffffu, br, o);
-            if (ov > best || (ov == best && orr < br)) { best = ov; br = orr; }
-        }
-        if (best <= 0 || best >= kInfBits) {           // zero, infinite or NaN pivot
-            if (lane == 0) atomicOr(err, 4);
-            return;
-        }
-        if (br != k)
-            for (int c = k + lane; c <= clast; c += 32) {
-                const double t = a[k * n + c];
-                a[k * n + c] = a[br * n + c];
-                a[br * n + c] = t;
+        if (warp == 0) {
+            long long best = -1;
+            int br = k;
+            for (int r = k + lane; r <= rlast; r += 32) {
+                const long long v = abs_bits(a[r * n + k]);
+                if (v > best) { best = v; br = r; }
             }
-        __syncwarp();
-        double ip = 0.0;
-        if (lane == 0) {
-            ip = 1.0 / a[k * n + k];
-            piv[k] = br;
-            dinv[k] = ip;
+            for (int o = 16; o > 0; o >>= 1) {
+                const long long ov = __shfl_xor_sync(0xffffffffu, best, o);
+                const int orr = __shfl_xor_sync(0xffffffffu, br, o);
+                if (ov > best || (ov == best && orr < br)) { best = ov; br = orr; }
+            }
+            if (lane == 0) {
+                if (best <= 0 || best >= kInfBits) bad = 1;   // zero, infinite or NaN pivot
+                else {
+                    prow = br;
+                    piv[k] = br;
+                    pinv = 1.0 / a[br * n + k];
+                    dinv[k] = pinv;
+                }
+            }
         }
-        ip = __shfl_sync(0xffffffffu, ip, 0);
-        for (int r = k + 1 + lane; r <= rlast; r += 32) a[r * n + k] *= ip;
-        __syncwarp();
-        for (int r = k + 1; r <= rlast; r++) {
+        __syncthreads();
+        if (bad) break;
+        const int p = prow;
+        if (p != k)
+            for (int c = k + tid; c <= clast; c += nthr) {
+                const double t = a[k * n + c];
+                a[k * n + c] = a[p * n + c];
+                a[p * n + c] = t;
+            }
+        __syncthreads();
+        const double ip = pinv;
+        for (int r = k + 1 + tid; r <= rlast; r += nthr) a[r * n + k] *= ip;
+        __syncthreads();
+        const int w = clast - k, rows = rlast - k;
+        for (int q = tid; q < rows * w; q += nthr) {
+            const int r = k + 1 + q / w, c = k + 1 + q % w;
             const double l = a[r * n + k];
-            if (abs_bits(l) == 0) continue;
-            for (int c = k + 1 + lane; c <= clast; c += 32) a[r * n + c] -= l * a[k * n + c];
+            if (abs_bits(l) != 0) a[r * n + c] -= l * a[k * n + c];
         }
-        __syncwarp();
+        __syncthreads();
     }
-    for (int q = lane; q < n * n; q += 32) M[q] = a[q];
+    if (bad) {
+        // leave an identity permutation behind so that no later reader
+        // indexes out of range, then report
+        for (int q = k + tid; q < n; q += nthr) {
+            piv[q] = q;
+            dinv[q] = 0.0;
+        }
+        if (tid == 0) atomicOr(err, 4);
+        return;
+    }
+    for (int q = tid; q < n * n; q += nthr) M[q] = a[q];
 }
 
-__global__ void __launch_bounds__(32) k_band_lu_warp(double *__restrict__ M, int n, int kl, int ku,
-                                                     int *__restrict__ piv, double *__restrict__ dinv,
-                                                     int *__restrict__ err) {
+__global__ void __launch_bounds__(kLUThreads) k_band_lu_warp(double *__restrict__ M, int n, int kl, int ku,
+                                                             int *__restrict__ piv, double *__restrict__ dinv,
+                                                             int *__restrict__ err) {
     band_lu_warp_block(M, n, kl, ku, piv, dinv, err);
 }
 
-// Columns 32 * col_block + lane of the inverse from the factors of k_band_lu_warp.
+// Columns 32 * col_block + lane of the inverse from the factors of
+// k_band_lu_warp, one column per lane and kInvRows row groups (threadIdx.y)
+// per column; does nothing when the factorisation reported a zero pivot.
+constexpr int kInvRows = 8;
+
 __device__ __forceinline__ void band_inv_cols_warp_block(const double *__restrict__ M, const int *__restrict__ piv,
                                                          const double *__restrict__ dinv, int n, int kl, int ku,
                                                          double *__restrict__ Minv, float *__restrict__ Minv32,
-                                                         int col_block) {
-    extern __shared__ double ysm[];                    // y[i][lane], n x 32
-    const int lane = threadIdx.x;
+                                                         int col_block, const int *__restrict__ err) {
+    extern __shared__ double ysm[];                    // y[i][lane], n x 32, then partial sums kInvRows x 32
+    if (*(volatile const int *)err & 4) return;
+    double *part = ysm + n * 32;
+    const int lane = threadIdx.x, ty = threadIdx.y;
     const int j = col_block * 32 + lane;
-    for (int i = 0; i < n; i++) ysm[i * 32 + lane] = (i == j) ? 1.0 : 0.0;
+    for (int i = ty; i < n; i += kInvRows) ysm[i * 32 + lane] = (i == j) ? 1.0 : 0.0;
+    __syncthreads();
     for (int k = 0; k < n; k++) {                      // P and L, in the factorisation's order
-        const int p = __ldg(piv + k);
-        if (p != k) {
+        const int p = min(max(__ldg(piv + k), k), n - 1);
+        if (p != k && ty == 0) {
             const double t = ysm[k * 32 + lane];
             ysm[k * 32 + lane] = ysm[p * 32 + lane];
             ysm[p * 32 + lane] = t;
         }
+        __syncthreads();
         const double yk = ysm[k * 32 + lane];
         const int rlast = min(n - 1, k + kl);
-        for (int r = k + 1; r <= rlast; r++) {
+        for (int r = k + 1 + ty; r <= rlast; r += kInvRows) {
             const double l = __ldg(M + (long long)r * n + k);
             if (abs_bits(l) != 0) ysm[r * 32 + lane] -= l * yk;
         }
+        __syncthreads();
     }
     const int ur = kl + ku;
     for (int i = n - 1; i >= 0; i--) {                 // U
-        double s = ysm[i * 32 + lane];
         const int clast = min(n - 1, i + ur);
-        for (int c = i + 1; c <= clast; c++) {
+        double s = 0.0;
+        for (int c = i + 1 + ty; c <= clast; c += kInvRows) {
             const double u = __ldg(M + (long long)i * n + c);
-            if (abs_bits(u) != 0) s -= u * ysm[c * 32 + lane];
+            if (abs_bits(u) != 0) s += u * ysm[c * 32 + lane];
         }
-        ysm[i * 32 + lane] = s * __ldg(dinv + i);
+        part[ty * 32 + lane] = s;
+        __syncthreads();
+        if (ty == 0) {
+            double t = 0.0;
+#pragma unroll
+            for (int q = 0; q < kInvRows; q++) t += part[q * 32 + lane];
+            ysm[i * 32 + lane] = (ysm[i * 32 + lane] - t) * __ldg(dinv + i);
+        }
+        __syncthreads();
     }
     if (j < n)
-        for (int i = 0; i < n; i++) {
+        for (int i = ty; i < n; i += kInvRows) {
             const double v = ysm[i * 32 + lane];
             Minv[(long long)i * n + j] = v;
             if (Minv32) Minv32[(long long)i * n + j] = (float)v;
         }
 }
 
-__global__ void __launch_bounds__(32) k_band_inv_cols_warp(const double *__restrict__ M, const int *__restrict__ piv,
-                                                           const double *__restrict__ dinv, int n, int kl, int ku,
-                                                           double *__restrict__ Minv, float *__restrict__ Minv32) {
-    band_inv_cols_warp_block(M, piv, dinv, n, kl, ku, Minv, Minv32, blockIdx.x);
+__global__ void __launch_bounds__(32 * kInvRows) k_band_inv_cols_warp(const double *__restrict__ M,
+                                                                      const int *__restrict__ piv,
+                                                                      const double *__restrict__ dinv, int n, int kl,
+                                                                      int ku, double *__restrict__ Minv,
+                                                                      float *__restrict__ Minv32,
+                                                                      const int *__restrict__ err) {
+    band_inv_cols_warp_block(M, piv, dinv, n, kl, ku, Minv, Minv32, blockIdx.x, err);
 }
 
 // Coarsest inverse for kBandSmemMax < n <= 1024 in three kernels that exploit
@@ -912,7 +957,8 @@ __global__ void __launch_bounds__(1024) k_band_lu(double *__restrict__ M, int n,
     const int ur = kl + ku;                      // reach of U after pivoting
     if (tid == 0) bad = 0;
     __syncthreads();
-    for (int k = 0; k < n; k++) {
+    int k = 0;
+    for (; k < n; k++) {
         const int rlast = min(n - 1, k + kl), clast = min(n - 1, k + ur);
         if (ty == 0) {
             double best = -1.0;
@@ -956,17 +1002,25 @@ __global__ void __launch_bounds__(1024) k_band_lu(double *__restrict__ M, int n,
         }
         __syncthreads();
     }
-    if (bad && tid == 0) atomicOr(err, 4);
+    if (bad) {
+        // identity permutation from the failing column on, then report
+        for (int q = k + tid; q < n; q += 1024) {
+            piv[q] = q;
+            dinv[q] = 0.0;
+        }
+        if (tid == 0) atomicOr(err, 4);
+    }
 }
 
 __global__ void k_band_inv_cols(const double *__restrict__ M, const int *__restrict__ piv,
-                                const double *__restrict__ dinv, int n, int kl, int ku, double *__restrict__ W) {
+                                const double *__restrict__ dinv, int n, int kl, int ku, double *__restrict__ W,
+                                const int *__restrict__ err) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= n) return;
+    if (j >= n || (*(volatile const int *)err & 4)) return;
     double *y = W + (long long)j * n;
     for (int i = 0; i < n; i++) y[i] = (i == j) ? 1.0 : 0.0;
     for (int k = 0; k < n; k++) {              // P and L, in the order the factorisation applied them
-        const int p = piv[k];
+        const int p = min(max(piv[k], k), n - 1);
         if (p != k) {
             const double t = y[k];
             y[k] = y[p];
