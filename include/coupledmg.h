@@ -118,7 +118,10 @@ MG_API mg_status mg_create(const mg_grid *grid, const mg_options *opt, void *wor
  * a < dim.  Builds the whole hierarchy on the device: the per-cell 2x2 blocks
  * of Eqs. 27-28, coarse coefficients (area-weighted faces, volume-weighted
  * l1..l4) and the exact coarsest solve.  MG_ERR_INVALID_COEFF if an input is
- * not finite or a local block is singular. */
+ * not finite or a local block is singular.  The inverse of the coarsest
+ * matrix is still being computed (on a private stream) when this returns;
+ * the next mg_solve waits for it and reports a singular coarsest matrix as
+ * MG_ERR_INVALID_COEFF.  The caller's arrays are no longer read on return. */
 MG_API mg_status mg_set_coeffs(mg_handle *h, const double *lambda, const double *const face_alpha[3],
                         const double *const face_k[3], int on_device);
 

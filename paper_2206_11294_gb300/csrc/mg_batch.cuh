@@ -763,6 +763,7 @@ mg_status mg_batch_solve(mg_batch *b, const double *const *rhs, double *const *x
     }
     DeviceGuard dg(b->device);
     cudaStream_t s = b->stream;
+    for (int p = 0; p < b->count; p++) CK(cudaStreamWaitEvent(s, b->h[p]->ev_inv, 0));   // per-handle set-ups
     {
         BIo *io = reinterpret_cast<BIo *>(b->host_io);
         for (int p = 0; p < b->count; p++) {
@@ -873,6 +874,7 @@ mg_status mg_batch_set_coeffs(mg_batch *b, const double *const *lambda, const do
     }
     DeviceGuard dg(b->device);
     cudaStream_t s = b->stream;
+    for (int p = 0; p < b->count; p++) CK(cudaStreamWaitEvent(s, b->h[p]->ev_inv, 0));   // in-flight inverses
     SetupIn *in = reinterpret_cast<SetupIn *>(b->host_io);
     for (int p = 0; p < b->count; p++) {
         mg_handle *h = b->h[p];

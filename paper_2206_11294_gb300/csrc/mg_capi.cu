@@ -72,6 +72,10 @@ struct mg_handle {
     int device;
     cudaStream_t stream;   // caller's stream: all work runs here
     cudaStream_t cap;      // private stream used only to capture graphs
+    cudaStream_t aux;      // private stream: the coarsest inverse, overlapping the solve's start
+    cudaEvent_t ev_asm;    // coarsest matrix assembled (main stream)
+    cudaEvent_t ev_inv;    // coarsest inverse ready (aux stream); cycle graphs wait on it
+    int *errh;             // pinned host copy of err_d
     int nlev;
     LevelBuf L[kMaxLevels];
     char *arena;
@@ -322,6 +326,8 @@ void enqueue_vcycle(const mg_handle *h, cudaStream_t s, int l) {
     const LevelBuf &lb = h->L[l];
     if (l == h->nlev - 1) {
         const Level<R> v = view<R>(lb);
+        // the coarsest inverse is computed on the aux stream after each set-up
+        cudaStreamWaitEvent(s, h->ev_inv, cudaEventWaitExternal);
         const int threads = 256;
         const unsigned blocks = (unsigned)((h->nc * 32LL + threads - 1) / threads);
         k_coarse_matvec<R><<<blocks, threads, 0, s>>>(coarse_inverse<R>(h), reinterpret_cast<const R *>(v.b),
@@ -528,6 +534,8 @@ mg_status setup_hierarchy(mg_handle *h, const double *lam, const double *const f
     cudaStream_t s = h->stream;
     const bool mixed = h->opt.precision == MG_MIXED;
     LevelBuf &f = h->L[0];
+    // the previous set-up's coarsest inverse must be done before anything is overwritten
+    CK(cudaStreamWaitEvent(s, h->ev_inv, 0));
     CK(cudaMemsetAsync(h->err_d, 0, sizeof(int), s));
     const double *lam_d = lam;
     const double *fad[3] = {nullptr, nullptr, nullptr}, *fkd[3] = {nullptr, nullptr, nullptr};
@@ -580,10 +588,25 @@ mg_status setup_hierarchy(mg_handle *h, const double *lam, const double *const f
         CK(cudaGetLastError());
         hl *= 2.0;
     }
+    // flags 1 and 2 come from the level kernels: read them before the coarsest
+    // matrix is assembled, then leave the assembly and the inverse running
+    CK(cudaMemcpyAsync(h->errh, h->err_d, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const int err = *h->errh;
+    if (err & 1) return fail(MG_ERR_INVALID_COEFF, "non-finite coefficient in lambda or the face arrays");
+    if (err & 2) return fail(MG_ERR_INVALID_COEFF, "a local 2x2 block is singular or not finite");
     const LevelBuf &c = h->L[h->nlev - 1];
     CK(cudaMemsetAsync(h->Mtmp, 0, sizeof(double) * h->nc * h->nc, s));
     k_coarse_assemble<DIM><<<lin_blocks(c.N), 256, 0, s>>>(c.n[0], c.n[1], c.n[2], c.G[0], c.G[1],
                                                            DIM == 3 ? c.G[2] : nullptr, c.D, c.l4, h->Mtmp);
+    CK(cudaGetLastError());
+    // The coarsest inverse runs on the aux stream, overlapping the caller's
+    // next work and the start of the next solve (whose cycles wait for it
+    // before their coarsest solve).  A singular coarsest matrix is reported by
+    // mg_solve.
+    CK(cudaEventRecord(h->ev_asm, s));
+    CK(cudaStreamWaitEvent(h->aux, h->ev_asm, 0));
+    cudaStream_t a = h->aux;
     // band of the coarsest matrix: the farthest neighbour cell is n0 (2D)
     // or n0*n1 (3D) cells away, two unknowns per cell
     const int off = DIM == 3 ? c.n[0] * c.n[1] : c.n[0];
@@ -591,27 +614,22 @@ mg_status setup_hierarchy(mg_handle *h, const double *lam, const double *const f
     if (h->nc <= kBandSmemMax) {
         const size_t smem_lu = sizeof(double) * (size_t)h->nc * h->nc;
         CK(cudaFuncSetAttribute(k_band_lu_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_lu));
-        k_band_lu_warp<<<1, kLUThreads, smem_lu, s>>>(h->Mtmp, h->nc, kl, kl, h->piv, h->dinv, h->err_d);
-        k_band_inv_cols_warp<<<(h->nc + 31) / 32, dim3(32, kInvRows), sizeof(double) * 32 * (size_t)(h->nc + kInvRows), s>>>(
-            h->Mtmp, h->piv, h->dinv, h->nc, kl, kl, h->Minv, mixed ? h->Minv32 : nullptr, h->err_d);
+        k_band_lu_warp<<<1, kLUThreads, smem_lu, a>>>(h->Mtmp, h->nc, kl, kl, h->piv, h->dinv, h->err_d);
+        k_band_inv_cols_warp<<<(h->nc + 31) / 32, dim3(32, kInvRows), sizeof(double) * 32 * (size_t)(h->nc + kInvRows),
+                               a>>>(h->Mtmp, h->piv, h->dinv, h->nc, kl, kl, h->Minv, mixed ? h->Minv32 : nullptr,
+                                    h->err_d);
     } else {
-        k_band_lu<<<1, dim3(32, 32, 1), 0, s>>>(h->Mtmp, h->nc, kl, kl, h->piv, h->dinv, h->err_d);
-        k_band_inv_cols<<<(h->nc + 127) / 128, 128, 0, s>>>(h->Mtmp, h->piv, h->dinv, h->nc, kl, kl, h->Mwork,
+        k_band_lu<<<1, dim3(32, 32, 1), 0, a>>>(h->Mtmp, h->nc, kl, kl, h->piv, h->dinv, h->err_d);
+        k_band_inv_cols<<<(h->nc + 127) / 128, 128, 0, a>>>(h->Mtmp, h->piv, h->dinv, h->nc, kl, kl, h->Mwork,
                                                             h->err_d);
-        k_transpose<<<lin_blocks((long long)h->nc * h->nc), 256, 0, s>>>(h->Mwork, h->Minv, h->nc);
+        k_transpose<<<lin_blocks((long long)h->nc * h->nc), 256, 0, a>>>(h->Mwork, h->Minv, h->nc);
+        if (mixed)
+            k_to_f32<<<lin_blocks((long long)h->nc * h->nc), 256, 0, a>>>(h->Minv, h->Minv32,
+                                                                         (long long)h->nc * h->nc);
     }
     CK(cudaGetLastError());
-    if (mixed && h->nc > kBandSmemMax) {
-        k_to_f32<<<lin_blocks((long long)h->nc * h->nc), 256, 0, s>>>(h->Minv, h->Minv32, (long long)h->nc * h->nc);
-        CK(cudaGetLastError());
-    }
+    CK(cudaEventRecord(h->ev_inv, a));
     counted(h, h->nlev + 1 + (h->nc <= kBandSmemMax ? 2 : 4));
-    int err = 0;
-    CK(cudaMemcpyAsync(&err, h->err_d, sizeof(int), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    if (err & 1) return fail(MG_ERR_INVALID_COEFF, "non-finite coefficient in lambda or the face arrays");
-    if (err & 2) return fail(MG_ERR_INVALID_COEFF, "a local 2x2 block is singular or not finite");
-    if (err & 4) return fail(MG_ERR_INVALID_COEFF, "the coarsest-level matrix is singular");
     return MG_OK;
 }
 
@@ -755,6 +773,10 @@ mg_status mg_create(const mg_grid *grid, const mg_options *opt, void *workspace,
     size_t dummy;
     plan(h, aligned, &dummy);
     if (cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_asm, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_inv, cudaEventDisableTiming) != cudaSuccess ||
+        cudaMallocHost(&h->errh, sizeof(int)) != cudaSuccess ||
         cudaMallocHost(&h->norms_h, 8 * sizeof(double)) != cudaSuccess ||
         cudaMemsetAsync(h->ticket, 0, sizeof(unsigned int), h->stream) != cudaSuccess ||
         cudaStreamSynchronize(h->stream) != cudaSuccess) {
@@ -802,7 +824,10 @@ mg_status mg_solve(mg_handle *h, const double *rhs, double *x, int on_device, mg
     else st = dim == 2 ? solve_mixed<2>(h, &s) : solve_mixed<3>(h, &s);
     if (st) return st;
     if ((st = x_out(h, x, on_device))) return st;
+    CK(cudaStreamWaitEvent(h->stream, h->ev_inv, 0));
+    CK(cudaMemcpyAsync(h->errh, h->err_d, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
+    if (*h->errh & 4) return fail(MG_ERR_INVALID_COEFF, "the coarsest-level matrix is singular");
     s.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     if (stats) *stats = s;
     if (s.status != MG_OK) {
@@ -921,7 +946,12 @@ mg_status mg_destroy(mg_handle *h) {
     if (h->stream) cudaStreamSynchronize(h->stream);
     if (h->g64) cudaGraphExecDestroy(h->g64);
     if (h->g32) cudaGraphExecDestroy(h->g32);
+    if (h->aux) cudaStreamSynchronize(h->aux);
     if (h->cap) cudaStreamDestroy(h->cap);
+    if (h->aux) cudaStreamDestroy(h->aux);
+    if (h->ev_asm) cudaEventDestroy(h->ev_asm);
+    if (h->ev_inv) cudaEventDestroy(h->ev_inv);
+    if (h->errh) cudaFreeHost(h->errh);
     for (int q = 0; q < 4; q++)
         if (h->ev[q]) cudaEventDestroy(h->ev[q]);
     if (h->norms_h) cudaFreeHost(h->norms_h);
