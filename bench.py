@@ -36,14 +36,14 @@ METRIC = "coupled p-T MG Mcell-Vcycles/s & solves/s at 1e-10 resid; HBM %peak; p
 UNIT = "Mcell-Vcycles/s"
 FALLBACK_HBM_GBS = 6800.0
 L2_FLUSH_BYTES = 256 << 20
-# algorithmic bytes per finest cell of one full red-black sweep:
-# read x 16 + b 16 + Dinv 32 + faces (2D 32, 3D 48) + l4 8, write x 16 (FP64);
-# half of that for the FP32 cycles of mixed precision
-SWEEP_BYTES_PER_CELL = {("fp64", 2): 120.0, ("fp64", 3): 136.0, ("mixed", 2): 60.0, ("mixed", 3): 68.0}
-# FP64 instructions per cell update of a sweep (each cell once per sweep):
-# neighbour products 2*2*dim (first a multiply, the rest FMAs), l4 * sT (1),
-# b - offdiag (2), the 2x2 Dinv product (4)
-SWEEP_FP64_INST_PER_CELL = {2: 15.0, 3: 19.0}
+# algorithmic bytes per finest cell of one full red-black sweep: read x 16 +
+# bt 16 (Dinv b) + W 32 (the cell's 2x2 update matrix) + faces (2D 32, 3D 48),
+# write x 16 (FP64); half of that for the FP32 cycles of mixed precision
+SWEEP_BYTES_PER_CELL = {("fp64", 2): 112.0, ("fp64", 3): 128.0, ("mixed", 2): 56.0, ("mixed", 3): 64.0}
+# FP64 instructions per cell update of a sweep (each cell once per sweep): the
+# two neighbour sums 2*2*dim (first a multiply, the rest FMAs), then
+# x = bt - W (sT, sp) as 4 FMAs
+SWEEP_FP64_INST_PER_CELL = {2: 12.0, 3: 16.0}
 # GB300 FP64 pipe: 1.25 TFLOP/s nominal = 2 FP64 FMA per clock per SM
 # (1.25e12 / (2 * 152 * 2.07e9) = 1.99); 152 SMs at 2.07 GHz
 FP64_INST_PEAK_G = 152 * 2 * 2.07

@@ -398,7 +398,7 @@ __global__ void __launch_bounds__(kBatchThreads) kb_residual64(const BLevel *__r
         const int gx = (L.n0 + kBX - 1) / kBX, gy = (L.n1 + kBY - 1) / kBY;
         int bx, by, bz;
         block_coords(e.y, gx, gy, bx, by, bz);
-        const double2 s = residual64_to32_block<DIM>(L, B.f.b, B.f.x, bx, by, bz);
+        const double2 s = residual64_to32_block<DIM>(L, B.f.b, B.f.bt, B.f.x, bx, by, bz);
         batch_finish(pr[p], st[p], e.y, s, initial, rtol, max_cycles, active_count);
     }
 }

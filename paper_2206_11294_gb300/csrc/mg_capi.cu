@@ -50,12 +50,13 @@ struct LevelBuf {
     double2 *xalt;          // ping-pong partner of x for fused sweeps (2D)
     double2 *G[3];
     dq *S;                  // scaled local terms s [[l1, l2], [0, l3]] (set-up)
-    dq *D, *Dinv;
+    dq *D, *Dinv, *W;
     double *l4;
-    float2 *x32, *b32;
+    double2 *bt;            // Dinv b
+    float2 *x32, *b32, *bt32;
     float2 *xalt32;
     float2 *G32[3];
-    fq *D32, *Dinv32;
+    fq *D32, *Dinv32, *W32;
     float *l4_32;
 };
 
@@ -200,7 +201,9 @@ void plan(mg_handle *h, char *base, size_t *bytes) {
         l.S = P.take<dq>(l.N);
         l.D = P.take<dq>(l.N);
         l.Dinv = P.take<dq>(l.N);
+        l.W = P.take<dq>(l.N);
         l.l4 = P.take<double>(l.N);
+        l.bt = P.take<double2>(l.N);
         if (mixed) {
             l.x32 = P.take<float2>(l.N);
             l.b32 = P.take<float2>(l.N);
@@ -208,7 +211,9 @@ void plan(mg_handle *h, char *base, size_t *bytes) {
             for (int a = 0; a < g.dim; a++) l.G32[a] = P.take<float2>(l.nf[a]);
             l.D32 = P.take<fq>(l.N);
             l.Dinv32 = P.take<fq>(l.N);
+            l.W32 = P.take<fq>(l.N);
             l.l4_32 = P.take<float>(l.N);
+            l.bt32 = P.take<float2>(l.N);
         }
         h->nlev++;
         if (!can_coarsen(n, g.dim, h->opt.coarse_min) || h->nlev == kMaxLevels) break;
@@ -240,11 +245,11 @@ void plan(mg_handle *h, char *base, size_t *bytes) {
 
 template <typename R> Level<R> view(const LevelBuf &l);
 template <> Level<double> view<double>(const LevelBuf &l) {
-    return Level<double>{l.n[0], l.n[1], l.n[2], l.N, l.x, l.b, l.G[0], l.G[1], l.G[2], l.D, l.Dinv, l.l4};
+    return Level<double>{l.n[0], l.n[1], l.n[2], l.N, l.x, l.b, l.G[0], l.G[1], l.G[2], l.D, l.Dinv, l.l4, l.W, l.bt};
 }
 template <> Level<float> view<float>(const LevelBuf &l) {
     return Level<float>{l.n[0], l.n[1], l.n[2], l.N, l.x32, l.b32, l.G32[0], l.G32[1], l.G32[2], l.D32, l.Dinv32,
-                        l.l4_32};
+                        l.l4_32, l.W32, l.bt32};
 }
 
 BcFlags bc_flags(const mg_grid &g) {
@@ -361,7 +366,8 @@ void enqueue_norm(const mg_handle *h, cudaStream_t s) {
 template <int DIM>
 void enqueue_residual_to32(const mg_handle *h, cudaStream_t s) {
     const LevelBuf &f = h->L[0];
-    k_residual64_to32<DIM><<<cell_grid(f, DIM, f.n[0]), kBlock, 0, s>>>(view<double>(f), f.b32, f.x32, h->partial,
+    k_residual64_to32<DIM><<<cell_grid(f, DIM, f.n[0]), kBlock, 0, s>>>(view<double>(f), f.b32, f.bt32, f.x32,
+                                                                         h->partial,
                                                                          h->ticket, h->norms_d);
     counted(h);
 }
@@ -507,10 +513,12 @@ SetupOut setup_out(const LevelBuf &l, bool mixed) {
     o.S = l.S;
     o.D = l.D;
     o.Dinv = l.Dinv;
+    o.W = l.W;
     o.l4 = l.l4;
     if (mixed) {
         o.D32 = l.D32;
         o.Dinv32 = l.Dinv32;
+        o.W32 = l.W32;
         o.l432 = l.l4_32;
     }
     return o;

@@ -32,7 +32,7 @@ __device__ __forceinline__ fq ldgq(const fq *p) {
 // sp = sum of G^p_f p_nb + l4 * sT (the p-row's T-Laplacian term, Eq. 28).
 // Neighbours beyond the grid contribute nothing (homogeneous boundary values;
 // inhomogeneous Dirichlet data are folded into the right-hand side).
-template <typename R, int DIM>
+template <typename R, int DIM, bool WITH_L4 = true>
 __device__ __forceinline__ void offdiag(const Level<R> &L, const typename Vec<R>::v2 *__restrict__ x,
                                         int i, int j, int k, long long c, R &sT, R &sp) {
     using V2 = typename Vec<R>::v2;
@@ -50,13 +50,21 @@ __device__ __forceinline__ void offdiag(const Level<R> &L, const typename Vec<R>
         if (k > 0)        { V2 g = ldg2(L.G2 + c);      V2 u = ldg2(x + c - pl); sT += g.x * u.x; sp += g.y * u.y; }
         if (k < L.n2 - 1) { V2 g = ldg2(L.G2 + c + pl); V2 u = ldg2(x + c + pl); sT += g.x * u.x; sp += g.y * u.y; }
     }
-    sp += __ldg(L.l4 + c) * sT;
+    if (WITH_L4) sp += __ldg(L.l4 + c) * sT;
+}
+
+// Gauss-Seidel update of one cell from its plain neighbour sums.
+template <typename R>
+__device__ __forceinline__ typename Vec<R>::v2 gs_update(const Level<R> &L, long long c, R sT, R sp) {
+    const auto bt = ldg2(L.bt + c);
+    const auto W = ldgq(L.W + c);
+    return mk2<R>(bt.x - W.a * sT - W.b * sp, bt.y - W.c * sT - W.d * sp);
 }
 
 // ---------------------------------------------------------------------------
 // Smoothing: one colour of a red-black block Gauss-Seidel sweep.  Each thread
 // owns one cell of the colour (red: i+j+k even) and solves its two rows for
-// (T_i, p_i):  x_i = Dinv_i (b_i - offdiag_i).
+// (T_i, p_i):  x_i = Dinv_i (b_i - offdiag_i) = bt_i - W_i (sT, sp).
 // Neighbours are of the other colour and are not written by this launch.
 // ---------------------------------------------------------------------------
 // The work of thread block (bx, by, bz) of the launch geometry
@@ -72,11 +80,8 @@ __device__ __forceinline__ void rbgs_colour_block(const Level<R> &L, int colour,
     if (i >= L.n0) return;
     const long long c = cell_id(i, j, k, L.n0, L.n1);
     R sT, sp;
-    offdiag<R, DIM>(L, L.x, i, j, k, c, sT, sp);
-    const V2 bb = ldg2(L.b + c);
-    const auto Di = ldgq(L.Dinv + c);
-    const R rT = bb.x - sT, rp = bb.y - sp;
-    L.x[c] = mk2<R>(Di.a * rT + Di.b * rp, Di.c * rT + Di.d * rp);
+    offdiag<R, DIM, false>(L, L.x, i, j, k, c, sT, sp);
+    L.x[c] = gs_update<R>(L, c, sT, sp);
 }
 
 template <typename R, int DIM>
@@ -109,7 +114,6 @@ __device__ __forceinline__ void offdiag_tile2d(const Level<R> &L, const typename
     const long long f1 = (long long)i + (long long)n0 * j;
     if (j > 0)      { V2 g = ldg2(L.G1 + f1);      V2 u = xs[ly - 1][lx]; sT += g.x * u.x; sp += g.y * u.y; }
     if (j < n1 - 1) { V2 g = ldg2(L.G1 + f1 + n0); V2 u = xs[ly + 1][lx]; sT += g.x * u.x; sp += g.y * u.y; }
-    sp += __ldg(L.l4 + c) * sT;
 }
 
 // Tile (bx, by) of the launch geometry (ceil(n0/64), ceil(n1/16)); shared with
@@ -142,10 +146,7 @@ __device__ __forceinline__ void rbgs_fused2d_block(const Level<R> &L, const type
         const long long c = (long long)gj * n0 + gi;
         R sT, sp;
         offdiag_tile2d<R>(L, xs, lx, ly, gi, gj, c, sT, sp);
-        const V2 bb = ldg2(L.b + c);
-        const auto Di = ldgq(L.Dinv + c);
-        const R rT = bb.x - sT, rp = bb.y - sp;
-        xs[ly][lx] = mk2<R>(Di.a * rT + Di.b * rp, Di.c * rT + Di.d * rp);
+        xs[ly][lx] = gs_update<R>(L, c, sT, sp);
     }
     __syncthreads();
     // black cells of the tile; each thread writes a pair of adjacent cells
@@ -164,10 +165,7 @@ __device__ __forceinline__ void rbgs_fused2d_block(const Level<R> &L, const type
             if ((gi + gj) & 1) {
                 R sT, sp;
                 offdiag_tile2d<R>(L, xs, lx, ly, gi, gj, c, sT, sp);
-                const V2 bb = ldg2(L.b + c);
-                const auto Di = ldgq(L.Dinv + c);
-                const R rT = bb.x - sT, rp = bb.y - sp;
-                v = mk2<R>(Di.a * rT + Di.b * rp, Di.c * rT + Di.d * rp);
+                v = gs_update<R>(L, c, sT, sp);
             }
             xout[c] = v;
         }
@@ -206,7 +204,10 @@ __device__ __forceinline__ void residual_restrict_block(const Level<R> &F, const
     }
     const R w = R(1) / R(1 << DIM);
     const long long cc = cell_id(I, J, K, C.n0, C.n1);
-    C.b[cc] = mk2<R>(aT * w, ap * w);
+    const R bT = aT * w, bp = ap * w;
+    C.b[cc] = mk2<R>(bT, bp);
+    const auto Di = ldgq(C.Dinv + cc);
+    C.bt[cc] = mk2<R>(Di.a * bT + Di.b * bp, Di.c * bT + Di.d * bp);
     C.x[cc] = mk2<R>(R(0), R(0));
 }
 
@@ -358,12 +359,11 @@ __device__ __forceinline__ double2 norm_block(const Level<double> &L, int bx, in
     if (i < L.n0 && j < L.n1) {
         const long long c = cell_id(i, j, k, L.n0, L.n1);
         double sT, sp;
-        offdiag<double, DIM>(L, L.x, i, j, k, c, sT, sp);
-        const double2 bb = ldg2(L.b + c), xx = ldg2(L.x + c);
-        const dq Di = ldgq(L.Dinv + c);
-        const double rT = bb.x - sT, rp = bb.y - sp;
-        const double zT = Di.a * rT + Di.b * rp - xx.x;
-        const double zp = Di.c * rT + Di.d * rp - xx.y;
+        offdiag<double, DIM, false>(L, L.x, i, j, k, c, sT, sp);
+        const double2 xx = ldg2(L.x + c);
+        const double2 u = gs_update<double>(L, c, sT, sp);   // = Dinv (b - offdiag)
+        const double zT = u.x - xx.x;
+        const double zp = u.y - xx.y;
         zT2 = zT * zT;
         zp2 = zp * zp;
     }
@@ -385,7 +385,8 @@ __global__ void __launch_bounds__(kBX * kBY) k_norm_partials(Level<double> L, do
 // the FP32 correction is zeroed, and the norm partials of Dinv r are formed.
 template <int DIM>
 __device__ __forceinline__ double2 residual64_to32_block(const Level<double> &L, float2 *__restrict__ b32,
-                                                         float2 *__restrict__ e32, int bx, int by, int bz) {
+                                                         float2 *__restrict__ bt32, float2 *__restrict__ e32,
+                                                         int bx, int by, int bz) {
     const int i = bx * kBX + threadIdx.x;
     const int j = by * kBY + threadIdx.y;
     const int k = DIM == 3 ? bz : 0;
@@ -404,6 +405,7 @@ __device__ __forceinline__ double2 residual64_to32_block(const Level<double> &L,
         zT2 = zT * zT;
         zp2 = zp * zp;
         b32[c] = make_float2((float)rT, (float)rp);
+        bt32[c] = make_float2((float)zT, (float)zp);     // Dinv r for the FP32 sweeps
         e32[c] = make_float2(0.f, 0.f);
     }
     block_sum2(zT2, zp2);
@@ -412,10 +414,11 @@ __device__ __forceinline__ double2 residual64_to32_block(const Level<double> &L,
 
 template <int DIM>
 __global__ void __launch_bounds__(kBX * kBY) k_residual64_to32(Level<double> L, float2 *__restrict__ b32,
-                                                             float2 *__restrict__ e32, double2 *__restrict__ partial,
+                                                             float2 *__restrict__ bt32, float2 *__restrict__ e32,
+                                                             double2 *__restrict__ partial,
                                                              unsigned int *__restrict__ ticket,
                                                              double *__restrict__ out) {
-    const double2 s = residual64_to32_block<DIM>(L, b32, e32, blockIdx.x, blockIdx.y, blockIdx.z);
+    const double2 s = residual64_to32_block<DIM>(L, b32, bt32, e32, blockIdx.x, blockIdx.y, blockIdx.z);
     if (threadIdx.x == 0 && threadIdx.y == 0)
         partial[blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)] = s;
     finish_norms(partial, gridDim.x * gridDim.y * gridDim.z, ticket, out);
@@ -491,7 +494,10 @@ __device__ __forceinline__ void prep_rhs_block(const Level<double> &L, const dou
     const double2 q = rhs[c];
     double gT, gp;
     boundary_data<DIM>(L, bv, i, j, k, gT, gp);
-    L.b[c] = make_double2(s * q.x - gT, s * q.y - gp);
+    const double bT = s * q.x - gT, bp = s * q.y - gp;
+    L.b[c] = make_double2(bT, bp);
+    const dq Di = ldgq(L.Dinv + c);
+    L.bt[c] = make_double2(Di.a * bT + Di.b * bp, Di.c * bT + Di.d * bp);
     if (xin) L.x[c] = xin[c];
 }
 
@@ -530,10 +536,10 @@ __global__ void __launch_bounds__(kBX * kBY) k_apply_paper(Level<double> L, BcVa
 // ---------------------------------------------------------------------------
 struct SetupOut {                 // one level's outputs
     double2 *G[3];
-    dq *S, *D, *Dinv;
+    dq *S, *D, *Dinv, *W;
     double *l4;
     float2 *G32[3];               // FP32 copies (mixed precision), or NULL
-    fq *D32, *Dinv32;
+    fq *D32, *Dinv32, *W32;
     float *l432;
 };
 
@@ -571,11 +577,14 @@ __device__ __forceinline__ void finish_cell(const SetupOut &o, long long c, cons
     if ((__double_as_longlong(det) & 0x7fffffffffffffffLL) == 0 || !finite_bits(det)) atomicOr(err, 2);
     const double id = 1.0 / det;
     const dq Di{D.d * id, -D.b * id, -D.c * id, D.a * id};
+    const dq Wc{Di.a + Di.b * l4, Di.b, Di.c + Di.d * l4, Di.d};
     o.D[c] = D;
     o.Dinv[c] = Di;
+    o.W[c] = Wc;
     if (o.D32) {
         o.D32[c] = fq{(float)D.a, (float)D.b, (float)D.c, (float)D.d};
         o.Dinv32[c] = fq{(float)Di.a, (float)Di.b, (float)Di.c, (float)Di.d};
+        o.W32[c] = fq{(float)Wc.a, (float)Wc.b, (float)Wc.c, (float)Wc.d};
         o.l432[c] = (float)l4;
     }
 }

@@ -19,6 +19,10 @@
 //             [[s l1 - sum G^T, s l2], [-l4 sum G^T, s l3 - sum G^p]]
 //   Dinv      its inverse                      R4  (row-major 2x2)
 //   l4        the p-row's weight of the T-Laplacian (Eq. 32)
+//   W         Dinv [[1, 0], [l4, 1]]: a cell's update from its neighbour sums
+//   bt        Dinv b, formed once per right-hand side
+// so that a Gauss-Seidel update is  x_i = bt_i - W_i (sT, sp)  with sT, sp the
+// plain neighbour sums of the T- and p-Laplacians.
 // Per face, one array per axis:
 //   G         (G^T, G^p) = (k, 1/rho) times rho_f / h^2 times the boundary factor
 #pragma once
@@ -43,6 +47,8 @@ struct Level {
     const typename Vec<R>::v2 *G0, *G1, *G2;   // face coefficients, axes 0..2
     const typename Vec<R>::q4 *D, *Dinv;
     const R *l4;
+    const typename Vec<R>::q4 *W;   // Dinv [[1, 0], [l4, 1]]
+    typename Vec<R>::v2 *bt;        // Dinv b
 };
 
 // Dirichlet flags per axis and side (prolongation ghost signs).
