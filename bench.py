@@ -56,6 +56,17 @@ def env_int(k, d):
         return d
 
 
+def replica_value(local_units: float, local_seconds: float, world: int, device: str = "cuda"):
+    """Weak-scaling value of replicas: units of all ranks / the slowest rank's time."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([local_seconds], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    tmax = float(t.item())
+    return local_units * world / tmax, tmax
+
+
 def workload_problems():
     from paper_2206_11294_gb300 import inputs as I
     return [I.bubbles_1024(), I.bubble_axi()]
@@ -197,11 +208,7 @@ def run_ours(args, rank, world):
     counters = [s.counters() for s in solvers]
     units = sum(p.grid.N * st["cycles"] for p, st in zip(probs * args.steps, stats)) / 1e6
     solves = len(stats)
-    t = torch.tensor([dev_ms / 1e3], dtype=torch.float64, device=f"cuda:{dev}")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    tmax = float(t.item())
-    value = units * world / tmax
+    value, tmax = replica_value(units, dev_ms / 1e3, world, device=f"cuda:{dev}")
     # roofline of the dominant kernel, from its live event timings
     c0 = counters[0]
     peak, peak_kind = measured_peak()
@@ -233,17 +240,21 @@ def run_ours(args, rank, world):
     # end to end through the C ABI from host buffers (copies inside the timed region)
     e2e = None
     if not args.no_e2e:
-        host_x = [p.x0.copy() for p in probs]
+        # the same step from pinned host buffers: every step copies lambda, the
+        # face arrays, rhs and x in and x out through the C ABI
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+        host = [dict(lam=pin(p.lam), fa=[pin(f) for f in p.fa], fk=[pin(f) for f in p.fk], b=pin(p.b),
+                     x0=pin(p.x0), x=pin(p.x0)) for p in probs]
         for s in solvers:
             s.set_timing(False)
         torch.cuda.synchronize()
         e_units = 0.0
         w0 = time.perf_counter()
         for k in range(args.steps):
-            for p, s, hx in zip(probs, solvers, host_x):
-                hx[:] = p.x0
-                s.set_coeffs(p.lam, p.fa, p.fk)
-                st = s.solve(p.b, hx)
+            for p, s, hd in zip(probs, solvers, host):
+                hd["x"].copy_(hd["x0"])
+                s.set_coeffs(hd["lam"], hd["fa"], hd["fk"])
+                st = s.solve(hd["b"], hd["x"])
                 e_units += p.grid.N * st["cycles"] / 1e6
         torch.cuda.synchronize()
         e_wall = time.perf_counter() - w0

@@ -60,32 +60,43 @@ def build(force: bool = False) -> str:
     return _LIB
 
 
+def configure(lib):
+    """Declares the argument types of an oracle library (also used by the tests
+    that load a deliberately mutated copy)."""
+    dp = C.POINTER(C.c_double)
+    gp = C.POINTER(OrcGrid)
+    pa3 = dp * 3
+    lib.orc_apply_paper.argtypes = [gp, dp, pa3, pa3, dp, dp, C.c_int]
+    lib.orc_apply_paper.restype = None
+    lib.orc_dense_solve.argtypes = [gp, dp, pa3, pa3, dp, dp]
+    lib.orc_dense_solve.restype = C.c_int
+    lib.orc_mg_solve.argtypes = [gp, dp, pa3, pa3, dp, dp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, dp]
+    lib.orc_mg_solve.restype = C.c_int
+    lib.orc_rbgs_sweeps.argtypes = [gp, dp, pa3, pa3, dp, dp, C.c_int]
+    lib.orc_rbgs_sweeps.restype = C.c_int
+    lib.orc_residual_norms.argtypes = [gp, dp, pa3, pa3, dp, dp, dp]
+    lib.orc_residual_norms.restype = C.c_int
+    lib.orc_num_levels.argtypes = [gp, C.c_int]
+    lib.orc_num_levels.restype = C.c_int
+    lib.orc_level_coeffs.argtypes = [gp, dp, pa3, pa3, C.c_int, C.c_int, dp, pa3, pa3]
+    lib.orc_level_coeffs.restype = C.c_int
+    lib.orc_apply_rows.argtypes = [gp, dp, pa3, pa3, dp, C.POINTER(C.c_long), C.c_long, dp]
+    lib.orc_apply_rows.restype = None
+    return lib
+
+
+def compile_source(src: str, out: str) -> str:
+    """Compiles an oracle source file with the oracle's flags."""
+    subprocess.check_call(["gcc", "-std=c99", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+                           "-o", out, src, "-lm"])
+    return out
+
+
 def _load():
     global _lib
     with _lock:
         if _lib is None:
-            lib = C.CDLL(build())
-            dp = C.POINTER(C.c_double)
-            gp = C.POINTER(OrcGrid)
-            pa3 = dp * 3
-            lib.orc_apply_paper.argtypes = [gp, dp, pa3, pa3, dp, dp, C.c_int]
-            lib.orc_apply_paper.restype = None
-            lib.orc_dense_solve.argtypes = [gp, dp, pa3, pa3, dp, dp]
-            lib.orc_dense_solve.restype = C.c_int
-            lib.orc_mg_solve.argtypes = [gp, dp, pa3, pa3, dp, dp, C.c_int, C.c_int, C.c_int,
-                                         C.c_int, C.c_double, dp]
-            lib.orc_mg_solve.restype = C.c_int
-            lib.orc_rbgs_sweeps.argtypes = [gp, dp, pa3, pa3, dp, dp, C.c_int]
-            lib.orc_rbgs_sweeps.restype = C.c_int
-            lib.orc_residual_norms.argtypes = [gp, dp, pa3, pa3, dp, dp, dp]
-            lib.orc_residual_norms.restype = C.c_int
-            lib.orc_num_levels.argtypes = [gp, C.c_int]
-            lib.orc_num_levels.restype = C.c_int
-            lib.orc_level_coeffs.argtypes = [gp, dp, pa3, pa3, C.c_int, C.c_int, dp, pa3, pa3]
-            lib.orc_level_coeffs.restype = C.c_int
-            lib.orc_apply_rows.argtypes = [gp, dp, pa3, pa3, dp, C.POINTER(C.c_long), C.c_long, dp]
-            lib.orc_apply_rows.restype = None
-            _lib = lib
+            _lib = configure(C.CDLL(build()))
     return _lib
 
 

@@ -155,11 +155,17 @@ def _is_torch(a) -> bool:
 
 
 def _ptr(a, on_device: bool, dtype=np.float64):
-    """(pointer, keepalive) for a numpy array (host) or a CUDA tensor (device)."""
+    """(pointer, keepalive) for a numpy array or a CPU torch tensor (host; pinned
+    CPU tensors give the fastest copies) or a CUDA tensor (device)."""
     if on_device:
         import torch
         if not (_is_torch(a) and a.is_cuda and a.dtype == torch.float64 and a.is_contiguous()):
             raise TypeError("device arrays must be contiguous float64 CUDA tensors")
+        return C.c_void_p(a.data_ptr()), a
+    if _is_torch(a):
+        import torch
+        if not (a.dtype == torch.float64 and a.is_contiguous()):
+            raise TypeError("host tensors must be contiguous float64")
         return C.c_void_p(a.data_ptr()), a
     arr = np.ascontiguousarray(a, dtype=dtype)
     return C.c_void_p(arr.ctypes.data), arr
@@ -259,7 +265,7 @@ class Solver:
         self._need(x, 2 * self.N, "x")
         dev = _side(b, x)
         bp, bk = _ptr(b, dev)
-        if not dev:
+        if not dev and not _is_torch(x):
             if not (isinstance(x, np.ndarray) and x.dtype == np.float64 and x.flags.c_contiguous):
                 raise TypeError("host x must be a C-contiguous float64 numpy array (solved in place)")
         xp, xk = _ptr(x, dev)

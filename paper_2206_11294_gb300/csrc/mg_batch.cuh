@@ -95,7 +95,7 @@ __global__ void __launch_bounds__(kBatchThreads) kb_rbgs_colour(const BLevel *__
 }
 
 template <typename R>
-__global__ void __launch_bounds__(kBatchThreads) kb_rbgs_fused2d(const BLevel *__restrict__ lv,
+__global__ void __launch_bounds__(kBatchThreads, 8) kb_rbgs_fused2d(const BLevel *__restrict__ lv,
                                                                  const BState *__restrict__ st,
                                                                  const int2 *__restrict__ tab, int n, int to_alt) {
     for (int v = blockIdx.x; v < n; v += gridDim.x) {

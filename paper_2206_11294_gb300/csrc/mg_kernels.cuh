@@ -172,8 +172,10 @@ __device__ __forceinline__ void rbgs_fused2d_block(const Level<R> &L, const type
     }
 }
 
+// 8 resident blocks per SM (at most 32 registers): the FP32 sweep is bound by
+// memory latency, so occupancy is what feeds it.
 template <typename R>
-__global__ void __launch_bounds__(256) k_rbgs_fused2d(Level<R> L, const typename Vec<R>::v2 *__restrict__ xin,
+__global__ void __launch_bounds__(256, 8) k_rbgs_fused2d(Level<R> L, const typename Vec<R>::v2 *__restrict__ xin,
                                                       typename Vec<R>::v2 *__restrict__ xout) {
     rbgs_fused2d_block<R>(L, xin, xout, blockIdx.x, blockIdx.y);
 }

@@ -1,0 +1,111 @@
+"""Planted mistakes: each mutant copy of the oracle (compiled on the CPU) must
+fail at least one of the pins, so the pins would catch that kind of error in
+the oracle itself (and, through the parity tests, in the CUDA path)."""
+import contextlib
+import os
+import shutil
+import tempfile
+
+import ctypes as C
+import numpy as np
+import pytest
+
+import fv_matrix as fv
+from paper_2206_11294_gb300 import inputs as I
+
+W, D, A = I.BC_WALL, I.BC_DIRICHLET, I.BC_AXIS
+
+MUTATIONS = {
+    # Dirichlet boundary value at h instead of h/2
+    "dirichlet_distance": ("sum += A * cf * (gv - u[2 * i]) / (0.5 * g->h);", "sum += A * cf * (gv - u[2 * i]) / g->h;"),
+    # p-row of the defining operator loses l4 div(k grad T) (Eq. 28)
+    "drop_l4_operator": ("y[2 * i + 1] = lapp + l[2] * p + l[3] * lapT;", "y[2 * i + 1] = lapp + l[2] * p;"),
+    # the same term dropped only inside the multigrid's rows: the defect
+    # correction still converges, so the sweep pin has to catch it
+    "drop_l4_smoother": ("out[1] = lapp + l[2] * u[2 * i + 1] + l[3] * lapT;", "out[1] = lapp + l[2] * u[2 * i + 1];"),
+    # axisymmetric r-face area taken at the cell centre
+    "axi_face_area": ("return (a == 0 ? r_face(g, f[0]) : r_cell(g, c[0])) * g->h;",
+                      "return (a == 0 ? r_cell(g, c[0]) : r_cell(g, c[0])) * g->h;"),
+    # sign error in the 2x2 block solve
+    "block_solve_sign": ("z[1] = (D[0] * s[1] - D[2] * s[0]) / det;", "z[1] = (D[0] * s[1] + D[2] * s[0]) / det;"),
+    # prolongation weights 1/2 instead of 3/4 and 1/4
+    "prolongation_weights": ("                    w *= 0.25;", "                    w *= 0.5;"),
+}
+
+
+@contextlib.contextmanager
+def mutant(orc, name):
+    old, new = MUTATIONS[name]
+    src = open(os.path.join(os.path.dirname(orc.__file__), "coupled_oracle.c")).read()
+    assert src.count(old) >= 1, name
+    d = tempfile.mkdtemp()
+    try:
+        path = os.path.join(d, "m.c")
+        open(path, "w").write(src.replace(old, new))
+        lib = orc.configure(C.CDLL(orc.compile_source(path, os.path.join(d, "m.so"))))
+        saved = orc._lib
+        orc._lib = lib
+        try:
+            yield
+        finally:
+            orc._lib = saved
+    finally:
+        shutil.rmtree(d, ignore_errors=True)
+
+
+def _pins_pass(orc) -> bool:
+    """A few pins (closed-form modes, sparse assembly, dense vs multigrid,
+    multigrid convergence); False as soon as one fails."""
+    rng = np.random.default_rng(0)
+    grids = [I.Grid(dim=2, axisym=0, n=(6, 10, 1), h=0.1, bc=((W, D), (D, W), (0, 0)),
+                    bcT=((1, 2), (3, 4), (0, 0)), bcp=((5, 6), (7, 8), (0, 0))),
+             I.Grid(dim=2, axisym=1, n=(4, 8, 1), h=0.1, bc=((A, D), (W, D), (0, 0)),
+                    bcT=((0, 2), (3, 4), (0, 0)), bcp=((0, 6), (7, 8), (0, 0)))]
+    for g in grids:
+        lam = rng.standard_normal((g.N, 4))
+        fa = [rng.uniform(0.5, 2, int(np.prod(g.face_shape(a)))) for a in range(g.dim)]
+        fk = [rng.uniform(0.5, 2, int(np.prod(g.face_shape(a)))) for a in range(g.dim)]
+        x = rng.standard_normal((g.N, 2))
+        M, aff = fv.paper_operator(g, lam, fa, fk)
+        ref = M @ x.reshape(-1) + aff
+        if np.abs(orc.apply_paper(g.as_dict(), lam, fa, fk, x).reshape(-1) - ref).max() > 1e-12 * np.abs(ref).max():
+            return False
+        # one red-black sweep = the block Gauss-Seidel step of the assembled matrix
+        b = rng.standard_normal((g.N, 2))
+        x1 = orc.rbgs_sweeps(g.as_dict(), lam, fa, fk, b, x, sweeps=1)
+        Md = M.toarray()
+        rhs = b.reshape(-1) - aff
+        idx = np.arange(g.N)
+        red = ((idx % g.n[0] + idx // g.n[0]) % 2 == 0)
+        order = np.concatenate([np.flatnonzero(red), np.flatnonzero(~red)])
+        perm = np.stack([2 * order, 2 * order + 1], axis=1).reshape(-1)
+        Mp, rp, xp = Md[perm][:, perm], rhs[perm], x.reshape(-1)[perm]
+        Lo = np.zeros_like(Mp)
+        for r in range(2 * g.N):
+            Lo[r, : 2 * (r // 2) + 2] = Mp[r, : 2 * (r // 2) + 2]
+        xn = np.linalg.solve(Lo, rp - (Mp - Lo) @ xp)
+        gs = np.empty_like(xn)
+        gs[perm] = xn
+        if np.abs(x1.reshape(-1) - gs).max() > 1e-11 * np.abs(gs).max():
+            return False
+        p = I.random_coeff_problem(g, seed=7, dt=1e-5)
+        xd = np.linalg.solve(fv.paper_operator(g, p.lam, p.fa, p.fk)[0].toarray(),
+                             p.b.reshape(-1) - fv.paper_operator(g, p.lam, p.fa, p.fk)[1]).reshape(-1, 2)
+        xm, cyc, _ = orc.mg_solve(g.as_dict(), p.lam, p.fa, p.fk, p.b, p.x0, coarse_min=2, max_cycles=80,
+                                  rtol=1e-14)
+        if np.linalg.norm(xm - xd) > 1e-10 * np.linalg.norm(xd - p.x0):
+            return False
+    p = I.stiff(I.bubble_2d, 64)
+    x, cyc, hist = orc.mg_solve(p.grid.as_dict(), p.lam, p.fa, p.fk, p.b, p.x0, max_cycles=40, rtol=1e-10)
+    q = hist[1:, 1] / hist[:-1, 1]
+    return cyc <= 20 and np.max(q[:-1]) < 0.3
+
+
+def test_unmutated_oracle_passes_the_pins(orc):
+    assert _pins_pass(orc)
+
+
+@pytest.mark.parametrize("name", list(MUTATIONS))
+def test_mutant_fails_a_pin(orc, name):
+    with mutant(orc, name):
+        assert not _pins_pass(orc), name

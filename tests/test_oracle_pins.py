@@ -433,3 +433,24 @@ def test_apply_rows_matches_apply(orc):
     ids = rng.choice(g.N, 17, replace=False)
     y = orc.apply_paper(g.as_dict(), lam, fa, fk, x)
     assert np.array_equal(orc.apply_rows(g.as_dict(), lam, fa, fk, x, ids), y[ids])
+
+
+def test_single_cell_grid_and_1d_strip(orc):
+    """Degenerate grids: one cell (no fluxes, the 2x2 block alone) and a
+    1 x 7 strip (a single row of cells, no coarsening)."""
+    g = I.Grid(dim=2, axisym=0, n=(1, 1, 1), h=0.3, bc=((D, D), (W, W), (0, 0)),
+               bcT=((300, 310), (0, 0), (0, 0)), bcp=((1e5, 2e5), (0, 0), (0, 0)))
+    rng = np.random.default_rng(12)
+    p = I.random_coeff_problem(g, seed=12, dt=1e-5)
+    M, aff = fv.paper_operator(g, p.lam, p.fa, p.fk)
+    ref = np.linalg.solve(M.toarray(), p.b.reshape(-1) - aff).reshape(-1, 2)
+    x, cyc, _ = orc.mg_solve(g.as_dict(), p.lam, p.fa, p.fk, p.b, p.x0, max_cycles=5, rtol=1e-14)
+    assert orc.num_levels(g.as_dict()) == 1 and cyc == 1
+    assert np.abs(x - ref).max() <= 1e-12 * np.abs(ref).max()
+    g2 = I.Grid(dim=2, axisym=0, n=(7, 1, 1), h=0.1, bc=((D, W), (W, W), (0, 0)),
+                bcT=((305, 0), (0, 0), (0, 0)), bcp=((1.5e5, 0), (0, 0), (0, 0)))
+    p2 = I.random_coeff_problem(g2, seed=13, dt=1e-5)
+    M2, aff2 = fv.paper_operator(g2, p2.lam, p2.fa, p2.fk)
+    ref2 = np.linalg.solve(M2.toarray(), p2.b.reshape(-1) - aff2).reshape(-1, 2)
+    x2, cyc2, _ = orc.mg_solve(g2.as_dict(), p2.lam, p2.fa, p2.fk, p2.b, p2.x0, max_cycles=5, rtol=1e-14)
+    assert np.abs(x2 - ref2).max() <= 1e-12 * np.abs(ref2).max()
