@@ -348,6 +348,63 @@ def run_batch(args):
     return out
 
 
+def run_wall3d(args):
+    """256^3 bubble 0.2 above a no-flux wall, Dirichlet p = 1e5, T = 300 on the
+    other faces: FP64 and mixed precision to 1e-10 (set-up + solve per step)."""
+    import numpy as np
+    import torch
+    from paper_2206_11294_gb300 import inputs as I
+    from paper_2206_11294_gb300.binding import Solver
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    p = I.bubble_wall_3d(args.n3d)
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    d = dict(lam=T(p.lam), fa=[T(f) for f in p.fa], fk=[T(f) for f in p.fk], b=T(p.b), x0=T(p.x0), x=T(p.x0))
+    out = {"workload": f"wall3d_{args.n3d}^3, set-up + solve to 1e-10 per step", "cells": p.grid.N}
+    peak, peak_kind = measured_peak()
+    results = {}
+    for prec in ("fp64", "mixed"):
+        s = Solver(p.grid, precision=prec, rtol=1e-10, max_cycles=60, stream=stream)
+        s.set_timing(True)
+        for _ in range(args.warmup):
+            d["x"].copy_(d["x0"])
+            s.set_coeffs(d["lam"], d["fa"], d["fk"])
+            s.solve(d["b"], d["x"])
+        torch.cuda.synchronize()
+        s.set_timing(True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        st = []
+        e0.record(stream)
+        for _ in range(args.steps):
+            d["x"].copy_(d["x0"])
+            s.set_coeffs(d["lam"], d["fa"], d["fk"])
+            st.append(s.solve(d["b"], d["x"]))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        secs = e0.elapsed_time(e1) / 1e3
+        c = s.counters()
+        spl = c["smooth_sweeps"] / max(1, c["smooth_launches"])
+        avg = c["smooth_ms"] / 1e3 / max(1, c["smooth_launches"])
+        byts = SWEEP_BYTES_PER_CELL[(prec, 3)] * c["smooth_cells"] * spl
+        ent = {"mcell_vcycles_per_s": sum(p.grid.N * x["cycles"] for x in st) / secs / 1e6,
+               "solves_per_s": len(st) / secs, "ms_per_step": secs * 1e3 / args.steps, "cycles": st[0]["cycles"],
+               "outer": st[0]["outer"], "sweep_us": avg * 1e6,
+               "sweep_hbm": {"achieved_GBs": byts / avg / 1e9, "frac": byts / avg / 1e9 / peak, "peak": peak,
+                             "peak_source": peak_kind}}
+        if prec == "fp64":
+            inst = SWEEP_FP64_INST_PER_CELL[3] * c["smooth_cells"] * spl
+            ent["sweep_alu"] = {"achieved_G_fp64_inst_s": inst / avg / 1e9,
+                                "frac": inst / avg / 1e9 / FP64_INST_PEAK_G}
+        results[prec] = d["x"].cpu().numpy()
+        out[prec] = ent
+        s.close()
+    dev = results["fp64"] - p.x0
+    out["mixed_vs_fp64_rel_l2"] = max(float(np.linalg.norm(results["mixed"][:, f] - results["fp64"][:, f]) /
+                                            np.linalg.norm(dev[:, f])) for f in range(2))
+    out["speedup_mixed_vs_fp64"] = out["mixed"]["solves_per_s"] / out["fp64"]["solves_per_s"]
+    return out
+
+
 def run_serve(args):
     """Poisson arrivals of mixed 2D (128..1024) and 3D (64..160) bubble solves,
     mixed precision, admitted against an HBM budget; p50/p99 per arrival rate."""
@@ -428,7 +485,8 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", default="bubbles", choices=["bubbles", "batch", "serve"])
+    ap.add_argument("--workload", default="bubbles", choices=["bubbles", "batch", "serve", "wall3d"])
+    ap.add_argument("--n3d", type=int, default=256)
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--serve-rates", type=float, nargs="+", default=[10, 30, 100, 300, 1000, 2000])
     ap.add_argument("--serve-seconds", type=float, default=4.0)
@@ -441,7 +499,7 @@ def main():
     rank = env_int("RANK", 0)
     if args.workload != "bubbles":
         if rank == 0:
-            out = run_batch(args) if args.workload == "batch" else run_serve(args)
+            out = {"batch": run_batch, "serve": run_serve, "wall3d": run_wall3d}[args.workload](args)
             print(json.dumps(out), flush=True)
         return
     if args.impl == "ours" and world > 1:
