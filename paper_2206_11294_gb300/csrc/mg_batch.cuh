@@ -72,12 +72,6 @@ template <typename R> __device__ __forceinline__ typename Vec<R>::v2 *pick_alt(c
 template <> __device__ __forceinline__ double2 *pick_alt<double>(const BLevel &L) { return L.xalt; }
 template <> __device__ __forceinline__ float2 *pick_alt<float>(const BLevel &L) { return L.xalt32; }
 
-__device__ __forceinline__ void block_coords(int local, int gx, int gy, int &bx, int &by, int &bz) {
-    bx = local % gx;
-    by = (local / gx) % gy;
-    bz = local / (gx * gy);
-}
-
 template <typename R, int DIM>
 __global__ void __launch_bounds__(kBatchThreads) kb_rbgs_colour(const BLevel *__restrict__ lv,
                                                                 const BState *__restrict__ st,

@@ -85,6 +85,7 @@ struct mg_handle {
     char *stage;
     size_t stage_bytes;
     int nc;                // unknowns of the coarsest level
+    int tail_lev;          // first level of the cluster tail (nlev: no tail)
     double *Minv, *Mtmp;
     double *Mwork;         // coarse inverse: columns before the transpose (banded path)
     int *piv;              // coarse inverse: pivot rows (banded path)
@@ -222,6 +223,12 @@ void plan(mg_handle *h, char *base, size_t *bytes) {
     const LevelBuf &f = h->L[0];
     const LevelBuf &c = h->L[h->nlev - 1];
     h->nc = (int)(2 * c.N);
+    // The cluster tail takes the levels below the finest whose cells fit
+    // kTailCells, when there are at least two of them.
+    h->tail_lev = h->nlev;
+    for (int l = 1; l < h->nlev; l++)
+        if (h->L[l].N <= kTailCells) { h->tail_lev = l; break; }
+    if (h->nlev - h->tail_lev < 2 || h->nlev - h->tail_lev > kTailMaxLevels) h->tail_lev = h->nlev;
     long long sumnf = 0;
     for (int a = 0; a < g.dim; a++) sumnf += f.nf[a];
     // lambda, then 1/rho and k of every axis (host-side coefficient intake)
@@ -326,9 +333,44 @@ template <typename R> const R *coarse_inverse(const mg_handle *h);
 template <> const double *coarse_inverse<double>(const mg_handle *h) { return h->Minv; }
 template <> const float *coarse_inverse<float>(const mg_handle *h) { return h->Minv32; }
 
+// Levels tail_lev .. coarsest as one launch of k_vcycle_tail on one cluster.
+template <typename R, int DIM>
+void enqueue_tail(const mg_handle *h, cudaStream_t s) {
+    TailArgs<R> A;
+    std::memset(&A, 0, sizeof(A));
+    A.nlev = h->nlev - h->tail_lev;
+    for (int q = 0; q < A.nlev; q++) A.L[q] = view<R>(h->L[h->tail_lev + q]);
+    A.bc = bc_flags(h->grid);
+    A.Minv = coarse_inverse<R>(h);
+    A.nc = h->nc;
+    A.nu1 = h->opt.nu1;
+    A.nu2 = h->opt.nu2;
+    cudaLaunchConfig_t cfg;
+    std::memset(&cfg, 0, sizeof(cfg));
+    cfg.gridDim = dim3(kTailCtas, 1, 1);
+    cfg.blockDim = kBlock;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = kTailCtas;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, k_vcycle_tail<R, DIM>, A);
+}
+
 template <typename R, int DIM>
 void enqueue_vcycle(const mg_handle *h, cudaStream_t s, int l) {
     const LevelBuf &lb = h->L[l];
+    if (l == h->tail_lev) {
+        // the coarsest inverse is computed on the aux stream after each set-up
+        cudaStreamWaitEvent(s, h->ev_inv, cudaEventWaitExternal);
+        enqueue_tail<R, DIM>(h, s);
+        counted(h);
+        return;
+    }
     if (l == h->nlev - 1) {
         const Level<R> v = view<R>(lb);
         // the coarsest inverse is computed on the aux stream after each set-up

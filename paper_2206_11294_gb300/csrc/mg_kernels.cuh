@@ -5,6 +5,8 @@
 //
 // The system each level holds is described in mg_types.cuh.
 #pragma once
+#include <cooperative_groups.h>
+
 #include "mg_types.cuh"
 
 namespace cmg {
@@ -18,6 +20,16 @@ template <> __device__ __forceinline__ double2 mk2<double>(double a, double b) {
 template <> __device__ __forceinline__ float2 mk2<float>(float a, float b) { return make_float2(a, b); }
 
 template <typename V> __device__ __forceinline__ V ldg2(const V *p) { return __ldg(p); }
+// Loads of data that a kernel may itself have written in an earlier stage (the
+// cluster tail): NC = false reads through L2 (coherent), NC = true through the
+// read-only path.
+template <bool NC, typename V> __device__ __forceinline__ V ldv(const V *p) { return NC ? __ldg(p) : __ldcg(p); }
+
+__device__ __forceinline__ void block_coords(int local, int gx, int gy, int &bx, int &by, int &bz) {
+    bx = local % gx;
+    by = (local / gx) % gy;
+    bz = local / (gx * gy);
+}
 __device__ __forceinline__ dq ldgq(const dq *p) {
     const double2 *q = reinterpret_cast<const double2 *>(p);
     double2 u = __ldg(q), v = __ldg(q + 1);
@@ -32,7 +44,7 @@ __device__ __forceinline__ fq ldgq(const fq *p) {
 // sp = sum of G^p_f p_nb + l4 * sT (the p-row's T-Laplacian term, Eq. 28).
 // Neighbours beyond the grid contribute nothing (homogeneous boundary values;
 // inhomogeneous Dirichlet data are folded into the right-hand side).
-template <typename R, int DIM, bool WITH_L4 = true>
+template <typename R, int DIM, bool WITH_L4 = true, bool NC = true>
 __device__ __forceinline__ void offdiag(const Level<R> &L, const typename Vec<R>::v2 *__restrict__ x,
                                         int i, int j, int k, long long c, R &sT, R &sp) {
     using V2 = typename Vec<R>::v2;
@@ -40,23 +52,23 @@ __device__ __forceinline__ void offdiag(const Level<R> &L, const typename Vec<R>
     sT = R(0);
     sp = R(0);
     const long long f0 = (long long)i + (long long)(n0 + 1) * ((long long)j + (long long)n1 * k);
-    if (i > 0)      { V2 g = ldg2(L.G0 + f0);     V2 u = ldg2(x + c - 1);  sT += g.x * u.x; sp += g.y * u.y; }
-    if (i < n0 - 1) { V2 g = ldg2(L.G0 + f0 + 1); V2 u = ldg2(x + c + 1);  sT += g.x * u.x; sp += g.y * u.y; }
+    if (i > 0)      { V2 g = ldg2(L.G0 + f0);     V2 u = ldv<NC>(x + c - 1);  sT += g.x * u.x; sp += g.y * u.y; }
+    if (i < n0 - 1) { V2 g = ldg2(L.G0 + f0 + 1); V2 u = ldv<NC>(x + c + 1);  sT += g.x * u.x; sp += g.y * u.y; }
     const long long f1 = (long long)i + (long long)n0 * ((long long)j + (long long)(n1 + 1) * k);
-    if (j > 0)      { V2 g = ldg2(L.G1 + f1);      V2 u = ldg2(x + c - n0); sT += g.x * u.x; sp += g.y * u.y; }
-    if (j < n1 - 1) { V2 g = ldg2(L.G1 + f1 + n0); V2 u = ldg2(x + c + n0); sT += g.x * u.x; sp += g.y * u.y; }
+    if (j > 0)      { V2 g = ldg2(L.G1 + f1);      V2 u = ldv<NC>(x + c - n0); sT += g.x * u.x; sp += g.y * u.y; }
+    if (j < n1 - 1) { V2 g = ldg2(L.G1 + f1 + n0); V2 u = ldv<NC>(x + c + n0); sT += g.x * u.x; sp += g.y * u.y; }
     if (DIM == 3) {
         const long long pl = (long long)n0 * n1;
-        if (k > 0)        { V2 g = ldg2(L.G2 + c);      V2 u = ldg2(x + c - pl); sT += g.x * u.x; sp += g.y * u.y; }
-        if (k < L.n2 - 1) { V2 g = ldg2(L.G2 + c + pl); V2 u = ldg2(x + c + pl); sT += g.x * u.x; sp += g.y * u.y; }
+        if (k > 0)        { V2 g = ldg2(L.G2 + c);      V2 u = ldv<NC>(x + c - pl); sT += g.x * u.x; sp += g.y * u.y; }
+        if (k < L.n2 - 1) { V2 g = ldg2(L.G2 + c + pl); V2 u = ldv<NC>(x + c + pl); sT += g.x * u.x; sp += g.y * u.y; }
     }
     if (WITH_L4) sp += __ldg(L.l4 + c) * sT;
 }
 
 // Gauss-Seidel update of one cell from its plain neighbour sums.
-template <typename R>
+template <typename R, bool NC = true>
 __device__ __forceinline__ typename Vec<R>::v2 gs_update(const Level<R> &L, long long c, R sT, R sp) {
-    const auto bt = ldg2(L.bt + c);
+    const auto bt = ldv<NC>(L.bt + c);
     const auto W = ldgq(L.W + c);
     return mk2<R>(bt.x - W.a * sT - W.b * sp, bt.y - W.c * sT - W.d * sp);
 }
@@ -69,7 +81,7 @@ __device__ __forceinline__ typename Vec<R>::v2 gs_update(const Level<R> &L, long
 // ---------------------------------------------------------------------------
 // The work of thread block (bx, by, bz) of the launch geometry
 // (ceil(ceil(n0/2)/32), ceil(n1/8), n2); shared with the batched kernels.
-template <typename R, int DIM>
+template <typename R, int DIM, bool NC = true>
 __device__ __forceinline__ void rbgs_colour_block(const Level<R> &L, int colour, int bx, int by, int bz) {
     using V2 = typename Vec<R>::v2;
     const int j = by * kBY + threadIdx.y;
@@ -80,8 +92,8 @@ __device__ __forceinline__ void rbgs_colour_block(const Level<R> &L, int colour,
     if (i >= L.n0) return;
     const long long c = cell_id(i, j, k, L.n0, L.n1);
     R sT, sp;
-    offdiag<R, DIM, false>(L, L.x, i, j, k, c, sT, sp);
-    L.x[c] = gs_update<R>(L, c, sT, sp);
+    offdiag<R, DIM, false, NC>(L, L.x, i, j, k, c, sT, sp);
+    L.x[c] = gs_update<R, NC>(L, c, sT, sp);
 }
 
 template <typename R, int DIM>
@@ -185,7 +197,7 @@ __global__ void __launch_bounds__(256, 8) k_rbgs_fused2d(Level<R> L, const typen
 // children's residuals (plain mean in the row-scaled form = volume-weighted
 // mean of the physical residuals).  Also zeroes the coarse initial guess.
 // ---------------------------------------------------------------------------
-template <typename R, int DIM>
+template <typename R, int DIM, bool NC = true>
 __device__ __forceinline__ void residual_restrict_block(const Level<R> &F, const Level<R> &C, int bx, int by, int bz) {
     using V2 = typename Vec<R>::v2;
     const int I = bx * kBX + threadIdx.x;
@@ -198,8 +210,8 @@ __device__ __forceinline__ void residual_restrict_block(const Level<R> &F, const
         const int i = 2 * I + (q & 1), j = 2 * J + ((q >> 1) & 1), k = DIM == 3 ? 2 * K + (q >> 2) : 0;
         const long long c = cell_id(i, j, k, F.n0, F.n1);
         R sT, sp;
-        offdiag<R, DIM>(F, F.x, i, j, k, c, sT, sp);
-        const V2 bb = ldg2(F.b + c), xx = ldg2(F.x + c);
+        offdiag<R, DIM, true, NC>(F, F.x, i, j, k, c, sT, sp);
+        const V2 bb = ldv<NC>(F.b + c), xx = ldv<NC>(F.x + c);
         const auto Dd = ldgq(F.D + c);
         aT += bb.x - sT - (Dd.a * xx.x + Dd.b * xx.y);
         ap += bb.y - sp - (Dd.c * xx.x + Dd.d * xx.y);
@@ -225,7 +237,7 @@ __global__ void __launch_bounds__(kBX * kBY) k_residual_restrict(Level<R> F, Lev
 // reflects the parent: same value at walls and the axis, opposite sign at
 // Dirichlet faces (the correction vanishes there).
 // ---------------------------------------------------------------------------
-template <typename R, int DIM>
+template <typename R, int DIM, bool NC = true>
 __device__ __forceinline__ void prolong_add_block(const Level<R> &C, const Level<R> &F, const BcFlags &bc, int bx,
                                                   int by, int bz) {
     using V2 = typename Vec<R>::v2;
@@ -259,13 +271,13 @@ __device__ __forceinline__ void prolong_add_block(const Level<R> &C, const Level
             if ((q >> a) & 1) { Q[a] = Qn[a]; flip ^= neg[a]; nq++; }
         const R w = DIM == 2 ? (nq == 0 ? R(9.0 / 16) : nq == 1 ? R(3.0 / 16) : R(1.0 / 16))
                              : (nq == 0 ? R(27.0 / 64) : nq == 1 ? R(9.0 / 64) : nq == 2 ? R(3.0 / 64) : R(1.0 / 64));
-        V2 e = ldg2(C.x + cell_id(Q[0], Q[1], Q[2], C.n0, C.n1));
+        V2 e = ldv<NC>(C.x + cell_id(Q[0], Q[1], Q[2], C.n0, C.n1));
         if (flip) { e.x = -e.x; e.y = -e.y; }
         aT += w * e.x;
         ap += w * e.y;
     }
     const long long c = cell_id(i, j, k, F.n0, F.n1);
-    V2 xv = F.x[c];
+    V2 xv = NC ? F.x[c] : __ldcg(F.x + c);
     xv.x += aT;
     xv.y += ap;
     F.x[c] = xv;
@@ -1057,6 +1069,87 @@ __global__ void k_transpose(const double *__restrict__ W, double *__restrict__ M
          q += (long long)gridDim.x * blockDim.x) {
         const int i = (int)(q / n), j = (int)(q - (long long)i * n);
         Minv[q] = W[(long long)j * n + i];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// The bottom of a V-cycle in one launch on a thread-block cluster: every level
+// at or below kTailCells cells (smoothing, restriction, the coarsest solve,
+// prolongation) runs as stages of one kernel, the CTAs of the cluster sharing
+// each stage's blocks and meeting at a hardware cluster barrier (release /
+// acquire) between stages.  Small levels otherwise cost a launch per stage
+// for almost no work.  The stages call the same block functions as the
+// separate kernels, reading data written in earlier stages through L2.
+// ---------------------------------------------------------------------------
+constexpr int kTailCells = 4096;
+constexpr int kTailMaxLevels = 12;
+constexpr int kTailCtas = 8;      // CTAs of the cluster (portable cluster size)
+
+template <typename R>
+struct TailArgs {
+    Level<R> L[kTailMaxLevels];   // first tail level .. coarsest
+    int nlev;
+    BcFlags bc;
+    const R *Minv;
+    int nc;
+    int nu1, nu2;
+};
+
+template <typename R, int DIM>
+__device__ __forceinline__ void tail_smooth(const Level<R> &L, int sweeps, int rank, int nb) {
+    namespace cg = cooperative_groups;
+    const int gx = ((L.n0 + 1) / 2 + kBX - 1) / kBX, gy = (L.n1 + kBY - 1) / kBY, gz = DIM == 3 ? L.n2 : 1;
+    const int nblk = gx * gy * gz;
+    for (int q = 0; q < sweeps; q++)
+        for (int colour = 0; colour < 2; colour++) {
+            for (int v = rank; v < nblk; v += nb) {
+                int bx, by, bz;
+                block_coords(v, gx, gy, bx, by, bz);
+                rbgs_colour_block<R, DIM, false>(L, colour, bx, by, bz);
+            }
+            cg::this_cluster().sync();
+        }
+}
+
+template <typename R, int DIM>
+__global__ void __launch_bounds__(kBX * kBY) k_vcycle_tail(const __grid_constant__ TailArgs<R> A) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank(), nb = (int)cl.num_blocks();
+    for (int l = 0; l + 1 < A.nlev; l++) {
+        tail_smooth<R, DIM>(A.L[l], A.nu1, rank, nb);
+        const Level<R> &C = A.L[l + 1];
+        const int gx = (C.n0 + kBX - 1) / kBX, gy = (C.n1 + kBY - 1) / kBY, gz = DIM == 3 ? C.n2 : 1;
+        for (int v = rank; v < gx * gy * gz; v += nb) {
+            int bx, by, bz;
+            block_coords(v, gx, gy, bx, by, bz);
+            residual_restrict_block<R, DIM, false>(A.L[l], C, bx, by, bz);
+        }
+        cl.sync();
+    }
+    {   // coarsest: x = Minv b, one warp per row
+        const Level<R> &C = A.L[A.nlev - 1];
+        const int lane = threadIdx.x, warp = threadIdx.y;
+        const R *b = reinterpret_cast<const R *>(C.b);
+        for (int row = rank * kBY + warp; row < A.nc; row += nb * kBY) {
+            R acc = R(0);
+            for (int c = lane; c < A.nc; c += 32) acc += __ldg(A.Minv + (long long)row * A.nc + c) * __ldcg(b + c);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+            if (lane == 0) reinterpret_cast<R *>(C.x)[row] = acc;
+        }
+        cl.sync();
+    }
+    for (int l = A.nlev - 2; l >= 0; l--) {
+        const Level<R> &F = A.L[l];
+        const int gx = (F.n0 + kBX - 1) / kBX, gy = (F.n1 + kBY - 1) / kBY, gz = DIM == 3 ? F.n2 : 1;
+        for (int v = rank; v < gx * gy * gz; v += nb) {
+            int bx, by, bz;
+            block_coords(v, gx, gy, bx, by, bz);
+            prolong_add_block<R, DIM, false>(A.L[l + 1], F, A.bc, bx, by, bz);
+        }
+        cl.sync();
+        tail_smooth<R, DIM>(F, A.nu2, rank, nb);
     }
 }
 
