@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(kBatchThreads, 8) kb_rbgs_fused2d(const BLevel
 template <typename R, int DIM>
 __global__ void __launch_bounds__(kBatchThreads) kb_restrict(const BLevel *__restrict__ lv,
                                                              const BState *__restrict__ st,
-                                                             const int2 *__restrict__ tab, int n) {
+                                                             const int2 *__restrict__ tab, int n, int red) {
     for (int v = blockIdx.x; v < n; v += gridDim.x) {
         const int2 e = tab[v];
         const BLevel &B = lv[e.x];
@@ -118,7 +118,8 @@ __global__ void __launch_bounds__(kBatchThreads) kb_restrict(const BLevel *__res
         const int gx = (Cc.n0 + kBX - 1) / kBX, gy = (Cc.n1 + kBY - 1) / kBY;
         int bx, by, bz;
         block_coords(e.y, gx, gy, bx, by, bz);
-        residual_restrict_block<R, DIM>(F, Cc, bx, by, bz);
+        if (red) residual_restrict_block<R, DIM, true, true>(F, Cc, bx, by, bz);
+        else residual_restrict_block<R, DIM, true, false>(F, Cc, bx, by, bz);
     }
 }
 
@@ -358,7 +359,7 @@ __device__ __forceinline__ void batch_finish(const BProb &P, BState &S, int loca
 template <int DIM>
 __global__ void __launch_bounds__(kBatchThreads) kb_norm(const BLevel *__restrict__ lv, const BProb *__restrict__ pr,
                                                          BState *__restrict__ st, const int2 *__restrict__ tab, int n,
-                                                         int initial, double rtol, int max_cycles,
+                                                         int initial, int red, double rtol, int max_cycles,
                                                          int *__restrict__ active_count) {
     for (int v = blockIdx.x; v < n; v += gridDim.x) {
         __syncthreads();
@@ -370,7 +371,7 @@ __global__ void __launch_bounds__(kBatchThreads) kb_norm(const BLevel *__restric
         const int gx = (L.n0 + kBX - 1) / kBX, gy = (L.n1 + kBY - 1) / kBY;
         int bx, by, bz;
         block_coords(e.y, gx, gy, bx, by, bz);
-        const double2 s = norm_block<DIM>(L, bx, by, bz);
+        const double2 s = (red && !initial) ? norm_block<DIM, true>(L, bx, by, bz) : norm_block<DIM, false>(L, bx, by, bz);
         batch_finish(pr[p], st[p], e.y, s, initial, rtol, max_cycles, active_count);
     }
 }
@@ -489,7 +490,8 @@ void b_vcycle(mg_batch *b, cudaStream_t s) {
         if (b->colour[d].second == 0) continue;
         b_smooth<R, DIM>(b, s, d, b->opt.nu1);
         const int nr = b->restr[d].second;
-        kb_restrict<R, DIM><<<batch_grid(nr), kBlock, 0, s>>>(b->lv, b->st, b->tabs + b->restr[d].first, nr);
+        kb_restrict<R, DIM><<<batch_grid(nr), kBlock, 0, s>>>(b->lv, b->st, b->tabs + b->restr[d].first, nr,
+                                                              b->opt.nu1 > 0);
         b->launches++;
     }
     const int ncs = b->coarse.second;
@@ -510,7 +512,8 @@ void b_norm(mg_batch *b, cudaStream_t s, int initial) {
     const int n = b->norm.second;
     if (b->opt.precision == MG_FP64)
         kb_norm<DIM><<<batch_grid(n), kBlock, 0, s>>>(b->lv, b->pr, b->st, b->tabs + b->norm.first, n, initial,
-                                                      b->opt.rtol, b->opt.max_cycles, b->active_count);
+                                                      b->opt.nu2 > 0, b->opt.rtol, b->opt.max_cycles,
+                                                      b->active_count);
     else
         kb_residual64<DIM><<<batch_grid(n), kBlock, 0, s>>>(b->lv, b->pr, b->st, b->tabs + b->norm.first, n, initial,
                                                             b->opt.rtol, b->opt.max_cycles, b->active_count);

@@ -387,7 +387,10 @@ void enqueue_vcycle(const mg_handle *h, cudaStream_t s, int l) {
     if (tm) cudaEventRecordWithFlags(h->ev[0], s, cudaEventRecordExternal);
     enqueue_smooth<R, DIM>(h, s, l, h->opt.nu1);
     if (tm) cudaEventRecordWithFlags(h->ev[1], s, cudaEventRecordExternal);
-    k_residual_restrict<R, DIM><<<cell_grid(cb, DIM, cb.n[0]), kBlock, 0, s>>>(view<R>(lb), view<R>(cb));
+    if (h->opt.nu1 > 0)
+        k_residual_restrict<R, DIM, true><<<cell_grid(cb, DIM, cb.n[0]), kBlock, 0, s>>>(view<R>(lb), view<R>(cb));
+    else
+        k_residual_restrict<R, DIM, false><<<cell_grid(cb, DIM, cb.n[0]), kBlock, 0, s>>>(view<R>(lb), view<R>(cb));
     counted(h);
     enqueue_vcycle<R, DIM>(h, s, l + 1);
     k_prolong_add<R, DIM><<<cell_grid(lb, DIM, lb.n[0]), kBlock, 0, s>>>(view<R>(cb), view<R>(lb), bc_flags(h->grid));
@@ -397,11 +400,16 @@ void enqueue_vcycle(const mg_handle *h, cudaStream_t s, int l) {
     if (tm) cudaEventRecordWithFlags(h->ev[3], s, cudaEventRecordExternal);
 }
 
+// after_sweep: x has just come out of a red-black sweep (red cells only).
 template <int DIM>
-void enqueue_norm(const mg_handle *h, cudaStream_t s) {
+void enqueue_norm(const mg_handle *h, cudaStream_t s, bool after_sweep) {
     const LevelBuf &f = h->L[0];
-    k_norm_partials<DIM><<<cell_grid(f, DIM, f.n[0]), kBlock, 0, s>>>(view<double>(f), h->partial, h->ticket,
-                                                                       h->norms_d);
+    if (after_sweep)
+        k_norm_partials<DIM, true><<<cell_grid(f, DIM, f.n[0]), kBlock, 0, s>>>(view<double>(f), h->partial,
+                                                                               h->ticket, h->norms_d);
+    else
+        k_norm_partials<DIM, false><<<cell_grid(f, DIM, f.n[0]), kBlock, 0, s>>>(view<double>(f), h->partial,
+                                                                                h->ticket, h->norms_d);
     counted(h);
 }
 
@@ -418,7 +426,7 @@ void enqueue_residual_to32(const mg_handle *h, cudaStream_t s) {
 template <int DIM>
 void enqueue_cycle64(const mg_handle *h, cudaStream_t s) {
     enqueue_vcycle<double, DIM>(h, s, 0);
-    enqueue_norm<DIM>(h, s);
+    enqueue_norm<DIM>(h, s, h->opt.nu2 > 0);
     cudaMemcpyAsync(h->norms_h, h->norms_d, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
 }
 
@@ -687,7 +695,7 @@ mg_status setup_hierarchy(mg_handle *h, const double *lam, const double *const f
 template <int DIM>
 mg_status solve64(mg_handle *h, mg_stats *st) {
     double n0[2], nk[2];
-    enqueue_norm<DIM>(h, h->stream);
+    enqueue_norm<DIM>(h, h->stream, false);
     CK(cudaMemcpyAsync(h->norms_h, h->norms_d, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     mg_status e = sync_norms(h, n0);
     if (e) return e;
@@ -929,8 +937,8 @@ mg_status mg_residual_norms(mg_handle *h, const double *rhs, const double *x, in
     if (!rhs || !x || !out) return fail(MG_ERR_INVALID_ARG, "bad arguments to mg_residual_norms");
     DeviceGuard dg(h->device);
     if ((st = prep(h, rhs, x, on_device))) return st;
-    if (h->grid.dim == 2) enqueue_norm<2>(h, h->stream);
-    else enqueue_norm<3>(h, h->stream);
+    if (h->grid.dim == 2) enqueue_norm<2>(h, h->stream, false);
+    else enqueue_norm<3>(h, h->stream, false);
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(h->norms_h, h->norms_d, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     return sync_norms(h, out);

@@ -196,8 +196,14 @@ __global__ void __launch_bounds__(256, 8) k_rbgs_fused2d(Level<R> L, const typen
 // Residual of the children, restricted: coarse b = mean of the 2^DIM
 // children's residuals (plain mean in the row-scaled form = volume-weighted
 // mean of the physical residuals).  Also zeroes the coarse initial guess.
+//
+// RED: the fine level has just ended a red-black sweep, whose second colour
+// (black, i+j+k odd) solved its 2x2 blocks against the final red values, so
+// the black residuals vanish (in exact arithmetic; computed, they are
+// rounding noise of b - A x) and only the red children (even child index
+// popcount) are evaluated.
 // ---------------------------------------------------------------------------
-template <typename R, int DIM, bool NC = true>
+template <typename R, int DIM, bool NC = true, bool RED = false>
 __device__ __forceinline__ void residual_restrict_block(const Level<R> &F, const Level<R> &C, int bx, int by, int bz) {
     using V2 = typename Vec<R>::v2;
     const int I = bx * kBX + threadIdx.x;
@@ -207,6 +213,7 @@ __device__ __forceinline__ void residual_restrict_block(const Level<R> &F, const
     R aT = R(0), ap = R(0);
 #pragma unroll
     for (int q = 0; q < (1 << DIM); q++) {
+        if (RED && (__popc(q) & 1)) continue;
         const int i = 2 * I + (q & 1), j = 2 * J + ((q >> 1) & 1), k = DIM == 3 ? 2 * K + (q >> 2) : 0;
         const long long c = cell_id(i, j, k, F.n0, F.n1);
         R sT, sp;
@@ -225,9 +232,9 @@ __device__ __forceinline__ void residual_restrict_block(const Level<R> &F, const
     C.x[cc] = mk2<R>(R(0), R(0));
 }
 
-template <typename R, int DIM>
+template <typename R, int DIM, bool RED>
 __global__ void __launch_bounds__(kBX * kBY) k_residual_restrict(Level<R> F, Level<R> C) {
-    residual_restrict_block<R, DIM>(F, C, blockIdx.x, blockIdx.y, blockIdx.z);
+    residual_restrict_block<R, DIM, true, RED>(F, C, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 // ---------------------------------------------------------------------------
@@ -364,13 +371,28 @@ __device__ __forceinline__ void finish_norms(double2 *partial, int nblocks, unsi
 
 // Sums of (Dinv r)_T^2 and (Dinv r)_p^2 over block (bx, by, bz) of the cell
 // grid (ceil(n0/32), ceil(n1/8), n2); valid in thread 0.
-template <int DIM>
+//
+// RED: x has just come out of a red-black sweep, so the block residual of
+// the black cells is exactly zero (z = gs_update - x recomputes the very
+// update that produced x, bit for bit); the first four warps evaluate the
+// block's red cells (16 per row) and the other four contribute zeros.
+template <int DIM, bool RED = false>
 __device__ __forceinline__ double2 norm_block(const Level<double> &L, int bx, int by, int bz) {
-    const int i = bx * kBX + threadIdx.x;
-    const int j = by * kBY + threadIdx.y;
+    int i, j;
     const int k = DIM == 3 ? bz : 0;
+    bool on;
+    if (RED) {
+        const int t = threadIdx.x + kBX * threadIdx.y;
+        j = by * kBY + (t >> 4);
+        i = bx * kBX + 2 * (t & 15) + ((j + k) & 1);
+        on = t < kBX * kBY / 2;
+    } else {
+        i = bx * kBX + threadIdx.x;
+        j = by * kBY + threadIdx.y;
+        on = true;
+    }
     double zT2 = 0.0, zp2 = 0.0;
-    if (i < L.n0 && j < L.n1) {
+    if (on && i < L.n0 && j < L.n1) {
         const long long c = cell_id(i, j, k, L.n0, L.n1);
         double sT, sp;
         offdiag<double, DIM, false>(L, L.x, i, j, k, c, sT, sp);
@@ -385,10 +407,10 @@ __device__ __forceinline__ double2 norm_block(const Level<double> &L, int bx, in
     return make_double2(zT2, zp2);
 }
 
-template <int DIM>
+template <int DIM, bool RED>
 __global__ void __launch_bounds__(kBX * kBY) k_norm_partials(Level<double> L, double2 *__restrict__ partial,
                                                            unsigned int *__restrict__ ticket, double *__restrict__ out) {
-    const double2 s = norm_block<DIM>(L, blockIdx.x, blockIdx.y, blockIdx.z);
+    const double2 s = norm_block<DIM, RED>(L, blockIdx.x, blockIdx.y, blockIdx.z);
     if (threadIdx.x == 0 && threadIdx.y == 0)
         partial[blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)] = s;
     finish_norms(partial, gridDim.x * gridDim.y * gridDim.z, ticket, out);
@@ -1123,7 +1145,8 @@ __global__ void __launch_bounds__(kBX * kBY) k_vcycle_tail(const __grid_constant
         for (int v = rank; v < gx * gy * gz; v += nb) {
             int bx, by, bz;
             block_coords(v, gx, gy, bx, by, bz);
-            residual_restrict_block<R, DIM, false>(A.L[l], C, bx, by, bz);
+            if (A.nu1 > 0) residual_restrict_block<R, DIM, false, true>(A.L[l], C, bx, by, bz);
+            else residual_restrict_block<R, DIM, false, false>(A.L[l], C, bx, by, bz);
         }
         cl.sync();
     }

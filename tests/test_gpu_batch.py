@@ -88,6 +88,31 @@ def test_batch_equals_solo(torch_cuda, precision, which):
         s.close()
 
 
+@pytest.mark.parametrize("nu1,nu2", [(0, 2), (2, 0)])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_batch_equals_solo_cycle_shapes(torch_cuda, precision, nu1, nu2):
+    """Without pre- (post-) smoothing the restriction (stopping norm) takes
+    every cell; the batch must follow the single path there as well."""
+    from paper_2206_11294_gb300.binding import Batch
+    probs = _problems_2d()[:6]
+    kw = dict(precision=precision, rtol=1e-10, max_cycles=80, nu1=nu1, nu2=nu2)
+    solo = _solvers(probs, **kw)
+    xs_solo, st_solo = [], []
+    for s, p in zip(solo, probs):
+        x = p.x0.copy()
+        st_solo.append(s.solve(p.b, x))
+        xs_solo.append(x)
+    batch = Batch(solo)
+    xs = [p.x0.copy() for p in probs]
+    st = batch.solve([p.b for p in probs], xs)
+    for q, p in enumerate(probs):
+        assert st[q]["cycles"] == st_solo[q]["cycles"], q
+        assert rel_dev(xs[q], xs_solo[q], p.x0) <= 1e-13, q
+    batch.close()
+    for s in solo:
+        s.close()
+
+
 def test_batch_membership_does_not_change_results(torch_cuda):
     """A problem solved in a batch of one and in the full mix: bitwise equal."""
     from paper_2206_11294_gb300.binding import Batch

@@ -145,6 +145,47 @@ def test_converged_fp64_same_cycles_as_oracle(torch_cuda, orc, name):
     s.close()
 
 
+SHAPE_CASES = ["literal_2d_ragged_walls", "stiff_axi_axis", "literal_3d_wall_dirichlet", "stiff_3d_walls_odd"]
+
+
+@pytest.mark.parametrize("name", SHAPE_CASES)
+@pytest.mark.parametrize("nu1,nu2", [(0, 2), (2, 0), (1, 1), (3, 1)])
+def test_cycle_shapes_fp64(torch_cuda, orc, name, nu1, nu2):
+    """V(nu1, nu2) shapes: with nu1 = 0 the restriction evaluates every child
+    (no sweep has zeroed the black residuals) and with nu2 = 0 the stopping
+    norm visits every cell; both against the oracle, fixed and converged."""
+    p, tol = CASES[name]
+    g = p.grid.as_dict()
+    # one cycle: the stopping norm against the oracle's, per field where it is
+    # still well above rounding noise (a field whose 2x2 blocks dominate is
+    # solved to noise level by one cycle)
+    s = _solver(p, rtol=0.0, max_cycles=1, nu1=nu1, nu2=nu2)
+    x = p.x0.copy()
+    st = s.solve(p.b, x)
+    _, _, hist = orc.mg_solve(g, p.lam, p.fa, p.fk, p.b, p.x0, nu1=nu1, nu2=nu2, max_cycles=1, rtol=0.0)
+    checked = 0
+    for f in range(2):
+        if hist[-1][f] > 1e-6 * hist[0][f]:
+            assert abs(st["rfinal"][f] - hist[-1][f]) <= 1e-6 * hist[-1][f], f
+            checked += 1
+    assert checked > 0 or name.startswith("literal")   # literal cases: noise level after one cycle
+    s.close()
+    s = _solver(p, rtol=0.0, max_cycles=3, nu1=nu1, nu2=nu2)
+    x = p.x0.copy()
+    st = s.solve(p.b, x)
+    ref, cyc, hist = orc.mg_solve(g, p.lam, p.fa, p.fk, p.b, p.x0, nu1=nu1, nu2=nu2, max_cycles=3, rtol=0.0)
+    assert st["cycles"] == 3 == cyc
+    assert rel_dev(x, ref, p.x0) <= tol
+    s.close()
+    s = _solver(p, rtol=1e-10, max_cycles=80, nu1=nu1, nu2=nu2)
+    x = p.x0.copy()
+    st = s.solve(p.b, x)
+    ref, cyc, hist = orc.mg_solve(g, p.lam, p.fa, p.fk, p.b, p.x0, nu1=nu1, nu2=nu2, max_cycles=80, rtol=1e-10)
+    assert st["cycles"] == cyc
+    assert rel_dev(x, ref, p.x0) <= tol
+    s.close()
+
+
 @pytest.mark.parametrize("name", list(CASES))
 def test_mixed_precision(torch_cuda, orc, name):
     """FP32 cycles inside FP64 refinement against the converged FP64 oracle.
