@@ -368,9 +368,8 @@ __global__ void __launch_bounds__(kBatchThreads) kb_norm(const BLevel *__restric
         const int p = B.problem;
         if (!initial && !st[p].active) continue;
         const Level<double> L = B.d;
-        const int gx = (L.n0 + kBX - 1) / kBX, gy = (L.n1 + kBY - 1) / kBY;
         int bx, by, bz;
-        block_coords(e.y, gx, gy, bx, by, bz);
+        block_coords(e.y, norm_gx(L.n0), norm_gy(L.n1), bx, by, bz);
         const double2 s = (red && !initial) ? norm_block<DIM, true>(L, bx, by, bz) : norm_block<DIM, false>(L, bx, by, bz);
         batch_finish(pr[p], st[p], e.y, s, initial, rtol, max_cycles, active_count);
     }
@@ -390,9 +389,8 @@ __global__ void __launch_bounds__(kBatchThreads) kb_residual64(const BLevel *__r
         const int p = B.problem;
         if (!initial && !st[p].active) continue;
         const Level<double> L = B.d;
-        const int gx = (L.n0 + kBX - 1) / kBX, gy = (L.n1 + kBY - 1) / kBY;
         int bx, by, bz;
-        block_coords(e.y, gx, gy, bx, by, bz);
+        block_coords(e.y, norm_gx(L.n0), norm_gy(L.n1), bx, by, bz);
         const double2 s = residual64_to32_block<DIM>(L, B.f.b, B.f.bt, B.f.x, bx, by, bz);
         batch_finish(pr[p], st[p], e.y, s, initial, rtol, max_cycles, active_count);
     }
@@ -436,7 +434,7 @@ struct mg_batch {
     int2 *tabs;
     // table slices: {offset, count}
     std::vector<std::pair<long long, int>> colour, fused, restr, prolong;
-    std::pair<long long, int> norm, coarse, cells0;
+    std::pair<long long, int> norm, coarse, cells0, cells0g;   // cells0g: level-0 cell grids
     cudaGraphExec_t graph;
     long long graph_kernels;
     long long launches;
@@ -626,18 +624,21 @@ mg_status mg_batch_create(int count, mg_handle *const *handles, mg_batch **out) 
         b->restr.push_back(slice(tr));
         b->prolong.push_back(slice(tp));
     }
-    std::vector<int2> tn, tco, tcell;
+    std::vector<int2> tn, tnorm, tco, tcell;
     for (int p = 0; p < count; p++) {
         const mg_handle *h = handles[p];
         const dim3 g0 = cell_grid(h->L[0], dim, h->L[0].n[0]);
         add_blocks(tn, base[p], (long long)g0.x * g0.y * g0.z);
+        const dim3 gn = norm_grid(h->L[0], dim);
+        add_blocks(tnorm, base[p], (long long)gn.x * gn.y * gn.z);
         for (int r = 0; r < (h->nc + 7) / 8; r++) tco.push_back(make_int2(p, r));
         add_blocks(tcell, base[p], (h->L[0].N + kBatchThreads - 1) / kBatchThreads);
     }
-    b->norm = slice(tn);
+    b->cells0g = slice(tn);
+    b->norm = slice(tnorm);
     b->coarse = slice(tco);
     b->cells0 = slice(tcell);
-    b->setup_fine_tab = b->norm;                  // level-0 cell grids, as the norm
+    b->setup_fine_tab = b->cells0g;
     for (int d = 1; d < b->dmax; d++) {
         std::vector<int2> ts;
         for (int p = 0; p < count; p++) {
@@ -784,9 +785,9 @@ mg_status mg_batch_solve(mg_batch *b, const double *const *rhs, double *const *x
             }
         }
         CK(cudaMemcpyAsync(b->io, io, sizeof(BIo) * b->count, cudaMemcpyHostToDevice, s));
-        const int n = b->norm.second;
-        if (b->dim == 2) kb_prep<2><<<batch_grid(n), kBlock, 0, s>>>(b->lv, b->io, b->tabs + b->norm.first, n);
-        else kb_prep<3><<<batch_grid(n), kBlock, 0, s>>>(b->lv, b->io, b->tabs + b->norm.first, n);
+        const int n = b->cells0g.second;
+        if (b->dim == 2) kb_prep<2><<<batch_grid(n), kBlock, 0, s>>>(b->lv, b->io, b->tabs + b->cells0g.first, n);
+        else kb_prep<3><<<batch_grid(n), kBlock, 0, s>>>(b->lv, b->io, b->tabs + b->cells0g.first, n);
         b->launches++;
         CK(cudaGetLastError());
     }

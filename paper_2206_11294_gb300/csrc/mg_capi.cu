@@ -179,6 +179,11 @@ dim3 cell_grid(const LevelBuf &l, int dim, int xthreads) {
                 (unsigned)(dim == 3 ? l.n[2] : 1));
 }
 
+// Blocks of the norm / FP64-residual kernels (64 x 32 cells each).
+dim3 norm_grid(const LevelBuf &l, int dim) {
+    return dim3((unsigned)norm_gx(l.n[0]), (unsigned)norm_gy(l.n[1]), (unsigned)(dim == 3 ? l.n[2] : 1));
+}
+
 // Lays out every buffer; with base == NULL only computes the size.
 void plan(mg_handle *h, char *base, size_t *bytes) {
     Planner P{base};
@@ -241,7 +246,7 @@ void plan(mg_handle *h, char *base, size_t *bytes) {
     h->piv = P.take<int>(h->nc);
     h->dinv = P.take<double>(h->nc);
     h->Minv32 = mixed ? P.take<float>((long long)h->nc * h->nc) : nullptr;
-    const dim3 gg = cell_grid(f, g.dim, f.n[0]);
+    const dim3 gg = norm_grid(f, g.dim);
     h->npartial = (int)(gg.x * gg.y * gg.z);
     h->partial = P.take<double2>(h->npartial);
     h->norms_d = P.take<double>(8);
@@ -405,18 +410,18 @@ template <int DIM>
 void enqueue_norm(const mg_handle *h, cudaStream_t s, bool after_sweep) {
     const LevelBuf &f = h->L[0];
     if (after_sweep)
-        k_norm_partials<DIM, true><<<cell_grid(f, DIM, f.n[0]), kBlock, 0, s>>>(view<double>(f), h->partial,
-                                                                               h->ticket, h->norms_d);
+        k_norm_partials<DIM, true><<<norm_grid(f, DIM), kBlock, 0, s>>>(view<double>(f), h->partial, h->ticket,
+                                                                       h->norms_d);
     else
-        k_norm_partials<DIM, false><<<cell_grid(f, DIM, f.n[0]), kBlock, 0, s>>>(view<double>(f), h->partial,
-                                                                                h->ticket, h->norms_d);
+        k_norm_partials<DIM, false><<<norm_grid(f, DIM), kBlock, 0, s>>>(view<double>(f), h->partial, h->ticket,
+                                                                        h->norms_d);
     counted(h);
 }
 
 template <int DIM>
 void enqueue_residual_to32(const mg_handle *h, cudaStream_t s) {
     const LevelBuf &f = h->L[0];
-    k_residual64_to32<DIM><<<cell_grid(f, DIM, f.n[0]), kBlock, 0, s>>>(view<double>(f), f.b32, f.bt32, f.x32,
+    k_residual64_to32<DIM><<<norm_grid(f, DIM), kBlock, 0, s>>>(view<double>(f), f.b32, f.bt32, f.x32,
                                                                          h->partial,
                                                                          h->ticket, h->norms_d);
     counted(h);

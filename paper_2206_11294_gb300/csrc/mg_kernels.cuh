@@ -369,39 +369,54 @@ __device__ __forceinline__ void finish_norms(double2 *partial, int nblocks, unsi
     }
 }
 
-// Sums of (Dinv r)_T^2 and (Dinv r)_p^2 over block (bx, by, bz) of the cell
-// grid (ceil(n0/32), ceil(n1/8), n2); valid in thread 0.
+// Norm and FP64-residual blocks cover 64 x 32 cells (x, y) of one z-plane:
+// each thread visits several cells and accumulates its squares with FMAs, so
+// the per-block FP64 reduction tree (shuffles, then one warp) is spread over
+// many cells; on a part with few FP64 units per SM it would otherwise cost as
+// much as the cells themselves.
+constexpr int kNormCols = 64;
+constexpr int kNormRows = 4;   // rows per thread: the block spans kBY * kNormRows rows
+__host__ __device__ __forceinline__ int norm_gx(int n0) { return (n0 + kNormCols - 1) / kNormCols; }
+__host__ __device__ __forceinline__ int norm_gy(int n1) { return (n1 + kBY * kNormRows - 1) / (kBY * kNormRows); }
+
+template <int DIM>
+__device__ __forceinline__ void norm_cell(const Level<double> &L, int i, int j, int k, double &zT2, double &zp2) {
+    const long long c = cell_id(i, j, k, L.n0, L.n1);
+    double sT, sp;
+    offdiag<double, DIM, false>(L, L.x, i, j, k, c, sT, sp);
+    const double2 xx = ldg2(L.x + c);
+    const double2 u = gs_update<double>(L, c, sT, sp);   // = Dinv (b - offdiag)
+    const double zT = u.x - xx.x;
+    const double zp = u.y - xx.y;
+    zT2 = fma(zT, zT, zT2);
+    zp2 = fma(zp, zp, zp2);
+}
+
+// Sums of (Dinv r)_T^2 and (Dinv r)_p^2 over block (bx, by, bz) of the norm
+// grid (ceil(n0/64), ceil(n1/32), n2); valid in thread 0.
 //
 // RED: x has just come out of a red-black sweep, so the block residual of
 // the black cells is exactly zero (z = gs_update - x recomputes the very
-// update that produced x, bit for bit); the first four warps evaluate the
-// block's red cells (16 per row) and the other four contribute zeros.
+// update that produced x, bit for bit) and each thread visits the one red
+// cell of its column pair per row.
 template <int DIM, bool RED = false>
 __device__ __forceinline__ double2 norm_block(const Level<double> &L, int bx, int by, int bz) {
-    int i, j;
     const int k = DIM == 3 ? bz : 0;
-    bool on;
-    if (RED) {
-        const int t = threadIdx.x + kBX * threadIdx.y;
-        j = by * kBY + (t >> 4);
-        i = bx * kBX + 2 * (t & 15) + ((j + k) & 1);
-        on = t < kBX * kBY / 2;
-    } else {
-        i = bx * kBX + threadIdx.x;
-        j = by * kBY + threadIdx.y;
-        on = true;
-    }
     double zT2 = 0.0, zp2 = 0.0;
-    if (on && i < L.n0 && j < L.n1) {
-        const long long c = cell_id(i, j, k, L.n0, L.n1);
-        double sT, sp;
-        offdiag<double, DIM, false>(L, L.x, i, j, k, c, sT, sp);
-        const double2 xx = ldg2(L.x + c);
-        const double2 u = gs_update<double>(L, c, sT, sp);   // = Dinv (b - offdiag)
-        const double zT = u.x - xx.x;
-        const double zp = u.y - xx.y;
-        zT2 = zT * zT;
-        zp2 = zp * zp;
+#pragma unroll 1
+    for (int r = 0; r < kNormRows; r++) {
+        const int j = (by * kNormRows + r) * kBY + threadIdx.y;
+        if (j >= L.n1) break;
+        if (RED) {
+            const int i = bx * kNormCols + 2 * threadIdx.x + ((j + k) & 1);
+            if (i < L.n0) norm_cell<DIM>(L, i, j, k, zT2, zp2);
+        } else {
+#pragma unroll
+            for (int e = 0; e < 2; e++) {
+                const int i = bx * kNormCols + e * kBX + threadIdx.x;
+                if (i < L.n0) norm_cell<DIM>(L, i, j, k, zT2, zp2);
+            }
+        }
     }
     block_sum2(zT2, zp2);
     return make_double2(zT2, zp2);
@@ -420,29 +435,42 @@ __global__ void __launch_bounds__(kBX * kBY) k_norm_partials(Level<double> L, do
 // written (rounded) as the FP32 right-hand side of the correction problem,
 // the FP32 correction is zeroed, and the norm partials of Dinv r are formed.
 template <int DIM>
+__device__ __forceinline__ void residual64_to32_cell(const Level<double> &L, float2 *__restrict__ b32,
+                                                     float2 *__restrict__ bt32, float2 *__restrict__ e32, int i, int j,
+                                                     int k, double &zT2, double &zp2) {
+    const long long c = cell_id(i, j, k, L.n0, L.n1);
+    double sT, sp;
+    offdiag<double, DIM>(L, L.x, i, j, k, c, sT, sp);
+    const double2 bb = ldg2(L.b + c), xx = ldg2(L.x + c);
+    const dq Dd = ldgq(L.D + c);
+    const dq Di = ldgq(L.Dinv + c);
+    const double rT = bb.x - sT - (Dd.a * xx.x + Dd.b * xx.y);
+    const double rp = bb.y - sp - (Dd.c * xx.x + Dd.d * xx.y);
+    const double zT = Di.a * rT + Di.b * rp;
+    const double zp = Di.c * rT + Di.d * rp;
+    zT2 = fma(zT, zT, zT2);
+    zp2 = fma(zp, zp, zp2);
+    b32[c] = make_float2((float)rT, (float)rp);
+    bt32[c] = make_float2((float)zT, (float)zp);     // Dinv r for the FP32 sweeps
+    e32[c] = make_float2(0.f, 0.f);
+}
+
+// Block (bx, by, bz) of the norm grid.
+template <int DIM>
 __device__ __forceinline__ double2 residual64_to32_block(const Level<double> &L, float2 *__restrict__ b32,
                                                          float2 *__restrict__ bt32, float2 *__restrict__ e32,
                                                          int bx, int by, int bz) {
-    const int i = bx * kBX + threadIdx.x;
-    const int j = by * kBY + threadIdx.y;
     const int k = DIM == 3 ? bz : 0;
     double zT2 = 0.0, zp2 = 0.0;
-    if (i < L.n0 && j < L.n1) {
-        const long long c = cell_id(i, j, k, L.n0, L.n1);
-        double sT, sp;
-        offdiag<double, DIM>(L, L.x, i, j, k, c, sT, sp);
-        const double2 bb = ldg2(L.b + c), xx = ldg2(L.x + c);
-        const dq Dd = ldgq(L.D + c);
-        const dq Di = ldgq(L.Dinv + c);
-        const double rT = bb.x - sT - (Dd.a * xx.x + Dd.b * xx.y);
-        const double rp = bb.y - sp - (Dd.c * xx.x + Dd.d * xx.y);
-        const double zT = Di.a * rT + Di.b * rp;
-        const double zp = Di.c * rT + Di.d * rp;
-        zT2 = zT * zT;
-        zp2 = zp * zp;
-        b32[c] = make_float2((float)rT, (float)rp);
-        bt32[c] = make_float2((float)zT, (float)zp);     // Dinv r for the FP32 sweeps
-        e32[c] = make_float2(0.f, 0.f);
+#pragma unroll 1
+    for (int r = 0; r < kNormRows; r++) {
+        const int j = (by * kNormRows + r) * kBY + threadIdx.y;
+        if (j >= L.n1) break;
+#pragma unroll
+        for (int e = 0; e < 2; e++) {
+            const int i = bx * kNormCols + e * kBX + threadIdx.x;
+            if (i < L.n0) residual64_to32_cell<DIM>(L, b32, bt32, e32, i, j, k, zT2, zp2);
+        }
     }
     block_sum2(zT2, zp2);
     return make_double2(zT2, zp2);
