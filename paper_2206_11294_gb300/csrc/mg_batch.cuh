@@ -273,7 +273,7 @@ __global__ void __launch_bounds__(kBatchThreads) kb_prep(const BLevel *__restric
         const int2 e = tab[v];
         const BLevel &B = lv[e.x];
         const BIo &P = io[B.problem];
-        const Level<double> L = B.d;
+        const Level<double> &L = B.d;    // in global memory: the boundary call takes its address
         const int gx = (L.n0 + kBX - 1) / kBX, gy = (L.n1 + kBY - 1) / kBY;
         int bx, by, bz;
         block_coords(e.y, gx, gy, bx, by, bz);
@@ -668,6 +668,7 @@ mg_status mg_batch_create(int count, mg_handle *const *handles, mg_batch **out) 
             S.gm.axisym = h->grid.axisym;
             S.gm.r0 = h->grid.r0;
             S.gm.h = hl;
+            S.gm.ih2 = 1.0 / (hl * hl);
             S.out = setup_out(h->L[l], mixed);
             if (l > 0) S.fine = setup_fine_of(h->L[l - 1], hl / 2.0);
             S.problem = p;

@@ -631,6 +631,7 @@ mg_status setup_hierarchy(mg_handle *h, const double *lam, const double *const f
     gm.axisym = g.axisym;
     gm.r0 = g.r0;
     gm.h = g.h;
+    gm.ih2 = 1.0 / (g.h * g.h);
     SetupIn in;
     in.lam = lam_d;
     for (int a = 0; a < 3; a++) {

@@ -403,10 +403,10 @@ template <int DIM, bool RED = false>
 __device__ __forceinline__ double2 norm_block(const Level<double> &L, int bx, int by, int bz) {
     const int k = DIM == 3 ? bz : 0;
     double zT2 = 0.0, zp2 = 0.0;
-#pragma unroll 1
+#pragma unroll
     for (int r = 0; r < kNormRows; r++) {
         const int j = (by * kNormRows + r) * kBY + threadIdx.y;
-        if (j >= L.n1) break;
+        if (j >= L.n1) continue;
         if (RED) {
             const int i = bx * kNormCols + 2 * threadIdx.x + ((j + k) & 1);
             if (i < L.n0) norm_cell<DIM>(L, i, j, k, zT2, zp2);
@@ -462,10 +462,10 @@ __device__ __forceinline__ double2 residual64_to32_block(const Level<double> &L,
                                                          int bx, int by, int bz) {
     const int k = DIM == 3 ? bz : 0;
     double zT2 = 0.0, zp2 = 0.0;
-#pragma unroll 1
+#pragma unroll
     for (int r = 0; r < kNormRows; r++) {
         const int j = (by * kNormRows + r) * kBY + threadIdx.y;
-        if (j >= L.n1) break;
+        if (j >= L.n1) continue;
 #pragma unroll
         for (int e = 0; e < 2; e++) {
             const int i = bx * kNormCols + e * kBX + threadIdx.x;
@@ -524,12 +524,13 @@ struct BcVals {
 };
 
 // Dirichlet data of a boundary cell's rows: G^T g_T and G^p g_p + l4 G^T g_T.
+// Called for cells on the grid's boundary only, as a real call: its
+// conditional FP64 products would otherwise be issued (predicated off) for
+// every interior cell too, and FP64 issue slots are this part's scarce unit.
 template <int DIM>
-__device__ __forceinline__ void boundary_data(const Level<double> &L, const BcVals &bv, int i, int j, int k,
-                                              double &gT, double &gp) {
+__device__ __noinline__ double2 boundary_rows(const Level<double> &L, const BcVals &bv, int i, int j, int k) {
     const int n0 = L.n0, n1 = L.n1;
-    gT = 0.0;
-    gp = 0.0;
+    double gT = 0.0, gp = 0.0;
     const long long f0 = (long long)i + (long long)(n0 + 1) * ((long long)j + (long long)n1 * k);
     if (i == 0 && bv.dir[0][0])      { double2 g = L.G0[f0];     gT += g.x * bv.T[0][0]; gp += g.y * bv.p[0][0]; }
     if (i == n0 - 1 && bv.dir[0][1]) { double2 g = L.G0[f0 + 1]; gT += g.x * bv.T[0][1]; gp += g.y * bv.p[0][1]; }
@@ -542,23 +543,37 @@ __device__ __forceinline__ void boundary_data(const Level<double> &L, const BcVa
         if (k == L.n2 - 1 && bv.dir[2][1]) { double2 g = L.G2[c + pl]; gT += g.x * bv.T[2][1]; gp += g.y * bv.p[2][1]; }
     }
     gp += L.l4[cell_id(i, j, k, n0, n1)] * gT;
+    return make_double2(gT, gp);
+}
+
+template <int DIM>
+__device__ __forceinline__ bool on_boundary(const Level<double> &L, int i, int j, int k) {
+    return i == 0 || i == L.n0 - 1 || j == 0 || j == L.n1 - 1 || (DIM == 3 && (k == 0 || k == L.n2 - 1));
 }
 
 // Block (bx, by, bz) of the cell grid; xin (may be NULL) is also copied into L.x.
-template <int DIM>
-__device__ __forceinline__ void prep_rhs_block(const Level<double> &L, const double2 *__restrict__ rhs,
-                                               const double2 *__restrict__ xin, const BcVals &bv, int axisym,
-                                               double r0, double h, int bx, int by, int bz) {
+// AXI: the rows carry the factor s_i = r_i (else 1, with no arithmetic).
+template <int DIM, bool AXI>
+__device__ __forceinline__ void prep_rhs_cells(const Level<double> &L, const double2 *__restrict__ rhs,
+                                               const double2 *__restrict__ xin, const BcVals &bv, double r0,
+                                               double h, int bx, int by, int bz) {
     const int i = bx * kBX + threadIdx.x;
     const int j = by * kBY + threadIdx.y;
     const int k = DIM == 3 ? bz : 0;
     if (i >= L.n0 || j >= L.n1) return;
     const long long c = cell_id(i, j, k, L.n0, L.n1);
-    const double s = axisym ? r0 + (i + 0.5) * h : 1.0;
     const double2 q = rhs[c];
-    double gT, gp;
-    boundary_data<DIM>(L, bv, i, j, k, gT, gp);
-    const double bT = s * q.x - gT, bp = s * q.y - gp;
+    double bT = q.x, bp = q.y;
+    if (AXI) {
+        const double s = r0 + (i + 0.5) * h;
+        bT = s * q.x;
+        bp = s * q.y;
+    }
+    if (on_boundary<DIM>(L, i, j, k)) {
+        const double2 g = boundary_rows<DIM>(L, bv, i, j, k);
+        bT -= g.x;
+        bp -= g.y;
+    }
     L.b[c] = make_double2(bT, bp);
     const dq Di = ldgq(L.Dinv + c);
     L.bt[c] = make_double2(Di.a * bT + Di.b * bp, Di.c * bT + Di.d * bp);
@@ -566,23 +581,37 @@ __device__ __forceinline__ void prep_rhs_block(const Level<double> &L, const dou
 }
 
 template <int DIM>
-__global__ void __launch_bounds__(kBX * kBY) k_prep_rhs(Level<double> L, const double2 *__restrict__ rhs,
-                                                      BcVals bv, int axisym, double r0, double h) {
+__device__ __forceinline__ void prep_rhs_block(const Level<double> &L, const double2 *__restrict__ rhs,
+                                               const double2 *__restrict__ xin, const BcVals &bv, int axisym,
+                                               double r0, double h, int bx, int by, int bz) {
+    if (axisym) prep_rhs_cells<DIM, true>(L, rhs, xin, bv, r0, h, bx, by, bz);
+    else prep_rhs_cells<DIM, false>(L, rhs, xin, bv, r0, h, bx, by, bz);
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(kBX * kBY) k_prep_rhs(const __grid_constant__ Level<double> L,
+                                                      const double2 *__restrict__ rhs, const __grid_constant__ BcVals bv,
+                                                      int axisym, double r0, double h) {
     prep_rhs_block<DIM>(L, rhs, nullptr, bv, axisym, r0, h, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 // y = L(x) (Eqs. 27-28): offdiag + boundary data + D x is s_i times the rows.
 template <int DIM>
-__global__ void __launch_bounds__(kBX * kBY) k_apply_paper(Level<double> L, BcVals bv, int axisym, double r0,
+__global__ void __launch_bounds__(kBX * kBY) k_apply_paper(const __grid_constant__ Level<double> L,
+                                                         const __grid_constant__ BcVals bv, int axisym, double r0,
                                                          double h, double2 *__restrict__ y) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     const int k = DIM == 3 ? (int)blockIdx.z : 0;
     if (i >= L.n0 || j >= L.n1) return;
     const long long c = cell_id(i, j, k, L.n0, L.n1);
-    double sT, sp, gT, gp;
+    double sT, sp, gT = 0.0, gp = 0.0;
     offdiag<double, DIM>(L, L.x, i, j, k, c, sT, sp);
-    boundary_data<DIM>(L, bv, i, j, k, gT, gp);
+    if (on_boundary<DIM>(L, i, j, k)) {
+        const double2 g = boundary_rows<DIM>(L, bv, i, j, k);
+        gT = g.x;
+        gp = g.y;
+    }
     const double2 xx = L.x[c];
     const dq Dd = L.D[c];
     const double s = axisym ? r0 + (i + 0.5) * h : 1.0;
@@ -611,6 +640,7 @@ struct SetupGeom {
     int n[3];
     int axisym;
     double r0, h;                 // this level's spacing
+    double ih2;                   // 1 / h^2 (finest level)
     double fac[3][2];             // boundary factor per axis / side: 2 Dirichlet, 0 wall/axis
 };
 
@@ -622,13 +652,15 @@ __device__ __forceinline__ bool finite_bits(double v) {
 template <int DIM>
 __device__ __forceinline__ void finish_cell(const SetupOut &o, long long c, const long long fid[3][2], int own[3][2],
                                             const double2 g[3][2], dq S, double l4, int *err) {
-    double sT = 0.0, sp = 0.0;
+    double sT = g[0][0].x, sp = g[0][0].y;   // face sums (the faces are finite and >= 0)
 #pragma unroll
     for (int a = 0; a < DIM; a++)
 #pragma unroll
         for (int sd = 0; sd < 2; sd++) {
-            sT += g[a][sd].x;
-            sp += g[a][sd].y;
+            if (a | sd) {
+                sT += g[a][sd].x;
+                sp += g[a][sd].y;
+            }
             if (own[a][sd]) {
                 o.G[a][fid[a][sd]] = g[a][sd];
                 if (o.G32[a]) o.G32[a][fid[a][sd]] = make_float2((float)g[a][sd].x, (float)g[a][sd].y);
@@ -670,8 +702,10 @@ struct SetupIn {
 
 // Finest level from lambda [N][4] and the per-axis arrays of 1/rho and k:
 // block (bx, by, bz) of the cell grid (ceil(n0/32), ceil(n1/8), n2).
-template <int DIM>
-__device__ __forceinline__ void setup_fine_block(const SetupGeom &gm, const SetupIn &in, const SetupOut &o, int *err,
+// AXI: faces carry r_f and the rows s_i = r_i; boundary faces (rare, a
+// separate branch) carry the boundary factor.
+template <int DIM, bool AXI>
+__device__ __forceinline__ void setup_fine_cells(const SetupGeom &gm, const SetupIn &in, const SetupOut &o, int *err,
                                                  int bx, int by, int bz) {
     const int i = bx * kBX + threadIdx.x;
     const int j = by * kBY + threadIdx.y;
@@ -681,32 +715,56 @@ __device__ __forceinline__ void setup_fine_block(const SetupGeom &gm, const Setu
     const long long c = cell_id(i, j, k, gm.n[0], gm.n[1]);
     const double l1 = lam[4 * c], l2 = lam[4 * c + 1], l3 = lam[4 * c + 2], l4 = lam[4 * c + 3];
     bool bad = !finite_bits(l1) || !finite_bits(l2) || !finite_bits(l3) || !finite_bits(l4);
-    const double s = gm.axisym ? gm.r0 + (i + 0.5) * gm.h : 1.0;
-    const double ih2 = 1.0 / (gm.h * gm.h);
+    const double s = AXI ? gm.r0 + (i + 0.5) * gm.h : 1.0;
+    const double ih2 = gm.ih2;
     const double *const *fa = in.fa, *const *fk = in.fk;
     const int pos[3] = {i, j, k};
     long long fid[3][2];
     face_ids(gm.n, i, j, k, fid);
     int own[3][2];
     double2 g[3][2];
+    double kf[3][2], af[3][2], wf[3][2];
+    bool edge = false;
 #pragma unroll
     for (int a = 0; a < DIM; a++)
 #pragma unroll
         for (int sd = 0; sd < 2; sd++) {
             const int fpos = pos[a] + sd;
-            // w = rho_f / h^2 times the boundary factor; FP64 multiplies only
-            // where the geometry or a boundary needs them
+            // w = rho_f / h^2 (times r_f or r_i on axisymmetric grids)
             double w = ih2;
-            if (gm.axisym) w *= (a == 0 ? gm.r0 + (i + sd) * gm.h : s);
-            if (fpos == 0) w *= gm.fac[a][0];
-            else if (fpos == gm.n[a]) w *= gm.fac[a][1];
+            if (AXI) w *= (a == 0 ? gm.r0 + (i + sd) * gm.h : s);
             const double al = fa[a][fid[a][sd]], kk = fk[a][fid[a][sd]];
             bad = bad || !finite_bits(al) || !finite_bits(kk);
+            kf[a][sd] = kk;
+            af[a][sd] = al;
+            wf[a][sd] = w;
             g[a][sd] = make_double2(kk * w, al * w);
             own[a][sd] = sd == 0 || fpos == gm.n[a];
+            edge = edge || fpos == 0 || fpos == gm.n[a];
         }
+    if (edge) {
+        // boundary faces: w times the factor (2 Dirichlet, 0 wall / axis)
+#pragma unroll
+        for (int a = 0; a < DIM; a++)
+#pragma unroll
+            for (int sd = 0; sd < 2; sd++) {
+                const int fpos = pos[a] + sd;
+                if (fpos == 0 || fpos == gm.n[a]) {
+                    const double w = wf[a][sd] * (fpos == 0 ? gm.fac[a][0] : gm.fac[a][1]);
+                    g[a][sd] = make_double2(kf[a][sd] * w, af[a][sd] * w);
+                }
+            }
+    }
     if (bad) atomicOr(err, 1);
-    finish_cell<DIM>(o, c, fid, own, g, dq{s * l1, s * l2, 0.0, s * l3}, l4, err);
+    const dq S = AXI ? dq{s * l1, s * l2, 0.0, s * l3} : dq{l1, l2, 0.0, l3};
+    finish_cell<DIM>(o, c, fid, own, g, S, l4, err);
+}
+
+template <int DIM>
+__device__ __forceinline__ void setup_fine_block(const SetupGeom &gm, const SetupIn &in, const SetupOut &o, int *err,
+                                                 int bx, int by, int bz) {
+    if (gm.axisym) setup_fine_cells<DIM, true>(gm, in, o, err, bx, by, bz);
+    else setup_fine_cells<DIM, false>(gm, in, o, err, bx, by, bz);
 }
 
 template <int DIM>
@@ -726,8 +784,8 @@ struct SetupFine {
     double h;
 };
 
-template <int DIM>
-__device__ __forceinline__ void setup_coarse_block(const SetupGeom &cg, const SetupFine &F, const SetupOut &o,
+template <int DIM, bool AXI>
+__device__ __forceinline__ void setup_coarse_cells(const SetupGeom &cg, const SetupFine &F, const SetupOut &o,
                                                    int *err, int bx, int by, int bz) {
     const int I = bx * kBX + threadIdx.x;
     const int J = by * kBY + threadIdx.y;
@@ -744,14 +802,18 @@ __device__ __forceinline__ void setup_coarse_block(const SetupGeom &cg, const Se
         const int i = 2 * I + (q & 1);
         const long long f = cell_id(i, 2 * J + ((q >> 1) & 1), DIM == 3 ? 2 * K + (q >> 2) : 0, fn0, fn1);
         const dq sf = Sf[f];
-        const double sc = cg.axisym ? cg.r0 + (i + 0.5) * hf : 1.0;
         a0 += sf.a; a1 += sf.b; a2 += sf.c; a3 += sf.d;
-        v4 += sc * l4f[f];
-        vs += sc;
+        if (AXI) {
+            const double sc = cg.r0 + (i + 0.5) * hf;
+            v4 += sc * l4f[f];
+            vs += sc;
+        } else {
+            v4 += l4f[f];
+        }
     }
     const double wb = 1.0 / (1 << DIM);
     const dq S{a0 * wb, a1 * wb, a2 * wb, a3 * wb};
-    const double l4 = v4 / vs;
+    const double l4 = AXI ? v4 / vs : v4 * wb;   // volume-weighted mean (a power-of-two mean is exact as a product)
     const int P[3] = {I, J, K};
     const int fm[3][2] = {{fn0 + 1, fn1}, {fn0, fn1 + 1}, {fn0, fn1}};   // fine face array dims (x, y) per axis
     const double2 *const *Gf = F.G;
@@ -787,6 +849,13 @@ __device__ __forceinline__ void setup_coarse_block(const SetupGeom &cg, const Se
             own[a][sd] = sd == 0 || P[a] + sd == cg.n[a];
         }
     finish_cell<DIM>(o, cc, fid, own, g, S, l4, err);
+}
+
+template <int DIM>
+__device__ __forceinline__ void setup_coarse_block(const SetupGeom &cg, const SetupFine &F, const SetupOut &o,
+                                                   int *err, int bx, int by, int bz) {
+    if (cg.axisym) setup_coarse_cells<DIM, true>(cg, F, o, err, bx, by, bz);
+    else setup_coarse_cells<DIM, false>(cg, F, o, err, bx, by, bz);
 }
 
 template <int DIM>
