@@ -152,7 +152,7 @@ def run_ours(args, rank, world):
     import numpy as np
     import torch
     import torch.distributed as dist
-    from paper_2206_11294_gb300.binding import Solver
+    from paper_2206_11294_gb300.binding import Solver, TILE_SHAPES
 
     dev = env_int("LOCAL_RANK", 0)
     torch.cuda.set_device(dev)
@@ -167,6 +167,14 @@ def run_ours(args, rank, world):
                            x0=T(p.x0), x=T(p.x0)))
         solvers.append(s)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=f"cuda:{dev}")
+    # kernel choices from the library's autotuner (before warm-up, untimed)
+    tunings = {}
+    if not args.no_tune:
+        from paper_2206_11294_gb300.autotune import TuningTable, describe
+        table = TuningTable(None)
+        for p, s, d in zip(probs, solvers, dev_in):
+            s.set_coeffs(d["lam"], d["fa"], d["fk"])
+            tunings[p.name] = describe(table.tune(s, reps=args.tune_reps))
 
     def step(collect):
         for s, d in zip(solvers, dev_in):
@@ -217,10 +225,14 @@ def run_ours(args, rank, world):
     per_launch = SWEEP_BYTES_PER_CELL[(args.precision, dim0)] * c0["smooth_cells"] * sweeps_per_launch
     avg_s = c0["smooth_ms"] / 1e3 / max(1, c0["smooth_launches"])
     achieved = per_launch / avg_s / 1e9 if avg_s > 0 else None
-    fused = args.precision == "mixed" and dim0 == 2
-    kernel = ("k_rbgs_fused2d<float>" if fused else
-              f"k_rbgs_colour<{'double' if args.precision == 'fp64' else 'float'},{dim0}>") \
-        + " on the finest level of " + probs[0].name
+    t0 = solvers[0].tuning()
+    rname = "double" if args.precision == "fp64" else "float"
+    if t0["sweep"][0] == "fused":
+        tx, ty = TILE_SHAPES[t0["tile"][0]]
+        kernel = f"k_rbgs_fused2d<{rname},{tx},{ty}>"
+    else:
+        kernel = f"k_rbgs_colour<{rname},{dim0}>"
+    kernel += " on the finest level of " + probs[0].name
     hbm = {"bound": "hbm", "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "GB/s",
            "frac": (achieved / peak) if achieved else None, "peak_source": peak_kind,
            "algorithmic_bytes_per_launch": per_launch, "avg_launch_us": avg_s * 1e6,
@@ -277,11 +289,12 @@ def run_ours(args, rank, world):
         "warmup": args.warmup, "ms_per_step": tmax * 1e3 / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
         "data": "synthetic (seeded bubble fields; Eqs. 29-34 coefficients)",
-        "config": {"workload": "bubbles16_1024x1024 + axi_512x1024, set-up + FP64 solve to 1e-10 per step",
+        "config": {"workload": "bubbles16_1024x1024 + axi_512x1024, set-up + solve to 1e-10 per step",
                    "cells_per_step": sum(p.grid.N for p in probs), "cycles_per_solve": cycles,
                    "solves_per_s": solves * world / tmax, "precision": args.precision,
                    "cycle": "V(2,2) red-black block GS, exact coarsest solve", "l2": "flushed between steps",
-                   "parallelism": f"replicas x{world}"},
+                   "parallelism": f"replicas x{world}",
+                   "tuning": tunings or "library defaults (--no-tune)"},
         "roofline": roofline,
         "cpu_baseline": cpu,
         "e2e": e2e,
@@ -485,6 +498,8 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="library default kernel choices, no autotuning")
+    ap.add_argument("--tune-reps", type=int, default=5)
     ap.add_argument("--workload", default="bubbles", choices=["bubbles", "batch", "serve", "wall3d"])
     ap.add_argument("--n3d", type=int, default=256)
     ap.add_argument("--batch-count", type=int, default=256)

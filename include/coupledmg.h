@@ -158,8 +158,53 @@ MG_API mg_status mg_set_timing(mg_handle *h, int enable);
 MG_API mg_status mg_counters(const mg_handle *h, long long *launches, double *smooth_ms,
                              long long *smooth_launches, long long *smooth_sweeps, long long *smooth_cells);
 
+/* Kernel choices of a hierarchy, and the autotuner that picks them.  The
+ * paper has no counterpart: every choice computes the same result, bit for
+ * bit (the same per-cell arithmetic in the same order); only the launch
+ * structure differs.
+ *   sweep[l]    level l's red-black sweeps: MG_SWEEP_COLOUR (one launch per
+ *               colour, in place) or MG_SWEEP_FUSED (2D grids only: one launch
+ *               per sweep on tiles staged in shared memory, the red values of
+ *               a one-cell ring recomputed per tile);
+ *   tile[l]     fused tile shape, cells: 0 = 64 x 16, 1 = 32 x 16, 2 = 32 x 8;
+ *   tail_level  the levels from this one to the coarsest run as one kernel on
+ *               a thread-block cluster (smoothing, restriction, coarsest solve,
+ *               prolongation separated by cluster barriers); >= levels: none.
+ *               Allowed from level 1 when at least two levels (and at most 12)
+ *               remain and the level has at most 16384 cells;
+ *   tail_ctas   thread blocks of that cluster: 8, or 16 where the device
+ *               allows non-portable cluster sizes.
+ * Defaults after mg_create: colour sweeps for FP64 cycles, fused 64 x 16 for
+ * the FP32 cycles of mixed precision on 2D grids; the tail from the first
+ * level below the finest with at most 4096 cells, 8 CTAs. */
+#define MG_MAX_LEVELS 32
+enum { MG_SWEEP_COLOUR = 1, MG_SWEEP_FUSED = 2 };
+typedef struct {
+    int levels;                 /* mg_get_tuning: the hierarchy's levels (ignored by mg_set_tuning) */
+    int sweep[MG_MAX_LEVELS];
+    int tile[MG_MAX_LEVELS];
+    int tail_level;
+    int tail_ctas;
+} mg_tuning;
+
+MG_API mg_status mg_get_tuning(const mg_handle *h, mg_tuning *out);
+/* MG_ERR_INVALID_ARG (handle unchanged) for a choice outside the rules above. */
+MG_API mg_status mg_set_tuning(mg_handle *h, const mg_tuning *t);
+
+/* Measures the choices on the handle's own hierarchy and keeps the fastest:
+ * per level, each sweep kernel (and tile shape) over `reps` pairs of sweeps;
+ * then each allowed tail (none, every allowed first level, 8 or 16 CTAs)
+ * over `reps` whole V-cycles.  Each candidate is captured as a CUDA graph and
+ * timed with CUDA events on the handle's stream (best of three replays).
+ * Needs coefficients (MG_ERR_STATE otherwise); overwrites the hierarchy's
+ * scratch state (every level's x, b and right-hand sides), not the
+ * coefficients, so the next mg_solve is unaffected.  Cycles run in the
+ * handle's precision (FP32 for mixed).  out (nullable) receives the chosen
+ * tuning, vcycle_ms (nullable) the chosen V-cycle's time.  Synchronous. */
+MG_API mg_status mg_autotune(mg_handle *h, int reps, mg_tuning *out, double *vcycle_ms);
+
 /* Batched solve of many independent problems in one set of launches
- * (uneven sizes; SURVEY-level workload: many bubble grids per time step).
+ * (uneven sizes, e.g. the many bubble grids of one time step).
  * The problems are handles created and given coefficients as usual; they
  * must share dim, options (nu1, nu2, precision, rtol, max_cycles,
  * inner_cycles), stream and device.  Each V-cycle stage runs as one

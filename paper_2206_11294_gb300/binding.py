@@ -31,7 +31,11 @@ EXPORTS = ["mg_default_options", "mg_workspace_size", "mg_create", "mg_set_coeff
            "mg_apply", "mg_smooth", "mg_residual_norms", "mg_set_device", "mg_levels", "mg_destroy",
            "mg_last_error", "mg_set_timing", "mg_counters", "mg_residual_norms_noalloc",
            "mg_batch_create", "mg_batch_solve", "mg_batch_counters", "mg_batch_destroy", "mg_set_stream",
-           "mg_batch_set_coeffs"]
+           "mg_batch_set_coeffs", "mg_get_tuning", "mg_set_tuning", "mg_autotune"]
+
+MG_MAX_LEVELS = 32
+MG_SWEEP_COLOUR, MG_SWEEP_FUSED = 1, 2
+TILE_SHAPES = [(64, 16), (32, 16), (32, 8)]      # fused tile shapes by index (cells x, y)
 
 
 class MgError(RuntimeError):
@@ -60,6 +64,29 @@ class MgStats(C.Structure):
         return dict(cycles=self.cycles, outer=self.outer, r0=list(self.r0), rfinal=list(self.rfinal),
                     seconds=self.seconds, status=STATUS_NAMES.get(self.status, self.status),
                     levels=self.levels)
+
+
+class MgTuning(C.Structure):
+    _fields_ = [("levels", C.c_int), ("sweep", C.c_int * MG_MAX_LEVELS), ("tile", C.c_int * MG_MAX_LEVELS),
+                ("tail_level", C.c_int), ("tail_ctas", C.c_int)]
+
+    def as_dict(self) -> dict:
+        n = self.levels
+        return dict(levels=n, sweep=["fused" if self.sweep[l] == MG_SWEEP_FUSED else "colour" for l in range(n)],
+                    tile=[int(self.tile[l]) for l in range(n)], tail_level=int(self.tail_level),
+                    tail_ctas=int(self.tail_ctas))
+
+    @staticmethod
+    def from_dict(d: dict) -> "MgTuning":
+        t = MgTuning()
+        t.levels = int(d.get("levels", len(d["sweep"])))
+        for l, s in enumerate(d["sweep"]):
+            t.sweep[l] = MG_SWEEP_FUSED if s in ("fused", MG_SWEEP_FUSED) else MG_SWEEP_COLOUR
+        for l, s in enumerate(d["tile"]):
+            t.tile[l] = int(s)
+        t.tail_level = int(d["tail_level"])
+        t.tail_ctas = int(d["tail_ctas"])
+        return t
 
 
 _lib = None
@@ -101,6 +128,9 @@ def load(path: str = LIB_PATH):
             "mg_batch_set_coeffs": ([P, C.POINTER(P), C.POINTER(P), C.POINTER(P), C.c_int], C.c_int),
             "mg_counters": ([P, C.POINTER(C.c_longlong), C.POINTER(C.c_double), C.POINTER(C.c_longlong),
                              C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)], C.c_int),
+            "mg_get_tuning": ([P, C.POINTER(MgTuning)], C.c_int),
+            "mg_set_tuning": ([P, C.POINTER(MgTuning)], C.c_int),
+            "mg_autotune": ([P, C.c_int, C.POINTER(MgTuning), dp], C.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -321,6 +351,23 @@ class Solver:
         check(self._lib.mg_counters(self._h, C.byref(n), C.byref(ms), C.byref(sl), C.byref(sw), C.byref(sc)))
         return dict(launches=n.value, smooth_ms=ms.value, smooth_launches=sl.value, smooth_sweeps=sw.value,
                     smooth_cells=sc.value)
+
+    def tuning(self) -> dict:
+        """The handle's kernel choices (see mg_tuning in the header)."""
+        t = MgTuning()
+        check(self._lib.mg_get_tuning(self._h, C.byref(t)))
+        return t.as_dict()
+
+    def set_tuning(self, tuning: dict):
+        t = MgTuning.from_dict(tuning)
+        check(self._lib.mg_set_tuning(self._h, C.byref(t)))
+
+    def autotune(self, reps: int = 10):
+        """Runs the library's autotuner on this hierarchy; returns (tuning, V-cycle ms)."""
+        t = MgTuning()
+        ms = C.c_double()
+        check(self._lib.mg_autotune(self._h, int(reps), C.byref(t), C.byref(ms)))
+        return t.as_dict(), ms.value
 
     def levels(self):
         n = C.c_int()

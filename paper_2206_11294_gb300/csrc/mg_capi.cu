@@ -86,6 +86,9 @@ struct mg_handle {
     size_t stage_bytes;
     int nc;                // unknowns of the coarsest level
     int tail_lev;          // first level of the cluster tail (nlev: no tail)
+    int tail_ctas;         // CTAs of the tail's cluster (8, or 16 where allowed)
+    int sweep[kMaxLevels]; // per level: MG_SWEEP_COLOUR or MG_SWEEP_FUSED
+    int tile[kMaxLevels];  // per level: fused tile shape (index into kTileX / kTileY)
     double *Minv, *Mtmp;
     double *Mwork;         // coarse inverse: columns before the transpose (banded path)
     int *piv;              // coarse inverse: pivot rows (banded path)
@@ -234,6 +237,15 @@ void plan(mg_handle *h, char *base, size_t *bytes) {
     for (int l = 1; l < h->nlev; l++)
         if (h->L[l].N <= kTailCells) { h->tail_lev = l; break; }
     if (h->nlev - h->tail_lev < 2 || h->nlev - h->tail_lev > kTailMaxLevels) h->tail_lev = h->nlev;
+    h->tail_ctas = kTailCtas;
+    // Default kernel choices until mg_autotune / mg_set_tuning: FP32 cycles
+    // (mixed precision) sweep fused in 2D; FP64 sweeps are bound by GB300's
+    // FP64 pipe, where the fused kernel's recomputed ring costs more than the
+    // DRAM traffic it saves, so they run as colour launches.
+    for (int l = 0; l < kMaxLevels; l++) {
+        h->sweep[l] = (g.dim == 2 && mixed) ? MG_SWEEP_FUSED : MG_SWEEP_COLOUR;
+        h->tile[l] = 0;
+    }
     long long sumnf = 0;
     for (int a = 0; a < g.dim; a++) sumnf += f.nf[a];
     // lambda, then 1/rho and k of every axis (host-side coefficient intake)
@@ -296,26 +308,32 @@ template <typename R> typename Vec<R>::v2 *xalt_of(const LevelBuf &l);
 template <> double2 *xalt_of<double>(const LevelBuf &l) { return l.xalt; }
 template <> float2 *xalt_of<float>(const LevelBuf &l) { return l.xalt32; }
 
-// Whether sweeps of this precision and dimension run fused.  FP32 (HBM-bound)
-// sweeps run fused in 2D.  FP64 sweeps are bound by GB300's FP64 pipe (2
-// instructions per clock per SM), where the fused kernel's recomputed ring
-// costs more than the DRAM traffic it saves, so they run as colour launches.
+// Whether the batched sweeps of this precision and dimension run fused:
+// FP32 (HBM-bound) sweeps in 2D.
 template <typename R, int DIM> constexpr bool fused_sweeps() { return DIM == 2 && sizeof(R) == 4; }
 
-// `sweeps` red-black sweeps on level l.  Fused: pairs of sweeps run as fused
-// launches x -> xalt -> x; a leftover odd sweep (and every non-fused sweep)
-// runs as two colour launches in place.  The result always ends in x.
+template <typename R, int TX, int TY>
+void launch_fused(const LevelBuf &lb, const Level<R> &v, cudaStream_t s) {
+    const dim3 gf((unsigned)((lb.n[0] + TX - 1) / TX), (unsigned)((lb.n[1] + TY - 1) / TY), 1);
+    typename Vec<R>::v2 *xa = xalt_of<R>(lb);
+    k_rbgs_fused2d<R, TX, TY><<<gf, kBlock, 0, s>>>(v, v.x, xa);
+    k_rbgs_fused2d<R, TX, TY><<<gf, kBlock, 0, s>>>(v, xa, v.x);
+}
+
+// `sweeps` red-black sweeps on level l with the given kernel choice.  Fused
+// (2D only): pairs of sweeps run as fused launches x -> xalt -> x; a leftover
+// odd sweep (and every non-fused sweep) runs as two colour launches in place.
+// The result always ends in x and is the same, bit for bit, for every choice.
 template <typename R, int DIM>
-void enqueue_smooth(const mg_handle *h, cudaStream_t s, int l, int sweeps) {
+void enqueue_sweeps(const mg_handle *h, cudaStream_t s, int l, int sweeps, int kind, int tile) {
     const LevelBuf &lb = h->L[l];
     Level<R> v = view<R>(lb);
     int q = 0;
-    if (fused_sweeps<R, DIM>()) {
-        const dim3 gf((unsigned)((lb.n[0] + kFTX - 1) / kFTX), (unsigned)((lb.n[1] + kFTY - 1) / kFTY), 1);
-        typename Vec<R>::v2 *xa = xalt_of<R>(lb);
+    if (DIM == 2 && kind == MG_SWEEP_FUSED) {
         for (; q + 1 < sweeps; q += 2) {
-            k_rbgs_fused2d<R><<<gf, kBlock, 0, s>>>(v, v.x, xa);
-            k_rbgs_fused2d<R><<<gf, kBlock, 0, s>>>(v, xa, v.x);
+            if (tile == 1) launch_fused<R, kTileX[1], kTileY[1]>(lb, v, s);
+            else if (tile == 2) launch_fused<R, kTileX[2], kTileY[2]>(lb, v, s);
+            else launch_fused<R, kTileX[0], kTileY[0]>(lb, v, s);
             counted(h, 2);
         }
     }
@@ -325,6 +343,11 @@ void enqueue_smooth(const mg_handle *h, cudaStream_t s, int l, int sweeps) {
         k_rbgs_colour<R, DIM><<<gr, kBlock, 0, s>>>(v, 1);
         counted(h, 2);
     }
+}
+
+template <typename R, int DIM>
+void enqueue_smooth(const mg_handle *h, cudaStream_t s, int l, int sweeps) {
+    enqueue_sweeps<R, DIM>(h, s, l, sweeps, h->sweep[l], h->tile[l]);
 }
 
 // Kernel launches and sweeps of one call of enqueue_smooth.
@@ -352,13 +375,13 @@ void enqueue_tail(const mg_handle *h, cudaStream_t s) {
     A.nu2 = h->opt.nu2;
     cudaLaunchConfig_t cfg;
     std::memset(&cfg, 0, sizeof(cfg));
-    cfg.gridDim = dim3(kTailCtas, 1, 1);
+    cfg.gridDim = dim3((unsigned)h->tail_ctas, 1, 1);
     cfg.blockDim = kBlock;
     cfg.dynamicSmemBytes = 0;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = kTailCtas;
+    attr[0].val.clusterDim.x = (unsigned)h->tail_ctas;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
@@ -540,7 +563,7 @@ mg_status accumulate_timing(mg_handle *h) {
     CK(cudaEventElapsedTime(&b, h->ev[2], h->ev[3]));
     h->smooth_ms += (double)a + (double)b;
     long long l1, s1, l2, s2;
-    const bool fused = h->grid.dim == 2 && h->opt.precision == MG_MIXED;
+    const bool fused = h->grid.dim == 2 && h->sweep[0] == MG_SWEEP_FUSED;
     smooth_launches(fused, h->opt.nu1, &l1, &s1);
     smooth_launches(fused, h->opt.nu2, &l2, &s2);
     h->smooth_launches += l1 + l2;
@@ -770,6 +793,139 @@ mg_status check_handle(const mg_handle *h, bool need_coeffs) {
     return MG_OK;
 }
 
+// ---------------------------------------------------------------- tuning
+bool tail_level_ok(const mg_handle *h, int l) {
+    return l >= 1 && h->nlev - l >= 2 && h->nlev - l <= kTailMaxLevels && h->L[l].N <= kTailMaxCells;
+}
+
+// 8 CTAs is a portable cluster size; 16 needs the kernel's opt-in and a
+// device that can place such a cluster.
+template <typename R, int DIM>
+bool tail_ctas_allowed(int ctas) {
+    if (ctas == kTailCtas) return true;
+    if (ctas != 16) return false;
+    if (cudaFuncSetAttribute(k_vcycle_tail<R, DIM>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    cudaLaunchConfig_t cfg;
+    std::memset(&cfg, 0, sizeof(cfg));
+    cfg.gridDim = dim3(16, 1, 1);
+    cfg.blockDim = kBlock;
+    cudaLaunchAttribute a;
+    a.id = cudaLaunchAttributeClusterDimension;
+    a.val.clusterDim.x = 16;
+    a.val.clusterDim.y = 1;
+    a.val.clusterDim.z = 1;
+    cfg.attrs = &a;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, k_vcycle_tail<R, DIM>, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return n > 0;
+}
+
+bool tail_ctas_ok(const mg_handle *h, int ctas) {
+    const bool mixed = h->opt.precision == MG_MIXED;
+    if (h->grid.dim == 2) return mixed ? tail_ctas_allowed<float, 2>(ctas) : tail_ctas_allowed<double, 2>(ctas);
+    return mixed ? tail_ctas_allowed<float, 3>(ctas) : tail_ctas_allowed<double, 3>(ctas);
+}
+
+void drop_graphs(mg_handle *h) {
+    if (h->g64) { cudaGraphExecDestroy(h->g64); h->g64 = nullptr; }
+    if (h->g32) { cudaGraphExecDestroy(h->g32); h->g32 = nullptr; }
+}
+
+// Captures body as a graph and times it: one warm-up replay, then the best of
+// three, with CUDA events on the handle's stream.
+template <typename F>
+mg_status time_graph(mg_handle *h, double *ms, F &&body) {
+    cudaGraphExec_t ex = nullptr;
+    long long kernels = 0;
+    mg_status st = capture(h, &ex, &kernels, body);
+    if (st) return st;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    float best = 1e30f;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e == cudaSuccess) e = cudaGraphLaunch(ex, h->stream);
+    for (int t = 0; t < 3 && e == cudaSuccess; t++) {
+        e = cudaEventRecord(e0, h->stream);
+        if (e == cudaSuccess) e = cudaGraphLaunch(ex, h->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float f = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&f, e0, e1);
+        if (e == cudaSuccess && f < best) best = f;
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaGraphExecDestroy(ex);
+    if (e != cudaSuccess) return fail(MG_ERR_CUDA, std::string("autotune timing: ") + cudaGetErrorString(e));
+    *ms = best;
+    return MG_OK;
+}
+
+template <typename R, int DIM>
+mg_status autotune_impl(mg_handle *h, int reps, double *vcycle_ms) {
+    mg_status st;
+    // sweeps, level by level (the coarsest level is solved, not smoothed)
+    for (int l = 0; l + 1 < h->nlev; l++) {
+        const int ncand = DIM == 2 ? 1 + kTileShapes : 1;
+        double best = 1e30;
+        int kind = MG_SWEEP_COLOUR, tile = 0;
+        for (int c = 0; c < ncand; c++) {
+            const int ck = c == 0 ? MG_SWEEP_COLOUR : MG_SWEEP_FUSED, ct = c == 0 ? 0 : c - 1;
+            double ms = 0.0;
+            st = time_graph(h, &ms, [&](cudaStream_t s) {
+                for (int r = 0; r < reps; r++) enqueue_sweeps<R, DIM>(h, s, l, 2, ck, ct);
+            });
+            if (st) return st;
+            if (ms < best) { best = ms; kind = ck; tile = ct; }
+        }
+        h->sweep[l] = kind;
+        h->tile[l] = tile;
+    }
+    // the cluster tail: none, or each allowed first level and cluster size
+    std::vector<std::pair<int, int>> cand{{h->nlev, kTailCtas}};
+    const bool wide = tail_ctas_allowed<R, DIM>(16);
+    for (int l = 1; l < h->nlev; l++)
+        if (tail_level_ok(h, l)) {
+            cand.push_back({l, kTailCtas});
+            if (wide) cand.push_back({l, 16});
+        }
+    double best = 1e30;
+    std::pair<int, int> pick = cand[0];
+    for (const auto &c : cand) {
+        h->tail_lev = c.first;
+        h->tail_ctas = c.second;
+        double ms = 0.0;
+        st = time_graph(h, &ms, [&](cudaStream_t s) {
+            for (int r = 0; r < reps; r++) enqueue_vcycle<R, DIM>(h, s, 0);
+        });
+        if (st) return st;
+        if (ms < best) { best = ms; pick = c; }
+    }
+    h->tail_lev = pick.first;
+    h->tail_ctas = pick.second;
+    if (vcycle_ms) *vcycle_ms = best / reps;
+    return MG_OK;
+}
+
+void get_tuning(const mg_handle *h, mg_tuning *t) {
+    std::memset(t, 0, sizeof(*t));
+    t->levels = h->nlev;
+    for (int l = 0; l < MG_MAX_LEVELS; l++) {
+        t->sweep[l] = l < h->nlev ? h->sweep[l] : MG_SWEEP_COLOUR;
+        t->tile[l] = l < h->nlev ? h->tile[l] : 0;
+    }
+    t->tail_level = h->tail_lev;
+    t->tail_ctas = h->tail_ctas;
+}
+
 }  // namespace
 
 // ====================================================================== C ABI
@@ -950,6 +1106,69 @@ mg_status mg_residual_norms(mg_handle *h, const double *rhs, const double *x, in
     return sync_norms(h, out);
 }
 
+mg_status mg_get_tuning(const mg_handle *h, mg_tuning *out) {
+    mg_status st = check_handle(h, false);
+    if (st) return st;
+    if (!out) return fail(MG_ERR_INVALID_ARG, "out is NULL");
+    get_tuning(h, out);
+    return MG_OK;
+}
+
+mg_status mg_set_tuning(mg_handle *h, const mg_tuning *t) {
+    mg_status st = check_handle(h, false);
+    if (st) return st;
+    if (!t) return fail(MG_ERR_INVALID_ARG, "tuning is NULL");
+    for (int l = 0; l < h->nlev; l++) {
+        if (t->sweep[l] != MG_SWEEP_COLOUR && t->sweep[l] != MG_SWEEP_FUSED)
+            return fail(MG_ERR_INVALID_ARG, "sweep kind must be MG_SWEEP_COLOUR or MG_SWEEP_FUSED");
+        if (t->sweep[l] == MG_SWEEP_FUSED && h->grid.dim != 2)
+            return fail(MG_ERR_INVALID_ARG, "fused sweeps are for 2D grids");
+        if (t->tile[l] < 0 || t->tile[l] >= kTileShapes) return fail(MG_ERR_INVALID_ARG, "tile shape out of range");
+    }
+    const bool no_tail = t->tail_level >= h->nlev;
+    if (!no_tail && !tail_level_ok(h, t->tail_level))
+        return fail(MG_ERR_INVALID_ARG, "tail level must be >= 1, leave 2 to 12 levels and have <= 16384 cells");
+    DeviceGuard dg(h->device);
+    if (!no_tail && !tail_ctas_ok(h, t->tail_ctas))
+        return fail(MG_ERR_INVALID_ARG, "tail cluster size must be 8, or 16 where the device allows it");
+    CK(cudaStreamSynchronize(h->stream));
+    for (int l = 0; l < h->nlev; l++) {
+        h->sweep[l] = t->sweep[l];
+        h->tile[l] = t->tile[l];
+    }
+    h->tail_lev = no_tail ? h->nlev : t->tail_level;
+    h->tail_ctas = no_tail ? kTailCtas : t->tail_ctas;
+    drop_graphs(h);
+    return MG_OK;
+}
+
+mg_status mg_autotune(mg_handle *h, int reps, mg_tuning *out, double *vcycle_ms) {
+    mg_status st = check_handle(h, true);
+    if (st) return st;
+    if (reps < 1 || reps > 1000) return fail(MG_ERR_INVALID_ARG, "reps must be in [1, 1000]");
+    DeviceGuard dg(h->device);
+    CK(cudaStreamSynchronize(h->stream));
+    // scratch state to zeros: every candidate then runs on the same finite data
+    for (int l = 0; l < h->nlev; l++) {
+        const LevelBuf &b = h->L[l];
+        void *ptrs[8] = {b.x, b.b, b.bt, b.xalt, b.x32, b.b32, b.bt32, b.xalt32};
+        const size_t sz[8] = {16, 16, 16, 16, 8, 8, 8, 8};
+        for (int q = 0; q < 8; q++)
+            if (ptrs[q]) CK(cudaMemsetAsync(ptrs[q], 0, sz[q] * (size_t)b.N, h->stream));
+    }
+    const int timing = h->timing;
+    h->timing = 0;
+    const bool mixed = h->opt.precision == MG_MIXED;
+    if (h->grid.dim == 2) st = mixed ? autotune_impl<float, 2>(h, reps, vcycle_ms) : autotune_impl<double, 2>(h, reps, vcycle_ms);
+    else st = mixed ? autotune_impl<float, 3>(h, reps, vcycle_ms) : autotune_impl<double, 3>(h, reps, vcycle_ms);
+    h->timing = timing;
+    drop_graphs(h);
+    CK(cudaStreamSynchronize(h->stream));
+    if (st) return st;
+    if (out) get_tuning(h, out);
+    return MG_OK;
+}
+
 mg_status mg_set_timing(mg_handle *h, int enable) {
     mg_status st = check_handle(h, false);
     if (st) return st;
@@ -958,8 +1177,7 @@ mg_status mg_set_timing(mg_handle *h, int enable) {
     if (enable && !h->ev[0])
         for (int q = 0; q < 4; q++) CK(cudaEventCreate(&h->ev[q]));
     // re-capture the cycle graphs with (or without) the event nodes
-    if (h->g64) { cudaGraphExecDestroy(h->g64); h->g64 = nullptr; }
-    if (h->g32) { cudaGraphExecDestroy(h->g32); h->g32 = nullptr; }
+    drop_graphs(h);
     h->timing = enable ? 1 : 0;
     h->enq = 0;
     h->smooth_ms = 0.0;

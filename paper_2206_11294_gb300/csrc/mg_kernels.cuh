@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(kBX * kBY) k_rbgs_colour(Level<R> L, int colou
 
 // ---------------------------------------------------------------------------
 // Fused 2D sweep: one launch does a whole red-black sweep (red, then black)
-// from xin to xout.  A CTA owns a kFTX x kFTY tile.  It stages xin with a
+// from xin to xout.  A CTA owns a TX x TY tile.  It stages xin with a
 // halo of 2 in shared memory, updates the red cells of the tile and of a
 // one-cell ring around it (the ring's red values are what the tile's black
 // cells see; neighbouring CTAs compute the same values), then the tile's
@@ -111,10 +111,15 @@ __global__ void __launch_bounds__(kBX * kBY) k_rbgs_colour(Level<R> L, int colou
 // buffers) keeps CTAs from seeing each other's updates.  Same arithmetic as
 // two k_rbgs_colour launches.
 // ---------------------------------------------------------------------------
-constexpr int kFTX = 64, kFTY = 16;
+constexpr int kFTX = 64, kFTY = 16;   // tile of the batched kernels and the default
 
-template <typename R>
-__device__ __forceinline__ void offdiag_tile2d(const Level<R> &L, const typename Vec<R>::v2 (*xs)[kFTX + 4], int lx,
+// Tile shapes a handle can select per level (index = mg_tuning tile value).
+constexpr int kTileShapes = 3;
+constexpr int kTileX[kTileShapes] = {64, 32, 32};
+constexpr int kTileY[kTileShapes] = {16, 16, 8};
+
+template <typename R, int TX>
+__device__ __forceinline__ void offdiag_tile2d(const Level<R> &L, const typename Vec<R>::v2 (*xs)[TX + 4], int lx,
                                                int ly, int i, int j, long long c, R &sT, R &sp) {
     using V2 = typename Vec<R>::v2;
     const int n0 = L.n0, n1 = L.n1;
@@ -128,28 +133,28 @@ __device__ __forceinline__ void offdiag_tile2d(const Level<R> &L, const typename
     if (j < n1 - 1) { V2 g = ldg2(L.G1 + f1 + n0); V2 u = xs[ly + 1][lx]; sT += g.x * u.x; sp += g.y * u.y; }
 }
 
-// Tile (bx, by) of the launch geometry (ceil(n0/64), ceil(n1/16)); shared with
+// Tile (bx, by) of the launch geometry (ceil(n0/TX), ceil(n1/TY)); shared with
 // the batched kernels (which call it repeatedly: it starts with a barrier so
 // the previous tile's readers are done with the shared stage).
-template <typename R>
+template <typename R, int TX = kFTX, int TY = kFTY>
 __device__ __forceinline__ void rbgs_fused2d_block(const Level<R> &L, const typename Vec<R>::v2 *__restrict__ xin,
                                                    typename Vec<R>::v2 *__restrict__ xout, int bx, int by) {
     using V2 = typename Vec<R>::v2;
-    __shared__ V2 xs[kFTY + 4][kFTX + 4];
+    __shared__ V2 xs[TY + 4][TX + 4];
     const int n0 = L.n0, n1 = L.n1;
-    const int i0 = bx * kFTX, j0 = by * kFTY;
+    const int i0 = bx * TX, j0 = by * TY;
     const int tid = threadIdx.x + blockDim.x * threadIdx.y;
     __syncthreads();
     // stage xin, halo 2 (cells beyond the grid are never read)
-    for (int q = tid; q < (kFTY + 4) * (kFTX + 4); q += 256) {
-        const int ly = q / (kFTX + 4), lx = q - ly * (kFTX + 4);
+    for (int q = tid; q < (TY + 4) * (TX + 4); q += 256) {
+        const int ly = q / (TX + 4), lx = q - ly * (TX + 4);
         const int gi = i0 + lx - 2, gj = j0 + ly - 2;
         if (gi >= 0 && gi < n0 && gj >= 0 && gj < n1) xs[ly][lx] = ldg2(xin + (long long)gj * n0 + gi);
     }
     __syncthreads();
     // red cells ((i + j) even) of the tile and its one-cell ring
-    constexpr int kRedPerRow = (kFTX + 2) / 2;
-    for (int q = tid; q < (kFTY + 2) * kRedPerRow; q += 256) {
+    constexpr int kRedPerRow = (TX + 2) / 2;
+    for (int q = tid; q < (TY + 2) * kRedPerRow; q += 256) {
         const int ry = q / kRedPerRow, rx = q - ry * kRedPerRow;
         const int gj = j0 - 1 + ry;
         const int gi = i0 - 1 + 2 * rx + ((i0 - 1 + gj) & 1);
@@ -157,13 +162,13 @@ __device__ __forceinline__ void rbgs_fused2d_block(const Level<R> &L, const type
         const int lx = gi - i0 + 2, ly = gj - j0 + 2;
         const long long c = (long long)gj * n0 + gi;
         R sT, sp;
-        offdiag_tile2d<R>(L, xs, lx, ly, gi, gj, c, sT, sp);
+        offdiag_tile2d<R, TX>(L, xs, lx, ly, gi, gj, c, sT, sp);
         xs[ly][lx] = gs_update<R>(L, c, sT, sp);
     }
     __syncthreads();
     // black cells of the tile; each thread writes a pair of adjacent cells
-    constexpr int kPairs = kFTX / 2;
-    for (int q = tid; q < kFTY * kPairs; q += 256) {
+    constexpr int kPairs = TX / 2;
+    for (int q = tid; q < TY * kPairs; q += 256) {
         const int ty = q / kPairs, px = q - ty * kPairs;
         const int gj = j0 + ty;
         if (gj >= n1) continue;
@@ -176,7 +181,7 @@ __device__ __forceinline__ void rbgs_fused2d_block(const Level<R> &L, const type
             V2 v = xs[ly][lx];
             if ((gi + gj) & 1) {
                 R sT, sp;
-                offdiag_tile2d<R>(L, xs, lx, ly, gi, gj, c, sT, sp);
+                offdiag_tile2d<R, TX>(L, xs, lx, ly, gi, gj, c, sT, sp);
                 v = gs_update<R>(L, c, sT, sp);
             }
             xout[c] = v;
@@ -184,12 +189,12 @@ __device__ __forceinline__ void rbgs_fused2d_block(const Level<R> &L, const type
     }
 }
 
-// 8 resident blocks per SM (at most 32 registers): the FP32 sweep is bound by
-// memory latency, so occupancy is what feeds it.
-template <typename R>
-__global__ void __launch_bounds__(256, 8) k_rbgs_fused2d(Level<R> L, const typename Vec<R>::v2 *__restrict__ xin,
-                                                      typename Vec<R>::v2 *__restrict__ xout) {
-    rbgs_fused2d_block<R>(L, xin, xout, blockIdx.x, blockIdx.y);
+// FP32: 8 resident blocks per SM (at most 32 registers): the sweep is bound by
+// memory latency, so occupancy is what feeds it.  FP64: 4.
+template <typename R, int TX, int TY>
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 8 : 4)
+    k_rbgs_fused2d(Level<R> L, const typename Vec<R>::v2 *__restrict__ xin, typename Vec<R>::v2 *__restrict__ xout) {
+    rbgs_fused2d_block<R, TX, TY>(L, xin, xout, blockIdx.x, blockIdx.y);
 }
 
 // ---------------------------------------------------------------------------
@@ -1203,6 +1208,7 @@ __global__ void k_transpose(const double *__restrict__ W, double *__restrict__ M
 constexpr int kTailCells = 4096;
 constexpr int kTailMaxLevels = 12;
 constexpr int kTailCtas = 8;      // CTAs of the cluster (portable cluster size)
+constexpr int kTailMaxCells = 16384;   // largest first tail level a tuning may choose
 
 template <typename R>
 struct TailArgs {

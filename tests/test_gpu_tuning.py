@@ -1,0 +1,153 @@
+"""Kernel choices (mg_set_tuning) and the native autotuner (mg_autotune).
+
+Every choice -- colour or fused sweeps with any tile shape per level, the
+cluster tail from any allowed level on 8 or 16 CTAs, or none -- runs the same
+per-cell arithmetic in the same order, so solves must agree bit for bit and
+stop after the same number of cycles."""
+import numpy as np
+import pytest
+
+from paper_2206_11294_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+def _problems():
+    W, D, A = I.BC_WALL, I.BC_DIRICHLET, I.BC_AXIS
+    return {
+        "2d": I.random_coeff_problem(I.Grid(dim=2, axisym=0, n=(192, 128, 1), h=1e-4, bc=((W, D), (D, W), (0, 0)),
+                                            bcT=((0, 300), (300, 0), (0, 0)), bcp=((0, 1e5), (1e5, 0), (0, 0))),
+                                     seed=71, dt=1e-5),
+        "axi": I.bubble_axi(nr=64, nz=128),
+        "3d": I.random_coeff_problem(I.Grid(dim=3, axisym=0, n=(64, 32, 32), h=1e-4, bc=((W, W), (W, W), (W, D)),
+                                            bcT=((0, 0), (0, 0), (0, 300)), bcp=((0, 0), (0, 0), (0, 1e5))),
+                                     seed=72, dt=1e-5),
+    }
+
+
+PROBS = _problems()
+
+
+def _solve(p, tuning=None, **kw):
+    from paper_2206_11294_gb300.binding import Solver
+    s = Solver(p.grid, rtol=1e-10, max_cycles=60, **kw)
+    s.set_coeffs(p.lam, p.fa, p.fk)
+    if tuning is not None:
+        s.set_tuning(tuning)
+    x = p.x0.copy()
+    st = s.solve(p.b, x)
+    return s, x, st
+
+
+def _variants(s):
+    """Explicit tunings covering every kind of choice the hierarchy allows."""
+    base = s.tuning()
+    n = base["levels"]
+    dim = s.grid.dim
+    out = []
+    colour = dict(base, sweep=["colour"] * n, tile=[0] * n, tail_level=n, tail_ctas=8)
+    out.append(colour)
+    if dim == 2:
+        for t in range(3):
+            out.append(dict(colour, sweep=["fused"] * n, tile=[t] * n))
+        out.append(dict(colour, sweep=["fused" if l % 2 else "colour" for l in range(n)],
+                        tile=[l % 3 for l in range(n)]))
+    sizes = s.levels()
+    for l in range(1, n - 1):
+        cells = int(np.prod(sizes[l]))
+        if n - l <= 12 and cells <= 16384:
+            for ctas in (8, 16):
+                out.append(dict(out[-1] if dim == 2 else colour, tail_level=l, tail_ctas=ctas))
+    return out
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("name", list(PROBS))
+def test_every_choice_gives_identical_results(torch_cuda, name, precision):
+    from paper_2206_11294_gb300.binding import MgError
+    p = PROBS[name]
+    s0, x0, st0 = _solve(p, precision=precision)
+    tried = 0
+    for v in _variants(s0):
+        try:
+            s, x, st = _solve(p, tuning=v, precision=precision)
+        except MgError as e:            # 16-CTA clusters where the device does not allow them
+            assert v["tail_ctas"] == 16 and "cluster size" in str(e)
+            continue
+        assert s.tuning()["sweep"] == v["sweep"]
+        assert st["cycles"] == st0["cycles"], v
+        assert np.array_equal(x, x0), v
+        tried += 1
+        s.close()
+    assert tried >= 2
+    s0.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("name", ["2d", "3d"])
+def test_autotune_picks_valid_choice_and_keeps_results(torch_cuda, name, precision):
+    p = PROBS[name]
+    s0, x0, st0 = _solve(p, precision=precision)
+    tuning, ms = s0.autotune(reps=3)
+    assert ms > 0
+    n = len(s0.levels())
+    assert tuning["levels"] == n
+    assert all(k in ("colour", "fused") for k in tuning["sweep"])
+    if p.grid.dim == 3:
+        assert set(tuning["sweep"]) == {"colour"}
+    assert tuning["tail_level"] >= n or 1 <= tuning["tail_level"] <= n - 2
+    assert tuning["tail_ctas"] in (8, 16)
+    assert s0.tuning() == tuning
+    x = p.x0.copy()
+    st = s0.solve(p.b, x)                     # scratch overwritten by the tuner: same solve
+    assert st["cycles"] == st0["cycles"]
+    assert np.array_equal(x, x0)
+    s0.close()
+
+
+def test_set_tuning_rejects_bad_choices(torch_cuda):
+    from paper_2206_11294_gb300.binding import MgError, MG_ERR_INVALID_ARG
+    s3, _, _ = _solve(PROBS["3d"])
+    s2, _, _ = _solve(PROBS["2d"])
+    for s, mutate in [(s3, lambda t: t["sweep"].__setitem__(0, "fused")),
+                      (s2, lambda t: t["tile"].__setitem__(1, 3)),
+                      (s2, lambda t: t.__setitem__("tail_level", 0)),
+                      (s2, lambda t: t.__setitem__("tail_level", t["levels"] - 1)),
+                      (s2, lambda t: t.update(tail_level=1, tail_ctas=12)),
+                      (s2, lambda t: t.update(tail_level=1))]:      # level 1 of 192x128 has 6144 cells: allowed
+        before = s.tuning()
+        t = dict(before, sweep=list(before["sweep"]), tile=list(before["tile"]))
+        mutate(t)
+        if t.get("tail_level") == 1 and t.get("tail_ctas") == before["tail_ctas"]:
+            s.set_tuning(t)                   # the valid one goes through
+            assert s.tuning()["tail_level"] == 1
+            s.set_tuning(before)
+            continue
+        with pytest.raises(MgError) as e:
+            s.set_tuning(t)
+        assert e.value.status == MG_ERR_INVALID_ARG
+        assert s.tuning() == before
+    s2.close()
+    s3.close()
+
+
+def test_table_reuses_measurement(torch_cuda):
+    from paper_2206_11294_gb300.autotune import TuningTable
+    p = PROBS["2d"]
+    table = TuningTable(None)
+    s1, _, _ = _solve(p)
+    t1 = table.tune(s1, reps=2)
+    s2, _, _ = _solve(p)
+    t2 = table.tune(s2, reps=2)
+    assert table.measured == 1 and table.reused == 1
+    assert t2 == t1 and s2.tuning() == t1
+    s1.close()
+    s2.close()
