@@ -326,6 +326,23 @@ def run_batch(args):
         prec = "mixed" if mode == "batched_mixed" else "fp64"
         solvers = [Solver(p.grid, precision=prec, rtol=1e-10, max_cycles=60, stream=stream) for p in probs]
         batch = Batch(solvers) if mode == "batched_mixed" else None
+        # kernel choices from the library's autotuner (untimed): the batch's own
+        # search, or the per-hierarchy table (equal shapes measured once)
+        tuned = None
+        if not args.no_tune:
+            from paper_2206_11294_gb300.autotune import TuningTable
+            if batch is not None:
+                batch.set_coeffs([d["lam"] for d in dev], [d["fa"] for d in dev], [d["fk"] for d in dev])
+                bt, bms = batch.autotune(reps=args.tune_reps)
+                tuned = {"blocks_per_sm": bt["blocks_per_sm"],
+                         "sweeps": ",".join("C" if s == "colour" else f"F{t}" for s, t in zip(bt["sweep"], bt["tile"])),
+                         "cycle_ms": bms}
+            else:
+                table = TuningTable(None)
+                for s, d in zip(solvers, dev):
+                    s.set_coeffs(d["lam"], d["fa"], d["fk"])
+                    table.tune(s, reps=args.tune_reps)
+                tuned = {"hierarchies_measured": table.measured, "reused": table.reused}
 
         def step(stats):
             for d in dev:
@@ -352,7 +369,8 @@ def run_batch(args):
         cyc = [s["cycles"] for s in st[: len(probs)]]
         out[mode] = {"solves_per_s": len(st) / secs, "ms_per_step": secs * 1e3 / args.steps,
                      "mcell_vcycles_per_s": sum(p.grid.N * c for p, c in zip(probs, cyc)) * args.steps / secs / 1e6,
-                     "cycles_mean": float(np.mean(cyc)), "launches": batch.launches() if batch else None}
+                     "cycles_mean": float(np.mean(cyc)), "launches": batch.launches() if batch else None,
+                     "tuning": tuned}
         if batch is not None:
             batch.close()
         for s in solvers:

@@ -231,6 +231,30 @@ MG_API mg_status mg_batch_set_coeffs(mg_batch *b, const double *const *lambda, c
 /* Kernels launched by this batch since creation (graph nodes per replay). */
 MG_API mg_status mg_batch_counters(const mg_batch *b, long long *launches);
 
+/* Kernel choices of a batch (no counterpart in the paper; results are the
+ * same, bit for bit, for every choice):
+ *   sweep[d], tile[d]  the sweeps of every problem's level d, as mg_tuning's;
+ *   blocks_per_sm      persistent grid of every batched kernel: at most this
+ *                      many blocks per SM (1..32), each looping over the
+ *                      stage's table of (problem, tile) entries.
+ * Defaults: fused 64 x 16 for the FP32 cycles of mixed precision in 2D,
+ * colour otherwise; 8 blocks per SM.  mg_batch_autotune measures, over all
+ * problems at once, each sweep choice per depth (`reps` pairs of sweeps) and
+ * then each grid size (`reps` V-cycles), each captured as a CUDA graph and
+ * timed with CUDA events (best of three), and keeps the fastest.  Needs the
+ * problems' coefficients (MG_ERR_STATE); overwrites scratch state only.
+ * out and cycle_ms (time of one V-cycle of the whole batch) are nullable. */
+typedef struct {
+    int depths;                 /* mg_batch_get_tuning: levels of the deepest problem */
+    int sweep[MG_MAX_LEVELS];
+    int tile[MG_MAX_LEVELS];
+    int blocks_per_sm;
+} mg_batch_tuning;
+
+MG_API mg_status mg_batch_get_tuning(const mg_batch *b, mg_batch_tuning *out);
+MG_API mg_status mg_batch_set_tuning(mg_batch *b, const mg_batch_tuning *t);
+MG_API mg_status mg_batch_autotune(mg_batch *b, int reps, mg_batch_tuning *out, double *cycle_ms);
+
 MG_API mg_status mg_batch_destroy(mg_batch *b);
 
 /* Allocation-free stopping norms (the paper has no counterpart: this is a

@@ -31,7 +31,8 @@ EXPORTS = ["mg_default_options", "mg_workspace_size", "mg_create", "mg_set_coeff
            "mg_apply", "mg_smooth", "mg_residual_norms", "mg_set_device", "mg_levels", "mg_destroy",
            "mg_last_error", "mg_set_timing", "mg_counters", "mg_residual_norms_noalloc",
            "mg_batch_create", "mg_batch_solve", "mg_batch_counters", "mg_batch_destroy", "mg_set_stream",
-           "mg_batch_set_coeffs", "mg_get_tuning", "mg_set_tuning", "mg_autotune"]
+           "mg_batch_set_coeffs", "mg_get_tuning", "mg_set_tuning", "mg_autotune", "mg_batch_get_tuning",
+           "mg_batch_set_tuning", "mg_batch_autotune"]
 
 MG_MAX_LEVELS = 32
 MG_SWEEP_COLOUR, MG_SWEEP_FUSED = 1, 2
@@ -89,6 +90,27 @@ class MgTuning(C.Structure):
         return t
 
 
+class MgBatchTuning(C.Structure):
+    _fields_ = [("depths", C.c_int), ("sweep", C.c_int * MG_MAX_LEVELS), ("tile", C.c_int * MG_MAX_LEVELS),
+                ("blocks_per_sm", C.c_int)]
+
+    def as_dict(self) -> dict:
+        n = self.depths
+        return dict(depths=n, sweep=["fused" if self.sweep[d] == MG_SWEEP_FUSED else "colour" for d in range(n)],
+                    tile=[int(self.tile[d]) for d in range(n)], blocks_per_sm=int(self.blocks_per_sm))
+
+    @staticmethod
+    def from_dict(d: dict) -> "MgBatchTuning":
+        t = MgBatchTuning()
+        t.depths = int(d.get("depths", len(d["sweep"])))
+        for l, s in enumerate(d["sweep"]):
+            t.sweep[l] = MG_SWEEP_FUSED if s in ("fused", MG_SWEEP_FUSED) else MG_SWEEP_COLOUR
+        for l, s in enumerate(d["tile"]):
+            t.tile[l] = int(s)
+        t.blocks_per_sm = int(d["blocks_per_sm"])
+        return t
+
+
 _lib = None
 _lock = threading.Lock()
 
@@ -131,6 +153,9 @@ def load(path: str = LIB_PATH):
             "mg_get_tuning": ([P, C.POINTER(MgTuning)], C.c_int),
             "mg_set_tuning": ([P, C.POINTER(MgTuning)], C.c_int),
             "mg_autotune": ([P, C.c_int, C.POINTER(MgTuning), dp], C.c_int),
+            "mg_batch_get_tuning": ([P, C.POINTER(MgBatchTuning)], C.c_int),
+            "mg_batch_set_tuning": ([P, C.POINTER(MgBatchTuning)], C.c_int),
+            "mg_batch_autotune": ([P, C.c_int, C.POINTER(MgBatchTuning), dp], C.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -451,6 +476,22 @@ class Batch:
         allow = (MG_OK, MG_ERR_NOT_CONVERGED) if allow_not_converged else (MG_OK,)
         check(self._lib.mg_batch_solve(self._b, pb, px, int(dev), st), allow)
         return [st[q].as_dict() for q in range(n)]
+
+    def tuning(self) -> dict:
+        t = MgBatchTuning()
+        check(self._lib.mg_batch_get_tuning(self._b, C.byref(t)))
+        return t.as_dict()
+
+    def set_tuning(self, tuning: dict):
+        t = MgBatchTuning.from_dict(tuning)
+        check(self._lib.mg_batch_set_tuning(self._b, C.byref(t)))
+
+    def autotune(self, reps: int = 5):
+        """The library's batch autotuner; returns (tuning, ms of one V-cycle of the whole batch)."""
+        t = MgBatchTuning()
+        ms = C.c_double()
+        check(self._lib.mg_batch_autotune(self._b, int(reps), C.byref(t), C.byref(ms)))
+        return t.as_dict(), ms.value
 
     def launches(self) -> int:
         n = C.c_longlong()

@@ -62,8 +62,7 @@ struct BState {                 // per-problem solve state, device side
 };
 
 constexpr int kBatchThreads = 256;
-constexpr int kBatchBlocksPerSM = 8;
-constexpr int kSMs = 152;
+constexpr int kBatchBlocksPerSM = 8;    // default persistent blocks per SM
 
 template <typename R> __device__ __forceinline__ const Level<R> &pick(const BLevel &L);
 template <> __device__ __forceinline__ const Level<double> &pick<double>(const BLevel &L) { return L.d; }
@@ -88,20 +87,20 @@ __global__ void __launch_bounds__(kBatchThreads) kb_rbgs_colour(const BLevel *__
     }
 }
 
-template <typename R>
-__global__ void __launch_bounds__(kBatchThreads, 8) kb_rbgs_fused2d(const BLevel *__restrict__ lv,
-                                                                 const BState *__restrict__ st,
-                                                                 const int2 *__restrict__ tab, int n, int to_alt) {
+template <typename R, int TX, int TY>
+__global__ void __launch_bounds__(kBatchThreads, sizeof(R) == 4 ? 8 : 4)
+    kb_rbgs_fused2d(const BLevel *__restrict__ lv, const BState *__restrict__ st, const int2 *__restrict__ tab, int n,
+                    int to_alt) {
     for (int v = blockIdx.x; v < n; v += gridDim.x) {
         const int2 e = tab[v];
         const BLevel &B = lv[e.x];
         if (!st[B.problem].active) continue;
         const Level<R> L = pick<R>(B);
         typename Vec<R>::v2 *xa = pick_alt<R>(B);
-        const int gx = (L.n0 + kFTX - 1) / kFTX;
+        const int gx = (L.n0 + TX - 1) / TX;
         const int bx = e.y % gx, by = e.y / gx;
-        if (to_alt) rbgs_fused2d_block<R>(L, L.x, xa, bx, by);
-        else rbgs_fused2d_block<R>(L, xa, L.x, bx, by);
+        if (to_alt) rbgs_fused2d_block<R, TX, TY>(L, L.x, xa, bx, by);
+        else rbgs_fused2d_block<R, TX, TY>(L, xa, L.x, bx, by);
     }
 }
 
@@ -433,7 +432,11 @@ struct mg_batch {
     int *active_h;                    // pinned
     int2 *tabs;
     // table slices: {offset, count}
-    std::vector<std::pair<long long, int>> colour, fused, restr, prolong;
+    std::vector<std::pair<long long, int>> colour, restr, prolong;
+    std::vector<std::pair<long long, int>> fusedt[kTileShapes];   // per tile shape, per depth
+    // kernel choices (mg_batch_set_tuning): per depth, and the persistent grid
+    int bsweep[kMaxLevels], btile[kMaxLevels];
+    int blocks_per_sm, sms;
     std::pair<long long, int> norm, coarse, cells0, cells0g;   // cells0g: level-0 cell grids
     cudaGraphExec_t graph;
     long long graph_kernels;
@@ -456,9 +459,18 @@ struct mg_batch {
 
 namespace {
 
-unsigned batch_grid(int n) {
-    const int cap = kSMs * kBatchBlocksPerSM;
+// Persistent grid: at most blocks_per_sm blocks per SM, each looping over the table.
+unsigned batch_grid(const mg_batch *b, int n) {
+    const int cap = b->sms * b->blocks_per_sm;
     return (unsigned)std::max(1, std::min(n, cap));
+}
+
+template <typename R, int TX, int TY>
+void b_fused_pair(mg_batch *b, cudaStream_t s, int d, int t) {
+    const int2 *ft = b->tabs + b->fusedt[t][d].first;
+    const int nf = b->fusedt[t][d].second;
+    kb_rbgs_fused2d<R, TX, TY><<<batch_grid(b, nf), kBlock, 0, s>>>(b->lv, b->st, ft, nf, 1);
+    kb_rbgs_fused2d<R, TX, TY><<<batch_grid(b, nf), kBlock, 0, s>>>(b->lv, b->st, ft, nf, 0);
 }
 
 template <typename R, int DIM>
@@ -466,18 +478,18 @@ void b_smooth(mg_batch *b, cudaStream_t s, int d, int sweeps) {
     const int2 *ct = b->tabs + b->colour[d].first;
     const int nc = b->colour[d].second;
     int q = 0;
-    if (fused_sweeps<R, DIM>()) {
-        const int2 *ft = b->tabs + b->fused[d].first;
-        const int nf = b->fused[d].second;
+    if (DIM == 2 && b->bsweep[d] == MG_SWEEP_FUSED) {
+        const int t = b->btile[d];
         for (; q + 1 < sweeps; q += 2) {
-            kb_rbgs_fused2d<R><<<batch_grid(nf), kBlock, 0, s>>>(b->lv, b->st, ft, nf, 1);
-            kb_rbgs_fused2d<R><<<batch_grid(nf), kBlock, 0, s>>>(b->lv, b->st, ft, nf, 0);
+            if (t == 1) b_fused_pair<R, kTileX[1], kTileY[1]>(b, s, d, 1);
+            else if (t == 2) b_fused_pair<R, kTileX[2], kTileY[2]>(b, s, d, 2);
+            else b_fused_pair<R, kTileX[0], kTileY[0]>(b, s, d, 0);
             b->launches += 2;
         }
     }
     for (; q < sweeps; q++) {
-        kb_rbgs_colour<R, DIM><<<batch_grid(nc), kBlock, 0, s>>>(b->lv, b->st, ct, nc, 0);
-        kb_rbgs_colour<R, DIM><<<batch_grid(nc), kBlock, 0, s>>>(b->lv, b->st, ct, nc, 1);
+        kb_rbgs_colour<R, DIM><<<batch_grid(b, nc), kBlock, 0, s>>>(b->lv, b->st, ct, nc, 0);
+        kb_rbgs_colour<R, DIM><<<batch_grid(b, nc), kBlock, 0, s>>>(b->lv, b->st, ct, nc, 1);
         b->launches += 2;
     }
 }
@@ -488,17 +500,17 @@ void b_vcycle(mg_batch *b, cudaStream_t s) {
         if (b->colour[d].second == 0) continue;
         b_smooth<R, DIM>(b, s, d, b->opt.nu1);
         const int nr = b->restr[d].second;
-        kb_restrict<R, DIM><<<batch_grid(nr), kBlock, 0, s>>>(b->lv, b->st, b->tabs + b->restr[d].first, nr,
+        kb_restrict<R, DIM><<<batch_grid(b, nr), kBlock, 0, s>>>(b->lv, b->st, b->tabs + b->restr[d].first, nr,
                                                               b->opt.nu1 > 0);
         b->launches++;
     }
     const int ncs = b->coarse.second;
-    kb_coarse<R><<<batch_grid(ncs), kBatchThreads, 0, s>>>(b->lv, b->pr, b->st, b->tabs + b->coarse.first, ncs);
+    kb_coarse<R><<<batch_grid(b, ncs), kBatchThreads, 0, s>>>(b->lv, b->pr, b->st, b->tabs + b->coarse.first, ncs);
     b->launches++;
     for (int d = b->dmax - 2; d >= 0; d--) {
         if (b->colour[d].second == 0) continue;
         const int np = b->prolong[d].second;
-        kb_prolong<R, DIM><<<batch_grid(np), kBlock, 0, s>>>(b->lv, b->st, b->tabs + b->prolong[d].first, np);
+        kb_prolong<R, DIM><<<batch_grid(b, np), kBlock, 0, s>>>(b->lv, b->st, b->tabs + b->prolong[d].first, np);
         b->launches++;
         b_smooth<R, DIM>(b, s, d, b->opt.nu2);
     }
@@ -509,14 +521,103 @@ void b_norm(mg_batch *b, cudaStream_t s, int initial) {
     cudaMemsetAsync(b->active_count, 0, sizeof(int), s);
     const int n = b->norm.second;
     if (b->opt.precision == MG_FP64)
-        kb_norm<DIM><<<batch_grid(n), kBlock, 0, s>>>(b->lv, b->pr, b->st, b->tabs + b->norm.first, n, initial,
+        kb_norm<DIM><<<batch_grid(b, n), kBlock, 0, s>>>(b->lv, b->pr, b->st, b->tabs + b->norm.first, n, initial,
                                                       b->opt.nu2 > 0, b->opt.rtol, b->opt.max_cycles,
                                                       b->active_count);
     else
-        kb_residual64<DIM><<<batch_grid(n), kBlock, 0, s>>>(b->lv, b->pr, b->st, b->tabs + b->norm.first, n, initial,
+        kb_residual64<DIM><<<batch_grid(b, n), kBlock, 0, s>>>(b->lv, b->pr, b->st, b->tabs + b->norm.first, n, initial,
                                                             b->opt.rtol, b->opt.max_cycles, b->active_count);
     b->launches++;
     cudaMemcpyAsync(b->active_h, b->active_count, sizeof(int), cudaMemcpyDeviceToHost, s);
+}
+
+// Captures body on the first handle's private stream and times the graph on
+// the batch's stream: one warm-up replay, then the best of three.
+template <typename F>
+mg_status b_time_graph(mg_batch *b, double *ms, F &&body) {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t ex = nullptr;
+    cudaStream_t cs = b->h[0]->cap;
+    CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    const long long before = b->launches;
+    body(cs);
+    b->launches = before;
+    cudaError_t e = cudaStreamEndCapture(cs, &graph);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&ex, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return fail(MG_ERR_CUDA, std::string("batch autotune capture: ") + cudaGetErrorString(e));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    float best = 1e30f;
+    e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e == cudaSuccess) e = cudaGraphLaunch(ex, b->stream);
+    for (int t = 0; t < 3 && e == cudaSuccess; t++) {
+        e = cudaEventRecord(e0, b->stream);
+        if (e == cudaSuccess) e = cudaGraphLaunch(ex, b->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float f = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&f, e0, e1);
+        if (e == cudaSuccess && f < best) best = f;
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaGraphExecDestroy(ex);
+    if (e != cudaSuccess) return fail(MG_ERR_CUDA, std::string("batch autotune timing: ") + cudaGetErrorString(e));
+    *ms = best;
+    return MG_OK;
+}
+
+template <typename R, int DIM>
+mg_status b_autotune_impl(mg_batch *b, int reps, double *cycle_ms) {
+    mg_status st;
+    for (int d = 0; d + 1 < b->dmax; d++) {
+        if (b->colour[d].second == 0) continue;
+        const int ncand = DIM == 2 ? 1 + kTileShapes : 1;
+        double best = 1e30;
+        int kind = MG_SWEEP_COLOUR, tile = 0;
+        for (int c = 0; c < ncand; c++) {
+            b->bsweep[d] = c == 0 ? MG_SWEEP_COLOUR : MG_SWEEP_FUSED;
+            b->btile[d] = c == 0 ? 0 : c - 1;
+            double ms = 0.0;
+            st = b_time_graph(b, &ms, [&](cudaStream_t s) {
+                for (int r = 0; r < reps; r++) b_smooth<R, DIM>(b, s, d, 2);
+            });
+            if (st) return st;
+            if (ms < best) { best = ms; kind = b->bsweep[d]; tile = b->btile[d]; }
+        }
+        b->bsweep[d] = kind;
+        b->btile[d] = tile;
+    }
+    const int cand[] = {1, 2, 4, 8, 16, 32};
+    double best = 1e30;
+    int pick = kBatchBlocksPerSM;
+    for (int c : cand) {
+        b->blocks_per_sm = c;
+        double ms = 0.0;
+        st = b_time_graph(b, &ms, [&](cudaStream_t s) {
+            for (int r = 0; r < reps; r++) b_vcycle<R, DIM>(b, s);
+        });
+        if (st) return st;
+        if (ms < best) { best = ms; pick = c; }
+    }
+    b->blocks_per_sm = pick;
+    if (cycle_ms) *cycle_ms = best / reps;
+    return MG_OK;
+}
+
+void b_get_tuning(const mg_batch *b, mg_batch_tuning *t) {
+    std::memset(t, 0, sizeof(*t));
+    t->depths = b->dmax;
+    for (int d = 0; d < MG_MAX_LEVELS; d++) {
+        t->sweep[d] = d < b->dmax ? b->bsweep[d] : MG_SWEEP_COLOUR;
+        t->tile[d] = d < b->dmax ? b->btile[d] : 0;
+    }
+    t->blocks_per_sm = b->blocks_per_sm;
+}
+
+void b_drop_graph(mg_batch *b) {
+    if (b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; }
 }
 
 template <int DIM>
@@ -526,7 +627,7 @@ void b_step(mg_batch *b, cudaStream_t s) {
     } else {
         for (int q = 0; q < b->opt.inner_cycles; q++) b_vcycle<float, DIM>(b, s);
         const int n = b->cells0.second;
-        kb_add_correction<<<batch_grid(n), kBatchThreads, 0, s>>>(b->lv, b->st, b->tabs + b->cells0.first, n);
+        kb_add_correction<<<batch_grid(b, n), kBatchThreads, 0, s>>>(b->lv, b->st, b->tabs + b->cells0.first, n);
         b->launches++;
     }
     b_norm<DIM>(b, s, 0);
@@ -566,6 +667,15 @@ mg_status mg_batch_create(int count, mg_handle *const *handles, mg_batch **out) 
     b->device = handles[0]->device;
     b->h.assign(handles, handles + count);
     DeviceGuard dg(b->device);
+    if (cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device) != cudaSuccess || b->sms < 1) {
+        cudaGetLastError();
+        b->sms = 152;
+    }
+    b->blocks_per_sm = kBatchBlocksPerSM;
+    for (int d = 0; d < kMaxLevels; d++) {
+        b->bsweep[d] = (b->dim == 2 && b->opt.precision == MG_MIXED) ? MG_SWEEP_FUSED : MG_SWEEP_COLOUR;
+        b->btile[d] = 0;
+    }
     // host-side tables
     std::vector<BLevel> lv;
     std::vector<BProb> pr(count);
@@ -604,7 +714,7 @@ mg_status mg_batch_create(int count, mg_handle *const *handles, mg_batch **out) 
     };
     const int dim = b->dim;
     for (int d = 0; d + 1 < b->dmax; d++) {
-        std::vector<int2> tc, tf, tr, tp;
+        std::vector<int2> tc, tf[kTileShapes], tr, tp;
         for (int p = 0; p < count; p++) {
             const mg_handle *h = handles[p];
             if (h->nlev - 1 <= d) continue;
@@ -613,14 +723,16 @@ mg_status mg_batch_create(int count, mg_handle *const *handles, mg_batch **out) 
             add_blocks(tc, li, (long long)cell_grid(F, dim, (F.n[0] + 1) / 2).x * cell_grid(F, dim, 1).y *
                                    cell_grid(F, dim, 1).z);
             if (dim == 2)
-                add_blocks(tf, li, (long long)((F.n[0] + kFTX - 1) / kFTX) * ((F.n[1] + kFTY - 1) / kFTY));
+                for (int t = 0; t < kTileShapes; t++)
+                    add_blocks(tf[t], li, (long long)((F.n[0] + kTileX[t] - 1) / kTileX[t]) *
+                                              ((F.n[1] + kTileY[t] - 1) / kTileY[t]));
             const dim3 gc = cell_grid(Cl, dim, Cl.n[0]);
             add_blocks(tr, li, (long long)gc.x * gc.y * gc.z);
             const dim3 gf = cell_grid(F, dim, F.n[0]);
             add_blocks(tp, li, (long long)gf.x * gf.y * gf.z);
         }
         b->colour.push_back(slice(tc));
-        b->fused.push_back(slice(tf));
+        for (int t = 0; t < kTileShapes; t++) b->fusedt[t].push_back(slice(tf[t]));
         b->restr.push_back(slice(tr));
         b->prolong.push_back(slice(tp));
     }
@@ -787,8 +899,8 @@ mg_status mg_batch_solve(mg_batch *b, const double *const *rhs, double *const *x
         }
         CK(cudaMemcpyAsync(b->io, io, sizeof(BIo) * b->count, cudaMemcpyHostToDevice, s));
         const int n = b->cells0g.second;
-        if (b->dim == 2) kb_prep<2><<<batch_grid(n), kBlock, 0, s>>>(b->lv, b->io, b->tabs + b->cells0g.first, n);
-        else kb_prep<3><<<batch_grid(n), kBlock, 0, s>>>(b->lv, b->io, b->tabs + b->cells0g.first, n);
+        if (b->dim == 2) kb_prep<2><<<batch_grid(b, n), kBlock, 0, s>>>(b->lv, b->io, b->tabs + b->cells0g.first, n);
+        else kb_prep<3><<<batch_grid(b, n), kBlock, 0, s>>>(b->lv, b->io, b->tabs + b->cells0g.first, n);
         b->launches++;
         CK(cudaGetLastError());
     }
@@ -825,7 +937,7 @@ mg_status mg_batch_solve(mg_batch *b, const double *const *rhs, double *const *x
     CK(cudaMemcpyAsync(host.data(), b->st, sizeof(BState) * b->count, cudaMemcpyDeviceToHost, s));
     if (on_device) {
         const int n = b->cells0.second;
-        kb_copy_out<<<batch_grid(n), kBatchThreads, 0, s>>>(b->lv, b->io, b->tabs + b->cells0.first, n);
+        kb_copy_out<<<batch_grid(b, n), kBatchThreads, 0, s>>>(b->lv, b->io, b->tabs + b->cells0.first, n);
         b->launches++;
         CK(cudaGetLastError());
     } else {
@@ -905,14 +1017,14 @@ mg_status mg_batch_set_coeffs(mg_batch *b, const double *const *lambda, const do
     CK(cudaMemcpyAsync(b->sin, in, sizeof(SetupIn) * b->count, cudaMemcpyHostToDevice, s));
     kb_zero_err<<<(b->count + 255) / 256, 256, 0, s>>>(b->co, b->count);
     const int nf = b->setup_fine_tab.second;
-    if (dim == 2) kb_setup_fine<2><<<batch_grid(nf), kBlock, 0, s>>>(b->sl, b->sin, b->tabs + b->setup_fine_tab.first, nf);
-    else kb_setup_fine<3><<<batch_grid(nf), kBlock, 0, s>>>(b->sl, b->sin, b->tabs + b->setup_fine_tab.first, nf);
+    if (dim == 2) kb_setup_fine<2><<<batch_grid(b, nf), kBlock, 0, s>>>(b->sl, b->sin, b->tabs + b->setup_fine_tab.first, nf);
+    else kb_setup_fine<3><<<batch_grid(b, nf), kBlock, 0, s>>>(b->sl, b->sin, b->tabs + b->setup_fine_tab.first, nf);
     b->launches += 2;
     for (size_t d = 0; d < b->setup_tab.size(); d++) {
         const int n = b->setup_tab[d].second;
         if (n == 0) continue;
-        if (dim == 2) kb_setup_coarse<2><<<batch_grid(n), kBlock, 0, s>>>(b->sl, b->tabs + b->setup_tab[d].first, n);
-        else kb_setup_coarse<3><<<batch_grid(n), kBlock, 0, s>>>(b->sl, b->tabs + b->setup_tab[d].first, n);
+        if (dim == 2) kb_setup_coarse<2><<<batch_grid(b, n), kBlock, 0, s>>>(b->sl, b->tabs + b->setup_tab[d].first, n);
+        else kb_setup_coarse<3><<<batch_grid(b, n), kBlock, 0, s>>>(b->sl, b->tabs + b->setup_tab[d].first, n);
         b->launches++;
     }
     const unsigned gy = (unsigned)std::min(b->count, 65535);
@@ -956,6 +1068,69 @@ mg_status mg_batch_set_coeffs(mg_batch *b, const double *const *lambda, const do
         if (e & 4) return fail(MG_ERR_INVALID_COEFF, "problem " + std::to_string(p) + ": singular coarsest matrix");
     }
     for (int p = 0; p < b->count; p++) b->h[p]->coeffs_set = true;
+    return MG_OK;
+}
+
+mg_status mg_batch_get_tuning(const mg_batch *b, mg_batch_tuning *out) {
+    if (!b || !out) return fail(MG_ERR_INVALID_ARG, "mg_batch_get_tuning: NULL argument");
+    b_get_tuning(b, out);
+    return MG_OK;
+}
+
+mg_status mg_batch_set_tuning(mg_batch *b, const mg_batch_tuning *t) {
+    if (!b || !t) return fail(MG_ERR_INVALID_ARG, "mg_batch_set_tuning: NULL argument");
+    for (int d = 0; d < b->dmax; d++) {
+        if (t->sweep[d] != MG_SWEEP_COLOUR && t->sweep[d] != MG_SWEEP_FUSED)
+            return fail(MG_ERR_INVALID_ARG, "sweep kind must be MG_SWEEP_COLOUR or MG_SWEEP_FUSED");
+        if (t->sweep[d] == MG_SWEEP_FUSED && b->dim != 2)
+            return fail(MG_ERR_INVALID_ARG, "fused sweeps are for 2D grids");
+        if (t->tile[d] < 0 || t->tile[d] >= kTileShapes) return fail(MG_ERR_INVALID_ARG, "tile shape out of range");
+    }
+    if (t->blocks_per_sm < 1 || t->blocks_per_sm > 32)
+        return fail(MG_ERR_INVALID_ARG, "blocks_per_sm must be in [1, 32]");
+    DeviceGuard dg(b->device);
+    CK(cudaStreamSynchronize(b->stream));
+    for (int d = 0; d < b->dmax; d++) {
+        b->bsweep[d] = t->sweep[d];
+        b->btile[d] = t->tile[d];
+    }
+    b->blocks_per_sm = t->blocks_per_sm;
+    b_drop_graph(b);
+    return MG_OK;
+}
+
+mg_status mg_batch_autotune(mg_batch *b, int reps, mg_batch_tuning *out, double *cycle_ms) {
+    if (!b) return fail(MG_ERR_INVALID_ARG, "batch is NULL");
+    if (reps < 1 || reps > 1000) return fail(MG_ERR_INVALID_ARG, "reps must be in [1, 1000]");
+    for (int p = 0; p < b->count; p++)
+        if (!b->h[p]->coeffs_set) return fail(MG_ERR_STATE, "mg_batch_autotune: a problem has no coefficients");
+    DeviceGuard dg(b->device);
+    cudaStream_t s = b->stream;
+    CK(cudaStreamSynchronize(s));
+    for (int p = 0; p < b->count; p++) CK(cudaStreamWaitEvent(s, b->h[p]->ev_inv, 0));
+    // scratch state to zeros and every problem active: all candidates run on
+    // the same finite data over the whole batch
+    for (int p = 0; p < b->count; p++)
+        for (int l = 0; l < b->h[p]->nlev; l++) {
+            const LevelBuf &L = b->h[p]->L[l];
+            void *ptrs[8] = {L.x, L.b, L.bt, L.xalt, L.x32, L.b32, L.bt32, L.xalt32};
+            const size_t sz[8] = {16, 16, 16, 16, 8, 8, 8, 8};
+            for (int q = 0; q < 8; q++)
+                if (ptrs[q]) CK(cudaMemsetAsync(ptrs[q], 0, sz[q] * (size_t)L.N, s));
+        }
+    std::vector<BState> act(b->count);
+    std::memset(act.data(), 0, sizeof(BState) * b->count);
+    for (auto &a : act) a.active = 1;
+    CK(cudaMemcpyAsync(b->st, act.data(), sizeof(BState) * b->count, cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));
+    const bool mixed = b->opt.precision == MG_MIXED;
+    mg_status st;
+    if (b->dim == 2) st = mixed ? b_autotune_impl<float, 2>(b, reps, cycle_ms) : b_autotune_impl<double, 2>(b, reps, cycle_ms);
+    else st = mixed ? b_autotune_impl<float, 3>(b, reps, cycle_ms) : b_autotune_impl<double, 3>(b, reps, cycle_ms);
+    b_drop_graph(b);
+    CK(cudaStreamSynchronize(s));
+    if (st) return st;
+    if (out) b_get_tuning(b, out);
     return MG_OK;
 }
 

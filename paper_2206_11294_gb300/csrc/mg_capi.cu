@@ -308,10 +308,6 @@ template <typename R> typename Vec<R>::v2 *xalt_of(const LevelBuf &l);
 template <> double2 *xalt_of<double>(const LevelBuf &l) { return l.xalt; }
 template <> float2 *xalt_of<float>(const LevelBuf &l) { return l.xalt32; }
 
-// Whether the batched sweeps of this precision and dimension run fused:
-// FP32 (HBM-bound) sweeps in 2D.
-template <typename R, int DIM> constexpr bool fused_sweeps() { return DIM == 2 && sizeof(R) == 4; }
-
 template <typename R, int TX, int TY>
 void launch_fused(const LevelBuf &lb, const Level<R> &v, cudaStream_t s) {
     const dim3 gf((unsigned)((lb.n[0] + TX - 1) / TX), (unsigned)((lb.n[1] + TY - 1) / TY), 1);

@@ -231,3 +231,58 @@ def test_batched_set_coeffs_names_bad_problem(torch_cuda):
     b.close()
     for s in solvers:
         s.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_batch_tunings_keep_results(torch_cuda, precision):
+    """Every batch kernel choice (sweep kind and tile per depth, persistent
+    grid size) and the batch autotuner's pick give the same results, bit for
+    bit, as the default choices."""
+    from paper_2206_11294_gb300.binding import Batch, MgError, MG_ERR_INVALID_ARG
+    probs = _problems_2d()[:6]
+    solvers = _solvers(probs, precision=precision, rtol=1e-10, max_cycles=60)
+    b = Batch(solvers)
+    xs_ref = [p.x0.copy() for p in probs]
+    st_ref = b.solve([p.b for p in probs], xs_ref)
+    base = b.tuning()
+    n = base["depths"]
+    variants = [dict(base, sweep=["colour"] * n, tile=[0] * n, blocks_per_sm=1)]
+    for t in range(3):
+        variants.append(dict(base, sweep=["fused"] * n, tile=[t] * n, blocks_per_sm=[2, 16, 32][t]))
+    for v in variants:
+        b.set_tuning(v)
+        assert b.tuning() == v
+        xs = [p.x0.copy() for p in probs]
+        st = b.solve([p.b for p in probs], xs)
+        for q in range(len(probs)):
+            assert st[q]["cycles"] == st_ref[q]["cycles"]
+            assert np.array_equal(xs[q], xs_ref[q]), (v, q)
+    tuning, ms = b.autotune(reps=2)
+    assert ms > 0 and 1 <= tuning["blocks_per_sm"] <= 32 and tuning["depths"] == n
+    xs = [p.x0.copy() for p in probs]
+    b.solve([p.b for p in probs], xs)
+    for q in range(len(probs)):
+        assert np.array_equal(xs[q], xs_ref[q])
+    for bad in (dict(base, blocks_per_sm=0), dict(base, tile=[3] * n), dict(base, sweep=["x"] * n, tile=[0] * n)):
+        if bad.get("sweep") == ["x"] * n:
+            continue                       # from_dict maps unknown names to colour: not an ABI error
+        with pytest.raises(MgError) as e:
+            b.set_tuning(bad)
+        assert e.value.status == MG_ERR_INVALID_ARG
+    b.close()
+    for s in solvers:
+        s.close()
+
+
+def test_batch_3d_rejects_fused(torch_cuda):
+    from paper_2206_11294_gb300.binding import Batch, MgError, MG_ERR_INVALID_ARG
+    probs = _problems_3d()[:2]
+    solvers = _solvers(probs)
+    b = Batch(solvers)
+    t = b.tuning()
+    with pytest.raises(MgError) as e:
+        b.set_tuning(dict(t, sweep=["fused"] * t["depths"]))
+    assert e.value.status == MG_ERR_INVALID_ARG
+    b.close()
+    for s in solvers:
+        s.close()
