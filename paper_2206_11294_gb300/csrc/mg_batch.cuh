@@ -202,9 +202,37 @@ struct BCoarse {
     float *Minv32;
     int *piv;
     double *dinv;
+    double *Mwork;                // banded path: columns of the inverse before the transpose
     int nc, kl;
     int *err;
 };
+
+// Banded path of the coarsest inverses (kBandSmemMax < nc), all problems in
+// three launches: one 32 x 32 block per problem factors; a 2D grid solves
+// the columns (x: column blocks, y: problem); a 2D grid transposes (and
+// rounds the FP32 copy for mixed precision).
+__global__ void __launch_bounds__(1024) kb_band_lu_big(const BCoarse *__restrict__ co, const int *__restrict__ ids) {
+    const BCoarse &C = co[ids[blockIdx.x]];
+    band_lu_block(C.M, C.nc, C.kl, C.kl, C.piv, C.dinv, C.err);
+}
+
+__global__ void __launch_bounds__(128) kb_band_inv_cols_big(const BCoarse *__restrict__ co,
+                                                            const int *__restrict__ ids) {
+    const BCoarse &C = co[ids[blockIdx.y]];
+    band_inv_col(C.M, C.piv, C.dinv, C.nc, C.kl, C.kl, C.Mwork, C.err, blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+__global__ void kb_transpose_big(const BCoarse *__restrict__ co, const int *__restrict__ ids) {
+    const BCoarse &C = co[ids[blockIdx.y]];
+    const int n = C.nc;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < (long long)n * n;
+         q += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(q / n), j = (int)(q - (long long)i * n);
+        const double v = C.Mwork[(long long)j * n + i];
+        C.Minv[q] = v;
+        if (C.Minv32) C.Minv32[q] = (float)v;
+    }
+}
 
 __global__ void __launch_bounds__(kBatchThreads) kb_zero_coarse(const BCoarse *__restrict__ co, int count) {
     for (int p = blockIdx.y; p < count; p += gridDim.y) {
@@ -447,6 +475,8 @@ struct mg_batch {
     BCoarse *co;
     BIo *io;
     int *inv_ids;
+    int *big_ids;                     // problems on the banded path (device)
+    int max_nc_big;
     int n_inv_smem;
     size_t inv_smem_bytes;
     int max_nc_small;
@@ -800,6 +830,7 @@ mg_status mg_batch_create(int count, mg_handle *const *handles, mg_batch **out) 
         C.Minv32 = mixed ? h->Minv32 : nullptr;
         C.piv = h->piv;
         C.dinv = h->dinv;
+        C.Mwork = h->Mwork;
         C.nc = h->nc;
         const int off = dim == 3 ? c.n[0] * c.n[1] : c.n[0];
         C.kl = std::min(h->nc - 1, 2 * off + 1);
@@ -810,6 +841,7 @@ mg_status mg_batch_create(int count, mg_handle *const *handles, mg_batch **out) 
             b->max_nc_small = std::max(b->max_nc_small, h->nc);
         } else {
             b->big_coarse.push_back(p);
+            b->max_nc_big = std::max(b->max_nc_big, h->nc);
         }
     }
     b->n_inv_smem = (int)inv_ids.size();
@@ -826,7 +858,8 @@ mg_status mg_batch_create(int count, mg_handle *const *handles, mg_batch **out) 
                  o_tab = take(sizeof(int2) * std::max<size_t>(1, tabs.size())),
                  o_sl = take(sizeof(BSetupLevel) * sl.size()), o_sin = take(sizeof(SetupIn) * count),
                  o_co = take(sizeof(BCoarse) * count), o_io = take(sizeof(BIo) * count),
-                 o_ids = take(sizeof(int) * std::max<size_t>(1, inv_ids.size())), o_err = take(sizeof(int) * count);
+                 o_ids = take(sizeof(int) * std::max<size_t>(1, inv_ids.size())), o_err = take(sizeof(int) * count),
+                 o_big = take(sizeof(int) * std::max<size_t>(1, b->big_coarse.size()));
     cudaError_t e = cudaMalloc(&b->mem, off);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -843,6 +876,7 @@ mg_status mg_batch_create(int count, mg_handle *const *handles, mg_batch **out) 
     b->co = reinterpret_cast<BCoarse *>(b->mem + o_co);
     b->io = reinterpret_cast<BIo *>(b->mem + o_io);
     b->inv_ids = reinterpret_cast<int *>(b->mem + o_ids);
+    b->big_ids = reinterpret_cast<int *>(b->mem + o_big);
     b->err_d = reinterpret_cast<int *>(b->mem + o_err);
     if (cudaMemcpy(b->lv, lv.data(), sizeof(BLevel) * lv.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(b->pr, pr.data(), sizeof(BProb) * count, cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -852,6 +886,8 @@ mg_status mg_batch_create(int count, mg_handle *const *handles, mg_batch **out) 
         cudaMemcpy(b->co, co.data(), sizeof(BCoarse) * count, cudaMemcpyHostToDevice) != cudaSuccess ||
         (inv_ids.size() && cudaMemcpy(b->inv_ids, inv_ids.data(), sizeof(int) * inv_ids.size(),
                                       cudaMemcpyHostToDevice) != cudaSuccess) ||
+        (b->big_coarse.size() && cudaMemcpy(b->big_ids, b->big_coarse.data(), sizeof(int) * b->big_coarse.size(),
+                                            cudaMemcpyHostToDevice) != cudaSuccess) ||
         cudaMemset(b->st, 0, sizeof(BState) * count) != cudaSuccess ||
         cudaMallocHost(&b->host_io, std::max(sizeof(SetupIn), sizeof(BIo)) * count) != cudaSuccess ||
         cudaMallocHost(&b->err_h, sizeof(int) * count) != cudaSuccess ||
@@ -1040,21 +1076,12 @@ mg_status mg_batch_set_coeffs(mg_batch *b, const double *const *lambda, const do
                                 sizeof(double) * 32 * (size_t)(b->max_nc_small + kInvRows), s>>>(b->co, b->inv_ids);
         b->launches += 2;
     }
-    for (int p : b->big_coarse) {           // medium coarsest levels: the banded three-kernel path
-        mg_handle *h = b->h[p];
-        const LevelBuf &c = h->L[h->nlev - 1];
-        const int off = dim == 3 ? c.n[0] * c.n[1] : c.n[0];
-        const int kl = std::min(h->nc - 1, 2 * off + 1);
-        k_band_lu<<<1, dim3(32, 32, 1), 0, s>>>(h->Mtmp, h->nc, kl, kl, h->piv, h->dinv, h->err_d);
-        k_band_inv_cols<<<(h->nc + 127) / 128, 128, 0, s>>>(h->Mtmp, h->piv, h->dinv, h->nc, kl, kl, h->Mwork,
-                                                            h->err_d);
-        k_transpose<<<lin_blocks((long long)h->nc * h->nc), 256, 0, s>>>(h->Mwork, h->Minv, h->nc);
+    if (!b->big_coarse.empty()) {           // medium coarsest levels: the banded path, all at once
+        const unsigned nb = (unsigned)b->big_coarse.size();
+        kb_band_lu_big<<<nb, dim3(32, 32, 1), 0, s>>>(b->co, b->big_ids);
+        kb_band_inv_cols_big<<<dim3((unsigned)((b->max_nc_big + 127) / 128), nb), 128, 0, s>>>(b->co, b->big_ids);
+        kb_transpose_big<<<dim3(64, nb), 256, 0, s>>>(b->co, b->big_ids);
         b->launches += 3;
-        if (h->opt.precision == MG_MIXED) {
-            k_to_f32<<<lin_blocks((long long)h->nc * h->nc), 256, 0, s>>>(h->Minv, h->Minv32,
-                                                                         (long long)h->nc * h->nc);
-            b->launches++;
-        }
     }
     kb_gather_err<<<(b->count + 255) / 256, 256, 0, s>>>(b->co, b->count, b->err_d);
     b->launches++;

@@ -1093,9 +1093,9 @@ __global__ void __launch_bounds__(32 * kInvRows) k_band_inv_cols_warp(const doub
 // 2. k_band_inv_cols: thread j solves L U x = P e_j (row swaps and the unit
 //    lower factor forward, U backward) into W[j][*].
 // 3. k_transpose: Minv[i][j] = W[j][i].
-__global__ void __launch_bounds__(1024) k_band_lu(double *__restrict__ M, int n, int kl, int ku,
-                                                  int *__restrict__ piv, double *__restrict__ dinv,
-                                                  int *__restrict__ err) {
+// One 32 x 32 block factors one matrix (shared with the batched kernel).
+__device__ __forceinline__ void band_lu_block(double *__restrict__ M, int n, int kl, int ku, int *__restrict__ piv,
+                                              double *__restrict__ dinv, int *__restrict__ err) {
     __shared__ int prow;
     __shared__ double pinv;
     __shared__ int bad;
@@ -1159,10 +1159,16 @@ __global__ void __launch_bounds__(1024) k_band_lu(double *__restrict__ M, int n,
     }
 }
 
-__global__ void k_band_inv_cols(const double *__restrict__ M, const int *__restrict__ piv,
-                                const double *__restrict__ dinv, int n, int kl, int ku, double *__restrict__ W,
-                                const int *__restrict__ err) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(1024) k_band_lu(double *__restrict__ M, int n, int kl, int ku,
+                                                  int *__restrict__ piv, double *__restrict__ dinv,
+                                                  int *__restrict__ err) {
+    band_lu_block(M, n, kl, ku, piv, dinv, err);
+}
+
+// Column j of the inverse into W[j][*] (one thread).
+__device__ __forceinline__ void band_inv_col(const double *__restrict__ M, const int *__restrict__ piv,
+                                             const double *__restrict__ dinv, int n, int kl, int ku,
+                                             double *__restrict__ W, const int *__restrict__ err, int j) {
     if (j >= n || (*(volatile const int *)err & 4)) return;
     double *y = W + (long long)j * n;
     for (int i = 0; i < n; i++) y[i] = (i == j) ? 1.0 : 0.0;
@@ -1186,6 +1192,12 @@ __global__ void k_band_inv_cols(const double *__restrict__ M, const int *__restr
         for (int c = i + 1; c <= clast; c++) s -= M[(long long)i * n + c] * y[c];
         y[i] = s * dinv[i];
     }
+}
+
+__global__ void k_band_inv_cols(const double *__restrict__ M, const int *__restrict__ piv,
+                                const double *__restrict__ dinv, int n, int kl, int ku, double *__restrict__ W,
+                                const int *__restrict__ err) {
+    band_inv_col(M, piv, dinv, n, kl, ku, W, err, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 __global__ void k_transpose(const double *__restrict__ W, double *__restrict__ Minv, int n) {

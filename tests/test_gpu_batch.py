@@ -286,3 +286,32 @@ def test_batch_3d_rejects_fused(torch_cuda):
     b.close()
     for s in solvers:
         s.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_batch_banded_coarsest_path(torch_cuda, precision):
+    """Problems whose coarsest level has more than 128 unknowns (15 x 15 and
+    13 x 13 cells) take the banded inverse, batched over problems: same
+    results as the per-handle set-up, bit for bit."""
+    from paper_2206_11294_gb300.binding import Batch, Solver
+    torch = torch_cuda
+    probs = [I.bubble_2d(n=n, seed=300 + q, n_bubbles=2, rmin=0.05, rmax=0.15, centred=False, gas_rho=1.0,
+                         name=f"m{q}") for q, n in enumerate([480, 416, 64, 480])]
+    kw = dict(precision=precision, rtol=1e-10, max_cycles=60)
+    ref = _solvers(probs, **kw)
+    assert all(len(s.levels()) >= 3 for s in ref)
+    xs_ref = []
+    for s, p in zip(ref, probs):
+        x = p.x0.copy()
+        s.solve(p.b, x)
+        xs_ref.append(x)
+    fresh = [Solver(p.grid, **kw) for p in probs]
+    b = Batch(fresh)
+    b.set_coeffs([p.lam for p in probs], [p.fa for p in probs], [p.fk for p in probs])
+    xs = [p.x0.copy() for p in probs]
+    b.solve([p.b for p in probs], xs)
+    for q in range(len(probs)):
+        assert np.array_equal(xs[q], xs_ref[q]), q
+    b.close()
+    for s in ref + fresh:
+        s.close()
