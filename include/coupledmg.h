@@ -167,16 +167,19 @@ MG_API mg_status mg_counters(const mg_handle *h, long long *launches, double *sm
  *               per sweep on tiles staged in shared memory, the red values of
  *               a one-cell ring recomputed per tile);
  *   tile[l]     fused tile shape, cells: 0 = 64 x 16, 1 = 32 x 16, 2 = 32 x 8;
- *   tail_level  the levels from this one to the coarsest run as one kernel on
- *               a thread-block cluster (smoothing, restriction, coarsest solve,
- *               prolongation separated by cluster barriers); >= levels: none.
- *               Allowed from level 1 when at least two levels (and at most 12)
- *               remain and the level has at most 16384 cells;
- *   tail_ctas   thread blocks of that cluster: 8, or 16 where the device
- *               allows non-portable cluster sizes.
+ *   tail_level  the levels from this one to the coarsest run as one kernel
+ *               (smoothing, restriction, coarsest solve, prolongation as
+ *               stages separated by barriers, the levels' state in shared
+ *               memory); >= levels: none.  Allowed from level 1 when at least
+ *               two levels (and at most 12) remain, the level has at most
+ *               16384 cells and the state fits 200 KB per thread block;
+ *   tail_ctas   thread blocks of that kernel: 1 (one block, block barriers),
+ *               8 (a cluster; distributed shared memory, cluster barriers),
+ *               or 16 where the device allows non-portable cluster sizes.
  * Defaults after mg_create: colour sweeps for FP64 cycles, fused 64 x 16 for
  * the FP32 cycles of mixed precision on 2D grids; the tail from the first
- * level below the finest with at most 4096 cells, 8 CTAs. */
+ * level below the finest with at most 4096 cells, 8 CTAs.  mg_autotune also
+ * tries one block. */
 #define MG_MAX_LEVELS 32
 enum { MG_SWEEP_COLOUR = 1, MG_SWEEP_FUSED = 2 };
 typedef struct {
@@ -192,15 +195,18 @@ MG_API mg_status mg_get_tuning(const mg_handle *h, mg_tuning *out);
 MG_API mg_status mg_set_tuning(mg_handle *h, const mg_tuning *t);
 
 /* Measures the choices on the handle's own hierarchy and keeps the fastest:
- * per level, each sweep kernel (and tile shape) over `reps` pairs of sweeps;
- * then each allowed tail (none, every allowed first level, 8 or 16 CTAs)
- * over `reps` whole V-cycles.  Each candidate is captured as a CUDA graph and
- * timed with CUDA events on the handle's stream (best of three replays).
+ * per level, each sweep kernel (and tile shape) as one CUDA graph of `reps`
+ * pairs of sweeps (median of five replays); then each allowed tail (none,
+ * every allowed first level, 8 or 16 CTAs) as a graph of one V-cycle
+ * launched 4 * reps + 1 times, each launch timed with CUDA events on the
+ * handle's stream and waited for, as the solve does per cycle (median), so
+ * the per-launch cost of the graph counts.
  * Needs coefficients (MG_ERR_STATE otherwise); overwrites the hierarchy's
  * scratch state (every level's x, b and right-hand sides), not the
  * coefficients, so the next mg_solve is unaffected.  Cycles run in the
  * handle's precision (FP32 for mixed).  out (nullable) receives the chosen
- * tuning, vcycle_ms (nullable) the chosen V-cycle's time.  Synchronous. */
+ * tuning, vcycle_ms (nullable) the chosen V-cycle's median time per launch.
+ * Synchronous. */
 MG_API mg_status mg_autotune(mg_handle *h, int reps, mg_tuning *out, double *vcycle_ms);
 
 /* Batched solve of many independent problems in one set of launches

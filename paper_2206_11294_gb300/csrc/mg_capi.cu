@@ -19,6 +19,7 @@
 #include "coupledmg.h"
 #include "mg_host.h"
 #include "mg_kernels.cuh"
+#include "mg_tail.cuh"
 
 using namespace cmg;
 
@@ -358,22 +359,37 @@ template <> const double *coarse_inverse<double>(const mg_handle *h) { return h-
 template <> const float *coarse_inverse<float>(const mg_handle *h) { return h->Minv32; }
 
 // Levels tail_lev .. coarsest as one launch of k_vcycle_tail on one cluster.
-template <typename R, int DIM>
-void enqueue_tail(const mg_handle *h, cudaStream_t s) {
+template <typename R>
+TailArgs<R> tail_args(const mg_handle *h, int first, int ctas, size_t *smem) {
     TailArgs<R> A;
     std::memset(&A, 0, sizeof(A));
-    A.nlev = h->nlev - h->tail_lev;
-    for (int q = 0; q < A.nlev; q++) A.L[q] = view<R>(h->L[h->tail_lev + q]);
+    A.nlev = h->nlev - first;
+    for (int q = 0; q < A.nlev; q++) A.L[q].g = view<R>(h->L[first + q]);
+    const int pairs = tail_layout(A, h->grid.dim, ctas);
+    *smem = (size_t)pairs * sizeof(typename Vec<R>::v2);
     A.bc = bc_flags(h->grid);
     A.Minv = coarse_inverse<R>(h);
     A.nc = h->nc;
     A.nu1 = h->opt.nu1;
     A.nu2 = h->opt.nu2;
+    return A;
+}
+
+template <typename R, int DIM>
+void enqueue_tail(const mg_handle *h, cudaStream_t s) {
+    size_t smem = 0;
+    TailArgs<R> A = tail_args<R>(h, h->tail_lev, h->tail_ctas, &smem);
+    if (h->tail_ctas == 1) {                  // one CTA, no cluster
+        cudaFuncSetAttribute(k_vcycle_tail<R, DIM, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_vcycle_tail<R, DIM, false><<<1, kBlock, smem, s>>>(A);
+        return;
+    }
+    cudaFuncSetAttribute(k_vcycle_tail<R, DIM, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaLaunchConfig_t cfg;
     std::memset(&cfg, 0, sizeof(cfg));
     cfg.gridDim = dim3((unsigned)h->tail_ctas, 1, 1);
     cfg.blockDim = kBlock;
-    cfg.dynamicSmemBytes = 0;
+    cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -382,7 +398,7 @@ void enqueue_tail(const mg_handle *h, cudaStream_t s) {
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    cudaLaunchKernelEx(&cfg, k_vcycle_tail<R, DIM>, A);
+    cudaLaunchKernelEx(&cfg, k_vcycle_tail<R, DIM, true>, A);
 }
 
 template <typename R, int DIM>
@@ -790,17 +806,23 @@ mg_status check_handle(const mg_handle *h, bool need_coeffs) {
 }
 
 // ---------------------------------------------------------------- tuning
-bool tail_level_ok(const mg_handle *h, int l) {
-    return l >= 1 && h->nlev - l >= 2 && h->nlev - l <= kTailMaxLevels && h->L[l].N <= kTailMaxCells;
+constexpr size_t kTailSmemMax = 200 * 1024;   // shared memory a tail CTA may use
+
+bool tail_level_ok(const mg_handle *h, int l, int ctas = kTailCtas) {
+    if (!(l >= 1 && h->nlev - l >= 2 && h->nlev - l <= kTailMaxLevels && h->L[l].N <= kTailMaxCells)) return false;
+    size_t smem = 0;
+    if (h->opt.precision == MG_MIXED) tail_args<float>(h, l, ctas, &smem);
+    else tail_args<double>(h, l, ctas, &smem);
+    return smem <= kTailSmemMax;
 }
 
 // 8 CTAs is a portable cluster size; 16 needs the kernel's opt-in and a
 // device that can place such a cluster.
 template <typename R, int DIM>
 bool tail_ctas_allowed(int ctas) {
-    if (ctas == kTailCtas) return true;
+    if (ctas == 1 || ctas == kTailCtas) return true;
     if (ctas != 16) return false;
-    if (cudaFuncSetAttribute(k_vcycle_tail<R, DIM>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+    if (cudaFuncSetAttribute(k_vcycle_tail<R, DIM, true>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
         cudaSuccess) {
         cudaGetLastError();
         return false;
@@ -817,7 +839,7 @@ bool tail_ctas_allowed(int ctas) {
     cfg.attrs = &a;
     cfg.numAttrs = 1;
     int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, k_vcycle_tail<R, DIM>, &cfg) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveClusters(&n, k_vcycle_tail<R, DIM, true>, &cfg) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
@@ -835,33 +857,38 @@ void drop_graphs(mg_handle *h) {
     if (h->g32) { cudaGraphExecDestroy(h->g32); h->g32 = nullptr; }
 }
 
-// Captures body as a graph and times it: one warm-up replay, then the best of
-// three, with CUDA events on the handle's stream.
+// Captures body as a graph and times it with CUDA events on the handle's
+// stream: one warm-up replay, then `launches` replays, each bracketed by
+// events and waited for (the solve's own pattern: one graph launch per cycle,
+// then a host synchronisation, so each time includes the launch overhead).
+// Returns the median.
 template <typename F>
-mg_status time_graph(mg_handle *h, double *ms, F &&body) {
+mg_status time_graph(mg_handle *h, int launches, double *ms, F &&body) {
     cudaGraphExec_t ex = nullptr;
     long long kernels = 0;
     mg_status st = capture(h, &ex, &kernels, body);
     if (st) return st;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
-    float best = 1e30f;
+    std::vector<float> t;
     cudaError_t e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
     if (e == cudaSuccess) e = cudaGraphLaunch(ex, h->stream);
-    for (int t = 0; t < 3 && e == cudaSuccess; t++) {
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    for (int q = 0; q < launches && e == cudaSuccess; q++) {
         e = cudaEventRecord(e0, h->stream);
         if (e == cudaSuccess) e = cudaGraphLaunch(ex, h->stream);
         if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
         if (e == cudaSuccess) e = cudaEventSynchronize(e1);
         float f = 0.f;
         if (e == cudaSuccess) e = cudaEventElapsedTime(&f, e0, e1);
-        if (e == cudaSuccess && f < best) best = f;
+        if (e == cudaSuccess) t.push_back(f);
     }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     cudaGraphExecDestroy(ex);
     if (e != cudaSuccess) return fail(MG_ERR_CUDA, std::string("autotune timing: ") + cudaGetErrorString(e));
-    *ms = best;
+    std::sort(t.begin(), t.end());
+    *ms = t[t.size() / 2];
     return MG_OK;
 }
 
@@ -876,7 +903,7 @@ mg_status autotune_impl(mg_handle *h, int reps, double *vcycle_ms) {
         for (int c = 0; c < ncand; c++) {
             const int ck = c == 0 ? MG_SWEEP_COLOUR : MG_SWEEP_FUSED, ct = c == 0 ? 0 : c - 1;
             double ms = 0.0;
-            st = time_graph(h, &ms, [&](cudaStream_t s) {
+            st = time_graph(h, 5, &ms, [&](cudaStream_t s) {
                 for (int r = 0; r < reps; r++) enqueue_sweeps<R, DIM>(h, s, l, 2, ck, ct);
             });
             if (st) return st;
@@ -888,26 +915,24 @@ mg_status autotune_impl(mg_handle *h, int reps, double *vcycle_ms) {
     // the cluster tail: none, or each allowed first level and cluster size
     std::vector<std::pair<int, int>> cand{{h->nlev, kTailCtas}};
     const bool wide = tail_ctas_allowed<R, DIM>(16);
-    for (int l = 1; l < h->nlev; l++)
-        if (tail_level_ok(h, l)) {
-            cand.push_back({l, kTailCtas});
-            if (wide) cand.push_back({l, 16});
-        }
+    for (int l = 1; l < h->nlev; l++) {
+        if (tail_level_ok(h, l, 1)) cand.push_back({l, 1});
+        if (tail_level_ok(h, l, kTailCtas)) cand.push_back({l, kTailCtas});
+        if (wide && tail_level_ok(h, l, 16)) cand.push_back({l, 16});
+    }
     double best = 1e30;
     std::pair<int, int> pick = cand[0];
     for (const auto &c : cand) {
         h->tail_lev = c.first;
         h->tail_ctas = c.second;
         double ms = 0.0;
-        st = time_graph(h, &ms, [&](cudaStream_t s) {
-            for (int r = 0; r < reps; r++) enqueue_vcycle<R, DIM>(h, s, 0);
-        });
+        st = time_graph(h, 4 * reps + 1, &ms, [&](cudaStream_t s) { enqueue_vcycle<R, DIM>(h, s, 0); });
         if (st) return st;
         if (ms < best) { best = ms; pick = c; }
     }
     h->tail_lev = pick.first;
     h->tail_ctas = pick.second;
-    if (vcycle_ms) *vcycle_ms = best / reps;
+    if (vcycle_ms) *vcycle_ms = best;
     return MG_OK;
 }
 
@@ -1122,11 +1147,14 @@ mg_status mg_set_tuning(mg_handle *h, const mg_tuning *t) {
         if (t->tile[l] < 0 || t->tile[l] >= kTileShapes) return fail(MG_ERR_INVALID_ARG, "tile shape out of range");
     }
     const bool no_tail = t->tail_level >= h->nlev;
-    if (!no_tail && !tail_level_ok(h, t->tail_level))
-        return fail(MG_ERR_INVALID_ARG, "tail level must be >= 1, leave 2 to 12 levels and have <= 16384 cells");
+    if (!no_tail && (t->tail_ctas != 1 && t->tail_ctas != kTailCtas && t->tail_ctas != 16))
+        return fail(MG_ERR_INVALID_ARG, "tail cluster size must be 1, 8, or 16 where the device allows it");
+    if (!no_tail && !tail_level_ok(h, t->tail_level, t->tail_ctas))
+        return fail(MG_ERR_INVALID_ARG, "tail level must be >= 1, leave 2 to 12 levels, have <= 16384 cells "
+                                        "and fit the tail's shared memory");
     DeviceGuard dg(h->device);
     if (!no_tail && !tail_ctas_ok(h, t->tail_ctas))
-        return fail(MG_ERR_INVALID_ARG, "tail cluster size must be 8, or 16 where the device allows it");
+        return fail(MG_ERR_INVALID_ARG, "tail cluster size must be 1, 8, or 16 where the device allows it");
     CK(cudaStreamSynchronize(h->stream));
     for (int l = 0; l < h->nlev; l++) {
         h->sweep[l] = t->sweep[l];

@@ -1208,87 +1208,4 @@ __global__ void k_transpose(const double *__restrict__ W, double *__restrict__ M
     }
 }
 
-// ---------------------------------------------------------------------------
-// The bottom of a V-cycle in one launch on a thread-block cluster: every level
-// at or below kTailCells cells (smoothing, restriction, the coarsest solve,
-// prolongation) runs as stages of one kernel, the CTAs of the cluster sharing
-// each stage's blocks and meeting at a hardware cluster barrier (release /
-// acquire) between stages.  Small levels otherwise cost a launch per stage
-// for almost no work.  The stages call the same block functions as the
-// separate kernels, reading data written in earlier stages through L2.
-// ---------------------------------------------------------------------------
-constexpr int kTailCells = 4096;
-constexpr int kTailMaxLevels = 12;
-constexpr int kTailCtas = 8;      // CTAs of the cluster (portable cluster size)
-constexpr int kTailMaxCells = 16384;   // largest first tail level a tuning may choose
-
-template <typename R>
-struct TailArgs {
-    Level<R> L[kTailMaxLevels];   // first tail level .. coarsest
-    int nlev;
-    BcFlags bc;
-    const R *Minv;
-    int nc;
-    int nu1, nu2;
-};
-
-template <typename R, int DIM>
-__device__ __forceinline__ void tail_smooth(const Level<R> &L, int sweeps, int rank, int nb) {
-    namespace cg = cooperative_groups;
-    const int gx = ((L.n0 + 1) / 2 + kBX - 1) / kBX, gy = (L.n1 + kBY - 1) / kBY, gz = DIM == 3 ? L.n2 : 1;
-    const int nblk = gx * gy * gz;
-    for (int q = 0; q < sweeps; q++)
-        for (int colour = 0; colour < 2; colour++) {
-            for (int v = rank; v < nblk; v += nb) {
-                int bx, by, bz;
-                block_coords(v, gx, gy, bx, by, bz);
-                rbgs_colour_block<R, DIM, false>(L, colour, bx, by, bz);
-            }
-            cg::this_cluster().sync();
-        }
-}
-
-template <typename R, int DIM>
-__global__ void __launch_bounds__(kBX * kBY) k_vcycle_tail(const __grid_constant__ TailArgs<R> A) {
-    namespace cg = cooperative_groups;
-    cg::cluster_group cl = cg::this_cluster();
-    const int rank = (int)cl.block_rank(), nb = (int)cl.num_blocks();
-    for (int l = 0; l + 1 < A.nlev; l++) {
-        tail_smooth<R, DIM>(A.L[l], A.nu1, rank, nb);
-        const Level<R> &C = A.L[l + 1];
-        const int gx = (C.n0 + kBX - 1) / kBX, gy = (C.n1 + kBY - 1) / kBY, gz = DIM == 3 ? C.n2 : 1;
-        for (int v = rank; v < gx * gy * gz; v += nb) {
-            int bx, by, bz;
-            block_coords(v, gx, gy, bx, by, bz);
-            if (A.nu1 > 0) residual_restrict_block<R, DIM, false, true>(A.L[l], C, bx, by, bz);
-            else residual_restrict_block<R, DIM, false, false>(A.L[l], C, bx, by, bz);
-        }
-        cl.sync();
-    }
-    {   // coarsest: x = Minv b, one warp per row
-        const Level<R> &C = A.L[A.nlev - 1];
-        const int lane = threadIdx.x, warp = threadIdx.y;
-        const R *b = reinterpret_cast<const R *>(C.b);
-        for (int row = rank * kBY + warp; row < A.nc; row += nb * kBY) {
-            R acc = R(0);
-            for (int c = lane; c < A.nc; c += 32) acc += __ldg(A.Minv + (long long)row * A.nc + c) * __ldcg(b + c);
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-            if (lane == 0) reinterpret_cast<R *>(C.x)[row] = acc;
-        }
-        cl.sync();
-    }
-    for (int l = A.nlev - 2; l >= 0; l--) {
-        const Level<R> &F = A.L[l];
-        const int gx = (F.n0 + kBX - 1) / kBX, gy = (F.n1 + kBY - 1) / kBY, gz = DIM == 3 ? F.n2 : 1;
-        for (int v = rank; v < gx * gy * gz; v += nb) {
-            int bx, by, bz;
-            block_coords(v, gx, gy, bx, by, bz);
-            prolong_add_block<R, DIM, false>(A.L[l + 1], F, A.bc, bx, by, bz);
-        }
-        cl.sync();
-        tail_smooth<R, DIM>(F, A.nu2, rank, nb);
-    }
-}
-
 }  // namespace cmg
