@@ -176,6 +176,9 @@ MG_API mg_status mg_counters(const mg_handle *h, long long *launches, double *sm
  *   tail_ctas   thread blocks of that kernel: 1 (one block, block barriers),
  *               8 (a cluster; distributed shared memory, cluster barriers),
  *               or 16 where the device allows non-portable cluster sizes.
+ *   persistent  colour sweeps, restriction and prolongation launch one block
+ *               per tile (0) or one persistent wave of blocks (SMs x resident
+ *               blocks) that walk the tiles (1).
  * Defaults after mg_create: colour sweeps for FP64 cycles, fused 64 x 16 for
  * the FP32 cycles of mixed precision on 2D grids; the tail from the first
  * level below the finest with at most 4096 cells, 8 CTAs.  mg_autotune also
@@ -188,6 +191,7 @@ typedef struct {
     int tile[MG_MAX_LEVELS];
     int tail_level;
     int tail_ctas;
+    int persistent;
 } mg_tuning;
 
 MG_API mg_status mg_get_tuning(const mg_handle *h, mg_tuning *out);
@@ -197,7 +201,8 @@ MG_API mg_status mg_set_tuning(mg_handle *h, const mg_tuning *t);
 /* Measures the choices on the handle's own hierarchy and keeps the fastest:
  * per level, each sweep kernel (and tile shape) as one CUDA graph of `reps`
  * pairs of sweeps (median of five replays); then each allowed tail (none,
- * every allowed first level, 8 or 16 CTAs) as a graph of one V-cycle
+ * every allowed first level on 1, 8 or 16 CTAs), with and without persistent
+ * waves, as a graph of one V-cycle
  * launched 4 * reps + 1 times, each launch timed with CUDA events on the
  * handle's stream and waited for, as the solve does per cycle (median), so
  * the per-launch cost of the graph counts.

@@ -99,4 +99,5 @@ def describe(tuning: dict) -> str:
     lv = ",".join("C" if s == "colour" else f"F{t}" for s, t in zip(tuning["sweep"], tuning["tile"]))
     tail = "none" if tuning["tail_level"] >= tuning["levels"] else \
         f"from L{tuning['tail_level']} on {tuning['tail_ctas']} CTAs"
-    return f"sweeps [{lv}], tail {tail}"
+    waves = ", persistent waves" if tuning.get("persistent") else ""
+    return f"sweeps [{lv}], tail {tail}{waves}"

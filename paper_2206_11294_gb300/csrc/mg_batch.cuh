@@ -572,7 +572,9 @@ mg_status b_time_graph(mg_batch *b, double *ms, F &&body) {
     const long long before = b->launches;
     body(cs);
     b->launches = before;
+    const cudaError_t le = cudaGetLastError();
     cudaError_t e = cudaStreamEndCapture(cs, &graph);
+    if (le != cudaSuccess) e = le;
     if (e == cudaSuccess) e = cudaGraphInstantiate(&ex, graph, 0);
     if (graph) cudaGraphDestroy(graph);
     if (e != cudaSuccess) return fail(MG_ERR_CUDA, std::string("batch autotune capture: ") + cudaGetErrorString(e));
@@ -955,7 +957,12 @@ mg_status mg_batch_solve(mg_batch *b, const double *const *rhs, double *const *x
         else b_step<3>(b, cs);
         b->graph_kernels = b->launches - before;
         b->launches = before;
+        const cudaError_t le = cudaGetLastError();    // a launch refused while capturing
         cudaError_t e = cudaStreamEndCapture(cs, &graph);
+        if (le != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return fail(MG_ERR_CUDA, std::string("batch graph capture: a launch failed: ") + cudaGetErrorString(le));
+        }
         if (e != cudaSuccess) return fail(MG_ERR_CUDA, std::string("batch graph capture: ") + cudaGetErrorString(e));
         e = cudaGraphInstantiate(&b->graph, graph, 0);
         cudaGraphDestroy(graph);
@@ -1069,8 +1076,7 @@ mg_status mg_batch_set_coeffs(mg_batch *b, const double *const *lambda, const do
     else kb_coarse_assemble<3><<<dim3(4, gy), kBatchThreads, 0, s>>>(b->co, b->count);
     b->launches += 2;
     if (b->n_inv_smem > 0) {
-        CK(cudaFuncSetAttribute(kb_band_lu_warp, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)b->inv_smem_bytes));
+        CK(raise_smem_limit((const void *)kb_band_lu_warp, (int)(sizeof(double) * kBandSmemMax * kBandSmemMax)));
         kb_band_lu_warp<<<b->n_inv_smem, kLUThreads, b->inv_smem_bytes, s>>>(b->co, b->inv_ids);
         kb_band_inv_cols_warp<<<dim3((b->max_nc_small + 31) / 32, b->n_inv_smem), dim3(32, kInvRows),
                                 sizeof(double) * 32 * (size_t)(b->max_nc_small + kInvRows), s>>>(b->co, b->inv_ids);

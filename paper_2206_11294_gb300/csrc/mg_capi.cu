@@ -13,6 +13,8 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -28,6 +30,7 @@ namespace {
 constexpr int kMaxLevels = 32;
 constexpr int kMaxCoarseUnknowns = 1024;
 constexpr size_t kAlign = 256;
+constexpr size_t kTailSmemMax = 200 * 1024;   // shared memory a tail CTA may use
 
 thread_local std::string g_err;
 
@@ -90,6 +93,7 @@ struct mg_handle {
     int tail_ctas;         // CTAs of the tail's cluster (8, or 16 where allowed)
     int sweep[kMaxLevels]; // per level: MG_SWEEP_COLOUR or MG_SWEEP_FUSED
     int tile[kMaxLevels];  // per level: fused tile shape (index into kTileX / kTileY)
+    int persistent;        // colour sweeps, restriction, prolongation: one persistent wave (1) or a block per tile (0)
     double *Minv, *Mtmp;
     double *Mwork;         // coarse inverse: columns before the transpose (banded path)
     int *piv;              // coarse inverse: pivot rows (banded path)
@@ -239,6 +243,7 @@ void plan(mg_handle *h, char *base, size_t *bytes) {
         if (h->L[l].N <= kTailCells) { h->tail_lev = l; break; }
     if (h->nlev - h->tail_lev < 2 || h->nlev - h->tail_lev > kTailMaxLevels) h->tail_lev = h->nlev;
     h->tail_ctas = kTailCtas;
+    h->persistent = 0;
     // Default kernel choices until mg_autotune / mg_set_tuning: FP32 cycles
     // (mixed precision) sweep fused in 2D; FP64 sweeps are bound by GB300's
     // FP64 pipe, where the fused kernel's recomputed ring costs more than the
@@ -297,6 +302,56 @@ BcVals bc_vals(const mg_grid &g) {
 
 dim3 kBlock(kBX, kBY, 1);
 
+// One persistent wave for a grid-stride kernel over `tiles` tiles: SMs x the
+// kernel's resident blocks per SM (from the occupancy calculator, cached per
+// kernel and device), at most the number of tiles.
+unsigned wave(const void *kernel, long long tiles, int dyn_smem = 0) {
+    static std::mutex mu;
+    static std::map<std::pair<const void *, int>, int> cache;   // (kernel, device) -> SMs x blocks per SM
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int slots = 0;
+    {
+        std::lock_guard<std::mutex> g(mu);
+        auto it = cache.find({kernel, dev});
+        if (it != cache.end()) slots = it->second;
+    }
+    if (slots == 0) {
+        int sms = 0, per = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, kBX * kBY, dyn_smem) != cudaSuccess) {
+            cudaGetLastError();
+            sms = 152;
+            per = 4;
+        }
+        slots = std::max(1, sms * std::max(1, per));
+        std::lock_guard<std::mutex> g(mu);
+        cache[{kernel, dev}] = slots;
+    }
+    return (unsigned)std::max(1LL, std::min(tiles, (long long)slots));
+}
+
+long long tiles_of(const dim3 &g) { return (long long)g.x * g.y * g.z; }
+
+
+
+// Raises a kernel's dynamic shared-memory limit to at least `bytes`, never
+// lowers it.  The limit is a process-wide attribute of the function: setting
+// it per launch would race with other threads launching the same kernel with
+// more shared memory (their launch fails), so it only grows, under a lock.
+cudaError_t raise_smem_limit(const void *fn, int bytes) {
+    static std::mutex mu;
+    static std::map<std::pair<const void *, int>, int> limit;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> g(mu);
+    int &cur = limit[{fn, dev}];
+    if (bytes <= cur) return cudaSuccess;
+    const cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) cur = bytes;
+    return e;
+}
+
 unsigned lin_blocks(long long n) {
     long long b = (n + 255) / 256;
     return (unsigned)(b < 1 ? 1 : (b > 152 * 16 ? 152 * 16 : b));
@@ -336,8 +391,14 @@ void enqueue_sweeps(const mg_handle *h, cudaStream_t s, int l, int sweeps, int k
     }
     const dim3 gr = cell_grid(lb, DIM, (lb.n[0] + 1) / 2);
     for (; q < sweeps; q++) {
-        k_rbgs_colour<R, DIM><<<gr, kBlock, 0, s>>>(v, 0);
-        k_rbgs_colour<R, DIM><<<gr, kBlock, 0, s>>>(v, 1);
+        if (h->persistent) {
+            const unsigned gw = wave((const void *)k_rbgs_colour<R, DIM, true>, tiles_of(gr));
+            k_rbgs_colour<R, DIM, true><<<gw, kBlock, 0, s>>>(v, 0);
+            k_rbgs_colour<R, DIM, true><<<gw, kBlock, 0, s>>>(v, 1);
+        } else {
+            k_rbgs_colour<R, DIM, false><<<gr, kBlock, 0, s>>>(v, 0);
+            k_rbgs_colour<R, DIM, false><<<gr, kBlock, 0, s>>>(v, 1);
+        }
         counted(h, 2);
     }
 }
@@ -380,11 +441,11 @@ void enqueue_tail(const mg_handle *h, cudaStream_t s) {
     size_t smem = 0;
     TailArgs<R> A = tail_args<R>(h, h->tail_lev, h->tail_ctas, &smem);
     if (h->tail_ctas == 1) {                  // one CTA, no cluster
-        cudaFuncSetAttribute(k_vcycle_tail<R, DIM, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        raise_smem_limit((const void *)k_vcycle_tail<R, DIM, false>, (int)kTailSmemMax);
         k_vcycle_tail<R, DIM, false><<<1, kBlock, smem, s>>>(A);
         return;
     }
-    cudaFuncSetAttribute(k_vcycle_tail<R, DIM, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    raise_smem_limit((const void *)k_vcycle_tail<R, DIM, true>, (int)kTailSmemMax);
     cudaLaunchConfig_t cfg;
     std::memset(&cfg, 0, sizeof(cfg));
     cfg.gridDim = dim3((unsigned)h->tail_ctas, 1, 1);
@@ -427,13 +488,30 @@ void enqueue_vcycle(const mg_handle *h, cudaStream_t s, int l) {
     if (tm) cudaEventRecordWithFlags(h->ev[0], s, cudaEventRecordExternal);
     enqueue_smooth<R, DIM>(h, s, l, h->opt.nu1);
     if (tm) cudaEventRecordWithFlags(h->ev[1], s, cudaEventRecordExternal);
-    if (h->opt.nu1 > 0)
-        k_residual_restrict<R, DIM, true><<<cell_grid(cb, DIM, cb.n[0]), kBlock, 0, s>>>(view<R>(lb), view<R>(cb));
-    else
-        k_residual_restrict<R, DIM, false><<<cell_grid(cb, DIM, cb.n[0]), kBlock, 0, s>>>(view<R>(lb), view<R>(cb));
+    const dim3 rg = cell_grid(cb, DIM, cb.n[0]);
+    if (h->opt.nu1 > 0) {
+        if (h->persistent)
+            k_residual_restrict<R, DIM, true, true>
+                <<<wave((const void *)k_residual_restrict<R, DIM, true, true>, tiles_of(rg)), kBlock, 0, s>>>(view<R>(lb),
+                                                                                                          view<R>(cb));
+        else
+            k_residual_restrict<R, DIM, true, false><<<rg, kBlock, 0, s>>>(view<R>(lb), view<R>(cb));
+    } else {
+        if (h->persistent)
+            k_residual_restrict<R, DIM, false, true>
+                <<<wave((const void *)k_residual_restrict<R, DIM, false, true>, tiles_of(rg)), kBlock, 0, s>>>(
+                    view<R>(lb), view<R>(cb));
+        else
+            k_residual_restrict<R, DIM, false, false><<<rg, kBlock, 0, s>>>(view<R>(lb), view<R>(cb));
+    }
     counted(h);
     enqueue_vcycle<R, DIM>(h, s, l + 1);
-    k_prolong_add<R, DIM><<<cell_grid(lb, DIM, lb.n[0]), kBlock, 0, s>>>(view<R>(cb), view<R>(lb), bc_flags(h->grid));
+    const dim3 pg = cell_grid(lb, DIM, lb.n[0]);
+    if (h->persistent)
+        k_prolong_add<R, DIM, true><<<wave((const void *)k_prolong_add<R, DIM, true>, tiles_of(pg)), kBlock, 0, s>>>(
+            view<R>(cb), view<R>(lb), bc_flags(h->grid));
+    else
+        k_prolong_add<R, DIM, false><<<pg, kBlock, 0, s>>>(view<R>(cb), view<R>(lb), bc_flags(h->grid));
     counted(h);
     if (tm) cudaEventRecordWithFlags(h->ev[2], s, cudaEventRecordExternal);
     enqueue_smooth<R, DIM>(h, s, l, h->opt.nu2);
@@ -444,22 +522,53 @@ void enqueue_vcycle(const mg_handle *h, cudaStream_t s, int l) {
 template <int DIM>
 void enqueue_norm(const mg_handle *h, cudaStream_t s, bool after_sweep) {
     const LevelBuf &f = h->L[0];
-    if (after_sweep)
-        k_norm_partials<DIM, true><<<norm_grid(f, DIM), kBlock, 0, s>>>(view<double>(f), h->partial, h->ticket,
-                                                                       h->norms_d);
-    else
-        k_norm_partials<DIM, false><<<norm_grid(f, DIM), kBlock, 0, s>>>(view<double>(f), h->partial, h->ticket,
-                                                                        h->norms_d);
+    const dim3 ng = norm_grid(f, DIM);
+    if (after_sweep) {
+        if (h->persistent)
+            k_norm_partials<DIM, true, true><<<wave((const void *)k_norm_partials<DIM, true, true>, tiles_of(ng)), kBlock,
+                                               0, s>>>(view<double>(f), h->partial, h->ticket, h->norms_d);
+        else
+            k_norm_partials<DIM, true, false><<<ng, kBlock, 0, s>>>(view<double>(f), h->partial, h->ticket, h->norms_d);
+    } else {
+        if (h->persistent)
+            k_norm_partials<DIM, false, true><<<wave((const void *)k_norm_partials<DIM, false, true>, tiles_of(ng)),
+                                                kBlock, 0, s>>>(view<double>(f), h->partial, h->ticket, h->norms_d);
+        else
+            k_norm_partials<DIM, false, false><<<ng, kBlock, 0, s>>>(view<double>(f), h->partial, h->ticket, h->norms_d);
+    }
     counted(h);
 }
 
 template <int DIM>
 void enqueue_residual_to32(const mg_handle *h, cudaStream_t s) {
     const LevelBuf &f = h->L[0];
-    k_residual64_to32<DIM><<<norm_grid(f, DIM), kBlock, 0, s>>>(view<double>(f), f.b32, f.bt32, f.x32,
+    const dim3 ng = norm_grid(f, DIM);
+    if (h->persistent)
+        k_residual64_to32<DIM, true><<<wave((const void *)k_residual64_to32<DIM, true>, tiles_of(ng)), kBlock, 0, s>>>(
+            view<double>(f), f.b32, f.bt32, f.x32, h->partial, h->ticket, h->norms_d);
+    else
+        k_residual64_to32<DIM, false><<<ng, kBlock, 0, s>>>(view<double>(f), f.b32, f.bt32, f.x32,
                                                                          h->partial,
                                                                          h->ticket, h->norms_d);
     counted(h);
+}
+
+// Fills wave()'s cache for this handle's kernels outside any stream capture.
+template <typename R, int DIM>
+void warm_waves_r() {
+    wave((const void *)k_rbgs_colour<R, DIM, true>, 1);
+    wave((const void *)k_residual_restrict<R, DIM, true, true>, 1);
+    wave((const void *)k_residual_restrict<R, DIM, false, true>, 1);
+    wave((const void *)k_prolong_add<R, DIM, true>, 1);
+}
+
+template <int DIM>
+void warm_waves() {
+    warm_waves_r<double, DIM>();
+    warm_waves_r<float, DIM>();
+    wave((const void *)k_norm_partials<DIM, true, true>, 1);
+    wave((const void *)k_norm_partials<DIM, false, true>, 1);
+    wave((const void *)k_residual64_to32<DIM, true>, 1);
 }
 
 // FP64: one V-cycle, then the stopping norm, copied to pinned host memory.
@@ -489,7 +598,12 @@ mg_status capture(mg_handle *h, cudaGraphExec_t *out, long long *kernels, F &&bo
     body(h->cap);
     *kernels = h->enq - before;
     h->enq = before;
+    const cudaError_t le = cudaGetLastError();        // a launch refused while capturing
     cudaError_t e = cudaStreamEndCapture(h->cap, &graph);
+    if (le != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return fail(MG_ERR_CUDA, std::string("graph capture: a launch failed: ") + cudaGetErrorString(le));
+    }
     if (e != cudaSuccess) return fail(MG_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
     e = cudaGraphInstantiate(out, graph, 0);
     cudaGraphDestroy(graph);
@@ -673,7 +787,8 @@ mg_status setup_hierarchy(mg_handle *h, const double *lam, const double *const f
         in.fa[a] = a < DIM ? fad[a] : nullptr;
         in.fk[a] = a < DIM ? fkd[a] : nullptr;
     }
-    k_setup_fine<DIM><<<cell_grid(f, DIM, f.n[0]), kBlock, 0, s>>>(gm, in, setup_out(f, mixed), h->err_d);
+    k_setup_fine<DIM><<<cell_grid(f, DIM, f.n[0]), kBlock, 0, s>>>(
+        gm, in, setup_out(f, mixed), h->err_d);
     CK(cudaGetLastError());
     double hl = g.h;
     for (int l = 1; l < h->nlev; l++) {
@@ -682,7 +797,8 @@ mg_status setup_hierarchy(mg_handle *h, const double *lam, const double *const f
         SetupGeom cg = gm;
         for (int a = 0; a < 3; a++) cg.n[a] = C.n[a];
         cg.h = 2.0 * hl;
-        k_setup_coarse<DIM><<<cell_grid(C, DIM, C.n[0]), kBlock, 0, s>>>(cg, setup_fine_of(F, hl), setup_out(C, mixed),
+        k_setup_coarse<DIM><<<cell_grid(C, DIM, C.n[0]), kBlock, 0, s>>>(
+            cg, setup_fine_of(F, hl), setup_out(C, mixed),
                                                                          h->err_d);
         CK(cudaGetLastError());
         hl *= 2.0;
@@ -712,7 +828,7 @@ mg_status setup_hierarchy(mg_handle *h, const double *lam, const double *const f
     const int kl = std::min(h->nc - 1, 2 * off + 1);
     if (h->nc <= kBandSmemMax) {
         const size_t smem_lu = sizeof(double) * (size_t)h->nc * h->nc;
-        CK(cudaFuncSetAttribute(k_band_lu_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_lu));
+        CK(raise_smem_limit((const void *)k_band_lu_warp, (int)(sizeof(double) * kBandSmemMax * kBandSmemMax)));
         k_band_lu_warp<<<1, kLUThreads, smem_lu, a>>>(h->Mtmp, h->nc, kl, kl, h->piv, h->dinv, h->err_d);
         k_band_inv_cols_warp<<<(h->nc + 31) / 32, dim3(32, kInvRows), sizeof(double) * 32 * (size_t)(h->nc + kInvRows),
                                a>>>(h->Mtmp, h->piv, h->dinv, h->nc, kl, kl, h->Minv, mixed ? h->Minv32 : nullptr,
@@ -806,8 +922,6 @@ mg_status check_handle(const mg_handle *h, bool need_coeffs) {
 }
 
 // ---------------------------------------------------------------- tuning
-constexpr size_t kTailSmemMax = 200 * 1024;   // shared memory a tail CTA may use
-
 bool tail_level_ok(const mg_handle *h, int l, int ctas = kTailCtas) {
     if (!(l >= 1 && h->nlev - l >= 2 && h->nlev - l <= kTailMaxLevels && h->L[l].N <= kTailMaxCells)) return false;
     size_t smem = 0;
@@ -922,16 +1036,20 @@ mg_status autotune_impl(mg_handle *h, int reps, double *vcycle_ms) {
     }
     double best = 1e30;
     std::pair<int, int> pick = cand[0];
-    for (const auto &c : cand) {
-        h->tail_lev = c.first;
-        h->tail_ctas = c.second;
-        double ms = 0.0;
-        st = time_graph(h, 4 * reps + 1, &ms, [&](cudaStream_t s) { enqueue_vcycle<R, DIM>(h, s, 0); });
-        if (st) return st;
-        if (ms < best) { best = ms; pick = c; }
-    }
+    int pick_p = 0;
+    for (int persist = 0; persist < 2; persist++)
+        for (const auto &c : cand) {
+            h->tail_lev = c.first;
+            h->tail_ctas = c.second;
+            h->persistent = persist;
+            double ms = 0.0;
+            st = time_graph(h, 4 * reps + 1, &ms, [&](cudaStream_t s) { enqueue_vcycle<R, DIM>(h, s, 0); });
+            if (st) return st;
+            if (ms < best) { best = ms; pick = c; pick_p = persist; }
+        }
     h->tail_lev = pick.first;
     h->tail_ctas = pick.second;
+    h->persistent = pick_p;
     if (vcycle_ms) *vcycle_ms = best;
     return MG_OK;
 }
@@ -945,6 +1063,7 @@ void get_tuning(const mg_handle *h, mg_tuning *t) {
     }
     t->tail_level = h->tail_lev;
     t->tail_ctas = h->tail_ctas;
+    t->persistent = h->persistent;
 }
 
 }  // namespace
@@ -1025,6 +1144,9 @@ mg_status mg_create(const mg_grid *grid, const mg_options *opt, void *workspace,
         mg_destroy(h);
         return fail(MG_ERR_CUDA, "stream or pinned buffer creation failed");
     }
+    if (h->grid.dim == 2) warm_waves<2>();
+    else warm_waves<3>();
+    cudaGetLastError();
     *out = h;
     return MG_OK;
 }
@@ -1160,8 +1282,10 @@ mg_status mg_set_tuning(mg_handle *h, const mg_tuning *t) {
         h->sweep[l] = t->sweep[l];
         h->tile[l] = t->tile[l];
     }
+    if (t->persistent != 0 && t->persistent != 1) return fail(MG_ERR_INVALID_ARG, "persistent must be 0 or 1");
     h->tail_lev = no_tail ? h->nlev : t->tail_level;
     h->tail_ctas = no_tail ? kTailCtas : t->tail_ctas;
+    h->persistent = t->persistent;
     drop_graphs(h);
     return MG_OK;
 }

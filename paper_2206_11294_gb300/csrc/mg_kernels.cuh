@@ -30,6 +30,26 @@ __device__ __forceinline__ void block_coords(int local, int gx, int gy, int &bx,
     by = (local / gx) % gy;
     bz = local / (gx * gy);
 }
+
+// Tiles of a (gx, gy, gz) geometry.  P false: the launch grid is that
+// geometry, a block per tile (no index arithmetic before the loads).  P true,
+// a persistent launch: the grid is one wave (SMs x resident blocks per SM, at
+// most the number of tiles) and each block walks the tiles with a grid
+// stride, so no partial last wave leaves SMs idle.
+#define CMG_TILES(P, gx, gy, gz, body)                                                     \
+    do {                                                                                 \
+        if (!(P)) {                                                                      \
+            const int bx = blockIdx.x, by = blockIdx.y, bz = blockIdx.z;                 \
+            body;                                                                        \
+        } else {                                                                         \
+            const int tiles_ = (gx) * (gy) * (gz);                                       \
+            for (int v_ = blockIdx.x; v_ < tiles_; v_ += gridDim.x) {                    \
+                int bx, by, bz;                                                          \
+                block_coords(v_, (gx), (gy), bx, by, bz);                                \
+                body;                                                                    \
+            }                                                                            \
+        }                                                                                \
+    } while (0)
 __device__ __forceinline__ dq ldgq(const dq *p) {
     const double2 *q = reinterpret_cast<const double2 *>(p);
     double2 u = __ldg(q), v = __ldg(q + 1);
@@ -96,9 +116,10 @@ __device__ __forceinline__ void rbgs_colour_block(const Level<R> &L, int colour,
     L.x[c] = gs_update<R, NC>(L, c, sT, sp);
 }
 
-template <typename R, int DIM>
+template <typename R, int DIM, bool P>
 __global__ void __launch_bounds__(kBX * kBY) k_rbgs_colour(Level<R> L, int colour) {
-    rbgs_colour_block<R, DIM>(L, colour, blockIdx.x, blockIdx.y, blockIdx.z);
+    CMG_TILES(P, ((L.n0 + 1) / 2 + kBX - 1) / kBX, (L.n1 + kBY - 1) / kBY, DIM == 3 ? L.n2 : 1,
+              (rbgs_colour_block<R, DIM>(L, colour, bx, by, bz)));
 }
 
 // ---------------------------------------------------------------------------
@@ -237,9 +258,10 @@ __device__ __forceinline__ void residual_restrict_block(const Level<R> &F, const
     C.x[cc] = mk2<R>(R(0), R(0));
 }
 
-template <typename R, int DIM, bool RED>
+template <typename R, int DIM, bool RED, bool P>
 __global__ void __launch_bounds__(kBX * kBY) k_residual_restrict(Level<R> F, Level<R> C) {
-    residual_restrict_block<R, DIM, true, RED>(F, C, blockIdx.x, blockIdx.y, blockIdx.z);
+    CMG_TILES(P, (C.n0 + kBX - 1) / kBX, (C.n1 + kBY - 1) / kBY, DIM == 3 ? C.n2 : 1,
+              (residual_restrict_block<R, DIM, true, RED>(F, C, bx, by, bz)));
 }
 
 // ---------------------------------------------------------------------------
@@ -295,9 +317,10 @@ __device__ __forceinline__ void prolong_add_block(const Level<R> &C, const Level
     F.x[c] = xv;
 }
 
-template <typename R, int DIM>
+template <typename R, int DIM, bool P>
 __global__ void __launch_bounds__(kBX * kBY) k_prolong_add(Level<R> C, Level<R> F, BcFlags bc) {
-    prolong_add_block<R, DIM>(C, F, bc, blockIdx.x, blockIdx.y, blockIdx.z);
+    CMG_TILES(P, (F.n0 + kBX - 1) / kBX, (F.n1 + kBY - 1) / kBY, DIM == 3 ? F.n2 : 1,
+              (prolong_add_block<R, DIM>(C, F, bc, bx, by, bz)));
 }
 
 // ---------------------------------------------------------------------------
@@ -374,13 +397,15 @@ __device__ __forceinline__ void finish_norms(double2 *partial, int nblocks, unsi
     }
 }
 
-// Norm and FP64-residual blocks cover 64 x 32 cells (x, y) of one z-plane:
-// each thread visits several cells and accumulates its squares with FMAs, so
-// the per-block FP64 reduction tree (shuffles, then one warp) is spread over
-// many cells; on a part with few FP64 units per SM it would otherwise cost as
-// much as the cells themselves.
+// Norm and FP64-residual tiles cover 64 x 32 cells (x, y) of one z-plane,
+// eight per thread (four rows unrolled, for loads in flight).  The solo
+// kernels run one persistent wave: each thread
+// accumulates the squares of all its tiles' cells with FMAs and the block
+// reduces once, so the FP64 reduction tree (shuffles, then one warp) is spread
+// over many cells; on a part with few FP64 units per SM it would otherwise
+// cost as much as the cells themselves.  (The batched kernels reduce per tile.)
 constexpr int kNormCols = 64;
-constexpr int kNormRows = 4;   // rows per thread: the block spans kBY * kNormRows rows
+constexpr int kNormRows = 4;   // rows per thread: the tile spans kBY * kNormRows rows
 __host__ __device__ __forceinline__ int norm_gx(int n0) { return (n0 + kNormCols - 1) / kNormCols; }
 __host__ __device__ __forceinline__ int norm_gy(int n1) { return (n1 + kBY * kNormRows - 1) / (kBY * kNormRows); }
 
@@ -397,17 +422,17 @@ __device__ __forceinline__ void norm_cell(const Level<double> &L, int i, int j, 
     zp2 = fma(zp, zp, zp2);
 }
 
-// Sums of (Dinv r)_T^2 and (Dinv r)_p^2 over block (bx, by, bz) of the norm
-// grid (ceil(n0/64), ceil(n1/32), n2); valid in thread 0.
+// Sums of (Dinv r)_T^2 and (Dinv r)_p^2 over tile (bx, by, bz) of the norm
+// grid (ceil(n0/64), ceil(n1/32), n2), added to zT2, zp2 (norm_block: reduced
+// over the block, valid in thread 0).
 //
 // RED: x has just come out of a red-black sweep, so the block residual of
 // the black cells is exactly zero (z = gs_update - x recomputes the very
 // update that produced x, bit for bit) and each thread visits the one red
 // cell of its column pair per row.
 template <int DIM, bool RED = false>
-__device__ __forceinline__ double2 norm_block(const Level<double> &L, int bx, int by, int bz) {
+__device__ __forceinline__ void norm_tile(const Level<double> &L, int bx, int by, int bz, double &zT2, double &zp2) {
     const int k = DIM == 3 ? bz : 0;
-    double zT2 = 0.0, zp2 = 0.0;
 #pragma unroll
     for (int r = 0; r < kNormRows; r++) {
         const int j = (by * kNormRows + r) * kBY + threadIdx.y;
@@ -423,16 +448,24 @@ __device__ __forceinline__ double2 norm_block(const Level<double> &L, int bx, in
             }
         }
     }
+}
+
+template <int DIM, bool RED = false>
+__device__ __forceinline__ double2 norm_block(const Level<double> &L, int bx, int by, int bz) {
+    double zT2 = 0.0, zp2 = 0.0;
+    norm_tile<DIM, RED>(L, bx, by, bz, zT2, zp2);
     block_sum2(zT2, zp2);
     return make_double2(zT2, zp2);
 }
 
-template <int DIM, bool RED>
+template <int DIM, bool RED, bool P>
 __global__ void __launch_bounds__(kBX * kBY) k_norm_partials(Level<double> L, double2 *__restrict__ partial,
                                                            unsigned int *__restrict__ ticket, double *__restrict__ out) {
-    const double2 s = norm_block<DIM, RED>(L, blockIdx.x, blockIdx.y, blockIdx.z);
-    if (threadIdx.x == 0 && threadIdx.y == 0)
-        partial[blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)] = s;
+    double zT2 = 0.0, zp2 = 0.0;     // a block's tiles accumulate, then one reduction
+    CMG_TILES(P, norm_gx(L.n0), norm_gy(L.n1), DIM == 3 ? L.n2 : 1, (norm_tile<DIM, RED>(L, bx, by, bz, zT2, zp2)));
+    block_sum2(zT2, zp2);
+    const int blk = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    if (threadIdx.x == 0 && threadIdx.y == 0) partial[blk] = make_double2(zT2, zp2);
     finish_norms(partial, gridDim.x * gridDim.y * gridDim.z, ticket, out);
 }
 
@@ -462,11 +495,10 @@ __device__ __forceinline__ void residual64_to32_cell(const Level<double> &L, flo
 
 // Block (bx, by, bz) of the norm grid.
 template <int DIM>
-__device__ __forceinline__ double2 residual64_to32_block(const Level<double> &L, float2 *__restrict__ b32,
-                                                         float2 *__restrict__ bt32, float2 *__restrict__ e32,
-                                                         int bx, int by, int bz) {
+__device__ __forceinline__ void residual64_to32_tile(const Level<double> &L, float2 *__restrict__ b32,
+                                                     float2 *__restrict__ bt32, float2 *__restrict__ e32, int bx,
+                                                     int by, int bz, double &zT2, double &zp2) {
     const int k = DIM == 3 ? bz : 0;
-    double zT2 = 0.0, zp2 = 0.0;
 #pragma unroll
     for (int r = 0; r < kNormRows; r++) {
         const int j = (by * kNormRows + r) * kBY + threadIdx.y;
@@ -477,19 +509,30 @@ __device__ __forceinline__ double2 residual64_to32_block(const Level<double> &L,
             if (i < L.n0) residual64_to32_cell<DIM>(L, b32, bt32, e32, i, j, k, zT2, zp2);
         }
     }
+}
+
+template <int DIM>
+__device__ __forceinline__ double2 residual64_to32_block(const Level<double> &L, float2 *__restrict__ b32,
+                                                         float2 *__restrict__ bt32, float2 *__restrict__ e32,
+                                                         int bx, int by, int bz) {
+    double zT2 = 0.0, zp2 = 0.0;
+    residual64_to32_tile<DIM>(L, b32, bt32, e32, bx, by, bz, zT2, zp2);
     block_sum2(zT2, zp2);
     return make_double2(zT2, zp2);
 }
 
-template <int DIM>
+template <int DIM, bool P>
 __global__ void __launch_bounds__(kBX * kBY) k_residual64_to32(Level<double> L, float2 *__restrict__ b32,
                                                              float2 *__restrict__ bt32, float2 *__restrict__ e32,
                                                              double2 *__restrict__ partial,
                                                              unsigned int *__restrict__ ticket,
                                                              double *__restrict__ out) {
-    const double2 s = residual64_to32_block<DIM>(L, b32, bt32, e32, blockIdx.x, blockIdx.y, blockIdx.z);
-    if (threadIdx.x == 0 && threadIdx.y == 0)
-        partial[blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)] = s;
+    double zT2 = 0.0, zp2 = 0.0;
+    CMG_TILES(P, norm_gx(L.n0), norm_gy(L.n1), DIM == 3 ? L.n2 : 1,
+              (residual64_to32_tile<DIM>(L, b32, bt32, e32, bx, by, bz, zT2, zp2)));
+    block_sum2(zT2, zp2);
+    const int blk = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    if (threadIdx.x == 0 && threadIdx.y == 0) partial[blk] = make_double2(zT2, zp2);
     finish_norms(partial, gridDim.x * gridDim.y * gridDim.z, ticket, out);
 }
 
@@ -597,7 +640,8 @@ template <int DIM>
 __global__ void __launch_bounds__(kBX * kBY) k_prep_rhs(const __grid_constant__ Level<double> L,
                                                       const double2 *__restrict__ rhs, const __grid_constant__ BcVals bv,
                                                       int axisym, double r0, double h) {
-    prep_rhs_block<DIM>(L, rhs, nullptr, bv, axisym, r0, h, blockIdx.x, blockIdx.y, blockIdx.z);
+    CMG_TILES(false, (L.n0 + kBX - 1) / kBX, (L.n1 + kBY - 1) / kBY, DIM == 3 ? L.n2 : 1,
+              (prep_rhs_block<DIM>(L, rhs, nullptr, bv, axisym, r0, h, bx, by, bz)));
 }
 
 // y = L(x) (Eqs. 27-28): offdiag + boundary data + D x is s_i times the rows.
@@ -774,7 +818,8 @@ __device__ __forceinline__ void setup_fine_block(const SetupGeom &gm, const Setu
 
 template <int DIM>
 __global__ void __launch_bounds__(kBX * kBY) k_setup_fine(SetupGeom gm, SetupIn in, SetupOut o, int *__restrict__ err) {
-    setup_fine_block<DIM>(gm, in, o, err, blockIdx.x, blockIdx.y, blockIdx.z);
+    CMG_TILES(false, (gm.n[0] + kBX - 1) / kBX, (gm.n[1] + kBY - 1) / kBY, DIM == 3 ? gm.n[2] : 1,
+              (setup_fine_block<DIM>(gm, in, o, err, bx, by, bz)));
 }
 
 // Coarse level from the level below: S = mean of the children's S, l4 the
@@ -866,7 +911,8 @@ __device__ __forceinline__ void setup_coarse_block(const SetupGeom &cg, const Se
 template <int DIM>
 __global__ void __launch_bounds__(kBX * kBY) k_setup_coarse(SetupGeom cg, SetupFine F, SetupOut o,
                                                           int *__restrict__ err) {
-    setup_coarse_block<DIM>(cg, F, o, err, blockIdx.x, blockIdx.y, blockIdx.z);
+    CMG_TILES(false, (cg.n[0] + kBX - 1) / kBX, (cg.n[1] + kBY - 1) / kBY, DIM == 3 ? cg.n[2] : 1,
+              (setup_coarse_block<DIM>(cg, F, o, err, bx, by, bz)));
 }
 
 // FP32 copy of an FP64 array (the coarsest inverse of mixed precision).

@@ -12,7 +12,7 @@ from paper_2206_11294_gb300 import binding as B
 
 def _tuning(levels=5):
     return dict(levels=levels, sweep=["colour", "fused", "fused", "colour", "colour"][:levels],
-                tile=[0, 1, 2, 0, 0][:levels], tail_level=3, tail_ctas=8)
+                tile=[0, 1, 2, 0, 0][:levels], tail_level=3, tail_ctas=8, persistent=1)
 
 
 def test_key_depends_on_shape_precision_and_cycle_not_on_spacing():
@@ -61,13 +61,15 @@ def test_ctypes_mirror_roundtrip():
     t = B.MgTuning.from_dict(_tuning())
     assert t.sweep[1] == B.MG_SWEEP_FUSED and t.sweep[0] == B.MG_SWEEP_COLOUR
     assert t.as_dict() == _tuning()
-    # layout of the C struct: levels, sweep[32], tile[32], tail_level, tail_ctas (all int)
-    assert C.sizeof(B.MgTuning) == 4 * (1 + 2 * B.MG_MAX_LEVELS + 2)
+    # layout of the C struct: levels, sweep[32], tile[32], tail_level, tail_ctas, persistent (all int)
+    assert C.sizeof(B.MgTuning) == 4 * (1 + 2 * B.MG_MAX_LEVELS + 3)
     assert B.MgTuning.tail_ctas.offset == 4 * (1 + 2 * B.MG_MAX_LEVELS + 1)
+    assert B.MgTuning.persistent.offset == 4 * (1 + 2 * B.MG_MAX_LEVELS + 2)
 
 
 def test_describe():
-    assert describe(_tuning()) == "sweeps [C,F1,F2,C,C], tail from L3 on 8 CTAs"
+    assert describe(_tuning()) == "sweeps [C,F1,F2,C,C], tail from L3 on 8 CTAs, persistent waves"
     d = _tuning()
     d["tail_level"] = 5
+    d["persistent"] = 0
     assert describe(d).endswith("tail none")

@@ -53,8 +53,9 @@ def _variants(s):
     n = base["levels"]
     dim = s.grid.dim
     out = []
-    colour = dict(base, sweep=["colour"] * n, tile=[0] * n, tail_level=n, tail_ctas=8)
+    colour = dict(base, sweep=["colour"] * n, tile=[0] * n, tail_level=n, tail_ctas=8, persistent=0)
     out.append(colour)
+    out.append(dict(colour, persistent=1))
     if dim == 2:
         for t in range(3):
             out.append(dict(colour, sweep=["fused"] * n, tile=[t] * n))
