@@ -103,9 +103,15 @@ class HierarchyCache:
 
 
 class Engine:
-    """The GPU side: hierarchies are binding.Solver handles on a slot's stream."""
+    """The GPU side: hierarchies are binding.Solver handles on a slot's stream.
 
-    def __init__(self, device: int = 0, precision: str = "mixed", rtol: float = 1e-10, max_cycles: int = 60):
+    tune: kernel choices per hierarchy come from the library's autotuner,
+    measured the first time a hierarchy shape is seen (after its coefficients
+    are set, before its first solve) and reused for every later hierarchy of
+    that shape through a shared autotune.TuningTable (optionally a file)."""
+
+    def __init__(self, device: int = 0, precision: str = "mixed", rtol: float = 1e-10, max_cycles: int = 60,
+                 tune: bool = False, tuning_table=None):
         import torch
         from . import binding
         self.torch = torch
@@ -114,6 +120,13 @@ class Engine:
         self.precision = precision
         self.rtol = rtol
         self.max_cycles = max_cycles
+        self.tune = tune
+        self.table = tuning_table
+        self._tuned = set()
+        self._tune_lock = threading.Lock()
+        if tune and self.table is None:
+            from .autotune import TuningTable
+            self.table = TuningTable(None)
         torch.cuda.set_device(device)
 
     def new_stream(self):
@@ -138,6 +151,7 @@ class Engine:
                                    max_cycles=self.max_cycles, device=self.device, stream=stream)
 
     def free(self, solver):
+        self._tuned.discard(id(solver))
         solver.close()
 
     def run(self, solvers: List, problems: List, stream) -> List[Tuple[Any, dict]]:
@@ -151,6 +165,10 @@ class Engine:
             bs, xs = [], []
             for s, p in zip(solvers, problems):
                 s.set_coeffs(T(p.lam), [T(f) for f in p.fa], [T(f) for f in p.fk])
+                if self.tune and id(s) not in self._tuned:
+                    with self._tune_lock:            # one measurement at a time on the device
+                        self.table.tune(s)
+                        self._tuned.add(id(s))
                 bs.append(T(p.b))
                 xs.append(T(p.x0.copy()))
             if len(solvers) == 1:

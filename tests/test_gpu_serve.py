@@ -28,8 +28,8 @@ def _pool():
     return out
 
 
-@pytest.mark.parametrize("precision", ["mixed", "fp64"])
-def test_served_results_equal_solo(precision):
+@pytest.mark.parametrize("precision,tune", [("mixed", False), ("fp64", False), ("mixed", True)])
+def test_served_results_equal_solo(precision, tune):
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
@@ -44,7 +44,7 @@ def test_served_results_equal_solo(precision):
         st = s.solve(p.b, x)
         solo[p.name] = (x, st)
         s.close()
-    eng = Engine(device=0, precision=precision, rtol=1e-10, max_cycles=60)
+    eng = Engine(device=0, precision=precision, rtol=1e-10, max_cycles=60, tune=tune)
     sizes = {p.name: eng.size(p) for p in pool}
     budget = int(0.6 * sum(sizes.values()))          # forces waiting and eviction
     srv = Server(eng, hbm_budget=budget, slots=3, max_batch=4)
@@ -61,3 +61,5 @@ def test_served_results_equal_solo(precision):
     assert stats["requests"] == 30
     assert stats["peak_bytes"] <= budget
     assert stats["mean_batch"] > 1.0                  # queued requests were batched
+    if tune:                                          # each shape measured once, reused after
+        assert eng.table.measured <= len(pool) and eng.table.measured + eng.table.reused >= 1
