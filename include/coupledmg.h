@@ -166,6 +166,11 @@ MG_API mg_status mg_counters(const mg_handle *h, long long *launches, double *sm
  *               colour, in place) or MG_SWEEP_FUSED (2D grids only: one launch
  *               per sweep on tiles staged in shared memory, the red values of
  *               a one-cell ring recomputed per tile);
+ *               or MG_SWEEP_ASYNC (2D only: the fused sweep with every operand
+ *               of a tile staged by bulk asynchronous copies completing on an
+ *               mbarrier, persistent blocks, the next tiles' copies in flight
+ *               while a tile is computed; a tile whose two stages exceed one
+ *               block's 227 KB of shared memory is refused, e.g. 64 x 16 FP64);
  *   tile[l]     fused tile shape, cells: 0 = 64 x 16, 1 = 32 x 16, 2 = 32 x 8;
  *   tail_level  the levels from this one to the coarsest run as one kernel
  *               (smoothing, restriction, coarsest solve, prolongation as
@@ -184,7 +189,7 @@ MG_API mg_status mg_counters(const mg_handle *h, long long *launches, double *sm
  * level below the finest with at most 4096 cells, 8 CTAs.  mg_autotune also
  * tries one block. */
 #define MG_MAX_LEVELS 32
-enum { MG_SWEEP_COLOUR = 1, MG_SWEEP_FUSED = 2 };
+enum { MG_SWEEP_COLOUR = 1, MG_SWEEP_FUSED = 2, MG_SWEEP_ASYNC = 3 };
 typedef struct {
     int levels;                 /* mg_get_tuning: the hierarchy's levels (ignored by mg_set_tuning) */
     int sweep[MG_MAX_LEVELS];

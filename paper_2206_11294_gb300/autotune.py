@@ -95,8 +95,9 @@ class TuningTable:
 
 
 def describe(tuning: dict) -> str:
-    """Short text form: per level C (colour) or F<tile>, then the tail."""
-    lv = ",".join("C" if s == "colour" else f"F{t}" for s, t in zip(tuning["sweep"], tuning["tile"]))
+    """Short text form: per level C (colour), F<tile> (fused) or A<tile> (async fused), then the tail."""
+    lv = ",".join("C" if s == "colour" else (f"A{t}" if s == "async" else f"F{t}")
+                  for s, t in zip(tuning["sweep"], tuning["tile"]))
     tail = "none" if tuning["tail_level"] >= tuning["levels"] else \
         f"from L{tuning['tail_level']} on {tuning['tail_ctas']} CTAs"
     waves = ", persistent waves" if tuning.get("persistent") else ""

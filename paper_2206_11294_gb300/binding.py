@@ -35,7 +35,9 @@ EXPORTS = ["mg_default_options", "mg_workspace_size", "mg_create", "mg_set_coeff
            "mg_batch_set_tuning", "mg_batch_autotune"]
 
 MG_MAX_LEVELS = 32
-MG_SWEEP_COLOUR, MG_SWEEP_FUSED = 1, 2
+MG_SWEEP_COLOUR, MG_SWEEP_FUSED, MG_SWEEP_ASYNC = 1, 2, 3
+_SWEEP_NAMES = {MG_SWEEP_COLOUR: "colour", MG_SWEEP_FUSED: "fused", MG_SWEEP_ASYNC: "async"}
+_SWEEP_CODES = {v: k for k, v in _SWEEP_NAMES.items()}
 TILE_SHAPES = [(64, 16), (32, 16), (32, 8)]      # fused tile shapes by index (cells x, y)
 
 
@@ -73,7 +75,7 @@ class MgTuning(C.Structure):
 
     def as_dict(self) -> dict:
         n = self.levels
-        return dict(levels=n, sweep=["fused" if self.sweep[l] == MG_SWEEP_FUSED else "colour" for l in range(n)],
+        return dict(levels=n, sweep=[_SWEEP_NAMES.get(int(self.sweep[l]), "colour") for l in range(n)],
                     tile=[int(self.tile[l]) for l in range(n)], tail_level=int(self.tail_level),
                     tail_ctas=int(self.tail_ctas), persistent=int(self.persistent))
 
@@ -82,7 +84,7 @@ class MgTuning(C.Structure):
         t = MgTuning()
         t.levels = int(d.get("levels", len(d["sweep"])))
         for l, s in enumerate(d["sweep"]):
-            t.sweep[l] = MG_SWEEP_FUSED if s in ("fused", MG_SWEEP_FUSED) else MG_SWEEP_COLOUR
+            t.sweep[l] = _SWEEP_CODES[s] if s in _SWEEP_CODES else int(s)
         for l, s in enumerate(d["tile"]):
             t.tile[l] = int(s)
         t.tail_level = int(d["tail_level"])

@@ -22,6 +22,7 @@
 #include "mg_host.h"
 #include "mg_kernels.cuh"
 #include "mg_tail.cuh"
+#include "mg_async.cuh"
 
 using namespace cmg;
 
@@ -60,6 +61,8 @@ struct LevelBuf {
     float2 *x32, *b32, *bt32;
     float2 *xalt32;
     float2 *G32[3];
+    float2 *G32p0;          // FP32 axis-0 faces with an even row pitch p0 (2D mixed: tensor-map loads)
+    int p0;
     fq *D32, *Dinv32, *W32;
     float *l4_32;
 };
@@ -94,6 +97,8 @@ struct mg_handle {
     int sweep[kMaxLevels]; // per level: MG_SWEEP_COLOUR or MG_SWEEP_FUSED
     int tile[kMaxLevels];  // per level: fused tile shape (index into kTileX / kTileY)
     int persistent;        // colour sweeps, restriction, prolongation: one persistent wave (1) or a block per tile (0)
+    TmaLevel *tmaps;       // tensor maps per (level, precision, tile), built on first use (host memory)
+    unsigned char *tmap_ok;
     double *Minv, *Mtmp;
     double *Mwork;         // coarse inverse: columns before the transpose (banded path)
     int *piv;              // coarse inverse: pivot rows (banded path)
@@ -223,6 +228,10 @@ void plan(mg_handle *h, char *base, size_t *bytes) {
             l.b32 = P.take<float2>(l.N);
             if (g.dim == 2) l.xalt32 = P.take<float2>(l.N);
             for (int a = 0; a < g.dim; a++) l.G32[a] = P.take<float2>(l.nf[a]);
+            if (g.dim == 2) {
+                l.p0 = (n[0] + 2) & ~1;
+                l.G32p0 = P.take<float2>((long long)l.p0 * n[1]);
+            }
             l.D32 = P.take<fq>(l.N);
             l.Dinv32 = P.take<fq>(l.N);
             l.W32 = P.take<fq>(l.N);
@@ -269,7 +278,7 @@ void plan(mg_handle *h, char *base, size_t *bytes) {
     h->partial = P.take<double2>(h->npartial);
     h->norms_d = P.take<double>(8);
     h->ticket = P.take<unsigned int>(1);
-    h->err_d = P.take<int>(1);
+    h->err_d = P.take<int>(2);            // [0] set-up flags, [1] bounded waits that gave up (per solve)
     *bytes = P.off + kAlign;
 }
 
@@ -372,6 +381,122 @@ void launch_fused(const LevelBuf &lb, const Level<R> &v, cudaStream_t s) {
     k_rbgs_fused2d<R, TX, TY><<<gf, kBlock, 0, s>>>(v, xa, v.x);
 }
 
+// ---------------------------------------------------------------- TMA sweeps
+// Shared memory of the TMA fused sweep with tile `tile`.
+template <typename R>
+int async_smem(int tile) {
+    switch (tile) {
+        case 1: return tma_smem_bytes<R, kTileX[1], kTileY[1]>();
+        case 2: return tma_smem_bytes<R, kTileX[2], kTileY[2]>();
+        default: return tma_smem_bytes<R, kTileX[0], kTileY[0]>();
+    }
+}
+constexpr int kSmemOptInMax = 227 * 1024;
+
+// Whether level l can run the TMA sweep with this tile in precision R.
+template <typename R>
+bool async_ok(const mg_handle *h, int l, int tile) {
+    if (h->grid.dim != 2 || async_smem<R>(tile) > kSmemOptInMax) return false;
+    if (sizeof(R) == 4 && ((h->L[l].n[0] & 1) || !h->L[l].G32p0)) return false;   // FP32 rows: 8 n0 bytes
+    return true;
+}
+
+using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                 const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiled encode_tiled() {
+    static EncodeTiled fn = []() -> EncodeTiled {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        return reinterpret_cast<EncodeTiled>(p);
+    }();
+    return fn;
+}
+
+// A 2D map over rows of `width` scalars (row pitch `pitch` scalars), box bx x by.
+bool map2d(CUtensorMap *m, bool f32, void *base, long long width, long long pitch, long long rows, int bx, int by) {
+    const EncodeTiled enc = encode_tiled();
+    if (!enc) return false;
+    const long long es = f32 ? 4 : 8;
+    const cuuint64_t dims[2] = {(cuuint64_t)width, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)(pitch * es)};
+    const cuuint32_t box[2] = {(cuuint32_t)bx, (cuuint32_t)by};
+    const cuuint32_t estr[2] = {1, 1};
+    return enc(m, f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, base, dims, strides, box,
+               estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// The 2x2 blocks W as a 3D map (4 scalars, n0 cells, n1 rows), box 4 x bx x by.
+bool map3d_w(CUtensorMap *m, bool f32, void *base, long long n0, long long n1, int bx, int by) {
+    const EncodeTiled enc = encode_tiled();
+    if (!enc) return false;
+    const long long es = f32 ? 4 : 8;
+    const cuuint64_t dims[3] = {4, (cuuint64_t)n0, (cuuint64_t)n1};
+    const cuuint64_t strides[2] = {(cuuint64_t)(4 * es), (cuuint64_t)(4 * es * n0)};
+    const cuuint32_t box[3] = {4, (cuuint32_t)bx, (cuuint32_t)by};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    return enc(m, f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, base, dims, strides, box,
+               estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Tensor maps of level l for the TMA sweep with tile (TX, TY), built once per handle.
+template <typename R, int TX, int TY>
+const TmaLevel *tma_maps(const mg_handle *hc, int l, int tile) {
+    mg_handle *h = const_cast<mg_handle *>(hc);
+    const int prec = sizeof(R) == 4 ? 1 : 0;
+    const int idx = (l * 2 + prec) * kTileShapes + tile;
+    if (!h->tmaps) {
+        h->tmaps = new (std::nothrow) TmaLevel[kMaxLevels * 2 * kTileShapes];
+        h->tmap_ok = new (std::nothrow) unsigned char[kMaxLevels * 2 * kTileShapes]();
+        if (!h->tmaps || !h->tmap_ok) return nullptr;
+    }
+    if (h->tmap_ok[idx]) return &h->tmaps[idx];
+    const LevelBuf &b = h->L[l];
+    const long long n0 = b.n[0], n1 = b.n[1];
+    const bool f32 = prec == 1;
+    TmaLevel &m = h->tmaps[idx];
+    void *x = f32 ? (void *)b.x32 : (void *)b.x, *xa = f32 ? (void *)b.xalt32 : (void *)b.xalt;
+    void *g0 = f32 ? (void *)b.G32p0 : (void *)b.G[0];
+    const long long p0 = f32 ? b.p0 : n0 + 1;
+    void *g1 = f32 ? (void *)b.G32[1] : (void *)b.G[1];
+    void *bt = f32 ? (void *)b.bt32 : (void *)b.bt;
+    void *w = f32 ? (void *)b.W32 : (void *)b.W;
+    const int W2 = 2 * (TX + 4);
+    const bool ok = map2d(&m.x[0], f32, x, 2 * n0, 2 * n0, n1, W2, TY + 4) &&
+                    map2d(&m.x[1], f32, xa, 2 * n0, 2 * n0, n1, W2, TY + 4) &&
+                    map2d(&m.g0, f32, g0, 2 * (n0 + 1), 2 * p0, n1, W2, TY + 2) &&
+                    map2d(&m.g1, f32, g1, 2 * n0, 2 * n0, n1 + 1, W2, TY + 3) &&
+                    map2d(&m.bt, f32, bt, 2 * n0, 2 * n0, n1, W2, TY + 2) &&
+                    map3d_w(&m.w, f32, w, n0, n1, TX + 4, TY + 2);
+    if (!ok) return nullptr;
+    h->tmap_ok[idx] = 1;
+    return &m;
+}
+
+template <typename R, int TX, int TY>
+void launch_fused_tma(const mg_handle *h, int l, int tile, const Level<R> &v, cudaStream_t s) {
+    const TmaLevel *m = tma_maps<R, TX, TY>(h, l, tile);
+    if (!m) return;                           // refused by mg_set_tuning before it can get here
+    const LevelBuf &lb = h->L[l];
+    const int smem = tma_smem_bytes<R, TX, TY>();
+    const void *fn = (const void *)k_rbgs_fused2d_tma<R, TX, TY>;
+    raise_smem_limit(fn, smem);
+    const long long tiles = (long long)((lb.n[0] + TX - 1) / TX) * ((lb.n[1] + TY - 1) / TY);
+    const unsigned grid = wave(fn, tiles, smem);
+    typename Vec<R>::v2 *xa = xalt_of<R>(lb);
+    k_rbgs_fused2d_tma<R, TX, TY><<<grid, kBlock, smem, s>>>(m->x[0], m->g0, m->g1, m->bt, m->w, v, xa, h->err_d + 1);
+    k_rbgs_fused2d_tma<R, TX, TY><<<grid, kBlock, smem, s>>>(m->x[1], m->g0, m->g1, m->bt, m->w, v, v.x, h->err_d + 1);
+}
+
 // `sweeps` red-black sweeps on level l with the given kernel choice.  Fused
 // (2D only): pairs of sweeps run as fused launches x -> xalt -> x; a leftover
 // odd sweep (and every non-fused sweep) runs as two colour launches in place.
@@ -386,6 +511,14 @@ void enqueue_sweeps(const mg_handle *h, cudaStream_t s, int l, int sweeps, int k
             if (tile == 1) launch_fused<R, kTileX[1], kTileY[1]>(lb, v, s);
             else if (tile == 2) launch_fused<R, kTileX[2], kTileY[2]>(lb, v, s);
             else launch_fused<R, kTileX[0], kTileY[0]>(lb, v, s);
+            counted(h, 2);
+        }
+    }
+    if (DIM == 2 && kind == MG_SWEEP_ASYNC) {
+        for (; q + 1 < sweeps; q += 2) {
+            if (tile == 1) launch_fused_tma<R, kTileX[1], kTileY[1]>(h, l, 1, v, s);
+            else if (tile == 2) launch_fused_tma<R, kTileX[2], kTileY[2]>(h, l, 2, v, s);
+            else launch_fused_tma<R, kTileX[0], kTileY[0]>(h, l, 0, v, s);
             counted(h, 2);
         }
     }
@@ -689,7 +822,7 @@ mg_status accumulate_timing(mg_handle *h) {
     CK(cudaEventElapsedTime(&b, h->ev[2], h->ev[3]));
     h->smooth_ms += (double)a + (double)b;
     long long l1, s1, l2, s2;
-    const bool fused = h->grid.dim == 2 && h->sweep[0] == MG_SWEEP_FUSED;
+    const bool fused = h->grid.dim == 2 && (h->sweep[0] == MG_SWEEP_FUSED || h->sweep[0] == MG_SWEEP_ASYNC);
     smooth_launches(fused, h->opt.nu1, &l1, &s1);
     smooth_launches(fused, h->opt.nu2, &l2, &s2);
     h->smooth_launches += l1 + l2;
@@ -724,6 +857,9 @@ SetupOut setup_out(const LevelBuf &l, bool mixed) {
         o.Dinv32 = l.Dinv32;
         o.W32 = l.W32;
         o.l432 = l.l4_32;
+        o.G0p = l.G32p0;
+        o.p0 = l.p0;
+        o.n0 = l.n[0];
     }
     return o;
 }
@@ -1011,11 +1147,13 @@ mg_status autotune_impl(mg_handle *h, int reps, double *vcycle_ms) {
     mg_status st;
     // sweeps, level by level (the coarsest level is solved, not smoothed)
     for (int l = 0; l + 1 < h->nlev; l++) {
-        const int ncand = DIM == 2 ? 1 + kTileShapes : 1;
+        const int ncand = DIM == 2 ? 1 + 2 * kTileShapes : 1;
         double best = 1e30;
         int kind = MG_SWEEP_COLOUR, tile = 0;
         for (int c = 0; c < ncand; c++) {
-            const int ck = c == 0 ? MG_SWEEP_COLOUR : MG_SWEEP_FUSED, ct = c == 0 ? 0 : c - 1;
+            const int ck = c == 0 ? MG_SWEEP_COLOUR : (c <= kTileShapes ? MG_SWEEP_FUSED : MG_SWEEP_ASYNC);
+            const int ct = c == 0 ? 0 : (c - 1) % kTileShapes;
+            if (ck == MG_SWEEP_ASYNC && !async_ok<R>(h, l, ct)) continue;
             double ms = 0.0;
             st = time_graph(h, 5, &ms, [&](cudaStream_t s) {
                 for (int r = 0; r < reps; r++) enqueue_sweeps<R, DIM>(h, s, l, 2, ck, ct);
@@ -1136,7 +1274,7 @@ mg_status mg_create(const mg_grid *grid, const mg_options *opt, void *workspace,
         cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&h->ev_asm, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&h->ev_inv, cudaEventDisableTiming) != cudaSuccess ||
-        cudaMallocHost(&h->errh, sizeof(int)) != cudaSuccess ||
+        cudaMallocHost(&h->errh, 2 * sizeof(int)) != cudaSuccess ||
         cudaMallocHost(&h->norms_h, 8 * sizeof(double)) != cudaSuccess ||
         cudaMemsetAsync(h->ticket, 0, sizeof(unsigned int), h->stream) != cudaSuccess ||
         cudaStreamSynchronize(h->stream) != cudaSuccess) {
@@ -1178,6 +1316,7 @@ mg_status mg_solve(mg_handle *h, const double *rhs, double *x, int on_device, mg
     if (st) return st;
     if (!rhs || !x) return fail(MG_ERR_INVALID_ARG, "rhs and x must not be NULL");
     DeviceGuard dg(h->device);
+    CK(cudaMemsetAsync(h->err_d + 1, 0, sizeof(int), h->stream));
     if ((st = prep(h, rhs, x, on_device))) return st;
     mg_stats s;
     std::memset(&s, 0, sizeof(s));
@@ -1188,9 +1327,10 @@ mg_status mg_solve(mg_handle *h, const double *rhs, double *x, int on_device, mg
     if (st) return st;
     if ((st = x_out(h, x, on_device))) return st;
     CK(cudaStreamWaitEvent(h->stream, h->ev_inv, 0));
-    CK(cudaMemcpyAsync(h->errh, h->err_d, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(h->errh, h->err_d, 2 * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
-    if (*h->errh & 4) return fail(MG_ERR_INVALID_COEFF, "the coarsest-level matrix is singular");
+    if (h->errh[0] & 4) return fail(MG_ERR_INVALID_COEFF, "the coarsest-level matrix is singular");
+    if (h->errh[1] & kErrAsyncTimeout) return fail(MG_ERR_TIMEOUT, "an asynchronous copy did not complete in time");
     s.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     if (stats) *stats = s;
     if (s.status != MG_OK) {
@@ -1262,11 +1402,15 @@ mg_status mg_set_tuning(mg_handle *h, const mg_tuning *t) {
     if (st) return st;
     if (!t) return fail(MG_ERR_INVALID_ARG, "tuning is NULL");
     for (int l = 0; l < h->nlev; l++) {
-        if (t->sweep[l] != MG_SWEEP_COLOUR && t->sweep[l] != MG_SWEEP_FUSED)
-            return fail(MG_ERR_INVALID_ARG, "sweep kind must be MG_SWEEP_COLOUR or MG_SWEEP_FUSED");
-        if (t->sweep[l] == MG_SWEEP_FUSED && h->grid.dim != 2)
+        if (t->sweep[l] != MG_SWEEP_COLOUR && t->sweep[l] != MG_SWEEP_FUSED && t->sweep[l] != MG_SWEEP_ASYNC)
+            return fail(MG_ERR_INVALID_ARG, "sweep kind must be MG_SWEEP_COLOUR, MG_SWEEP_FUSED or MG_SWEEP_ASYNC");
+        if (t->sweep[l] != MG_SWEEP_COLOUR && h->grid.dim != 2)
             return fail(MG_ERR_INVALID_ARG, "fused sweeps are for 2D grids");
         if (t->tile[l] < 0 || t->tile[l] >= kTileShapes) return fail(MG_ERR_INVALID_ARG, "tile shape out of range");
+        if (t->sweep[l] == MG_SWEEP_ASYNC && l + 1 < h->nlev &&
+            !(h->opt.precision == MG_MIXED ? async_ok<float>(h, l, t->tile[l]) : async_ok<double>(h, l, t->tile[l])))
+            return fail(MG_ERR_INVALID_ARG, "async sweep does not fit this level (shared memory per block, or an "
+                                            "odd FP32 row length)");
     }
     const bool no_tail = t->tail_level >= h->nlev;
     if (!no_tail && (t->tail_ctas != 1 && t->tail_ctas != kTailCtas && t->tail_ctas != 16))
@@ -1386,6 +1530,8 @@ mg_status mg_destroy(mg_handle *h) {
         if (h->ev[q]) cudaEventDestroy(h->ev[q]);
     if (h->norms_h) cudaFreeHost(h->norms_h);
     if (h->owns_arena && h->arena) cudaFree(h->arena);
+    delete[] h->tmaps;
+    delete[] h->tmap_ok;
     delete h;
     return MG_OK;
 }

@@ -117,7 +117,7 @@ __device__ __forceinline__ void rbgs_colour_block(const Level<R> &L, int colour,
 }
 
 template <typename R, int DIM, bool P>
-__global__ void __launch_bounds__(kBX * kBY) k_rbgs_colour(Level<R> L, int colour) {
+__global__ void __launch_bounds__(kBX * kBY, 8) k_rbgs_colour(Level<R> L, int colour) {
     CMG_TILES(P, ((L.n0 + 1) / 2 + kBX - 1) / kBX, (L.n1 + kBY - 1) / kBY, DIM == 3 ? L.n2 : 1,
               (rbgs_colour_block<R, DIM>(L, colour, bx, by, bz)));
 }
@@ -683,6 +683,8 @@ struct SetupOut {                 // one level's outputs
     float2 *G32[3];               // FP32 copies (mixed precision), or NULL
     fq *D32, *Dinv32, *W32;
     float *l432;
+    float2 *G0p;                  // 2D mixed: FP32 axis-0 faces again, row pitch p0 (even), or NULL
+    int p0, n0;
 };
 
 struct SetupGeom {
@@ -713,6 +715,10 @@ __device__ __forceinline__ void finish_cell(const SetupOut &o, long long c, cons
             if (own[a][sd]) {
                 o.G[a][fid[a][sd]] = g[a][sd];
                 if (o.G32[a]) o.G32[a][fid[a][sd]] = make_float2((float)g[a][sd].x, (float)g[a][sd].y);
+                if (a == 0 && o.G0p) {
+                    const long long f = fid[0][sd], row = f / (o.n0 + 1);
+                    o.G0p[f - row * (o.n0 + 1) + row * o.p0] = make_float2((float)g[0][sd].x, (float)g[0][sd].y);
+                }
             }
         }
     o.S[c] = S;

@@ -67,6 +67,13 @@ def test_ctypes_mirror_roundtrip():
     assert B.MgTuning.persistent.offset == 4 * (1 + 2 * B.MG_MAX_LEVELS + 2)
 
 
+def test_sweep_names_roundtrip():
+    d = _tuning()
+    d["sweep"] = ["async", "fused", "colour", "async", "colour"]
+    assert B.MgTuning.from_dict(d).as_dict() == d
+    assert describe(d).startswith("sweeps [A0,F1,C,A0,C]")
+
+
 def test_describe():
     assert describe(_tuning()) == "sweeps [C,F1,F2,C,C], tail from L3 on 8 CTAs, persistent waves"
     d = _tuning()

@@ -59,6 +59,8 @@ def _variants(s):
     if dim == 2:
         for t in range(3):
             out.append(dict(colour, sweep=["fused"] * n, tile=[t] * n))
+        for t in range(3):
+            out.append(dict(colour, sweep=["async"] * n, tile=[t] * n))
         out.append(dict(colour, sweep=["fused" if l % 2 else "colour" for l in range(n)],
                         tile=[l % 3 for l in range(n)]))
     sizes = s.levels()
@@ -83,7 +85,8 @@ def test_every_choice_gives_identical_results(torch_cuda, name, precision):
         except MgError as e:            # 16-CTA clusters where the device does not allow them, or a
             # one-block tail whose levels do not fit its shared memory
             assert (v["tail_ctas"] == 16 and "cluster size" in str(e)) or \
-                (v["tail_ctas"] == 1 and "shared memory" in str(e)), str(e)
+                (v["tail_ctas"] == 1 and "shared memory" in str(e)) or \
+                ("async" in v["sweep"] and "does not fit" in str(e)), str(e)
             continue
         assert s.tuning()["sweep"] == v["sweep"]
         assert st["cycles"] == st0["cycles"], v
@@ -103,7 +106,7 @@ def test_autotune_picks_valid_choice_and_keeps_results(torch_cuda, name, precisi
     assert ms > 0
     n = len(s0.levels())
     assert tuning["levels"] == n
-    assert all(k in ("colour", "fused") for k in tuning["sweep"])
+    assert all(k in ("colour", "fused", "async") for k in tuning["sweep"])
     if p.grid.dim == 3:
         assert set(tuning["sweep"]) == {"colour"}
     assert tuning["tail_level"] >= n or 1 <= tuning["tail_level"] <= n - 2
@@ -121,6 +124,7 @@ def test_set_tuning_rejects_bad_choices(torch_cuda):
     s3, _, _ = _solve(PROBS["3d"])
     s2, _, _ = _solve(PROBS["2d"])
     for s, mutate in [(s3, lambda t: t["sweep"].__setitem__(0, "fused")),
+                      (s3, lambda t: t["sweep"].__setitem__(0, "async")),
                       (s2, lambda t: t["tile"].__setitem__(1, 3)),
                       (s2, lambda t: t.__setitem__("tail_level", 0)),
                       (s2, lambda t: t.__setitem__("tail_level", t["levels"] - 1)),
