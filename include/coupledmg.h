@@ -163,7 +163,8 @@ MG_API mg_status mg_counters(const mg_handle *h, long long *launches, double *sm
  * bit (the same per-cell arithmetic in the same order); only the launch
  * structure differs.
  *   sweep[l]    level l's red-black sweeps: MG_SWEEP_COLOUR (one launch per
- *               colour, in place) or MG_SWEEP_FUSED (2D grids only: one launch
+ *               colour, in place), MG_SWEEP_COLOUR2 (the same with two rows
+ *               per thread, half the blocks) or MG_SWEEP_FUSED (2D grids only: one launch
  *               per sweep on tiles staged in shared memory, the red values of
  *               a one-cell ring recomputed per tile);
  *               or MG_SWEEP_ASYNC (2D only: the fused sweep with every operand
@@ -189,7 +190,7 @@ MG_API mg_status mg_counters(const mg_handle *h, long long *launches, double *sm
  * level below the finest with at most 4096 cells, 8 CTAs.  mg_autotune also
  * tries one block. */
 #define MG_MAX_LEVELS 32
-enum { MG_SWEEP_COLOUR = 1, MG_SWEEP_FUSED = 2, MG_SWEEP_ASYNC = 3 };
+enum { MG_SWEEP_COLOUR = 1, MG_SWEEP_FUSED = 2, MG_SWEEP_ASYNC = 3, MG_SWEEP_COLOUR2 = 4 };
 typedef struct {
     int levels;                 /* mg_get_tuning: the hierarchy's levels (ignored by mg_set_tuning) */
     int sweep[MG_MAX_LEVELS];

@@ -95,9 +95,10 @@ class TuningTable:
 
 
 def describe(tuning: dict) -> str:
-    """Short text form: per level C (colour), F<tile> (fused) or A<tile> (async fused), then the tail."""
-    lv = ",".join("C" if s == "colour" else (f"A{t}" if s == "async" else f"F{t}")
-                  for s, t in zip(tuning["sweep"], tuning["tile"]))
+    """Short text form: per level C (colour), C2 (colour, two rows per thread), F<tile> (fused) or
+    A<tile> (TMA-fed fused), then the tail."""
+    code = {"colour": lambda t: "C", "colour2": lambda t: "C2", "async": lambda t: f"A{t}", "fused": lambda t: f"F{t}"}
+    lv = ",".join(code[s](t) for s, t in zip(tuning["sweep"], tuning["tile"]))
     tail = "none" if tuning["tail_level"] >= tuning["levels"] else \
         f"from L{tuning['tail_level']} on {tuning['tail_ctas']} CTAs"
     waves = ", persistent waves" if tuning.get("persistent") else ""

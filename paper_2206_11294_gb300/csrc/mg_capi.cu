@@ -523,6 +523,14 @@ void enqueue_sweeps(const mg_handle *h, cudaStream_t s, int l, int sweeps, int k
         }
     }
     const dim3 gr = cell_grid(lb, DIM, (lb.n[0] + 1) / 2);
+    if (kind == MG_SWEEP_COLOUR2) {
+        const dim3 g2(gr.x, (unsigned)((lb.n[1] + 2 * kBY - 1) / (2 * kBY)), gr.z);
+        for (; q < sweeps; q++) {
+            k_rbgs_colour2<R, DIM><<<g2, kBlock, 0, s>>>(v, 0);
+            k_rbgs_colour2<R, DIM><<<g2, kBlock, 0, s>>>(v, 1);
+            counted(h, 2);
+        }
+    }
     for (; q < sweeps; q++) {
         if (h->persistent) {
             const unsigned gw = wave((const void *)k_rbgs_colour<R, DIM, true>, tiles_of(gr));
@@ -1147,12 +1155,14 @@ mg_status autotune_impl(mg_handle *h, int reps, double *vcycle_ms) {
     mg_status st;
     // sweeps, level by level (the coarsest level is solved, not smoothed)
     for (int l = 0; l + 1 < h->nlev; l++) {
-        const int ncand = DIM == 2 ? 1 + 2 * kTileShapes : 1;
+        // candidates: colour, colour with two rows per thread, then (2D) fused and TMA-fed fused per tile
+        const int ncand = DIM == 2 ? 2 + 2 * kTileShapes : 2;
         double best = 1e30;
         int kind = MG_SWEEP_COLOUR, tile = 0;
         for (int c = 0; c < ncand; c++) {
-            const int ck = c == 0 ? MG_SWEEP_COLOUR : (c <= kTileShapes ? MG_SWEEP_FUSED : MG_SWEEP_ASYNC);
-            const int ct = c == 0 ? 0 : (c - 1) % kTileShapes;
+            const int ck = c == 0 ? MG_SWEEP_COLOUR
+                                  : (c == 1 ? MG_SWEEP_COLOUR2 : (c < 2 + kTileShapes ? MG_SWEEP_FUSED : MG_SWEEP_ASYNC));
+            const int ct = c < 2 ? 0 : (c - 2) % kTileShapes;
             if (ck == MG_SWEEP_ASYNC && !async_ok<R>(h, l, ct)) continue;
             double ms = 0.0;
             st = time_graph(h, 5, &ms, [&](cudaStream_t s) {
@@ -1402,9 +1412,11 @@ mg_status mg_set_tuning(mg_handle *h, const mg_tuning *t) {
     if (st) return st;
     if (!t) return fail(MG_ERR_INVALID_ARG, "tuning is NULL");
     for (int l = 0; l < h->nlev; l++) {
-        if (t->sweep[l] != MG_SWEEP_COLOUR && t->sweep[l] != MG_SWEEP_FUSED && t->sweep[l] != MG_SWEEP_ASYNC)
-            return fail(MG_ERR_INVALID_ARG, "sweep kind must be MG_SWEEP_COLOUR, MG_SWEEP_FUSED or MG_SWEEP_ASYNC");
-        if (t->sweep[l] != MG_SWEEP_COLOUR && h->grid.dim != 2)
+        if (t->sweep[l] != MG_SWEEP_COLOUR && t->sweep[l] != MG_SWEEP_FUSED && t->sweep[l] != MG_SWEEP_ASYNC &&
+            t->sweep[l] != MG_SWEEP_COLOUR2)
+            return fail(MG_ERR_INVALID_ARG, "sweep kind must be MG_SWEEP_COLOUR, MG_SWEEP_COLOUR2, MG_SWEEP_FUSED or "
+                                            "MG_SWEEP_ASYNC");
+        if ((t->sweep[l] == MG_SWEEP_FUSED || t->sweep[l] == MG_SWEEP_ASYNC) && h->grid.dim != 2)
             return fail(MG_ERR_INVALID_ARG, "fused sweeps are for 2D grids");
         if (t->tile[l] < 0 || t->tile[l] >= kTileShapes) return fail(MG_ERR_INVALID_ARG, "tile shape out of range");
         if (t->sweep[l] == MG_SWEEP_ASYNC && l + 1 < h->nlev &&

@@ -116,6 +116,35 @@ __device__ __forceinline__ void rbgs_colour_block(const Level<R> &L, int colour,
     L.x[c] = gs_update<R, NC>(L, c, sT, sp);
 }
 
+// Two rows per thread (rows j and j + 8 of a 32 x 16 block of colour cells):
+// both updates are formed before either is stored, so their loads overlap,
+// and half as many blocks make a launch (a grid whose block count would leave
+// a partial last wave can then fit one wave).  Same per-cell arithmetic.
+template <typename R, int DIM>
+__global__ void __launch_bounds__(kBX * kBY, 7) k_rbgs_colour2(Level<R> L, int colour) {
+    using V2 = typename Vec<R>::v2;
+    const int k = DIM == 3 ? (int)blockIdx.z : 0;
+    V2 out[2];
+    long long cid[2];
+    bool ok[2];
+#pragma unroll
+    for (int r = 0; r < 2; r++) {
+        const int j = (int)blockIdx.y * 2 * kBY + r * kBY + (int)threadIdx.y;
+        const int par = (j + k + colour) & 1;
+        const int i = 2 * ((int)blockIdx.x * kBX + (int)threadIdx.x) + par;
+        ok[r] = j < L.n1 && i < L.n0;
+        cid[r] = cell_id(i, j, k, L.n0, L.n1);
+        if (ok[r]) {
+            R sT, sp;
+            offdiag<R, DIM, false>(L, L.x, i, j, k, cid[r], sT, sp);
+            out[r] = gs_update<R>(L, cid[r], sT, sp);
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < 2; r++)
+        if (ok[r]) L.x[cid[r]] = out[r];
+}
+
 template <typename R, int DIM, bool P>
 __global__ void __launch_bounds__(kBX * kBY, 8) k_rbgs_colour(Level<R> L, int colour) {
     CMG_TILES(P, ((L.n0 + 1) / 2 + kBX - 1) / kBX, (L.n1 + kBY - 1) / kBY, DIM == 3 ? L.n2 : 1,

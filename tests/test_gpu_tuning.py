@@ -56,6 +56,7 @@ def _variants(s):
     colour = dict(base, sweep=["colour"] * n, tile=[0] * n, tail_level=n, tail_ctas=8, persistent=0)
     out.append(colour)
     out.append(dict(colour, persistent=1))
+    out.append(dict(colour, sweep=["colour2"] * n))
     if dim == 2:
         for t in range(3):
             out.append(dict(colour, sweep=["fused"] * n, tile=[t] * n))
@@ -106,9 +107,9 @@ def test_autotune_picks_valid_choice_and_keeps_results(torch_cuda, name, precisi
     assert ms > 0
     n = len(s0.levels())
     assert tuning["levels"] == n
-    assert all(k in ("colour", "fused", "async") for k in tuning["sweep"])
+    assert all(k in ("colour", "colour2", "fused", "async") for k in tuning["sweep"])
     if p.grid.dim == 3:
-        assert set(tuning["sweep"]) == {"colour"}
+        assert set(tuning["sweep"]) <= {"colour", "colour2"}
     assert tuning["tail_level"] >= n or 1 <= tuning["tail_level"] <= n - 2
     assert tuning["tail_ctas"] in (1, 8, 16)
     assert s0.tuning() == tuning
