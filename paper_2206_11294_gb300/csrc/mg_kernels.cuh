@@ -334,10 +334,10 @@ __device__ __forceinline__ void prolong_add_block(const Level<R> &C, const Level
             if ((q >> a) & 1) { Q[a] = Qn[a]; flip ^= neg[a]; nq++; }
         const R w = DIM == 2 ? (nq == 0 ? R(9.0 / 16) : nq == 1 ? R(3.0 / 16) : R(1.0 / 16))
                              : (nq == 0 ? R(27.0 / 64) : nq == 1 ? R(9.0 / 64) : nq == 2 ? R(3.0 / 64) : R(1.0 / 64));
-        V2 e = ldv<NC>(C.x + cell_id(Q[0], Q[1], Q[2], C.n0, C.n1));
-        if (flip) { e.x = -e.x; e.y = -e.y; }
-        aT += w * e.x;
-        ap += w * e.y;
+        const V2 e = ldv<NC>(C.x + cell_id(Q[0], Q[1], Q[2], C.n0, C.n1));
+        const R ws = flip ? -w : w;   // the ghost's sign goes on the constant weight: no FP64 negations
+        aT += ws * e.x;
+        ap += ws * e.y;
     }
     const long long c = cell_id(i, j, k, F.n0, F.n1);
     V2 xv = NC ? F.x[c] : __ldcg(F.x + c);

@@ -230,10 +230,10 @@ __device__ __forceinline__ void tail_prolong(const TailCta<R> &C, const TailLeve
                 if ((qq >> a) & 1) { Q[a] = Qn[a]; flip ^= neg[a]; nq++; }
             const R wq = DIM == 2 ? (nq == 0 ? R(9.0 / 16) : nq == 1 ? R(3.0 / 16) : R(1.0 / 16))
                                   : (nq == 0 ? R(27.0 / 64) : nq == 1 ? R(9.0 / 64) : nq == 2 ? R(3.0 / 64) : R(1.0 / 64));
-            V2 e = *tail_at<R, DIM, CL>(C, Cl, 0, Q[0], Q[1], Q[2]);
-            if (flip) { e.x = -e.x; e.y = -e.y; }
-            aT += wq * e.x;
-            ap += wq * e.y;
+            const V2 e = *tail_at<R, DIM, CL>(C, Cl, 0, Q[0], Q[1], Q[2]);
+            const R ws = flip ? -wq : wq;
+            aT += ws * e.x;
+            ap += ws * e.y;
         }
         V2 *xp = tail_at<R, DIM, CL>(C, F, 0, i, j, k);
         V2 xv = *xp;
