@@ -275,8 +275,8 @@ __device__ __forceinline__ void residual_restrict_block(const Level<R> &F, const
         offdiag<R, DIM, true, NC>(F, F.x, i, j, k, c, sT, sp);
         const V2 bb = ldv<NC>(F.b + c), xx = ldv<NC>(F.x + c);
         const auto Dd = ldgq(F.D + c);
-        aT += bb.x - sT - (Dd.a * xx.x + Dd.b * xx.y);
-        ap += bb.y - sp - (Dd.c * xx.x + Dd.d * xx.y);
+        aT += ((bb.x - sT) - Dd.a * xx.x) - Dd.b * xx.y;   // two FMAs per row
+        ap += ((bb.y - sp) - Dd.c * xx.x) - Dd.d * xx.y;
     }
     const R w = R(1) / R(1 << DIM);
     const long long cc = cell_id(I, J, K, C.n0, C.n1);
@@ -511,8 +511,8 @@ __device__ __forceinline__ void residual64_to32_cell(const Level<double> &L, flo
     const double2 bb = ldg2(L.b + c), xx = ldg2(L.x + c);
     const dq Dd = ldgq(L.D + c);
     const dq Di = ldgq(L.Dinv + c);
-    const double rT = bb.x - sT - (Dd.a * xx.x + Dd.b * xx.y);
-    const double rp = bb.y - sp - (Dd.c * xx.x + Dd.d * xx.y);
+    const double rT = ((bb.x - sT) - Dd.a * xx.x) - Dd.b * xx.y;   // two FMAs per row
+    const double rp = ((bb.y - sp) - Dd.c * xx.x) - Dd.d * xx.y;
     const double zT = Di.a * rT + Di.b * rp;
     const double zp = Di.c * rT + Di.d * rp;
     zT2 = fma(zT, zT, zT2);
