@@ -160,3 +160,38 @@ def test_table_reuses_measurement(torch_cuda):
     assert t2 == t1 and s2.tuning() == t1
     s1.close()
     s2.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_tma_sweep_on_ragged_grid(torch_cuda, precision):
+    """The TMA-fed sweep on a grid that no tile shape divides (200 x 72: tiles
+    hang over the right and top edges, where the boxes are zero-filled): same
+    result, bit for bit, as colour sweeps; a level it cannot run is refused."""
+    from paper_2206_11294_gb300.binding import MgError, MG_ERR_INVALID_ARG
+    W, D = I.BC_WALL, I.BC_DIRICHLET
+    p = I.random_coeff_problem(I.Grid(dim=2, axisym=0, n=(200, 72, 1), h=1e-4, bc=((D, W), (W, D), (0, 0)),
+                                      bcT=((300, 0), (0, 300), (0, 0)), bcp=((1e5, 0), (0, 1e5), (0, 0))),
+                               seed=73, dt=1e-5)
+    s0, x0, st0 = _solve(p, precision=precision)
+    base = s0.tuning()
+    n = base["levels"]
+    sizes = s0.levels()
+    # FP64 64 x 16 tiles need more than one block's shared memory; FP32 needs an even row length
+    allowed = lambda l, t: (precision == "mixed" or t != 0) and (precision == "fp64" or sizes[l][0] % 2 == 0)
+    for t in range(3):
+        v = dict(base, sweep=["colour"] * n, tile=[0] * n, tail_level=n)
+        for l in range(n - 1):
+            if allowed(l, t):
+                v["sweep"][l], v["tile"][l] = "async", t
+        s, x, st = _solve(p, tuning=v, precision=precision)
+        assert st["cycles"] == st0["cycles"]
+        assert np.array_equal(x, x0), t
+        s.close()
+    if precision == "fp64":                           # 64 x 16 FP64 tiles: refused, handle unchanged
+        bad = dict(base, sweep=list(base["sweep"]), tile=list(base["tile"]))
+        bad["sweep"][0], bad["tile"][0] = "async", 0
+        with pytest.raises(MgError) as e:
+            s0.set_tuning(bad)
+        assert e.value.status == MG_ERR_INVALID_ARG and "does not fit" in str(e.value)
+        assert s0.tuning() == base
+    s0.close()
