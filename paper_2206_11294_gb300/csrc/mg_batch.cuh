@@ -479,6 +479,7 @@ struct mg_batch {
     int max_nc_big;
     int n_inv_smem;
     size_t inv_smem_bytes;
+    size_t inv_cols_smem_bytes;       // the inverse-columns kernel (staged factors)
     int max_nc_small;
     std::vector<int> big_coarse;      // problems whose coarsest inverse takes the banded three-kernel path
     std::pair<long long, int> setup_fine_tab;
@@ -840,6 +841,8 @@ mg_status mg_batch_create(int count, mg_handle *const *handles, mg_batch **out) 
         if (h->nc <= kBandSmemMax) {
             inv_ids.push_back(p);
             b->inv_smem_bytes = std::max(b->inv_smem_bytes, sizeof(double) * (size_t)h->nc * h->nc);
+            b->inv_cols_smem_bytes = std::max(b->inv_cols_smem_bytes,
+                                              sizeof(double) * (size_t)inv_smem_doubles(h->nc, C.kl, C.kl));
             b->max_nc_small = std::max(b->max_nc_small, h->nc);
         } else {
             b->big_coarse.push_back(p);
@@ -1078,8 +1081,9 @@ mg_status mg_batch_set_coeffs(mg_batch *b, const double *const *lambda, const do
     if (b->n_inv_smem > 0) {
         CK(raise_smem_limit((const void *)kb_band_lu_warp, (int)(sizeof(double) * kBandSmemMax * kBandSmemMax)));
         kb_band_lu_warp<<<b->n_inv_smem, kLUThreads, b->inv_smem_bytes, s>>>(b->co, b->inv_ids);
+        CK(raise_smem_limit((const void *)kb_band_inv_cols_warp, (int)b->inv_cols_smem_bytes));
         kb_band_inv_cols_warp<<<dim3((b->max_nc_small + 31) / 32, b->n_inv_smem), dim3(32, kInvRows),
-                                sizeof(double) * 32 * (size_t)(b->max_nc_small + kInvRows), s>>>(b->co, b->inv_ids);
+                                b->inv_cols_smem_bytes, s>>>(b->co, b->inv_ids);
         b->launches += 2;
     }
     if (!b->big_coarse.empty()) {           // medium coarsest levels: the banded path, all at once

@@ -974,7 +974,10 @@ mg_status setup_hierarchy(mg_handle *h, const double *lam, const double *const f
         const size_t smem_lu = sizeof(double) * (size_t)h->nc * h->nc;
         CK(raise_smem_limit((const void *)k_band_lu_warp, (int)(sizeof(double) * kBandSmemMax * kBandSmemMax)));
         k_band_lu_warp<<<1, kLUThreads, smem_lu, a>>>(h->Mtmp, h->nc, kl, kl, h->piv, h->dinv, h->err_d);
-        k_band_inv_cols_warp<<<(h->nc + 31) / 32, dim3(32, kInvRows), sizeof(double) * 32 * (size_t)(h->nc + kInvRows),
+        const int smem_inv = (int)(sizeof(double) * inv_smem_doubles(h->nc, kl, kl));
+        CK(raise_smem_limit((const void *)k_band_inv_cols_warp,
+                            (int)(sizeof(double) * inv_smem_doubles(kBandSmemMax, kBandSmemMax - 1, kBandSmemMax - 1))));
+        k_band_inv_cols_warp<<<(h->nc + 31) / 32, dim3(32, kInvRows), smem_inv,
                                a>>>(h->Mtmp, h->piv, h->dinv, h->nc, kl, kl, h->Minv, mixed ? h->Minv32 : nullptr,
                                     h->err_d);
     } else {

@@ -1095,17 +1095,44 @@ __global__ void __launch_bounds__(kLUThreads) k_band_lu_warp(double *__restrict_
 // Columns 32 * col_block + lane of the inverse from the factors of
 // k_band_lu_warp, one column per lane and kInvRows row groups (threadIdx.y)
 // per column; does nothing when the factorisation reported a zero pivot.
+// The factors' band is staged in shared memory first: the substitutions are
+// 2n dependent steps, and a global load in each (a column of M, one sector
+// per row) would put an L2 round trip on every step.
 constexpr int kInvRows = 8;
+
+// Shared-memory layout of the staged factors: a band of width kl + ku + kl + 1
+// (row r holds columns r - kl .. r + kl + ku, U's reach after pivoting), or the
+// dense matrix where the band would be at least as wide.
+__host__ __device__ __forceinline__ int inv_band_width(int n, int kl, int ku) {
+    const int bw = kl + (kl + ku) + 1;
+    return bw >= n ? n : bw;
+}
+
+// Dynamic shared memory of band_inv_cols_warp_block, in doubles.
+__host__ __device__ __forceinline__ long long inv_smem_doubles(int n, int kl, int ku) {
+    return 32LL * n + 32LL * kInvRows + (long long)n * inv_band_width(n, kl, ku);
+}
 
 __device__ __forceinline__ void band_inv_cols_warp_block(const double *__restrict__ M, const int *__restrict__ piv,
                                                          const double *__restrict__ dinv, int n, int kl, int ku,
                                                          double *__restrict__ Minv, float *__restrict__ Minv32,
                                                          int col_block, const int *__restrict__ err) {
-    extern __shared__ double ysm[];                    // y[i][lane], n x 32, then partial sums kInvRows x 32
+    extern __shared__ double ysm[];   // y[i][lane], n x 32; partial sums kInvRows x 32; the staged factors
     if (*(volatile const int *)err & 4) return;
     double *part = ysm + n * 32;
+    double *fac = part + kInvRows * 32;
     const int lane = threadIdx.x, ty = threadIdx.y;
+    const int tid = lane + 32 * ty;
     const int j = col_block * 32 + lane;
+    const int bw = inv_band_width(n, kl, ku);
+    const bool dense = bw == n;
+    // factor entry (r, c), c within r - kl .. r + kl + ku
+    auto F = [&](int r, int c) -> double { return dense ? fac[r * n + c] : fac[r * bw + (c - r + kl)]; };
+    for (int q = tid; q < n * bw; q += 32 * kInvRows) {
+        const int r = q / bw, o = q - r * bw;
+        const int c = dense ? o : r - kl + o;
+        fac[q] = (c >= 0 && c < n) ? __ldg(M + (long long)r * n + c) : 0.0;
+    }
     for (int i = ty; i < n; i += kInvRows) ysm[i * 32 + lane] = (i == j) ? 1.0 : 0.0;
     __syncthreads();
     for (int k = 0; k < n; k++) {                      // P and L, in the factorisation's order
@@ -1119,7 +1146,7 @@ __device__ __forceinline__ void band_inv_cols_warp_block(const double *__restric
         const double yk = ysm[k * 32 + lane];
         const int rlast = min(n - 1, k + kl);
         for (int r = k + 1 + ty; r <= rlast; r += kInvRows) {
-            const double l = __ldg(M + (long long)r * n + k);
+            const double l = F(r, k);
             if (abs_bits(l) != 0) ysm[r * 32 + lane] -= l * yk;
         }
         __syncthreads();
@@ -1129,7 +1156,7 @@ __device__ __forceinline__ void band_inv_cols_warp_block(const double *__restric
         const int clast = min(n - 1, i + ur);
         double s = 0.0;
         for (int c = i + 1 + ty; c <= clast; c += kInvRows) {
-            const double u = __ldg(M + (long long)i * n + c);
+            const double u = F(i, c);
             if (abs_bits(u) != 0) s += u * ysm[c * 32 + lane];
         }
         part[ty * 32 + lane] = s;
