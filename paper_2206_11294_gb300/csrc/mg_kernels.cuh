@@ -887,13 +887,15 @@ __device__ __forceinline__ void setup_coarse_cells(const SetupGeom &cg, const Se
         const int i = 2 * I + (q & 1);
         const long long f = cell_id(i, 2 * J + ((q >> 1) & 1), DIM == 3 ? 2 * K + (q >> 2) : 0, fn0, fn1);
         const dq sf = Sf[f];
-        a0 += sf.a; a1 += sf.b; a2 += sf.c; a3 += sf.d;
+        // sums start from the first child: an addition to 0.0 would still take an FP64 issue slot
+        if (q == 0) { a0 = sf.a; a1 = sf.b; a2 = sf.c; a3 = sf.d; }
+        else { a0 += sf.a; a1 += sf.b; a2 += sf.c; a3 += sf.d; }
         if (AXI) {
             const double sc = cg.r0 + (i + 0.5) * hf;
-            v4 += sc * l4f[f];
-            vs += sc;
+            if (q == 0) { v4 = sc * l4f[f]; vs = sc; }
+            else { v4 += sc * l4f[f]; vs += sc; }
         } else {
-            v4 += l4f[f];
+            v4 = q == 0 ? l4f[f] : v4 + l4f[f];
         }
     }
     const double wb = 1.0 / (1 << DIM);
@@ -927,8 +929,8 @@ __device__ __forceinline__ void setup_coarse_cells(const SetupGeom &cg, const Se
                 if (DIM == 2) fpos[2] = 0;
                 const double2 v = Gf[a][(long long)fpos[0] + (long long)fm[a][0] * ((long long)fpos[1] +
                                                                                   (long long)fm[a][1] * fpos[2])];
-                sT += v.x;
-                sp += v.y;
+                if (q == 0) { sT = v.x; sp = v.y; }
+                else { sT += v.x; sp += v.y; }
             }
             g[a][sd] = make_double2(sT * wf, sp * wf);
             own[a][sd] = sd == 0 || P[a] + sd == cg.n[a];
