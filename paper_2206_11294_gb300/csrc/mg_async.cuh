@@ -192,25 +192,24 @@ __global__ void __launch_bounds__(256, 1)
             xs[ly * W2 + lx] = update(lx, ly, sT, sp);
         }
         __syncthreads();
-        // black cells of the tile; each thread writes a pair of adjacent cells
-        constexpr int kPairs = TX / 2;
-        for (int q = tid; q < TY * kPairs; q += 256) {
-            const int ty = q / kPairs, px = q - ty * kPairs;
+        // black cells of the tile, one per thread (no warp mixes colours), in place
+        constexpr int kBlackPerRow = TX / 2;
+        for (int q = tid; q < TY * kBlackPerRow; q += 256) {
+            const int ty = q / kBlackPerRow, rx = q - ty * kBlackPerRow;
             const int gj = j0 + ty;
-            if (gj >= n1) continue;
-#pragma unroll
-            for (int e = 0; e < 2; e++) {
-                const int gi = i0 + 2 * px + e;
-                if (gi >= n0) continue;
-                const int lx = gi - i0 + 2, ly = ty + 2;
-                V2 v = xs[ly * W2 + lx];
-                if ((gi + gj) & 1) {
-                    R sT, sp;
-                    offd(gi, gj, lx, ly, sT, sp);
-                    v = update(lx, ly, sT, sp);
-                }
-                xout[(long long)gj * n0 + gi] = v;
-            }
+            const int gi = i0 + 2 * rx + ((i0 + gj + 1) & 1);
+            if (gi >= n0 || gj >= n1) continue;
+            const int lx = gi - i0 + 2, ly = ty + 2;
+            R sT, sp;
+            offd(gi, gj, lx, ly, sT, sp);
+            xs[ly * W2 + lx] = update(lx, ly, sT, sp);
+        }
+        __syncthreads();
+        // the tile, both colours, coalesced
+        for (int q = tid; q < TY * TX; q += 256) {
+            const int ty = q / TX, tx = q - ty * TX;
+            const int gi = i0 + tx, gj = j0 + ty;
+            if (gi < n0 && gj < n1) xout[(long long)gj * n0 + gi] = xs[(ty + 2) * W2 + tx + 2];
         }
         __syncthreads();                      // every thread is done with stage s
         const int tn = t + kAsyncStages * gridDim.x;

@@ -216,26 +216,27 @@ __device__ __forceinline__ void rbgs_fused2d_block(const Level<R> &L, const type
         xs[ly][lx] = gs_update<R>(L, c, sT, sp);
     }
     __syncthreads();
-    // black cells of the tile; each thread writes a pair of adjacent cells
-    constexpr int kPairs = TX / 2;
-    for (int q = tid; q < TY * kPairs; q += 256) {
-        const int ty = q / kPairs, px = q - ty * kPairs;
+    // black cells of the tile, one per thread (a warp never mixes colours, so
+    // no FP64 issue slot goes to a predicated-off lane); in place in xs, where
+    // black cells read only red values
+    constexpr int kBlackPerRow = TX / 2;
+    for (int q = tid; q < TY * kBlackPerRow; q += 256) {
+        const int ty = q / kBlackPerRow, rx = q - ty * kBlackPerRow;
         const int gj = j0 + ty;
-        if (gj >= n1) continue;
-#pragma unroll
-        for (int e = 0; e < 2; e++) {
-            const int gi = i0 + 2 * px + e;
-            if (gi >= n0) continue;
-            const int lx = gi - i0 + 2, ly = ty + 2;
-            const long long c = (long long)gj * n0 + gi;
-            V2 v = xs[ly][lx];
-            if ((gi + gj) & 1) {
-                R sT, sp;
-                offdiag_tile2d<R, TX>(L, xs, lx, ly, gi, gj, c, sT, sp);
-                v = gs_update<R>(L, c, sT, sp);
-            }
-            xout[c] = v;
-        }
+        const int gi = i0 + 2 * rx + ((i0 + gj + 1) & 1);
+        if (gi >= n0 || gj >= n1) continue;
+        const int lx = gi - i0 + 2, ly = ty + 2;
+        const long long c = (long long)gj * n0 + gi;
+        R sT, sp;
+        offdiag_tile2d<R, TX>(L, xs, lx, ly, gi, gj, c, sT, sp);
+        xs[ly][lx] = gs_update<R>(L, c, sT, sp);
+    }
+    __syncthreads();
+    // the tile, both colours, coalesced
+    for (int q = tid; q < TY * TX; q += 256) {
+        const int ty = q / TX, tx = q - ty * TX;
+        const int gi = i0 + tx, gj = j0 + ty;
+        if (gi < n0 && gj < n1) xout[(long long)gj * n0 + gi] = xs[ty + 2][tx + 2];
     }
 }
 
