@@ -1436,12 +1436,12 @@ mg_status mg_set_tuning(mg_handle *h, const mg_tuning *t) {
     DeviceGuard dg(h->device);
     if (!no_tail && !tail_ctas_ok(h, t->tail_ctas))
         return fail(MG_ERR_INVALID_ARG, "tail cluster size must be 1, 8, or 16 where the device allows it");
+    if (t->persistent != 0 && t->persistent != 1) return fail(MG_ERR_INVALID_ARG, "persistent must be 0 or 1");
     CK(cudaStreamSynchronize(h->stream));
     for (int l = 0; l < h->nlev; l++) {
         h->sweep[l] = t->sweep[l];
         h->tile[l] = t->tile[l];
     }
-    if (t->persistent != 0 && t->persistent != 1) return fail(MG_ERR_INVALID_ARG, "persistent must be 0 or 1");
     h->tail_lev = no_tail ? h->nlev : t->tail_level;
     h->tail_ctas = no_tail ? kTailCtas : t->tail_ctas;
     h->persistent = t->persistent;

@@ -131,6 +131,8 @@ def test_set_tuning_rejects_bad_choices(torch_cuda):
                       (s2, lambda t: t.__setitem__("tail_level", t["levels"] - 1)),
                       (s2, lambda t: t.update(tail_level=1, tail_ctas=12)),
                       (s2, lambda t: t.update(tail_level=1, tail_ctas=1)),   # 6144 FP64 cells: > 200 KB
+                      # a valid sweep change with an invalid flag: nothing of it may be applied
+                      (s2, lambda t: t.update(persistent=2, sweep=["fused"] + t["sweep"][1:])),
                       (s2, lambda t: t.update(tail_level=1))]:      # level 1 of 192x128 has 6144 cells: allowed
         before = s.tuning()
         t = dict(before, sweep=list(before["sweep"]), tile=list(before["tile"]))
