@@ -947,13 +947,11 @@ mg_status setup_hierarchy(mg_handle *h, const double *lam, const double *const f
         CK(cudaGetLastError());
         hl *= 2.0;
     }
-    // flags 1 and 2 come from the level kernels: read them before the coarsest
-    // matrix is assembled, then leave the assembly and the inverse running
-    CK(cudaMemcpyAsync(h->errh, h->err_d, sizeof(int), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    const int err = *h->errh;
-    if (err & 1) return fail(MG_ERR_INVALID_COEFF, "non-finite coefficient in lambda or the face arrays");
-    if (err & 2) return fail(MG_ERR_INVALID_COEFF, "a local 2x2 block is singular or not finite");
+    // The coarsest matrix is assembled and its inverse started before the
+    // host waits for the flags of the level kernels, so the device runs the
+    // whole set-up without a gap.  With invalid coefficients the inverse
+    // works on non-finite values (bounded loops, no fault) and the call fails;
+    // the next set-up waits for it before overwriting anything.
     const LevelBuf &c = h->L[h->nlev - 1];
     CK(cudaMemsetAsync(h->Mtmp, 0, sizeof(double) * h->nc * h->nc, s));
     k_coarse_assemble<DIM><<<lin_blocks(c.N), 256, 0, s>>>(c.n[0], c.n[1], c.n[2], c.G[0], c.G[1],
@@ -992,6 +990,13 @@ mg_status setup_hierarchy(mg_handle *h, const double *lam, const double *const f
     CK(cudaGetLastError());
     CK(cudaEventRecord(h->ev_inv, a));
     counted(h, h->nlev + 1 + (h->nc <= kBandSmemMax ? 2 : 4));
+    // flags 1 and 2 come from the level kernels, which precede this copy on
+    // the stream (the inverse on the private stream keeps running)
+    CK(cudaMemcpyAsync(h->errh, h->err_d, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const int err = *h->errh;
+    if (err & 1) return fail(MG_ERR_INVALID_COEFF, "non-finite coefficient in lambda or the face arrays");
+    if (err & 2) return fail(MG_ERR_INVALID_COEFF, "a local 2x2 block is singular or not finite");
     return MG_OK;
 }
 

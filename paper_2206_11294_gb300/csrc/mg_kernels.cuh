@@ -276,8 +276,11 @@ __device__ __forceinline__ void residual_restrict_block(const Level<R> &F, const
         offdiag<R, DIM, true, NC>(F, F.x, i, j, k, c, sT, sp);
         const V2 bb = ldv<NC>(F.b + c), xx = ldv<NC>(F.x + c);
         const auto Dd = ldgq(F.D + c);
-        aT += ((bb.x - sT) - Dd.a * xx.x) - Dd.b * xx.y;   // two FMAs per row
-        ap += ((bb.y - sp) - Dd.c * xx.x) - Dd.d * xx.y;
+        const R rT = ((bb.x - sT) - Dd.a * xx.x) - Dd.b * xx.y;   // two FMAs per row
+        const R rp = ((bb.y - sp) - Dd.c * xx.x) - Dd.d * xx.y;
+        // the sums start from child 0 (always evaluated): no FP64 addition to 0
+        aT = q == 0 ? rT : aT + rT;
+        ap = q == 0 ? rp : ap + rp;
     }
     const R w = R(1) / R(1 << DIM);
     const long long cc = cell_id(I, J, K, C.n0, C.n1);

@@ -181,8 +181,11 @@ __device__ __forceinline__ void tail_restrict(const TailCta<R> &C, const TailLev
             tail_offdiag<R, DIM, CL, true>(C, F, i, j, k, c, sT, sp);
             const V2 bb = *tail_at<R, DIM, CL>(C, F, 1, i, j, k), xx = *tail_at<R, DIM, CL>(C, F, 0, i, j, k);
             const auto Dd = ldgq(FL.D + c);
-            aT += ((bb.x - sT) - Dd.a * xx.x) - Dd.b * xx.y;   // two FMAs per row
-            ap += ((bb.y - sp) - Dd.c * xx.x) - Dd.d * xx.y;
+            const R rT = ((bb.x - sT) - Dd.a * xx.x) - Dd.b * xx.y;   // two FMAs per row
+            const R rp = ((bb.y - sp) - Dd.c * xx.x) - Dd.d * xx.y;
+            // the sums start from child 0 (always evaluated): no FP64 addition to 0
+            aT = qq == 0 ? rT : aT + rT;
+            ap = qq == 0 ? rp : ap + rp;
         }
         const R wgt = R(1) / R(1 << DIM);
         const long long cc = cell_id(I, J, K, CG.n0, CG.n1);

@@ -245,7 +245,25 @@ def test_invalid_coefficients_rejected(torch_cuda):
     with pytest.raises(MgError) as e:
         s.set_coeffs(lam, p.fa, p.fk)
     assert e.value.status == MG_ERR_INVALID_COEFF
+    # the rejected set-up (whose coarsest inverse ran on non-finite values)
+    # leaves nothing behind: valid coefficients then solve as on a new handle
+    s.set_coeffs(p.lam, p.fa, p.fk)
+    x = p.x0.copy()
+    st = s.solve(p.b, x)
+    fresh = Solver(p.grid)
+    fresh.set_coeffs(p.lam, p.fa, p.fk)
+    xf = p.x0.copy()
+    stf = fresh.solve(p.b, xf)
+    assert st["cycles"] == stf["cycles"] and np.array_equal(x, xf)
+    # a rejected set-up after a valid one: no solve until coefficients are set again
+    with pytest.raises(MgError) as e:
+        s.set_coeffs(lam, p.fa, p.fk)
+    assert e.value.status == MG_ERR_INVALID_COEFF
+    with pytest.raises(MgError) as e:
+        s.solve(p.b, p.x0.copy())
+    assert e.value.status == MG_ERR_STATE
     s.close()
+    fresh.close()
 
 
 def test_not_converged_status(torch_cuda):
