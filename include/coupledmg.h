@@ -146,11 +146,13 @@ MG_API mg_status mg_residual_norms(mg_handle *h, const double *rhs, const double
                             double out[2]);
 
 /* Instrumentation.  mg_set_timing(h, 1) resets the counters and, from then
- * on, brackets the finest level's smoothing in every cycle with CUDA events
- * on the handle's stream (the cycle graphs are re-captured with event
- * nodes); 0 turns that off.  mg_counters reports, since the last reset:
+ * on, brackets one smoothing pass of the finest level in every cycle (the
+ * pre-smoothing, or the post-smoothing when nu1 = 0) with CUDA events on the
+ * handle's stream (the cycle graphs are re-captured with the two event
+ * nodes when the setting changes); 0 turns that off.  Either call resets the
+ * counters.  mg_counters reports, since the last reset:
  *   launches          kernels this handle launched (graph nodes counted per replay)
- *   smooth_ms         device time of the finest-level smoothing kernels (timing on)
+ *   smooth_ms         device time of the timed finest-level smoothing kernels (timing on)
  *   smooth_launches   how many such kernel launches that time covers
  *   smooth_sweeps     how many red-black sweeps those launches performed
  *   smooth_cells      finest-level cells per sweep */

@@ -116,7 +116,7 @@ struct mg_handle {
     long long enq;              // kernels launched since the last reset (graph nodes per replay)
     long long graph_kernels64, graph_kernels32;
     int timing;
-    cudaEvent_t ev[4];          // finest-level smoothing: pre start/end, post start/end
+    cudaEvent_t ev[2];          // start / end of the timed finest-level smoothing pass
     double smooth_ms;
     long long smooth_launches;
     long long smooth_sweeps;
@@ -625,10 +625,14 @@ void enqueue_vcycle(const mg_handle *h, cudaStream_t s, int l) {
         return;
     }
     const LevelBuf &cb = h->L[l + 1];
-    const bool tm = h->timing && l == 0;
-    if (tm) cudaEventRecordWithFlags(h->ev[0], s, cudaEventRecordExternal);
+    // timing brackets one smoothing pass of the finest level per cycle: the
+    // pre-smoothing, or the post-smoothing when there is none (two event nodes
+    // per cycle, not four: each costs the step a little)
+    const bool tm_pre = h->timing && l == 0 && h->opt.nu1 > 0;
+    const bool tm_post = h->timing && l == 0 && h->opt.nu1 == 0;
+    if (tm_pre) cudaEventRecordWithFlags(h->ev[0], s, cudaEventRecordExternal);
     enqueue_smooth<R, DIM>(h, s, l, h->opt.nu1);
-    if (tm) cudaEventRecordWithFlags(h->ev[1], s, cudaEventRecordExternal);
+    if (tm_pre) cudaEventRecordWithFlags(h->ev[1], s, cudaEventRecordExternal);
     const dim3 rg = cell_grid(cb, DIM, cb.n[0]);
     if (h->opt.nu1 > 0) {
         if (h->persistent)
@@ -654,9 +658,9 @@ void enqueue_vcycle(const mg_handle *h, cudaStream_t s, int l) {
     else
         k_prolong_add<R, DIM, false><<<pg, kBlock, 0, s>>>(view<R>(cb), view<R>(lb), bc_flags(h->grid));
     counted(h);
-    if (tm) cudaEventRecordWithFlags(h->ev[2], s, cudaEventRecordExternal);
+    if (tm_post) cudaEventRecordWithFlags(h->ev[0], s, cudaEventRecordExternal);
     enqueue_smooth<R, DIM>(h, s, l, h->opt.nu2);
-    if (tm) cudaEventRecordWithFlags(h->ev[3], s, cudaEventRecordExternal);
+    if (tm_post) cudaEventRecordWithFlags(h->ev[1], s, cudaEventRecordExternal);
 }
 
 // after_sweep: x has just come out of a red-black sweep (red cells only).
@@ -825,16 +829,14 @@ mg_status sync_norms(mg_handle *h, double out[2]) {
 // After a synchronised cycle: add the finest-level smoothing time it recorded.
 mg_status accumulate_timing(mg_handle *h) {
     if (!h->timing || h->L[0].N == 0 || h->nlev < 2) return MG_OK;
-    float a = 0.f, b = 0.f;
+    float a = 0.f;
     CK(cudaEventElapsedTime(&a, h->ev[0], h->ev[1]));
-    CK(cudaEventElapsedTime(&b, h->ev[2], h->ev[3]));
-    h->smooth_ms += (double)a + (double)b;
-    long long l1, s1, l2, s2;
+    h->smooth_ms += (double)a;
+    long long l1, s1;
     const bool fused = h->grid.dim == 2 && (h->sweep[0] == MG_SWEEP_FUSED || h->sweep[0] == MG_SWEEP_ASYNC);
-    smooth_launches(fused, h->opt.nu1, &l1, &s1);
-    smooth_launches(fused, h->opt.nu2, &l2, &s2);
-    h->smooth_launches += l1 + l2;
-    h->smooth_sweeps += s1 + s2;
+    smooth_launches(fused, h->opt.nu1 > 0 ? h->opt.nu1 : h->opt.nu2, &l1, &s1);
+    h->smooth_launches += l1;
+    h->smooth_sweeps += s1;
     return MG_OK;
 }
 
@@ -1487,9 +1489,9 @@ mg_status mg_set_timing(mg_handle *h, int enable) {
     DeviceGuard dg(h->device);
     CK(cudaStreamSynchronize(h->stream));
     if (enable && !h->ev[0])
-        for (int q = 0; q < 4; q++) CK(cudaEventCreate(&h->ev[q]));
-    // re-capture the cycle graphs with (or without) the event nodes
-    drop_graphs(h);
+        for (int q = 0; q < 2; q++) CK(cudaEventCreate(&h->ev[q]));
+    // re-capture the cycle graphs with (or without) the event nodes when that changes
+    if ((enable ? 1 : 0) != h->timing) drop_graphs(h);
     h->timing = enable ? 1 : 0;
     h->enq = 0;
     h->smooth_ms = 0.0;
@@ -1546,7 +1548,7 @@ mg_status mg_destroy(mg_handle *h) {
     if (h->ev_asm) cudaEventDestroy(h->ev_asm);
     if (h->ev_inv) cudaEventDestroy(h->ev_inv);
     if (h->errh) cudaFreeHost(h->errh);
-    for (int q = 0; q < 4; q++)
+    for (int q = 0; q < 2; q++)
         if (h->ev[q]) cudaEventDestroy(h->ev[q]);
     if (h->norms_h) cudaFreeHost(h->norms_h);
     if (h->owns_arena && h->arena) cudaFree(h->arena);

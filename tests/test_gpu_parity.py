@@ -320,3 +320,33 @@ def test_full_size_3d_sampled_residual(torch_cuda, orc, precision, tol):
     for f in range(2):
         assert np.linalg.norm(r[:, f]) <= tol * np.linalg.norm(r0[:, f]) * 10, (f, st)
     s.close()
+
+
+@pytest.mark.parametrize("nu1,nu2", [(2, 2), (0, 3), (3, 1)])
+def test_timing_counters(torch_cuda, nu1, nu2):
+    """mg_set_timing brackets one finest-level smoothing pass per cycle (the
+    pre-smoothing, or the post-smoothing when nu1 = 0); the counters say how
+    many launches and sweeps that time covers, and timing does not change the
+    result."""
+    p = I.bubble_2d(128)
+    s = _solver(p, rtol=0.0, max_cycles=3, nu1=nu1, nu2=nu2)
+    s.set_tuning(dict(s.tuning(), sweep=["colour"] * len(s.levels())))
+    x0 = p.x0.copy()
+    s.solve(p.b, x0)
+    s.set_timing(True)
+    x = p.x0.copy()
+    st = s.solve(p.b, x)
+    c = s.counters()
+    per = nu1 if nu1 > 0 else nu2
+    assert st["cycles"] == 3
+    assert c["smooth_sweeps"] == 3 * per and c["smooth_launches"] == 3 * 2 * per   # two colour launches a sweep
+    assert c["smooth_ms"] > 0.0 and c["smooth_cells"] == p.grid.N and c["launches"] > c["smooth_launches"]
+    assert np.array_equal(x, x0)
+    s.set_timing(True)                  # unchanged setting: counters reset, graphs kept
+    assert s.counters()["launches"] == 0 and s.counters()["smooth_ms"] == 0.0
+    s.set_timing(False)
+    x = p.x0.copy()
+    s.solve(p.b, x)
+    c = s.counters()
+    assert c["smooth_launches"] == 0 and c["launches"] > 0 and np.array_equal(x, x0)
+    s.close()
