@@ -112,6 +112,9 @@ struct mg_handle {
     double *norms_h;       // pinned host: [2]
     bool coeffs_set;
     cudaGraphExec_t g64, g32;   // FP64 cycle+norm; mixed inner cycles+update+residual
+    cudaGraphExec_t gsetup;     // set-up of the levels for the input pointers in setup_key
+    const void *setup_key[7];
+    long long graph_kernels_setup;
     // instrumentation
     long long enq;              // kernels launched since the last reset (graph nodes per replay)
     long long graph_kernels64, graph_kernels32;
@@ -885,6 +888,34 @@ SetupFine setup_fine_of(const LevelBuf &F, double h) {
     return s;
 }
 
+// The set-up of every level on stream s: flag reset, the finest level from
+// the inputs, each coarser level from the one below, and the coarsest matrix.
+template <int DIM>
+void enqueue_setup_levels(mg_handle *h, cudaStream_t s, const SetupGeom &gm, const SetupIn &in) {
+    const bool mixed = h->opt.precision == MG_MIXED;
+    const LevelBuf &f = h->L[0];
+    cudaMemsetAsync(h->err_d, 0, sizeof(int), s);
+    k_setup_fine<DIM><<<cell_grid(f, DIM, f.n[0]), kBlock, 0, s>>>(gm, in, setup_out(f, mixed), h->err_d);
+    counted(h);
+    double hl = h->grid.h;
+    for (int l = 1; l < h->nlev; l++) {
+        const LevelBuf &F = h->L[l - 1];
+        const LevelBuf &C = h->L[l];
+        SetupGeom cg = gm;
+        for (int a = 0; a < 3; a++) cg.n[a] = C.n[a];
+        cg.h = 2.0 * hl;
+        k_setup_coarse<DIM><<<cell_grid(C, DIM, C.n[0]), kBlock, 0, s>>>(cg, setup_fine_of(F, hl), setup_out(C, mixed),
+                                                                         h->err_d);
+        counted(h);
+        hl *= 2.0;
+    }
+    const LevelBuf &c = h->L[h->nlev - 1];
+    cudaMemsetAsync(h->Mtmp, 0, sizeof(double) * h->nc * h->nc, s);
+    k_coarse_assemble<DIM><<<lin_blocks(c.N), 256, 0, s>>>(c.n[0], c.n[1], c.n[2], c.G[0], c.G[1],
+                                                           DIM == 3 ? c.G[2] : nullptr, c.D, c.l4, h->Mtmp);
+    counted(h);
+}
+
 template <int DIM>
 mg_status setup_hierarchy(mg_handle *h, const double *lam, const double *const fa[3], const double *const fk[3],
                           int on_device) {
@@ -894,7 +925,6 @@ mg_status setup_hierarchy(mg_handle *h, const double *lam, const double *const f
     LevelBuf &f = h->L[0];
     // the previous set-up's coarsest inverse must be done before anything is overwritten
     CK(cudaStreamWaitEvent(s, h->ev_inv, 0));
-    CK(cudaMemsetAsync(h->err_d, 0, sizeof(int), s));
     const double *lam_d = lam;
     const double *fad[3] = {nullptr, nullptr, nullptr}, *fkd[3] = {nullptr, nullptr, nullptr};
     if (!on_device) {
@@ -933,32 +963,28 @@ mg_status setup_hierarchy(mg_handle *h, const double *lam, const double *const f
         in.fa[a] = a < DIM ? fad[a] : nullptr;
         in.fk[a] = a < DIM ? fkd[a] : nullptr;
     }
-    k_setup_fine<DIM><<<cell_grid(f, DIM, f.n[0]), kBlock, 0, s>>>(
-        gm, in, setup_out(f, mixed), h->err_d);
-    CK(cudaGetLastError());
-    double hl = g.h;
-    for (int l = 1; l < h->nlev; l++) {
-        const LevelBuf &F = h->L[l - 1];
-        LevelBuf &C = h->L[l];
-        SetupGeom cg = gm;
-        for (int a = 0; a < 3; a++) cg.n[a] = C.n[a];
-        cg.h = 2.0 * hl;
-        k_setup_coarse<DIM><<<cell_grid(C, DIM, C.n[0]), kBlock, 0, s>>>(
-            cg, setup_fine_of(F, hl), setup_out(C, mixed),
-                                                                         h->err_d);
-        CK(cudaGetLastError());
-        hl *= 2.0;
-    }
-    // The coarsest matrix is assembled and its inverse started before the
-    // host waits for the flags of the level kernels, so the device runs the
-    // whole set-up without a gap.  With invalid coefficients the inverse
+    // The level work is one CUDA graph per handle, captured again only when
+    // the input pointers change: launched one kernel at a time from the host,
+    // the small coarse levels would leave the device waiting on launches.
+    // The coarsest matrix is assembled (and its inverse started below) before
+    // the host waits for the flags of the level kernels, so the device runs
+    // the whole set-up without a gap.  With invalid coefficients the inverse
     // works on non-finite values (bounded loops, no fault) and the call fails;
     // the next set-up waits for it before overwriting anything.
+    const void *key[7] = {lam_d, in.fa[0], in.fa[1], in.fa[2], in.fk[0], in.fk[1], in.fk[2]};
+    if (!h->gsetup || std::memcmp(key, h->setup_key, sizeof(key)) != 0) {
+        if (h->gsetup) {
+            cudaGraphExecDestroy(h->gsetup);
+            h->gsetup = nullptr;
+        }
+        const mg_status e = capture(h, &h->gsetup, &h->graph_kernels_setup,
+                                    [&](cudaStream_t cs) { enqueue_setup_levels<DIM>(h, cs, gm, in); });
+        if (e) return e;
+        std::memcpy(h->setup_key, key, sizeof(key));
+    }
+    CK(cudaGraphLaunch(h->gsetup, s));
+    h->enq += h->graph_kernels_setup;
     const LevelBuf &c = h->L[h->nlev - 1];
-    CK(cudaMemsetAsync(h->Mtmp, 0, sizeof(double) * h->nc * h->nc, s));
-    k_coarse_assemble<DIM><<<lin_blocks(c.N), 256, 0, s>>>(c.n[0], c.n[1], c.n[2], c.G[0], c.G[1],
-                                                           DIM == 3 ? c.G[2] : nullptr, c.D, c.l4, h->Mtmp);
-    CK(cudaGetLastError());
     // The coarsest inverse runs on the aux stream, overlapping the caller's
     // next work and the start of the next solve (whose cycles wait for it
     // before their coarsest solve).  A singular coarsest matrix is reported by
@@ -991,7 +1017,7 @@ mg_status setup_hierarchy(mg_handle *h, const double *lam, const double *const f
     }
     CK(cudaGetLastError());
     CK(cudaEventRecord(h->ev_inv, a));
-    counted(h, h->nlev + 1 + (h->nc <= kBandSmemMax ? 2 : 4));
+    counted(h, h->nc <= kBandSmemMax ? 2 : 4);
     // flags 1 and 2 come from the level kernels, which precede this copy on
     // the stream (the inverse on the private stream keeps running)
     CK(cudaMemcpyAsync(h->errh, h->err_d, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -1541,6 +1567,7 @@ mg_status mg_destroy(mg_handle *h) {
     DeviceGuard dg(h->device);
     if (h->stream) cudaStreamSynchronize(h->stream);
     if (h->g64) cudaGraphExecDestroy(h->g64);
+    if (h->gsetup) cudaGraphExecDestroy(h->gsetup);
     if (h->g32) cudaGraphExecDestroy(h->g32);
     if (h->aux) cudaStreamSynchronize(h->aux);
     if (h->cap) cudaStreamDestroy(h->cap);
