@@ -30,6 +30,7 @@ namespace {
 
 constexpr int kMaxLevels = 32;
 constexpr int kMaxCoarseUnknowns = 1024;
+constexpr int kSetupGraphs = 4;
 constexpr size_t kAlign = 256;
 constexpr size_t kTailSmemMax = 200 * 1024;   // shared memory a tail CTA may use
 
@@ -112,9 +113,12 @@ struct mg_handle {
     double *norms_h;       // pinned host: [2]
     bool coeffs_set;
     cudaGraphExec_t g64, g32;   // FP64 cycle+norm; mixed inner cycles+update+residual
-    cudaGraphExec_t gsetup;     // set-up of the levels for the input pointers in setup_key
-    const void *setup_key[7];
-    long long graph_kernels_setup;
+    struct SetupGraph {         // set-up of the levels for the input pointers in key
+        cudaGraphExec_t exec;
+        const void *key[7];
+        long long kernels;
+    } gsetup[kSetupGraphs];     // a few input sets (e.g. double-buffered inputs), replaced round-robin
+    int gsetup_next;
     // instrumentation
     long long enq;              // kernels launched since the last reset (graph nodes per replay)
     long long graph_kernels64, graph_kernels32;
@@ -972,18 +976,23 @@ mg_status setup_hierarchy(mg_handle *h, const double *lam, const double *const f
     // works on non-finite values (bounded loops, no fault) and the call fails;
     // the next set-up waits for it before overwriting anything.
     const void *key[7] = {lam_d, in.fa[0], in.fa[1], in.fa[2], in.fk[0], in.fk[1], in.fk[2]};
-    if (!h->gsetup || std::memcmp(key, h->setup_key, sizeof(key)) != 0) {
-        if (h->gsetup) {
-            cudaGraphExecDestroy(h->gsetup);
-            h->gsetup = nullptr;
+    mg_handle::SetupGraph *sg = nullptr;
+    for (auto &cand : h->gsetup)
+        if (cand.exec && std::memcmp(key, cand.key, sizeof(key)) == 0) sg = &cand;
+    if (!sg) {
+        sg = &h->gsetup[h->gsetup_next];
+        h->gsetup_next = (h->gsetup_next + 1) % kSetupGraphs;
+        if (sg->exec) {
+            cudaGraphExecDestroy(sg->exec);
+            sg->exec = nullptr;
         }
-        const mg_status e = capture(h, &h->gsetup, &h->graph_kernels_setup,
-                                    [&](cudaStream_t cs) { enqueue_setup_levels<DIM>(h, cs, gm, in); });
+        const mg_status e =
+            capture(h, &sg->exec, &sg->kernels, [&](cudaStream_t cs) { enqueue_setup_levels<DIM>(h, cs, gm, in); });
         if (e) return e;
-        std::memcpy(h->setup_key, key, sizeof(key));
+        std::memcpy(sg->key, key, sizeof(key));
     }
-    CK(cudaGraphLaunch(h->gsetup, s));
-    h->enq += h->graph_kernels_setup;
+    CK(cudaGraphLaunch(sg->exec, s));
+    h->enq += sg->kernels;
     const LevelBuf &c = h->L[h->nlev - 1];
     // The coarsest inverse runs on the aux stream, overlapping the caller's
     // next work and the start of the next solve (whose cycles wait for it
@@ -1567,7 +1576,8 @@ mg_status mg_destroy(mg_handle *h) {
     DeviceGuard dg(h->device);
     if (h->stream) cudaStreamSynchronize(h->stream);
     if (h->g64) cudaGraphExecDestroy(h->g64);
-    if (h->gsetup) cudaGraphExecDestroy(h->gsetup);
+    for (auto &sg : h->gsetup)
+        if (sg.exec) cudaGraphExecDestroy(sg.exec);
     if (h->g32) cudaGraphExecDestroy(h->g32);
     if (h->aux) cudaStreamSynchronize(h->aux);
     if (h->cap) cudaStreamDestroy(h->cap);

@@ -373,6 +373,15 @@ def test_setup_graph_follows_inputs(torch_cuda):
     T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
     dev = {n: dict(lam=T(p.lam), fa=[T(f) for f in p.fa], fk=[T(f) for f in p.fk]) for n, p in (("a", pa), ("b", pb))}
     s = Solver(pa.grid)
+    # more distinct pointer sets than the handle keeps graphs for (4): replaced ones are captured again
+    extra = [(n, dict(lam=T(p.lam), fa=[T(f) for f in p.fa], fk=[T(f) for f in p.fk]))
+             for n, p in (("a", pa), ("b", pb), ("a", pa), ("b", pb))]
+    for n, d in extra + extra:
+        p = pa if n == "a" else pb
+        s.set_coeffs(d["lam"], d["fa"], d["fk"])
+        x = p.x0.copy()
+        st = s.solve(p.b, x)
+        assert st["cycles"] == ref[n][1] and np.array_equal(x, ref[n][0]), n
     for name, how in [("a", "host"), ("b", "host"), ("a", "dev"), ("b", "dev"), ("a", "dev"), ("b", "refill")]:
         p = pa if name == "a" else pb
         if how == "host":
