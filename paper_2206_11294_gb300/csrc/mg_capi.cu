@@ -110,7 +110,8 @@ struct mg_handle {
     double *norms_d;       // device: [2] latest norms
     unsigned int *ticket;  // device: last-block counter of the norm kernels (re-armed by them)
     int *err_d;
-    double *norms_h;       // pinned host: [2]
+    double *norms_h;       // pinned host: [0..1] latest norms, [2..3] initial norms of a solve
+    bool x_stale;          // the handle's x ran an iteration the stop test did not allow: not copied back
     bool coeffs_set;
     cudaGraphExec_t g64, g32;   // FP64 cycle+norm; mixed inner cycles+update+residual
     struct SetupGraph {         // set-up of the levels for the input pointers in key
@@ -1038,31 +1039,50 @@ mg_status setup_hierarchy(mg_handle *h, const double *lam, const double *const f
 }
 
 // ---------------------------------------------------------------- solves
-template <int DIM>
-mg_status solve64(mg_handle *h, mg_stats *st) {
+// The stop-test loop of both precisions.  `initial` enqueues the initial
+// norms (into norms_d); g is the graph of one iteration, which copies its
+// norms to norms_h[0..1]; an iteration is `per_iter` V-cycles.  The first
+// iteration is launched before the initial norms are read, so one host wait
+// serves both: it only changes the handle's own x, which mg_solve does not
+// copy back (x_stale) when the initial state already meets the stop test.
+template <typename FInit>
+mg_status run_loop(mg_handle *h, mg_stats *st, cudaGraphExec_t g, long long kernels, int per_iter, FInit &&initial) {
     double n0[2], nk[2];
-    enqueue_norm<DIM>(h, h->stream, false);
-    CK(cudaMemcpyAsync(h->norms_h, h->norms_d, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
-    mg_status e = sync_norms(h, n0);
-    if (e) return e;
-    nk[0] = n0[0];
-    nk[1] = n0[1];
-    if (!h->g64) {
-        e = capture(h, &h->g64, &h->graph_kernels64, [&](cudaStream_t s) { enqueue_cycle64<DIM>(h, s); });
-        if (e) return e;
+    initial(h->stream);
+    CK(cudaMemcpyAsync(h->norms_h + 2, h->norms_d, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    const bool ahead = h->opt.max_cycles >= 1 && h->opt.rtol < 1.0;
+    if (ahead) {
+        CK(cudaGraphLaunch(g, h->stream));
+        h->enq += kernels;
     }
-    int cyc = 0;
+    CK(cudaStreamSynchronize(h->stream));
+    n0[0] = nk[0] = h->norms_h[2];
+    n0[1] = nk[1] = h->norms_h[3];
+    int it = 0;
     bool ok = converged(n0, nk, h->opt.rtol) || (n0[0] == 0.0 && n0[1] == 0.0);
-    while (!ok && cyc < h->opt.max_cycles) {
-        CK(cudaGraphLaunch(h->g64, h->stream));
-        h->enq += h->graph_kernels64;
-        if ((e = sync_norms(h, nk))) return e;
-        if ((e = accumulate_timing(h))) return e;
-        cyc++;
+    if (ahead) {
+        if (ok) {
+            h->x_stale = true;
+        } else {
+            nk[0] = h->norms_h[0];
+            nk[1] = h->norms_h[1];
+            mg_status e = accumulate_timing(h);
+            if (e) return e;
+            it = 1;
+            ok = converged(n0, nk, h->opt.rtol);
+        }
+    }
+    while (!ok && it < h->opt.max_cycles) {
+        CK(cudaGraphLaunch(g, h->stream));
+        h->enq += kernels;
+        mg_status e = sync_norms(h, nk);
+        if (!e) e = accumulate_timing(h);
+        if (e) return e;
+        it++;
         ok = converged(n0, nk, h->opt.rtol);
     }
-    st->cycles = cyc;
-    st->outer = cyc;
+    st->cycles = it * per_iter;
+    st->outer = it;
     st->r0[0] = n0[0];
     st->r0[1] = n0[1];
     st->rfinal[0] = nk[0];
@@ -1072,36 +1092,23 @@ mg_status solve64(mg_handle *h, mg_stats *st) {
 }
 
 template <int DIM>
-mg_status solve_mixed(mg_handle *h, mg_stats *st) {
-    double n0[2], nk[2];
-    enqueue_residual_to32<DIM>(h, h->stream);
-    CK(cudaMemcpyAsync(h->norms_h, h->norms_d, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
-    mg_status e = sync_norms(h, n0);
-    if (e) return e;
-    nk[0] = n0[0];
-    nk[1] = n0[1];
-    if (!h->g32) {
-        e = capture(h, &h->g32, &h->graph_kernels32, [&](cudaStream_t s) { enqueue_step32<DIM>(h, s); });
+mg_status solve64(mg_handle *h, mg_stats *st) {
+    if (!h->g64) {
+        const mg_status e = capture(h, &h->g64, &h->graph_kernels64, [&](cudaStream_t s) { enqueue_cycle64<DIM>(h, s); });
         if (e) return e;
     }
-    int outer = 0;
-    bool ok = converged(n0, nk, h->opt.rtol) || (n0[0] == 0.0 && n0[1] == 0.0);
-    while (!ok && outer < h->opt.max_cycles) {
-        CK(cudaGraphLaunch(h->g32, h->stream));
-        h->enq += h->graph_kernels32;
-        if ((e = sync_norms(h, nk))) return e;
-        if ((e = accumulate_timing(h))) return e;
-        outer++;
-        ok = converged(n0, nk, h->opt.rtol);
+    return run_loop(h, st, h->g64, h->graph_kernels64, 1,
+                    [&](cudaStream_t s) { enqueue_norm<DIM>(h, s, false); });
+}
+
+template <int DIM>
+mg_status solve_mixed(mg_handle *h, mg_stats *st) {
+    if (!h->g32) {
+        const mg_status e = capture(h, &h->g32, &h->graph_kernels32, [&](cudaStream_t s) { enqueue_step32<DIM>(h, s); });
+        if (e) return e;
     }
-    st->cycles = outer * h->opt.inner_cycles;
-    st->outer = outer;
-    st->r0[0] = n0[0];
-    st->r0[1] = n0[1];
-    st->rfinal[0] = nk[0];
-    st->rfinal[1] = nk[1];
-    st->status = (ok || !(h->opt.rtol > 0.0)) ? MG_OK : MG_ERR_NOT_CONVERGED;
-    return MG_OK;
+    return run_loop(h, st, h->g32, h->graph_kernels32, h->opt.inner_cycles,
+                    [&](cudaStream_t s) { enqueue_residual_to32<DIM>(h, s); });
 }
 
 mg_status check_handle(const mg_handle *h, bool need_coeffs) {
@@ -1372,6 +1379,7 @@ mg_status mg_solve(mg_handle *h, const double *rhs, double *x, int on_device, mg
     if (!rhs || !x) return fail(MG_ERR_INVALID_ARG, "rhs and x must not be NULL");
     DeviceGuard dg(h->device);
     CK(cudaMemsetAsync(h->err_d + 1, 0, sizeof(int), h->stream));
+    h->x_stale = false;
     if ((st = prep(h, rhs, x, on_device))) return st;
     mg_stats s;
     std::memset(&s, 0, sizeof(s));
@@ -1380,7 +1388,7 @@ mg_status mg_solve(mg_handle *h, const double *rhs, double *x, int on_device, mg
     if (h->opt.precision == MG_FP64) st = dim == 2 ? solve64<2>(h, &s) : solve64<3>(h, &s);
     else st = dim == 2 ? solve_mixed<2>(h, &s) : solve_mixed<3>(h, &s);
     if (st) return st;
-    if ((st = x_out(h, x, on_device))) return st;
+    if (!h->x_stale && (st = x_out(h, x, on_device))) return st;
     CK(cudaStreamWaitEvent(h->stream, h->ev_inv, 0));
     CK(cudaMemcpyAsync(h->errh, h->err_d, 2 * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));

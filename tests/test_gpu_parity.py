@@ -400,3 +400,43 @@ def test_setup_graph_follows_inputs(torch_cuda):
         assert st["cycles"] == ref[name][1], (name, how)
         assert np.array_equal(x, ref[name][0]), (name, how)
     s.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("on_device", [False, True])
+def test_no_cycle_when_stop_test_met_at_start(torch_cuda, precision, on_device):
+    """The first iteration is launched before the initial norms are read; when
+    they already meet the stop test (exactly zero here, or rtol >= 1), or no
+    cycle is allowed, the solve reports zero cycles and x is left as given, bit
+    for bit, from host and from device arrays."""
+    torch = torch_cuda
+    p = I.bubble_2d(64)                              # walls: no boundary data
+    zero_b = np.zeros_like(p.b)
+    zero_x = np.zeros_like(p.x0)
+    cases = [(dict(), zero_b, zero_x), (dict(rtol=2.0), p.b, p.x0), (dict(max_cycles=0), p.b, p.x0)]
+    for kw, b, x0 in cases:
+        s = _solver(p, precision=precision, **kw)
+        if on_device:
+            bd = torch.from_numpy(np.ascontiguousarray(b)).cuda()
+            xd = torch.from_numpy(np.ascontiguousarray(x0)).cuda()
+            st = s.solve(bd, xd, allow_not_converged=True)
+            x = xd.cpu().numpy()
+        else:
+            x = x0.copy()
+            st = s.solve(b, x, allow_not_converged=True)
+        assert st["cycles"] == 0 and st["outer"] == 0, kw
+        assert np.array_equal(x, x0), kw
+        assert list(st["rfinal"]) == list(st["r0"])
+        if "max_cycles" in kw:
+            assert st["status"] == "MG_ERR_NOT_CONVERGED"
+        else:
+            assert st["status"] == "MG_OK"
+        # the handle stays usable: a normal solve afterwards matches a fresh handle
+        x = p.x0.copy()
+        st = s.solve(p.b, x, allow_not_converged=True)
+        f = _solver(p, precision=precision, **kw)
+        xf = p.x0.copy()
+        stf = f.solve(p.b, xf, allow_not_converged=True)
+        assert st["cycles"] == stf["cycles"] and np.array_equal(x, xf)
+        s.close()
+        f.close()
