@@ -35,6 +35,16 @@ sys.path.insert(0, ROOT)
 METRIC = "coupled p-T MG Mcell-Vcycles/s & solves/s at 1e-10 resid; HBM %peak; p50/p99"
 UNIT = "Mcell-Vcycles/s"
 FALLBACK_HBM_GBS = 6800.0
+# DRAM bytes per launch of a dominant kernel, from the committed ncu captures
+# (profiles/); an entry holds while that kernel's source is unchanged.
+# "cold": ncu's default capture (caches flushed before the launch, the
+# recipe's figure); "warm": caches as the solve leaves them (median of the
+# 16 finest-level launches of one solve sequence).
+TRAFFIC = {
+    "k_rbgs_colour<double,2> on the finest level of bubbles16_1024x1024": {
+        "cold": 103.8e6, "warm": 33.8e6,
+        "source": "profiles/k_rbgs_colour_f64_bubbles1024.md (cold), k_rbgs_colour_f64_bubbles1024_warm.md (warm)"},
+}
 L2_FLUSH_BYTES = 256 << 20
 # algorithmic bytes per finest cell of one full red-black sweep: read x 16 +
 # bt 16 (Dinv b) + W 32 (the cell's 2x2 update matrix) + faces (2D 32, 3D 48),
@@ -236,10 +246,13 @@ def run_ours(args, rank, world):
     else:
         kernel = f"k_rbgs_colour<{rname},{dim0}>"
     kernel += " on the finest level of " + probs[0].name
+    tr = TRAFFIC.get(kernel)
+    traffic = args.traffic if args.traffic is not None else (tr["cold"] if tr else None)
+    traffic_note = None if args.traffic is not None or not tr else dict(tr)
     hbm = {"bound": "hbm", "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "GB/s",
            "frac": (achieved / peak) if achieved else None, "peak_source": peak_kind,
            "algorithmic_bytes_per_launch": per_launch, "avg_launch_us": avg_s * 1e6,
-           "launches_timed": c0["smooth_launches"], "traffic": args.traffic}
+           "launches_timed": c0["smooth_launches"], "traffic": traffic, "traffic_ncu": traffic_note}
     if args.precision == "fp64":
         inst = SWEEP_FP64_INST_PER_CELL[dim0] * c0["smooth_cells"] * sweeps_per_launch
         ach_i = inst / avg_s / 1e9 if avg_s > 0 else None
@@ -247,7 +260,8 @@ def run_ours(args, rank, world):
                     "unit": "G FP64 inst/s", "frac": (ach_i / FP64_INST_PEAK_G) if ach_i else None,
                     "peak_source": "derived: 152 SMs x 2 FP64 inst/clk/SM x 2.07 GHz (1.25 TFLOP/s FP64 nominal)",
                     "algorithmic_fp64_inst_per_launch": inst, "avg_launch_us": avg_s * 1e6,
-                    "launches_timed": c0["smooth_launches"], "traffic": args.traffic, "hbm": hbm}
+                    "launches_timed": c0["smooth_launches"], "traffic": traffic, "traffic_ncu": traffic_note,
+                    "hbm": hbm}
     else:
         roofline = hbm
     cycles = [st["cycles"] for st in stats[: len(probs)]]
