@@ -1,0 +1,206 @@
+"""FP64 CPU oracle of the steps on either side of the solve (test infrastructure).
+
+Only the tests, ``__graft_entry__.smoke()`` and the CPU leg of ``bench.py`` may
+import this module.  The CUDA library never calls it and shares no code with
+it.  Plain numpy, float64, element by element in the paper's notation.
+
+Before the solve (Sec. 3, from the advected state of Eq. Yadv):
+- ``mixture_pT``   p^(adv) from the averaged total energy (Eq. 20), then
+                   T^(adv) from p^(adv) (Eq. 23), both by the mixture's NASG EOS;
+- ``phase_beta``   thermal dilation of a phase at (T, p) (Eq. 10);
+- ``phase_c2``     squared speed of sound of a phase (Eq. 11);
+- ``div_faces``    the cell divergence of a face-normal velocity field;
+- ``assemble``     lambda_1..lambda_4, lambda_T, lambda_p (Eqs. 29-34), the face
+                   coefficients 1/rho and k, and the initial guess
+                   (T^(adv), p^(adv)).
+After it:
+- ``correct``      the velocity at the faces, u^{n+1} = u* - dt/rho grad p^{n+1}
+                   (Eq. unp1), and the phase pressures of Eqs. 37-38.
+
+Readings where the paper is silent (each listed in the design doc):
+- overlines are volume-fraction averages of the phase expressions; with the
+  partial densities m_i = C_i rho_i they read C_i (1 - rho_i b_i) = C_i - m_i b_i
+  and C_i rho_i q_i = m_i q_i, so no phase density is needed for p and T;
+- the bracket gamma/(rho c^2) - beta^2 T/(rho c_p), beta, beta/(rho c_p) and
+  rho c_p are averaged by C_i phase by phase; a phase with C_i = 0 adds nothing;
+- lambda_4 = beta/(rho c_p dt) (Eq. 32 as printed lacks the 1/dt that dividing
+  Eq. 19 by dt gives); ``lambda4="printed"`` gives the printed form;
+- faces: 1/rho_f with rho_f the mean of the two cells' mixture densities, k_f =
+  C_f k_1 + (1 - C_f) k_2 with C_f the mean of the two cells' C; a boundary face
+  takes its cell's values;
+- div u* and grad p are the finite-volume differences of the solve's operator
+  (axisymmetric: r_f / r_i weights on the r-faces), so that the divergence of
+  the corrected velocity is div u* - dt times the operator's p-Laplacian.
+"""
+from __future__ import annotations
+
+from typing import Dict, List, Sequence
+
+import numpy as np
+
+BC_WALL, BC_DIRICHLET, BC_AXIS = 0, 1, 2
+
+
+def _phase(ph) -> dict:
+    return ph if isinstance(ph, dict) else dict(ph.__dict__)
+
+
+def phase_beta(T, p, ph):
+    """Eq. 10: beta_i = (Gamma_i - 1) c_v,i / ((Gamma_i - 1) c_v,i T + b_i (p + Pi_i))."""
+    ph = _phase(ph)
+    g1cv = (ph["Gamma"] - 1.0) * ph["cv"]
+    return g1cv / (g1cv * T + ph["b"] * (p + ph["Pi"]))
+
+
+def phase_c2(p, rho_i, ph):
+    """Eq. 11: c_i^2 = Gamma_i (p + Pi_i) / (rho_i (1 - rho_i b_i))."""
+    ph = _phase(ph)
+    return ph["Gamma"] * (p + ph["Pi"]) / (rho_i * (1.0 - rho_i * ph["b"]))
+
+
+def mixture_pT(C, m1, m2, E, mom: Sequence[np.ndarray], ph1, ph2):
+    """Eq. 20 then Eq. 23 on the averaged state (C = C_1, C_2 = 1 - C)."""
+    ph1, ph2 = _phase(ph1), _phase(ph2)
+    Cs, ms = (C, 1.0 - C), (m1, m2)
+    rho = m1 + m2
+    kinetic = 0.5 * sum(mo * mo for mo in mom) / rho           # (1/2) rho |u|^2 with u = (rho u) / rho
+    shift = 0.0
+    denom = 0.0
+    for Ci, mi, ph in zip(Cs, ms, (ph1, ph2)):
+        free = Ci - mi * ph["b"]                                  # C_i (1 - rho_i b_i)
+        shift = shift + ph["Gamma"] * ph["Pi"] / (ph["Gamma"] - 1.0) * free + mi * ph["q"]
+        denom = denom + free / (ph["Gamma"] - 1.0)
+    p = (E - kinetic - shift) / denom
+    num = 0.0
+    heat = 0.0
+    for Ci, mi, ph in zip(Cs, ms, (ph1, ph2)):
+        free = Ci - mi * ph["b"]
+        num = num + free * p + ph["Pi"] * free                    # (1 - rho b) p + Pi (1 - rho b), averaged
+        heat = heat + mi * (ph["cp"] - ph["cv"])                  # rho (c_p - c_v), averaged
+    T = num / heat
+    return p, T
+
+
+def _cell_xyz(grid, a: int) -> np.ndarray:
+    """Cell-centre coordinate index i_a + 1/2 along axis a, broadcast to (n2, n1, n0)."""
+    n = grid.n
+    shape = [1, 1, 1]
+    shape[2 - a] = n[a]
+    return (np.arange(n[a], dtype=np.float64) + 0.5).reshape(shape)
+
+
+def _face_slices(a: int):
+    lo = [slice(None)] * 3
+    hi = [slice(None)] * 3
+    lo[2 - a] = slice(0, -1)
+    hi[2 - a] = slice(1, None)
+    return tuple(lo), tuple(hi)
+
+
+def div_faces(grid, uf: Sequence[np.ndarray]) -> np.ndarray:
+    """Sum over axes of (flux through the high face - flux through the low face) / (cell size); face arrays
+    shaped grid.face_shape(a).  Axisymmetric grids weight the r-faces (axis 0) by r_f / r_i."""
+    h = grid.h
+    out = np.zeros((grid.n[2], grid.n[1], grid.n[0]), dtype=np.float64)
+    for a in range(grid.dim):
+        lo, hi = _face_slices(a)
+        u = np.asarray(uf[a], dtype=np.float64)
+        if grid.axisym and a == 0:
+            ri = grid.r0 + _cell_xyz(grid, 0) * h
+            rlo, rhi = ri - 0.5 * h, ri + 0.5 * h
+            out = out + (rhi * u[hi] - rlo * u[lo]) / (ri * h)
+        else:
+            out = out + (u[hi] - u[lo]) / h
+    return out
+
+
+def _neighbour_mean(v: np.ndarray, a: int) -> np.ndarray:
+    """Face values of a cell field along axis a: the mean of the two cells, the cell's own at the boundary."""
+    s = list(v.shape)
+    s[2 - a] += 1
+    f = np.empty(s, dtype=np.float64)
+    lo, hi = _face_slices(a)
+    inner = [slice(None)] * 3
+    inner[2 - a] = slice(1, -1)
+    first = [slice(None)] * 3
+    first[2 - a] = slice(0, 1)
+    last = [slice(None)] * 3
+    last[2 - a] = slice(-1, None)
+    f[tuple(inner)] = 0.5 * (v[lo] + v[hi])
+    f[tuple(first)] = v[tuple(first)]
+    f[tuple(last)] = v[tuple(last)]
+    return f
+
+
+def assemble(grid, ph1, ph2, dt: float, C, m1, m2, E, mom: Sequence[np.ndarray], uf: Sequence[np.ndarray],
+             lambda4: str = "restored") -> Dict[str, np.ndarray]:
+    """The inputs of the solve from the advected state.  Cell arrays shaped
+    (n2, n1, n0), face arrays grid.face_shape(a).  Returns lam (N x 4), b
+    (N x 2), x0 (N x 2), fa / fk (per axis), and p, T, div."""
+    ph1, ph2 = _phase(ph1), _phase(ph2)
+    p, T = mixture_pT(C, m1, m2, E, mom, ph1, ph2)
+    Cs, ms = (C, 1.0 - C), (m1, m2)
+    rho_cp = 0.0
+    beta = 0.0
+    b_over = 0.0
+    bracket = 0.0
+    for Ci, mi, ph in zip(Cs, ms, (ph1, ph2)):
+        bi = phase_beta(T, p, ph)
+        present = Ci > 0.0
+        rho_i = np.where(present, mi / np.where(present, Ci, 1.0), 1.0)   # phase density where the phase is present
+        c2 = phase_c2(p, rho_i, ph)
+        gamma_i = ph["cp"] / ph["cv"]
+        rho_cp = rho_cp + mi * ph["cp"]
+        beta = beta + Ci * bi
+        b_over = b_over + np.where(present, Ci * bi / (rho_i * ph["cp"]), 0.0)
+        bracket = bracket + np.where(present, Ci * (gamma_i / (rho_i * c2) - bi * bi * T / (rho_i * ph["cp"])), 0.0)
+    div = div_faces(grid, uf)
+    l1 = -rho_cp / dt                                            # Eq. 29
+    l2 = beta * T / dt                                           # Eq. 30
+    l3 = -bracket / (dt * dt)                                    # Eq. 31
+    l4 = b_over / dt if lambda4 == "restored" else b_over        # Eq. 32 (1/dt restored)
+    lT = l1 * T + l2 * p                                         # Eq. 33
+    lp = l3 * p + div / dt                                       # Eq. 34
+    rho = m1 + m2
+    fa: List[np.ndarray] = []
+    fk: List[np.ndarray] = []
+    for a in range(grid.dim):
+        fa.append(1.0 / _neighbour_mean(rho, a))
+        Cf = _neighbour_mean(C, a)
+        fk.append(Cf * ph1["k"] + (1.0 - Cf) * ph2["k"])
+    flat = lambda v: np.ascontiguousarray(v, dtype=np.float64).reshape(-1)
+    lam = np.stack([flat(l1), flat(l2), flat(l3), flat(l4)], axis=1)
+    return dict(lam=lam, b=np.stack([flat(lT), flat(lp)], axis=1), x0=np.stack([flat(T), flat(p)], axis=1),
+                fa=fa, fk=fk, p=p, T=T, div=div)
+
+
+def correct(grid, dt: float, sigma: float, x: np.ndarray, C, kappa, fa: Sequence[np.ndarray],
+            uf: Sequence[np.ndarray]) -> Dict[str, object]:
+    """Eq. unp1 at the faces: u^{n+1} = u* - dt (1/rho)_f (grad p^{n+1})_f, with
+    the operator's face gradients: (p_R - p_L)/h inside, 2 (g - p_cell)/h
+    towards a Dirichlet value g, zero at walls and the axis.  Then Eqs. 37-38:
+    p_1 = p + (1 - C) sigma kappa, p_2 = p - C sigma kappa."""
+    n = grid.n
+    p = np.asarray(x, dtype=np.float64).reshape(n[2], n[1], n[0], 2)[..., 1]
+    h = grid.h
+    out = []
+    for a in range(grid.dim):
+        lo, hi = _face_slices(a)
+        g = np.zeros(grid.face_shape(a), dtype=np.float64)
+        inner = [slice(None)] * 3
+        inner[2 - a] = slice(1, -1)
+        g[tuple(inner)] = (p[hi] - p[lo]) / h
+        for side in (0, 1):
+            if grid.bc[a][side] != BC_DIRICHLET:
+                continue
+            gval = grid.bcp[a][side]
+            face = [slice(None)] * 3
+            cell = [slice(None)] * 3
+            face[2 - a] = slice(0, 1) if side == 0 else slice(-1, None)
+            cell[2 - a] = slice(0, 1) if side == 0 else slice(-1, None)
+            pc = p[tuple(cell)]
+            g[tuple(face)] = 2.0 * (pc - gval) / h if side == 0 else 2.0 * (gval - pc) / h
+        out.append(np.asarray(uf[a], dtype=np.float64) - dt * np.asarray(fa[a], dtype=np.float64) * g)
+    sk = sigma * np.asarray(kappa, dtype=np.float64)
+    Cc = np.asarray(C, dtype=np.float64)
+    return dict(uf=out, p1=p + (1.0 - Cc) * sk, p2=p - Cc * sk)

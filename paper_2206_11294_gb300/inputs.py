@@ -335,3 +335,127 @@ def random_coeff_problem(g: Grid, seed: int, jump: float = 1000.0, dt: float = 1
     # random initial guess around the background
     p.x0 = p.x0 * (1.0 + 1e-3 * rng.standard_normal(p.x0.shape))
     return p
+
+
+# ---------------------------------------------------------------------------
+# Advected state of one time step (the input of the coefficient assembly).
+# The fields are built from chosen temperature, pressure and velocity fields
+# through the NASG equations of state: the phase density from the thermal
+# relation rho_i (c_p,i - c_v,i) T = (p + Pi_i)(1 - rho_i b_i) (the one-phase
+# form of Eq. 23) and the internal energy from Eq. 9.  Liquid water of Table 1
+# and air as an ideal gas (Gamma = gamma = 1.4, Pi = b = q = 0, Sec. 2).
+# ---------------------------------------------------------------------------
+NASG_AIR = dict(Gamma=1.4, Pi=0.0, b=0.0, q=0.0, cp=1005.0, cv=717.857142857)
+
+
+@dataclasses.dataclass
+class NasgPhase:
+    Gamma: float
+    Pi: float
+    b: float
+    q: float
+    cp: float
+    cv: float
+    k: float
+
+
+def water_phase(k: float = 0.6) -> NasgPhase:
+    return NasgPhase(k=k, **NASG_WATER)
+
+
+def air_phase(k: float = 0.026) -> NasgPhase:
+    return NasgPhase(k=k, **NASG_AIR)
+
+
+@dataclasses.dataclass
+class AdvectedState:
+    name: str
+    grid: Grid
+    ph1: NasgPhase                # phase 1 (C = 1), the liquid
+    ph2: NasgPhase
+    dt: float
+    C: np.ndarray                 # (n2, n1, n0) volume fraction of phase 1
+    m1: np.ndarray                # C rho_1
+    m2: np.ndarray                # (1 - C) rho_2
+    E: np.ndarray                 # averaged total energy per volume
+    mom: List[np.ndarray]         # averaged momentum per axis
+    uf: List[np.ndarray]          # face-normal velocity u* per axis, shape grid.face_shape(a)
+    kappa: np.ndarray             # interface curvature (for Eqs. 37-38)
+    sigma: float
+    T: np.ndarray                 # the fields the state was built from
+    p: np.ndarray
+
+
+def phase_density(T, p, ph: NasgPhase):
+    """rho from rho (c_p - c_v) T = (p + Pi)(1 - rho b)."""
+    return (p + ph.Pi) / ((ph.cp - ph.cv) * T + ph.b * (p + ph.Pi))
+
+
+def phase_energy(p, rho, ph: NasgPhase):
+    """rho e from Eq. 9."""
+    return (p + ph.Gamma * ph.Pi) / (ph.Gamma - 1.0) * (1.0 - rho * ph.b) + rho * ph.q
+
+
+def advected_state(g: Grid, Cc: np.ndarray, seed: int, dt: float = 1e-7, dT: float = 4.0, dp: float = 3e3,
+                   u0: float = 0.5, sigma: float = 0.072, name: str = "") -> AdvectedState:
+    """Smooth seeded T, p, velocity fields (a few modes plus 1e-3 noise) on a
+    volume-fraction field; face velocities u* are the cell velocity's face means
+    plus noise, zero on walls and the axis."""
+    rng = np.random.default_rng(seed)
+    shape = (g.n[2], g.n[1], g.n[0])
+    X = [(np.arange(g.n[a], dtype=np.float64) + 0.5) / g.n[a] for a in range(3)]
+    grid3 = np.meshgrid(X[2], X[1], X[0], indexing="ij")
+    xs = [grid3[2], grid3[1], grid3[0]]
+
+    def smooth(amp: float) -> np.ndarray:
+        f = np.zeros(shape)
+        for _ in range(3):
+            k = rng.integers(1, 4, size=3)
+            ph = rng.uniform(0, 2 * np.pi, size=3)
+            term = np.ones(shape)
+            for a in range(g.dim):
+                term = term * np.cos(np.pi * k[a] * xs[a] + ph[a])
+            f = f + term * rng.uniform(0.3, 1.0)
+        return amp * f / 3.0 * (1.0 + 1e-3 * rng.standard_normal(shape))
+
+    T = T_INF + smooth(dT)
+    p = P_INF + smooth(dp)
+    u = [smooth(u0) for _ in range(g.dim)]
+    ph1, ph2 = water_phase(), air_phase()
+    C = np.clip(np.asarray(Cc, dtype=np.float64).reshape(shape), 0.0, 1.0)
+    r1, r2 = phase_density(T, p, ph1), phase_density(T, p, ph2)
+    m1, m2 = C * r1, (1.0 - C) * r2
+    rho = m1 + m2
+    E = C * phase_energy(p, r1, ph1) + (1.0 - C) * phase_energy(p, r2, ph2) + 0.5 * rho * sum(v * v for v in u)
+    mom = [rho * v for v in u]
+    uf = []
+    for a in range(g.dim):
+        fs = list(shape)
+        fs[2 - a] += 1
+        f = np.zeros(fs)
+        lo = [slice(None)] * 3
+        hi = [slice(None)] * 3
+        lo[2 - a] = slice(0, -1)
+        hi[2 - a] = slice(1, None)
+        inner = [slice(None)] * 3
+        inner[2 - a] = slice(1, -1)
+        f[tuple(inner)] = 0.5 * (u[a][tuple(lo)] + u[a][tuple(hi)])
+        f = f + 1e-3 * u0 * rng.standard_normal(fs)
+        for side in (0, 1):
+            if g.bc[a][side] != BC_DIRICHLET:
+                edge = [slice(None)] * 3
+                edge[2 - a] = slice(0, 1) if side == 0 else slice(-1, None)
+                f[tuple(edge)] = 0.0
+        uf.append(f)
+    kappa = rng.uniform(-50.0, 50.0, size=shape)
+    return AdvectedState(name=name or f"state{seed}", grid=g, ph1=ph1, ph2=ph2, dt=dt, C=C, m1=m1, m2=m2, E=E,
+                         mom=mom, uf=uf, kappa=kappa, sigma=sigma, T=T, p=p)
+
+
+def bubbles_state_1024(n: int = 1024, seed: int = 2) -> AdvectedState:
+    """The advected state on the 16-bubble 1024^2 grid of bubbles_1024."""
+    g = Grid(dim=2, axisym=0, n=(n, n, 1), h=1.0 / n, bc=_walls(2))
+    rng = np.random.default_rng(seed)
+    centres, radii = _place_bubbles(rng, 16, 0.02, 0.08, 2, (1.0, 1.0))
+    Cc = volume_fraction(g, centres, radii)
+    return advected_state(g, Cc, seed + 100, name=f"bubbles16_{n}x{n}_state")
