@@ -276,6 +276,70 @@ MG_API mg_status mg_batch_autotune(mg_batch *b, int reps, mg_batch_tuning *out, 
 
 MG_API mg_status mg_batch_destroy(mg_batch *b);
 
+/* ---------------------------------------------------------------------
+ * The steps on either side of the solve (Sec. 3, Algorithm 1): the
+ * coefficients of Eqs. 27-34 from the advected state of a time step, and the
+ * velocity and phase-pressure update from its solution.  All arrays are
+ * device pointers of the current device (host pointers are rejected with
+ * MG_ERR_INVALID_ARG), cells and faces in the layouts above; [N][2] and
+ * [N][4] arrays 16-byte aligned.  The work runs on `stream` (a cudaStream_t,
+ * NULL = legacy default) and the call returns after it completed.  Inputs
+ * are not checked for finiteness (mg_set_coeffs checks what it receives).
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    double Gamma, Pi, b, q;   /* NASG parameters of Eq. 9 (Table 1); ideal gas: Gamma = gamma, Pi = b = q = 0 */
+    double cp, cv;            /* heat capacities at constant pressure and volume, J/(kg K), cp > cv > 0 */
+    double k;                 /* thermal conductivity, W/(m K) */
+} mg_phase;
+
+typedef struct {              /* the advected state (Eq. Yadv) */
+    const double *C;          /* [N] volume fraction of phase 1, in [0, 1] */
+    const double *m1, *m2;    /* [N] partial densities C rho_1 and (1 - C) rho_2, kg/m^3 */
+    const double *E;          /* [N] averaged total energy per volume, sum of C_i rho_i e_T,i, J/m^3 */
+    const double *mom[3];     /* [N] averaged momentum, axes a < dim */
+    const double *uf[3];      /* face-normal velocity u* (Eq. provel) on the faces of axis a < dim */
+} mg_state;
+
+typedef struct {              /* what mg_set_coeffs and mg_solve take */
+    double *lambda;           /* [N][4] lambda_1..lambda_4 (Eqs. 29-32) */
+    double *rhs;              /* [N][2] (lambda_T, lambda_p) (Eqs. 33-34) */
+    double *x0;               /* [N][2] (T^(adv), p^(adv)), the initial guess; may be NULL */
+    double *face_alpha[3];    /* 1/rho on the faces of axis a < dim */
+    double *face_k[3];        /* k on the faces of axis a < dim */
+} mg_assembly;
+
+/* Coefficient assembly.  Per cell, with C_1 = C, C_2 = 1 - C and overlines
+ * the C_i-weighted averages of the phase expressions:
+ *   p^(adv) from the averaged total energy minus the kinetic energy
+ *     |rho u|^2 / (2 rho), rho = m1 + m2, by the mixture's NASG EOS (Eq. 20);
+ *   T^(adv) from p^(adv) (Eq. 23);
+ *   beta_i (Eq. 10) and c_i^2 (Eq. 11) at (T^(adv), p^(adv)), rho_i = m_i / C_i;
+ *   lambda_1 = -(m1 cp1 + m2 cp2) / dt, lambda_2 = beta T / dt,
+ *   lambda_3 = -bracket / dt^2 with bracket the average of
+ *     gamma_i / (rho_i c_i^2) - beta_i^2 T / (rho_i cp_i), gamma_i = cp_i / cv_i,
+ *   lambda_4 = average of beta_i / (rho_i cp_i), divided by dt unless
+ *     lambda4_printed != 0 (Eq. 32 as printed lacks the 1/dt that dividing
+ *     Eq. 19 by dt gives),
+ *   lambda_T = lambda_1 T + lambda_2 p, lambda_p = lambda_3 p + div(u*) / dt,
+ *     div the finite-volume divergence (r_f / r_i on axisymmetric r-faces);
+ *   faces: 1/rho_f with rho_f the mean of the two cells' rho, k_f = C_f k1 +
+ *     (1 - C_f) k2 with C_f the mean of their C; a boundary face takes its cell's.
+ * A phase with C_i = 0 in a cell contributes nothing there.  dt > 0. */
+MG_API mg_status mg_assemble(const mg_grid *grid, const mg_phase phases[2], double dt, int lambda4_printed,
+                             const mg_state *state, const mg_assembly *out, void *stream);
+
+/* Update after the solve.  x [N][2] is the solution (T, p) of mg_solve;
+ * face_alpha the faces' 1/rho (from mg_assemble); uf_star the u* of the state.
+ *   uf_out[a] = uf_star[a] - dt face_alpha[a] (grad p)_f  (Eq. unp1 at the
+ *     faces), with (p_R - p_L)/h inside, 2 (g - p)/h towards a Dirichlet value
+ *     g of grid->bc_p, and 0 at walls and the axis - the face gradients of the
+ *     solve's operator, so div uf_out = div u* - dt div((1/rho) grad p);
+ *   p1 = p + (1 - C) sigma kappa, p2 = p - C sigma kappa (Eqs. 37-38).
+ * uf_out may equal uf_star (in place). */
+MG_API mg_status mg_correct(const mg_grid *grid, double dt, double sigma, const double *x, const double *C,
+                            const double *kappa, const double *const face_alpha[3], const double *const uf_star[3],
+                            double *const uf_out[3], double *p1, double *p2, void *stream);
+
 /* Allocation-free stopping norms (the paper has no counterpart: this is a
  * library service).  For callers that cannot allocate device memory - their
  * device memory is owned by another allocator, or their time loop must not

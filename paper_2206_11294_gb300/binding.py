@@ -32,7 +32,7 @@ EXPORTS = ["mg_default_options", "mg_workspace_size", "mg_create", "mg_set_coeff
            "mg_last_error", "mg_set_timing", "mg_counters", "mg_residual_norms_noalloc",
            "mg_batch_create", "mg_batch_solve", "mg_batch_counters", "mg_batch_destroy", "mg_set_stream",
            "mg_batch_set_coeffs", "mg_get_tuning", "mg_set_tuning", "mg_autotune", "mg_batch_get_tuning",
-           "mg_batch_set_tuning", "mg_batch_autotune"]
+           "mg_batch_set_tuning", "mg_batch_autotune", "mg_assemble", "mg_correct"]
 
 MG_MAX_LEVELS = 32
 MG_SWEEP_COLOUR, MG_SWEEP_FUSED, MG_SWEEP_ASYNC, MG_SWEEP_COLOUR2 = 1, 2, 3, 4
@@ -115,6 +115,21 @@ class MgBatchTuning(C.Structure):
         return t
 
 
+class MgPhase(C.Structure):
+    _fields_ = [("Gamma", C.c_double), ("Pi", C.c_double), ("b", C.c_double), ("q", C.c_double),
+                ("cp", C.c_double), ("cv", C.c_double), ("k", C.c_double)]
+
+
+class MgState(C.Structure):
+    _fields_ = [("C", C.c_void_p), ("m1", C.c_void_p), ("m2", C.c_void_p), ("E", C.c_void_p),
+                ("mom", C.c_void_p * 3), ("uf", C.c_void_p * 3)]
+
+
+class MgAssembly(C.Structure):
+    _fields_ = [("lam", C.c_void_p), ("rhs", C.c_void_p), ("x0", C.c_void_p),
+                ("face_alpha", C.c_void_p * 3), ("face_k", C.c_void_p * 3)]
+
+
 _lib = None
 _lock = threading.Lock()
 
@@ -160,6 +175,9 @@ def load(path: str = LIB_PATH):
             "mg_batch_get_tuning": ([P, C.POINTER(MgBatchTuning)], C.c_int),
             "mg_batch_set_tuning": ([P, C.POINTER(MgBatchTuning)], C.c_int),
             "mg_batch_autotune": ([P, C.c_int, C.POINTER(MgBatchTuning), dp], C.c_int),
+            "mg_assemble": ([C.POINTER(MgGrid), MgPhase * 2, C.c_double, C.c_int, C.POINTER(MgState),
+                             C.POINTER(MgAssembly), P], C.c_int),
+            "mg_correct": ([C.POINTER(MgGrid), C.c_double, C.c_double, P, P, P, pa3, pa3, pa3, P, P, P], C.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -251,6 +269,60 @@ def residual_norms_noalloc(grid, lam, fa, fk, b, x, out, stream=None) -> None:
         stream = torch.cuda.current_stream()
     check(load().mg_residual_norms_noalloc(C.byref(g), _ptr(lam, True)[0], pa, pk, _ptr(b, True)[0],
                                            _ptr(x, True)[0], _ptr(out, True)[0], C.c_void_p(stream.cuda_stream)))
+
+
+def make_phase(ph) -> MgPhase:
+    """From an object or dict with Gamma, Pi, b, q, cp, cv, k."""
+    get = (lambda key: ph[key]) if isinstance(ph, dict) else (lambda key: getattr(ph, key))
+    return MgPhase(*(float(get(key)) for key in ("Gamma", "Pi", "b", "q", "cp", "cv", "k")))
+
+
+def assemble(grid, phases, dt: float, C_, m1, m2, E, mom: Sequence, uf: Sequence, out: dict,
+             lambda4_printed: bool = False, stream=None) -> None:
+    """mg_assemble: every array a contiguous float64 CUDA tensor.  out holds
+    "lam" (N x 4), "b" (N x 2), optionally "x0" (N x 2), and per-axis lists
+    "fa", "fk"; they are written in place."""
+    import torch
+    g = make_grid(grid)
+    keep = []
+
+    def dev(a):
+        p, k_ = _ptr(a, True)
+        keep.append(k_)
+        return p
+
+    st = MgState()
+    st.C, st.m1, st.m2, st.E = dev(C_), dev(m1), dev(m2), dev(E)
+    res = MgAssembly()
+    res.lam, res.rhs = dev(out["lam"]), dev(out["b"])
+    res.x0 = dev(out["x0"]) if out.get("x0") is not None else None
+    for a in range(g.dim):
+        st.mom[a] = dev(mom[a])
+        st.uf[a] = dev(uf[a])
+        res.face_alpha[a] = dev(out["fa"][a])
+        res.face_k[a] = dev(out["fk"][a])
+    ph = (MgPhase * 2)(make_phase(phases[0]), make_phase(phases[1]))
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    check(load().mg_assemble(C.byref(g), ph, float(dt), int(bool(lambda4_printed)), C.byref(st), C.byref(res),
+                             C.c_void_p(stream.cuda_stream)))
+
+
+def correct(grid, dt: float, sigma: float, x, C_, kappa, fa: Sequence, uf_star: Sequence, uf_out: Sequence, p1, p2,
+            stream=None) -> None:
+    """mg_correct: every array a contiguous float64 CUDA tensor; uf_out, p1, p2 are written."""
+    import torch
+    g = make_grid(grid)
+    pa, pu, po = (C.c_void_p * 3)(), (C.c_void_p * 3)(), (C.c_void_p * 3)()
+    for a in range(g.dim):
+        pa[a] = _ptr(fa[a], True)[0]
+        pu[a] = _ptr(uf_star[a], True)[0]
+        po[a] = _ptr(uf_out[a], True)[0]
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    check(load().mg_correct(C.byref(g), float(dt), float(sigma), _ptr(x, True)[0], _ptr(C_, True)[0],
+                            _ptr(kappa, True)[0], pa, pu, po, _ptr(p1, True)[0], _ptr(p2, True)[0],
+                            C.c_void_p(stream.cuda_stream)))
 
 
 class Solver:

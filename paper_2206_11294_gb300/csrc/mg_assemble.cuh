@@ -1,0 +1,201 @@
+// The steps on either side of the solve, per cell on the device (FP64).
+//
+// Before it (k_assemble): from the advected state of a time step (Eq. Yadv:
+// volume fraction C, partial densities m_i = C_i rho_i, averaged total energy,
+// averaged momentum, face velocities u*) the pressure p^(adv) by the mixture's
+// NASG equation of state (Eq. 20), the temperature T^(adv) (Eq. 23), the
+// thermal dilation (Eq. 10) and sound speed (Eq. 11) of each phase, the
+// coefficients lambda_1..lambda_4, lambda_T, lambda_p (Eqs. 29-34) and the face
+// coefficients 1/rho and k that mg_set_coeffs and mg_solve take.
+//
+// After it (k_correct): the face velocity u^{n+1} = u* - dt (1/rho)_f grad p
+// (Eq. unp1) with the solve operator's face gradients, and the phase pressures
+// p_1 = p + (1 - C) sigma kappa, p_2 = p - C sigma kappa (Eqs. 37-38).
+//
+// Overlines are volume-fraction averages of the phase expressions, written in
+// the partial densities: C_i (1 - rho_i b_i) = C_i - m_i b_i, C_i rho_i q_i =
+// m_i q_i, C_i / rho_i = C_i^2 / m_i, so pure cells need no special case; a
+// phase with C_i = 0 contributes nothing.
+#pragma once
+#include "mg_types.cuh"
+
+namespace cmg {
+
+// Per-phase constants, derived on the host from the NASG parameters.
+struct PhaseK {
+    double Gamma, Pi, b, q, cp, k;
+    double shift;          // Gamma Pi / (Gamma - 1)
+    double inv_g1;         // 1 / (Gamma - 1)
+    double cpcv;           // c_p - c_v
+    double g1cv;           // (Gamma - 1) c_v          (Eq. 10)
+    double gam_over_G;     // gamma / Gamma, gamma = c_p / c_v
+    double inv_cp;         // 1 / c_p
+};
+
+struct AssembleArgs {
+    int n[3];
+    int axisym;
+    double r0, h, inv_h;
+    double inv_dt, inv_dt2, l4_scale;   // l4_scale: 1/dt (restored lambda_4) or 1 (as printed)
+    PhaseK ph[2];
+    const double *C, *m1, *m2, *E;
+    const double *mom[3];
+    const double *uf[3];
+    double2 *lam;          // [N][2 pairs]: (l1, l2), (l3, l4)
+    double2 *rhs;          // [N]: (lambda_T, lambda_p)
+    double2 *x0;           // [N]: (T, p) or NULL
+    double *fa[3], *fk[3];
+};
+
+__device__ __forceinline__ long long face_index(const int n[3], int a, int i, int j, int k) {
+    const long long n0 = n[0] + (a == 0), n1 = n[1] + (a == 1);
+    return (long long)i + n0 * ((long long)j + n1 * k);
+}
+
+// One phase's share of the lambda averages at (T, p): beta C_i, the bracket of
+// Eq. 8 times C_i, and beta / (rho c_p) times C_i.
+__device__ __forceinline__ void phase_terms(const PhaseK &P, double Ci, double mi, double T, double p, double &beta_c,
+                                            double &bracket_c, double &bover_c) {
+    const double beta = P.g1cv / (P.g1cv * T + P.b * (p + P.Pi));       // Eq. 10
+    if (!(Ci > 0.0)) {
+        beta_c = bracket_c = bover_c = 0.0;
+        return;
+    }
+    // C_i gamma / (rho_i c_i^2) with c_i^2 of Eq. 11: gamma (C_i - m_i b_i) / (Gamma (p + Pi))
+    const double comp = P.gam_over_G * (Ci - mi * P.b) / (p + P.Pi);
+    const double c_over_rho = Ci * Ci / mi;                              // C_i / rho_i
+    const double bcp = beta * c_over_rho * P.inv_cp;                     // C_i beta / (rho_i c_p)
+    beta_c = Ci * beta;
+    bracket_c = comp - beta * T * bcp;
+    bover_c = bcp;
+}
+
+template <int DIM, bool AXI>
+__global__ void __launch_bounds__(256) k_assemble(const __grid_constant__ AssembleArgs A) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = DIM == 3 ? (int)blockIdx.z : 0;
+    if (i >= A.n[0] || j >= A.n[1]) return;
+    const int n0 = A.n[0], n1 = A.n[1];
+    const long long c = (long long)i + (long long)n0 * ((long long)j + (long long)n1 * k);
+    const double C = A.C[c], m1 = A.m1[c], m2 = A.m2[c], E = A.E[c];
+    const double C2 = 1.0 - C;
+    const double rho = m1 + m2;
+    double mm = 0.0;
+#pragma unroll
+    for (int a = 0; a < DIM; a++) {
+        const double u = A.mom[a][c];
+        mm = a == 0 ? u * u : mm + u * u;
+    }
+    const double kinetic = 0.5 * mm / rho;
+    const PhaseK &P1 = A.ph[0], &P2 = A.ph[1];
+    const double free1 = C - m1 * P1.b, free2 = C2 - m2 * P2.b;
+    // Eq. 20
+    const double shift = (P1.shift * free1 + m1 * P1.q) + (P2.shift * free2 + m2 * P2.q);
+    const double denom = free1 * P1.inv_g1 + free2 * P2.inv_g1;
+    const double p = (E - kinetic - shift) / denom;
+    // Eq. 23
+    const double T = ((free1 * p + P1.Pi * free1) + (free2 * p + P2.Pi * free2)) / (m1 * P1.cpcv + m2 * P2.cpcv);
+    double b1, k1, o1, b2, k2, o2;
+    phase_terms(P1, C, m1, T, p, b1, k1, o1);
+    phase_terms(P2, C2, m2, T, p, b2, k2, o2);
+    const double rho_cp = m1 * P1.cp + m2 * P2.cp;
+    // div u* (axisymmetric r-faces weighted by r_f / r_i)
+    double div = 0.0;
+#pragma unroll
+    for (int a = 0; a < DIM; a++) {
+        const int pos[3] = {i, j, k};
+        const long long flo = face_index(A.n, a, i, j, k);
+        const long long fhi = face_index(A.n, a, pos[0] + (a == 0), pos[1] + (a == 1), pos[2] + (a == 2));
+        const double ulo = A.uf[a][flo], uhi = A.uf[a][fhi];
+        double t;
+        if (AXI && a == 0) {
+            const double ri = A.r0 + (i + 0.5) * A.h;
+            t = ((ri + 0.5 * A.h) * uhi - (ri - 0.5 * A.h) * ulo) / (ri * A.h);
+        } else {
+            t = (uhi - ulo) * A.inv_h;
+        }
+        div = a == 0 ? t : div + t;
+    }
+    const double l1 = -rho_cp * A.inv_dt;                 // Eq. 29
+    const double l2 = (b1 + b2) * T * A.inv_dt;           // Eq. 30
+    const double l3 = -(k1 + k2) * A.inv_dt2;             // Eq. 31
+    const double l4 = (o1 + o2) * A.l4_scale;             // Eq. 32
+    A.lam[2 * c] = make_double2(l1, l2);
+    A.lam[2 * c + 1] = make_double2(l3, l4);
+    A.rhs[c] = make_double2(l1 * T + l2 * p, l3 * p + div * A.inv_dt);   // Eqs. 33-34
+    if (A.x0) A.x0[c] = make_double2(T, p);
+    // faces owned by this cell: the low face of each axis, and the high face on the high boundary
+#pragma unroll
+    for (int a = 0; a < DIM; a++) {
+        const int pos[3] = {i, j, k};
+#pragma unroll
+        for (int sd = 0; sd < 2; sd++) {
+            const int fpos = pos[a] + sd;
+            if (sd == 1 && fpos != A.n[a]) continue;
+            double rf, Cf;
+            if (fpos == 0 || fpos == A.n[a]) {
+                rf = rho;
+                Cf = C;
+            } else {
+                const long long cn = c - (a == 0 ? 1LL : a == 1 ? (long long)n0 : (long long)n0 * n1);
+                rf = 0.5 * (rho + (A.m1[cn] + A.m2[cn]));
+                Cf = 0.5 * (C + A.C[cn]);
+            }
+            const long long f = face_index(A.n, a, pos[0] + (a == 0 ? sd : 0), pos[1] + (a == 1 ? sd : 0),
+                                           pos[2] + (a == 2 ? sd : 0));
+            A.fa[a][f] = 1.0 / rf;
+            A.fk[a][f] = Cf * P1.k + (1.0 - Cf) * P2.k;
+        }
+    }
+}
+
+struct CorrectArgs {
+    int n[3];
+    int dir[3][2];           // Dirichlet faces
+    double gp[3][2];         // their pressure values
+    double dt, inv_h, two_inv_h, sigma;
+    const double2 *x;        // [N] (T, p)
+    const double *C, *kappa;
+    const double *fa[3], *uf[3];
+    double *uo[3];
+    double *p1, *p2;
+};
+
+template <int DIM>
+__global__ void __launch_bounds__(256) k_correct(const __grid_constant__ CorrectArgs A) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = DIM == 3 ? (int)blockIdx.z : 0;
+    if (i >= A.n[0] || j >= A.n[1]) return;
+    const int n0 = A.n[0], n1 = A.n[1];
+    const long long c = (long long)i + (long long)n0 * ((long long)j + (long long)n1 * k);
+    const double p = A.x[c].y;
+#pragma unroll
+    for (int a = 0; a < DIM; a++) {
+        const int pos[3] = {i, j, k};
+#pragma unroll
+        for (int sd = 0; sd < 2; sd++) {
+            const int fpos = pos[a] + sd;
+            if (sd == 1 && fpos != A.n[a]) continue;
+            double g;
+            if (fpos == 0) {
+                g = A.dir[a][0] ? (p - A.gp[a][0]) * A.two_inv_h : 0.0;     // towards the low boundary value
+            } else if (fpos == A.n[a]) {
+                g = A.dir[a][1] ? (A.gp[a][1] - p) * A.two_inv_h : 0.0;
+            } else {
+                const long long cn = c - (a == 0 ? 1LL : a == 1 ? (long long)n0 : (long long)n0 * n1);
+                g = (p - A.x[cn].y) * A.inv_h;
+            }
+            const long long f = face_index(A.n, a, pos[0] + (a == 0 ? sd : 0), pos[1] + (a == 1 ? sd : 0),
+                                           pos[2] + (a == 2 ? sd : 0));
+            A.uo[a][f] = A.uf[a][f] - A.dt * A.fa[a][f] * g;
+        }
+    }
+    const double sk = A.sigma * A.kappa[c];
+    const double Cc = A.C[c];
+    A.p1[c] = p + (1.0 - Cc) * sk;
+    A.p2[c] = p - Cc * sk;
+}
+
+}  // namespace cmg

@@ -23,6 +23,7 @@
 #include "mg_kernels.cuh"
 #include "mg_tail.cuh"
 #include "mg_async.cuh"
+#include "mg_assemble.cuh"
 
 using namespace cmg;
 
@@ -139,8 +140,9 @@ bool can_coarsen(const int n[3], int dim, int coarse_min) {
     return true;
 }
 
-mg_status check_grid(const mg_grid *g, const mg_options *o) {
-    if (!g || !o) return fail(MG_ERR_INVALID_ARG, "grid and options must not be NULL");
+// The grid alone: dimensions, spacing, boundary kinds and values.
+mg_status check_grid_geom(const mg_grid *g) {
+    if (!g) return fail(MG_ERR_INVALID_ARG, "grid must not be NULL");
     if (g->dim != 2 && g->dim != 3) return fail(MG_ERR_INVALID_ARG, "dim must be 2 or 3");
     if (g->axisym && g->dim != 2) return fail(MG_ERR_INVALID_ARG, "axisymmetric grids are 2D (r, z)");
     for (int a = 0; a < 3; a++) {
@@ -164,6 +166,13 @@ mg_status check_grid(const mg_grid *g, const mg_options *o) {
         }
     if (g->axisym && g->r0 == 0.0 && g->bc[0][0] == MG_BC_DIRICHLET)
         return fail(MG_ERR_INVALID_ARG, "the symmetry axis (r0 = 0) cannot carry a Dirichlet condition");
+    return MG_OK;
+}
+
+mg_status check_grid(const mg_grid *g, const mg_options *o) {
+    if (!g || !o) return fail(MG_ERR_INVALID_ARG, "grid and options must not be NULL");
+    const mg_status st = check_grid_geom(g);
+    if (st) return st;
     if (o->nu1 < 0 || o->nu2 < 0 || o->nu1 > 16 || o->nu2 > 16 || o->nu1 + o->nu2 == 0)
         return fail(MG_ERR_INVALID_ARG, "nu1, nu2 must be in 0..16 and not both zero");
     if (o->precision != MG_FP64 && o->precision != MG_MIXED) return fail(MG_ERR_INVALID_ARG, "unknown precision");
@@ -1436,6 +1445,146 @@ mg_status mg_smooth(mg_handle *h, const double *rhs, double *x, int sweeps, int 
     CK(cudaGetLastError());
     if ((st = x_out(h, x, on_device))) return st;
     CK(cudaStreamSynchronize(h->stream));
+    return MG_OK;
+}
+
+// ---------------------------------------------------------------- assembly and update
+namespace {
+bool device_ptr(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+mg_status check_phase(const mg_phase &P) {
+    const double v[7] = {P.Gamma, P.Pi, P.b, P.q, P.cp, P.cv, P.k};
+    for (double x : v)
+        if (!std::isfinite(x)) return fail(MG_ERR_INVALID_ARG, "phase parameters must be finite");
+    if (!(P.Gamma > 1.0)) return fail(MG_ERR_INVALID_ARG, "phase Gamma must be > 1");
+    if (!(P.cv > 0.0) || !(P.cp > P.cv)) return fail(MG_ERR_INVALID_ARG, "phase heat capacities need cp > cv > 0");
+    if (P.b < 0.0 || P.k < 0.0) return fail(MG_ERR_INVALID_ARG, "phase b and k must be >= 0");
+    return MG_OK;
+}
+
+PhaseK phase_k(const mg_phase &P) {
+    PhaseK K;
+    K.Gamma = P.Gamma;
+    K.Pi = P.Pi;
+    K.b = P.b;
+    K.q = P.q;
+    K.cp = P.cp;
+    K.k = P.k;
+    K.shift = P.Gamma * P.Pi / (P.Gamma - 1.0);
+    K.inv_g1 = 1.0 / (P.Gamma - 1.0);
+    K.cpcv = P.cp - P.cv;
+    K.g1cv = (P.Gamma - 1.0) * P.cv;
+    K.gam_over_G = (P.cp / P.cv) / P.Gamma;
+    K.inv_cp = 1.0 / P.cp;
+    return K;
+}
+}  // namespace
+
+mg_status mg_assemble(const mg_grid *grid, const mg_phase phases[2], double dt, int lambda4_printed,
+                      const mg_state *s, const mg_assembly *out, void *stream) {
+    mg_status st = check_grid_geom(grid);
+    if (st) return st;
+    if (!phases || !s || !out) return fail(MG_ERR_INVALID_ARG, "phases, state and out must not be NULL");
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(MG_ERR_INVALID_ARG, "dt must be positive and finite");
+    for (int q = 0; q < 2; q++)
+        if ((st = check_phase(phases[q]))) return st;
+    const int dim = grid->dim;
+    bool ok = device_ptr(s->C) && device_ptr(s->m1) && device_ptr(s->m2) && device_ptr(s->E) &&
+              device_ptr(out->lambda) && device_ptr(out->rhs) && (!out->x0 || device_ptr(out->x0));
+    for (int a = 0; a < dim; a++)
+        ok = ok && device_ptr(s->mom[a]) && device_ptr(s->uf[a]) && device_ptr(out->face_alpha[a]) &&
+             device_ptr(out->face_k[a]);
+    if (!ok) return fail(MG_ERR_INVALID_ARG, "every array must be a device pointer of the current device");
+    if (!aligned16(out->lambda) || !aligned16(out->rhs) || (out->x0 && !aligned16(out->x0)))
+        return fail(MG_ERR_INVALID_ARG, "lambda, rhs and x0 must be 16-byte aligned");
+    AssembleArgs A;
+    std::memset(&A, 0, sizeof(A));
+    for (int a = 0; a < 3; a++) A.n[a] = grid->n[a];
+    A.axisym = grid->axisym;
+    A.r0 = grid->r0;
+    A.h = grid->h;
+    A.inv_h = 1.0 / grid->h;
+    A.inv_dt = 1.0 / dt;
+    A.inv_dt2 = 1.0 / (dt * dt);
+    A.l4_scale = lambda4_printed ? 1.0 : 1.0 / dt;
+    A.ph[0] = phase_k(phases[0]);
+    A.ph[1] = phase_k(phases[1]);
+    A.C = s->C;
+    A.m1 = s->m1;
+    A.m2 = s->m2;
+    A.E = s->E;
+    for (int a = 0; a < dim; a++) {
+        A.mom[a] = s->mom[a];
+        A.uf[a] = s->uf[a];
+        A.fa[a] = out->face_alpha[a];
+        A.fk[a] = out->face_k[a];
+    }
+    A.lam = reinterpret_cast<double2 *>(out->lambda);
+    A.rhs = reinterpret_cast<double2 *>(out->rhs);
+    A.x0 = reinterpret_cast<double2 *>(out->x0);
+    const dim3 gr((unsigned)((grid->n[0] + kBX - 1) / kBX), (unsigned)((grid->n[1] + kBY - 1) / kBY),
+                  (unsigned)(dim == 3 ? grid->n[2] : 1));
+    cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+    if (dim == 3) k_assemble<3, false><<<gr, kBlock, 0, cs>>>(A);
+    else if (grid->axisym) k_assemble<2, true><<<gr, kBlock, 0, cs>>>(A);
+    else k_assemble<2, false><<<gr, kBlock, 0, cs>>>(A);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(cs));
+    return MG_OK;
+}
+
+mg_status mg_correct(const mg_grid *grid, double dt, double sigma, const double *x, const double *C,
+                     const double *kappa, const double *const face_alpha[3], const double *const uf_star[3],
+                     double *const uf_out[3], double *p1, double *p2, void *stream) {
+    mg_status st = check_grid_geom(grid);
+    if (st) return st;
+    if (!face_alpha || !uf_star || !uf_out) return fail(MG_ERR_INVALID_ARG, "face array lists must not be NULL");
+    if (!(dt > 0.0) || !std::isfinite(dt) || !std::isfinite(sigma))
+        return fail(MG_ERR_INVALID_ARG, "dt must be positive and finite, sigma finite");
+    const int dim = grid->dim;
+    bool ok = device_ptr(x) && device_ptr(C) && device_ptr(kappa) && device_ptr(p1) && device_ptr(p2);
+    for (int a = 0; a < dim; a++)
+        ok = ok && device_ptr(face_alpha[a]) && device_ptr(uf_star[a]) && device_ptr(uf_out[a]);
+    if (!ok) return fail(MG_ERR_INVALID_ARG, "every array must be a device pointer of the current device");
+    if (!aligned16(x)) return fail(MG_ERR_INVALID_ARG, "x must be 16-byte aligned");
+    CorrectArgs A;
+    std::memset(&A, 0, sizeof(A));
+    for (int a = 0; a < 3; a++) {
+        A.n[a] = grid->n[a];
+        for (int sd = 0; sd < 2; sd++) {
+            A.dir[a][sd] = a < dim && grid->bc[a][sd] == MG_BC_DIRICHLET;
+            A.gp[a][sd] = a < dim ? grid->bc_p[a][sd] : 0.0;
+        }
+    }
+    A.dt = dt;
+    A.inv_h = 1.0 / grid->h;
+    A.two_inv_h = 2.0 / grid->h;
+    A.sigma = sigma;
+    A.x = reinterpret_cast<const double2 *>(x);
+    A.C = C;
+    A.kappa = kappa;
+    for (int a = 0; a < dim; a++) {
+        A.fa[a] = face_alpha[a];
+        A.uf[a] = uf_star[a];
+        A.uo[a] = uf_out[a];
+    }
+    A.p1 = p1;
+    A.p2 = p2;
+    const dim3 gr((unsigned)((grid->n[0] + kBX - 1) / kBX), (unsigned)((grid->n[1] + kBY - 1) / kBY),
+                  (unsigned)(dim == 3 ? grid->n[2] : 1));
+    cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+    if (dim == 3) k_correct<3><<<gr, kBlock, 0, cs>>>(A);
+    else k_correct<2><<<gr, kBlock, 0, cs>>>(A);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(cs));
     return MG_OK;
 }
 
