@@ -488,6 +488,95 @@ def run_wall3d(args):
     return out
 
 
+# Algorithmic bytes per cell of the assembly and update kernels (2D): what
+# each must read and write once (face arrays: one face per cell and axis).
+ASSEMBLE_BYTES_2D = (4 + 2 + 2) * 8 + (4 + 2 + 2 + 2 + 2) * 8    # C m1 m2 E, mom, u*; lambda, rhs, x0, 1/rho, k
+CORRECT_BYTES_2D = (2 + 1 + 1 + 2 + 2) * 8 + (2 + 1 + 1) * 8      # x, C, kappa, 1/rho, u*; u^(n+1), p1, p2
+
+
+def run_timestep(args):
+    """The device work of one time step on the 16-bubble 1024^2 advected state:
+    coefficient assembly (mg_assemble_async: Eqs. 10, 11, 20, 23, 29-34), set-up and
+    solve to 1e-10 from (T^(adv), p^(adv)), and the velocity / phase-pressure
+    update (mg_correct_async: Eq. unp1, Eqs. 37-38).  Inputs resident on the device;
+    the L2 is flushed between steps."""
+    import numpy as np
+    import torch
+    from paper_2206_11294_gb300 import binding as B
+    from paper_2206_11294_gb300 import inputs as I
+    from paper_2206_11294_gb300.binding import Solver
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    s = I.bubbles_state_1024()
+    g = s.grid
+    N = g.N
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+    z = lambda *shape: torch.zeros(*shape, dtype=torch.float64, device="cuda")
+    d = dict(C=T(s.C), m1=T(s.m1), m2=T(s.m2), E=T(s.E), mom=[T(m) for m in s.mom], uf=[T(u) for u in s.uf],
+             kappa=T(s.kappa))
+    out = dict(lam=z(N, 4), b=z(N, 2), x0=z(N, 2), fa=[z(*g.face_shape(a)) for a in range(2)],
+               fk=[z(*g.face_shape(a)) for a in range(2)])
+    x = z(N, 2)
+    uo = [torch.empty_like(u) for u in d["uf"]]
+    p1, p2 = z(*s.C.shape), z(*s.C.shape)
+    solver = Solver(g, precision=args.precision, rtol=1e-10, max_cycles=50, stream=stream)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+
+    def assemble():
+        B.assemble(g, (s.ph1, s.ph2), s.dt, d["C"], d["m1"], d["m2"], d["E"], d["mom"], d["uf"], out)
+
+    def correct():
+        B.correct(g, s.dt, s.sigma, x, d["C"], d["kappa"], out["fa"], d["uf"], uo, p1, p2)
+
+    assemble()
+    solver.set_coeffs(out["lam"], out["fa"], out["fk"])
+    tuning = None
+    if not args.no_tune:
+        from paper_2206_11294_gb300.autotune import describe
+        tuning = describe(solver.autotune(args.tune_reps)[0])
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    stats = []
+
+    def step(marks):
+        marks[0].record(stream)
+        assemble()
+        marks[1].record(stream)
+        solver.set_coeffs(out["lam"], out["fa"], out["fk"])
+        x.copy_(out["x0"])
+        stats.append(solver.solve(out["b"], x))
+        marks[2].record(stream)
+        correct()
+        marks[3].record(stream)
+
+    for _ in range(args.warmup):
+        step([ev() for _ in range(4)])
+    torch.cuda.synchronize()
+    stats.clear()
+    marks = [[ev() for _ in range(4)] for _ in range(args.steps)]
+    clocks = ClockSampler(gpu_identity(torch, 0))
+    for k in range(args.steps):
+        flush.zero_()
+        step(marks[k])
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    total = sum(m[0].elapsed_time(m[3]) for m in marks) / args.steps
+    t_asm = sum(m[0].elapsed_time(m[1]) for m in marks) / args.steps
+    t_cor = sum(m[2].elapsed_time(m[3]) for m in marks) / args.steps
+    peak, peak_kind = measured_peak()
+    roof = lambda byts, ms: {"bound": "hbm", "achieved": byts / (ms * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
+                             "frac": byts / (ms * 1e-3) / 1e9 / peak, "peak_source": peak_kind,
+                             "algorithmic_bytes": byts, "avg_launch_us": ms * 1e3}
+    cycles = [st["cycles"] for st in stats]
+    return {"workload": "one time step, bubbles16_1024x1024 advected state: assembly + set-up + solve to 1e-10 + "
+                        "velocity / phase-pressure update", "metric": "time steps/s", "cells": N,
+            "precision": args.precision, "steps_per_s": 1e3 / total, "ms_per_step": total,
+            "assemble_ms": t_asm, "solve_ms": total - t_asm - t_cor, "correct_ms": t_cor,
+            "cycles_per_solve": cycles[0] if cycles else None, "tuning": tuning,
+            "assemble_roofline": roof(ASSEMBLE_BYTES_2D * N, t_asm),
+            "correct_roofline": roof(CORRECT_BYTES_2D * N, t_cor),
+            "l2": "flushed between steps", "clocks": clk, "data": "synthetic (seeded advected state, NASG water / air)"}
+
+
 def run_serve(args):
     """Poisson arrivals of mixed 2D (128..1024) and 3D (64..160) bubble solves,
     mixed precision, admitted against an HBM budget; p50/p99 per arrival rate."""
@@ -581,7 +670,7 @@ def main():
     ap.add_argument("--no-tune", action="store_true", help="library default kernel choices, no autotuning")
     ap.add_argument("--tune-reps", type=int, default=5)
     ap.add_argument("--tuning-table", default=None, help="JSON table of autotuned choices to apply (and extend)")
-    ap.add_argument("--workload", default="bubbles", choices=["bubbles", "batch", "serve", "wall3d"])
+    ap.add_argument("--workload", default="bubbles", choices=["bubbles", "batch", "serve", "wall3d", "timestep"])
     ap.add_argument("--n3d", type=int, default=256)
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--serve-rates", type=float, nargs="+", default=[10, 30, 100, 300, 1000, 2000])
@@ -595,7 +684,8 @@ def main():
     rank = env_int("RANK", 0)
     if args.workload != "bubbles":
         if rank == 0:
-            out = {"batch": run_batch, "serve": run_serve, "wall3d": run_wall3d}[args.workload](args)
+            out = {"batch": run_batch, "serve": run_serve, "wall3d": run_wall3d,
+                   "timestep": run_timestep}[args.workload](args)
             print(json.dumps(out), flush=True)
         return
     if args.impl == "ours" and world > 1:

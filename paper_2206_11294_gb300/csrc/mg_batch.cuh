@@ -22,6 +22,8 @@ struct BLevel {                 // one (problem, level), device side
     Level<float> f;
     double2 *xalt;
     float2 *xalt32;
+    double2 *delta;             // finest level, mixed precision: the correction from the initial guess
+                                // (the handle's staging area); x keeps the initial guess
     BcFlags bc;
     int problem;
 };
@@ -415,15 +417,32 @@ __global__ void __launch_bounds__(kBatchThreads) kb_residual64(const BLevel *__r
         const BLevel &B = lv[e.x];
         const int p = B.problem;
         if (!initial && !st[p].active) continue;
-        const Level<double> L = B.d;
+        Level<double> L = B.d;
         int bx, by, bz;
         block_coords(e.y, norm_gx(L.n0), norm_gy(L.n1), bx, by, bz);
-        const double2 s = residual64_to32_block<DIM>(L, B.f.b, B.f.bt, B.f.x, bx, by, bz);
+        // defect correction: the initial call stores r0 = b - A x0 over b and sets delta = 0; later calls
+        // form r0 - A delta
+        if (!initial) L.x = B.delta;
+        const double2 s = residual64_to32_block<DIM>(L, B.f.b, B.f.bt, B.f.x, initial ? L.b : nullptr,
+                                                     initial ? B.delta : nullptr, bx, by, bz);
         batch_finish(pr[p], st[p], e.y, s, initial, rtol, max_cycles, active_count);
     }
 }
 
-// Mixed precision: x64 += e32 on the finest level of active problems.
+// Mixed precision, at the end: x = x0 + delta.
+__global__ void __launch_bounds__(kBatchThreads) kb_finish_correction(const BLevel *__restrict__ lv,
+                                                                      const int2 *__restrict__ tab, int n) {
+    for (int v = blockIdx.x; v < n; v += gridDim.x) {
+        const int2 e = tab[v];
+        const BLevel &B = lv[e.x];
+        const long long c = (long long)e.y * kBatchThreads + threadIdx.x;
+        if (c >= B.d.N) continue;
+        const double2 a = B.d.x[c], d = B.delta[c];
+        B.d.x[c] = make_double2(a.x + d.x, a.y + d.y);
+    }
+}
+
+// Mixed precision: delta += e32 on the finest level of active problems.
 __global__ void __launch_bounds__(kBatchThreads) kb_add_correction(const BLevel *__restrict__ lv,
                                                                    const BState *__restrict__ st,
                                                                    const int2 *__restrict__ tab, int n) {
@@ -434,10 +453,10 @@ __global__ void __launch_bounds__(kBatchThreads) kb_add_correction(const BLevel 
         const long long c = (long long)e.y * kBatchThreads + threadIdx.x;
         if (c >= B.d.N) continue;
         const float2 d = B.f.x[c];
-        double2 xv = B.d.x[c];
+        double2 xv = B.delta[c];
         xv.x += (double)d.x;
         xv.y += (double)d.y;
-        B.d.x[c] = xv;
+        B.delta[c] = xv;
     }
 }
 
@@ -726,6 +745,7 @@ mg_status mg_batch_create(int count, mg_handle *const *handles, mg_batch **out) 
             if (h->opt.precision == MG_MIXED) d.f = view<float>(L);
             d.xalt = L.xalt;
             d.xalt32 = L.xalt32;
+            d.delta = l == 0 ? reinterpret_cast<double2 *>(h->stage) : nullptr;
             d.bc = bc_flags(h->grid);
             d.problem = p;
             lv.push_back(d);
@@ -947,6 +967,7 @@ mg_status mg_batch_solve(mg_batch *b, const double *const *rhs, double *const *x
     }
     if (b->dim == 2) b_norm<2>(b, s, 1);
     else b_norm<3>(b, s, 1);
+    const bool mixed = b->opt.precision == MG_MIXED;
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(s));
     int active = *b->active_h;
@@ -978,6 +999,11 @@ mg_status mg_batch_solve(mg_batch *b, const double *const *rhs, double *const *x
         CK(cudaStreamSynchronize(s));
         active = *b->active_h;
         steps++;
+    }
+    if (mixed) {
+        const int n = b->cells0.second;
+        kb_finish_correction<<<batch_grid(b, n), kBatchThreads, 0, s>>>(b->lv, b->tabs + b->cells0.first, n);
+        b->launches++;
     }
     std::vector<BState> host(b->count);
     CK(cudaMemcpyAsync(host.data(), b->st, sizeof(BState) * b->count, cudaMemcpyDeviceToHost, s));

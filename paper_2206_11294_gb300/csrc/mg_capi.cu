@@ -701,17 +701,32 @@ void enqueue_norm(const mg_handle *h, cudaStream_t s, bool after_sweep) {
     counted(h);
 }
 
+// Mixed precision solves for the correction delta from the initial guess x0
+// (the paper's defect correction, the steps after Eq. 34): x keeps x0, delta
+// lives in the staging area (at least 32 bytes per cell, free once prep has
+// run).
+double2 *mixed_delta(const mg_handle *h) { return reinterpret_cast<double2 *>(h->stage); }
+
+// FP64 residual of the finest level, as the FP32 right-hand side, with its
+// norms.  initial: r0 = b - A x0, written over b, and delta set to zero;
+// otherwise r = r0 - A delta.  Forming b - A x every step instead subtracts
+// terms of the size of b (lambda_T ~ 1e16 at these units) and leaves a
+// rounding floor that a good initial guess puts near the tolerance.
 template <int DIM>
-void enqueue_residual_to32(const mg_handle *h, cudaStream_t s) {
+void enqueue_residual_to32(const mg_handle *h, cudaStream_t s, bool initial = false) {
     const LevelBuf &f = h->L[0];
     const dim3 ng = norm_grid(f, DIM);
+    Level<double> v = view<double>(f);
+    double2 *delta = mixed_delta(h);
+    if (!initial) v.x = delta;
+    double2 *r_out = initial ? f.b : nullptr;
+    double2 *r_out2 = initial ? delta : nullptr;
     if (h->persistent)
         k_residual64_to32<DIM, true><<<wave((const void *)k_residual64_to32<DIM, true>, tiles_of(ng)), kBlock, 0, s>>>(
-            view<double>(f), f.b32, f.bt32, f.x32, h->partial, h->ticket, h->norms_d);
+            v, f.b32, f.bt32, f.x32, r_out, r_out2, h->partial, h->ticket, h->norms_d);
     else
-        k_residual64_to32<DIM, false><<<ng, kBlock, 0, s>>>(view<double>(f), f.b32, f.bt32, f.x32,
-                                                                         h->partial,
-                                                                         h->ticket, h->norms_d);
+        k_residual64_to32<DIM, false><<<ng, kBlock, 0, s>>>(v, f.b32, f.bt32, f.x32, r_out, r_out2, h->partial,
+                                                             h->ticket, h->norms_d);
     counted(h);
 }
 
@@ -746,7 +761,7 @@ template <int DIM>
 void enqueue_step32(const mg_handle *h, cudaStream_t s) {
     for (int q = 0; q < h->opt.inner_cycles; q++) enqueue_vcycle<float, DIM>(h, s, 0);
     const LevelBuf &f = h->L[0];
-    k_add_correction<<<lin_blocks(f.N), 256, 0, s>>>(f.x, f.x32, f.N);
+    k_add_correction<<<lin_blocks(f.N), 256, 0, s>>>(mixed_delta(h), f.x32, f.N);
     counted(h);
     enqueue_residual_to32<DIM>(h, s);
     cudaMemcpyAsync(h->norms_h, h->norms_d, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
@@ -1116,8 +1131,18 @@ mg_status solve_mixed(mg_handle *h, mg_stats *st) {
         const mg_status e = capture(h, &h->g32, &h->graph_kernels32, [&](cudaStream_t s) { enqueue_step32<DIM>(h, s); });
         if (e) return e;
     }
-    return run_loop(h, st, h->g32, h->graph_kernels32, h->opt.inner_cycles,
-                    [&](cudaStream_t s) { enqueue_residual_to32<DIM>(h, s); });
+    // r0 = b - A x0 once, delta from A delta = r0 by FP32 cycles with the
+    // FP64 residual r0 - A delta after each outer step, then x = x0 + delta
+    const LevelBuf &f = h->L[0];
+    const mg_status e = run_loop(h, st, h->g32, h->graph_kernels32, h->opt.inner_cycles,
+                                 [&](cudaStream_t s) { enqueue_residual_to32<DIM>(h, s, true); });
+    if (e) return e;
+    if (!h->x_stale) {
+        k_add_pairs<<<lin_blocks(f.N), 256, 0, h->stream>>>(f.x, mixed_delta(h), f.N);
+        counted(h);
+        CK(cudaGetLastError());
+    }
+    return MG_OK;
 }
 
 mg_status check_handle(const mg_handle *h, bool need_coeffs) {
@@ -1488,8 +1513,8 @@ PhaseK phase_k(const mg_phase &P) {
 }
 }  // namespace
 
-mg_status mg_assemble(const mg_grid *grid, const mg_phase phases[2], double dt, int lambda4_printed,
-                      const mg_state *s, const mg_assembly *out, void *stream) {
+mg_status mg_assemble_async(const mg_grid *grid, const mg_phase phases[2], double dt, int lambda4_printed,
+                            const mg_state *s, const mg_assembly *out, void *stream) {
     mg_status st = check_grid_geom(grid);
     if (st) return st;
     if (!phases || !s || !out) return fail(MG_ERR_INVALID_ARG, "phases, state and out must not be NULL");
@@ -1537,13 +1562,12 @@ mg_status mg_assemble(const mg_grid *grid, const mg_phase phases[2], double dt, 
     else if (grid->axisym) k_assemble<2, true><<<gr, kBlock, 0, cs>>>(A);
     else k_assemble<2, false><<<gr, kBlock, 0, cs>>>(A);
     CK(cudaGetLastError());
-    CK(cudaStreamSynchronize(cs));
     return MG_OK;
 }
 
-mg_status mg_correct(const mg_grid *grid, double dt, double sigma, const double *x, const double *C,
-                     const double *kappa, const double *const face_alpha[3], const double *const uf_star[3],
-                     double *const uf_out[3], double *p1, double *p2, void *stream) {
+mg_status mg_correct_async(const mg_grid *grid, double dt, double sigma, const double *x, const double *C,
+                           const double *kappa, const double *const face_alpha[3], const double *const uf_star[3],
+                           double *const uf_out[3], double *p1, double *p2, void *stream) {
     mg_status st = check_grid_geom(grid);
     if (st) return st;
     if (!face_alpha || !uf_star || !uf_out) return fail(MG_ERR_INVALID_ARG, "face array lists must not be NULL");
@@ -1584,7 +1608,6 @@ mg_status mg_correct(const mg_grid *grid, double dt, double sigma, const double 
     if (dim == 3) k_correct<3><<<gr, kBlock, 0, cs>>>(A);
     else k_correct<2><<<gr, kBlock, 0, cs>>>(A);
     CK(cudaGetLastError());
-    CK(cudaStreamSynchronize(cs));
     return MG_OK;
 }
 

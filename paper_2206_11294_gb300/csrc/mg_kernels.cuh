@@ -507,8 +507,9 @@ __global__ void __launch_bounds__(kBX * kBY) k_norm_partials(Level<double> L, do
 // the FP32 correction is zeroed, and the norm partials of Dinv r are formed.
 template <int DIM>
 __device__ __forceinline__ void residual64_to32_cell(const Level<double> &L, float2 *__restrict__ b32,
-                                                     float2 *__restrict__ bt32, float2 *__restrict__ e32, int i, int j,
-                                                     int k, double &zT2, double &zp2) {
+                                                     float2 *__restrict__ bt32, float2 *__restrict__ e32,
+                                                     double2 *__restrict__ r_out, double2 *__restrict__ r_out2, int i,
+                                                     int j, int k, double &zT2, double &zp2) {
     const long long c = cell_id(i, j, k, L.n0, L.n1);
     double sT, sp;
     offdiag<double, DIM>(L, L.x, i, j, k, c, sT, sp);
@@ -524,12 +525,17 @@ __device__ __forceinline__ void residual64_to32_cell(const Level<double> &L, flo
     b32[c] = make_float2((float)rT, (float)rp);
     bt32[c] = make_float2((float)zT, (float)zp);     // Dinv r for the FP32 sweeps
     e32[c] = make_float2(0.f, 0.f);
+    if (r_out) {                                     // the initial residual of the defect correction:
+        r_out[c] = make_double2(rT, rp);             // r0 over b (only this thread reads b[c], before this store),
+        r_out2[c] = make_double2(0.0, 0.0);          // and the correction starts at zero
+    }
 }
 
 // Block (bx, by, bz) of the norm grid.
 template <int DIM>
 __device__ __forceinline__ void residual64_to32_tile(const Level<double> &L, float2 *__restrict__ b32,
-                                                     float2 *__restrict__ bt32, float2 *__restrict__ e32, int bx,
+                                                     float2 *__restrict__ bt32, float2 *__restrict__ e32,
+                                                     double2 *__restrict__ r_out, double2 *__restrict__ r_out2, int bx,
                                                      int by, int bz, double &zT2, double &zp2) {
     const int k = DIM == 3 ? bz : 0;
 #pragma unroll
@@ -539,7 +545,7 @@ __device__ __forceinline__ void residual64_to32_tile(const Level<double> &L, flo
 #pragma unroll
         for (int e = 0; e < 2; e++) {
             const int i = bx * kNormCols + e * kBX + threadIdx.x;
-            if (i < L.n0) residual64_to32_cell<DIM>(L, b32, bt32, e32, i, j, k, zT2, zp2);
+            if (i < L.n0) residual64_to32_cell<DIM>(L, b32, bt32, e32, r_out, r_out2, i, j, k, zT2, zp2);
         }
     }
 }
@@ -547,9 +553,10 @@ __device__ __forceinline__ void residual64_to32_tile(const Level<double> &L, flo
 template <int DIM>
 __device__ __forceinline__ double2 residual64_to32_block(const Level<double> &L, float2 *__restrict__ b32,
                                                          float2 *__restrict__ bt32, float2 *__restrict__ e32,
-                                                         int bx, int by, int bz) {
+                                                         double2 *__restrict__ r_out, double2 *__restrict__ r_out2, int bx,
+                                                         int by, int bz) {
     double zT2 = 0.0, zp2 = 0.0;
-    residual64_to32_tile<DIM>(L, b32, bt32, e32, bx, by, bz, zT2, zp2);
+    residual64_to32_tile<DIM>(L, b32, bt32, e32, r_out, r_out2, bx, by, bz, zT2, zp2);
     block_sum2(zT2, zp2);
     return make_double2(zT2, zp2);
 }
@@ -557,19 +564,29 @@ __device__ __forceinline__ double2 residual64_to32_block(const Level<double> &L,
 template <int DIM, bool P>
 __global__ void __launch_bounds__(kBX * kBY) k_residual64_to32(Level<double> L, float2 *__restrict__ b32,
                                                              float2 *__restrict__ bt32, float2 *__restrict__ e32,
+                                                             double2 *__restrict__ r_out,
+                                                             double2 *__restrict__ r_out2,
                                                              double2 *__restrict__ partial,
                                                              unsigned int *__restrict__ ticket,
                                                              double *__restrict__ out) {
     double zT2 = 0.0, zp2 = 0.0;
     CMG_TILES(P, norm_gx(L.n0), norm_gy(L.n1), DIM == 3 ? L.n2 : 1,
-              (residual64_to32_tile<DIM>(L, b32, bt32, e32, bx, by, bz, zT2, zp2)));
+              (residual64_to32_tile<DIM>(L, b32, bt32, e32, r_out, r_out2, bx, by, bz, zT2, zp2)));
     block_sum2(zT2, zp2);
     const int blk = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
     if (threadIdx.x == 0 && threadIdx.y == 0) partial[blk] = make_double2(zT2, zp2);
     finish_norms(partial, gridDim.x * gridDim.y * gridDim.z, ticket, out);
 }
 
-// x64 += e32 (the refinement update)
+// x += delta: the solution from the initial guess and the accumulated correction
+__global__ void k_add_pairs(double2 *__restrict__ x, const double2 *__restrict__ delta, long long N) {
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
+        const double2 a = x[c], d = delta[c];
+        x[c] = make_double2(a.x + d.x, a.y + d.y);
+    }
+}
+
+// x64 += e32 (the refinement update; mixed solves pass the correction delta as x64)
 __global__ void k_add_correction(double2 *__restrict__ x, const float2 *__restrict__ e, long long N) {
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
         const float2 d = e[c];
