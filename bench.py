@@ -567,12 +567,16 @@ def run_timestep(args):
                              "frac": byts / (ms * 1e-3) / 1e9 / peak, "peak_source": peak_kind,
                              "algorithmic_bytes": byts, "avg_launch_us": ms * 1e3}
     cycles = [st["cycles"] for st in stats]
+    asm = roof(ASSEMBLE_BYTES_2D * N, t_asm)
+    # the assembly is bound by the FP64 pipe, not HBM (ncu: profiles/k_assemble_bubbles1024.md)
+    asm_alu = {"bound": "alu", "fp64_pipe_busy_elapsed_ncu": 0.836, "fp64_inst_per_cell_ncu": 150,
+               "source": "profiles/k_assemble_bubbles1024.md", "hbm": asm}
     return {"workload": "one time step, bubbles16_1024x1024 advected state: assembly + set-up + solve to 1e-10 + "
                         "velocity / phase-pressure update", "metric": "time steps/s", "cells": N,
             "precision": args.precision, "steps_per_s": 1e3 / total, "ms_per_step": total,
             "assemble_ms": t_asm, "solve_ms": total - t_asm - t_cor, "correct_ms": t_cor,
             "cycles_per_solve": cycles[0] if cycles else None, "tuning": tuning,
-            "assemble_roofline": roof(ASSEMBLE_BYTES_2D * N, t_asm),
+            "assemble_roofline": asm_alu,
             "correct_roofline": roof(CORRECT_BYTES_2D * N, t_cor),
             "l2": "flushed between steps", "clocks": clk, "data": "synthetic (seeded advected state, NASG water / air)"}
 
