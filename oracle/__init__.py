@@ -70,7 +70,7 @@ def configure(lib):
     lib.orc_apply_paper.restype = None
     lib.orc_dense_solve.argtypes = [gp, dp, pa3, pa3, dp, dp]
     lib.orc_dense_solve.restype = C.c_int
-    lib.orc_mg_solve.argtypes = [gp, dp, pa3, pa3, dp, dp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, dp]
+    lib.orc_mg_solve.argtypes = [gp, dp, pa3, pa3, dp, dp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, dp, C.c_int]
     lib.orc_mg_solve.restype = C.c_int
     lib.orc_rbgs_sweeps.argtypes = [gp, dp, pa3, pa3, dp, dp, C.c_int]
     lib.orc_rbgs_sweeps.restype = C.c_int
@@ -163,8 +163,11 @@ def dense_solve(g, lam, fa, fk, b) -> np.ndarray:
     return x
 
 
-def mg_solve(g, lam, fa, fk, b, x0, nu1=2, nu2=2, coarse_min=4, max_cycles=50, rtol=1e-10):
-    """Returns (x, cycles, history) where history[k] = per-field norms before cycle k."""
+CYCLES = {"V": 0, "W": 1, "F": 2}
+
+
+def mg_solve(g, lam, fa, fk, b, x0, nu1=2, nu2=2, coarse_min=4, max_cycles=50, rtol=1e-10, cycle="V"):
+    """Returns (x, cycles, history) where history[k] = per-field norms before cycle k.  cycle: V, W or F."""
     lib = _load()
     gs = _grid(g)
     lam, b = _c64(lam), _c64(b)
@@ -173,7 +176,7 @@ def mg_solve(g, lam, fa, fk, b, x0, nu1=2, nu2=2, coarse_min=4, max_cycles=50, r
     pk, kk = _faces(fk)
     hist = np.zeros(2 * (max_cycles + 1))
     rc = lib.orc_mg_solve(C.byref(gs), _dp(lam), pa, pk, _dp(b), _dp(x), int(nu1), int(nu2),
-                          int(coarse_min), int(max_cycles), float(rtol), _dp(hist))
+                          int(coarse_min), int(max_cycles), float(rtol), _dp(hist), CYCLES[cycle])
     if rc < 0:
         raise RuntimeError(f"oracle mg solve failed ({rc})")
     return x, rc, hist.reshape(-1, 2)[: rc + 1]

@@ -534,15 +534,26 @@ static int coarse_solve(level *L)
     return rc;
 }
 
-static int vcycle(level *Ls, int l, int nlev, int nu1, int nu2)
+/* One multigrid cycle from level l: pre-smoothing, restriction of the
+ * residual, the coarse-grid correction, prolongation, post-smoothing.
+ * type 0 (V): one coarse cycle; 1 (W): two W-cycles on the coarser level;
+ * 2 (F): an F-cycle then a V-cycle on the coarser level.  The second coarse
+ * cycle continues from the first one's coarse solution with the same
+ * restricted right-hand side; at the coarsest level the exact solve is done
+ * once (a second exact solve would give the same values). */
+static int mgcycle(level *Ls, int l, int nlev, int nu1, int nu2, int type)
 {
     level *L = &Ls[l];
     if (l == nlev - 1) return coarse_solve(L);
     for (int s = 0; s < nu1; s++) rbgs_sweep(L, NULL, NULL);
     level_residual(L);
     restrict_residual(L, &Ls[l + 1]);
-    int rc = vcycle(Ls, l + 1, nlev, nu1, nu2);
+    int rc = mgcycle(Ls, l + 1, nlev, nu1, nu2, type);
     if (rc) return rc;
+    if (type != 0 && l + 1 < nlev - 1) {
+        rc = mgcycle(Ls, l + 1, nlev, nu1, nu2, type == 1 ? 1 : 0);
+        if (rc) return rc;
+    }
     prolong_add(&Ls[l + 1], L);
     for (int s = 0; s < nu2; s++) rbgs_sweep(L, NULL, NULL);
     return 0;
@@ -590,7 +601,7 @@ int orc_num_levels(const orc_grid *g, int coarse_min)
 
 /*
  * Solve L(x) = b (Eqs. 27-34) by the defect-correction loop with one
- * V(nu1, nu2) cycle as the correction solve.
+ * V(nu1, nu2) cycle (or W, F: cycle_type 1, 2) as the correction solve.
  *   x       in: initial guess a~; out: result
  *   rtol    stop when both per-field norms fell by rtol (rtol <= 0: run
  *           exactly max_cycles cycles)
@@ -600,7 +611,7 @@ int orc_num_levels(const orc_grid *g, int coarse_min)
  */
 int orc_mg_solve(const orc_grid *g, const double *lam, double *const fa[3], double *const fk[3],
                  const double *b, double *x, int nu1, int nu2, int coarse_min, int max_cycles,
-                 double rtol, double *hist)
+                 double rtol, double *hist, int cycle_type)
 {
     int nlev = orc_num_levels(g, coarse_min);
     level *Ls = calloc(nlev, sizeof(level));
@@ -638,7 +649,7 @@ int orc_mg_solve(const orc_grid *g, const double *lam, double *const fa[3], doub
         /* step 3: L(da) ~= res by one V-cycle from da = 0 */
         memcpy(Ls[0].rhs, res, sizeof(double) * 2 * N);
         memset(Ls[0].u, 0, sizeof(double) * 2 * N);
-        rc = vcycle(Ls, 0, nlev, nu1, nu2);
+        rc = mgcycle(Ls, 0, nlev, nu1, nu2, cycle_type);
         if (rc) goto done;
         /* step 4: a += da */
         for (long i = 0; i < 2 * N; i++) x[i] += Ls[0].u[i];

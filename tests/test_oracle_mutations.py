@@ -109,3 +109,39 @@ def test_unmutated_oracle_passes_the_pins(orc):
 def test_mutant_fails_a_pin(orc, name):
     with mutant(orc, name):
         assert not _pins_pass(orc), name
+
+
+# Planted mistakes in the cycle variants, against the W/F pin (two coarse visits
+# per level contract faster than one).
+CYCLE_MUTATIONS = {
+    # the second coarse visit of W- and F-cycles left out: every cycle is a V-cycle
+    "no_second_visit": ("if (type != 0 && l + 1 < nlev - 1) {", "if (0 && l + 1 < nlev - 1) {"),
+    # the second visit restarts the coarse correction from zero, discarding the first
+    "second_visit_restarts": ("        rc = mgcycle(Ls, l + 1, nlev, nu1, nu2, type == 1 ? 1 : 0);",
+                              "        memset(Ls[l + 1].u, 0, sizeof(double) * 2 * Ls[l + 1].N);\n"
+                              "        rc = mgcycle(Ls, l + 1, nlev, nu1, nu2, type == 1 ? 1 : 0);"),
+}
+
+
+def _cycle_pins_pass(orc) -> bool:
+    p = I.stiff(I.bubble_2d, 32)
+    gd = p.grid.as_dict()
+    rate = {}
+    for c in "VW":
+        _, _, hist = orc.mg_solve(gd, p.lam, p.fa, p.fk, p.b, p.x0, max_cycles=6, rtol=0.0, cycle=c)
+        rate[c] = np.exp(np.log(hist[1:6] / hist[0:5]).mean(axis=0))
+    return bool(np.all(rate["W"] <= 0.8 * rate["V"]))
+
+
+def test_unmutated_oracle_passes_the_cycle_pin(orc):
+    assert _cycle_pins_pass(orc)
+
+
+@pytest.mark.parametrize("name", list(CYCLE_MUTATIONS))
+def test_cycle_mutant_fails_the_pin(orc, name):
+    MUTATIONS[name] = CYCLE_MUTATIONS[name]
+    try:
+        with mutant(orc, name):
+            assert not _cycle_pins_pass(orc), name
+    finally:
+        del MUTATIONS[name]

@@ -454,3 +454,41 @@ def test_single_cell_grid_and_1d_strip(orc):
     ref2 = np.linalg.solve(M2.toarray(), p2.b.reshape(-1) - aff2).reshape(-1, 2)
     x2, cyc2, _ = orc.mg_solve(g2.as_dict(), p2.lam, p2.fa, p2.fk, p2.b, p2.x0, max_cycles=5, rtol=1e-14)
     assert np.abs(x2 - ref2).max() <= 1e-12 * np.abs(ref2).max()
+
+
+# ----------------------------------------------------------------------------
+# W- and F-cycles (the cycle variants of the correction solve)
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("cycle", ["W", "F"])
+@pytest.mark.parametrize("name", list(GRIDS))
+def test_w_f_cycles_match_dense(orc, name, cycle):
+    """Converged W- and F-cycle solves equal the exact solution, like V."""
+    g = GRIDS[name]
+    p = I.random_coeff_problem(g, seed=7, dt=1e-5)
+    gd = g.as_dict()
+    xd = orc.dense_solve(gd, p.lam, p.fa, p.fk, p.b)
+    xm, cyc, hist = orc.mg_solve(gd, p.lam, p.fa, p.fk, p.b, p.x0, coarse_min=2, max_cycles=80, rtol=1e-14,
+                                 cycle=cycle)
+    assert rel_dev(xm, xd, p.x0) <= 1e-11
+
+
+def test_w_f_equal_v_on_two_levels(orc):
+    """With one coarse level (the exactly solved one) every cycle type does the
+    same work: the second coarse visit is not made."""
+    p = I.bubble_2d(8)
+    gd = p.grid.as_dict()
+    out = [orc.mg_solve(gd, p.lam, p.fa, p.fk, p.b, p.x0, max_cycles=2, rtol=0.0, cycle=c)[0] for c in "VWF"]
+    assert np.array_equal(out[0], out[1]) and np.array_equal(out[0], out[2])
+
+
+def test_w_f_contract_faster_than_v(orc):
+    """On the stiff bubble (coarse correction matters) two coarse visits per
+    level reduce the error per cycle well below one visit."""
+    p = I.stiff(I.bubble_2d, 32)
+    gd = p.grid.as_dict()
+    rate = {}
+    for c in "VWF":
+        _, _, hist = orc.mg_solve(gd, p.lam, p.fa, p.fk, p.b, p.x0, max_cycles=6, rtol=0.0, cycle=c)
+        rate[c] = np.exp(np.log(hist[1:6] / hist[0:5]).mean(axis=0))
+    for c in "WF":
+        assert np.all(rate[c] <= 0.8 * rate["V"]), (c, rate)
