@@ -172,7 +172,8 @@ def run_ours(args, rank, world):
     dev_in = []
     solvers = []
     for p in probs:
-        s = Solver(p.grid, precision=args.precision, rtol=1e-10, max_cycles=50, device=dev, stream=stream)
+        s = Solver(p.grid, precision=args.precision, rtol=1e-10, max_cycles=50, device=dev, stream=stream,
+                   cycle=args.cycle)
         dev_in.append(dict(lam=T(p.lam), fa=[T(f) for f in p.fa], fk=[T(f) for f in p.fk], b=T(p.b),
                            x0=T(p.x0), x=T(p.x0)))
         solvers.append(s)
@@ -344,7 +345,8 @@ def run_ours(args, rank, world):
         "config": {"workload": "bubbles16_1024x1024 + axi_512x1024, set-up + solve to 1e-10 per step",
                    "cells_per_step": sum(p.grid.N for p in probs), "cycles_per_solve": cycles,
                    "solves_per_s": solves * world / tmax, "precision": args.precision,
-                   "cycle": "V(2,2) red-black block GS, exact coarsest solve", "l2": "flushed between steps",
+                   "cycle": f"{args.cycle}(2,2) red-black block GS, exact coarsest solve",
+                   "l2": "flushed between steps",
                    "parallelism": f"replicas x{world}",
                    "tuning": tunings or "library defaults (--no-tune)"},
         "roofline": roofline,
@@ -681,6 +683,7 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=4.0)
     ap.add_argument("--serve-max", type=int, default=600)
     ap.add_argument("--serve-budget", type=int, default=40 << 30)
+    ap.add_argument("--cycle", default="V", choices=["V", "W", "F"], help="cycle of the correction solve")
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per launch of the dominant kernel from an ncu capture (profiles/)")
     args = ap.parse_args()

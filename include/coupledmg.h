@@ -83,7 +83,14 @@ typedef struct {
     int max_cycles;      /* FP64: V-cycles; MIXED: outer refinement steps */
     int coarse_min;      /* coarsen while every n_a is even and n_a/2 >= coarse_min (default 4) */
     int inner_cycles;    /* MIXED: FP32 V-cycles per outer step (default 1) */
+    int cycle;           /* MG_CYCLE_V (default), MG_CYCLE_W or MG_CYCLE_F: the correction solve's cycle.  W visits
+                            each coarser level twice (W, W), F twice (F, then V); the second visit continues from
+                            the first one's coarse solution; the exactly solved coarsest level is solved once.  W and
+                            F run without the V-cycle tail kernel (mg_tuning.tail_level is ignored); batches take V
+                            only. */
 } mg_options;
+
+enum { MG_CYCLE_V = 0, MG_CYCLE_W = 1, MG_CYCLE_F = 2 };
 
 typedef struct {
     int cycles;          /* V-cycles run (MIXED: total FP32 cycles) */
@@ -282,9 +289,12 @@ MG_API mg_status mg_batch_destroy(mg_batch *b);
  * velocity and phase-pressure update from its solution.  All arrays are
  * device pointers of the current device (host pointers are rejected with
  * MG_ERR_INVALID_ARG), cells and faces in the layouts above; [N][2] and
- * [N][4] arrays 16-byte aligned.  The work runs on `stream` (a cudaStream_t,
- * NULL = legacy default) and the call returns after it completed.  Inputs
- * are not checked for finiteness (mg_set_coeffs checks what it receives).
+ * [N][4] arrays 16-byte aligned.  Arguments are validated before anything is
+ * launched; the work is then enqueued on `stream` (a cudaStream_t, NULL =
+ * legacy default) and the call returns without waiting for it: later work on
+ * the same stream (mg_set_coeffs, mg_solve on a handle created with that
+ * stream) sees its results.  Inputs are not checked for finiteness
+ * (mg_set_coeffs checks what it receives).
  * ------------------------------------------------------------------------- */
 typedef struct {
     double Gamma, Pi, b, q;   /* NASG parameters of Eq. 9 (Table 1); ideal gas: Gamma = gamma, Pi = b = q = 0 */
@@ -325,20 +335,21 @@ typedef struct {              /* what mg_set_coeffs and mg_solve take */
  *   faces: 1/rho_f with rho_f the mean of the two cells' rho, k_f = C_f k1 +
  *     (1 - C_f) k2 with C_f the mean of their C; a boundary face takes its cell's.
  * A phase with C_i = 0 in a cell contributes nothing there.  dt > 0. */
-MG_API mg_status mg_assemble(const mg_grid *grid, const mg_phase phases[2], double dt, int lambda4_printed,
-                             const mg_state *state, const mg_assembly *out, void *stream);
+MG_API mg_status mg_assemble_async(const mg_grid *grid, const mg_phase phases[2], double dt, int lambda4_printed,
+                                   const mg_state *state, const mg_assembly *out, void *stream);
 
 /* Update after the solve.  x [N][2] is the solution (T, p) of mg_solve;
- * face_alpha the faces' 1/rho (from mg_assemble); uf_star the u* of the state.
+ * face_alpha the faces' 1/rho (from mg_assemble_async); uf_star the u* of the state.
  *   uf_out[a] = uf_star[a] - dt face_alpha[a] (grad p)_f  (Eq. unp1 at the
  *     faces), with (p_R - p_L)/h inside, 2 (g - p)/h towards a Dirichlet value
  *     g of grid->bc_p, and 0 at walls and the axis - the face gradients of the
  *     solve's operator, so div uf_out = div u* - dt div((1/rho) grad p);
  *   p1 = p + (1 - C) sigma kappa, p2 = p - C sigma kappa (Eqs. 37-38).
  * uf_out may equal uf_star (in place). */
-MG_API mg_status mg_correct(const mg_grid *grid, double dt, double sigma, const double *x, const double *C,
-                            const double *kappa, const double *const face_alpha[3], const double *const uf_star[3],
-                            double *const uf_out[3], double *p1, double *p2, void *stream);
+MG_API mg_status mg_correct_async(const mg_grid *grid, double dt, double sigma, const double *x, const double *C,
+                                  const double *kappa, const double *const face_alpha[3],
+                                  const double *const uf_star[3], double *const uf_out[3], double *p1, double *p2,
+                                  void *stream);
 
 /* Allocation-free stopping norms (the paper has no counterpart: this is a
  * library service).  For callers that cannot allocate device memory - their

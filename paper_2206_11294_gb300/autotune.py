@@ -21,7 +21,7 @@ from typing import Dict, Optional
 
 
 def table_key(device_name: str, grid, precision: str, nu1: int = 2, nu2: int = 2, coarse_min: int = 4,
-              inner_cycles: int = 1) -> str:
+              inner_cycles: int = 1, cycle: str = "V") -> str:
     """Key of a hierarchy.  `grid` is an inputs.Grid, a dict with its keys, or a binding.MgGrid."""
     if hasattr(grid, "_fields_"):          # ctypes MgGrid
         dim, n = int(grid.dim), tuple(int(v) for v in grid.n)
@@ -31,7 +31,7 @@ def table_key(device_name: str, grid, precision: str, nu1: int = 2, nu2: int = 2
         dim, n = int(grid.dim), tuple(int(v) for v in grid.n)
     shape = "x".join(str(v) for v in n[:dim])
     inner = f"/i{inner_cycles}" if precision == "mixed" else ""
-    return f"{device_name}|{dim}d|{shape}|{precision}{inner}|V({nu1},{nu2})|cmin{coarse_min}"
+    return f"{device_name}|{dim}d|{shape}|{precision}{inner}|{cycle}({nu1},{nu2})|cmin{coarse_min}"
 
 
 class TuningTable:
@@ -77,7 +77,7 @@ class TuningTable:
         o = solver.options
         prec = "mixed" if int(o.precision) == 1 else "fp64"
         return table_key(torch.cuda.get_device_name(solver.device), solver.grid, prec, int(o.nu1), int(o.nu2),
-                         int(o.coarse_min), int(o.inner_cycles))
+                         int(o.coarse_min), int(o.inner_cycles), "VWF"[int(o.cycle)])
 
     def tune(self, solver, reps: int = 10) -> dict:
         """Applies the stored choices for this solver's key, or measures them

@@ -32,7 +32,7 @@ EXPORTS = ["mg_default_options", "mg_workspace_size", "mg_create", "mg_set_coeff
            "mg_last_error", "mg_set_timing", "mg_counters", "mg_residual_norms_noalloc",
            "mg_batch_create", "mg_batch_solve", "mg_batch_counters", "mg_batch_destroy", "mg_set_stream",
            "mg_batch_set_coeffs", "mg_get_tuning", "mg_set_tuning", "mg_autotune", "mg_batch_get_tuning",
-           "mg_batch_set_tuning", "mg_batch_autotune", "mg_assemble", "mg_correct"]
+           "mg_batch_set_tuning", "mg_batch_autotune", "mg_assemble_async", "mg_correct_async"]
 
 MG_MAX_LEVELS = 32
 MG_SWEEP_COLOUR, MG_SWEEP_FUSED, MG_SWEEP_ASYNC, MG_SWEEP_COLOUR2 = 1, 2, 3, 4
@@ -56,7 +56,7 @@ class MgGrid(C.Structure):
 
 class MgOptions(C.Structure):
     _fields_ = [("nu1", C.c_int), ("nu2", C.c_int), ("precision", C.c_int), ("rtol", C.c_double),
-                ("max_cycles", C.c_int), ("coarse_min", C.c_int), ("inner_cycles", C.c_int)]
+                ("max_cycles", C.c_int), ("coarse_min", C.c_int), ("inner_cycles", C.c_int), ("cycle", C.c_int)]
 
 
 class MgStats(C.Structure):
@@ -175,9 +175,9 @@ def load(path: str = LIB_PATH):
             "mg_batch_get_tuning": ([P, C.POINTER(MgBatchTuning)], C.c_int),
             "mg_batch_set_tuning": ([P, C.POINTER(MgBatchTuning)], C.c_int),
             "mg_batch_autotune": ([P, C.c_int, C.POINTER(MgBatchTuning), dp], C.c_int),
-            "mg_assemble": ([C.POINTER(MgGrid), MgPhase * 2, C.c_double, C.c_int, C.POINTER(MgState),
-                             C.POINTER(MgAssembly), P], C.c_int),
-            "mg_correct": ([C.POINTER(MgGrid), C.c_double, C.c_double, P, P, P, pa3, pa3, pa3, P, P, P], C.c_int),
+            "mg_assemble_async": ([C.POINTER(MgGrid), MgPhase * 2, C.c_double, C.c_int, C.POINTER(MgState),
+                                   C.POINTER(MgAssembly), P], C.c_int),
+            "mg_correct_async": ([C.POINTER(MgGrid), C.c_double, C.c_double, P, P, P, pa3, pa3, pa3, P, P, P], C.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -217,13 +217,17 @@ def make_grid(g) -> MgGrid:
     return s
 
 
+CYCLES = {"V": 0, "W": 1, "F": 2}
+
+
 def make_options(precision="fp64", rtol=1e-10, max_cycles=50, nu1=2, nu2=2, coarse_min=4,
-                 inner_cycles=1) -> MgOptions:
+                 inner_cycles=1, cycle="V") -> MgOptions:
     o = MgOptions()
     check(load().mg_default_options(C.byref(o)))
     o.precision = MG_MIXED if precision in ("mixed", MG_MIXED) else MG_FP64
     o.rtol, o.max_cycles, o.nu1, o.nu2 = float(rtol), int(max_cycles), int(nu1), int(nu2)
     o.coarse_min, o.inner_cycles = int(coarse_min), int(inner_cycles)
+    o.cycle = CYCLES[cycle] if isinstance(cycle, str) else int(cycle)
     return o
 
 
@@ -279,9 +283,10 @@ def make_phase(ph) -> MgPhase:
 
 def assemble(grid, phases, dt: float, C_, m1, m2, E, mom: Sequence, uf: Sequence, out: dict,
              lambda4_printed: bool = False, stream=None) -> None:
-    """mg_assemble: every array a contiguous float64 CUDA tensor.  out holds
+    """mg_assemble_async: every array a contiguous float64 CUDA tensor.  out holds
     "lam" (N x 4), "b" (N x 2), optionally "x0" (N x 2), and per-axis lists
-    "fa", "fk"; they are written in place."""
+    "fa", "fk"; they are written in place, in the order of `stream` (the call
+    does not wait for the work)."""
     import torch
     g = make_grid(grid)
     keep = []
@@ -304,13 +309,14 @@ def assemble(grid, phases, dt: float, C_, m1, m2, E, mom: Sequence, uf: Sequence
     ph = (MgPhase * 2)(make_phase(phases[0]), make_phase(phases[1]))
     if stream is None:
         stream = torch.cuda.current_stream()
-    check(load().mg_assemble(C.byref(g), ph, float(dt), int(bool(lambda4_printed)), C.byref(st), C.byref(res),
+    check(load().mg_assemble_async(C.byref(g), ph, float(dt), int(bool(lambda4_printed)), C.byref(st), C.byref(res),
                              C.c_void_p(stream.cuda_stream)))
 
 
 def correct(grid, dt: float, sigma: float, x, C_, kappa, fa: Sequence, uf_star: Sequence, uf_out: Sequence, p1, p2,
             stream=None) -> None:
-    """mg_correct: every array a contiguous float64 CUDA tensor; uf_out, p1, p2 are written."""
+    """mg_correct_async: every array a contiguous float64 CUDA tensor; uf_out, p1, p2 are written in the order of
+    `stream` (the call does not wait for the work)."""
     import torch
     g = make_grid(grid)
     pa, pu, po = (C.c_void_p * 3)(), (C.c_void_p * 3)(), (C.c_void_p * 3)()
@@ -320,7 +326,7 @@ def correct(grid, dt: float, sigma: float, x, C_, kappa, fa: Sequence, uf_star: 
         po[a] = _ptr(uf_out[a], True)[0]
     if stream is None:
         stream = torch.cuda.current_stream()
-    check(load().mg_correct(C.byref(g), float(dt), float(sigma), _ptr(x, True)[0], _ptr(C_, True)[0],
+    check(load().mg_correct_async(C.byref(g), float(dt), float(sigma), _ptr(x, True)[0], _ptr(C_, True)[0],
                             _ptr(kappa, True)[0], pa, pu, po, _ptr(p1, True)[0], _ptr(p2, True)[0],
                             C.c_void_p(stream.cuda_stream)))
 
@@ -329,12 +335,13 @@ class Solver:
     """One mg_handle: a grid, its device hierarchy and a stream."""
 
     def __init__(self, grid, precision="fp64", rtol=1e-10, max_cycles=50, nu1=2, nu2=2, coarse_min=4,
-                 inner_cycles=1, device: Optional[int] = None, stream=None, torch_workspace: bool = True):
+                 inner_cycles=1, device: Optional[int] = None, stream=None, torch_workspace: bool = True,
+                 cycle="V"):
         import torch
         lib = load()
         self._lib = lib
         self.grid = make_grid(grid)
-        self.options = make_options(precision, rtol, max_cycles, nu1, nu2, coarse_min, inner_cycles)
+        self.options = make_options(precision, rtol, max_cycles, nu1, nu2, coarse_min, inner_cycles, cycle)
         dev = torch.cuda.current_device() if device is None else int(device)
         self.device = dev
         check(lib.mg_set_device(dev))

@@ -687,7 +687,7 @@ void b_step(mg_batch *b, cudaStream_t s) {
 
 bool same_options(const mg_options &a, const mg_options &c) {
     return a.nu1 == c.nu1 && a.nu2 == c.nu2 && a.precision == c.precision && a.rtol == c.rtol &&
-           a.max_cycles == c.max_cycles && a.inner_cycles == c.inner_cycles;
+           a.max_cycles == c.max_cycles && a.inner_cycles == c.inner_cycles && a.cycle == c.cycle;
 }
 
 void add_blocks(std::vector<int2> &t, int level_index, long long blocks) {
@@ -710,6 +710,7 @@ mg_status mg_batch_create(int count, mg_handle *const *handles, mg_batch **out) 
                         "mg_batch_create: handles must share dim, options (nu1, nu2, precision, rtol, "
                         "max_cycles, inner_cycles), stream and device");
     }
+    if (handles[0]->opt.cycle != MG_CYCLE_V) return fail(MG_ERR_INVALID_ARG, "mg_batch_create: batches run V-cycles");
     mg_batch *b = new (std::nothrow) mg_batch();
     if (!b) return fail(MG_ERR_OOM, "host allocation failed");
     b->count = count;

@@ -179,6 +179,8 @@ mg_status check_grid(const mg_grid *g, const mg_options *o) {
     if (o->max_cycles < 0 || o->coarse_min < 1 || o->inner_cycles < 1 || o->inner_cycles > 64)
         return fail(MG_ERR_INVALID_ARG, "max_cycles >= 0, coarse_min >= 1, inner_cycles in 1..64");
     if (!std::isfinite(o->rtol)) return fail(MG_ERR_INVALID_ARG, "rtol must be finite");
+    if (o->cycle != MG_CYCLE_V && o->cycle != MG_CYCLE_W && o->cycle != MG_CYCLE_F)
+        return fail(MG_ERR_INVALID_ARG, "cycle must be MG_CYCLE_V, MG_CYCLE_W or MG_CYCLE_F");
     int n[3] = {g->n[0], g->n[1], g->n[2]}, lev = 1;
     while (can_coarsen(n, g->dim, o->coarse_min) && lev < kMaxLevels) {
         for (int a = 0; a < g->dim; a++) n[a] /= 2;
@@ -621,9 +623,16 @@ void enqueue_tail(const mg_handle *h, cudaStream_t s) {
 }
 
 template <typename R, int DIM>
-void enqueue_vcycle(const mg_handle *h, cudaStream_t s, int l) {
+void enqueue_vcycle(const mg_handle *h, cudaStream_t s, int l, int type);
+
+template <typename R, int DIM>
+// One cycle from level l: V, or (type) W / F, whose coarse-grid correction
+// visits level l + 1 twice (W then W, F then V), the second visit continuing
+// from the first one's coarse solution, except at the exactly solved coarsest
+// level.  The tail kernel runs V-cycles only, so W and F cycles never use it.
+void enqueue_vcycle(const mg_handle *h, cudaStream_t s, int l, int type) {
     const LevelBuf &lb = h->L[l];
-    if (l == h->tail_lev) {
+    if (l == h->tail_lev && h->opt.cycle == MG_CYCLE_V) {
         // the coarsest inverse is computed on the aux stream after each set-up
         cudaStreamWaitEvent(s, h->ev_inv, cudaEventWaitExternal);
         enqueue_tail<R, DIM>(h, s);
@@ -667,7 +676,9 @@ void enqueue_vcycle(const mg_handle *h, cudaStream_t s, int l) {
             k_residual_restrict<R, DIM, false, false><<<rg, kBlock, 0, s>>>(view<R>(lb), view<R>(cb));
     }
     counted(h);
-    enqueue_vcycle<R, DIM>(h, s, l + 1);
+    enqueue_vcycle<R, DIM>(h, s, l + 1, type);
+    if (type != MG_CYCLE_V && l + 1 < h->nlev - 1)
+        enqueue_vcycle<R, DIM>(h, s, l + 1, type == MG_CYCLE_W ? MG_CYCLE_W : MG_CYCLE_V);
     const dim3 pg = cell_grid(lb, DIM, lb.n[0]);
     if (h->persistent)
         k_prolong_add<R, DIM, true><<<wave((const void *)k_prolong_add<R, DIM, true>, tiles_of(pg)), kBlock, 0, s>>>(
@@ -751,7 +762,7 @@ void warm_waves() {
 // FP64: one V-cycle, then the stopping norm, copied to pinned host memory.
 template <int DIM>
 void enqueue_cycle64(const mg_handle *h, cudaStream_t s) {
-    enqueue_vcycle<double, DIM>(h, s, 0);
+    enqueue_vcycle<double, DIM>(h, s, 0, h->opt.cycle);
     enqueue_norm<DIM>(h, s, h->opt.nu2 > 0);
     cudaMemcpyAsync(h->norms_h, h->norms_d, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
 }
@@ -759,7 +770,7 @@ void enqueue_cycle64(const mg_handle *h, cudaStream_t s) {
 // Mixed: FP32 V-cycles on the correction, FP64 update, FP64 residual + norm.
 template <int DIM>
 void enqueue_step32(const mg_handle *h, cudaStream_t s) {
-    for (int q = 0; q < h->opt.inner_cycles; q++) enqueue_vcycle<float, DIM>(h, s, 0);
+    for (int q = 0; q < h->opt.inner_cycles; q++) enqueue_vcycle<float, DIM>(h, s, 0, h->opt.cycle);
     const LevelBuf &f = h->L[0];
     k_add_correction<<<lin_blocks(f.N), 256, 0, s>>>(mixed_delta(h), f.x32, f.N);
     counted(h);
@@ -1263,7 +1274,7 @@ mg_status autotune_impl(mg_handle *h, int reps, double *vcycle_ms) {
     // the cluster tail: none, or each allowed first level and cluster size
     std::vector<std::pair<int, int>> cand{{h->nlev, kTailCtas}};
     const bool wide = tail_ctas_allowed<R, DIM>(16);
-    for (int l = 1; l < h->nlev; l++) {
+    for (int l = 1; l < h->nlev && h->opt.cycle == MG_CYCLE_V; l++) {     // the tail runs V-cycles only
         if (tail_level_ok(h, l, 1)) cand.push_back({l, 1});
         if (tail_level_ok(h, l, kTailCtas)) cand.push_back({l, kTailCtas});
         if (wide && tail_level_ok(h, l, 16)) cand.push_back({l, 16});
@@ -1277,7 +1288,8 @@ mg_status autotune_impl(mg_handle *h, int reps, double *vcycle_ms) {
             h->tail_ctas = c.second;
             h->persistent = persist;
             double ms = 0.0;
-            st = time_graph(h, 4 * reps + 1, &ms, [&](cudaStream_t s) { enqueue_vcycle<R, DIM>(h, s, 0); });
+            st = time_graph(h, 4 * reps + 1, &ms,
+                            [&](cudaStream_t s) { enqueue_vcycle<R, DIM>(h, s, 0, h->opt.cycle); });
             if (st) return st;
             if (ms < best) { best = ms; pick = c; pick_p = persist; }
         }
@@ -1314,6 +1326,7 @@ mg_status mg_default_options(mg_options *o) {
     o->max_cycles = 50;
     o->coarse_min = 4;
     o->inner_cycles = 1;
+    o->cycle = MG_CYCLE_V;
     return MG_OK;
 }
 

@@ -41,6 +41,14 @@ def test_default_options(lib):
     assert lib.mg_default_options(C.byref(o)) == 0
     assert (o.nu1, o.nu2, o.precision, o.max_cycles, o.coarse_min, o.inner_cycles) == (2, 2, 0, 50, 4, 1)
     assert o.rtol == 1e-10
+    assert o.cycle == B.CYCLES["V"] == 0 and B.CYCLES == {"V": 0, "W": 1, "F": 2}
+
+
+def test_cycle_option_validated(lib):
+    st, _ = _size(lib, _grid(n=(64, 64, 1)), cycle="W")
+    assert st == 0
+    st, _ = _size(lib, _grid(n=(64, 64, 1)), cycle=3)
+    assert st != 0
 
 
 def _grid(**kw):

@@ -145,6 +145,47 @@ def test_converged_fp64_same_cycles_as_oracle(torch_cuda, orc, name):
     s.close()
 
 
+@pytest.mark.parametrize("cycle", ["W", "F"])
+@pytest.mark.parametrize("name", ["literal_2d_ragged_walls", "stiff_axi_axis", "literal_3d_wall_dirichlet",
+                                  "stiff_3d_walls_odd"])
+def test_w_f_cycles_vs_oracle(torch_cuda, orc, name, cycle):
+    """W- and F-cycles: fixed cycles against the oracle's, and converged solves
+    with the oracle's cycle count; mixed precision converges to the oracle's
+    solution."""
+    p, tol = CASES[name]
+    g = p.grid.as_dict()
+    s = _solver(p, rtol=0.0, max_cycles=2, cycle=cycle)
+    x = p.x0.copy()
+    st = s.solve(p.b, x)
+    ref, cyc, _ = orc.mg_solve(g, p.lam, p.fa, p.fk, p.b, p.x0, max_cycles=2, rtol=0.0, cycle=cycle)
+    assert st["cycles"] == 2 == cyc
+    assert rel_dev(x, ref, p.x0) <= tol
+    s.close()
+    s = _solver(p, rtol=1e-10, max_cycles=60, cycle=cycle)
+    x = p.x0.copy()
+    st = s.solve(p.b, x)
+    ref, cyc, _ = orc.mg_solve(g, p.lam, p.fa, p.fk, p.b, p.x0, max_cycles=60, rtol=1e-10, cycle=cycle)
+    assert st["cycles"] == cyc
+    assert rel_dev(x, ref, p.x0) <= tol
+    s.close()
+    s = _solver(p, rtol=1e-10, max_cycles=60, cycle=cycle, precision="mixed")
+    xm = p.x0.copy()
+    st = s.solve(p.b, xm)
+    assert st["status"] == "MG_OK"
+    assert rel_dev(xm, ref, p.x0) <= 1e-8
+    s.close()
+
+
+def test_w_f_cycles_refused_by_batches(torch_cuda):
+    from paper_2206_11294_gb300.binding import Batch, MgError, MG_ERR_INVALID_ARG
+    p, _ = CASES["literal_2d_ragged_walls"]
+    s = _solver(p, cycle="W")
+    with pytest.raises(MgError) as e:
+        Batch([s])
+    assert e.value.status == MG_ERR_INVALID_ARG and "V-cycles" in str(e.value)
+    s.close()
+
+
 SHAPE_CASES = ["literal_2d_ragged_walls", "stiff_axi_axis", "literal_3d_wall_dirichlet", "stiff_3d_walls_odd"]
 
 
