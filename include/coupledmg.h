@@ -327,15 +327,18 @@ typedef struct {              /* what mg_set_coeffs and mg_solve take */
  *   lambda_1 = -(m1 cp1 + m2 cp2) / dt, lambda_2 = beta T / dt,
  *   lambda_3 = -bracket / dt^2 with bracket the average of
  *     gamma_i / (rho_i c_i^2) - beta_i^2 T / (rho_i cp_i), gamma_i = cp_i / cv_i,
- *   lambda_4 = average of beta_i / (rho_i cp_i), divided by dt unless
- *     lambda4_printed != 0 (Eq. 32 as printed lacks the 1/dt that dividing
- *     Eq. 19 by dt gives),
+ *   lambda_4 = average of beta_i / (rho_i cp_i), divided by dt unless flags
+ *     has MG_ASSEMBLE_LAMBDA4_PRINTED (Eq. 32 as printed lacks the 1/dt that
+ *     dividing Eq. 19 by dt gives),
  *   lambda_T = lambda_1 T + lambda_2 p, lambda_p = lambda_3 p + div(u*) / dt,
  *     div the finite-volume divergence (r_f / r_i on axisymmetric r-faces);
  *   faces: 1/rho_f with rho_f the mean of the two cells' rho, k_f = C_f k1 +
- *     (1 - C_f) k2 with C_f the mean of their C; a boundary face takes its cell's.
+ *     (1 - C_f) k2 with C_f the mean of their C, or with MG_ASSEMBLE_HARMONIC_K
+ *     the series mean 2 k_L k_R / (k_L + k_R) of the cells' k = C k1 + (1 - C) k2
+ *     (conduction through the two half cells); a boundary face takes its cell's.
  * A phase with C_i = 0 in a cell contributes nothing there.  dt > 0. */
-MG_API mg_status mg_assemble_async(const mg_grid *grid, const mg_phase phases[2], double dt, int lambda4_printed,
+enum { MG_ASSEMBLE_LAMBDA4_PRINTED = 1, MG_ASSEMBLE_HARMONIC_K = 2 };
+MG_API mg_status mg_assemble_async(const mg_grid *grid, const mg_phase phases[2], double dt, int flags,
                                    const mg_state *state, const mg_assembly *out, void *stream);
 
 /* Update after the solve.  x [N][2] is the solution (T, p) of mg_solve;

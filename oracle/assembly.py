@@ -27,7 +27,9 @@ Readings where the paper is silent (each listed in the design doc):
   Eq. 19 by dt gives); ``lambda4="printed"`` gives the printed form;
 - faces: 1/rho_f with rho_f the mean of the two cells' mixture densities, k_f =
   C_f k_1 + (1 - C_f) k_2 with C_f the mean of the two cells' C; a boundary face
-  takes its cell's values;
+  takes its cell's values; ``face_k="harmonic"`` instead takes the series mean
+  2 k_L k_R / (k_L + k_R) of the cells' mixture conductivities k = C k_1 +
+  (1 - C) k_2 (heat crossing two half cells);
 - div u* and grad p are the finite-volume differences of the solve's operator
   (axisymmetric: r_f / r_i weights on the r-faces), so that the divergence of
   the corrected velocity is div u* - dt times the operator's p-Laplacian.
@@ -132,8 +134,18 @@ def _neighbour_mean(v: np.ndarray, a: int) -> np.ndarray:
     return f
 
 
+def _harmonic_faces(v: np.ndarray, a: int) -> np.ndarray:
+    """Face values 2 v_L v_R / (v_L + v_R) along axis a; the cell's own at the boundary."""
+    f = _neighbour_mean(v, a)              # boundary faces: the cell's value
+    lo, hi = _face_slices(a)
+    inner = [slice(None)] * 3
+    inner[2 - a] = slice(1, -1)
+    f[tuple(inner)] = 2.0 * v[lo] * v[hi] / (v[lo] + v[hi])
+    return f
+
+
 def assemble(grid, ph1, ph2, dt: float, C, m1, m2, E, mom: Sequence[np.ndarray], uf: Sequence[np.ndarray],
-             lambda4: str = "restored") -> Dict[str, np.ndarray]:
+             lambda4: str = "restored", face_k: str = "arithmetic") -> Dict[str, np.ndarray]:
     """The inputs of the solve from the advected state.  Cell arrays shaped
     (n2, n1, n0), face arrays grid.face_shape(a).  Returns lam (N x 4), b
     (N x 2), x0 (N x 2), fa / fk (per axis), and p, T, div."""
@@ -166,8 +178,11 @@ def assemble(grid, ph1, ph2, dt: float, C, m1, m2, E, mom: Sequence[np.ndarray],
     fk: List[np.ndarray] = []
     for a in range(grid.dim):
         fa.append(1.0 / _neighbour_mean(rho, a))
-        Cf = _neighbour_mean(C, a)
-        fk.append(Cf * ph1["k"] + (1.0 - Cf) * ph2["k"])
+        if face_k == "harmonic":
+            fk.append(_harmonic_faces(C * ph1["k"] + (1.0 - C) * ph2["k"], a))
+        else:
+            Cf = _neighbour_mean(C, a)
+            fk.append(Cf * ph1["k"] + (1.0 - Cf) * ph2["k"])
     flat = lambda v: np.ascontiguousarray(v, dtype=np.float64).reshape(-1)
     lam = np.stack([flat(l1), flat(l2), flat(l3), flat(l4)], axis=1)
     return dict(lam=lam, b=np.stack([flat(lT), flat(lp)], axis=1), x0=np.stack([flat(T), flat(p)], axis=1),

@@ -281,8 +281,11 @@ def make_phase(ph) -> MgPhase:
     return MgPhase(*(float(get(key)) for key in ("Gamma", "Pi", "b", "q", "cp", "cv", "k")))
 
 
+MG_ASSEMBLE_LAMBDA4_PRINTED, MG_ASSEMBLE_HARMONIC_K = 1, 2
+
+
 def assemble(grid, phases, dt: float, C_, m1, m2, E, mom: Sequence, uf: Sequence, out: dict,
-             lambda4_printed: bool = False, stream=None) -> None:
+             lambda4_printed: bool = False, harmonic_k: bool = False, stream=None) -> None:
     """mg_assemble_async: every array a contiguous float64 CUDA tensor.  out holds
     "lam" (N x 4), "b" (N x 2), optionally "x0" (N x 2), and per-axis lists
     "fa", "fk"; they are written in place, in the order of `stream` (the call
@@ -309,7 +312,8 @@ def assemble(grid, phases, dt: float, C_, m1, m2, E, mom: Sequence, uf: Sequence
     ph = (MgPhase * 2)(make_phase(phases[0]), make_phase(phases[1]))
     if stream is None:
         stream = torch.cuda.current_stream()
-    check(load().mg_assemble_async(C.byref(g), ph, float(dt), int(bool(lambda4_printed)), C.byref(st), C.byref(res),
+    flags = (MG_ASSEMBLE_LAMBDA4_PRINTED if lambda4_printed else 0) | (MG_ASSEMBLE_HARMONIC_K if harmonic_k else 0)
+    check(load().mg_assemble_async(C.byref(g), ph, float(dt), flags, C.byref(st), C.byref(res),
                              C.c_void_p(stream.cuda_stream)))
 
 

@@ -37,6 +37,7 @@ struct AssembleArgs {
     int axisym;
     double r0, h, inv_h;
     double inv_dt, inv_dt2, l4_scale;   // l4_scale: 1/dt (restored lambda_4) or 1 (as printed)
+    int harmonic_k;                     // face k: 2 k_L k_R / (k_L + k_R) of the cells' mixture k, else C_f-weighted
     PhaseK ph[2];
     const double *C, *m1, *m2, *E;
     const double *mom[3];
@@ -133,19 +134,22 @@ __global__ void __launch_bounds__(256) k_assemble(const __grid_constant__ Assemb
         for (int sd = 0; sd < 2; sd++) {
             const int fpos = pos[a] + sd;
             if (sd == 1 && fpos != A.n[a]) continue;
-            double rf, Cf;
-            if (fpos == 0 || fpos == A.n[a]) {
-                rf = rho;
-                Cf = C;
+            const bool edge = fpos == 0 || fpos == A.n[a];
+            const long long cn = edge ? c : c - (a == 0 ? 1LL : a == 1 ? (long long)n0 : (long long)n0 * n1);
+            const double Cn = edge ? C : A.C[cn];
+            const double rf = edge ? rho : 0.5 * (rho + (A.m1[cn] + A.m2[cn]));
+            double kf;
+            if (A.harmonic_k) {                     // uniform over the launch
+                const double kc = C * P1.k + C2 * P2.k, kn = Cn * P1.k + (1.0 - Cn) * P2.k;
+                kf = edge ? kc : 2.0 * kn * kc / (kn + kc);      // series conduction through the two half cells
             } else {
-                const long long cn = c - (a == 0 ? 1LL : a == 1 ? (long long)n0 : (long long)n0 * n1);
-                rf = 0.5 * (rho + (A.m1[cn] + A.m2[cn]));
-                Cf = 0.5 * (C + A.C[cn]);
+                const double Cf = edge ? C : 0.5 * (C + Cn);
+                kf = Cf * P1.k + (1.0 - Cf) * P2.k;
             }
             const long long f = face_index(A.n, a, pos[0] + (a == 0 ? sd : 0), pos[1] + (a == 1 ? sd : 0),
                                            pos[2] + (a == 2 ? sd : 0));
             A.fa[a][f] = 1.0 / rf;
-            A.fk[a][f] = Cf * P1.k + (1.0 - Cf) * P2.k;
+            A.fk[a][f] = kf;
         }
     }
 }

@@ -1526,12 +1526,14 @@ PhaseK phase_k(const mg_phase &P) {
 }
 }  // namespace
 
-mg_status mg_assemble_async(const mg_grid *grid, const mg_phase phases[2], double dt, int lambda4_printed,
+mg_status mg_assemble_async(const mg_grid *grid, const mg_phase phases[2], double dt, int flags,
                             const mg_state *s, const mg_assembly *out, void *stream) {
     mg_status st = check_grid_geom(grid);
     if (st) return st;
     if (!phases || !s || !out) return fail(MG_ERR_INVALID_ARG, "phases, state and out must not be NULL");
     if (!(dt > 0.0) || !std::isfinite(dt)) return fail(MG_ERR_INVALID_ARG, "dt must be positive and finite");
+    if (flags & ~(MG_ASSEMBLE_LAMBDA4_PRINTED | MG_ASSEMBLE_HARMONIC_K))
+        return fail(MG_ERR_INVALID_ARG, "unknown assembly flags");
     for (int q = 0; q < 2; q++)
         if ((st = check_phase(phases[q]))) return st;
     const int dim = grid->dim;
@@ -1552,7 +1554,8 @@ mg_status mg_assemble_async(const mg_grid *grid, const mg_phase phases[2], doubl
     A.inv_h = 1.0 / grid->h;
     A.inv_dt = 1.0 / dt;
     A.inv_dt2 = 1.0 / (dt * dt);
-    A.l4_scale = lambda4_printed ? 1.0 : 1.0 / dt;
+    A.l4_scale = (flags & MG_ASSEMBLE_LAMBDA4_PRINTED) ? 1.0 : 1.0 / dt;
+    A.harmonic_k = (flags & MG_ASSEMBLE_HARMONIC_K) ? 1 : 0;
     A.ph[0] = phase_k(phases[0]);
     A.ph[1] = phase_k(phases[1]);
     A.C = s->C;

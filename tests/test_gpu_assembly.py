@@ -61,7 +61,7 @@ def _dev(torch, s):
                 kappa=T(s.kappa))
 
 
-def _gpu_assemble(torch, s, lambda4_printed=False, with_x0=True):
+def _gpu_assemble(torch, s, lambda4_printed=False, with_x0=True, harmonic_k=False):
     from paper_2206_11294_gb300 import binding as B
     g = s.grid
     d = _dev(torch, s)
@@ -70,7 +70,7 @@ def _gpu_assemble(torch, s, lambda4_printed=False, with_x0=True):
     out = dict(lam=z(N, 4), b=z(N, 2), x0=z(N, 2) if with_x0 else None,
                fa=[z(*g.face_shape(a)) for a in range(g.dim)], fk=[z(*g.face_shape(a)) for a in range(g.dim)])
     B.assemble(g, (s.ph1, s.ph2), s.dt, d["C"], d["m1"], d["m2"], d["E"], d["mom"], d["uf"], out,
-               lambda4_printed=lambda4_printed)
+               lambda4_printed=lambda4_printed, harmonic_k=harmonic_k)
     torch.cuda.synchronize()
     host = {k: (v.cpu().numpy() if v is not None and not isinstance(v, list) else
                 ([t.cpu().numpy() for t in v] if isinstance(v, list) else None)) for k, v in out.items()}
@@ -107,6 +107,15 @@ def test_assemble_matches_oracle(torch_cuda, orc, name, lambda4):
     s = _state(g)
     got, _, _ = _gpu_assemble(torch_cuda, s, lambda4_printed=lambda4 == "printed")
     ref = orc.assemble(g, s.ph1, s.ph2, s.dt, s.C, s.m1, s.m2, s.E, s.mom, s.uf, lambda4=lambda4)
+    _compare(g, s, got, ref)
+
+
+@pytest.mark.parametrize("name", list(GRIDS))
+def test_assemble_harmonic_face_k(torch_cuda, orc, name):
+    g = GRIDS[name]
+    s = _state(g, seed=25)
+    got, _, _ = _gpu_assemble(torch_cuda, s, harmonic_k=True)
+    ref = orc.assemble(g, s.ph1, s.ph2, s.dt, s.C, s.m1, s.m2, s.E, s.mom, s.uf, face_k="harmonic")
     _compare(g, s, got, ref)
 
 

@@ -264,3 +264,24 @@ def test_planted_mistake_is_caught(monkeypatch, label, old, new, pin):
     monkeypatch.setitem(globals(), "A", _mutant(old, new))
     with pytest.raises(AssertionError):
         pin()
+
+
+def test_harmonic_face_k_is_series_conduction():
+    """Steady conduction through two half cells of conductivities k_L and k_R in
+    series: the flux is (T_R - T_L) / (h/(2 k_L) + h/(2 k_R)), so the face
+    coefficient of the difference (T_R - T_L)/h is 1 / (1/(2 k_L) + 1/(2 k_R))."""
+    g = I.Grid(dim=2, axisym=0, n=(8, 4, 1), h=1e-3, bc=((W, W), (W, W), (0, 0)))
+    ph1, ph2, C, m1, m2, E, mom, uf = _uniform_state(g, 0.0)
+    C = np.zeros_like(C)
+    C[:, :, :4] = 1.0                                  # liquid left, gas right: the interface at face i = 4
+    r1, r2 = I.phase_density(310.0, 2e5, ph1), I.phase_density(310.0, 2e5, ph2)
+    m1, m2 = C * r1, (1 - C) * r2
+    E = C * I.phase_energy(2e5, r1, ph1) + (1 - C) * I.phase_energy(2e5, r2, ph2)
+    out = A.assemble(g, ph1, ph2, 1e-7, C, m1, m2, E, mom, uf, face_k="harmonic")
+    kL, kR = ph1.k, ph2.k
+    series = 1.0 / (g.h / (2 * kL) / g.h + g.h / (2 * kR) / g.h)
+    np.testing.assert_allclose(out["fk"][0][:, :, 4], series, rtol=1e-14)
+    np.testing.assert_allclose(out["fk"][0][:, :, 2], kL, rtol=1e-14)     # inside one phase: its own k
+    np.testing.assert_allclose(out["fk"][0][:, :, 6], kR, rtol=1e-14)
+    arith = A.assemble(g, ph1, ph2, 1e-7, C, m1, m2, E, mom, uf)
+    np.testing.assert_allclose(arith["fk"][0][:, :, 4], 0.5 * (kL + kR), rtol=1e-14)
