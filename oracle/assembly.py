@@ -15,7 +15,10 @@ Before the solve (Sec. 3, from the advected state of Eq. Yadv):
                    (T^(adv), p^(adv)).
 After it:
 - ``correct``      the velocity at the faces, u^{n+1} = u* - dt/rho grad p^{n+1}
-                   (Eq. unp1), and the phase pressures of Eqs. 37-38.
+                   (Eq. unp1), and the phase pressures of Eqs. 37-38;
+- ``energy``       the phase total energies at the end of the step (Eq. 39):
+                   pressure work, viscous work and heat conduction as face
+                   fluxes, each face flux one value shared by its two cells.
 
 Readings where the paper is silent (each listed in the design doc):
 - overlines are volume-fraction averages of the phase expressions; with the
@@ -32,7 +35,14 @@ Readings where the paper is silent (each listed in the design doc):
   (1 - C) k_2 (heat crossing two half cells);
 - div u* and grad p are the finite-volume differences of the solve's operator
   (axisymmetric: r_f / r_i weights on the r-faces), so that the divergence of
-  the corrected velocity is div u* - dt times the operator's p-Laplacian.
+  the corrected velocity is div u* - dt times the operator's p-Laplacian;
+- Eq. 39: cell velocities are the means of the two face velocities; on a face
+  the normal velocity is the face's own, the tangential velocities and p_i the
+  means of the two cells, normal derivatives the difference across the face and
+  tangential derivatives the mean of the two cells' central differences
+  (one-sided in the first and last cell); walls and the axis carry no energy
+  flux, a Dirichlet face carries -g_p u_f + k_i 2 (g_T - T)/h and no viscous
+  flux; the divergence is multiplied by C_i (the phase's share).
 """
 from __future__ import annotations
 
@@ -219,3 +229,91 @@ def correct(grid, dt: float, sigma: float, x: np.ndarray, C, kappa, fa: Sequence
     sk = sigma * np.asarray(kappa, dtype=np.float64)
     Cc = np.asarray(C, dtype=np.float64)
     return dict(uf=out, p1=p + (1.0 - Cc) * sk, p2=p - Cc * sk)
+
+
+# ---------------------------------------------------------------------------
+# Eq. 39: the phase total energies at the end of the step.
+# ---------------------------------------------------------------------------
+def cell_velocity(grid, uf: Sequence[np.ndarray]) -> List[np.ndarray]:
+    """Cell-centre velocity components: the mean of the two face velocities along each axis (Algorithm 1)."""
+    out = []
+    for a in range(grid.dim):
+        lo, hi = _face_slices(a)
+        u = np.asarray(uf[a], dtype=np.float64)
+        out.append(0.5 * (u[lo] + u[hi]))
+    return out
+
+
+def _cell_derivative(v: np.ndarray, b: int, h: float) -> np.ndarray:
+    """d v / d x_b at the cells: central differences inside, one-sided at the first and last cell."""
+    d = np.empty_like(v)
+    n = v.shape[2 - b]
+    sl = lambda s: tuple(s if ax == 2 - b else slice(None) for ax in range(3))
+    if n == 1:
+        return np.zeros_like(v)
+    d[sl(slice(1, -1))] = (v[sl(slice(2, None))] - v[sl(slice(0, -2))]) / (2.0 * h)
+    d[sl(slice(0, 1))] = (v[sl(slice(1, 2))] - v[sl(slice(0, 1))]) / h
+    d[sl(slice(-1, None))] = (v[sl(slice(-1, None))] - v[sl(slice(-2, -1))]) / h
+    return d
+
+
+def energy(grid, ph1, ph2, dt: float, C, p1, p2, T, uf: Sequence[np.ndarray], E1, E2) -> Dict[str, np.ndarray]:
+    """Eq. 39 for both phases: (C_i rho_i e_T,i)^{n+1} = (C_i rho_i e_T,i)^(adv) +
+    dt C_i div F_i with the face fluxes of axis a
+        F_i = -p_i,f u_f + mu_i (S . u)_{a,f} + k_i (dT/dx_a)_f,
+    S = grad u + grad u^T.  u_f: the face velocity (u^{n+1} of Eq. unp1); cell
+    velocities: means of the two face velocities; p_i,f, u_b,f (b != a): means of
+    the two cells; normal derivatives across the face, tangential ones the mean
+    of the two cells' (central, one-sided at the edge).  Boundary faces: walls and
+    the axis carry no flux; a Dirichlet face carries -g_p u_f + k_i 2 (g_T - T)/h
+    towards the boundary value (no viscous flux).  Both phases share T (thermal
+    equilibrium).  The divergence uses the solve's finite volumes (r_f / r_i on
+    axisymmetric r-faces)."""
+    ph1, ph2 = _phase(ph1), _phase(ph2)
+    h = grid.h
+    dim = grid.dim
+    ucell = cell_velocity(grid, uf)
+    dcell = [[_cell_derivative(ucell[a], b, h) for b in range(dim)] for a in range(dim)]   # dcell[a][b] = du_a/dx_b
+    Tc = np.asarray(T, dtype=np.float64)
+    out = {}
+    for name, ph, pi, Ci, Ei in (("E1", ph1, p1, C, E1), ("E2", ph2, p2, 1.0 - np.asarray(C), E2)):
+        mu, k = ph.get("mu", 0.0), ph["k"]
+        div = np.zeros_like(Tc)
+        for a in range(dim):
+            lo, hi = _face_slices(a)
+            u_f = np.asarray(uf[a], dtype=np.float64)
+            F = np.zeros(grid.face_shape(a), dtype=np.float64)
+            inner = [slice(None)] * 3
+            inner[2 - a] = slice(1, -1)
+            inner = tuple(inner)
+            # pressure work and heat flux on interior faces
+            pf = 0.5 * (pi[lo] + pi[hi])
+            dTdn = (Tc[hi] - Tc[lo]) / h
+            visc = 0.0
+            for b in range(dim):
+                if b == a:
+                    s_ab = 2.0 * (ucell[a][hi] - ucell[a][lo]) / h
+                    ub = u_f[inner]
+                else:
+                    s_ab = 0.5 * (dcell[a][b][lo] + dcell[a][b][hi]) + (ucell[b][hi] - ucell[b][lo]) / h
+                    ub = 0.5 * (ucell[b][lo] + ucell[b][hi])
+                visc = visc + s_ab * ub
+            F[inner] = -pf * u_f[inner] + mu * visc + k * dTdn
+            for side in (0, 1):
+                if grid.bc[a][side] != BC_DIRICHLET:
+                    continue
+                face = [slice(None)] * 3
+                cell = [slice(None)] * 3
+                face[2 - a] = slice(0, 1) if side == 0 else slice(-1, None)
+                cell[2 - a] = slice(0, 1) if side == 0 else slice(-1, None)
+                Tb = Tc[tuple(cell)]
+                gT, gp = grid.bcT[a][side], grid.bcp[a][side]
+                dT = 2.0 * (Tb - gT) / h if side == 0 else 2.0 * (gT - Tb) / h
+                F[tuple(face)] = -gp * u_f[tuple(face)] + k * dT
+            if grid.axisym and a == 0:
+                ri = grid.r0 + _cell_xyz(grid, 0) * h
+                div = div + ((ri + 0.5 * h) * F[hi] - (ri - 0.5 * h) * F[lo]) / (ri * h)
+            else:
+                div = div + (F[hi] - F[lo]) / h
+        out[name] = np.asarray(Ei, dtype=np.float64) + dt * np.asarray(Ci, dtype=np.float64) * div
+    return out

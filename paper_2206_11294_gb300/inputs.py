@@ -357,14 +357,15 @@ class NasgPhase:
     cp: float
     cv: float
     k: float
+    mu: float = 0.0               # dynamic viscosity (Eq. 3), for the energy update of Eq. 39
 
 
-def water_phase(k: float = 0.6) -> NasgPhase:
-    return NasgPhase(k=k, **NASG_WATER)
+def water_phase(k: float = 0.6, mu: float = 8.5e-4) -> NasgPhase:
+    return NasgPhase(k=k, mu=mu, **NASG_WATER)
 
 
-def air_phase(k: float = 0.026) -> NasgPhase:
-    return NasgPhase(k=k, **NASG_AIR)
+def air_phase(k: float = 0.026, mu: float = 1.85e-5) -> NasgPhase:
+    return NasgPhase(k=k, mu=mu, **NASG_AIR)
 
 
 @dataclasses.dataclass

@@ -285,3 +285,189 @@ def test_harmonic_face_k_is_series_conduction():
     np.testing.assert_allclose(out["fk"][0][:, :, 6], kR, rtol=1e-14)
     arith = A.assemble(g, ph1, ph2, 1e-7, C, m1, m2, E, mom, uf)
     np.testing.assert_allclose(arith["fk"][0][:, :, 4], 0.5 * (kL + kR), rtol=1e-14)
+
+
+# ----------------------------------------------------------------------------
+# Eq. 39: the phase energies at the end of the step
+# ----------------------------------------------------------------------------
+def _faces_from(g, f):
+    """Face arrays of each axis from a function f(a, X) of the face-centre coordinates."""
+    out = []
+    for a in range(g.dim):
+        s = g.face_shape(a)
+        X = []
+        for b in range(3):
+            n = s[2 - b]
+            off = (g.r0 if (g.axisym and b == 0) else 0.0)
+            x = (np.arange(n, dtype=float) + (0.0 if b == a else 0.5)) * g.h + off
+            shape = [1, 1, 1]
+            shape[2 - b] = n
+            X.append(np.broadcast_to(x.reshape(shape), s))
+        out.append(np.array(f(a, X), dtype=float) * np.ones(s))
+    return out
+
+
+def _energy_inputs(g, C=1.0, p=1e5, T=300.0, mu=0.0, k=0.0, uf=None):
+    shape = (g.n[2], g.n[1], g.n[0])
+    ph = I.NasgPhase(Gamma=1.4, Pi=0.0, b=0.0, q=0.0, cp=1005.0, cv=717.86, k=k, mu=mu)
+    Cc = np.full(shape, C) if np.isscalar(C) else C
+    pf = np.full(shape, p) if np.isscalar(p) else p
+    Tf = np.full(shape, T) if np.isscalar(T) else T
+    uf = uf if uf is not None else [np.zeros(g.face_shape(a)) for a in range(g.dim)]
+    E = np.full(shape, 2.5e5)
+    return ph, Cc, pf, Tf, uf, E
+
+
+G2 = I.Grid(dim=2, axisym=0, n=(16, 12, 1), h=1e-3, bc=((W, W), (W, W), (0, 0)))
+
+
+def _dE_close(dE, expect, E):
+    """The change is read off E (~2.5e5): a few ulps of E, not of the change."""
+    np.testing.assert_allclose(dE, expect, rtol=1e-9, atol=8 * np.finfo(float).eps * np.abs(E).max())
+GAXI = I.Grid(dim=2, axisym=1, n=(12, 16, 1), h=1e-3, r0=0.0, bc=((AX, W), (W, W), (0, 0)))
+
+
+def test_energy_at_rest_unchanged():
+    ph, C, p, T, uf, E = _energy_inputs(G2, mu=1e-3, k=0.6)
+    out = A.energy(G2, ph, ph, 1e-6, C, p, p, T, uf, E, E)
+    assert np.array_equal(out["E1"], E) and np.array_equal(out["E2"], E)
+
+
+def test_energy_couette_viscous_heating():
+    """u_x = gamma y, u_y = 0: (S . u)_y = mu gamma^2 y, whose divergence is the
+    viscous heating mu gamma^2 (rows whose two y-faces are inside)."""
+    g, gam, mu, dt = G2, 300.0, 2e-3, 1e-6
+    uf = _faces_from(g, lambda a, X: gam * X[1] if a == 0 else 0.0 * X[1])
+    ph, C, p, T, _, E = _energy_inputs(g, p=0.0, mu=mu, uf=uf)
+    out = A.energy(g, ph, ph, dt, C, p, p, T, uf, E, E)
+    _dE_close((out["E1"] - E)[:, 1:-1, :], dt * mu * gam ** 2, E)
+
+
+def test_energy_heat_conduction_of_a_quadratic():
+    """No flow, T = T0 + a x^2: div(k grad T) = 2 a k exactly inside; C_i weights each phase."""
+    g, a_, k, dt = G2, 4e4, 0.6, 1e-6
+    x = (np.arange(g.n[0]) + 0.5) * g.h
+    T = 300.0 + a_ * np.broadcast_to(x ** 2, (g.n[2], g.n[1], g.n[0]))
+    ph, C, p, _, uf, E = _energy_inputs(g, C=0.3, k=k)
+    out = A.energy(g, ph, ph, dt, C, p, p, T, uf, E, E)
+    _dE_close((out["E1"] - E)[:, :, 1:-1], dt * 0.3 * 2 * a_ * k, E)
+    _dE_close((out["E2"] - E)[:, :, 1:-1], dt * 0.7 * 2 * a_ * k, E)
+
+
+@pytest.mark.parametrize("g", [G2, GAXI], ids=["2d", "axi"])
+def test_energy_pressure_work_of_a_linear_flow(g):
+    """Uniform p, u_a = c_a x_a: -div(p u) = -p (c_0 + c_1) (axisymmetric: u_r = c r has div = 2c)."""
+    cs = (250.0, -120.0)
+    uf = _faces_from(g, lambda a, X: cs[a] * X[a])
+    ph, C, p, T, _, E = _energy_inputs(g, p=2e5, uf=uf)
+    out = A.energy(g, ph, ph, 1e-6, C, p, p, T, uf, E, E)
+    divu = (2 * cs[0] if g.axisym else cs[0]) + cs[1]
+    _dE_close((out["E1"] - E)[:, 1:-1, 1:-1], -1e-6 * 2e5 * divu, E)
+
+
+@pytest.mark.parametrize("g", [G2, GAXI, I.Grid(dim=3, axisym=0, n=(8, 6, 10), h=1e-3,
+                                                bc=((W, W), (W, W), (W, W)))], ids=["2d", "axi", "3d"])
+def test_energy_conserved_with_walls(g):
+    """One phase everywhere, walls: every flux crosses between two cells and the
+    boundary carries none, so the volume-weighted sum of the change vanishes."""
+    rng = np.random.default_rng(8)
+    shape = (g.n[2], g.n[1], g.n[0])
+    uf = [rng.normal(0, 0.3, g.face_shape(a)) for a in range(g.dim)]
+    for a in range(g.dim):
+        uf[a][tuple(slice(0, 1) if ax == 2 - a else slice(None) for ax in range(3))] = 0.0
+        uf[a][tuple(slice(-1, None) if ax == 2 - a else slice(None) for ax in range(3))] = 0.0
+    ph, C, _, _, _, E = _energy_inputs(g, mu=1e-3, k=0.6)
+    p = 1e5 + rng.normal(0, 300.0, shape)
+    T = 300.0 + rng.normal(0, 2.0, shape)
+    out = A.energy(g, ph, ph, 1e-6, C, p, p, T, uf, E, E)
+    V = np.ones(shape) if not g.axisym else (g.r0 + (np.arange(g.n[0]) + 0.5) * g.h) * np.ones(shape)
+    change = np.sum(V * (out["E1"] - E))
+    scale = np.sum(V * np.abs(out["E1"] - E))
+    assert abs(change) <= 1e-12 * scale
+
+
+def test_energy_phases_add_to_one_phase():
+    """Equal properties and pressures: the two phase updates sum to the one-phase update."""
+    g = G2
+    rng = np.random.default_rng(9)
+    shape = (g.n[2], g.n[1], g.n[0])
+    uf = [rng.normal(0, 0.3, g.face_shape(a)) for a in range(g.dim)]
+    C = rng.uniform(0, 1, shape)
+    ph, _, _, _, _, E = _energy_inputs(g, mu=1e-3, k=0.6)
+    p = 1e5 + rng.normal(0, 300.0, shape)
+    T = 300.0 + rng.normal(0, 2.0, shape)
+    two = A.energy(g, ph, ph, 1e-6, C, p, p, T, uf, E, E)
+    one = A.energy(g, ph, ph, 1e-6, np.ones(shape), p, p, T, uf, E, E)
+    np.testing.assert_allclose(two["E1"] + two["E2"] - 2 * E, one["E1"] - E, rtol=1e-9, atol=1e-9 * np.abs(one["E1"] - E).max())
+
+
+def _viscous_linear_pin():
+    """Pure straining u_a = c_a x_a with p = 0: (S . u)_a = 2 c_a^2 x_a, whose divergence is 2 (c_0^2 + c_1^2)."""
+    g, mu, dt = G2, 1e-3, 1e-6
+    cs = (250.0, -120.0)
+    uf = _faces_from(g, lambda a, X: cs[a] * X[a])
+    ph, C, p, T, _, E = _energy_inputs(g, p=0.0, mu=mu, uf=uf)
+    out = A.energy(g, ph, ph, dt, C, p, p, T, uf, E, E)
+    _dE_close((out["E1"] - E)[:, 2:-2, 2:-2], dt * mu * 2 * (cs[0] ** 2 + cs[1] ** 2), E)
+
+
+def test_energy_pure_straining_viscous_work():
+    _viscous_linear_pin()
+
+
+def test_energy_pressure_work_quadratic_pressure():
+    """Uniform u_x = U, p = a x^2: -div(p u) = -U p'(x) = -2 a U x exactly with
+    the two-cell face mean of p (central difference of a quadratic)."""
+    g, U, a_, dt = G2, 3.0, 2e8, 1e-6
+    uf = _faces_from(g, lambda a, X: U + 0.0 * X[0] if a == 0 else 0.0 * X[0])
+    x = (np.arange(g.n[0]) + 0.5) * g.h
+    shape = (g.n[2], g.n[1], g.n[0])
+    p = 1e5 + a_ * np.broadcast_to(x ** 2, shape)
+    ph, C, _, T, _, E = _energy_inputs(g, uf=uf)
+    out = A.energy(g, ph, ph, dt, C, p, p, T, uf, E, E)
+    _dE_close((out["E1"] - E)[:, :, 1:-1], np.broadcast_to(-dt * 2 * a_ * U * x, shape)[:, :, 1:-1], E)
+
+
+def _taylor_green_error(n):
+    """Viscous work of u = U (sin pi x cos pi y, -cos pi x sin pi y) on the unit
+    square: div(mu S . u) = 2 mu U^2 pi^2 (cos 2 pi x cos^2 pi y + cos^2 pi x cos 2 pi y)
+    (S_xy = 0 for this flow).  Max error over cells two or more from the walls."""
+    g = I.Grid(dim=2, axisym=0, n=(n, n, 1), h=1.0 / n, bc=((W, W), (W, W), (0, 0)))
+    U, mu, dt = 2.0, 1e-3, 1.0
+    pi = np.pi
+    uf = _faces_from(g, lambda a, X: U * np.sin(pi * X[0]) * np.cos(pi * X[1]) if a == 0
+                     else -U * np.cos(pi * X[0]) * np.sin(pi * X[1]))
+    ph, C, p, T, _, E = _energy_inputs(g, p=0.0, mu=mu, uf=uf)
+    E = np.zeros_like(E)
+    out = A.energy(g, ph, ph, dt, C, p, p, T, uf, E, E)
+    xc = (np.arange(n) + 0.5) / n
+    X, Y = np.meshgrid(xc, xc, indexing="xy")
+    exact = 2 * mu * U ** 2 * pi ** 2 * (np.cos(2 * pi * X) * np.cos(pi * Y) ** 2 + np.cos(pi * X) ** 2 * np.cos(2 * pi * Y))
+    return np.max(np.abs(out["E1"][0] - exact)[2:-2, 2:-2])
+
+
+def test_energy_viscous_work_second_order():
+    e1, e2 = _taylor_green_error(32), _taylor_green_error(64)
+    assert e2 < e1 and e1 / e2 > 3.5, (e1, e2)
+
+
+ENERGY_MUTATIONS = [
+    ("normal strain without its factor 2", "s_ab = 2.0 * (ucell[a][hi] - ucell[a][lo]) / h",
+     "s_ab = (ucell[a][hi] - ucell[a][lo]) / h", _viscous_linear_pin),
+    ("heat flux with the wrong sign", "F[inner] = -pf * u_f[inner] + mu * visc + k * dTdn",
+     "F[inner] = -pf * u_f[inner] + mu * visc - k * dTdn", test_energy_heat_conduction_of_a_quadratic),
+    ("pressure-work face value from one cell", "pf = 0.5 * (pi[lo] + pi[hi])", "pf = pi[lo]",
+     test_energy_pressure_work_quadratic_pressure),
+    ("axisymmetric energy flux without r weights",
+     "div = div + ((ri + 0.5 * h) * F[hi] - (ri - 0.5 * h) * F[lo]) / (ri * h)", "div = div + (F[hi] - F[lo]) / h",
+     lambda: test_energy_pressure_work_of_a_linear_flow(GAXI)),
+    ("tangential derivative from one cell", "s_ab = 0.5 * (dcell[a][b][lo] + dcell[a][b][hi]) + (ucell[b][hi] - ucell[b][lo]) / h",
+     "s_ab = dcell[a][b][lo] + (ucell[b][hi] - ucell[b][lo]) / h", test_energy_viscous_work_second_order),
+]
+
+
+@pytest.mark.parametrize("label,old,new,pin", ENERGY_MUTATIONS, ids=[m[0] for m in ENERGY_MUTATIONS])
+def test_planted_energy_mistake_is_caught(monkeypatch, label, old, new, pin):
+    monkeypatch.setitem(globals(), "A", _mutant(old, new))
+    with pytest.raises(AssertionError):
+        pin()
