@@ -494,14 +494,16 @@ def run_wall3d(args):
 # each must read and write once (face arrays: one face per cell and axis).
 ASSEMBLE_BYTES_2D = (4 + 2 + 2) * 8 + (4 + 2 + 2 + 2 + 2) * 8    # C m1 m2 E, mom, u*; lambda, rhs, x0, 1/rho, k
 CORRECT_BYTES_2D = (2 + 1 + 1 + 2 + 2) * 8 + (2 + 1 + 1) * 8      # x, C, kappa, 1/rho, u*; u^(n+1), p1, p2
+ENERGY_BYTES_2D = (2 + 1 + 2 + 2 + 2) * 8 + 2 * 8                 # x, C, p1 p2, u^(n+1), E1 E2; E1, E2 out
 
 
 def run_timestep(args):
     """The device work of one time step on the 16-bubble 1024^2 advected state:
     coefficient assembly (mg_assemble_async: Eqs. 10, 11, 20, 23, 29-34), set-up and
-    solve to 1e-10 from (T^(adv), p^(adv)), and the velocity / phase-pressure
-    update (mg_correct_async: Eq. unp1, Eqs. 37-38).  Inputs resident on the device;
-    the L2 is flushed between steps."""
+    solve to 1e-10 from (T^(adv), p^(adv)), the velocity / phase-pressure
+    update (mg_correct_async: Eq. unp1, Eqs. 37-38) and the phase-energy update
+    (mg_energy_async: Eq. 39).  Inputs resident on the device; the L2 is flushed
+    between steps."""
     import numpy as np
     import torch
     from paper_2206_11294_gb300 import binding as B
@@ -521,6 +523,10 @@ def run_timestep(args):
     x = z(N, 2)
     uo = [torch.empty_like(u) for u in d["uf"]]
     p1, p2 = z(*s.C.shape), z(*s.C.shape)
+    rho1, rho2 = I.phase_density(s.T, s.p, s.ph1), I.phase_density(s.T, s.p, s.ph2)
+    E1 = T(s.C * I.phase_energy(s.p, rho1, s.ph1))
+    E2 = T((1 - s.C) * I.phase_energy(s.p, rho2, s.ph2))
+    E1o, E2o = torch.empty_like(E1), torch.empty_like(E2)
     solver = Solver(g, precision=args.precision, rtol=1e-10, max_cycles=50, stream=stream)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
 
@@ -529,6 +535,9 @@ def run_timestep(args):
 
     def correct():
         B.correct(g, s.dt, s.sigma, x, d["C"], d["kappa"], out["fa"], d["uf"], uo, p1, p2)
+
+    def energy():
+        B.energy(g, (s.ph1, s.ph2), s.dt, x, d["C"], p1, p2, uo, E1, E2, E1o, E2o)
 
     assemble()
     solver.set_coeffs(out["lam"], out["fa"], out["fk"])
@@ -549,21 +558,24 @@ def run_timestep(args):
         marks[2].record(stream)
         correct()
         marks[3].record(stream)
+        energy()
+        marks[4].record(stream)
 
     for _ in range(args.warmup):
-        step([ev() for _ in range(4)])
+        step([ev() for _ in range(5)])
     torch.cuda.synchronize()
     stats.clear()
-    marks = [[ev() for _ in range(4)] for _ in range(args.steps)]
+    marks = [[ev() for _ in range(5)] for _ in range(args.steps)]
     clocks = ClockSampler(gpu_identity(torch, 0))
     for k in range(args.steps):
         flush.zero_()
         step(marks[k])
     torch.cuda.synchronize()
     clk = clocks.stop()
-    total = sum(m[0].elapsed_time(m[3]) for m in marks) / args.steps
+    total = sum(m[0].elapsed_time(m[4]) for m in marks) / args.steps
     t_asm = sum(m[0].elapsed_time(m[1]) for m in marks) / args.steps
     t_cor = sum(m[2].elapsed_time(m[3]) for m in marks) / args.steps
+    t_en = sum(m[3].elapsed_time(m[4]) for m in marks) / args.steps
     peak, peak_kind = measured_peak()
     roof = lambda byts, ms: {"bound": "hbm", "achieved": byts / (ms * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
                              "frac": byts / (ms * 1e-3) / 1e9 / peak, "peak_source": peak_kind,
@@ -574,12 +586,14 @@ def run_timestep(args):
     asm_alu = {"bound": "alu", "fp64_pipe_busy_elapsed_ncu": 0.836, "fp64_inst_per_cell_ncu": 150,
                "source": "profiles/k_assemble_bubbles1024.md", "hbm": asm}
     return {"workload": "one time step, bubbles16_1024x1024 advected state: assembly + set-up + solve to 1e-10 + "
-                        "velocity / phase-pressure update", "metric": "time steps/s", "cells": N,
+                        "velocity / phase-pressure update + phase-energy update", "metric": "time steps/s",
+            "cells": N,
             "precision": args.precision, "steps_per_s": 1e3 / total, "ms_per_step": total,
-            "assemble_ms": t_asm, "solve_ms": total - t_asm - t_cor, "correct_ms": t_cor,
+            "assemble_ms": t_asm, "solve_ms": total - t_asm - t_cor - t_en, "correct_ms": t_cor, "energy_ms": t_en,
             "cycles_per_solve": cycles[0] if cycles else None, "tuning": tuning,
             "assemble_roofline": asm_alu,
             "correct_roofline": roof(CORRECT_BYTES_2D * N, t_cor),
+            "energy_roofline": roof(ENERGY_BYTES_2D * N, t_en),
             "l2": "flushed between steps", "clocks": clk, "data": "synthetic (seeded advected state, NASG water / air)"}
 
 

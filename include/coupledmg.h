@@ -299,7 +299,8 @@ MG_API mg_status mg_batch_destroy(mg_batch *b);
 typedef struct {
     double Gamma, Pi, b, q;   /* NASG parameters of Eq. 9 (Table 1); ideal gas: Gamma = gamma, Pi = b = q = 0 */
     double cp, cv;            /* heat capacities at constant pressure and volume, J/(kg K), cp > cv > 0 */
-    double k;                 /* thermal conductivity, W/(m K) */
+    double k;                 /* thermal conductivity, W/(m K), >= 0 */
+    double mu;                /* dynamic viscosity, Pa s, >= 0 (read by mg_energy_async only) */
 } mg_phase;
 
 typedef struct {              /* the advected state (Eq. Yadv) */
@@ -353,6 +354,27 @@ MG_API mg_status mg_correct_async(const mg_grid *grid, double dt, double sigma, 
                                   const double *kappa, const double *const face_alpha[3],
                                   const double *const uf_star[3], double *const uf_out[3], double *p1, double *p2,
                                   void *stream);
+
+/* Phase energies at the end of the step (Eq. 39):
+ *   E_i_out = E_i + dt C_i div F_i,  C_1 = C, C_2 = 1 - C,
+ * with the face flux of axis a
+ *   F_i = -p_i,f u_f + mu_i (S . u)_{a,f} + k_i (dT/dx_a)_f,  S = grad u + grad u^T,
+ * u_f the face velocity uf[a] (u^{n+1} from mg_correct_async), T the first
+ * component of x [N][2] (the solution of mg_solve), p1, p2 the phase pressures
+ * (from mg_correct_async), E1, E2 the advected phase energies C_i rho_i e_T,i
+ * per volume.  A cell's velocity is the mean of its two face velocities; on a
+ * face the tangential velocities and p_i are the means of the two cells, normal
+ * derivatives the difference across the face, tangential derivatives the mean
+ * of the two cells' central differences (one-sided in the first and last cell).
+ * Walls and the axis carry no flux; a Dirichlet face carries
+ * -bc_p u_f + k_i 2 (bc_T - T)/h towards the boundary value, and no viscous
+ * flux.  div is the finite-volume divergence (r_f / r_i on axisymmetric
+ * r-faces).  Each face flux is one value shared by its two cells, so the update
+ * is conservative to rounding.  E1_out may equal E1 and E2_out E2 (in place);
+ * no other output may alias an input.  dt > 0. */
+MG_API mg_status mg_energy_async(const mg_grid *grid, const mg_phase phases[2], double dt, const double *x,
+                                 const double *C, const double *p1, const double *p2, const double *const uf[3],
+                                 const double *E1, const double *E2, double *E1_out, double *E2_out, void *stream);
 
 /* Allocation-free stopping norms (the paper has no counterpart: this is a
  * library service).  For callers that cannot allocate device memory - their

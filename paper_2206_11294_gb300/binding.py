@@ -32,7 +32,8 @@ EXPORTS = ["mg_default_options", "mg_workspace_size", "mg_create", "mg_set_coeff
            "mg_last_error", "mg_set_timing", "mg_counters", "mg_residual_norms_noalloc",
            "mg_batch_create", "mg_batch_solve", "mg_batch_counters", "mg_batch_destroy", "mg_set_stream",
            "mg_batch_set_coeffs", "mg_get_tuning", "mg_set_tuning", "mg_autotune", "mg_batch_get_tuning",
-           "mg_batch_set_tuning", "mg_batch_autotune", "mg_assemble_async", "mg_correct_async"]
+           "mg_batch_set_tuning", "mg_batch_autotune", "mg_assemble_async", "mg_correct_async",
+           "mg_energy_async"]
 
 MG_MAX_LEVELS = 32
 MG_SWEEP_COLOUR, MG_SWEEP_FUSED, MG_SWEEP_ASYNC, MG_SWEEP_COLOUR2 = 1, 2, 3, 4
@@ -117,7 +118,7 @@ class MgBatchTuning(C.Structure):
 
 class MgPhase(C.Structure):
     _fields_ = [("Gamma", C.c_double), ("Pi", C.c_double), ("b", C.c_double), ("q", C.c_double),
-                ("cp", C.c_double), ("cv", C.c_double), ("k", C.c_double)]
+                ("cp", C.c_double), ("cv", C.c_double), ("k", C.c_double), ("mu", C.c_double)]
 
 
 class MgState(C.Structure):
@@ -178,6 +179,8 @@ def load(path: str = LIB_PATH):
             "mg_assemble_async": ([C.POINTER(MgGrid), MgPhase * 2, C.c_double, C.c_int, C.POINTER(MgState),
                                    C.POINTER(MgAssembly), P], C.c_int),
             "mg_correct_async": ([C.POINTER(MgGrid), C.c_double, C.c_double, P, P, P, pa3, pa3, pa3, P, P, P], C.c_int),
+            "mg_energy_async": ([C.POINTER(MgGrid), C.POINTER(MgPhase), C.c_double, P, P, P, P, pa3, P, P, P, P, P],
+                                C.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -276,9 +279,9 @@ def residual_norms_noalloc(grid, lam, fa, fk, b, x, out, stream=None) -> None:
 
 
 def make_phase(ph) -> MgPhase:
-    """From an object or dict with Gamma, Pi, b, q, cp, cv, k."""
-    get = (lambda key: ph[key]) if isinstance(ph, dict) else (lambda key: getattr(ph, key))
-    return MgPhase(*(float(get(key)) for key in ("Gamma", "Pi", "b", "q", "cp", "cv", "k")))
+    """From an object or dict with Gamma, Pi, b, q, cp, cv, k and optionally mu (0 if absent)."""
+    get = (lambda key: ph.get(key, 0.0)) if isinstance(ph, dict) else (lambda key: getattr(ph, key, 0.0))
+    return MgPhase(*(float(get(key)) for key in ("Gamma", "Pi", "b", "q", "cp", "cv", "k", "mu")))
 
 
 MG_ASSEMBLE_LAMBDA4_PRINTED, MG_ASSEMBLE_HARMONIC_K = 1, 2
@@ -333,6 +336,22 @@ def correct(grid, dt: float, sigma: float, x, C_, kappa, fa: Sequence, uf_star: 
     check(load().mg_correct_async(C.byref(g), float(dt), float(sigma), _ptr(x, True)[0], _ptr(C_, True)[0],
                             _ptr(kappa, True)[0], pa, pu, po, _ptr(p1, True)[0], _ptr(p2, True)[0],
                             C.c_void_p(stream.cuda_stream)))
+
+
+def energy(grid, phases, dt: float, x, C_, p1, p2, uf: Sequence, E1, E2, E1_out, E2_out, stream=None) -> None:
+    """mg_energy_async: every array a contiguous float64 CUDA tensor; E1_out, E2_out (which may be E1, E2) are
+    written in the order of `stream` (the call does not wait for the work)."""
+    import torch
+    g = make_grid(grid)
+    pu = (C.c_void_p * 3)()
+    for a in range(g.dim):
+        pu[a] = _ptr(uf[a], True)[0]
+    ph = (MgPhase * 2)(make_phase(phases[0]), make_phase(phases[1]))
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    d = lambda a: _ptr(a, True)[0]
+    check(load().mg_energy_async(C.byref(g), ph, float(dt), d(x), d(C_), d(p1), d(p2), pu, d(E1), d(E2),
+                                 d(E1_out), d(E2_out), C.c_void_p(stream.cuda_stream)))
 
 
 class Solver:

@@ -202,4 +202,158 @@ __global__ void __launch_bounds__(256) k_correct(const __grid_constant__ Correct
     A.p2[c] = p - Cc * sk;
 }
 
+// ---------------------------------------------------------------- Eq. 39
+// Phase total energies at the end of the step: (C_i rho_i e_T,i)^{n+1} =
+// (C_i rho_i e_T,i)^(adv) + dt C_i div F_i, with the face flux of axis a
+//   F_i = -p_i,f u_f + mu_i (S . u)_{a,f} + k_i (dT/dx_a)_f,   S = grad u + grad u^T.
+// Cell velocities are the means of their two face velocities; on a face the
+// normal velocity is the face's own, the tangential ones and p_i the means of
+// the two cells, the normal derivatives the difference across the face and the
+// tangential derivatives the mean of the two cells' (central, one-sided in the
+// first and last cell).  Walls and the axis carry no flux; a Dirichlet face
+// carries -g_p u_f + k_i 2 (g_T - T)/h towards the boundary value.
+//
+// A block computes every face flux of its tile into shared memory through one
+// code path (faces on the tile's edge are computed by both blocks that share
+// them, by the same instructions on the same inputs, so both get the same
+// bits), then each cell takes the divergence.  The update is conservative:
+// summed over the cells with their volumes, (E_i^{n+1} - E_i) / (dt C_i)
+// telescopes to the fluxes through the boundary faces.
+struct EnergyArgs {
+    int n[3];
+    int dir[3][2];                 // Dirichlet faces
+    double gT[3][2], gp[3][2];     // their values
+    double r0, h, inv_h, half_inv_h, two_inv_h, dt;
+    double k[2], mu[2];
+    const double2 *x;              // [N] (T, p)
+    const double *C, *p1, *p2;
+    const double *uf[3];
+    const double *E1, *E2;
+    double *E1o, *E2o;
+};
+
+// Velocity component a at a cell: the mean of its two faces of axis a.
+template <int DIM>
+__device__ __forceinline__ double cell_u(const EnergyArgs &A, int a, int i, int j, int k) {
+    const long long f = face_index(A.n, a, i, j, k);
+    const long long st = a == 0 ? 1LL : a == 1 ? (long long)A.n[0] : (long long)A.n[0] * A.n[1];
+    return 0.5 * (A.uf[a][f] + A.uf[a][f + st]);
+}
+
+// d u_a / d x_b at cell pos: central inside, one-sided in the first and last cell.
+template <int DIM>
+__device__ __forceinline__ double cell_du(const EnergyArgs &A, int a, int b, const int pos[3]) {
+    const int nb = A.n[b];
+    if (nb < 2) return 0.0;
+    int up[3] = {pos[0], pos[1], pos[2]}, dn[3] = {pos[0], pos[1], pos[2]};
+    up[b] = pos[b] + 1 < nb ? pos[b] + 1 : pos[b];
+    dn[b] = pos[b] > 0 ? pos[b] - 1 : pos[b];
+    const double d = cell_u<DIM>(A, a, up[0], up[1], up[2]) - cell_u<DIM>(A, a, dn[0], dn[1], dn[2]);
+    return d * (up[b] - dn[b] == 2 ? A.half_inv_h : A.inv_h);
+}
+
+// (F_1, F_2) on the face of axis a at face position f (f[a] in 0..n[a]).
+template <int DIM>
+__device__ __forceinline__ double2 energy_face_flux(const EnergyArgs &A, int a, const int f[3]) {
+    const int fa = f[a];
+    const double u_f = A.uf[a][face_index(A.n, a, f[0], f[1], f[2])];
+    if (fa == 0 || fa == A.n[a]) {
+        const int side = fa == 0 ? 0 : 1;
+        if (!A.dir[a][side]) return make_double2(0.0, 0.0);
+        int c[3] = {f[0], f[1], f[2]};
+        if (side) c[a] = fa - 1;
+        const double Tb = A.x[(long long)c[0] + (long long)A.n[0] * ((long long)c[1] + (long long)A.n[1] * c[2])].x;
+        const double dT = (side == 0 ? Tb - A.gT[a][0] : A.gT[a][1] - Tb) * A.two_inv_h;
+        const double pw = -A.gp[a][side] * u_f;
+        return make_double2(pw + A.k[0] * dT, pw + A.k[1] * dT);
+    }
+    int L[3] = {f[0], f[1], f[2]};
+    L[a] = fa - 1;
+    const int *R = f;
+    const long long cl = (long long)L[0] + (long long)A.n[0] * ((long long)L[1] + (long long)A.n[1] * L[2]);
+    const long long cr = (long long)R[0] + (long long)A.n[0] * ((long long)R[1] + (long long)A.n[1] * R[2]);
+    const double dTdn = (A.x[cr].x - A.x[cl].x) * A.inv_h;
+    double visc = 0.0;
+#pragma unroll
+    for (int b = 0; b < DIM; b++) {
+        const double ubL = cell_u<DIM>(A, b, L[0], L[1], L[2]), ubR = cell_u<DIM>(A, b, R[0], R[1], R[2]);
+        double s, ub;
+        if (b == a) {
+            s = 2.0 * (ubR - ubL) * A.inv_h;
+            ub = u_f;
+        } else {
+            s = 0.5 * (cell_du<DIM>(A, a, b, L) + cell_du<DIM>(A, a, b, R)) + (ubR - ubL) * A.inv_h;
+            ub = 0.5 * (ubL + ubR);
+        }
+        visc = b == 0 ? s * ub : visc + s * ub;
+    }
+    const double pf1 = 0.5 * (A.p1[cl] + A.p1[cr]), pf2 = 0.5 * (A.p2[cl] + A.p2[cr]);
+    return make_double2(-pf1 * u_f + A.mu[0] * visc + A.k[0] * dTdn, -pf2 * u_f + A.mu[1] * visc + A.k[1] * dTdn);
+}
+
+template <int DIM, bool AXI, int TX, int TY>
+__global__ void __launch_bounds__(TX * TY) k_energy(const __grid_constant__ EnergyArgs A) {
+    constexpr int NX = (TX + 1) * TY, NY = TX * (TY + 1), NZ = DIM == 3 ? 2 * TX * TY : 0;
+    __shared__ double2 F[NX + NY + NZ];
+    const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY, k = DIM == 3 ? (int)blockIdx.z : 0;
+    const int tid = threadIdx.x + TX * threadIdx.y;
+    for (int t = tid; t < NX + NY + NZ; t += TX * TY) {
+        int a, f[3];
+        if (t < NX) {
+            a = 0;
+            f[0] = i0 + t % (TX + 1);
+            f[1] = j0 + t / (TX + 1);
+            f[2] = k;
+        } else if (t < NX + NY) {
+            const int u = t - NX;
+            a = 1;
+            f[0] = i0 + u % TX;
+            f[1] = j0 + u / TX;
+            f[2] = k;
+        } else {
+            const int u = t - NX - NY;
+            a = 2;
+            f[0] = i0 + u % TX;
+            f[1] = j0 + (u / TX) % TY;
+            f[2] = k + u / (TX * TY);
+        }
+        bool in = true;
+#pragma unroll
+        for (int b = 0; b < 3; b++) in = in && f[b] < A.n[b] + (b == a);
+        F[t] = in ? energy_face_flux<DIM>(A, a, f) : make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+    const int li = threadIdx.x, lj = threadIdx.y, i = i0 + li, j = j0 + lj;
+    if (i >= A.n[0] || j >= A.n[1]) return;
+    const long long c = (long long)i + (long long)A.n[0] * ((long long)j + (long long)A.n[1] * k);
+    double2 lo[3], hi[3];
+    lo[0] = F[lj * (TX + 1) + li];
+    hi[0] = F[lj * (TX + 1) + li + 1];
+    lo[1] = F[NX + lj * TX + li];
+    hi[1] = F[NX + (lj + 1) * TX + li];
+    if (DIM == 3) {
+        lo[2] = F[NX + NY + lj * TX + li];
+        hi[2] = F[NX + NY + TX * TY + lj * TX + li];
+    }
+    double d1 = 0.0, d2 = 0.0;
+#pragma unroll
+    for (int a = 0; a < DIM; a++) {
+        double t1, t2;
+        if (AXI && a == 0) {
+            const double ri = A.r0 + (i + 0.5) * A.h;
+            const double wl = ri - 0.5 * A.h, wh = ri + 0.5 * A.h, s = 1.0 / (ri * A.h);
+            t1 = (wh * hi[0].x - wl * lo[0].x) * s;
+            t2 = (wh * hi[0].y - wl * lo[0].y) * s;
+        } else {
+            t1 = (hi[a].x - lo[a].x) * A.inv_h;
+            t2 = (hi[a].y - lo[a].y) * A.inv_h;
+        }
+        d1 = a == 0 ? t1 : d1 + t1;
+        d2 = a == 0 ? t2 : d2 + t2;
+    }
+    const double Cc = A.C[c];
+    A.E1o[c] = A.E1[c] + A.dt * Cc * d1;
+    A.E2o[c] = A.E2[c] + A.dt * (1.0 - Cc) * d2;
+}
+
 }  // namespace cmg

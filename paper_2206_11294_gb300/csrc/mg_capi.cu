@@ -1499,12 +1499,12 @@ bool device_ptr(const void *p) {
 }
 
 mg_status check_phase(const mg_phase &P) {
-    const double v[7] = {P.Gamma, P.Pi, P.b, P.q, P.cp, P.cv, P.k};
+    const double v[8] = {P.Gamma, P.Pi, P.b, P.q, P.cp, P.cv, P.k, P.mu};
     for (double x : v)
         if (!std::isfinite(x)) return fail(MG_ERR_INVALID_ARG, "phase parameters must be finite");
     if (!(P.Gamma > 1.0)) return fail(MG_ERR_INVALID_ARG, "phase Gamma must be > 1");
     if (!(P.cv > 0.0) || !(P.cp > P.cv)) return fail(MG_ERR_INVALID_ARG, "phase heat capacities need cp > cv > 0");
-    if (P.b < 0.0 || P.k < 0.0) return fail(MG_ERR_INVALID_ARG, "phase b and k must be >= 0");
+    if (P.b < 0.0 || P.k < 0.0 || P.mu < 0.0) return fail(MG_ERR_INVALID_ARG, "phase b, k and mu must be >= 0");
     return MG_OK;
 }
 
@@ -1623,6 +1623,66 @@ mg_status mg_correct_async(const mg_grid *grid, double dt, double sigma, const d
     cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
     if (dim == 3) k_correct<3><<<gr, kBlock, 0, cs>>>(A);
     else k_correct<2><<<gr, kBlock, 0, cs>>>(A);
+    CK(cudaGetLastError());
+    return MG_OK;
+}
+
+mg_status mg_energy_async(const mg_grid *grid, const mg_phase phases[2], double dt, const double *x, const double *C,
+                          const double *p1, const double *p2, const double *const uf[3], const double *E1,
+                          const double *E2, double *E1_out, double *E2_out, void *stream) {
+    mg_status st = check_grid_geom(grid);
+    if (st) return st;
+    if (!phases || !uf) return fail(MG_ERR_INVALID_ARG, "phases and uf must not be NULL");
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(MG_ERR_INVALID_ARG, "dt must be positive and finite");
+    for (int q = 0; q < 2; q++)
+        if ((st = check_phase(phases[q]))) return st;
+    const int dim = grid->dim;
+    bool ok = device_ptr(x) && device_ptr(C) && device_ptr(p1) && device_ptr(p2) && device_ptr(E1) &&
+              device_ptr(E2) && device_ptr(E1_out) && device_ptr(E2_out);
+    for (int a = 0; a < dim; a++) ok = ok && device_ptr(uf[a]);
+    if (!ok) return fail(MG_ERR_INVALID_ARG, "every array must be a device pointer of the current device");
+    if (!aligned16(x)) return fail(MG_ERR_INVALID_ARG, "x must be 16-byte aligned");
+    bool alias = E1_out == E2_out || E1_out == E2 || E2_out == E1;
+    for (const double *o : {(const double *)E1_out, (const double *)E2_out}) {
+        alias = alias || o == x || o == C || o == p1 || o == p2;
+        for (int a = 0; a < dim; a++) alias = alias || o == uf[a];
+    }
+    if (alias) return fail(MG_ERR_INVALID_ARG, "E1_out and E2_out may alias only their own phase's input");
+    EnergyArgs A;
+    std::memset(&A, 0, sizeof(A));
+    for (int a = 0; a < 3; a++) {
+        A.n[a] = grid->n[a];
+        for (int sd = 0; sd < 2; sd++) {
+            A.dir[a][sd] = a < dim && grid->bc[a][sd] == MG_BC_DIRICHLET;
+            A.gT[a][sd] = a < dim ? grid->bc_T[a][sd] : 0.0;
+            A.gp[a][sd] = a < dim ? grid->bc_p[a][sd] : 0.0;
+        }
+    }
+    A.r0 = grid->r0;
+    A.h = grid->h;
+    A.inv_h = 1.0 / grid->h;
+    A.half_inv_h = 0.5 / grid->h;
+    A.two_inv_h = 2.0 / grid->h;
+    A.dt = dt;
+    for (int q = 0; q < 2; q++) {
+        A.k[q] = phases[q].k;
+        A.mu[q] = phases[q].mu;
+    }
+    A.x = reinterpret_cast<const double2 *>(x);
+    A.C = C;
+    A.p1 = p1;
+    A.p2 = p2;
+    for (int a = 0; a < dim; a++) A.uf[a] = uf[a];
+    A.E1 = E1;
+    A.E2 = E2;
+    A.E1o = E1_out;
+    A.E2o = E2_out;
+    const dim3 gr((unsigned)((grid->n[0] + kBX - 1) / kBX), (unsigned)((grid->n[1] + kBY - 1) / kBY),
+                  (unsigned)(dim == 3 ? grid->n[2] : 1));
+    cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+    if (dim == 3) k_energy<3, false, kBX, kBY><<<gr, kBlock, 0, cs>>>(A);
+    else if (grid->axisym) k_energy<2, true, kBX, kBY><<<gr, kBlock, 0, cs>>>(A);
+    else k_energy<2, false, kBX, kBY><<<gr, kBlock, 0, cs>>>(A);
     CK(cudaGetLastError());
     return MG_OK;
 }

@@ -271,3 +271,137 @@ def test_full_size_mixed_solve_converges(torch_cuda, inner):
     for f in range(2):
         err = np.linalg.norm((xs["mixed"] - x0)[:, f] - dev[:, f]) / np.linalg.norm(dev[:, f])
         assert err <= 1e-8, (f, err)
+
+
+# ---------------------------------------------------------------- Eq. 39
+def _energy_case(torch, orc, g, seed):
+    """The state, its assembled guess plus noise as the solution, and the corrected velocity and phase pressures
+    (both from the oracle, so the energy step is compared on its own)."""
+    s = _state(g, seed=seed)
+    ref = orc.assemble(g, s.ph1, s.ph2, s.dt, s.C, s.m1, s.m2, s.E, s.mom, s.uf)
+    rng = np.random.default_rng(seed)
+    x = ref["x0"] + rng.normal(0, 1.0, ref["x0"].shape) * np.array([1.0, 300.0])
+    rc = orc.correct(g, s.dt, s.sigma, x, s.C, s.kappa, ref["fa"], s.uf)
+    rho1, rho2 = I.phase_density(s.T, s.p, s.ph1), I.phase_density(s.T, s.p, s.ph2)
+    E1 = s.C * I.phase_energy(s.p, rho1, s.ph1)
+    E2 = (1 - s.C) * I.phase_energy(s.p, rho2, s.ph2)
+    return s, x, rc, E1, E2
+
+
+def _flux_bound(g, ph, p, T, uf, dt):
+    """64 ulps of the largest face term, through the divergence: the increment is a difference of face fluxes of
+    size p u, mu u^2 / h and k T / h, evaluated in another order of operations than the oracle's."""
+    U = max(float(np.abs(u).max()) for u in uf)
+    P = max(float(np.abs(p).max()), max(abs(v) for s in g.bcp for v in s))
+    Tm = max(float(np.abs(T).max()), max(abs(v) for s in g.bcT for v in s))
+    F = P * U + ph.mu * 8 * U * U / g.h + ph.k * 4 * Tm / g.h
+    return 64 * EPS * dt * 4 * g.dim * F / g.h
+
+
+def _gpu_energy(torch, g, s, x, rc, E1, E2, in_place=False):
+    from paper_2206_11294_gb300 import binding as B
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+    e1, e2 = T(E1), T(E2)
+    o1, o2 = (e1, e2) if in_place else (torch.empty_like(e1), torch.empty_like(e2))
+    B.energy(g, (s.ph1, s.ph2), s.dt, T(x), T(s.C), T(rc["p1"]), T(rc["p2"]), [T(u) for u in rc["uf"]], e1, e2, o1, o2)
+    torch.cuda.synchronize()
+    return o1.cpu().numpy(), o2.cpu().numpy()
+
+
+@pytest.mark.parametrize("name", list(GRIDS))
+def test_energy_matches_oracle(torch_cuda, orc, name):
+    g = GRIDS[name]
+    s, x, rc, E1, E2 = _energy_case(torch_cuda, orc, g, 31)
+    Z = np.zeros_like(E1)
+    T = x[:, 0].reshape(E1.shape)
+    ref = orc.energy(g, s.ph1, s.ph2, s.dt, s.C, rc["p1"], rc["p2"], T, rc["uf"], Z, Z)
+    got1, got2 = _gpu_energy(torch_cuda, g, s, x, rc, Z, Z)
+    for got, r, ph, p in ((got1, ref["E1"], s.ph1, rc["p1"]), (got2, ref["E2"], s.ph2, rc["p2"])):
+        assert np.abs(r).max() > 0
+        bound = _flux_bound(g, ph, p, T, rc["uf"], s.dt)
+        _close(got, r, 1.0, scale=bound + 1e-12 * np.abs(r), what=f"dE {name}")
+    # with the advected energies, in place
+    ref = orc.energy(g, s.ph1, s.ph2, s.dt, s.C, rc["p1"], rc["p2"], T, rc["uf"], E1, E2)
+    got1, got2 = _gpu_energy(torch_cuda, g, s, x, rc, E1, E2, in_place=True)
+    for got, r, ph, p, E in ((got1, ref["E1"], s.ph1, rc["p1"], E1), (got2, ref["E2"], s.ph2, rc["p2"], E2)):
+        bound = _flux_bound(g, ph, p, T, rc["uf"], s.dt) + 4 * EPS * np.abs(E)
+        _close(got, r, 1.0, scale=bound + 1e-12 * np.abs(r - E), what=f"E {name}")
+
+
+def test_energy_conservative_with_walls(torch_cuda, orc):
+    """Walls all round: the volume sum of div F_i is zero up to rounding (each face flux is one value for its two
+    cells, including the faces on the edge of a thread block's tile)."""
+    g = GRIDS["2d_walls"]
+    s, x, rc, _, _ = _energy_case(torch_cuda, orc, g, 32)
+    s.C = np.full_like(s.C, 0.5)
+    Z = np.zeros_like(s.C)
+    got1, got2 = _gpu_energy(torch_cuda, g, s, x, rc, Z, Z)
+    T = x[:, 0].reshape(Z.shape)
+    for got, ph, p in ((got1, s.ph1, rc["p1"]), (got2, s.ph2, rc["p2"])):
+        div = got / (0.5 * s.dt)
+        per_cell = _flux_bound(g, ph, p, T, rc["uf"], s.dt) / (0.5 * s.dt)
+        assert np.abs(div).max() > 1e3 * per_cell
+        assert abs(div.sum()) <= per_cell * np.sqrt(g.N), (div.sum(), per_cell)
+
+
+def test_energy_full_size_matches_oracle(torch_cuda, orc):
+    """The 16-bubble 1024^2 state through the whole step on the device: assemble, solve, correct, energy; the
+    energy against the oracle's on the device's own solution and corrected fields."""
+    from paper_2206_11294_gb300 import binding as B
+    from paper_2206_11294_gb300.binding import Solver
+    torch = torch_cuda
+    s = I.bubbles_state_1024()
+    g = s.grid
+    got, d, out = _gpu_assemble(torch, s)
+    solver = Solver(g, rtol=1e-10)
+    solver.set_coeffs(out["lam"], out["fa"], out["fk"])
+    x = out["x0"].clone()
+    st = solver.solve(out["b"], x)
+    assert st["status"] == "MG_OK"
+    uo = [torch.empty_like(u) for u in d["uf"]]
+    p1, p2 = torch.empty_like(d["C"]), torch.empty_like(d["C"])
+    B.correct(g, s.dt, s.sigma, x, d["C"], d["kappa"], out["fa"], d["uf"], uo, p1, p2)
+    rho1, rho2 = I.phase_density(s.T, s.p, s.ph1), I.phase_density(s.T, s.p, s.ph2)
+    E1 = s.C * I.phase_energy(s.p, rho1, s.ph1)
+    E2 = (1 - s.C) * I.phase_energy(s.p, rho2, s.ph2)
+    e1, e2 = (torch.from_numpy(E1).cuda(), torch.from_numpy(E2).cuda())
+    o1, o2 = torch.empty_like(e1), torch.empty_like(e2)
+    B.energy(g, (s.ph1, s.ph2), s.dt, x, d["C"], p1, p2, uo, e1, e2, o1, o2)
+    torch.cuda.synchronize()
+    xh = x.cpu().numpy()
+    T = xh[:, 0].reshape(E1.shape)
+    ufh = [u.cpu().numpy() for u in uo]
+    p1h, p2h = p1.cpu().numpy(), p2.cpu().numpy()
+    ref = orc.energy(g, s.ph1, s.ph2, s.dt, s.C, p1h, p2h, T, ufh, E1, E2)
+    for got, r, ph, p, E in ((o1, ref["E1"], s.ph1, p1h, E1), (o2, ref["E2"], s.ph2, p2h, E2)):
+        bound = _flux_bound(g, ph, p, T, ufh, s.dt) + 4 * EPS * np.abs(E)
+        _close(got.cpu().numpy(), r, 1.0, scale=bound + 1e-12 * np.abs(r - E), what="E full size")
+    solver.close()
+
+
+def test_energy_invalid_arguments_rejected(torch_cuda, orc):
+    from paper_2206_11294_gb300 import binding as B
+    from paper_2206_11294_gb300.binding import MgError, MG_ERR_INVALID_ARG
+    import dataclasses
+    torch = torch_cuda
+    g = GRIDS["2d_walls"]
+    s, x, rc, E1, E2 = _energy_case(torch, orc, g, 33)
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+    xd, Cd, p1, p2, uf = T(x), T(s.C), T(rc["p1"]), T(rc["p2"]), [T(u) for u in rc["uf"]]
+    e1, e2 = T(E1), T(E2)
+    o1, o2 = torch.zeros_like(e1), torch.zeros_like(e2)
+    bad = dataclasses.replace(s.ph1, mu=-1.0)
+    cases = [
+        dict(dt=-1.0),
+        dict(phases=(bad, s.ph2)),
+        dict(o1=p1),                 # an output over a neighbour-read input
+        dict(o1=o2),
+        dict(o1=e2),
+    ]
+    for c in cases:
+        with pytest.raises(MgError) as e:
+            B.energy(g, c.get("phases", (s.ph1, s.ph2)), c.get("dt", s.dt), xd, Cd, p1, p2, uf, e1, e2,
+                     c.get("o1", o1), o2)
+        assert e.value.status == MG_ERR_INVALID_ARG
+    torch.cuda.synchronize()
+    assert float(o1.abs().sum()) == 0.0 and float(o2.abs().sum()) == 0.0
