@@ -597,6 +597,64 @@ def run_timestep(args):
             "l2": "flushed between steps", "clocks": clk, "data": "synthetic (seeded advected state, NASG water / air)"}
 
 
+def run_momentum(args):
+    """The implicit momentum predictor on the 16-bubble 1024^2 state: rho = m1 + m2, mu = C mu_1 + (1 - C) mu_2,
+    R = (rho u)^(adv) / dt, from u^(adv) to rtol 1e-10, at the time step's dt (1e-7) and at dt = 1e-3, where
+    viscosity dominates in the gas (mu dt / (rho h^2) ~ 16).  Set-up (coefficients, hierarchy) and solve per step,
+    L2 flushed between steps."""
+    import numpy as np
+    import torch
+    from paper_2206_11294_gb300 import inputs as I
+    from paper_2206_11294_gb300.binding import Momentum
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    s = I.bubbles_state_1024()
+    g = s.grid
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+    rho_h = s.m1 + s.m2
+    rho, mu = T(rho_h), T(s.C * s.ph1.mu + (1 - s.C) * s.ph2.mu)
+    u0 = [T(m_ / rho_h) for m_ in s.mom]
+    u = [torch.empty_like(v) for v in u0]
+    m = Momentum(g, precision=args.precision, stream=stream)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    out = {"workload": "momentum predictor, bubbles16_1024x1024: set-up + solve to 1e-10 from u^(adv)",
+           "metric": "momentum solves/s", "cells": g.N, "precision": args.precision, "regimes": []}
+    for dt in (1e-7, 1e-3):
+        R = [T(m_ / dt) for m_ in s.mom]
+        stats = []
+
+        def step():
+            m.set_coeffs(dt, rho, mu)
+            for a in range(g.dim):
+                u[a].copy_(u0[a])
+            stats.append(m.solve(R, u, rtol=1e-10, max_iters=200))
+
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        stats.clear()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        clocks = ClockSampler(gpu_identity(torch, 0))
+        ms = 0.0
+        for _ in range(args.steps):
+            flush.zero_()
+            e0.record(stream)
+            step()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms += e0.elapsed_time(e1)
+        clk = clocks.stop()
+        ms /= args.steps
+        out["regimes"].append({"dt": dt, "solves_per_s": 1e3 / ms, "ms_per_solve": ms,
+                               "iterations": stats[0]["iterations"], "cycles": stats[0]["cycles"],
+                               "rfinal_over_r0": stats[0]["rfinal"] / stats[0]["r0"] if stats[0]["r0"] else 0.0,
+                               "clocks": clk})
+    m.close()
+    out["l2"] = "flushed between steps"
+    out["data"] = "synthetic (seeded advected state, NASG water / air, mu 8.5e-4 / 1.85e-5 Pa s)"
+    return out
+
+
 def run_serve(args):
     """Poisson arrivals of mixed 2D (128..1024) and 3D (64..160) bubble solves,
     mixed precision, admitted against an HBM budget; p50/p99 per arrival rate."""
@@ -690,7 +748,7 @@ def main():
     ap.add_argument("--no-tune", action="store_true", help="library default kernel choices, no autotuning")
     ap.add_argument("--tune-reps", type=int, default=5)
     ap.add_argument("--tuning-table", default=None, help="JSON table of autotuned choices to apply (and extend)")
-    ap.add_argument("--workload", default="bubbles", choices=["bubbles", "batch", "serve", "wall3d", "timestep"])
+    ap.add_argument("--workload", default="bubbles", choices=["bubbles", "batch", "serve", "wall3d", "timestep", "momentum"])
     ap.add_argument("--n3d", type=int, default=256)
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--serve-rates", type=float, nargs="+", default=[10, 30, 100, 300, 1000, 2000])
@@ -706,7 +764,7 @@ def main():
     if args.workload != "bubbles":
         if rank == 0:
             out = {"batch": run_batch, "serve": run_serve, "wall3d": run_wall3d,
-                   "timestep": run_timestep}[args.workload](args)
+                   "timestep": run_timestep, "momentum": run_momentum}[args.workload](args)
             print(json.dumps(out), flush=True)
         return
     if args.impl == "ours" and world > 1:

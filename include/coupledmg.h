@@ -376,6 +376,70 @@ MG_API mg_status mg_energy_async(const mg_grid *grid, const mg_phase phases[2], 
                                  const double *C, const double *p1, const double *p2, const double *const uf[3],
                                  const double *E1, const double *E2, double *E1_out, double *E2_out, void *stream);
 
+/* ---------------------------------------------------------------------
+ * The implicit momentum predictor (Sec. 3, the equation before Eq. unp1):
+ *   (rho/dt) u - div(mu (grad u + grad u^T)) = R
+ * for the cell-centred velocity u (dim components), with rho and mu the
+ * cells' averaged density and viscosity and R = (rho u)^(adv)/dt - grad p^n +
+ * sigma kappa grad C^{n+1} as the caller forms it.  No bulk viscosity
+ * (Stokes' hypothesis, Sec. 2).  Discretisation, in finite volumes on the
+ * grid of the pressure-temperature solve:
+ *   face stress tau_{ca} = mu_f ((du_c/dx_a)_f + (du_a/dx_c)_f), mu_f the mean
+ *     of the two cells' mu; normal derivatives across the face, tangential
+ *     ones the mean of the two cells' central differences (one-sided in the
+ *     first and last cell);
+ *   walls (MG_BC_WALL): the normal component is zero on the wall (stress
+ *     2 mu 2u/h towards it); tangential components slip freely (no shear), or
+ *     with MG_MOMENTUM_NO_SLIP are zero on the wall too (shear mu 2u/h);
+ *   pressure boundaries (MG_BC_DIRICHLET) and the axis: no stress;
+ *   axisymmetric: r-face stresses weighted by r_f / r_i, and the hoop term
+ *     2 mu u_r / r^2 in the r-row.
+ * Solution: defect correction on the full residual r = R - A(u); each step
+ * solves the component-diagonal part of A (mu weighted 2x on the faces normal
+ * to a component) with the pair multigrid of this library, (u_x, u_y) in one
+ * hierarchy and, in 3D, u_z in a second.  Stopping norm ||dt r / rho||_2 over
+ * all components and cells.
+ * All arrays are device pointers of the handle's device; u, R, y are per
+ * component, [N] each (cells in the layout above).  Not thread-safe.
+ * ------------------------------------------------------------------------- */
+typedef struct mg_momentum mg_momentum;
+
+typedef struct {
+    int iterations;           /* outer defect-correction steps */
+    int cycles;               /* multigrid cycles of the correction solves, in total */
+    double r0, rfinal;        /* stopping norm ||dt r / rho||_2 at the start and at the end */
+    double seconds;           /* wall time of the call */
+    int status;               /* mg_status of the solve */
+} mg_momentum_stats;
+
+enum { MG_MOMENTUM_NO_SLIP = 1 };
+
+/* grid: as for mg_create; flags: 0 or MG_MOMENTUM_NO_SLIP.  inner: options of
+ * the correction solves (NULL: library defaults with one cycle per step); its
+ * rtol is ignored and max_cycles is the number of cycles (MIXED: outer
+ * refinement steps) per correction.  stream: a cudaStream_t for all work. */
+MG_API mg_status mg_momentum_create(const mg_grid *grid, int flags, const mg_options *inner, void *stream,
+                                    mg_momentum **out);
+
+/* Coefficient intake and set-up of the correction hierarchies: rho, mu [N]
+ * (> 0 and >= 0 for a meaningful system; checked only for finiteness through
+ * the hierarchies' set-up: MG_ERR_INVALID_COEFF), dt > 0.  The caller's arrays
+ * are copied and no longer read on return. */
+MG_API mg_status mg_momentum_set_coeffs(mg_momentum *m, double dt, const double *rho, const double *mu);
+
+/* y = A(u), synchronous.  y must not alias u. */
+MG_API mg_status mg_momentum_apply(mg_momentum *m, const double *const u[3], double *const y[3]);
+
+/* Solves A u = R; u in: initial guess, out: solution.  Stops when
+ * ||dt r/rho|| <= rtol ||dt r0/rho|| (rtol <= 0: runs max_iters steps) or
+ * after max_iters steps (MG_ERR_NOT_CONVERGED when rtol > 0; u and stats are
+ * still written).  R must not alias u.  stats may be NULL.  MG_ERR_STATE
+ * before a successful mg_momentum_set_coeffs. */
+MG_API mg_status mg_momentum_solve(mg_momentum *m, const double *const R[3], double *const u[3], double rtol,
+                                   int max_iters, mg_momentum_stats *stats);
+
+MG_API mg_status mg_momentum_destroy(mg_momentum *m);
+
 /* Allocation-free stopping norms (the paper has no counterpart: this is a
  * library service).  For callers that cannot allocate device memory - their
  * device memory is owned by another allocator, or their time loop must not

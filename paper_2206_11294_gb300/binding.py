@@ -33,7 +33,8 @@ EXPORTS = ["mg_default_options", "mg_workspace_size", "mg_create", "mg_set_coeff
            "mg_batch_create", "mg_batch_solve", "mg_batch_counters", "mg_batch_destroy", "mg_set_stream",
            "mg_batch_set_coeffs", "mg_get_tuning", "mg_set_tuning", "mg_autotune", "mg_batch_get_tuning",
            "mg_batch_set_tuning", "mg_batch_autotune", "mg_assemble_async", "mg_correct_async",
-           "mg_energy_async"]
+           "mg_energy_async", "mg_momentum_create", "mg_momentum_set_coeffs", "mg_momentum_apply",
+           "mg_momentum_solve", "mg_momentum_destroy"]
 
 MG_MAX_LEVELS = 32
 MG_SWEEP_COLOUR, MG_SWEEP_FUSED, MG_SWEEP_ASYNC, MG_SWEEP_COLOUR2 = 1, 2, 3, 4
@@ -121,6 +122,15 @@ class MgPhase(C.Structure):
                 ("cp", C.c_double), ("cv", C.c_double), ("k", C.c_double), ("mu", C.c_double)]
 
 
+class MgMomentumStats(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("cycles", C.c_int), ("r0", C.c_double), ("rfinal", C.c_double),
+                ("seconds", C.c_double), ("status", C.c_int)]
+
+    def as_dict(self) -> dict:
+        return dict(iterations=self.iterations, cycles=self.cycles, r0=self.r0, rfinal=self.rfinal,
+                    seconds=self.seconds, status=STATUS_NAMES.get(self.status, self.status))
+
+
 class MgState(C.Structure):
     _fields_ = [("C", C.c_void_p), ("m1", C.c_void_p), ("m2", C.c_void_p), ("E", C.c_void_p),
                 ("mom", C.c_void_p * 3), ("uf", C.c_void_p * 3)]
@@ -181,6 +191,11 @@ def load(path: str = LIB_PATH):
             "mg_correct_async": ([C.POINTER(MgGrid), C.c_double, C.c_double, P, P, P, pa3, pa3, pa3, P, P, P], C.c_int),
             "mg_energy_async": ([C.POINTER(MgGrid), C.POINTER(MgPhase), C.c_double, P, P, P, P, pa3, P, P, P, P, P],
                                 C.c_int),
+            "mg_momentum_create": ([C.POINTER(MgGrid), C.c_int, C.POINTER(MgOptions), P, C.POINTER(P)], C.c_int),
+            "mg_momentum_set_coeffs": ([P, C.c_double, P, P], C.c_int),
+            "mg_momentum_apply": ([P, pa3, pa3], C.c_int),
+            "mg_momentum_solve": ([P, pa3, pa3, C.c_double, C.c_int, C.POINTER(MgMomentumStats)], C.c_int),
+            "mg_momentum_destroy": ([P], C.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -285,6 +300,7 @@ def make_phase(ph) -> MgPhase:
 
 
 MG_ASSEMBLE_LAMBDA4_PRINTED, MG_ASSEMBLE_HARMONIC_K = 1, 2
+MG_MOMENTUM_NO_SLIP = 1
 
 
 def assemble(grid, phases, dt: float, C_, m1, m2, E, mom: Sequence, uf: Sequence, out: dict,
@@ -511,6 +527,66 @@ class Solver:
             self._lib.mg_destroy(self._h)
             self._h = None
         self._ws = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+class Momentum:
+    """mg_momentum: the implicit momentum predictor (rho/dt) u - div(mu (grad u + grad u^T)) = R on one grid.
+    Arrays are contiguous float64 CUDA tensors of the grid's cells, one per velocity component."""
+
+    def __init__(self, grid, no_slip: bool = False, precision="fp64", inner_cycles_per_step: int = 1, nu1=2, nu2=2,
+                 coarse_min=4, device: Optional[int] = None, stream=None):
+        import torch
+        lib = load()
+        self._lib = lib
+        self.grid = make_grid(grid)
+        dev = torch.cuda.current_device() if device is None else int(device)
+        self.device = dev
+        check(lib.mg_set_device(dev))
+        opt = make_options(precision, 0.0, inner_cycles_per_step, nu1, nu2, coarse_min)
+        if stream is None:
+            stream = torch.cuda.current_stream(dev)
+        self.stream = stream
+        handle = C.c_void_p()
+        check(lib.mg_momentum_create(C.byref(self.grid), MG_MOMENTUM_NO_SLIP if no_slip else 0, C.byref(opt),
+                                     C.c_void_p(stream.cuda_stream), C.byref(handle)))
+        self._h = handle
+
+    def _list(self, v):
+        arr = (C.c_void_p * 3)()
+        for a in range(self.grid.dim):
+            arr[a] = _ptr(v[a], True)[0]
+        return arr
+
+    def set_coeffs(self, dt: float, rho, mu) -> None:
+        check(self._lib.mg_momentum_set_coeffs(self._h, float(dt), _ptr(rho, True)[0], _ptr(mu, True)[0]))
+
+    def apply(self, u: Sequence, y: Sequence) -> None:
+        check(self._lib.mg_momentum_apply(self._h, self._list(u), self._list(y)))
+
+    def solve(self, R: Sequence, u: Sequence, rtol: float = 1e-10, max_iters: int = 100,
+              allow_not_converged: bool = False) -> dict:
+        st = MgMomentumStats()
+        allow = (MG_OK, MG_ERR_NOT_CONVERGED) if allow_not_converged else (MG_OK,)
+        check(self._lib.mg_momentum_solve(self._h, self._list(R), self._list(u), float(rtol), int(max_iters),
+                                          C.byref(st)), allow)
+        return st.as_dict()
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.mg_momentum_destroy(self._h)
+            self._h = None
 
     def __del__(self):
         try:

@@ -24,6 +24,7 @@
 #include "mg_tail.cuh"
 #include "mg_async.cuh"
 #include "mg_assemble.cuh"
+#include "mg_momentum.cuh"
 
 using namespace cmg;
 
@@ -1848,6 +1849,359 @@ mg_status mg_destroy(mg_handle *h) {
     delete[] h->tmaps;
     delete[] h->tmap_ok;
     delete h;
+    return MG_OK;
+}
+
+// ---------------------------------------------------------------- momentum predictor
+struct mg_momentum {
+    mg_grid grid;
+    int flags, device;
+    cudaStream_t stream;
+    mg_handle *hA, *hB;                // correction hierarchies: (u_0, u_1) and, in 3D, (u_2, unused)
+    long long N, nblocks;
+    double dt;
+    bool have_coeffs;
+    char *arena;
+    double *rho, *mu;
+    double *r0[3], *delta[3];          // initial residual and accumulated correction, per component
+    double2 *lamA, *lamB, *rA, *rB, *xA, *xB;
+    double *fA[2][3], *fB[3], *fzero[3];
+    double *partial, *norm_d, *norm_h;
+};
+
+namespace {
+mg_grid momentum_inner_grid(const mg_grid &g) {
+    mg_grid gin = g;
+    for (int a = 0; a < 3; a++)
+        for (int sd = 0; sd < 2; sd++) {
+            const int bc = g.bc[a][sd];
+            gin.bc[a][sd] = a >= g.dim ? bc : bc == MG_BC_WALL ? MG_BC_DIRICHLET : bc == MG_BC_AXIS ? MG_BC_AXIS
+                                                                                                 : MG_BC_WALL;
+            gin.bc_T[a][sd] = gin.bc_p[a][sd] = 0.0;
+        }
+    return gin;
+}
+
+dim3 cell_grid(const mg_grid &g) {
+    return dim3((unsigned)((g.n[0] + kBX - 1) / kBX), (unsigned)((g.n[1] + kBY - 1) / kBY),
+                (unsigned)(g.dim == 3 ? g.n[2] : 1));
+}
+
+MomArgs momentum_args(const mg_momentum *m) {
+    MomArgs A;
+    std::memset(&A, 0, sizeof(A));
+    const mg_grid &g = m->grid;
+    for (int a = 0; a < 3; a++) {
+        A.n[a] = g.n[a];
+        for (int sd = 0; sd < 2; sd++) A.wall[a][sd] = a < g.dim && g.bc[a][sd] == MG_BC_WALL;
+    }
+    A.no_slip = (m->flags & MG_MOMENTUM_NO_SLIP) ? 1 : 0;
+    A.r0 = g.r0;
+    A.h = g.h;
+    A.inv_h = 1.0 / g.h;
+    A.half_inv_h = 0.5 / g.h;
+    A.two_inv_h = 2.0 / g.h;
+    A.inv_dt = 1.0 / m->dt;
+    A.dt = m->dt;
+    A.rho = m->rho;
+    A.mu = m->mu;
+    return A;
+}
+
+mg_status launch_momentum(const mg_momentum *m, const MomArgs &A, bool apply) {
+    const dim3 gr = cell_grid(m->grid);
+    cudaStream_t s = m->stream;
+    if (apply) {
+        if (m->grid.dim == 3) k_mom_residual<3, false, true, kBX, kBY><<<gr, kBlock, 0, s>>>(A);
+        else if (m->grid.axisym) k_mom_residual<2, true, true, kBX, kBY><<<gr, kBlock, 0, s>>>(A);
+        else k_mom_residual<2, false, true, kBX, kBY><<<gr, kBlock, 0, s>>>(A);
+    } else {
+        if (m->grid.dim == 3) k_mom_residual<3, false, false, kBX, kBY><<<gr, kBlock, 0, s>>>(A);
+        else if (m->grid.axisym) k_mom_residual<2, true, false, kBX, kBY><<<gr, kBlock, 0, s>>>(A);
+        else k_mom_residual<2, false, false, kBX, kBY><<<gr, kBlock, 0, s>>>(A);
+    }
+    CK(cudaGetLastError());
+    return MG_OK;
+}
+
+// r = R - A(u) into the correction right-hand sides (and into r_out, if given); returns ||dt r / rho||_2 (one
+// host wait).
+mg_status momentum_residual(mg_momentum *m, const double *const R[3], const double *const u[3], double *const r_out[3],
+                            double *norm) {
+    MomArgs A = momentum_args(m);
+    for (int a = 0; a < m->grid.dim; a++) {
+        A.u[a] = u[a];
+        A.R[a] = R[a];
+        A.r_out[a] = r_out ? r_out[a] : nullptr;
+    }
+    A.rA = m->rA;
+    A.rB = m->rB;
+    A.partial = m->partial;
+    mg_status st = launch_momentum(m, A, false);
+    if (st) return st;
+    k_mom_norm<<<1, 1024, 0, m->stream>>>(m->partial, m->nblocks, m->norm_d);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(m->norm_h, m->norm_d, sizeof(double), cudaMemcpyDeviceToHost, m->stream));
+    CK(cudaStreamSynchronize(m->stream));
+    *norm = std::sqrt(m->norm_h[0]);
+    return MG_OK;
+}
+
+bool momentum_ptrs(const mg_momentum *m, const double *const v[3]) {
+    if (!v) return false;
+    for (int a = 0; a < m->grid.dim; a++)
+        if (!device_ptr(v[a])) return false;
+    return true;
+}
+}  // namespace
+
+mg_status mg_momentum_destroy(mg_momentum *m) {
+    if (!m) return MG_OK;
+    DeviceGuard dg(m->device);
+    if (m->stream) cudaStreamSynchronize(m->stream);
+    mg_destroy(m->hA);
+    mg_destroy(m->hB);
+    if (m->arena) cudaFree(m->arena);
+    if (m->norm_h) cudaFreeHost(m->norm_h);
+    delete m;
+    return MG_OK;
+}
+
+mg_status mg_momentum_create(const mg_grid *grid, int flags, const mg_options *inner, void *stream,
+                             mg_momentum **out) {
+    if (!out) return fail(MG_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    mg_status st = check_grid_geom(grid);
+    if (st) return st;
+    if (flags & ~MG_MOMENTUM_NO_SLIP) return fail(MG_ERR_INVALID_ARG, "unknown momentum flags");
+    mg_options opt;
+    if (inner) {
+        opt = *inner;
+    } else {
+        mg_default_options(&opt);
+        opt.max_cycles = 1;
+    }
+    if (opt.max_cycles < 1) return fail(MG_ERR_INVALID_ARG, "inner max_cycles must be >= 1");
+    opt.rtol = 0.0;
+    const mg_grid gin = momentum_inner_grid(*grid);
+    mg_momentum *m = new (std::nothrow) mg_momentum;
+    if (!m) return fail(MG_ERR_OOM, "host allocation failed");
+    std::memset(m, 0, sizeof(*m));
+    m->grid = *grid;
+    m->flags = flags;
+    m->stream = reinterpret_cast<cudaStream_t>(stream);
+    cudaGetDevice(&m->device);
+    const int dim = grid->dim;
+    if ((st = mg_create(&gin, &opt, nullptr, 0, stream, &m->hA)) ||
+        (dim == 3 && (st = mg_create(&gin, &opt, nullptr, 0, stream, &m->hB)))) {
+        const std::string msg = g_err;
+        mg_momentum_destroy(m);
+        return fail(st, msg);
+    }
+    m->N = (long long)grid->n[0] * grid->n[1] * grid->n[2];
+    const dim3 gr = cell_grid(*grid);
+    m->nblocks = (long long)gr.x * gr.y * gr.z;
+    long long nf[3] = {0, 0, 0};
+    for (int a = 0; a < dim; a++)
+        nf[a] = (long long)(grid->n[0] + (a == 0)) * (grid->n[1] + (a == 1)) * (grid->n[2] + (a == 2));
+    // one arena: offsets rounded to 256 bytes
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off += (bytes + 255) & ~size_t(255);
+        return o;
+    };
+    const size_t N = (size_t)m->N;
+    const size_t o_rho = take(N * 8), o_mu = take(N * 8), o_lamA = take(N * 32), o_rA = take(N * 16),
+                 o_xA = take(N * 16);
+    size_t o_r0[3] = {}, o_d[3] = {};
+    for (int a = 0; a < dim; a++) {
+        o_r0[a] = take(N * 8);
+        o_d[a] = take(N * 8);
+    }
+    const size_t o_lamB = dim == 3 ? take(N * 32) : 0, o_rB = dim == 3 ? take(N * 16) : 0,
+                 o_xB = dim == 3 ? take(N * 16) : 0;
+    size_t o_f[4][3] = {};
+    for (int q = 0; q < (dim == 3 ? 4 : 2); q++)
+        for (int a = 0; a < dim; a++) o_f[q][a] = take((size_t)nf[a] * 8);
+    const size_t o_part = take((size_t)m->nblocks * 8), o_norm = take(8);
+    DeviceGuard dg(m->device);
+    if (cudaMalloc(&m->arena, off) != cudaSuccess || cudaMallocHost(&m->norm_h, sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        mg_momentum_destroy(m);
+        return fail(MG_ERR_OOM, "device allocation failed");
+    }
+    auto at = [&](size_t o) { return m->arena + o; };
+    m->rho = reinterpret_cast<double *>(at(o_rho));
+    m->mu = reinterpret_cast<double *>(at(o_mu));
+    m->lamA = reinterpret_cast<double2 *>(at(o_lamA));
+    m->rA = reinterpret_cast<double2 *>(at(o_rA));
+    m->xA = reinterpret_cast<double2 *>(at(o_xA));
+    for (int a = 0; a < dim; a++) {
+        m->r0[a] = reinterpret_cast<double *>(at(o_r0[a]));
+        m->delta[a] = reinterpret_cast<double *>(at(o_d[a]));
+    }
+    if (dim == 3) {
+        m->lamB = reinterpret_cast<double2 *>(at(o_lamB));
+        m->rB = reinterpret_cast<double2 *>(at(o_rB));
+        m->xB = reinterpret_cast<double2 *>(at(o_xB));
+    }
+    for (int a = 0; a < dim; a++) {
+        m->fA[0][a] = reinterpret_cast<double *>(at(o_f[0][a]));
+        m->fA[1][a] = reinterpret_cast<double *>(at(o_f[1][a]));
+        if (dim == 3) {
+            m->fB[a] = reinterpret_cast<double *>(at(o_f[2][a]));
+            m->fzero[a] = reinterpret_cast<double *>(at(o_f[3][a]));
+            CK(cudaMemsetAsync(m->fzero[a], 0, (size_t)nf[a] * 8, m->stream));
+        }
+    }
+    m->partial = reinterpret_cast<double *>(at(o_part));
+    m->norm_d = reinterpret_cast<double *>(at(o_norm));
+    CK(cudaStreamSynchronize(m->stream));
+    *out = m;
+    return MG_OK;
+}
+
+mg_status mg_momentum_set_coeffs(mg_momentum *m, double dt, const double *rho, const double *mu) {
+    if (!m) return fail(MG_ERR_INVALID_ARG, "momentum handle is NULL");
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(MG_ERR_INVALID_ARG, "dt must be positive and finite");
+    DeviceGuard dg(m->device);
+    if (!device_ptr(rho) || !device_ptr(mu))
+        return fail(MG_ERR_INVALID_ARG, "rho and mu must be device pointers of the handle's device");
+    m->have_coeffs = false;
+    const mg_grid &g = m->grid;
+    const int dim = g.dim;
+    MomCoeffArgs A;
+    std::memset(&A, 0, sizeof(A));
+    for (int a = 0; a < 3; a++) {
+        A.n[a] = g.n[a];
+        for (int sd = 0; sd < 2; sd++) A.wall[a][sd] = a < dim && g.bc[a][sd] == MG_BC_WALL;
+    }
+    A.no_slip = (m->flags & MG_MOMENTUM_NO_SLIP) ? 1 : 0;
+    A.r0 = g.r0;
+    A.h = g.h;
+    A.inv_dt = 1.0 / dt;
+    A.rho = rho;
+    A.mu = mu;
+    A.rho_o = m->rho;
+    A.mu_o = m->mu;
+    A.lamA = m->lamA;
+    A.lamB = m->lamB;
+    for (int a = 0; a < dim; a++) {
+        A.fA[0][a] = m->fA[0][a];
+        A.fA[1][a] = m->fA[1][a];
+        A.fB[a] = m->fB[a];
+    }
+    const dim3 gr = cell_grid(g);
+    if (dim == 3) k_mom_coeffs<3, false><<<gr, kBlock, 0, m->stream>>>(A);
+    else if (g.axisym) k_mom_coeffs<2, true><<<gr, kBlock, 0, m->stream>>>(A);
+    else k_mom_coeffs<2, false><<<gr, kBlock, 0, m->stream>>>(A);
+    CK(cudaGetLastError());
+    const double *faA[3] = {m->fA[1][0], m->fA[1][1], m->fA[1][2]};
+    const double *fkA[3] = {m->fA[0][0], m->fA[0][1], m->fA[0][2]};
+    mg_status st = mg_set_coeffs(m->hA, reinterpret_cast<const double *>(m->lamA), faA, fkA, 1);
+    if (st) return st;
+    if (dim == 3) {
+        const double *faB[3] = {m->fzero[0], m->fzero[1], m->fzero[2]};
+        const double *fkB[3] = {m->fB[0], m->fB[1], m->fB[2]};
+        if ((st = mg_set_coeffs(m->hB, reinterpret_cast<const double *>(m->lamB), faB, fkB, 1))) return st;
+    }
+    m->dt = dt;
+    m->have_coeffs = true;
+    return MG_OK;
+}
+
+mg_status mg_momentum_apply(mg_momentum *m, const double *const u[3], double *const y[3]) {
+    if (!m) return fail(MG_ERR_INVALID_ARG, "momentum handle is NULL");
+    if (!m->have_coeffs) return fail(MG_ERR_STATE, "mg_momentum_set_coeffs has not succeeded on this handle");
+    DeviceGuard dg(m->device);
+    if (!momentum_ptrs(m, u) || !momentum_ptrs(m, y))
+        return fail(MG_ERR_INVALID_ARG, "u and y must be device pointers of the handle's device");
+    for (int a = 0; a < m->grid.dim; a++)
+        for (int b = 0; b < m->grid.dim; b++)
+            if (y[a] == u[b]) return fail(MG_ERR_INVALID_ARG, "y must not alias u");
+    MomArgs A = momentum_args(m);
+    for (int a = 0; a < m->grid.dim; a++) {
+        A.u[a] = u[a];
+        A.y[a] = y[a];
+    }
+    mg_status st = launch_momentum(m, A, true);
+    if (st) return st;
+    CK(cudaStreamSynchronize(m->stream));
+    return MG_OK;
+}
+
+mg_status mg_momentum_solve(mg_momentum *m, const double *const R[3], double *const u[3], double rtol, int max_iters,
+                            mg_momentum_stats *stats) {
+    if (!m) return fail(MG_ERR_INVALID_ARG, "momentum handle is NULL");
+    if (!m->have_coeffs) return fail(MG_ERR_STATE, "mg_momentum_set_coeffs has not succeeded on this handle");
+    if (!std::isfinite(rtol) || max_iters < 0) return fail(MG_ERR_INVALID_ARG, "rtol must be finite, max_iters >= 0");
+    DeviceGuard dg(m->device);
+    if (!momentum_ptrs(m, R) || !momentum_ptrs(m, u))
+        return fail(MG_ERR_INVALID_ARG, "R and u must be device pointers of the handle's device");
+    const int dim = m->grid.dim;
+    for (int a = 0; a < dim; a++)
+        for (int b = 0; b < dim; b++)
+            if (R[a] == u[b]) return fail(MG_ERR_INVALID_ARG, "R must not alias u");
+    const auto t0 = std::chrono::steady_clock::now();
+    // Correction form: r0 = R - A(u0) once, then r = r0 - A(delta) and u = u0 + delta at the end.  Forming
+    // R - A(u) at every step would stall at the rounding of R (rho u / dt), far above the residual when dt is
+    // small and u0 is close to the solution.
+    const double *uc[3] = {u[0], dim > 1 ? u[1] : nullptr, dim > 2 ? u[2] : nullptr};
+    const double *r0c[3] = {m->r0[0], m->r0[1], m->r0[2]};
+    const double *dc[3] = {m->delta[0], m->delta[1], m->delta[2]};
+    double r0 = 0.0, r = 0.0;
+    mg_status st = momentum_residual(m, R, uc, m->r0, &r0);
+    if (st) return st;
+    for (int a = 0; a < dim; a++) CK(cudaMemsetAsync(m->delta[a], 0, (size_t)m->N * 8, m->stream));
+    if (!std::isfinite(r0)) return fail(MG_ERR_INVALID_COEFF, "non-finite momentum residual");
+    r = r0;
+    int it = 0, cycles = 0;
+    mg_status result = MG_OK;
+    for (;;) {
+        if (r == 0.0 || (rtol > 0.0 && r <= rtol * r0)) break;
+        if (it >= max_iters) {
+            result = rtol > 0.0 ? MG_ERR_NOT_CONVERGED : MG_OK;
+            break;
+        }
+        CK(cudaMemsetAsync(m->xA, 0, (size_t)m->N * 16, m->stream));
+        mg_stats sa;
+        if ((st = mg_solve(m->hA, reinterpret_cast<const double *>(m->rA), reinterpret_cast<double *>(m->xA), 1, &sa)))
+            return st;
+        cycles += sa.cycles;
+        if (dim == 3) {
+            CK(cudaMemsetAsync(m->xB, 0, (size_t)m->N * 16, m->stream));
+            if ((st = mg_solve(m->hB, reinterpret_cast<const double *>(m->rB), reinterpret_cast<double *>(m->xB), 1,
+                               &sa)))
+                return st;
+            cycles += sa.cycles;
+        }
+        const int blocks = (int)std::min<long long>((m->N + 255) / 256, 152LL * 16);
+        double *const *d = m->delta;
+        if (dim == 3) k_mom_update<3><<<blocks, 256, 0, m->stream>>>(m->N, m->xA, m->xB, d[0], d[1], d[2]);
+        else k_mom_update<2><<<blocks, 256, 0, m->stream>>>(m->N, m->xA, m->xB, d[0], d[1], nullptr);
+        CK(cudaGetLastError());
+        if ((st = momentum_residual(m, r0c, dc, nullptr, &r))) return st;
+        it++;
+        if (!std::isfinite(r)) return fail(MG_ERR_INVALID_COEFF, "non-finite momentum residual");
+    }
+    if (it > 0) {
+        const int blocks = (int)std::min<long long>((m->N + 255) / 256, 152LL * 16);
+        double *const *d = m->delta;
+        if (dim == 3) k_mom_add<3><<<blocks, 256, 0, m->stream>>>(m->N, d[0], d[1], d[2], u[0], u[1], u[2]);
+        else k_mom_add<2><<<blocks, 256, 0, m->stream>>>(m->N, d[0], d[1], nullptr, u[0], u[1], nullptr);
+        CK(cudaGetLastError());
+        CK(cudaStreamSynchronize(m->stream));
+    }
+    if (stats) {
+        stats->iterations = it;
+        stats->cycles = cycles;
+        stats->r0 = r0;
+        stats->rfinal = r;
+        stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        stats->status = result;
+    }
+    if (result) return fail(result, "momentum solve did not reach rtol in max_iters steps");
     return MG_OK;
 }
 

@@ -1,0 +1,298 @@
+// The implicit momentum predictor (Sec. 3, the equation before Eq. unp1):
+//   (rho/dt) u - div(mu (grad u + grad u^T)) = R
+// per cell and component, with rho, mu the cells' averaged density and
+// viscosity.  Solved by defect correction: the full residual r = R - A(u)
+// (k_mom_residual) drives a correction solve with the component-diagonal part
+// of A - (rho/dt) u_c - div(mu_c,a grad u_c), mu_c,a = 2 mu on the faces
+// normal to component c and mu on the others - on the pair multigrid of the
+// pressure-temperature solve (two components per hierarchy, coupling
+// coefficients lambda_2 = lambda_4 = 0).  The cross terms div(mu grad u^T)
+// off the diagonal are the difference the outer loop removes.
+//
+// Boundary faces: walls hold the normal component at zero (a Dirichlet face
+// of the inner grid with coefficient 2 mu) and let the tangential ones slip
+// (coefficient 0: no shear) or, with no-slip, hold them at zero too
+// (coefficient mu); pressure boundaries and the axis pass no stress.  On
+// axisymmetric grids the r-row has the hoop term 2 mu u_r / r^2.
+// Tangential derivatives on a face are the mean of the two cells' central
+// differences (one-sided in the first and last cell).
+#pragma once
+#include "mg_assemble.cuh"
+
+namespace cmg {
+
+struct MomCoeffArgs {
+    int n[3];
+    int wall[3][2];          // wall faces (normal component held at zero)
+    int no_slip;
+    double r0, h, inv_dt;
+    const double *rho, *mu;
+    double *rho_o, *mu_o;    // owned copies for the residual
+    double2 *lamA, *lamB;    // [N][2 pairs] of the inner hierarchies (B: 3D, component z)
+    double *fA[2][3];        // face coefficients of components 0 and 1 (inner T and p slots)
+    double *fB[3];           // component 2 (3D)
+};
+
+template <int DIM, bool AXI>
+__global__ void __launch_bounds__(256) k_mom_coeffs(const __grid_constant__ MomCoeffArgs A) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = DIM == 3 ? (int)blockIdx.z : 0;
+    if (i >= A.n[0] || j >= A.n[1]) return;
+    const int n0 = A.n[0], n1 = A.n[1];
+    const long long c = (long long)i + (long long)n0 * ((long long)j + (long long)n1 * k);
+    const double rho = A.rho[c], mu = A.mu[c];
+    A.rho_o[c] = rho;
+    A.mu_o[c] = mu;
+    const double m = -rho * A.inv_dt;
+    double l0 = m;
+    if (AXI) {
+        const double ri = A.r0 + (i + 0.5) * A.h;
+        l0 = m - 2.0 * mu / (ri * ri);                      // hoop term of the r-row
+    }
+    A.lamA[2 * c] = make_double2(l0, 0.0);
+    A.lamA[2 * c + 1] = make_double2(m, 0.0);
+    if (DIM == 3) {
+        A.lamB[2 * c] = make_double2(m, 0.0);
+        A.lamB[2 * c + 1] = make_double2(m, 0.0);           // unused slot: p = 0 for a zero right-hand side
+    }
+#pragma unroll
+    for (int a = 0; a < DIM; a++) {
+        const int pos[3] = {i, j, k};
+#pragma unroll
+        for (int sd = 0; sd < 2; sd++) {
+            const int fpos = pos[a] + sd;
+            if (sd == 1 && fpos != A.n[a]) continue;
+            const bool edge = fpos == 0 || fpos == A.n[a];
+            double base[3];
+            if (edge) {
+                const int side = fpos == 0 ? 0 : 1;
+                const bool w = A.wall[a][side] != 0;
+#pragma unroll
+                for (int q = 0; q < DIM; q++) base[q] = w && (q == a || A.no_slip) ? mu : 0.0;
+            } else {
+                const long long cn = c - (a == 0 ? 1LL : a == 1 ? (long long)n0 : (long long)n0 * n1);
+                const double mf = 0.5 * (mu + A.mu[cn]);
+#pragma unroll
+                for (int q = 0; q < DIM; q++) base[q] = mf;
+            }
+            const long long f = face_index(A.n, a, pos[0] + (a == 0 ? sd : 0), pos[1] + (a == 1 ? sd : 0),
+                                           pos[2] + (a == 2 ? sd : 0));
+            A.fA[0][a][f] = a == 0 ? 2.0 * base[0] : base[0];
+            A.fA[1][a][f] = a == 1 ? 2.0 * base[1] : base[1];
+            if (DIM == 3) A.fB[a][f] = a == 2 ? 2.0 * base[2] : base[2];
+        }
+    }
+}
+
+struct MomArgs {
+    int n[3];
+    int wall[3][2];
+    int no_slip;
+    double r0, h, inv_h, half_inv_h, two_inv_h, inv_dt, dt;
+    const double *rho, *mu;
+    const double *u[3];
+    const double *R[3];       // residual mode: the right-hand side
+    double2 *rA, *rB;         // residual mode: -r as the inner right-hand sides (B: 3D, (-r_z, 0))
+    double *partial;          // residual mode: per block sum of (dt r / rho)^2 over its cells and components
+    double *r_out[3];         // residual mode, optional: r itself
+    double *y[3];             // apply mode: A(u)
+};
+
+__device__ __forceinline__ long long cell_of(const int n[3], int i, int j, int k) {
+    return (long long)i + (long long)n[0] * ((long long)j + (long long)n[1] * k);
+}
+
+// d u_q / d x_b at a cell: central inside, one-sided in the first and last cell.
+__device__ __forceinline__ double mom_du(const MomArgs &A, int q, int b, const int pos[3]) {
+    const int nb = A.n[b];
+    if (nb < 2) return 0.0;
+    int up[3] = {pos[0], pos[1], pos[2]}, dn[3] = {pos[0], pos[1], pos[2]};
+    up[b] = pos[b] + 1 < nb ? pos[b] + 1 : pos[b];
+    dn[b] = pos[b] > 0 ? pos[b] - 1 : pos[b];
+    const double d = A.u[q][cell_of(A.n, up[0], up[1], up[2])] - A.u[q][cell_of(A.n, dn[0], dn[1], dn[2])];
+    return d * (up[b] - dn[b] == 2 ? A.half_inv_h : A.inv_h);
+}
+
+// tau_{c a} for every component c on the face of axis a at face position f.
+template <int DIM>
+__device__ __forceinline__ void mom_face_stress(const MomArgs &A, int a, const int f[3], double tau[DIM]) {
+    const int fa = f[a];
+    if (fa == 0 || fa == A.n[a]) {
+        const int side = fa == 0 ? 0 : 1;
+        int cpos[3] = {f[0], f[1], f[2]};
+        if (side) cpos[a] = fa - 1;
+        const long long cc = cell_of(A.n, cpos[0], cpos[1], cpos[2]);
+        const bool w = A.wall[a][side] != 0;
+        const double mu = A.mu[cc];
+#pragma unroll
+        for (int q = 0; q < DIM; q++) {
+            if (w && (q == a || A.no_slip)) {
+                const double ub = A.u[q][cc];
+                const double d = (side == 0 ? ub : -ub) * A.two_inv_h;     // towards the wall value 0
+                tau[q] = (q == a ? 2.0 * mu : mu) * d;
+            } else {
+                tau[q] = 0.0;
+            }
+        }
+        return;
+    }
+    int L[3] = {f[0], f[1], f[2]};
+    L[a] = fa - 1;
+    const long long cl = cell_of(A.n, L[0], L[1], L[2]), cr = cell_of(A.n, f[0], f[1], f[2]);
+    const double mf = 0.5 * (A.mu[cl] + A.mu[cr]);
+#pragma unroll
+    for (int q = 0; q < DIM; q++) {
+        const double normal = (A.u[q][cr] - A.u[q][cl]) * A.inv_h;
+        if (q == a) {
+            tau[q] = mf * (normal + normal);
+        } else {
+            const double tang = 0.5 * (mom_du(A, a, q, L) + mom_du(A, a, q, f));
+            tau[q] = mf * (normal + tang);
+        }
+    }
+}
+
+template <int DIM, bool AXI, bool APPLY, int TX, int TY>
+__global__ void __launch_bounds__(TX * TY) k_mom_residual(const __grid_constant__ MomArgs A) {
+    constexpr int NX = (TX + 1) * TY, NY = TX * (TY + 1), NZ = DIM == 3 ? 2 * TX * TY : 0, NF = NX + NY + NZ;
+    __shared__ double F[DIM][NF];
+    __shared__ double red[TX * TY / 32];
+    const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY, k = DIM == 3 ? (int)blockIdx.z : 0;
+    const int tid = threadIdx.x + TX * threadIdx.y;
+    for (int t = tid; t < NF; t += TX * TY) {
+        int a, f[3];
+        if (t < NX) {
+            a = 0;
+            f[0] = i0 + t % (TX + 1);
+            f[1] = j0 + t / (TX + 1);
+            f[2] = k;
+        } else if (t < NX + NY) {
+            const int v = t - NX;
+            a = 1;
+            f[0] = i0 + v % TX;
+            f[1] = j0 + v / TX;
+            f[2] = k;
+        } else {
+            const int v = t - NX - NY;
+            a = 2;
+            f[0] = i0 + v % TX;
+            f[1] = j0 + (v / TX) % TY;
+            f[2] = k + v / (TX * TY);
+        }
+        bool in = true;
+#pragma unroll
+        for (int b = 0; b < 3; b++) in = in && f[b] < A.n[b] + (b == a);
+        double tau[DIM];
+        if (in) {
+            mom_face_stress<DIM>(A, a, f, tau);
+        } else {
+#pragma unroll
+            for (int q = 0; q < DIM; q++) tau[q] = 0.0;
+        }
+#pragma unroll
+        for (int q = 0; q < DIM; q++) F[q][t] = tau[q];
+    }
+    __syncthreads();
+    const int li = threadIdx.x, lj = threadIdx.y, i = i0 + li, j = j0 + lj;
+    double s = 0.0;
+    if (i < A.n[0] && j < A.n[1]) {
+        const long long c = cell_of(A.n, i, j, k);
+        const double rho = A.rho[c];
+        const int ilo[3] = {lj * (TX + 1) + li, NX + lj * TX + li, NX + NY + lj * TX + li};
+        const int ihi[3] = {lj * (TX + 1) + li + 1, NX + (lj + 1) * TX + li, NX + NY + TX * TY + lj * TX + li};
+        double ri = 0.0, wl = 0.0, wh = 0.0, inv_rh = 0.0;
+        if (AXI) {
+            ri = A.r0 + (i + 0.5) * A.h;
+            wl = ri - 0.5 * A.h;
+            wh = ri + 0.5 * A.h;
+            inv_rh = 1.0 / (ri * A.h);
+        }
+        double Au[DIM];
+#pragma unroll
+        for (int q = 0; q < DIM; q++) {
+            double div = 0.0;
+#pragma unroll
+            for (int a = 0; a < DIM; a++) {
+                const double lo = F[q][ilo[a]], hi = F[q][ihi[a]];
+                const double t = (AXI && a == 0) ? (wh * hi - wl * lo) * inv_rh : (hi - lo) * A.inv_h;
+                div = a == 0 ? t : div + t;
+            }
+            const double uq = A.u[q][c];
+            double v = rho * A.inv_dt * uq - div;
+            if (AXI && q == 0) v += 2.0 * A.mu[c] * uq / (ri * ri);
+            Au[q] = v;
+        }
+        if (APPLY) {
+#pragma unroll
+            for (int q = 0; q < DIM; q++) A.y[q][c] = Au[q];
+        } else {
+            double r[DIM];
+            const double w = A.dt / rho;
+#pragma unroll
+            for (int q = 0; q < DIM; q++) {
+                r[q] = A.R[q][c] - Au[q];
+                s += (w * r[q]) * (w * r[q]);
+            }
+            A.rA[c] = make_double2(-r[0], -r[1]);
+            if (DIM == 3) A.rB[c] = make_double2(-r[DIM - 1], 0.0);
+            if (A.r_out[0]) {
+#pragma unroll
+                for (int q = 0; q < DIM; q++) A.r_out[q][c] = r[q];
+            }
+        }
+    }
+    if constexpr (!APPLY) {
+        // fixed-order block sum of the stopping norm
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if ((tid & 31) == 0) red[tid >> 5] = s;
+        __syncthreads();
+        if (tid == 0) {
+            double b = 0.0;
+            for (int w = 0; w < TX * TY / 32; w++) b += red[w];
+            A.partial[blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * (long long)blockIdx.z)] = b;
+        }
+    }
+}
+
+// Sum of the per-block partials in a fixed order (one block).
+__global__ void __launch_bounds__(1024) k_mom_norm(const double *partial, long long nblocks, double *out) {
+    __shared__ double red[32];
+    double s = 0.0;
+    for (long long b = threadIdx.x; b < nblocks; b += blockDim.x) s += partial[b];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += red[w];
+        out[0] = t;
+    }
+}
+
+// u += delta, per component.
+template <int DIM>
+__global__ void __launch_bounds__(256) k_mom_add(long long N, const double *d0, const double *d1, const double *d2,
+                                                 double *u0, double *u1, double *u2) {
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
+        u0[c] += d0[c];
+        u1[c] += d1[c];
+        if (DIM == 3) u2[c] += d2[c];
+    }
+}
+
+// delta += the correction solves' solutions (A = (u_0, u_1), B = (u_2, unused)).
+template <int DIM>
+__global__ void __launch_bounds__(256) k_mom_update(long long N, const double2 *xA, const double2 *xB, double *u0,
+                                                    double *u1, double *u2) {
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
+        const double2 d = xA[c];
+        u0[c] += d.x;
+        u1[c] += d.y;
+        if (DIM == 3) u2[c] += xB[c].x;
+    }
+}
+
+}  // namespace cmg
