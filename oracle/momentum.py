@@ -17,7 +17,13 @@ cells' averaged density and viscosity.
 - ``apply``           the left-hand side A(u), face flux by face flux;
 - ``matrix``          A as a sparse matrix, column by column from ``apply``;
 - ``solve``           the exact solution of A u = R by a sparse direct solve
-                      (small grids).
+                      (small grids);
+- ``cell_gradient``   the gradient of a cell field at the cells: the mean of
+                      the cell's two face gradients along each axis;
+- ``rhs``             R = (rho u)^(adv)/dt - grad p^n + sigma kappa grad C;
+- ``provisional_faces`` Eq. provel, u* = u_pred + (dt/rho) grad p^n at the
+                      cells, then the faces' normal components for the
+                      projection (Eq. unp1).
 
 Readings where the paper is silent (each listed in the design doc):
 - mu_f is the mean of the two cells' mu; a boundary face takes its cell's;
@@ -34,7 +40,12 @@ Readings where the paper is silent (each listed in the design doc):
 - axisymmetric (axis 0 = r, axis 1 = z): r-face fluxes weighted by r_f / r_i,
   and the hoop stress adds 2 mu u_r / r_i^2 to the r-row (the hoop component
   of the stress is 2 mu u_r / r; it adds nothing to the z-row);
-- no bulk viscosity (Stokes' hypothesis, Sec. 2).
+- no bulk viscosity (Stokes' hypothesis, Sec. 2);
+- cell gradients are the means of the face gradients of the projection's
+  operator: (s_R - s_L)/h inside; for p, 2 (g - p)/h towards a Dirichlet value
+  and 0 at walls and the axis; for C, 0 at every boundary (no value given);
+- the face velocity u*_f is the mean of the two cells' normal components of
+  u*; walls and the axis carry 0, a pressure boundary its cell's value.
 """
 from __future__ import annotations
 
@@ -152,3 +163,49 @@ def solve(grid, rho, mu, dt: float, R: Sequence[np.ndarray], no_slip: bool = Fal
     x = spla.spsolve(A, b)
     shape = (grid.n[2], grid.n[1], grid.n[0])
     return [x[c * grid.N:(c + 1) * grid.N].reshape(shape) for c in range(grid.dim)]
+
+
+def cell_gradient(grid, s, dirichlet=None) -> List[np.ndarray]:
+    """d s / d x_a at the cells, a < dim: the mean of the low and high face gradients.  dirichlet: None (zero
+    gradient at every boundary) or per-axis, per-side boundary values used where grid.bc is BC_DIRICHLET."""
+    h = grid.h
+    s = np.asarray(s, dtype=np.float64)
+    out = []
+    for a in range(grid.dim):
+        g = np.zeros(grid.face_shape(a), dtype=np.float64)
+        g[_sl(a, slice(1, -1))] = (s[_sl(a, slice(1, None))] - s[_sl(a, slice(0, -1))]) / h
+        if dirichlet is not None:
+            for side in (0, 1):
+                if grid.bc[a][side] != BC_DIRICHLET:
+                    continue
+                cell = _sl(a, slice(0, 1) if side == 0 else slice(-1, None))
+                gv = dirichlet[a][side]
+                g[cell] = 2.0 * (s[cell] - gv) / h if side == 0 else 2.0 * (gv - s[cell]) / h
+        out.append(0.5 * (g[_sl(a, slice(0, -1))] + g[_sl(a, slice(1, None))]))
+    return out
+
+
+def rhs(grid, dt: float, sigma: float, mom: Sequence[np.ndarray], p, kappa, C) -> List[np.ndarray]:
+    """R_c = (rho u)_c^(adv) / dt - (dp^n/dx_c) + sigma kappa (dC/dx_c), per cell."""
+    gp = cell_gradient(grid, p, grid.bcp)
+    gC = cell_gradient(grid, C)
+    kap = np.asarray(kappa, dtype=np.float64)
+    return [np.asarray(mom[c], dtype=np.float64) / dt - gp[c] + sigma * kap * gC[c] for c in range(grid.dim)]
+
+
+def provisional_faces(grid, dt: float, rho, p, u_pred: Sequence[np.ndarray]) -> List[np.ndarray]:
+    """Eq. provel at the cells, u* = u_pred + (dt/rho) grad p^n, then per axis a the face-normal component: the mean
+    of the two cells' u*_a inside, 0 at walls and the axis, the cell's value at a pressure boundary."""
+    gp = cell_gradient(grid, p, grid.bcp)
+    rho = np.asarray(rho, dtype=np.float64)
+    out = []
+    for a in range(grid.dim):
+        ua = np.asarray(u_pred[a], dtype=np.float64) + dt / rho * gp[a]
+        f = np.zeros(grid.face_shape(a), dtype=np.float64)
+        f[_sl(a, slice(1, -1))] = 0.5 * (ua[_sl(a, slice(0, -1))] + ua[_sl(a, slice(1, None))])
+        for side in (0, 1):
+            if grid.bc[a][side] == BC_DIRICHLET:
+                cell = _sl(a, slice(0, 1) if side == 0 else slice(-1, None))
+                f[cell] = ua[cell]
+        out.append(f)
+    return out

@@ -189,6 +189,107 @@ def test_solve_recovers_manufactured_velocity(kind):
             np.testing.assert_allclose(got[c], u[c], rtol=1e-9, atol=1e-9)
 
 
+GD = I.Grid(dim=2, axisym=0, n=(10, 8, 1), h=0.1, bc=((D, W), (W, D), (0, 0)),
+            bcp=((0.0, 0.0), (0.0, 0.0), (0.0, 0.0)))
+
+
+def _linear(g, a0, grad):
+    X = _centres(g)
+    return a0 + sum(grad[a] * X[a] for a in range(g.dim))
+
+
+def _dirichlet_of_linear(g, a0, grad):
+    """Boundary values of the linear field on each face plane (they vary along it only through other axes: the
+    pins below use fields that vary along one axis, so each boundary value is one number)."""
+    vals = []
+    for a in range(3):
+        lo = a0 + (grad[a] * 0.0 if a < g.dim else 0.0)
+        hi = a0 + (grad[a] * g.n[a] * g.h if a < g.dim else 0.0)
+        vals.append((lo, hi))
+    return vals
+
+
+@pytest.mark.parametrize("axis", [0, 1])
+def test_cell_gradient_of_a_linear_field(axis):
+    """Inside: the slope.  At a Dirichlet face with the field's own boundary value: the slope too.  At a wall
+    (zero face gradient) the boundary cell gets half the slope; without boundary values every boundary cell does."""
+    slope = [0.0, 0.0]
+    slope[axis] = 3.0
+    bc = [(W, W), (W, W), (0, 0)]
+    bc[axis] = (D, W)                                  # boundary values only where the field is one number per plane
+    g = I.Grid(dim=2, axisym=0, n=(10, 8, 1), h=0.1, bc=tuple(bc))
+    s = _linear(g, 2.0, slope)
+    gd = M.cell_gradient(g, s, _dirichlet_of_linear(g, 2.0, slope))
+    expect = np.full(s.shape, 3.0)
+    lo, hi = _sl_cells(axis, 0), _sl_cells(axis, -1)
+    if g.bc[axis][0] != D:
+        expect[lo] = 1.5
+    if g.bc[axis][1] != D:
+        expect[hi] = 1.5
+    np.testing.assert_allclose(gd[axis], expect, rtol=1e-12)
+    np.testing.assert_allclose(gd[1 - axis], 0.0, atol=1e-12)
+    g0 = M.cell_gradient(g, s)
+    expect = np.full(s.shape, 3.0)
+    expect[lo] = expect[hi] = 1.5
+    np.testing.assert_allclose(g0[axis], expect, rtol=1e-12)
+
+
+def _sl_cells(a, i):
+    s = [slice(None)] * 3
+    s[2 - a] = slice(i, i + 1) if i >= 0 else slice(i, None)
+    return tuple(s)
+
+
+def test_rhs_closed_form():
+    """R = mom/dt - grad p + sigma kappa grad C for linear p and C, uniform kappa, inside."""
+    g = GD
+    rng = np.random.default_rng(3)
+    shape = (1, g.n[1], g.n[0])
+    mom = [rng.normal(size=shape) for _ in range(2)]
+    gp, gC = (2e3, -5e2), (4.0, 7.0)
+    p, C = _linear(g, 1e5, gp), _linear(g, 0.3, gC)
+    dt, sigma, kap = 1e-4, 0.07, 50.0
+    R = M.rhs(g, dt, sigma, mom, p, np.full(shape, kap), C)
+    s = _interior(g, 1)
+    for c in range(2):
+        np.testing.assert_allclose(R[c][s], (mom[c] / dt - gp[c] + sigma * kap * gC[c])[s], rtol=1e-12)
+
+
+def test_provisional_faces_of_a_linear_velocity():
+    """u_pred,x = U + S x, p uniform: inside, u*_f is the field at the face; walls carry 0; a pressure boundary its
+    cell's value."""
+    g = I.Grid(dim=2, axisym=0, n=(10, 8, 1), h=0.1, bc=((D, W), (W, D), (0, 0)),
+               bcp=((1e5, 0.0), (0.0, 1e5), (0.0, 0.0)))
+    X = _centres(g)
+    U, S = 0.4, 2.0
+    shape = (1, g.n[1], g.n[0])
+    u = [U + S * X[0], np.zeros(shape)]
+    uf = M.provisional_faces(g, 1e-3, np.full(shape, 2.0), np.full(shape, 1e5), u)
+    xf = np.arange(g.n[0] + 1) * g.h
+    expect = np.broadcast_to(U + S * xf, g.face_shape(0)).copy()
+    expect[:, :, 0] = U + S * 0.5 * g.h               # axis 0, low side: pressure boundary -> the cell's value
+    expect[:, :, -1] = 0.0                            # high side: wall
+    np.testing.assert_allclose(uf[0], expect, rtol=1e-13, atol=1e-15)
+    np.testing.assert_allclose(uf[1], 0.0, atol=1e-15)
+
+
+def test_pressure_only_step_leaves_no_provisional_velocity():
+    """No momentum, viscosity or surface tension: the predictor gives u_pred = -(dt/rho) grad p^n, and Eq. provel
+    removes exactly that, so u* vanishes on every face (the projection then carries the whole pressure gradient)."""
+    g = GD
+    rng = np.random.default_rng(5)
+    shape = (1, g.n[1], g.n[0])
+    rho = rng.uniform(1.0, 1000.0, shape)
+    p = 1e5 + rng.normal(0.0, 1e3, shape)
+    dt = 1e-3
+    R = M.rhs(g, dt, 0.0, [np.zeros(shape)] * 2, p, np.zeros(shape), np.zeros(shape))
+    u_pred = M.solve(g, rho, np.zeros(shape), dt, R)
+    uf = M.provisional_faces(g, dt, rho, p, u_pred)
+    scale = max(np.abs(dt / rho * gp).max() for gp in M.cell_gradient(g, p, g.bcp))
+    for a in range(2):
+        np.testing.assert_allclose(uf[a], 0.0, atol=1e-12 * scale)
+
+
 def _mutant(old, new):
     assert _SRC.count(old) >= 1, old
     m = types.ModuleType("momentum_mutant")
@@ -215,6 +316,16 @@ MUTATIONS = [
      lambda: test_wall_tangential_uniform_flow(False)),
     ("tangential derivative from one cell", "F[inner] = muf[inner] * (normal + 0.5 * (dc[lo] + dc[hi]))",
      "F[inner] = muf[inner] * (normal + dc[lo])", lambda: test_quadratic_velocity_linear_viscosity_exact(2)),
+    ("Eq. provel with the wrong sign", "ua = np.asarray(u_pred[a], dtype=np.float64) + dt / rho * gp[a]",
+     "ua = np.asarray(u_pred[a], dtype=np.float64) - dt / rho * gp[a]",
+     test_pressure_only_step_leaves_no_provisional_velocity),
+    ("face velocity from one cell",
+     "f[_sl(a, slice(1, -1))] = 0.5 * (ua[_sl(a, slice(0, -1))] + ua[_sl(a, slice(1, None))])",
+     "f[_sl(a, slice(1, -1))] = ua[_sl(a, slice(0, -1))]", test_provisional_faces_of_a_linear_velocity),
+    ("Dirichlet face gradient at h", "g[cell] = 2.0 * (s[cell] - gv) / h if side == 0 else 2.0 * (gv - s[cell]) / h",
+     "g[cell] = (s[cell] - gv) / h if side == 0 else (gv - s[cell]) / h", lambda: test_cell_gradient_of_a_linear_field(0)),
+    ("surface-tension force with the wrong sign", "- gp[c] + sigma * kap * gC[c]", "- gp[c] - sigma * kap * gC[c]",
+     test_rhs_closed_form),
 ]
 
 
