@@ -499,7 +499,9 @@ ENERGY_BYTES_2D = (2 + 1 + 2 + 2 + 2) * 8 + 2 * 8                 # x, C, p1 p2,
 
 def run_timestep(args):
     """The device work of one time step on the 16-bubble 1024^2 advected state:
-    coefficient assembly (mg_assemble_async: Eqs. 10, 11, 20, 23, 29-34), set-up and
+    the momentum predictor (mg_momentum_rhs_async, mg_momentum_* set-up and solve to
+    1e-10 from u^(adv), mg_provisional_async: Eq. provel), coefficient assembly on its
+    u* (mg_assemble_async: Eqs. 10, 11, 20, 23, 29-34), set-up and
     solve to 1e-10 from (T^(adv), p^(adv)), the velocity / phase-pressure
     update (mg_correct_async: Eq. unp1, Eqs. 37-38) and the phase-energy update
     (mg_energy_async: Eq. 39).  Inputs resident on the device; the L2 is flushed
@@ -508,7 +510,7 @@ def run_timestep(args):
     import torch
     from paper_2206_11294_gb300 import binding as B
     from paper_2206_11294_gb300 import inputs as I
-    from paper_2206_11294_gb300.binding import Solver
+    from paper_2206_11294_gb300.binding import Momentum, Solver
     torch.cuda.set_device(0)
     stream = torch.cuda.current_stream()
     s = I.bubbles_state_1024()
@@ -527,18 +529,37 @@ def run_timestep(args):
     E1 = T(s.C * I.phase_energy(s.p, rho1, s.ph1))
     E2 = T((1 - s.C) * I.phase_energy(s.p, rho2, s.ph2))
     E1o, E2o = torch.empty_like(E1), torch.empty_like(E2)
+    # momentum predictor inputs: p^n (the state's pressure), rho^(n+1) = m1 + m2, mu = C mu_1 + (1 - C) mu_2
+    p_n = T(s.p)
+    rho_d = d["m1"] + d["m2"]
+    mu_d = T(s.C * s.ph1.mu + (1 - s.C) * s.ph2.mu)
+    R = [torch.empty_like(d["C"]) for _ in range(2)]
+    u_pred = [torch.empty_like(d["C"]) for _ in range(2)]
+    u0 = [m_ / rho_d for m_ in d["mom"]]
+    ustar = [torch.empty_like(u) for u in d["uf"]]
+    mom_solver = Momentum(g, precision=args.precision, stream=stream)
+    mom_stats = []
     solver = Solver(g, precision=args.precision, rtol=1e-10, max_cycles=50, stream=stream)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
 
+    def predict():
+        B.momentum_rhs(g, s.dt, s.sigma, d["mom"], p_n, d["kappa"], d["C"], R)
+        mom_solver.set_coeffs(s.dt, rho_d, mu_d)
+        for a in range(2):
+            u_pred[a].copy_(u0[a])
+        mom_stats.append(mom_solver.solve(R, u_pred, rtol=1e-10, max_iters=100))
+        B.provisional(g, s.dt, rho_d, p_n, u_pred, ustar)
+
     def assemble():
-        B.assemble(g, (s.ph1, s.ph2), s.dt, d["C"], d["m1"], d["m2"], d["E"], d["mom"], d["uf"], out)
+        B.assemble(g, (s.ph1, s.ph2), s.dt, d["C"], d["m1"], d["m2"], d["E"], d["mom"], ustar, out)
 
     def correct():
-        B.correct(g, s.dt, s.sigma, x, d["C"], d["kappa"], out["fa"], d["uf"], uo, p1, p2)
+        B.correct(g, s.dt, s.sigma, x, d["C"], d["kappa"], out["fa"], ustar, uo, p1, p2)
 
     def energy():
         B.energy(g, (s.ph1, s.ph2), s.dt, x, d["C"], p1, p2, uo, E1, E2, E1o, E2o)
 
+    predict()
     assemble()
     solver.set_coeffs(out["lam"], out["fa"], out["fk"])
     tuning = None
@@ -550,32 +571,34 @@ def run_timestep(args):
 
     def step(marks):
         marks[0].record(stream)
-        assemble()
+        predict()
         marks[1].record(stream)
+        assemble()
+        marks[2].record(stream)
         solver.set_coeffs(out["lam"], out["fa"], out["fk"])
         x.copy_(out["x0"])
         stats.append(solver.solve(out["b"], x))
-        marks[2].record(stream)
-        correct()
         marks[3].record(stream)
-        energy()
+        correct()
         marks[4].record(stream)
+        energy()
+        marks[5].record(stream)
 
     for _ in range(args.warmup):
-        step([ev() for _ in range(5)])
+        step([ev() for _ in range(6)])
     torch.cuda.synchronize()
     stats.clear()
-    marks = [[ev() for _ in range(5)] for _ in range(args.steps)]
+    mom_stats.clear()
+    marks = [[ev() for _ in range(6)] for _ in range(args.steps)]
     clocks = ClockSampler(gpu_identity(torch, 0))
     for k in range(args.steps):
         flush.zero_()
         step(marks[k])
     torch.cuda.synchronize()
     clk = clocks.stop()
-    total = sum(m[0].elapsed_time(m[4]) for m in marks) / args.steps
-    t_asm = sum(m[0].elapsed_time(m[1]) for m in marks) / args.steps
-    t_cor = sum(m[2].elapsed_time(m[3]) for m in marks) / args.steps
-    t_en = sum(m[3].elapsed_time(m[4]) for m in marks) / args.steps
+    avg = lambda a, b: sum(m[a].elapsed_time(m[b]) for m in marks) / args.steps
+    total, t_pred, t_asm, t_solve, t_cor, t_en = avg(0, 5), avg(0, 1), avg(1, 2), avg(2, 3), avg(3, 4), avg(4, 5)
+    mom_solver.close()
     peak, peak_kind = measured_peak()
     roof = lambda byts, ms: {"bound": "hbm", "achieved": byts / (ms * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
                              "frac": byts / (ms * 1e-3) / 1e9 / peak, "peak_source": peak_kind,
@@ -586,10 +609,12 @@ def run_timestep(args):
     asm_alu = {"bound": "alu", "fp64_pipe_busy_elapsed_ncu": 0.836, "fp64_inst_per_cell_ncu": 150,
                "source": "profiles/k_assemble_bubbles1024.md", "hbm": asm}
     return {"workload": "one time step, bubbles16_1024x1024 advected state: assembly + set-up + solve to 1e-10 + "
-                        "velocity / phase-pressure update + phase-energy update", "metric": "time steps/s",
+                        "velocity / phase-pressure update + phase-energy update, after the momentum predictor "
+                        "(right-hand side, set-up + solve to 1e-10, Eq. provel)", "metric": "time steps/s",
             "cells": N,
             "precision": args.precision, "steps_per_s": 1e3 / total, "ms_per_step": total,
-            "assemble_ms": t_asm, "solve_ms": total - t_asm - t_cor - t_en, "correct_ms": t_cor, "energy_ms": t_en,
+            "predictor_ms": t_pred, "predictor_iterations": mom_stats[0]["iterations"] if mom_stats else None,
+            "assemble_ms": t_asm, "solve_ms": t_solve, "correct_ms": t_cor, "energy_ms": t_en,
             "cycles_per_solve": cycles[0] if cycles else None, "tuning": tuning,
             "assemble_roofline": asm_alu,
             "correct_roofline": roof(CORRECT_BYTES_2D * N, t_cor),

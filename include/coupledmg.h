@@ -440,6 +440,29 @@ MG_API mg_status mg_momentum_solve(mg_momentum *m, const double *const R[3], dou
 
 MG_API mg_status mg_momentum_destroy(mg_momentum *m);
 
+/* The steps either side of the predictor, enqueued on `stream` without
+ * waiting (device pointers of the current device, as for mg_assemble_async).
+ * Cell gradients are the means of a cell's two face gradients along each
+ * axis, the face gradients being those of the projection: (s_R - s_L)/h
+ * inside; for p, 2 (g - p)/h towards a Dirichlet value g of grid->bc_p and 0
+ * at walls and the axis; for C, 0 at every boundary.
+ *
+ * Right-hand side: R_c = mom_c / dt - (dp/dx_c) + sigma kappa (dC/dx_c), with
+ * mom the advected momentum (rho u)^(adv), p the pressure p^n of the last
+ * step, C the volume fraction and kappa the curvature at the new time level.
+ * R[a] may equal mom[a] (in place); R must not alias p, C or kappa. */
+MG_API mg_status mg_momentum_rhs_async(const mg_grid *grid, double dt, double sigma, const double *const mom[3],
+                                       const double *p, const double *kappa, const double *C, double *const R[3],
+                                       void *stream);
+
+/* Eq. provel: u* = u_pred + (dt/rho) grad p^n at the cells, and its
+ * face-normal components for the projection (the u* that mg_assemble_async
+ * and mg_correct_async take): the mean of the two cells' values inside, 0 at
+ * walls and the axis, the cell's value at a pressure (Dirichlet) boundary.
+ * uf_out must not alias rho, p or u_pred. */
+MG_API mg_status mg_provisional_async(const mg_grid *grid, double dt, const double *rho, const double *p,
+                                      const double *const u_pred[3], double *const uf_out[3], void *stream);
+
 /* Allocation-free stopping norms (the paper has no counterpart: this is a
  * library service).  For callers that cannot allocate device memory - their
  * device memory is owned by another allocator, or their time loop must not

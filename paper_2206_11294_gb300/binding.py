@@ -34,7 +34,7 @@ EXPORTS = ["mg_default_options", "mg_workspace_size", "mg_create", "mg_set_coeff
            "mg_batch_set_coeffs", "mg_get_tuning", "mg_set_tuning", "mg_autotune", "mg_batch_get_tuning",
            "mg_batch_set_tuning", "mg_batch_autotune", "mg_assemble_async", "mg_correct_async",
            "mg_energy_async", "mg_momentum_create", "mg_momentum_set_coeffs", "mg_momentum_apply",
-           "mg_momentum_solve", "mg_momentum_destroy"]
+           "mg_momentum_solve", "mg_momentum_destroy", "mg_momentum_rhs_async", "mg_provisional_async"]
 
 MG_MAX_LEVELS = 32
 MG_SWEEP_COLOUR, MG_SWEEP_FUSED, MG_SWEEP_ASYNC, MG_SWEEP_COLOUR2 = 1, 2, 3, 4
@@ -196,6 +196,8 @@ def load(path: str = LIB_PATH):
             "mg_momentum_apply": ([P, pa3, pa3], C.c_int),
             "mg_momentum_solve": ([P, pa3, pa3, C.c_double, C.c_int, C.POINTER(MgMomentumStats)], C.c_int),
             "mg_momentum_destroy": ([P], C.c_int),
+            "mg_momentum_rhs_async": ([C.POINTER(MgGrid), C.c_double, C.c_double, pa3, P, P, P, pa3, P], C.c_int),
+            "mg_provisional_async": ([C.POINTER(MgGrid), C.c_double, P, P, pa3, pa3, P], C.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -539,6 +541,34 @@ class Solver:
 
     def __exit__(self, *a):
         self.close()
+
+
+def _ptr3(g, arrs):
+    out = (C.c_void_p * 3)()
+    for a in range(g.dim):
+        out[a] = _ptr(arrs[a], True)[0]
+    return out
+
+
+def momentum_rhs(grid, dt: float, sigma: float, mom: Sequence, p, kappa, C_, R: Sequence, stream=None) -> None:
+    """mg_momentum_rhs_async: every array a contiguous float64 CUDA tensor; R written in the order of `stream`."""
+    import torch
+    g = make_grid(grid)
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    check(load().mg_momentum_rhs_async(C.byref(g), float(dt), float(sigma), _ptr3(g, mom), _ptr(p, True)[0],
+                                       _ptr(kappa, True)[0], _ptr(C_, True)[0], _ptr3(g, R),
+                                       C.c_void_p(stream.cuda_stream)))
+
+
+def provisional(grid, dt: float, rho, p, u_pred: Sequence, uf_out: Sequence, stream=None) -> None:
+    """mg_provisional_async: every array a contiguous float64 CUDA tensor; uf_out written in the order of `stream`."""
+    import torch
+    g = make_grid(grid)
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    check(load().mg_provisional_async(C.byref(g), float(dt), _ptr(rho, True)[0], _ptr(p, True)[0],
+                                      _ptr3(g, u_pred), _ptr3(g, uf_out), C.c_void_p(stream.cuda_stream)))
 
 
 class Momentum:

@@ -2205,6 +2205,85 @@ mg_status mg_momentum_solve(mg_momentum *m, const double *const R[3], double *co
     return MG_OK;
 }
 
+namespace {
+MomSideArgs side_args(const mg_grid *grid, double dt) {
+    MomSideArgs A;
+    std::memset(&A, 0, sizeof(A));
+    for (int a = 0; a < 3; a++) {
+        A.n[a] = grid->n[a];
+        for (int sd = 0; sd < 2; sd++) {
+            A.dir[a][sd] = a < grid->dim && grid->bc[a][sd] == MG_BC_DIRICHLET;
+            A.gp[a][sd] = a < grid->dim ? grid->bc_p[a][sd] : 0.0;
+        }
+    }
+    A.inv_h = 1.0 / grid->h;
+    A.two_inv_h = 2.0 / grid->h;
+    A.half_inv_h = 0.5 / grid->h;
+    A.dt = dt;
+    A.inv_dt = 1.0 / dt;
+    return A;
+}
+}  // namespace
+
+mg_status mg_momentum_rhs_async(const mg_grid *grid, double dt, double sigma, const double *const mom[3],
+                                const double *p, const double *kappa, const double *C, double *const R[3],
+                                void *stream) {
+    mg_status st = check_grid_geom(grid);
+    if (st) return st;
+    if (!mom || !R) return fail(MG_ERR_INVALID_ARG, "mom and R must not be NULL");
+    if (!(dt > 0.0) || !std::isfinite(dt) || !std::isfinite(sigma))
+        return fail(MG_ERR_INVALID_ARG, "dt must be positive and finite, sigma finite");
+    const int dim = grid->dim;
+    bool ok = device_ptr(p) && device_ptr(kappa) && device_ptr(C);
+    for (int a = 0; a < dim; a++) ok = ok && device_ptr(mom[a]) && device_ptr(R[a]);
+    if (!ok) return fail(MG_ERR_INVALID_ARG, "every array must be a device pointer of the current device");
+    for (int a = 0; a < dim; a++)
+        if (R[a] == p || R[a] == C || R[a] == kappa) return fail(MG_ERR_INVALID_ARG, "R must not alias p, C or kappa");
+    MomSideArgs A = side_args(grid, dt);
+    A.sigma = sigma;
+    A.p = p;
+    A.C = C;
+    A.kappa = kappa;
+    for (int a = 0; a < dim; a++) {
+        A.mom[a] = mom[a];
+        A.R[a] = R[a];
+    }
+    cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+    if (dim == 3) k_mom_rhs<3><<<cell_grid(*grid), kBlock, 0, cs>>>(A);
+    else k_mom_rhs<2><<<cell_grid(*grid), kBlock, 0, cs>>>(A);
+    CK(cudaGetLastError());
+    return MG_OK;
+}
+
+mg_status mg_provisional_async(const mg_grid *grid, double dt, const double *rho, const double *p,
+                               const double *const u_pred[3], double *const uf_out[3], void *stream) {
+    mg_status st = check_grid_geom(grid);
+    if (st) return st;
+    if (!u_pred || !uf_out) return fail(MG_ERR_INVALID_ARG, "u_pred and uf_out must not be NULL");
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(MG_ERR_INVALID_ARG, "dt must be positive and finite");
+    const int dim = grid->dim;
+    bool ok = device_ptr(rho) && device_ptr(p);
+    for (int a = 0; a < dim; a++) ok = ok && device_ptr(u_pred[a]) && device_ptr(uf_out[a]);
+    if (!ok) return fail(MG_ERR_INVALID_ARG, "every array must be a device pointer of the current device");
+    for (int a = 0; a < dim; a++) {
+        if (uf_out[a] == rho || uf_out[a] == p) return fail(MG_ERR_INVALID_ARG, "uf_out must not alias an input");
+        for (int b = 0; b < dim; b++)
+            if (uf_out[a] == u_pred[b]) return fail(MG_ERR_INVALID_ARG, "uf_out must not alias an input");
+    }
+    MomSideArgs A = side_args(grid, dt);
+    A.p = p;
+    A.rho = rho;
+    for (int a = 0; a < dim; a++) {
+        A.u[a] = u_pred[a];
+        A.uf[a] = uf_out[a];
+    }
+    cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+    if (dim == 3) k_provisional<3><<<cell_grid(*grid), kBlock, 0, cs>>>(A);
+    else k_provisional<2><<<cell_grid(*grid), kBlock, 0, cs>>>(A);
+    CK(cudaGetLastError());
+    return MG_OK;
+}
+
 const char *mg_last_error(void) { return g_err.c_str(); }
 
 }  // extern "C"

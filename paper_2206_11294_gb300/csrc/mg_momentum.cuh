@@ -295,4 +295,86 @@ __global__ void __launch_bounds__(256) k_mom_update(long long N, const double2 *
     }
 }
 
+// ---------------------------------------------------------------- either side of the predictor
+// Cell gradients are the means of a cell's two face gradients along each axis,
+// the face gradients being those of the projection: (s_R - s_L)/h inside; for
+// p, 2 (g - p)/h towards a Dirichlet value and 0 at walls and the axis; for C,
+// 0 at every boundary.
+struct MomSideArgs {
+    int n[3];
+    int dir[3][2];            // Dirichlet faces of p
+    double gp[3][2];          // their values
+    double inv_h, two_inv_h, half_inv_h, dt, inv_dt, sigma;
+    const double *p, *C, *kappa, *rho;
+    const double *mom[3], *u[3];
+    double *R[3], *uf[3];
+};
+
+__device__ __forceinline__ double face_grad(const MomSideArgs &A, const double *s, bool dirichlet, int a,
+                                            const int pos[3], int fpos, long long c, long long stride) {
+    if (fpos == 0) return dirichlet && A.dir[a][0] ? (s[c] - A.gp[a][0]) * A.two_inv_h : 0.0;
+    if (fpos == A.n[a]) return dirichlet && A.dir[a][1] ? (A.gp[a][1] - s[c]) * A.two_inv_h : 0.0;
+    // interior face between the cell at fpos - 1 and the one at fpos (c is the cell at pos[a])
+    const long long lo = c + (long long)(fpos - 1 - pos[a]) * stride, hi = lo + stride;
+    return (s[hi] - s[lo]) * A.inv_h;
+}
+
+__device__ __forceinline__ double cell_grad(const MomSideArgs &A, const double *s, bool dirichlet, int a,
+                                            const int pos[3], long long c) {
+    const long long st = a == 0 ? 1LL : a == 1 ? (long long)A.n[0] : (long long)A.n[0] * A.n[1];
+    const double lo = face_grad(A, s, dirichlet, a, pos, pos[a], c, st);
+    const double hi = face_grad(A, s, dirichlet, a, pos, pos[a] + 1, c, st);
+    return 0.5 * (lo + hi);
+}
+
+// R = (rho u)^(adv)/dt - grad p^n + sigma kappa grad C per cell.
+template <int DIM>
+__global__ void __launch_bounds__(256) k_mom_rhs(const __grid_constant__ MomSideArgs A) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = DIM == 3 ? (int)blockIdx.z : 0;
+    if (i >= A.n[0] || j >= A.n[1]) return;
+    const long long c = cell_of(A.n, i, j, k);
+    const int pos[3] = {i, j, k};
+    const double sk = A.sigma * A.kappa[c];
+#pragma unroll
+    for (int a = 0; a < DIM; a++) {
+        const double gpa = cell_grad(A, A.p, true, a, pos, c), gCa = cell_grad(A, A.C, false, a, pos, c);
+        A.R[a][c] = A.mom[a][c] * A.inv_dt - gpa + sk * gCa;
+    }
+}
+
+// Eq. provel at the cells, u* = u_pred + (dt/rho) grad p^n, and the face-normal components: the mean of the two
+// cells' inside, 0 at walls and the axis, the cell's value at a pressure boundary.  Each cell writes its low face
+// of every axis and, in the last cell, the high one.
+template <int DIM>
+__global__ void __launch_bounds__(256) k_provisional(const __grid_constant__ MomSideArgs A) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = DIM == 3 ? (int)blockIdx.z : 0;
+    if (i >= A.n[0] || j >= A.n[1]) return;
+    const long long c = cell_of(A.n, i, j, k);
+    const int pos[3] = {i, j, k};
+#pragma unroll
+    for (int a = 0; a < DIM; a++) {
+        const long long st = a == 0 ? 1LL : a == 1 ? (long long)A.n[0] : (long long)A.n[0] * A.n[1];
+        const double us = A.u[a][c] + A.dt / A.rho[c] * cell_grad(A, A.p, true, a, pos, c);
+        // low face
+        double v;
+        if (pos[a] == 0) {
+            v = A.dir[a][0] ? us : 0.0;
+        } else {
+            int pl[3] = {pos[0], pos[1], pos[2]};
+            pl[a] = pos[a] - 1;
+            const long long cl = c - st;
+            const double ul = A.u[a][cl] + A.dt / A.rho[cl] * cell_grad(A, A.p, true, a, pl, cl);
+            v = 0.5 * (ul + us);
+        }
+        A.uf[a][face_index(A.n, a, i, j, k)] = v;
+        if (pos[a] == A.n[a] - 1) {
+            A.uf[a][face_index(A.n, a, i + (a == 0), j + (a == 1), k + (a == 2))] = A.dir[a][1] ? us : 0.0;
+        }
+    }
+}
+
 }  // namespace cmg

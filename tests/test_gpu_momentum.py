@@ -183,3 +183,83 @@ def test_invalid_use_rejected(torch_cuda):
         B.check(B.load().mg_momentum_create(C.byref(B.make_grid(g)), 4, None, None, C.byref(h)))
     assert e.value.status == MG_ERR_INVALID_ARG
     m.close()
+
+
+def _side_inputs(g, seed):
+    rng = np.random.default_rng(seed)
+    shape = (g.n[2], g.n[1], g.n[0])
+    mom = [rng.normal(0.0, 50.0, shape) for _ in range(g.dim)]
+    p = 1e5 + rng.normal(0.0, 300.0, shape)
+    kappa = rng.normal(0.0, 100.0, shape)
+    C = rng.uniform(0.0, 1.0, shape)
+    rho = rng.uniform(1.0, 1000.0, shape)
+    u = [rng.normal(size=shape) for _ in range(g.dim)]
+    return mom, p, kappa, C, rho, u
+
+
+def _with_pressure_values(g):
+    import dataclasses
+    return dataclasses.replace(g, bcp=((1.01e5, 0.99e5), (1.0e5, 1.02e5), (0.98e5, 1.0e5)))
+
+
+@pytest.mark.parametrize("name", list(GRIDS))
+def test_rhs_and_provisional_match_oracle(torch_cuda, orc, name):
+    from paper_2206_11294_gb300 import binding as B
+    torch = torch_cuda
+    g = _with_pressure_values(GRIDS[name])
+    mom, p, kappa, C, rho, u = _side_inputs(g, 80 + len(name))
+    dt, sigma = 1e-4, 0.072
+    R = [torch.empty(p.shape, dtype=torch.float64, device="cuda") for _ in range(g.dim)]
+    B.momentum_rhs(g, dt, sigma, [_dev(torch, m_) for m_ in mom], _dev(torch, p), _dev(torch, kappa), _dev(torch, C), R)
+    uf = [torch.empty(g.face_shape(a), dtype=torch.float64, device="cuda") for a in range(g.dim)]
+    B.provisional(g, dt, _dev(torch, rho), _dev(torch, p), [_dev(torch, v) for v in u], uf)
+    torch.cuda.synchronize()
+    ref_R = orc.rhs(g, dt, sigma, mom, p, kappa, C)
+    gp = orc.cell_gradient(g, p, g.bcp)
+    gC = orc.cell_gradient(g, C)
+    for c in range(g.dim):
+        scale = np.abs(mom[c] / dt) + np.abs(gp[c]) + np.abs(sigma * kappa * gC[c]) + 1e-300
+        err = np.abs(R[c].cpu().numpy() - ref_R[c])
+        assert np.all(err <= 1e-13 * scale), (c, float((err / scale).max()))
+    ref_f = orc.provisional_faces(g, dt, rho, p, u)
+    for a in range(g.dim):
+        ustar = np.abs(u[a]) + np.abs(dt / rho * gp[a])
+        s = np.zeros(g.face_shape(a))
+        lo = [slice(None)] * 3
+        hi = [slice(None)] * 3
+        lo[2 - a] = slice(0, -1)
+        hi[2 - a] = slice(1, None)
+        s[tuple(lo)] += ustar
+        s[tuple(hi)] += ustar
+        err = np.abs(uf[a].cpu().numpy() - ref_f[a])
+        assert np.all(err <= 1e-13 * s + 1e-300), (a, float((err / (s + 1e-300)).max()))
+
+
+def test_predictor_chain_matches_oracle(torch_cuda, orc):
+    """R, the predictor solve and Eq. provel on the device against the oracle's R, its direct solve and its
+    face velocities (the solve converged to rtol 1e-12)."""
+    from paper_2206_11294_gb300 import binding as B
+    from paper_2206_11294_gb300.binding import Momentum
+    torch = torch_cuda
+    g = _with_pressure_values(GRIDS["2d_ragged"])
+    mom, p, kappa, C, rho, _ = _side_inputs(g, 90)
+    mu = np.random.default_rng(91).uniform(1e-3, 1.0, rho.shape)
+    dt, sigma = 1e-3, 0.072
+    R = [torch.empty(p.shape, dtype=torch.float64, device="cuda") for _ in range(g.dim)]
+    B.momentum_rhs(g, dt, sigma, [_dev(torch, m_) for m_ in mom], _dev(torch, p), _dev(torch, kappa), _dev(torch, C), R)
+    m = Momentum(g)
+    m.set_coeffs(dt, _dev(torch, rho), _dev(torch, mu))
+    u = [_dev(torch, m_ / rho) for m_ in mom]
+    st = m.solve(R, u, rtol=1e-12, max_iters=300)
+    assert st["status"] == "MG_OK", st
+    uf = [torch.empty(g.face_shape(a), dtype=torch.float64, device="cuda") for a in range(g.dim)]
+    B.provisional(g, dt, _dev(torch, rho), _dev(torch, p), u, uf)
+    torch.cuda.synchronize()
+    ref_R = orc.rhs(g, dt, sigma, mom, p, kappa, C)
+    u_ref = orc.solve(g, rho, mu, dt, ref_R)
+    ref_f = orc.provisional_faces(g, dt, rho, p, u_ref)
+    for a in range(g.dim):
+        got = uf[a].cpu().numpy()
+        err = np.linalg.norm(got - ref_f[a]) / np.linalg.norm(ref_f[a])
+        assert err <= 1e-9, (a, err, st)
+    m.close()
