@@ -415,9 +415,10 @@ typedef struct {
 enum { MG_MOMENTUM_NO_SLIP = 1 };
 
 /* grid: as for mg_create; flags: 0 or MG_MOMENTUM_NO_SLIP.  inner: options of
- * the correction solves (NULL: library defaults with one cycle per step); its
- * rtol is ignored and max_cycles is the number of cycles (MIXED: outer
- * refinement steps) per correction.  stream: a cudaStream_t for all work. */
+ * the correction solves (NULL: library defaults with one cycle per step);
+ * precision must be MG_FP64, rtol is ignored and max_cycles is the number of
+ * cycles per correction (run from zero, without stopping norms).  stream: a
+ * cudaStream_t for all work. */
 MG_API mg_status mg_momentum_create(const mg_grid *grid, int flags, const mg_options *inner, void *stream,
                                     mg_momentum **out);
 

@@ -575,7 +575,7 @@ class Momentum:
     """mg_momentum: the implicit momentum predictor (rho/dt) u - div(mu (grad u + grad u^T)) = R on one grid.
     Arrays are contiguous float64 CUDA tensors of the grid's cells, one per velocity component."""
 
-    def __init__(self, grid, no_slip: bool = False, precision="fp64", inner_cycles_per_step: int = 1, nu1=2, nu2=2,
+    def __init__(self, grid, no_slip: bool = False, inner_cycles_per_step: int = 1, nu1=2, nu2=2,
                  coarse_min=4, device: Optional[int] = None, stream=None):
         import torch
         lib = load()
@@ -584,7 +584,7 @@ class Momentum:
         dev = torch.cuda.current_device() if device is None else int(device)
         self.device = dev
         check(lib.mg_set_device(dev))
-        opt = make_options(precision, 0.0, inner_cycles_per_step, nu1, nu2, coarse_min)
+        opt = make_options("fp64", 0.0, inner_cycles_per_step, nu1, nu2, coarse_min)
         if stream is None:
             stream = torch.cuda.current_stream(dev)
         self.stream = stream

@@ -116,6 +116,8 @@ struct mg_handle {
     bool x_stale;          // the handle's x ran an iteration the stop test did not allow: not copied back
     bool coeffs_set;
     cudaGraphExec_t g64, g32;   // FP64 cycle+norm; mixed inner cycles+update+residual
+    cudaGraphExec_t gcorr;      // fixed FP64 cycles without norms (correction solves of the momentum predictor)
+    long long graph_kernels_corr;
     struct SetupGraph {         // set-up of the levels for the input pointers in key
         cudaGraphExec_t exec;
         const void *key[7];
@@ -1157,6 +1159,35 @@ mg_status solve_mixed(mg_handle *h, mg_stats *st) {
     return MG_OK;
 }
 
+// opt.max_cycles FP64 cycles from x = 0 with no stopping norms and no host wait: a fixed linear map of rhs, the
+// correction solve of the momentum predictor's outer loop.  The result stays in L[0].x.
+template <int DIM>
+mg_status correction_cycles(mg_handle *h, const double2 *rhs) {
+    if (!h->gcorr) {
+        const mg_status e = capture(h, &h->gcorr, &h->graph_kernels_corr, [&](cudaStream_t s) {
+            for (int q = 0; q < h->opt.max_cycles; q++) enqueue_vcycle<double, DIM>(h, s, 0, h->opt.cycle);
+        });
+        if (e) return e;
+    }
+    const LevelBuf &f = h->L[0];
+    CK(cudaMemsetAsync(f.x, 0, sizeof(double2) * f.N, h->stream));
+    enqueue_prep<DIM>(h, rhs);
+    CK(cudaGetLastError());
+    CK(cudaGraphLaunch(h->gcorr, h->stream));
+    h->enq += h->graph_kernels_corr;
+    return MG_OK;
+}
+
+// The device error flags a solve reports (singular coarsest matrix, a bounded wait that gave up); one host wait.
+mg_status handle_errors(mg_handle *h) {
+    CK(cudaStreamWaitEvent(h->stream, h->ev_inv, 0));
+    CK(cudaMemcpyAsync(h->errh, h->err_d, 2 * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    if (h->errh[0] & 4) return fail(MG_ERR_INVALID_COEFF, "the coarsest-level matrix is singular");
+    if (h->errh[1] & kErrAsyncTimeout) return fail(MG_ERR_TIMEOUT, "an asynchronous copy did not complete in time");
+    return MG_OK;
+}
+
 mg_status check_handle(const mg_handle *h, bool need_coeffs) {
     if (!h) return fail(MG_ERR_INVALID_ARG, "handle is NULL");
     if (need_coeffs && !h->coeffs_set) return fail(MG_ERR_STATE, "mg_set_coeffs has not succeeded on this handle");
@@ -1210,6 +1241,7 @@ bool tail_ctas_ok(const mg_handle *h, int ctas) {
 
 void drop_graphs(mg_handle *h) {
     if (h->g64) { cudaGraphExecDestroy(h->g64); h->g64 = nullptr; }
+    if (h->gcorr) { cudaGraphExecDestroy(h->gcorr); h->gcorr = nullptr; }
     if (h->g32) { cudaGraphExecDestroy(h->g32); h->g32 = nullptr; }
 }
 
@@ -1833,6 +1865,7 @@ mg_status mg_destroy(mg_handle *h) {
     DeviceGuard dg(h->device);
     if (h->stream) cudaStreamSynchronize(h->stream);
     if (h->g64) cudaGraphExecDestroy(h->g64);
+    if (h->gcorr) cudaGraphExecDestroy(h->gcorr);
     for (auto &sg : h->gsetup)
         if (sg.exec) cudaGraphExecDestroy(sg.exec);
     if (h->g32) cudaGraphExecDestroy(h->g32);
@@ -1864,7 +1897,7 @@ struct mg_momentum {
     char *arena;
     double *rho, *mu;
     double *r0[3], *delta[3];          // initial residual and accumulated correction, per component
-    double2 *lamA, *lamB, *rA, *rB, *xA, *xB;
+    double2 *lamA, *lamB, *rA, *rB;
     double *fA[2][3], *fB[3], *fzero[3];
     double *partial, *norm_d, *norm_h;
 };
@@ -1982,6 +2015,7 @@ mg_status mg_momentum_create(const mg_grid *grid, int flags, const mg_options *i
         opt.max_cycles = 1;
     }
     if (opt.max_cycles < 1) return fail(MG_ERR_INVALID_ARG, "inner max_cycles must be >= 1");
+    if (opt.precision != MG_FP64) return fail(MG_ERR_INVALID_ARG, "the correction solves run in FP64 (MG_FP64)");
     opt.rtol = 0.0;
     const mg_grid gin = momentum_inner_grid(*grid);
     mg_momentum *m = new (std::nothrow) mg_momentum;
@@ -2012,15 +2046,13 @@ mg_status mg_momentum_create(const mg_grid *grid, int flags, const mg_options *i
         return o;
     };
     const size_t N = (size_t)m->N;
-    const size_t o_rho = take(N * 8), o_mu = take(N * 8), o_lamA = take(N * 32), o_rA = take(N * 16),
-                 o_xA = take(N * 16);
+    const size_t o_rho = take(N * 8), o_mu = take(N * 8), o_lamA = take(N * 32), o_rA = take(N * 16);
     size_t o_r0[3] = {}, o_d[3] = {};
     for (int a = 0; a < dim; a++) {
         o_r0[a] = take(N * 8);
         o_d[a] = take(N * 8);
     }
-    const size_t o_lamB = dim == 3 ? take(N * 32) : 0, o_rB = dim == 3 ? take(N * 16) : 0,
-                 o_xB = dim == 3 ? take(N * 16) : 0;
+    const size_t o_lamB = dim == 3 ? take(N * 32) : 0, o_rB = dim == 3 ? take(N * 16) : 0;
     size_t o_f[4][3] = {};
     for (int q = 0; q < (dim == 3 ? 4 : 2); q++)
         for (int a = 0; a < dim; a++) o_f[q][a] = take((size_t)nf[a] * 8);
@@ -2036,7 +2068,6 @@ mg_status mg_momentum_create(const mg_grid *grid, int flags, const mg_options *i
     m->mu = reinterpret_cast<double *>(at(o_mu));
     m->lamA = reinterpret_cast<double2 *>(at(o_lamA));
     m->rA = reinterpret_cast<double2 *>(at(o_rA));
-    m->xA = reinterpret_cast<double2 *>(at(o_xA));
     for (int a = 0; a < dim; a++) {
         m->r0[a] = reinterpret_cast<double *>(at(o_r0[a]));
         m->delta[a] = reinterpret_cast<double *>(at(o_d[a]));
@@ -2044,7 +2075,6 @@ mg_status mg_momentum_create(const mg_grid *grid, int flags, const mg_options *i
     if (dim == 3) {
         m->lamB = reinterpret_cast<double2 *>(at(o_lamB));
         m->rB = reinterpret_cast<double2 *>(at(o_rB));
-        m->xB = reinterpret_cast<double2 *>(at(o_xB));
     }
     for (int a = 0; a < dim; a++) {
         m->fA[0][a] = reinterpret_cast<double *>(at(o_f[0][a]));
@@ -2151,6 +2181,8 @@ mg_status mg_momentum_solve(mg_momentum *m, const double *const R[3], double *co
     const double *r0c[3] = {m->r0[0], m->r0[1], m->r0[2]};
     const double *dc[3] = {m->delta[0], m->delta[1], m->delta[2]};
     double r0 = 0.0, r = 0.0;
+    CK(cudaMemsetAsync(m->hA->err_d + 1, 0, sizeof(int), m->stream));
+    if (dim == 3) CK(cudaMemsetAsync(m->hB->err_d + 1, 0, sizeof(int), m->stream));
     mg_status st = momentum_residual(m, R, uc, m->r0, &r0);
     if (st) return st;
     for (int a = 0; a < dim; a++) CK(cudaMemsetAsync(m->delta[a], 0, (size_t)m->N * 8, m->stream));
@@ -2164,22 +2196,18 @@ mg_status mg_momentum_solve(mg_momentum *m, const double *const R[3], double *co
             result = rtol > 0.0 ? MG_ERR_NOT_CONVERGED : MG_OK;
             break;
         }
-        CK(cudaMemsetAsync(m->xA, 0, (size_t)m->N * 16, m->stream));
-        mg_stats sa;
-        if ((st = mg_solve(m->hA, reinterpret_cast<const double *>(m->rA), reinterpret_cast<double *>(m->xA), 1, &sa)))
-            return st;
-        cycles += sa.cycles;
         if (dim == 3) {
-            CK(cudaMemsetAsync(m->xB, 0, (size_t)m->N * 16, m->stream));
-            if ((st = mg_solve(m->hB, reinterpret_cast<const double *>(m->rB), reinterpret_cast<double *>(m->xB), 1,
-                               &sa)))
-                return st;
-            cycles += sa.cycles;
+            if ((st = correction_cycles<3>(m->hA, m->rA)) || (st = correction_cycles<3>(m->hB, m->rB))) return st;
+            cycles += 2 * m->hA->opt.max_cycles;
+        } else {
+            if ((st = correction_cycles<2>(m->hA, m->rA))) return st;
+            cycles += m->hA->opt.max_cycles;
         }
         const int blocks = (int)std::min<long long>((m->N + 255) / 256, 152LL * 16);
         double *const *d = m->delta;
-        if (dim == 3) k_mom_update<3><<<blocks, 256, 0, m->stream>>>(m->N, m->xA, m->xB, d[0], d[1], d[2]);
-        else k_mom_update<2><<<blocks, 256, 0, m->stream>>>(m->N, m->xA, m->xB, d[0], d[1], nullptr);
+        const double2 *xa = m->hA->L[0].x, *xb = dim == 3 ? m->hB->L[0].x : nullptr;
+        if (dim == 3) k_mom_update<3><<<blocks, 256, 0, m->stream>>>(m->N, xa, xb, d[0], d[1], d[2]);
+        else k_mom_update<2><<<blocks, 256, 0, m->stream>>>(m->N, xa, xb, d[0], d[1], nullptr);
         CK(cudaGetLastError());
         if ((st = momentum_residual(m, r0c, dc, nullptr, &r))) return st;
         it++;
@@ -2192,6 +2220,7 @@ mg_status mg_momentum_solve(mg_momentum *m, const double *const R[3], double *co
         else k_mom_add<2><<<blocks, 256, 0, m->stream>>>(m->N, d[0], d[1], nullptr, u[0], u[1], nullptr);
         CK(cudaGetLastError());
         CK(cudaStreamSynchronize(m->stream));
+        if ((st = handle_errors(m->hA)) || (dim == 3 && (st = handle_errors(m->hB)))) return st;
     }
     if (stats) {
         stats->iterations = it;

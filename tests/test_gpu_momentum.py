@@ -182,6 +182,10 @@ def test_invalid_use_rejected(torch_cuda):
     with pytest.raises(MgError) as e:
         B.check(B.load().mg_momentum_create(C.byref(B.make_grid(g)), 4, None, None, C.byref(h)))
     assert e.value.status == MG_ERR_INVALID_ARG
+    o = B.make_options("mixed", 0.0, 1)                  # the correction solves run in FP64
+    with pytest.raises(MgError) as e:
+        B.check(B.load().mg_momentum_create(C.byref(B.make_grid(g)), 0, C.byref(o), None, C.byref(h)))
+    assert e.value.status == MG_ERR_INVALID_ARG
     m.close()
 
 
