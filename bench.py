@@ -672,6 +672,8 @@ def run_momentum(args):
         ms /= args.steps
         out["regimes"].append({"dt": dt, "solves_per_s": 1e3 / ms, "ms_per_solve": ms,
                                "iterations": stats[0]["iterations"], "cycles": stats[0]["cycles"],
+                               "corrections": "point-Jacobi" if stats[0]["jacobi"] else "multigrid",
+                               "jacobi_bound": stats[0]["nu"],
                                "rfinal_over_r0": stats[0]["rfinal"] / stats[0]["r0"] if stats[0]["r0"] else 0.0,
                                "clocks": clk})
     m.close()

@@ -397,8 +397,13 @@ MG_API mg_status mg_energy_async(const mg_grid *grid, const mg_phase phases[2], 
  * Solution: defect correction on the full residual r = R - A(u); each step
  * solves the component-diagonal part of A (mu weighted 2x on the faces normal
  * to a component) with the pair multigrid of this library, (u_x, u_y) in one
- * hierarchy and, in 3D, u_z in a second.  Stopping norm ||dt r / rho||_2 over
- * all components and cells.
+ * hierarchy and, in 3D, u_z in a second.  When the set-up finds the Jacobi
+ * bound nu = max over rows of 2 (sum of the component-diagonal operator's
+ * off-diagonal entries) / diagonal at most 0.01 (the viscous diffusion number
+ * is small: the mass term rho/dt dominates), each step is instead a
+ * point-Jacobi step, which contracts the residual at least by nu, and no
+ * hierarchy is set up.  Stopping norm ||dt r / rho||_2 over all components and
+ * cells.
  * All arrays are device pointers of the handle's device; u, R, y are per
  * component, [N] each (cells in the layout above).  Not thread-safe.
  * ------------------------------------------------------------------------- */
@@ -410,11 +415,15 @@ typedef struct {
     double r0, rfinal;        /* stopping norm ||dt r / rho||_2 at the start and at the end */
     double seconds;           /* wall time of the call */
     int status;               /* mg_status of the solve */
+    int jacobi;               /* 1: the corrections were point-Jacobi steps, 0: multigrid */
+    double nu;                /* Jacobi bound of the set-up: max over rows of 2 (off-diagonal sum) / diagonal */
 } mg_momentum_stats;
 
-enum { MG_MOMENTUM_NO_SLIP = 1 };
+/* MG_MOMENTUM_MULTIGRID: multigrid corrections whatever the Jacobi bound. */
+enum { MG_MOMENTUM_NO_SLIP = 1, MG_MOMENTUM_MULTIGRID = 2 };
 
-/* grid: as for mg_create; flags: 0 or MG_MOMENTUM_NO_SLIP.  inner: options of
+/* grid: as for mg_create; flags: MG_MOMENTUM_NO_SLIP, MG_MOMENTUM_MULTIGRID or
+ * both.  inner: options of
  * the correction solves (NULL: library defaults with one cycle per step);
  * precision must be MG_FP64, rtol is ignored and max_cycles is the number of
  * cycles per correction (run from zero, without stopping norms).  stream: a

@@ -124,11 +124,12 @@ class MgPhase(C.Structure):
 
 class MgMomentumStats(C.Structure):
     _fields_ = [("iterations", C.c_int), ("cycles", C.c_int), ("r0", C.c_double), ("rfinal", C.c_double),
-                ("seconds", C.c_double), ("status", C.c_int)]
+                ("seconds", C.c_double), ("status", C.c_int), ("jacobi", C.c_int), ("nu", C.c_double)]
 
     def as_dict(self) -> dict:
         return dict(iterations=self.iterations, cycles=self.cycles, r0=self.r0, rfinal=self.rfinal,
-                    seconds=self.seconds, status=STATUS_NAMES.get(self.status, self.status))
+                    seconds=self.seconds, status=STATUS_NAMES.get(self.status, self.status),
+                    jacobi=bool(self.jacobi), nu=self.nu)
 
 
 class MgState(C.Structure):
@@ -302,7 +303,7 @@ def make_phase(ph) -> MgPhase:
 
 
 MG_ASSEMBLE_LAMBDA4_PRINTED, MG_ASSEMBLE_HARMONIC_K = 1, 2
-MG_MOMENTUM_NO_SLIP = 1
+MG_MOMENTUM_NO_SLIP, MG_MOMENTUM_MULTIGRID = 1, 2
 
 
 def assemble(grid, phases, dt: float, C_, m1, m2, E, mom: Sequence, uf: Sequence, out: dict,
@@ -576,7 +577,7 @@ class Momentum:
     Arrays are contiguous float64 CUDA tensors of the grid's cells, one per velocity component."""
 
     def __init__(self, grid, no_slip: bool = False, inner_cycles_per_step: int = 1, nu1=2, nu2=2,
-                 coarse_min=4, device: Optional[int] = None, stream=None):
+                 coarse_min=4, device: Optional[int] = None, stream=None, multigrid_only: bool = False):
         import torch
         lib = load()
         self._lib = lib
@@ -589,7 +590,8 @@ class Momentum:
             stream = torch.cuda.current_stream(dev)
         self.stream = stream
         handle = C.c_void_p()
-        check(lib.mg_momentum_create(C.byref(self.grid), MG_MOMENTUM_NO_SLIP if no_slip else 0, C.byref(opt),
+        flags = (MG_MOMENTUM_NO_SLIP if no_slip else 0) | (MG_MOMENTUM_MULTIGRID if multigrid_only else 0)
+        check(lib.mg_momentum_create(C.byref(self.grid), flags, C.byref(opt),
                                      C.c_void_p(stream.cuda_stream), C.byref(handle)))
         self._h = handle
 

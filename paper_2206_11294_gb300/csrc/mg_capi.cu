@@ -1897,6 +1897,9 @@ struct mg_momentum {
     char *arena;
     double *rho, *mu;
     double *r0[3], *delta[3];          // initial residual and accumulated correction, per component
+    double *inv_diag[3];               // 1 / diagonal of the component-diagonal operator, per component
+    double nu;                         // Jacobi bound of the last set-up: max over rows of 2 off / diag
+    bool jacobi;                       // corrections by point-Jacobi (no hierarchy set up)
     double2 *lamA, *lamB, *rA, *rB;
     double *fA[2][3], *fB[3], *fzero[3];
     double *partial, *norm_d, *norm_h;
@@ -2006,7 +2009,7 @@ mg_status mg_momentum_create(const mg_grid *grid, int flags, const mg_options *i
     *out = nullptr;
     mg_status st = check_grid_geom(grid);
     if (st) return st;
-    if (flags & ~MG_MOMENTUM_NO_SLIP) return fail(MG_ERR_INVALID_ARG, "unknown momentum flags");
+    if (flags & ~(MG_MOMENTUM_NO_SLIP | MG_MOMENTUM_MULTIGRID)) return fail(MG_ERR_INVALID_ARG, "unknown momentum flags");
     mg_options opt;
     if (inner) {
         opt = *inner;
@@ -2047,10 +2050,11 @@ mg_status mg_momentum_create(const mg_grid *grid, int flags, const mg_options *i
     };
     const size_t N = (size_t)m->N;
     const size_t o_rho = take(N * 8), o_mu = take(N * 8), o_lamA = take(N * 32), o_rA = take(N * 16);
-    size_t o_r0[3] = {}, o_d[3] = {};
+    size_t o_r0[3] = {}, o_d[3] = {}, o_id[3] = {};
     for (int a = 0; a < dim; a++) {
         o_r0[a] = take(N * 8);
         o_d[a] = take(N * 8);
+        o_id[a] = take(N * 8);
     }
     const size_t o_lamB = dim == 3 ? take(N * 32) : 0, o_rB = dim == 3 ? take(N * 16) : 0;
     size_t o_f[4][3] = {};
@@ -2071,6 +2075,7 @@ mg_status mg_momentum_create(const mg_grid *grid, int flags, const mg_options *i
     for (int a = 0; a < dim; a++) {
         m->r0[a] = reinterpret_cast<double *>(at(o_r0[a]));
         m->delta[a] = reinterpret_cast<double *>(at(o_d[a]));
+        m->inv_diag[a] = reinterpret_cast<double *>(at(o_id[a]));
     }
     if (dim == 3) {
         m->lamB = reinterpret_cast<double2 *>(at(o_lamB));
@@ -2111,8 +2116,11 @@ mg_status mg_momentum_set_coeffs(mg_momentum *m, double dt, const double *rho, c
     A.r0 = g.r0;
     A.h = g.h;
     A.inv_dt = 1.0 / dt;
+    A.inv_h2 = 1.0 / (g.h * g.h);
     A.rho = rho;
     A.mu = mu;
+    A.partial = m->partial;        // one Jacobi bound per block
+    for (int a = 0; a < dim; a++) A.inv_diag[a] = m->inv_diag[a];
     A.rho_o = m->rho;
     A.mu_o = m->mu;
     A.lamA = m->lamA;
@@ -2127,14 +2135,27 @@ mg_status mg_momentum_set_coeffs(mg_momentum *m, double dt, const double *rho, c
     else if (g.axisym) k_mom_coeffs<2, true><<<gr, kBlock, 0, m->stream>>>(A);
     else k_mom_coeffs<2, false><<<gr, kBlock, 0, m->stream>>>(A);
     CK(cudaGetLastError());
-    const double *faA[3] = {m->fA[1][0], m->fA[1][1], m->fA[1][2]};
-    const double *fkA[3] = {m->fA[0][0], m->fA[0][1], m->fA[0][2]};
-    mg_status st = mg_set_coeffs(m->hA, reinterpret_cast<const double *>(m->lamA), faA, fkA, 1);
-    if (st) return st;
-    if (dim == 3) {
-        const double *faB[3] = {m->fzero[0], m->fzero[1], m->fzero[2]};
-        const double *fkB[3] = {m->fB[0], m->fB[1], m->fB[2]};
-        if ((st = mg_set_coeffs(m->hB, reinterpret_cast<const double *>(m->lamB), faB, fkB, 1))) return st;
+    k_mom_max<<<1, 1024, 0, m->stream>>>(m->partial, m->nblocks, m->norm_d);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(m->norm_h, m->norm_d, sizeof(double), cudaMemcpyDeviceToHost, m->stream));
+    CK(cudaStreamSynchronize(m->stream));
+    const double nu = m->norm_h[0];
+    if (!std::isfinite(nu)) return fail(MG_ERR_INVALID_COEFF, "non-finite momentum coefficients");
+    m->nu = nu;
+    // Point-Jacobi corrections contract the residual by at least nu per step; below kJacobiNu they beat a V-cycle
+    // and need no hierarchy.
+    constexpr double kJacobiNu = 0.01;
+    m->jacobi = !(m->flags & MG_MOMENTUM_MULTIGRID) && nu <= kJacobiNu;
+    if (!m->jacobi) {
+        const double *faA[3] = {m->fA[1][0], m->fA[1][1], m->fA[1][2]};
+        const double *fkA[3] = {m->fA[0][0], m->fA[0][1], m->fA[0][2]};
+        mg_status st = mg_set_coeffs(m->hA, reinterpret_cast<const double *>(m->lamA), faA, fkA, 1);
+        if (st) return st;
+        if (dim == 3) {
+            const double *faB[3] = {m->fzero[0], m->fzero[1], m->fzero[2]};
+            const double *fkB[3] = {m->fB[0], m->fB[1], m->fB[2]};
+            if ((st = mg_set_coeffs(m->hB, reinterpret_cast<const double *>(m->lamB), faB, fkB, 1))) return st;
+        }
     }
     m->dt = dt;
     m->have_coeffs = true;
@@ -2196,18 +2217,28 @@ mg_status mg_momentum_solve(mg_momentum *m, const double *const R[3], double *co
             result = rtol > 0.0 ? MG_ERR_NOT_CONVERGED : MG_OK;
             break;
         }
-        if (dim == 3) {
-            if ((st = correction_cycles<3>(m->hA, m->rA)) || (st = correction_cycles<3>(m->hB, m->rB))) return st;
-            cycles += 2 * m->hA->opt.max_cycles;
-        } else {
-            if ((st = correction_cycles<2>(m->hA, m->rA))) return st;
-            cycles += m->hA->opt.max_cycles;
-        }
         const int blocks = (int)std::min<long long>((m->N + 255) / 256, 152LL * 16);
         double *const *d = m->delta;
-        const double2 *xa = m->hA->L[0].x, *xb = dim == 3 ? m->hB->L[0].x : nullptr;
-        if (dim == 3) k_mom_update<3><<<blocks, 256, 0, m->stream>>>(m->N, xa, xb, d[0], d[1], d[2]);
-        else k_mom_update<2><<<blocks, 256, 0, m->stream>>>(m->N, xa, xb, d[0], d[1], nullptr);
+        double *const *id = m->inv_diag;
+        if (m->jacobi) {
+            if (dim == 3)
+                k_mom_jacobi<3><<<blocks, 256, 0, m->stream>>>(m->N, m->rA, m->rB, id[0], id[1], id[2], d[0], d[1],
+                                                               d[2]);
+            else
+                k_mom_jacobi<2><<<blocks, 256, 0, m->stream>>>(m->N, m->rA, nullptr, id[0], id[1], nullptr, d[0],
+                                                               d[1], nullptr);
+        } else {
+            if (dim == 3) {
+                if ((st = correction_cycles<3>(m->hA, m->rA)) || (st = correction_cycles<3>(m->hB, m->rB))) return st;
+                cycles += 2 * m->hA->opt.max_cycles;
+            } else {
+                if ((st = correction_cycles<2>(m->hA, m->rA))) return st;
+                cycles += m->hA->opt.max_cycles;
+            }
+            const double2 *xa = m->hA->L[0].x, *xb = dim == 3 ? m->hB->L[0].x : nullptr;
+            if (dim == 3) k_mom_update<3><<<blocks, 256, 0, m->stream>>>(m->N, xa, xb, d[0], d[1], d[2]);
+            else k_mom_update<2><<<blocks, 256, 0, m->stream>>>(m->N, xa, xb, d[0], d[1], nullptr);
+        }
         CK(cudaGetLastError());
         if ((st = momentum_residual(m, r0c, dc, nullptr, &r))) return st;
         it++;
@@ -2220,7 +2251,7 @@ mg_status mg_momentum_solve(mg_momentum *m, const double *const R[3], double *co
         else k_mom_add<2><<<blocks, 256, 0, m->stream>>>(m->N, d[0], d[1], nullptr, u[0], u[1], nullptr);
         CK(cudaGetLastError());
         CK(cudaStreamSynchronize(m->stream));
-        if ((st = handle_errors(m->hA)) || (dim == 3 && (st = handle_errors(m->hB)))) return st;
+        if (!m->jacobi && ((st = handle_errors(m->hA)) || (dim == 3 && (st = handle_errors(m->hB))))) return st;
     }
     if (stats) {
         stats->iterations = it;
@@ -2229,6 +2260,8 @@ mg_status mg_momentum_solve(mg_momentum *m, const double *const R[3], double *co
         stats->rfinal = r;
         stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
         stats->status = result;
+        stats->jacobi = m->jacobi ? 1 : 0;
+        stats->nu = m->nu;
     }
     if (result) return fail(result, "momentum solve did not reach rtol in max_iters steps");
     return MG_OK;

@@ -25,20 +25,63 @@ struct MomCoeffArgs {
     int n[3];
     int wall[3][2];          // wall faces (normal component held at zero)
     int no_slip;
-    double r0, h, inv_dt;
+    double r0, h, inv_dt, inv_h2;
     const double *rho, *mu;
     double *rho_o, *mu_o;    // owned copies for the residual
     double2 *lamA, *lamB;    // [N][2 pairs] of the inner hierarchies (B: 3D, component z)
     double *fA[2][3];        // face coefficients of components 0 and 1 (inner T and p slots)
     double *fB[3];           // component 2 (3D)
+    double *inv_diag[3];     // per component: 1 / the diagonal of the component-diagonal operator
+    double *partial;         // per block: the largest Jacobi bound 2 off / diag of its cells and components
 };
 
+// Coefficient of component q on the face of axis a on side sd (0 low, 1 high) of a cell: 2 mu_f on faces normal to
+// q, mu_f on the others; boundary faces mu of the cell at walls (normal component, or every component with
+// no-slip), else 0.  Also the ghost factor: 2 at a wall face (value zero half a cell away), 1 inside.
+__device__ __forceinline__ double mom_face_coef(const MomCoeffArgs &A, int q, int a, int sd, const int pos[3],
+                                                long long c, double mu, double *fac) {
+    const int fpos = pos[a] + sd;
+    double base;
+    if (fpos == 0 || fpos == A.n[a]) {
+        const bool w = A.wall[a][sd] != 0;
+        base = w && (q == a || A.no_slip) ? mu : 0.0;
+        *fac = 2.0;
+    } else {
+        const long long st = a == 0 ? 1LL : a == 1 ? (long long)A.n[0] : (long long)A.n[0] * A.n[1];
+        base = 0.5 * (mu + A.mu[sd ? c + st : c - st]);
+        *fac = 1.0;
+    }
+    return q == a ? 2.0 * base : base;
+}
+
+template <int DIM, bool AXI>
+__device__ __forceinline__ double mom_coeffs_cell(const MomCoeffArgs &A, int i, int j, int k);
+
+// Coefficients of the correction hierarchies, the inverse diagonals and, per block, the largest Jacobi bound.
 template <int DIM, bool AXI>
 __global__ void __launch_bounds__(256) k_mom_coeffs(const __grid_constant__ MomCoeffArgs A) {
+    __shared__ double red[8];
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     const int k = DIM == 3 ? (int)blockIdx.z : 0;
-    if (i >= A.n[0] || j >= A.n[1]) return;
+    double nu = (i < A.n[0] && j < A.n[1]) ? mom_coeffs_cell<DIM, AXI>(A, i, j, k) : 0.0;
+    const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double y = __shfl_down_sync(0xffffffffu, nu, o);
+        nu = (y > nu || y != y) ? y : nu;
+    }
+    if ((tid & 31) == 0) red[tid >> 5] = nu;
+    __syncthreads();
+    if (tid == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x * blockDim.y) / 32; w++) t = (red[w] > t || red[w] != red[w]) ? red[w] : t;
+        A.partial[blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * (long long)blockIdx.z)] = t;
+    }
+}
+
+template <int DIM, bool AXI>
+__device__ __forceinline__ double mom_coeffs_cell(const MomCoeffArgs &A, int i, int j, int k) {
     const int n0 = A.n[0], n1 = A.n[1];
     const long long c = (long long)i + (long long)n0 * ((long long)j + (long long)n1 * k);
     const double rho = A.rho[c], mu = A.mu[c];
@@ -52,6 +95,34 @@ __global__ void __launch_bounds__(256) k_mom_coeffs(const __grid_constant__ MomC
     }
     A.lamA[2 * c] = make_double2(l0, 0.0);
     A.lamA[2 * c + 1] = make_double2(m, 0.0);
+    double bound;
+    {
+        // diagonal of the component-diagonal operator and the Jacobi bound: the off-diagonal entries of a row
+        // (its face coefficients, and at most as much again from the cross terms) against its diagonal
+        const int pos[3] = {i, j, k};
+        double ri = 0.0;
+        if (AXI) ri = A.r0 + (i + 0.5) * A.h;
+        double nu = 0.0;
+#pragma unroll
+        for (int q = 0; q < DIM; q++) {
+            double off = 0.0;
+#pragma unroll
+            for (int a = 0; a < DIM; a++) {
+#pragma unroll
+                for (int sd = 0; sd < 2; sd++) {
+                    double fac;
+                    const double cf = mom_face_coef(A, q, a, sd, pos, c, mu, &fac);
+                    const double w = (AXI && a == 0) ? (ri + (sd ? 0.5 : -0.5) * A.h) / ri : 1.0;
+                    off += w * cf * fac * A.inv_h2;
+                }
+            }
+            const double diag = rho * A.inv_dt + off + ((AXI && q == 0) ? 2.0 * mu / (ri * ri) : 0.0);
+            A.inv_diag[q][c] = 1.0 / diag;
+            const double b = 2.0 * off / diag;
+            nu = (b > nu || b != b) ? b : nu;
+        }
+        bound = nu;
+    }
     if (DIM == 3) {
         A.lamB[2 * c] = make_double2(m, 0.0);
         A.lamB[2 * c + 1] = make_double2(m, 0.0);           // unused slot: p = 0 for a zero right-hand side
@@ -83,6 +154,7 @@ __global__ void __launch_bounds__(256) k_mom_coeffs(const __grid_constant__ MomC
             if (DIM == 3) A.fB[a][f] = a == 2 ? 2.0 * base[2] : base[2];
         }
     }
+    return bound;
 }
 
 struct MomArgs {
@@ -253,6 +325,41 @@ __global__ void __launch_bounds__(TX * TY) k_mom_residual(const __grid_constant_
             for (int w = 0; w < TX * TY / 32; w++) b += red[w];
             A.partial[blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * (long long)blockIdx.z)] = b;
         }
+    }
+}
+
+// Largest value of an array (one block); non-finite values propagate as NaN.
+__global__ void __launch_bounds__(1024) k_mom_max(const double *v, long long n, double *out) {
+    __shared__ double red[32];
+    double s = 0.0;
+    for (long long b = threadIdx.x; b < n; b += blockDim.x) {
+        const double x = v[b];
+        s = (x > s || x != x) ? x : s;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double y = __shfl_down_sync(0xffffffffu, s, o);
+        s = (y > s || y != y) ? y : s;
+    }
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) t = (red[w] > t || red[w] != red[w]) ? red[w] : t;
+        out[0] = t;
+    }
+}
+
+// Point-Jacobi correction: delta_q += r_q / diag_q, r read back from the correction right-hand sides (-r).
+template <int DIM>
+__global__ void __launch_bounds__(256) k_mom_jacobi(long long N, const double2 *rA, const double2 *rB,
+                                                    const double *i0, const double *i1, const double *i2, double *d0,
+                                                    double *d1, double *d2) {
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
+        const double2 r = rA[c];
+        d0[c] -= r.x * i0[c];
+        d1[c] -= r.y * i1[c];
+        if (DIM == 3) d2[c] -= rB[c].x * i2[c];
     }
 }
 

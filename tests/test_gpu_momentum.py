@@ -153,6 +153,41 @@ def test_full_size_bubbles_state(torch_cuda, orc):
         # R - A(u) is formed from terms of size rho u / dt: below a few ulps of those no check can see further
         floor = 16 * np.finfo(float).eps * np.sqrt(sum(np.sum((dt * r / rho) ** 2) for r in R))
         assert num <= 2e-10 * den + floor, (dt, num, den, floor, st)
+        # the diffusion number picks the corrections: point-Jacobi at the time step's dt, multigrid at 1e-3
+        assert st["jacobi"] == (dt == 1e-7), st
+        if dt == 1e-7:
+            mg = Momentum(g, multigrid_only=True)
+            mg.set_coeffs(dt, _dev(torch, rho), _dev(torch, mu))
+            um = [_dev(torch, v) for v in u0]
+            sm = mg.solve([_dev(torch, r) for r in R], um, rtol=1e-10, max_iters=200)
+            assert not sm["jacobi"] and sm["nu"] == st["nu"], (sm, st)
+            for c in range(g.dim):
+                d_j = u[c] - u0[c]
+                d_m = um[c].cpu().numpy() - u0[c]
+                assert np.linalg.norm(d_j - d_m) <= 1e-8 * np.linalg.norm(d_j), c
+            mg.close()
+    m.close()
+
+
+@pytest.mark.parametrize("name", list(GRIDS))
+def test_jacobi_corrections_recover_discrete_solution(torch_cuda, orc, name):
+    """A small diffusion number (mu dt / (rho h^2) <= 1e-5, Jacobi bound <= 2e-3 in 3D): point-Jacobi corrections,
+    no hierarchy."""
+    from paper_2206_11294_gb300.binding import Momentum
+    torch = torch_cuda
+    g = GRIDS[name]
+    rho, mu, _, exact = _fields(g, 95 + len(name))
+    mu = mu * 1e-4
+    dt = 1e-4
+    R = orc.apply(g, rho, mu, dt, exact)
+    m = Momentum(g)
+    m.set_coeffs(dt, _dev(torch, rho), _dev(torch, mu))
+    ud = [torch.zeros(rho.shape, dtype=torch.float64, device="cuda") for _ in range(g.dim)]
+    st = m.solve([_dev(torch, r) for r in R], ud, rtol=1e-12, max_iters=50)
+    assert st["jacobi"] and st["cycles"] == 0 and st["iterations"] <= 6, st
+    for c in range(g.dim):
+        err = np.linalg.norm(ud[c].cpu().numpy() - exact[c]) / np.linalg.norm(exact[c])
+        assert err <= 1e-11, (c, err, st)
     m.close()
 
 
