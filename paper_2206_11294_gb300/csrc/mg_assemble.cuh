@@ -232,29 +232,37 @@ struct EnergyArgs {
     double *E1o, *E2o;
 };
 
-// Velocity component a at a cell: the mean of its two faces of axis a.
-template <int DIM>
-__device__ __forceinline__ double cell_u(const EnergyArgs &A, int a, int i, int j, int k) {
-    const long long f = face_index(A.n, a, i, j, k);
-    const long long st = a == 0 ? 1LL : a == 1 ? (long long)A.n[0] : (long long)A.n[0] * A.n[1];
-    return 0.5 * (A.uf[a][f] + A.uf[a][f + st]);
-}
+// Cell velocities of a block's tile and a one-cell halo (planes k-1..k+1 in 3D), staged in shared memory: the
+// mean of each cell's two faces of each axis.  Every cell an interior face flux of the tile reads - its two cells
+// and their neighbours for the tangential derivatives - lies in this region; staged cells outside the grid hold 0
+// and are never read (derivatives are clamped to the grid).
+template <int DIM, int TX, int TY>
+struct EnergyTile {
+    static constexpr int SX = TX + 2, SY = TY + 2, SZ = DIM == 3 ? 3 : 1, NS = SX * SY * SZ;
+    int i0, j0, k0;
+    const double *U;                 // [DIM][NS]
+    __device__ __forceinline__ double u(int q, int i, int j, int k) const {
+        return U[q * NS + (i - i0 + 1) + SX * ((j - j0 + 1) + SY * (DIM == 3 ? k - k0 + 1 : 0))];
+    }
+};
 
-// d u_a / d x_b at cell pos: central inside, one-sided in the first and last cell.
-template <int DIM>
-__device__ __forceinline__ double cell_du(const EnergyArgs &A, int a, int b, const int pos[3]) {
+// d u_a / d x_b at a cell from the staged velocities: central inside, one-sided in the first and last cell.
+template <int DIM, int TX, int TY>
+__device__ __forceinline__ double cell_du(const EnergyArgs &A, const EnergyTile<DIM, TX, TY> &S, int a, int b,
+                                          const int pos[3]) {
     const int nb = A.n[b];
     if (nb < 2) return 0.0;
     int up[3] = {pos[0], pos[1], pos[2]}, dn[3] = {pos[0], pos[1], pos[2]};
     up[b] = pos[b] + 1 < nb ? pos[b] + 1 : pos[b];
     dn[b] = pos[b] > 0 ? pos[b] - 1 : pos[b];
-    const double d = cell_u<DIM>(A, a, up[0], up[1], up[2]) - cell_u<DIM>(A, a, dn[0], dn[1], dn[2]);
+    const double d = S.u(a, up[0], up[1], up[2]) - S.u(a, dn[0], dn[1], dn[2]);
     return d * (up[b] - dn[b] == 2 ? A.half_inv_h : A.inv_h);
 }
 
 // (F_1, F_2) on the face of axis a at face position f (f[a] in 0..n[a]).
-template <int DIM>
-__device__ __forceinline__ double2 energy_face_flux(const EnergyArgs &A, int a, const int f[3]) {
+template <int DIM, int TX, int TY>
+__device__ __forceinline__ double2 energy_face_flux(const EnergyArgs &A, const EnergyTile<DIM, TX, TY> &S, int a,
+                                                    const int f[3]) {
     const int fa = f[a];
     const double u_f = A.uf[a][face_index(A.n, a, f[0], f[1], f[2])];
     if (fa == 0 || fa == A.n[a]) {
@@ -276,13 +284,13 @@ __device__ __forceinline__ double2 energy_face_flux(const EnergyArgs &A, int a, 
     double visc = 0.0;
 #pragma unroll
     for (int b = 0; b < DIM; b++) {
-        const double ubL = cell_u<DIM>(A, b, L[0], L[1], L[2]), ubR = cell_u<DIM>(A, b, R[0], R[1], R[2]);
+        const double ubL = S.u(b, L[0], L[1], L[2]), ubR = S.u(b, R[0], R[1], R[2]);
         double s, ub;
         if (b == a) {
             s = 2.0 * (ubR - ubL) * A.inv_h;
             ub = u_f;
         } else {
-            s = 0.5 * (cell_du<DIM>(A, a, b, L) + cell_du<DIM>(A, a, b, R)) + (ubR - ubL) * A.inv_h;
+            s = 0.5 * (cell_du<DIM, TX, TY>(A, S, a, b, L) + cell_du<DIM, TX, TY>(A, S, a, b, R)) + (ubR - ubL) * A.inv_h;
             ub = 0.5 * (ubL + ubR);
         }
         visc = b == 0 ? s * ub : visc + s * ub;
@@ -294,9 +302,25 @@ __device__ __forceinline__ double2 energy_face_flux(const EnergyArgs &A, int a, 
 template <int DIM, bool AXI, int TX, int TY>
 __global__ void __launch_bounds__(TX * TY) k_energy(const __grid_constant__ EnergyArgs A) {
     constexpr int NX = (TX + 1) * TY, NY = TX * (TY + 1), NZ = DIM == 3 ? 2 * TX * TY : 0;
+    using Tile = EnergyTile<DIM, TX, TY>;
     __shared__ double2 F[NX + NY + NZ];
+    __shared__ double U[DIM * Tile::NS];
     const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY, k = DIM == 3 ? (int)blockIdx.z : 0;
     const int tid = threadIdx.x + TX * threadIdx.y;
+    for (int t = tid; t < DIM * Tile::NS; t += TX * TY) {
+        const int q = t / Tile::NS, v = t - q * Tile::NS;
+        const int si = v % Tile::SX, sj = (v / Tile::SX) % Tile::SY, sk = v / (Tile::SX * Tile::SY);
+        const int ci = i0 - 1 + si, cj = j0 - 1 + sj, ck = DIM == 3 ? k - 1 + sk : 0;
+        double val = 0.0;
+        if (ci >= 0 && ci < A.n[0] && cj >= 0 && cj < A.n[1] && ck >= 0 && ck < A.n[2]) {
+            const long long f = face_index(A.n, q, ci, cj, ck);
+            const long long st = q == 0 ? 1LL : q == 1 ? (long long)A.n[0] : (long long)A.n[0] * A.n[1];
+            val = 0.5 * (A.uf[q][f] + A.uf[q][f + st]);
+        }
+        U[t] = val;
+    }
+    __syncthreads();
+    const Tile S{i0, j0, k, U};
     for (int t = tid; t < NX + NY + NZ; t += TX * TY) {
         int a, f[3];
         if (t < NX) {
@@ -320,7 +344,7 @@ __global__ void __launch_bounds__(TX * TY) k_energy(const __grid_constant__ Ener
         bool in = true;
 #pragma unroll
         for (int b = 0; b < 3; b++) in = in && f[b] < A.n[b] + (b == a);
-        F[t] = in ? energy_face_flux<DIM>(A, a, f) : make_double2(0.0, 0.0);
+        F[t] = in ? energy_face_flux<DIM, TX, TY>(A, S, a, f) : make_double2(0.0, 0.0);
     }
     __syncthreads();
     const int li = threadIdx.x, lj = threadIdx.y, i = i0 + li, j = j0 + lj;
