@@ -1895,7 +1895,7 @@ struct mg_momentum {
     double dt;
     bool have_coeffs;
     char *arena;
-    double *rho, *mu;
+    double *rho_dt, *wgt, *mu;         // rho / dt, dt / rho and mu per cell (owned copies)
     double *r0[3], *delta[3];          // initial residual and accumulated correction, per component
     double *inv_diag[3];               // 1 / diagonal of the component-diagonal operator, per component
     double nu;                         // Jacobi bound of the last set-up: max over rows of 2 off / diag
@@ -1939,7 +1939,8 @@ MomArgs momentum_args(const mg_momentum *m) {
     A.two_inv_h = 2.0 / g.h;
     A.inv_dt = 1.0 / m->dt;
     A.dt = m->dt;
-    A.rho = m->rho;
+    A.rho_dt = m->rho_dt;
+    A.wgt = m->wgt;
     A.mu = m->mu;
     return A;
 }
@@ -2049,7 +2050,8 @@ mg_status mg_momentum_create(const mg_grid *grid, int flags, const mg_options *i
         return o;
     };
     const size_t N = (size_t)m->N;
-    const size_t o_rho = take(N * 8), o_mu = take(N * 8), o_lamA = take(N * 32), o_rA = take(N * 16);
+    const size_t o_rho = take(N * 8), o_wgt = take(N * 8), o_mu = take(N * 8), o_lamA = take(N * 32),
+                 o_rA = take(N * 16);
     size_t o_r0[3] = {}, o_d[3] = {}, o_id[3] = {};
     for (int a = 0; a < dim; a++) {
         o_r0[a] = take(N * 8);
@@ -2068,7 +2070,8 @@ mg_status mg_momentum_create(const mg_grid *grid, int flags, const mg_options *i
         return fail(MG_ERR_OOM, "device allocation failed");
     }
     auto at = [&](size_t o) { return m->arena + o; };
-    m->rho = reinterpret_cast<double *>(at(o_rho));
+    m->rho_dt = reinterpret_cast<double *>(at(o_rho));
+    m->wgt = reinterpret_cast<double *>(at(o_wgt));
     m->mu = reinterpret_cast<double *>(at(o_mu));
     m->lamA = reinterpret_cast<double2 *>(at(o_lamA));
     m->rA = reinterpret_cast<double2 *>(at(o_rA));
@@ -2115,13 +2118,15 @@ mg_status mg_momentum_set_coeffs(mg_momentum *m, double dt, const double *rho, c
     A.no_slip = (m->flags & MG_MOMENTUM_NO_SLIP) ? 1 : 0;
     A.r0 = g.r0;
     A.h = g.h;
+    A.dt = dt;
     A.inv_dt = 1.0 / dt;
     A.inv_h2 = 1.0 / (g.h * g.h);
     A.rho = rho;
     A.mu = mu;
     A.partial = m->partial;        // one Jacobi bound per block
     for (int a = 0; a < dim; a++) A.inv_diag[a] = m->inv_diag[a];
-    A.rho_o = m->rho;
+    A.rho_dt = m->rho_dt;
+    A.wgt = m->wgt;
     A.mu_o = m->mu;
     A.lamA = m->lamA;
     A.lamB = m->lamB;
@@ -2131,9 +2136,9 @@ mg_status mg_momentum_set_coeffs(mg_momentum *m, double dt, const double *rho, c
         A.fB[a] = m->fB[a];
     }
     const dim3 gr = cell_grid(g);
-    if (dim == 3) k_mom_coeffs<3, false><<<gr, kBlock, 0, m->stream>>>(A);
-    else if (g.axisym) k_mom_coeffs<2, true><<<gr, kBlock, 0, m->stream>>>(A);
-    else k_mom_coeffs<2, false><<<gr, kBlock, 0, m->stream>>>(A);
+    if (dim == 3) k_mom_diag<3, false><<<gr, kBlock, 0, m->stream>>>(A);
+    else if (g.axisym) k_mom_diag<2, true><<<gr, kBlock, 0, m->stream>>>(A);
+    else k_mom_diag<2, false><<<gr, kBlock, 0, m->stream>>>(A);
     CK(cudaGetLastError());
     k_mom_max<<<1, 1024, 0, m->stream>>>(m->partial, m->nblocks, m->norm_d);
     CK(cudaGetLastError());
@@ -2147,6 +2152,10 @@ mg_status mg_momentum_set_coeffs(mg_momentum *m, double dt, const double *rho, c
     constexpr double kJacobiNu = 0.01;
     m->jacobi = !(m->flags & MG_MOMENTUM_MULTIGRID) && nu <= kJacobiNu;
     if (!m->jacobi) {
+        if (dim == 3) k_mom_hier<3, false><<<gr, kBlock, 0, m->stream>>>(A);
+        else if (g.axisym) k_mom_hier<2, true><<<gr, kBlock, 0, m->stream>>>(A);
+        else k_mom_hier<2, false><<<gr, kBlock, 0, m->stream>>>(A);
+        CK(cudaGetLastError());
         const double *faA[3] = {m->fA[1][0], m->fA[1][1], m->fA[1][2]};
         const double *fkA[3] = {m->fA[0][0], m->fA[0][1], m->fA[0][2]};
         mg_status st = mg_set_coeffs(m->hA, reinterpret_cast<const double *>(m->lamA), faA, fkA, 1);

@@ -25,46 +25,74 @@ struct MomCoeffArgs {
     int n[3];
     int wall[3][2];          // wall faces (normal component held at zero)
     int no_slip;
-    double r0, h, inv_dt, inv_h2;
-    const double *rho, *mu;
-    double *rho_o, *mu_o;    // owned copies for the residual
-    double2 *lamA, *lamB;    // [N][2 pairs] of the inner hierarchies (B: 3D, component z)
-    double *fA[2][3];        // face coefficients of components 0 and 1 (inner T and p slots)
-    double *fB[3];           // component 2 (3D)
+    double r0, h, dt, inv_dt, inv_h2;
+    const double *rho, *mu;  // the caller's (k_mom_diag)
+    double *rho_dt, *wgt;    // owned: rho / dt (mass term) and dt / rho (stopping weight)
+    double *mu_o;            // owned copy of mu
     double *inv_diag[3];     // per component: 1 / the diagonal of the component-diagonal operator
     double *partial;         // per block: the largest Jacobi bound 2 off / diag of its cells and components
+    double2 *lamA, *lamB;    // [N][2 pairs] of the correction hierarchies (B: 3D, component z)
+    double *fA[2][3];        // face coefficients of components 0 and 1 (the hierarchies' T and p slots)
+    double *fB[3];           // component 2 (3D)
 };
 
-// Coefficient of component q on the face of axis a on side sd (0 low, 1 high) of a cell: 2 mu_f on faces normal to
-// q, mu_f on the others; boundary faces mu of the cell at walls (normal component, or every component with
-// no-slip), else 0.  Also the ghost factor: 2 at a wall face (value zero half a cell away), 1 inside.
-__device__ __forceinline__ double mom_face_coef(const MomCoeffArgs &A, int q, int a, int sd, const int pos[3],
-                                                long long c, double mu, double *fac) {
-    const int fpos = pos[a] + sd;
-    double base;
-    if (fpos == 0 || fpos == A.n[a]) {
-        const bool w = A.wall[a][sd] != 0;
-        base = w && (q == a || A.no_slip) ? mu : 0.0;
-        *fac = 2.0;
-    } else {
-        const long long st = a == 0 ? 1LL : a == 1 ? (long long)A.n[0] : (long long)A.n[0] * A.n[1];
-        base = 0.5 * (mu + A.mu[sd ? c + st : c - st]);
-        *fac = 1.0;
-    }
-    return q == a ? 2.0 * base : base;
+__device__ __forceinline__ long long axis_stride(const int n[3], int a) {
+    return a == 0 ? 1LL : a == 1 ? (long long)n[0] : (long long)n[0] * n[1];
 }
 
+// Per cell: the owned copies, the inverse diagonals of the component-diagonal operator and the row bound
+// 2 (off-diagonal sum) / diagonal; per block, the largest bound.  A face's coefficient for component q is 2 mu_f on
+// faces normal to q and mu_f on the others, mu_f the mean of the two cells' mu; on a boundary face mu of the cell at
+// walls (normal component, or every component with no-slip, ghost factor 2) and 0 elsewhere.
 template <int DIM, bool AXI>
-__device__ __forceinline__ double mom_coeffs_cell(const MomCoeffArgs &A, int i, int j, int k);
-
-// Coefficients of the correction hierarchies, the inverse diagonals and, per block, the largest Jacobi bound.
-template <int DIM, bool AXI>
-__global__ void __launch_bounds__(256) k_mom_coeffs(const __grid_constant__ MomCoeffArgs A) {
+__global__ void __launch_bounds__(256) k_mom_diag(const __grid_constant__ MomCoeffArgs A) {
     __shared__ double red[8];
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     const int k = DIM == 3 ? (int)blockIdx.z : 0;
-    double nu = (i < A.n[0] && j < A.n[1]) ? mom_coeffs_cell<DIM, AXI>(A, i, j, k) : 0.0;
+    double nu = 0.0;
+    if (i < A.n[0] && j < A.n[1]) {
+        const long long c = (long long)i + (long long)A.n[0] * ((long long)j + (long long)A.n[1] * k);
+        const double rho = A.rho[c], mu = A.mu[c];
+        const double rdt = rho * A.inv_dt;
+        A.rho_dt[c] = rdt;
+        A.wgt[c] = A.dt / rho;
+        A.mu_o[c] = mu;
+        const int pos[3] = {i, j, k};
+        double ri = 0.0;
+        if (AXI) ri = A.r0 + (i + 0.5) * A.h;
+        double off[DIM];
+#pragma unroll
+        for (int q = 0; q < DIM; q++) off[q] = 0.0;
+#pragma unroll
+        for (int a = 0; a < DIM; a++) {
+#pragma unroll
+            for (int sd = 0; sd < 2; sd++) {
+                const int fpos = pos[a] + sd;
+                const double w = ((AXI && a == 0) ? (ri + (sd ? 0.5 : -0.5) * A.h) / ri : 1.0) * A.inv_h2;
+                if (fpos == 0 || fpos == A.n[a]) {
+                    if (A.wall[a][sd]) {
+#pragma unroll
+                        for (int q = 0; q < DIM; q++)
+                            if (q == a || A.no_slip) off[q] += w * 2.0 * (q == a ? 2.0 * mu : mu);
+                    }
+                } else {
+                    const long long st = axis_stride(A.n, a);
+                    const double mf = 0.5 * (mu + A.mu[sd ? c + st : c - st]);
+#pragma unroll
+                    for (int q = 0; q < DIM; q++) off[q] += w * (q == a ? 2.0 * mf : mf);
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < DIM; q++) {
+            const double diag = rdt + off[q] + ((AXI && q == 0) ? 2.0 * mu / (ri * ri) : 0.0);
+            const double inv = 1.0 / diag;
+            A.inv_diag[q][c] = inv;
+            const double b = 2.0 * off[q] * inv;
+            nu = (b > nu || b != b) ? b : nu;
+        }
+    }
     const int tid = threadIdx.x + blockDim.x * threadIdx.y;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -80,14 +108,19 @@ __global__ void __launch_bounds__(256) k_mom_coeffs(const __grid_constant__ MomC
     }
 }
 
+// Coefficients of the correction hierarchies (multigrid corrections only): lambda_1 = lambda_3 = -rho/dt
+// (- 2 mu / r^2 for u_r), lambda_2 = lambda_4 = 0, and the face coefficients of each cell's low faces (and high
+// faces on the high boundary).  Reads the owned rho/dt and mu written by k_mom_diag.
 template <int DIM, bool AXI>
-__device__ __forceinline__ double mom_coeffs_cell(const MomCoeffArgs &A, int i, int j, int k) {
+__global__ void __launch_bounds__(256) k_mom_hier(const __grid_constant__ MomCoeffArgs A) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = DIM == 3 ? (int)blockIdx.z : 0;
+    if (i >= A.n[0] || j >= A.n[1]) return;
     const int n0 = A.n[0], n1 = A.n[1];
     const long long c = (long long)i + (long long)n0 * ((long long)j + (long long)n1 * k);
-    const double rho = A.rho[c], mu = A.mu[c];
-    A.rho_o[c] = rho;
-    A.mu_o[c] = mu;
-    const double m = -rho * A.inv_dt;
+    const double mu = A.mu_o[c];
+    const double m = -A.rho_dt[c];
     double l0 = m;
     if (AXI) {
         const double ri = A.r0 + (i + 0.5) * A.h;
@@ -95,34 +128,6 @@ __device__ __forceinline__ double mom_coeffs_cell(const MomCoeffArgs &A, int i, 
     }
     A.lamA[2 * c] = make_double2(l0, 0.0);
     A.lamA[2 * c + 1] = make_double2(m, 0.0);
-    double bound;
-    {
-        // diagonal of the component-diagonal operator and the Jacobi bound: the off-diagonal entries of a row
-        // (its face coefficients, and at most as much again from the cross terms) against its diagonal
-        const int pos[3] = {i, j, k};
-        double ri = 0.0;
-        if (AXI) ri = A.r0 + (i + 0.5) * A.h;
-        double nu = 0.0;
-#pragma unroll
-        for (int q = 0; q < DIM; q++) {
-            double off = 0.0;
-#pragma unroll
-            for (int a = 0; a < DIM; a++) {
-#pragma unroll
-                for (int sd = 0; sd < 2; sd++) {
-                    double fac;
-                    const double cf = mom_face_coef(A, q, a, sd, pos, c, mu, &fac);
-                    const double w = (AXI && a == 0) ? (ri + (sd ? 0.5 : -0.5) * A.h) / ri : 1.0;
-                    off += w * cf * fac * A.inv_h2;
-                }
-            }
-            const double diag = rho * A.inv_dt + off + ((AXI && q == 0) ? 2.0 * mu / (ri * ri) : 0.0);
-            A.inv_diag[q][c] = 1.0 / diag;
-            const double b = 2.0 * off / diag;
-            nu = (b > nu || b != b) ? b : nu;
-        }
-        bound = nu;
-    }
     if (DIM == 3) {
         A.lamB[2 * c] = make_double2(m, 0.0);
         A.lamB[2 * c + 1] = make_double2(m, 0.0);           // unused slot: p = 0 for a zero right-hand side
@@ -142,8 +147,7 @@ __device__ __forceinline__ double mom_coeffs_cell(const MomCoeffArgs &A, int i, 
 #pragma unroll
                 for (int q = 0; q < DIM; q++) base[q] = w && (q == a || A.no_slip) ? mu : 0.0;
             } else {
-                const long long cn = c - (a == 0 ? 1LL : a == 1 ? (long long)n0 : (long long)n0 * n1);
-                const double mf = 0.5 * (mu + A.mu[cn]);
+                const double mf = 0.5 * (mu + A.mu_o[c - axis_stride(A.n, a)]);
 #pragma unroll
                 for (int q = 0; q < DIM; q++) base[q] = mf;
             }
@@ -154,7 +158,6 @@ __device__ __forceinline__ double mom_coeffs_cell(const MomCoeffArgs &A, int i, 
             if (DIM == 3) A.fB[a][f] = a == 2 ? 2.0 * base[2] : base[2];
         }
     }
-    return bound;
 }
 
 struct MomArgs {
@@ -162,7 +165,7 @@ struct MomArgs {
     int wall[3][2];
     int no_slip;
     double r0, h, inv_h, half_inv_h, two_inv_h, inv_dt, dt;
-    const double *rho, *mu;
+    const double *rho_dt, *wgt, *mu;   // rho / dt, dt / rho, mu per cell
     const double *u[3];
     const double *R[3];       // residual mode: the right-hand side
     double2 *rA, *rB;         // residual mode: -r as the inner right-hand sides (B: 3D, (-r_z, 0))
@@ -270,7 +273,7 @@ __global__ void __launch_bounds__(TX * TY) k_mom_residual(const __grid_constant_
     double s = 0.0;
     if (i < A.n[0] && j < A.n[1]) {
         const long long c = cell_of(A.n, i, j, k);
-        const double rho = A.rho[c];
+        const double rdt = A.rho_dt[c];
         const int ilo[3] = {lj * (TX + 1) + li, NX + lj * TX + li, NX + NY + lj * TX + li};
         const int ihi[3] = {lj * (TX + 1) + li + 1, NX + (lj + 1) * TX + li, NX + NY + TX * TY + lj * TX + li};
         double ri = 0.0, wl = 0.0, wh = 0.0, inv_rh = 0.0;
@@ -291,7 +294,7 @@ __global__ void __launch_bounds__(TX * TY) k_mom_residual(const __grid_constant_
                 div = a == 0 ? t : div + t;
             }
             const double uq = A.u[q][c];
-            double v = rho * A.inv_dt * uq - div;
+            double v = rdt * uq - div;
             if (AXI && q == 0) v += 2.0 * A.mu[c] * uq / (ri * ri);
             Au[q] = v;
         }
@@ -300,7 +303,7 @@ __global__ void __launch_bounds__(TX * TY) k_mom_residual(const __grid_constant_
             for (int q = 0; q < DIM; q++) A.y[q][c] = Au[q];
         } else {
             double r[DIM];
-            const double w = A.dt / rho;
+            const double w = A.wgt[c];
 #pragma unroll
             for (int q = 0; q < DIM; q++) {
                 r[q] = A.R[q][c] - Au[q];
