@@ -303,7 +303,7 @@ def make_phase(ph) -> MgPhase:
 
 
 MG_ASSEMBLE_LAMBDA4_PRINTED, MG_ASSEMBLE_HARMONIC_K = 1, 2
-MG_MOMENTUM_NO_SLIP, MG_MOMENTUM_MULTIGRID = 1, 2
+MG_MOMENTUM_NO_SLIP, MG_MOMENTUM_MULTIGRID, MG_MOMENTUM_KRYLOV = 1, 2, 4
 
 
 def assemble(grid, phases, dt: float, C_, m1, m2, E, mom: Sequence, uf: Sequence, out: dict,
@@ -577,7 +577,8 @@ class Momentum:
     Arrays are contiguous float64 CUDA tensors of the grid's cells, one per velocity component."""
 
     def __init__(self, grid, no_slip: bool = False, inner_cycles_per_step: int = 1, nu1=2, nu2=2,
-                 coarse_min=4, device: Optional[int] = None, stream=None, multigrid_only: bool = False):
+                 coarse_min=4, device: Optional[int] = None, stream=None, multigrid_only: bool = False,
+                 krylov: bool = False):
         import torch
         lib = load()
         self._lib = lib
@@ -590,7 +591,8 @@ class Momentum:
             stream = torch.cuda.current_stream(dev)
         self.stream = stream
         handle = C.c_void_p()
-        flags = (MG_MOMENTUM_NO_SLIP if no_slip else 0) | (MG_MOMENTUM_MULTIGRID if multigrid_only else 0)
+        flags = ((MG_MOMENTUM_NO_SLIP if no_slip else 0) | (MG_MOMENTUM_MULTIGRID if multigrid_only else 0) |
+                 (MG_MOMENTUM_KRYLOV if krylov else 0))
         check(lib.mg_momentum_create(C.byref(self.grid), flags, C.byref(opt),
                                      C.c_void_p(stream.cuda_stream), C.byref(handle)))
         self._h = handle

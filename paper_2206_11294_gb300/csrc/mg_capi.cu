@@ -1900,6 +1900,8 @@ struct mg_momentum {
     double *inv_diag[3];               // 1 / diagonal of the component-diagonal operator, per component
     double nu;                         // Jacobi bound of the last set-up: max over rows of 2 off / diag
     bool jacobi;                       // corrections by point-Jacobi (no hierarchy set up)
+    double *V, *Z;                     // Krylov basis (kKryM + 1 vectors of dim N) and one work vector
+    double *kpart, *kdot_d, *kdot_h;   // dot partials, dots (device), dots (pinned host)
     double2 *lamA, *lamB, *rA, *rB;
     double *fA[2][3], *fB[3], *fzero[3];
     double *partial, *norm_d, *norm_h;
@@ -1984,6 +1986,130 @@ mg_status momentum_residual(mg_momentum *m, const double *const R[3], const doub
     return MG_OK;
 }
 
+// ---- restarted GMRES on A delta = r0, right-preconditioned by the correction solve
+// nd weighted dots <V_d, w> (d < nd, V_d at V + d * stride) read back to out; one host wait.
+mg_status kry_dots(mg_momentum *m, const double *V, int nd, const double *w, double *out) {
+    const long long N = m->N, stride = (long long)m->grid.dim * N;
+    k_kry_dots<<<kKryBlocks, 256, 0, m->stream>>>(N, m->grid.dim, m->wgt, V, stride, nd, w, m->kpart);
+    k_kry_reduce<<<1, 32 * nd, 0, m->stream>>>(m->kpart, kKryBlocks, nd, m->kdot_d);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(m->kdot_h, m->kdot_d, nd * sizeof(double), cudaMemcpyDeviceToHost, m->stream));
+    CK(cudaStreamSynchronize(m->stream));
+    for (int d = 0; d < nd; d++) out[d] = m->kdot_h[d];
+    return MG_OK;
+}
+
+int lin_grid(long long M) { return (int)std::min<long long>((M + 255) / 256, 152LL * 16); }
+
+// z = M^-1 v (the fixed multigrid correction, a linear map), or z += M^-1 v with add.
+mg_status kry_precond(mg_momentum *m, const double *v, double *const z[3], bool add) {
+    const long long N = m->N;
+    const int dim = m->grid.dim;
+    mg_status st;
+    if (dim == 3) {
+        k_kry_pack<3><<<lin_grid(N), 256, 0, m->stream>>>(N, v, m->rA, m->rB);
+        CK(cudaGetLastError());
+        if ((st = correction_cycles<3>(m->hA, m->rA)) || (st = correction_cycles<3>(m->hB, m->rB))) return st;
+        if (add) k_kry_unpack<3, true><<<lin_grid(N), 256, 0, m->stream>>>(N, m->hA->L[0].x, m->hB->L[0].x, z[0], z[1], z[2]);
+        else k_kry_unpack<3, false><<<lin_grid(N), 256, 0, m->stream>>>(N, m->hA->L[0].x, m->hB->L[0].x, z[0], z[1], z[2]);
+    } else {
+        k_kry_pack<2><<<lin_grid(N), 256, 0, m->stream>>>(N, v, m->rA, nullptr);
+        CK(cudaGetLastError());
+        if ((st = correction_cycles<2>(m->hA, m->rA))) return st;
+        if (add) k_kry_unpack<2, true><<<lin_grid(N), 256, 0, m->stream>>>(N, m->hA->L[0].x, nullptr, z[0], z[1], nullptr);
+        else k_kry_unpack<2, false><<<lin_grid(N), 256, 0, m->stream>>>(N, m->hA->L[0].x, nullptr, z[0], z[1], nullptr);
+    }
+    CK(cudaGetLastError());
+    return MG_OK;
+}
+
+// GMRES(kKryM) from delta (in m->delta) on A delta = r0 (in m->r0); r: the norm of r0 - A delta on entry and exit.
+mg_status momentum_gmres(mg_momentum *m, double target, int max_iters, int *iters, int *precs, double *r) {
+    const int dim = m->grid.dim;
+    const long long N = m->N, M = (long long)dim * N;
+    const double *r0c[3] = {m->r0[0], m->r0[1], m->r0[2]};
+    const double *dc[3] = {m->delta[0], m->delta[1], m->delta[2]};
+    auto vec = [&](int d) { return m->V + d * M; };
+    auto comps = [&](double *v, double *out[3]) {
+        for (int q = 0; q < 3; q++) out[q] = q < dim ? v + q * N : nullptr;
+    };
+    mg_status st;
+    for (;;) {
+        double *v0[3];
+        comps(vec(0), v0);
+        if ((st = momentum_residual(m, r0c, dc, v0, r))) return st;
+        if (!std::isfinite(*r)) return fail(MG_ERR_INVALID_COEFF, "non-finite momentum residual");
+        if (*r <= target || *iters >= max_iters) return MG_OK;
+        KryCoef none;
+        std::memset(&none, 0, sizeof(none));
+        k_kry_orth<<<lin_grid(M), 256, 0, m->stream>>>(M, nullptr, 0, 0, none, 1.0 / *r, vec(0));
+        CK(cudaGetLastError());
+        double H[kKryM + 1][kKryM], g[kKryM + 1], cs[kKryM], sn[kKryM];
+        std::memset(H, 0, sizeof(H));
+        std::memset(g, 0, sizeof(g));
+        g[0] = *r;
+        int kk = 0;
+        for (int j = 0; j < kKryM; j++) {
+            double *z[3], *w[3];
+            comps(m->Z, z);
+            comps(vec(j + 1), w);
+            if ((st = kry_precond(m, vec(j), z, false))) return st;
+            *precs += 1;
+            MomArgs A = momentum_args(m);
+            for (int q = 0; q < dim; q++) {
+                A.u[q] = z[q];
+                A.y[q] = w[q];
+            }
+            if ((st = launch_momentum(m, A, true))) return st;
+            KryCoef h, h2;
+            std::memset(&h, 0, sizeof(h));
+            std::memset(&h2, 0, sizeof(h2));
+            if ((st = kry_dots(m, m->V, j + 1, vec(j + 1), h.c))) return st;
+            k_kry_orth<<<lin_grid(M), 256, 0, m->stream>>>(M, m->V, M, j + 1, h, 1.0, vec(j + 1));
+            CK(cudaGetLastError());
+            if ((st = kry_dots(m, m->V, j + 1, vec(j + 1), h2.c))) return st;      // second pass (CGS2)
+            k_kry_orth<<<lin_grid(M), 256, 0, m->stream>>>(M, m->V, M, j + 1, h2, 1.0, vec(j + 1));
+            CK(cudaGetLastError());
+            double nn;
+            if ((st = kry_dots(m, vec(j + 1), 1, vec(j + 1), &nn))) return st;
+            const double hn = std::sqrt(std::max(nn, 0.0));
+            for (int i = 0; i <= j; i++) H[i][j] = h.c[i] + h2.c[i];
+            H[j + 1][j] = hn;
+            for (int i = 0; i < j; i++) {                     // earlier rotations
+                const double a = H[i][j], b = H[i + 1][j];
+                H[i][j] = cs[i] * a + sn[i] * b;
+                H[i + 1][j] = -sn[i] * a + cs[i] * b;
+            }
+            const double a = H[j][j], b = H[j + 1][j], den = std::hypot(a, b);
+            cs[j] = den > 0.0 ? a / den : 1.0;
+            sn[j] = den > 0.0 ? b / den : 0.0;
+            H[j][j] = den;
+            H[j + 1][j] = 0.0;
+            g[j + 1] = -sn[j] * g[j];
+            g[j] = cs[j] * g[j];
+            kk = j + 1;
+            *iters += 1;
+            if (hn > 0.0) {
+                k_kry_orth<<<lin_grid(M), 256, 0, m->stream>>>(M, nullptr, 0, 0, none, 1.0 / hn, vec(j + 1));
+                CK(cudaGetLastError());
+            }
+            if (std::fabs(g[j + 1]) <= target || *iters >= max_iters || !(hn > 0.0)) break;
+        }
+        KryCoef y;
+        std::memset(&y, 0, sizeof(y));
+        for (int i = kk - 1; i >= 0; i--) {                   // H y = g, upper triangular
+            double s = g[i];
+            for (int l = i + 1; l < kk; l++) s -= H[i][l] * y.c[l];
+            y.c[i] = H[i][i] != 0.0 ? s / H[i][i] : 0.0;
+        }
+        k_kry_combine<<<lin_grid(M), 256, 0, m->stream>>>(M, m->V, M, kk, y, m->Z);
+        CK(cudaGetLastError());
+        double *d[3] = {m->delta[0], m->delta[1], m->delta[2]};
+        if ((st = kry_precond(m, m->Z, d, true))) return st;    // delta += M^-1 (V y)
+        *precs += 1;
+    }
+}
+
 bool momentum_ptrs(const mg_momentum *m, const double *const v[3]) {
     if (!v) return false;
     for (int a = 0; a < m->grid.dim; a++)
@@ -2000,6 +2126,7 @@ mg_status mg_momentum_destroy(mg_momentum *m) {
     mg_destroy(m->hB);
     if (m->arena) cudaFree(m->arena);
     if (m->norm_h) cudaFreeHost(m->norm_h);
+    if (m->kdot_h) cudaFreeHost(m->kdot_h);
     delete m;
     return MG_OK;
 }
@@ -2010,7 +2137,8 @@ mg_status mg_momentum_create(const mg_grid *grid, int flags, const mg_options *i
     *out = nullptr;
     mg_status st = check_grid_geom(grid);
     if (st) return st;
-    if (flags & ~(MG_MOMENTUM_NO_SLIP | MG_MOMENTUM_MULTIGRID)) return fail(MG_ERR_INVALID_ARG, "unknown momentum flags");
+    if (flags & ~(MG_MOMENTUM_NO_SLIP | MG_MOMENTUM_MULTIGRID | MG_MOMENTUM_KRYLOV))
+        return fail(MG_ERR_INVALID_ARG, "unknown momentum flags");
     mg_options opt;
     if (inner) {
         opt = *inner;
@@ -2063,8 +2191,12 @@ mg_status mg_momentum_create(const mg_grid *grid, int flags, const mg_options *i
     for (int q = 0; q < (dim == 3 ? 4 : 2); q++)
         for (int a = 0; a < dim; a++) o_f[q][a] = take((size_t)nf[a] * 8);
     const size_t o_part = take((size_t)m->nblocks * 8), o_norm = take(8);
+    const bool kry = (flags & MG_MOMENTUM_KRYLOV) != 0;
+    const size_t o_V = kry ? take((size_t)(kKryM + 1) * dim * N * 8) : 0, o_Z = kry ? take((size_t)dim * N * 8) : 0,
+                 o_kp = kry ? take((size_t)(kKryM + 1) * kKryBlocks * 8) : 0, o_kd = kry ? take((kKryM + 1) * 8) : 0;
     DeviceGuard dg(m->device);
-    if (cudaMalloc(&m->arena, off) != cudaSuccess || cudaMallocHost(&m->norm_h, sizeof(double)) != cudaSuccess) {
+    if (cudaMalloc(&m->arena, off) != cudaSuccess || cudaMallocHost(&m->norm_h, sizeof(double)) != cudaSuccess ||
+        (kry && cudaMallocHost(&m->kdot_h, (kKryM + 1) * sizeof(double)) != cudaSuccess)) {
         cudaGetLastError();
         mg_momentum_destroy(m);
         return fail(MG_ERR_OOM, "device allocation failed");
@@ -2095,6 +2227,12 @@ mg_status mg_momentum_create(const mg_grid *grid, int flags, const mg_options *i
     }
     m->partial = reinterpret_cast<double *>(at(o_part));
     m->norm_d = reinterpret_cast<double *>(at(o_norm));
+    if (kry) {
+        m->V = reinterpret_cast<double *>(at(o_V));
+        m->Z = reinterpret_cast<double *>(at(o_Z));
+        m->kpart = reinterpret_cast<double *>(at(o_kp));
+        m->kdot_d = reinterpret_cast<double *>(at(o_kd));
+    }
     CK(cudaStreamSynchronize(m->stream));
     *out = m;
     return MG_OK;
@@ -2220,7 +2358,14 @@ mg_status mg_momentum_solve(mg_momentum *m, const double *const R[3], double *co
     r = r0;
     int it = 0, cycles = 0;
     mg_status result = MG_OK;
-    for (;;) {
+    if (m->V && !m->jacobi && !(r == 0.0 || (rtol > 0.0 && r <= rtol * r0))) {
+        int precs = 0;
+        const double target = rtol > 0.0 ? rtol * r0 : 0.0;
+        if ((st = momentum_gmres(m, target, max_iters, &it, &precs, &r))) return st;
+        cycles = precs * m->hA->opt.max_cycles * (dim == 3 ? 2 : 1);
+        if (!(r == 0.0 || (rtol > 0.0 && r <= rtol * r0))) result = rtol > 0.0 ? MG_ERR_NOT_CONVERGED : MG_OK;
+    }
+    for (; !m->V || m->jacobi;) {
         if (r == 0.0 || (rtol > 0.0 && r <= rtol * r0)) break;
         if (it >= max_iters) {
             result = rtol > 0.0 ? MG_ERR_NOT_CONVERGED : MG_OK;

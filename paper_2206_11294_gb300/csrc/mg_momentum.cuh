@@ -405,6 +405,107 @@ __global__ void __launch_bounds__(256) k_mom_update(long long N, const double2 *
     }
 }
 
+// ---------------------------------------------------------------- Krylov acceleration (restarted GMRES)
+// Vectors hold all components, component q at offset q N.  The inner product is weighted like the stopping norm:
+// <x, y> = sum over cells and components of (dt / rho)^2 x y.
+constexpr int kKryM = 16;                 // restart length
+constexpr int kKryBlocks = 152 * 4;       // grid of the reduction kernels (grid-stride)
+
+struct KryCoef {
+    double c[kKryM + 1];
+};
+
+// partial[d * gridDim.x + block] = block's share of <V_d, w>, d < nd (V_d at V + d * stride).
+__global__ void __launch_bounds__(256) k_kry_dots(long long N, int dim, const double *wgt, const double *V,
+                                                  long long stride, int nd, const double *w, double *partial) {
+    __shared__ double red[8][kKryM + 1];
+    double s[kKryM + 1];
+#pragma unroll
+    for (int d = 0; d <= kKryM; d++) s[d] = 0.0;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
+        const double g = wgt[c] * wgt[c];
+        for (int q = 0; q < dim; q++) {
+            const double wv = g * w[q * N + c];
+#pragma unroll
+            for (int d = 0; d <= kKryM; d++)
+                if (d < nd) s[d] += wv * V[d * stride + q * N + c];
+        }
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int d = 0; d <= kKryM; d++) {
+        if (d >= nd) break;
+        double v = s[d];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) red[wid][d] = v;
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < nd) {
+        double t = 0.0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); q++) t += red[q][threadIdx.x];
+        partial[(long long)threadIdx.x * gridDim.x + blockIdx.x] = t;
+    }
+}
+
+// out[d] = sum of the nblocks partials of dot d, in a fixed order (one block, one warp per dot).
+__global__ void __launch_bounds__(1024) k_kry_reduce(const double *partial, int nblocks, int nd, double *out) {
+    const int lane = threadIdx.x & 31, d = threadIdx.x >> 5;
+    if (d >= nd) return;
+    double s = 0.0;
+    for (int b = lane; b < nblocks; b += 32) s += partial[(long long)d * nblocks + b];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) out[d] = s;
+}
+
+// w = scale * (w - sum_d h_d V_d), d < nd (scale 1: plain orthogonalisation).
+__global__ void __launch_bounds__(256) k_kry_orth(long long M, const double *V, long long stride, int nd,
+                                                  const __grid_constant__ KryCoef h, double scale, double *w) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < M; e += (long long)gridDim.x * blockDim.x) {
+        double v = w[e];
+        for (int d = 0; d < nd; d++) v -= h.c[d] * V[d * stride + e];
+        w[e] = scale * v;
+    }
+}
+
+// out = sum_d y_d V_d, d < nd.
+__global__ void __launch_bounds__(256) k_kry_combine(long long M, const double *V, long long stride, int nd,
+                                                     const __grid_constant__ KryCoef y, double *out) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < M; e += (long long)gridDim.x * blockDim.x) {
+        double v = 0.0;
+        for (int d = 0; d < nd; d++) v += y.c[d] * V[d * stride + e];
+        out[e] = v;
+    }
+}
+
+// The correction right-hand sides for M^-1 v: -v in the pair layouts (A = (v_0, v_1), B = (v_2, 0)).
+template <int DIM>
+__global__ void __launch_bounds__(256) k_kry_pack(long long N, const double *v, double2 *rA, double2 *rB) {
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
+        rA[c] = make_double2(-v[c], -v[N + c]);
+        if (DIM == 3) rB[c] = make_double2(-v[2 * N + c], 0.0);
+    }
+}
+
+// z = the correction solves' solutions, per component (add: z += instead).
+template <int DIM, bool ADD>
+__global__ void __launch_bounds__(256) k_kry_unpack(long long N, const double2 *xA, const double2 *xB, double *z0,
+                                                    double *z1, double *z2) {
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
+        const double2 a = xA[c];
+        if (ADD) {
+            z0[c] += a.x;
+            z1[c] += a.y;
+            if (DIM == 3) z2[c] += xB[c].x;
+        } else {
+            z0[c] = a.x;
+            z1[c] = a.y;
+            if (DIM == 3) z2[c] = xB[c].x;
+        }
+    }
+}
+
 // ---------------------------------------------------------------- either side of the predictor
 // Cell gradients are the means of a cell's two face gradients along each axis,
 // the face gradients being those of the projection: (s_R - s_L)/h inside; for
