@@ -105,3 +105,29 @@ def test_product_path_has_no_oracle_dependency():
         if path.endswith((".py", ".cu", ".cuh", ".h")):
             src = open(path).read()
             assert "import oracle" not in src and "coupled_oracle" not in src, path
+
+
+def test_momentum_and_side_steps_validate_on_the_host(lib):
+    """Argument checks of the momentum predictor and the steps around the solves, made before any device work."""
+    from paper_2206_11294_gb300 import binding as B
+    g = _grid(n=(64, 64, 1))
+    h = C.c_void_p()
+    assert lib.mg_momentum_create(C.byref(g), 8, None, None, C.byref(h)) == B.MG_ERR_INVALID_ARG
+    assert not h.value
+    o = B.make_options("mixed", 0.0, 1)
+    assert lib.mg_momentum_create(C.byref(g), 0, C.byref(o), None, C.byref(h)) == B.MG_ERR_INVALID_ARG
+    o = B.make_options("fp64", 0.0, 0)
+    assert lib.mg_momentum_create(C.byref(g), 0, C.byref(o), None, C.byref(h)) == B.MG_ERR_INVALID_ARG
+    assert lib.mg_momentum_create(C.byref(g), 0, None, None, None) == B.MG_ERR_INVALID_ARG
+    assert lib.mg_momentum_set_coeffs(None, 1e-3, None, None) == B.MG_ERR_INVALID_ARG
+    pa = (C.c_void_p * 3)()
+    assert lib.mg_momentum_solve(None, pa, pa, 1e-10, 10, None) == B.MG_ERR_INVALID_ARG
+    assert lib.mg_momentum_apply(None, pa, pa) == B.MG_ERR_INVALID_ARG
+    assert lib.mg_momentum_destroy(None) == B.MG_OK
+    for dt in (0.0, -1.0, float("nan")):
+        assert lib.mg_momentum_rhs_async(C.byref(g), dt, 0.07, pa, None, None, None, pa, None) == B.MG_ERR_INVALID_ARG
+        assert lib.mg_provisional_async(C.byref(g), dt, None, None, pa, pa, None) == B.MG_ERR_INVALID_ARG
+        ph = (B.MgPhase * 2)()
+        assert lib.mg_energy_async(C.byref(g), ph, dt, None, None, None, None, pa, None, None, None, None,
+                                   None) == B.MG_ERR_INVALID_ARG
+    assert "dt" in B.last_error()
