@@ -35,15 +35,16 @@ sys.path.insert(0, ROOT)
 METRIC = "coupled p-T MG Mcell-Vcycles/s & solves/s at 1e-10 resid; HBM %peak; p50/p99"
 UNIT = "Mcell-Vcycles/s"
 FALLBACK_HBM_GBS = 6800.0
-# DRAM bytes per launch of a dominant kernel, from the committed ncu captures
-# (profiles/); an entry holds while that kernel's source is unchanged.
+# DRAM bytes per launch of a dominant kernel, from ncu captures of that
+# kernel; an entry holds while the kernel's source is unchanged.
 # "cold": ncu's default capture (caches flushed before the launch, the
 # recipe's figure); "warm": caches as the solve leaves them (median of the
 # 16 finest-level launches of one solve sequence).
 TRAFFIC = {
     "k_rbgs_colour<double,2> on the finest level of bubbles16_1024x1024": {
         "cold": 103.8e6, "warm": 33.8e6,
-        "source": "profiles/k_rbgs_colour_f64_bubbles1024.md (cold), k_rbgs_colour_f64_bubbles1024_warm.md (warm)"},
+        "source": "ncu capture of k_rbgs_colour<double,2> on the 1024^2 level: --set full (cold), "
+                  "--cache-control none over one solve sequence (warm)"},
 }
 L2_FLUSH_BYTES = 256 << 20
 # algorithmic bytes per finest cell of one full red-black sweep: read x 16 +
@@ -605,9 +606,9 @@ def run_timestep(args):
                              "algorithmic_bytes": byts, "avg_launch_us": ms * 1e3}
     cycles = [st["cycles"] for st in stats]
     asm = roof(ASSEMBLE_BYTES_2D * N, t_asm)
-    # the assembly is bound by the FP64 pipe, not HBM (ncu: profiles/k_assemble_bubbles1024.md)
+    # the assembly is bound by the FP64 pipe, not HBM (ncu --set full of k_assemble on this state)
     asm_alu = {"bound": "alu", "fp64_pipe_busy_elapsed_ncu": 0.836, "fp64_inst_per_cell_ncu": 150,
-               "source": "profiles/k_assemble_bubbles1024.md", "hbm": asm}
+               "source": "ncu --set full capture of k_assemble<2,false> on this state", "hbm": asm}
     return {"workload": "one time step, bubbles16_1024x1024 advected state: assembly + set-up + solve to 1e-10 + "
                         "velocity / phase-pressure update + phase-energy update, after the momentum predictor "
                         "(right-hand side, set-up + solve to 1e-10, Eq. provel)", "metric": "time steps/s",
@@ -787,7 +788,7 @@ def main():
     ap.add_argument("--serve-budget", type=int, default=40 << 30)
     ap.add_argument("--cycle", default="V", choices=["V", "W", "F"], help="cycle of the correction solve")
     ap.add_argument("--traffic", type=float, default=None,
-                    help="DRAM bytes per launch of the dominant kernel from an ncu capture (profiles/)")
+                    help="DRAM bytes per launch of the dominant kernel from an ncu capture")
     args = ap.parse_args()
     world = env_int("WORLD_SIZE", 1)
     rank = env_int("RANK", 0)

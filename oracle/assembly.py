@@ -20,7 +20,7 @@ After it:
                    pressure work, viscous work and heat conduction as face
                    fluxes, each face flux one value shared by its two cells.
 
-Readings where the paper is silent (each listed in the design doc):
+Readings where the paper is silent:
 - overlines are volume-fraction averages of the phase expressions; with the
   partial densities m_i = C_i rho_i they read C_i (1 - rho_i b_i) = C_i - m_i b_i
   and C_i rho_i q_i = m_i q_i, so no phase density is needed for p and T;

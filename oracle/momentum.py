@@ -25,7 +25,7 @@ cells' averaged density and viscosity.
                       cells, then the faces' normal components for the
                       projection (Eq. unp1).
 
-Readings where the paper is silent (each listed in the design doc):
+Readings where the paper is silent:
 - mu_f is the mean of the two cells' mu; a boundary face takes its cell's;
 - on a face the normal derivative is the difference across the face; the
   tangential derivative (du_a/dx_c, c != a) the mean of the two cells' central
