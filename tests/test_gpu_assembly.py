@@ -405,3 +405,16 @@ def test_energy_invalid_arguments_rejected(torch_cuda, orc):
         assert e.value.status == MG_ERR_INVALID_ARG
     torch.cuda.synchronize()
     assert float(o1.abs().sum()) == 0.0 and float(o2.abs().sum()) == 0.0
+
+
+def test_energy_of_an_absent_phase_is_unchanged(torch_cuda, orc):
+    """Cells of one phase only (C exactly 0 or 1 in halves): the absent phase's energy comes back bit for bit."""
+    g = GRIDS["2d_walls"]
+    s, x, rc, E1, E2 = _energy_case(torch_cuda, orc, g, 34)
+    C = np.zeros_like(s.C)
+    C[:, :, : g.n[0] // 2] = 1.0
+    s.C = C
+    got1, got2 = _gpu_energy(torch_cuda, g, s, x, rc, E1, E2)
+    np.testing.assert_array_equal(got1[C == 0.0], E1[C == 0.0])
+    np.testing.assert_array_equal(got2[C == 1.0], E2[C == 1.0])
+    assert np.any(got1[C == 1.0] != E1[C == 1.0]) and np.any(got2[C == 0.0] != E2[C == 0.0])

@@ -313,3 +313,42 @@ def test_predictor_chain_matches_oracle(torch_cuda, orc):
         err = np.linalg.norm(got - ref_f[a]) / np.linalg.norm(ref_f[a])
         assert err <= 1e-9, (a, err, st)
     m.close()
+
+
+@pytest.mark.parametrize("name", ["2d", "axi", "3d"])
+def test_inviscid_predictor_is_one_jacobi_step(torch_cuda, name):
+    """mu = 0 (the paper's inviscid water): A = (rho/dt) I, the Jacobi bound is 0 and one step gives u = dt R / rho."""
+    from paper_2206_11294_gb300.binding import Momentum
+    torch = torch_cuda
+    g = GRIDS[name]
+    rho, _, dt, _ = _fields(g, 101)
+    rng = np.random.default_rng(102)
+    R = [rng.normal(0.0, 1e6, rho.shape) for _ in range(g.dim)]
+    m = Momentum(g)
+    m.set_coeffs(dt, _dev(torch, rho), _dev(torch, np.zeros_like(rho)))
+    ud = [torch.zeros(rho.shape, dtype=torch.float64, device="cuda") for _ in range(g.dim)]
+    st = m.solve([_dev(torch, r) for r in R], ud, rtol=1e-12, max_iters=10)
+    assert st["jacobi"] and st["nu"] == 0.0 and st["iterations"] == 1 and st["rfinal"] <= 1e-15 * st["r0"], st
+    for c in range(g.dim):
+        np.testing.assert_allclose(ud[c].cpu().numpy(), dt * R[c] / rho, rtol=1e-15, atol=0)
+    m.close()
+
+
+def test_uniform_provisional_velocity(torch_cuda, orc):
+    """Uniform u_pred and a uniform pressure equal to the boundary values: interior faces carry u exactly, walls 0."""
+    from paper_2206_11294_gb300 import binding as B
+    import dataclasses
+    torch = torch_cuda
+    g = dataclasses.replace(GRIDS["2d"], bcp=((1e5, 1e5), (1e5, 1e5), (0.0, 0.0)))
+    shape = (1, g.n[1], g.n[0])
+    u = [np.full(shape, 0.3), np.full(shape, -0.7)]
+    uf = [torch.empty(g.face_shape(a), dtype=torch.float64, device="cuda") for a in range(2)]
+    B.provisional(g, 1e-3, _dev(torch, np.full(shape, 2.0)), _dev(torch, np.full(shape, 1e5)), [_dev(torch, v) for v in u], uf)
+    torch.cuda.synchronize()
+    for a in range(2):
+        got = uf[a].cpu().numpy()
+        ref = orc.provisional_faces(g, 1e-3, np.full(shape, 2.0), np.full(shape, 1e5), u)[a]
+        np.testing.assert_array_equal(got, ref)
+        inner = [slice(None)] * 3
+        inner[2 - a] = slice(1, -1)
+        np.testing.assert_array_equal(got[tuple(inner)], u[a][0, 0, 0])
