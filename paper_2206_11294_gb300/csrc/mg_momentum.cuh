@@ -7,7 +7,11 @@
 // normal to component c and mu on the others - on the pair multigrid of the
 // pressure-temperature solve (two components per hierarchy, coupling
 // coefficients lambda_2 = lambda_4 = 0).  The cross terms div(mu grad u^T)
-// off the diagonal are the difference the outer loop removes.
+// off the diagonal are the difference the outer loop removes.  When the
+// set-up's row bound 2 (off-diagonal sum) / diagonal is small (the mass term
+// dominates), the corrections are point-Jacobi steps instead (k_mom_jacobi);
+// optionally the loop is restarted GMRES right-preconditioned by the
+// multigrid correction (the k_kry_* kernels).
 //
 // Boundary faces: walls hold the normal component at zero (a Dirichlet face
 // of the inner grid with coefficient 2 mu) and let the tangential ones slip
