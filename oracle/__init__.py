@@ -16,6 +16,8 @@ defect-correction loop after them; see the C file for the exact statements):
 - ``residual_norms``  the per-field stopping norm ||D^-1 r||_2
 - ``level_coeffs``    coarse-level blocks and faces of the hierarchy
 - ``apply_rows``      L(x) at selected cells (residual checks of large solutions)
+- ``restrict``        a fine residual restricted to the coarse right-hand side
+- ``prolong_add``     a coarse correction interpolated and added to fine unknowns
 """
 from __future__ import annotations
 
@@ -82,6 +84,10 @@ def configure(lib):
     lib.orc_level_coeffs.restype = C.c_int
     lib.orc_apply_rows.argtypes = [gp, dp, pa3, pa3, dp, C.POINTER(C.c_long), C.c_long, dp]
     lib.orc_apply_rows.restype = None
+    lib.orc_restrict.argtypes = [gp, dp, dp]
+    lib.orc_restrict.restype = C.c_int
+    lib.orc_prolong_add.argtypes = [gp, dp, dp]
+    lib.orc_prolong_add.restype = C.c_int
     return lib
 
 
@@ -253,4 +259,38 @@ def apply_rows(g, lam, fa, fk, x, ids) -> np.ndarray:
     out = np.empty((ids.size, 2))
     lib.orc_apply_rows(C.byref(gs), _dp(lam), pa, pk, _dp(x), ids.ctypes.data_as(C.POINTER(C.c_long)),
                        int(ids.size), _dp(out))
+    return out
+
+
+def _coarse_cells(g) -> int:
+    gs = _grid(g)
+    n = [gs.n[0], gs.n[1], gs.n[2]]
+    for a in range(gs.dim):
+        if n[a] % 2:
+            raise ValueError("every n_a must be even to coarsen")
+        n[a] //= 2
+    return n[0] * n[1] * n[2]
+
+
+def restrict(g, r) -> np.ndarray:
+    """The coarse right-hand side [N_c, 2] that a V-cycle forms from the fine residual r [N, 2] on grid g."""
+    lib = _load()
+    gs = _grid(g)
+    r = _c64(r)
+    out = np.empty((_coarse_cells(g), 2))
+    if lib.orc_restrict(C.byref(gs), _dp(r), _dp(out)):
+        raise RuntimeError("oracle restriction failed")
+    return out
+
+
+def prolong_add(g, uc, uf) -> np.ndarray:
+    """uf + P uc: the coarse correction uc [N_c, 2] interpolated onto grid g and added to uf [N, 2]."""
+    lib = _load()
+    gs = _grid(g)
+    uc = _c64(uc)
+    if uc.shape[0] != _coarse_cells(g):
+        raise ValueError("uc has the wrong number of cells")
+    out = _c64(uf).copy()
+    if lib.orc_prolong_add(C.byref(gs), _dp(uc), _dp(out)):
+        raise RuntimeError("oracle prolongation failed")
     return out

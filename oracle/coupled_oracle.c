@@ -743,3 +743,54 @@ void orc_apply_rows(const orc_grid *g, const double *lam, double *const fa[3], d
         out[2 * q + 1] = lapp + l[2] * p + l[3] * lapT;         /* Eq. 28 */
     }
 }
+
+/* ------------------------------------------------------------------ */
+/* The grid transfers alone (pinned separately by the CPU tests)       */
+/* ------------------------------------------------------------------ */
+
+/* The grid of the next coarser level: every n_a halved, spacing 2h, the
+ * same boundary kinds and r0, homogeneous boundary values. */
+static orc_grid coarse_grid_of(const orc_grid *g)
+{
+    orc_grid c = *g;
+    for (int a = 0; a < c.dim; a++) c.n[a] /= 2;
+    c.h = 2.0 * g->h;
+    memset(c.bcT, 0, sizeof(c.bcT));
+    memset(c.bcp, 0, sizeof(c.bcp));
+    return c;
+}
+
+/* Restriction of a fine residual r (N x 2 on grid g, every n_a even) to the
+ * coarse right-hand side bc (N/2^dim x 2), as a V-cycle forms it. */
+int orc_restrict(const orc_grid *g, const double *r, double *bc)
+{
+    level F, C;
+    orc_grid cg = coarse_grid_of(g);
+    int rc = alloc_level(&F, g) || alloc_level(&C, &cg) ? -2 : 0;
+    if (rc == 0) {
+        memcpy(F.r, r, sizeof(double) * 2 * F.N);
+        restrict_residual(&F, &C);
+        memcpy(bc, C.rhs, sizeof(double) * 2 * C.N);
+    }
+    free_level(&F);
+    free_level(&C);
+    return rc;
+}
+
+/* Prolongation of a coarse correction uc (on the coarse grid of g) added to
+ * the fine unknowns uf (N x 2 on grid g), as a V-cycle applies it. */
+int orc_prolong_add(const orc_grid *g, const double *uc, double *uf)
+{
+    level F, C;
+    orc_grid cg = coarse_grid_of(g);
+    int rc = alloc_level(&F, g) || alloc_level(&C, &cg) ? -2 : 0;
+    if (rc == 0) {
+        memcpy(C.u, uc, sizeof(double) * 2 * C.N);
+        memcpy(F.u, uf, sizeof(double) * 2 * F.N);
+        prolong_add(&C, &F);
+        memcpy(uf, F.u, sizeof(double) * 2 * F.N);
+    }
+    free_level(&F);
+    free_level(&C);
+    return rc;
+}

@@ -145,3 +145,48 @@ def test_cycle_mutant_fails_the_pin(orc, name):
             assert not _cycle_pins_pass(orc), name
     finally:
         del MUTATIONS[name]
+
+
+# Planted mistakes in the grid transfers, against the transfer pins of
+# test_oracle_pins.py (each only slows the multigrid down: no converged-solution
+# pin sees it).
+TRANSFER_MUTATIONS = {
+    # restriction as a plain mean of the children, ignoring their volumes (r_i h^2 on axisymmetric grids)
+    "restrict_plain_mean": ("            s0 += V * F->r[2 * f];\n            s1 += V * F->r[2 * f + 1];\n"
+                            "            vsum += V;",
+                            "            s0 += 1.0 * F->r[2 * f];\n            s1 += 1.0 * F->r[2 * f + 1];\n"
+                            "            vsum += 1.0;"),
+    # the Dirichlet ghost of the prolongation taken even (same value) instead of odd
+    "prolong_no_dirichlet_sign": ("if (C->g.bc[a][side] == BC_DIRICHLET) sign = -sign;", "if (0) sign = -sign;"),
+    # every ghost taken odd, the walls' and the axis's too
+    "prolong_odd_wall_ghost": ("if (C->g.bc[a][side] == BC_DIRICHLET) sign = -sign;", "sign = -sign;"),
+    # prolongation stencil leaning the wrong way (toward the far coarse neighbour)
+    "prolong_wrong_side": ("int s[3] = {(c[0] & 1) ? 1 : -1, (c[1] & 1) ? 1 : -1, (c[2] & 1) ? 1 : -1};",
+                           "int s[3] = {(c[0] & 1) ? -1 : 1, (c[1] & 1) ? -1 : 1, (c[2] & 1) ? -1 : 1};"),
+}
+
+
+def _transfer_pins_pass(orc) -> bool:
+    import test_oracle_pins as P
+    try:
+        for name in P.TRANSFER_GRIDS:
+            P.test_restriction_conserves_the_volume_integral(orc, name)
+            P.test_prolongation_reproduces_multilinear_fields(orc, name)
+        P.test_prolongation_boundary_ghosts(orc)
+    except AssertionError:
+        return False
+    return True
+
+
+def test_unmutated_oracle_passes_the_transfer_pins(orc):
+    assert _transfer_pins_pass(orc)
+
+
+@pytest.mark.parametrize("name", list(TRANSFER_MUTATIONS))
+def test_transfer_mutant_fails_a_pin(orc, name):
+    MUTATIONS[name] = TRANSFER_MUTATIONS[name]
+    try:
+        with mutant(orc, name):
+            assert not _transfer_pins_pass(orc), name
+    finally:
+        del MUTATIONS[name]

@@ -492,3 +492,151 @@ def test_w_f_contract_faster_than_v(orc):
         rate[c] = np.exp(np.log(hist[1:6] / hist[0:5]).mean(axis=0))
     for c in "WF":
         assert np.all(rate[c] <= 0.8 * rate["V"]), (c, rate)
+
+
+# ---------------------------------------------------------------- grid transfers
+# Restriction and prolongation are pinned on their own: a slip in either only
+# slows the multigrid down, so no converged-solution pin can see it.
+TRANSFER_GRIDS = {
+    "2d_mixed": I.Grid(dim=2, axisym=0, n=(8, 12, 1), h=0.1, bc=((W, D), (D, W), (0, 0))),
+    "axi_axis": I.Grid(dim=2, axisym=1, n=(8, 12, 1), h=0.1, bc=((A, D), (W, D), (0, 0))),
+    "axi_annulus": I.Grid(dim=2, axisym=1, n=(6, 8, 1), h=0.1, r0=0.3, bc=((D, W), (W, D), (0, 0))),
+    "3d_mixed": I.Grid(dim=3, axisym=0, n=(4, 6, 8), h=0.2, bc=((D, D), (W, D), (D, W))),
+}
+
+
+def _cell_volumes(g):
+    """V_i of every cell (x-fastest): h^dim, or r_i h^2 with r_i = r0 + (i + 1/2) h on axisymmetric grids."""
+    i = np.arange(g.N) % g.n[0]
+    if g.axisym:
+        return (g.r0 + (i + 0.5) * g.h) * g.h * g.h
+    return np.full(g.N, g.h ** g.dim)
+
+
+def _coarse(g):
+    return I.Grid(dim=g.dim, axisym=g.axisym, n=tuple(g.n[a] // 2 if a < g.dim else 1 for a in range(3)),
+                  h=2 * g.h, r0=g.r0, bc=g.bc)
+
+
+def _children(g, I_):
+    """Fine cell ids of the 2^dim children of coarse cell I_ (coarse grid of g)."""
+    nc = [g.n[a] // 2 if a < g.dim else 1 for a in range(3)]
+    ci, cj, ck = I_ % nc[0], (I_ // nc[0]) % nc[1], I_ // (nc[0] * nc[1])
+    out = []
+    for q in range(1 << g.dim):
+        i, j = 2 * ci + (q & 1), 2 * cj + ((q >> 1) & 1)
+        k = 2 * ck + ((q >> 2) & 1) if g.dim == 3 else 0
+        out.append(i + g.n[0] * (j + g.n[1] * k))
+    return out
+
+
+@pytest.mark.parametrize("name", list(TRANSFER_GRIDS))
+def test_restriction_conserves_the_volume_integral(orc, name):
+    """V_I R_I = sum over the children of V_i r_i for every coarse cell: the
+    coarse right-hand side carries the same integral of the residual as its
+    children (the coarse row is the fine rows' finite-volume sum).  On
+    axisymmetric grids the children's volumes differ (r_i h^2), so a plain
+    mean fails this; the volume-weighted mean (Sec. 3 gives volume averages
+    C phi_1 + (1 - C) phi_2 of cell quantities) satisfies it."""
+    g = TRANSFER_GRIDS[name]
+    rng = np.random.default_rng(11)
+    r = rng.standard_normal((g.N, 2))
+    R = orc.restrict(g.as_dict(), r)
+    gc = _coarse(g)
+    V, Vc = _cell_volumes(g), _cell_volumes(gc)
+    for I_ in range(gc.N):
+        ch = _children(g, I_)
+        integral = (V[ch, None] * r[ch]).sum(axis=0)
+        assert np.allclose(Vc[I_] * R[I_], integral, rtol=1e-13, atol=1e-15 * np.abs(V[ch, None] * r[ch]).sum())
+    # a constant residual restricts to the same constant
+    assert np.allclose(orc.restrict(g.as_dict(), np.ones((g.N, 2))), 1.0, rtol=1e-15)
+
+
+def _centres_1d(g, a, coarse=False):
+    n = g.n[a] // 2 if coarse else g.n[a]
+    h = 2 * g.h if coarse else g.h
+    lo = g.r0 if (g.axisym and a == 0) else 0.0
+    return lo + (np.arange(n) + 0.5) * h
+
+
+def _field(g, coarse, fn):
+    """fn(X, Y, Z) evaluated at the cell centres of g (or of its coarse grid), x-fastest."""
+    ax = [_centres_1d(g, a, coarse) if a < g.dim else np.zeros(1) for a in range(3)]
+    Z, Y, X = np.meshgrid(ax[2], ax[1], ax[0], indexing="ij")
+    return fn(X, Y, Z).reshape(-1)
+
+
+@pytest.mark.parametrize("name", list(TRANSFER_GRIDS))
+def test_prolongation_reproduces_multilinear_fields(orc, name):
+    """Cell-centred bi/tri-linear interpolation (weights 3/4 and 1/4 per axis)
+    reproduces any field in span{1, x} x span{1, y} (x span{1, z}) exactly at
+    every fine cell whose interpolation stencil stays inside the grid (all but
+    the first and last fine cell along each axis)."""
+    g = TRANSFER_GRIDS[name]
+    fns = [lambda X, Y, Z: 1.5 + 2.0 * X - 3.0 * Y + 0.5 * Z + 4.0 * X * Y - Y * Z + 2.0 * X * Y * Z,
+           lambda X, Y, Z: -0.7 + X * Y + 3.0 * Z]
+    uc = np.stack([_field(g, True, f) for f in fns], axis=1)
+    exact = np.stack([_field(g, False, f) for f in fns], axis=1)
+    base = np.random.default_rng(5).standard_normal((g.N, 2))
+    got = orc.prolong_add(g.as_dict(), uc, base) - base
+    idx = np.arange(g.N)
+    c = [idx % g.n[0], (idx // g.n[0]) % g.n[1], idx // (g.n[0] * g.n[1])]
+    inner = np.ones(g.N, bool)
+    for a in range(g.dim):
+        inner &= (c[a] > 0) & (c[a] < g.n[a] - 1)
+    assert inner.sum() > 0
+    assert np.allclose(got[inner], exact[inner], rtol=0, atol=1e-13 * np.abs(exact).max())
+
+
+def test_prolongation_boundary_ghosts(orc):
+    """At the boundary the interpolation reads a ghost of the coarse cell:
+    odd at a Dirichlet face (the correction vanishes on the face, whose value
+    is fixed), even at a wall or the axis (zero normal gradient).  A field
+    that is linear in the normal coordinate and zero on a Dirichlet face is
+    odd about it, so it is reproduced exactly in the cells next to that face;
+    a field constant in the normal coordinate of a wall is even about it and
+    is reproduced next to the wall.  `skip` lists the boundary layers (axis,
+    side) where the field has neither symmetry."""
+    cases = [
+        (I.Grid(dim=2, axisym=0, n=(8, 12, 1), h=0.1, bc=((W, W), (D, W), (0, 0))),
+         lambda X, Y, Z: Y * (2.0 + 0.5 * X), [(0, 0), (0, 1), (1, 1)]),          # odd about y = 0
+        (I.Grid(dim=2, axisym=0, n=(8, 12, 1), h=0.1, bc=((W, W), (W, D), (0, 0))),
+         lambda X, Y, Z: (1.2 - Y) * (1.0 - 0.25 * X), [(0, 0), (0, 1), (1, 0)]),  # odd about y = 1.2
+        (I.Grid(dim=2, axisym=1, n=(8, 12, 1), h=0.1, bc=((A, D), (W, W), (0, 0))),
+         lambda X, Y, Z: (0.8 - X) + 0.0 * Y, [(0, 0)]),                          # odd about r = 0.8, even in z
+        (I.Grid(dim=2, axisym=1, n=(6, 8, 1), h=0.1, r0=0.3, bc=((D, W), (W, W), (0, 0))),
+         lambda X, Y, Z: 2.0 * (X - 0.3) + 0.0 * Y, [(0, 1)]),                    # odd about r = r0
+        (I.Grid(dim=3, axisym=0, n=(4, 6, 8), h=0.2, bc=((W, W), (W, W), (D, W))),
+         lambda X, Y, Z: Z * (1.0 + 0.3 * X - 0.2 * Y + 0.1 * X * Y),
+         [(0, 0), (0, 1), (1, 0), (1, 1), (2, 1)]),                               # odd about z = 0
+        (I.Grid(dim=3, axisym=0, n=(4, 6, 8), h=0.2, bc=((D, W), (W, W), (W, W))),
+         lambda X, Y, Z: X * (2.0 + 0.0 * Y + 0.0 * Z), [(0, 1)]),                # odd about x = 0, even in y, z
+    ]
+    for g, fn, skip in cases:
+        uc = np.stack([_field(g, True, fn), -2.0 * _field(g, True, fn)], axis=1)
+        exact = np.stack([_field(g, False, fn), -2.0 * _field(g, False, fn)], axis=1)
+        got = orc.prolong_add(g.as_dict(), uc, np.zeros((g.N, 2)))
+        idx = np.arange(g.N)
+        c = [idx % g.n[0], (idx // g.n[0]) % g.n[1], idx // (g.n[0] * g.n[1])]
+        keep = np.ones(g.N, bool)
+        for a, side in skip:
+            keep &= c[a] != (0 if side == 0 else g.n[a] - 1)
+        a_d, s_d = [(a, s_) for a in range(g.dim) for s_ in range(2) if g.bc[a][s_] == D][0]
+        assert np.any(keep & (c[a_d] == (0 if s_d == 0 else g.n[a_d] - 1)))
+        err = np.abs(got - exact)[keep].max()
+        assert err <= 1e-13 * np.abs(exact).max(), (g.bc, err)
+
+
+def test_mg_convergence_factor_axisymmetric_dirichlet(orc):
+    """Multigrid sanity on axisymmetric grids with Dirichlet faces, on the axis
+    and off it, at the paper's bubble scale (stiff p-row): the measured
+    contraction per V(2,2) cycle stays below 0.2 for both fields."""
+    for g in [I.Grid(dim=2, axisym=1, n=(64, 128, 1), h=1e-4, bc=((A, D), (D, D), (0, 0)),
+                     bcT=((0, 300), (300, 300), (0, 0)), bcp=((0, 1e5), (1e5, 1e5), (0, 0))),
+              I.Grid(dim=2, axisym=1, n=(64, 128, 1), h=1e-4, r0=4e-4, bc=((D, D), (D, W), (0, 0)),
+                     bcT=((300, 300), (300, 300), (0, 0)), bcp=((1e5, 1e5), (1e5, 1e5), (0, 0)))]:
+        p = I.random_coeff_problem(g, seed=3, dt=1e-5)
+        _, cyc, hist = orc.mg_solve(g.as_dict(), p.lam, p.fa, p.fk, p.b, p.x0, max_cycles=8, rtol=0.0)
+        q = hist[1:] / hist[:-1]
+        rate = np.exp(np.log(q[1:6]).mean(axis=0))
+        assert np.all(rate < 0.2), rate
