@@ -13,6 +13,7 @@ defect-correction loop after them; see the C file for the exact statements):
 - ``dense_solve``     exact solution of L(x) = b by Gaussian elimination
 - ``mg_solve``        defect-correction loop with V(nu1, nu2) cycles
 - ``rbgs_sweeps``     in-place red-black block Gauss-Seidel sweeps
+- ``wjac_sweeps``     weighted block Jacobi sweeps
 - ``residual_norms``  the per-field stopping norm ||D^-1 r||_2
 - ``level_coeffs``    coarse-level blocks and faces of the hierarchy
 - ``apply_rows``      L(x) at selected cells (residual checks of large solutions)
@@ -72,10 +73,13 @@ def configure(lib):
     lib.orc_apply_paper.restype = None
     lib.orc_dense_solve.argtypes = [gp, dp, pa3, pa3, dp, dp]
     lib.orc_dense_solve.restype = C.c_int
-    lib.orc_mg_solve.argtypes = [gp, dp, pa3, pa3, dp, dp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, dp, C.c_int]
+    lib.orc_mg_solve.argtypes = [gp, dp, pa3, pa3, dp, dp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, dp, C.c_int,
+                                 C.c_int, C.c_double]
     lib.orc_mg_solve.restype = C.c_int
     lib.orc_rbgs_sweeps.argtypes = [gp, dp, pa3, pa3, dp, dp, C.c_int]
     lib.orc_rbgs_sweeps.restype = C.c_int
+    lib.orc_wjac_sweeps.argtypes = [gp, dp, pa3, pa3, dp, dp, C.c_int, C.c_double]
+    lib.orc_wjac_sweeps.restype = C.c_int
     lib.orc_residual_norms.argtypes = [gp, dp, pa3, pa3, dp, dp, dp]
     lib.orc_residual_norms.restype = C.c_int
     lib.orc_num_levels.argtypes = [gp, C.c_int]
@@ -170,10 +174,13 @@ def dense_solve(g, lam, fa, fk, b) -> np.ndarray:
 
 
 CYCLES = {"V": 0, "W": 1, "F": 2}
+SMOOTHERS = {"rbgs": 0, "wjac": 1}
 
 
-def mg_solve(g, lam, fa, fk, b, x0, nu1=2, nu2=2, coarse_min=4, max_cycles=50, rtol=1e-10, cycle="V"):
-    """Returns (x, cycles, history) where history[k] = per-field norms before cycle k.  cycle: V, W or F."""
+def mg_solve(g, lam, fa, fk, b, x0, nu1=2, nu2=2, coarse_min=4, max_cycles=50, rtol=1e-10, cycle="V",
+             smoother="rbgs", omega=0.8):
+    """Returns (x, cycles, history) where history[k] = per-field norms before cycle k.  cycle: V, W or F;
+    smoother: rbgs (red-black block Gauss-Seidel) or wjac (weighted block Jacobi with weight omega)."""
     lib = _load()
     gs = _grid(g)
     lam, b = _c64(lam), _c64(b)
@@ -182,7 +189,8 @@ def mg_solve(g, lam, fa, fk, b, x0, nu1=2, nu2=2, coarse_min=4, max_cycles=50, r
     pk, kk = _faces(fk)
     hist = np.zeros(2 * (max_cycles + 1))
     rc = lib.orc_mg_solve(C.byref(gs), _dp(lam), pa, pk, _dp(b), _dp(x), int(nu1), int(nu2),
-                          int(coarse_min), int(max_cycles), float(rtol), _dp(hist), CYCLES[cycle])
+                          int(coarse_min), int(max_cycles), float(rtol), _dp(hist), CYCLES[cycle],
+                          SMOOTHERS[smoother], float(omega))
     if rc < 0:
         raise RuntimeError(f"oracle mg solve failed ({rc})")
     return x, rc, hist.reshape(-1, 2)[: rc + 1]
@@ -196,6 +204,18 @@ def rbgs_sweeps(g, lam, fa, fk, b, x0, sweeps=1) -> np.ndarray:
     pa, ka = _faces(fa)
     pk, kk = _faces(fk)
     if lib.orc_rbgs_sweeps(C.byref(gs), _dp(lam), pa, pk, _dp(b), _dp(x), int(sweeps)):
+        raise RuntimeError("oracle sweeps failed")
+    return x
+
+
+def wjac_sweeps(g, lam, fa, fk, b, x0, sweeps=1, omega=0.8) -> np.ndarray:
+    lib = _load()
+    gs = _grid(g)
+    lam, b = _c64(lam), _c64(b)
+    x = _c64(x0).copy()
+    pa, ka = _faces(fa)
+    pk, kk = _faces(fk)
+    if lib.orc_wjac_sweeps(C.byref(gs), _dp(lam), pa, pk, _dp(b), _dp(x), int(sweeps), float(omega)):
         raise RuntimeError("oracle sweeps failed")
     return x
 

@@ -41,6 +41,9 @@
  *     keeping its l4 div(k grad T) term;
  *   - V(nu1, nu2) cycle, red-black block Gauss-Seidel (red = even i+j+k,
  *     red first), each cell's two equations solved exactly for (T_i, p_i);
+ *     or, as the other smoother, weighted block Jacobi: every cell's two
+ *     equations solved against the previous iterate's neighbours, the cell
+ *     then moving a fraction omega of the way to that solution;
  *   - restriction: volume-weighted mean of the 2^dim children;
  *   - prolongation: cell-centred bi/tri-linear (weights 3/4 and 1/4 per axis),
  *     reflecting ghosts (same value at walls and the axis, opposite sign at
@@ -343,6 +346,43 @@ static void rbgs_sweep(level *L, double *const bcT2, double *const bcp2)
     }
 }
 
+/* One weighted block Jacobi sweep: every cell's two equations are solved
+ * for (T_i, p_i) with all other unknowns held at the previous iterate (the
+ * same z_i as a Gauss-Seidel update, but from old neighbours only), and the
+ * cell moves a fraction omega of the way: u_i <- u_i + omega (z_i - u_i). */
+static int wjac_sweep(level *L, double *const bcT2, double *const bcp2, double omega)
+{
+    double *z = malloc(sizeof(double) * 2 * L->N);
+    if (!z) return -2;
+    for (long i = 0; i < L->N; i++) {
+        int c[3];
+        cell_of(&L->g, i, c);
+        double e[2], D[4], s[2];
+        paper_row(L, L->u, bcT2, bcp2, c, e);
+        diag_block(L, c, D);
+        s[0] = L->rhs[2 * i] - (e[0] - (D[0] * L->u[2 * i] + D[1] * L->u[2 * i + 1]));
+        s[1] = L->rhs[2 * i + 1] - (e[1] - (D[2] * L->u[2 * i] + D[3] * L->u[2 * i + 1]));
+        solve2(D, s, z + 2 * i);
+    }
+    for (long i = 0; i < 2 * L->N; i++) L->u[i] = L->u[i] + omega * (z[i] - L->u[i]);
+    free(z);
+    return 0;
+}
+
+/* The smoother of a cycle: kind 0 = red-black block Gauss-Seidel, 1 =
+ * weighted block Jacobi with weight omega. */
+typedef struct {
+    int kind;
+    double omega;
+} smoother;
+
+static int smooth(level *L, const smoother *sm, double *const bcT2, double *const bcp2)
+{
+    if (sm->kind == 1) return wjac_sweep(L, bcT2, bcp2, sm->omega);
+    rbgs_sweep(L, bcT2, bcp2);
+    return 0;
+}
+
 /* ------------------------------------------------------------------ */
 /* Hierarchy                                                           */
 /* ------------------------------------------------------------------ */
@@ -541,21 +581,24 @@ static int coarse_solve(level *L)
  * cycle continues from the first one's coarse solution with the same
  * restricted right-hand side; at the coarsest level the exact solve is done
  * once (a second exact solve would give the same values). */
-static int mgcycle(level *Ls, int l, int nlev, int nu1, int nu2, int type)
+static int mgcycle(level *Ls, int l, int nlev, int nu1, int nu2, int type, const smoother *sm)
 {
     level *L = &Ls[l];
+    int rc;
     if (l == nlev - 1) return coarse_solve(L);
-    for (int s = 0; s < nu1; s++) rbgs_sweep(L, NULL, NULL);
+    for (int s = 0; s < nu1; s++)
+        if ((rc = smooth(L, sm, NULL, NULL))) return rc;
     level_residual(L);
     restrict_residual(L, &Ls[l + 1]);
-    int rc = mgcycle(Ls, l + 1, nlev, nu1, nu2, type);
+    rc = mgcycle(Ls, l + 1, nlev, nu1, nu2, type, sm);
     if (rc) return rc;
     if (type != 0 && l + 1 < nlev - 1) {
-        rc = mgcycle(Ls, l + 1, nlev, nu1, nu2, type == 1 ? 1 : 0);
+        rc = mgcycle(Ls, l + 1, nlev, nu1, nu2, type == 1 ? 1 : 0, sm);
         if (rc) return rc;
     }
     prolong_add(&Ls[l + 1], L);
-    for (int s = 0; s < nu2; s++) rbgs_sweep(L, NULL, NULL);
+    for (int s = 0; s < nu2; s++)
+        if ((rc = smooth(L, sm, NULL, NULL))) return rc;
     return 0;
 }
 
@@ -601,7 +644,9 @@ int orc_num_levels(const orc_grid *g, int coarse_min)
 
 /*
  * Solve L(x) = b (Eqs. 27-34) by the defect-correction loop with one
- * V(nu1, nu2) cycle (or W, F: cycle_type 1, 2) as the correction solve.
+ * V(nu1, nu2) cycle (or W, F: cycle_type 1, 2) as the correction solve,
+ * smoothed by red-black block Gauss-Seidel (smoother_kind 0) or weighted
+ * block Jacobi with weight omega (smoother_kind 1).
  *   x       in: initial guess a~; out: result
  *   rtol    stop when both per-field norms fell by rtol (rtol <= 0: run
  *           exactly max_cycles cycles)
@@ -611,8 +656,9 @@ int orc_num_levels(const orc_grid *g, int coarse_min)
  */
 int orc_mg_solve(const orc_grid *g, const double *lam, double *const fa[3], double *const fk[3],
                  const double *b, double *x, int nu1, int nu2, int coarse_min, int max_cycles,
-                 double rtol, double *hist, int cycle_type)
+                 double rtol, double *hist, int cycle_type, int smoother_kind, double omega)
 {
+    smoother sm = {smoother_kind, omega};
     int nlev = orc_num_levels(g, coarse_min);
     level *Ls = calloc(nlev, sizeof(level));
     double *res = NULL;
@@ -649,7 +695,7 @@ int orc_mg_solve(const orc_grid *g, const double *lam, double *const fa[3], doub
         /* step 3: L(da) ~= res by one V-cycle from da = 0 */
         memcpy(Ls[0].rhs, res, sizeof(double) * 2 * N);
         memset(Ls[0].u, 0, sizeof(double) * 2 * N);
-        rc = mgcycle(Ls, 0, nlev, nu1, nu2, cycle_type);
+        rc = mgcycle(Ls, 0, nlev, nu1, nu2, cycle_type, &sm);
         if (rc) goto done;
         /* step 4: a += da */
         for (long i = 0; i < 2 * N; i++) x[i] += Ls[0].u[i];
@@ -677,6 +723,22 @@ int orc_rbgs_sweeps(const orc_grid *g, const double *lam, double *const fa[3],
     memcpy(x, L.u, sizeof(double) * 2 * L.N);
     free_level(&L);
     return 0;
+}
+
+/* Weighted block Jacobi sweeps on level 0 with the grid's Dirichlet values. */
+int orc_wjac_sweeps(const orc_grid *g, const double *lam, double *const fa[3],
+                    double *const fk[3], const double *b, double *x, int sweeps, double omega)
+{
+    level L;
+    int rc = 0;
+    if (alloc_level(&L, g)) { free_level(&L); return -2; }
+    fill_level0(&L, lam, fa, fk);
+    memcpy(L.rhs, b, sizeof(double) * 2 * L.N);
+    memcpy(L.u, x, sizeof(double) * 2 * L.N);
+    for (int s = 0; s < sweeps && rc == 0; s++) rc = wjac_sweep(&L, &L.g.bcT[0][0], &L.g.bcp[0][0], omega);
+    memcpy(x, L.u, sizeof(double) * 2 * L.N);
+    free_level(&L);
+    return rc;
 }
 
 /* Per-field || D^{-1} res ||_2 of the current x (the stopping norm). */

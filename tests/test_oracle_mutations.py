@@ -117,9 +117,9 @@ CYCLE_MUTATIONS = {
     # the second coarse visit of W- and F-cycles left out: every cycle is a V-cycle
     "no_second_visit": ("if (type != 0 && l + 1 < nlev - 1) {", "if (0 && l + 1 < nlev - 1) {"),
     # the second visit restarts the coarse correction from zero, discarding the first
-    "second_visit_restarts": ("        rc = mgcycle(Ls, l + 1, nlev, nu1, nu2, type == 1 ? 1 : 0);",
+    "second_visit_restarts": ("        rc = mgcycle(Ls, l + 1, nlev, nu1, nu2, type == 1 ? 1 : 0, sm);",
                               "        memset(Ls[l + 1].u, 0, sizeof(double) * 2 * Ls[l + 1].N);\n"
-                              "        rc = mgcycle(Ls, l + 1, nlev, nu1, nu2, type == 1 ? 1 : 0);"),
+                              "        rc = mgcycle(Ls, l + 1, nlev, nu1, nu2, type == 1 ? 1 : 0, sm);"),
 }
 
 
@@ -188,5 +188,41 @@ def test_transfer_mutant_fails_a_pin(orc, name):
     try:
         with mutant(orc, name):
             assert not _transfer_pins_pass(orc), name
+    finally:
+        del MUTATIONS[name]
+
+
+# Planted mistakes in the weighted block Jacobi smoother, against its pin.
+WJAC_MUTATIONS = {
+    # the weight omega left out: every cell jumps to its block solution
+    "wjac_undamped": ("for (long i = 0; i < 2 * L->N; i++) L->u[i] = L->u[i] + omega * (z[i] - L->u[i]);",
+                      "for (long i = 0; i < 2 * L->N; i++) L->u[i] = z[i];"),
+    # cells updated in place, so later cells see new neighbours (a Gauss-Seidel sweep)
+    "wjac_in_place": ("        solve2(D, s, z + 2 * i);\n",
+                      "        solve2(D, s, z + 2 * i);\n"
+                      "        L->u[2 * i] = z[2 * i];\n        L->u[2 * i + 1] = z[2 * i + 1];\n"),
+}
+
+
+def _wjac_pins_pass(orc) -> bool:
+    import test_oracle_pins as P
+    try:
+        for name in ("2d_mixed", "axi_axis", "3d_mixed"):
+            P.test_wjac_sweep_is_damped_block_jacobi(orc, name, 0.8)
+    except AssertionError:
+        return False
+    return True
+
+
+def test_unmutated_oracle_passes_the_wjac_pin(orc):
+    assert _wjac_pins_pass(orc)
+
+
+@pytest.mark.parametrize("name", list(WJAC_MUTATIONS))
+def test_wjac_mutant_fails_the_pin(orc, name):
+    MUTATIONS[name] = WJAC_MUTATIONS[name]
+    try:
+        with mutant(orc, name):
+            assert not _wjac_pins_pass(orc), name
     finally:
         del MUTATIONS[name]

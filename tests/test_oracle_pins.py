@@ -640,3 +640,65 @@ def test_mg_convergence_factor_axisymmetric_dirichlet(orc):
         q = hist[1:] / hist[:-1]
         rate = np.exp(np.log(q[1:6]).mean(axis=0))
         assert np.all(rate < 0.2), rate
+
+
+# ---------------------------------------------------------------- weighted block Jacobi
+def _block_jacobi_step(g, lam, fa, fk, b, x, omega):
+    """x + omega D^-1 (b - A x) with A and its 2x2 diagonal blocks D taken from
+    the independently assembled sparse operator of Eqs. 27-28."""
+    M, aff = fv.paper_operator(g, lam, fa, fk)
+    M = M.tocsr()
+    r = b.reshape(-1) - aff - M @ x.reshape(-1)
+    out = x.copy()
+    for i in range(g.N):
+        Dblk = M[2 * i: 2 * i + 2, 2 * i: 2 * i + 2].toarray()
+        out[i] += omega * np.linalg.solve(Dblk, r[2 * i: 2 * i + 2])
+    return out
+
+
+@pytest.mark.parametrize("name", list(GRIDS))
+@pytest.mark.parametrize("omega", [0.8, 0.55])
+def test_wjac_sweep_is_damped_block_jacobi(orc, name, omega):
+    """One and two weighted block Jacobi sweeps equal the damped block Jacobi
+    step x + omega D^-1 (b - A x) of the assembled matrix, D the 2x2 blocks of
+    each cell's own (T_i, p_i) in its two rows, every cell from the previous
+    iterate."""
+    g = GRIDS[name]
+    rng = np.random.default_rng(12)
+    lam, fa, fk = rand_lam(g.N, rng), rand_faces(g, rng), rand_faces(g, rng)
+    b = rng.standard_normal((g.N, 2))
+    x0 = rng.standard_normal((g.N, 2))
+    ref1 = _block_jacobi_step(g, lam, fa, fk, b, x0, omega)
+    ref2 = _block_jacobi_step(g, lam, fa, fk, b, ref1, omega)
+    x1 = orc.wjac_sweeps(g.as_dict(), lam, fa, fk, b, x0, sweeps=1, omega=omega)
+    x2 = orc.wjac_sweeps(g.as_dict(), lam, fa, fk, b, x0, sweeps=2, omega=omega)
+    assert np.abs(x1 - ref1).max() <= 1e-12 * np.abs(ref1).max()
+    assert np.abs(x2 - ref2).max() <= 1e-12 * np.abs(ref2).max()
+
+
+@pytest.mark.parametrize("name", list(GRIDS))
+def test_wjac_mg_matches_dense_with_jumps(orc, name):
+    """Multigrid smoothed by weighted block Jacobi converges to the exact
+    solution of the paper's system (the smoother changes the iteration, not
+    its fixed point)."""
+    g = GRIDS[name]
+    p = I.random_coeff_problem(g, seed=7, dt=1e-5)
+    gd = g.as_dict()
+    xd = orc.dense_solve(gd, p.lam, p.fa, p.fk, p.b)
+    xm, cyc, hist = orc.mg_solve(gd, p.lam, p.fa, p.fk, p.b, p.x0, coarse_min=2, max_cycles=200,
+                                 rtol=1e-14, smoother="wjac", omega=0.8)
+    assert rel_dev(xm, xd, p.x0) <= 1e-11
+
+
+def test_wjac_mg_convergence_factor_stiff(orc):
+    """Multigrid sanity with the Jacobi smoother at the paper's bubble scale:
+    V(2,2) with omega = 0.8 contracts both fields per cycle (measured factor
+    below 0.5), more slowly than red-black Gauss-Seidel."""
+    p = I.stiff(I.bubble_2d, 64)
+    gd = p.grid.as_dict()
+    rate = {}
+    for sm in ("rbgs", "wjac"):
+        _, _, hist = orc.mg_solve(gd, p.lam, p.fa, p.fk, p.b, p.x0, max_cycles=6, rtol=0.0, smoother=sm)
+        rate[sm] = np.exp(np.log(hist[1:6] / hist[0:5]).mean(axis=0))
+    assert np.all(rate["wjac"] < 0.5), rate
+    assert np.all(rate["rbgs"] <= rate["wjac"]), rate
