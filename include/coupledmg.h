@@ -88,9 +88,17 @@ typedef struct {
                             the first one's coarse solution; the exactly solved coarsest level is solved once.  W and
                             F run without the V-cycle tail kernel (mg_tuning.tail_level is ignored); batches take V
                             only. */
+    int smoother;        /* MG_SMOOTH_RBGS (default): red-black block Gauss-Seidel, red (even i+j+k) first;
+                            MG_SMOOTH_WJAC: weighted block Jacobi, each cell's two rows solved against the
+                            previous iterate, then x_i += omega (z_i - x_i).  The paper names a multigrid solver
+                            without its smoother (Sec. 3); both give the same fixed point.  WJAC runs one kernel
+                            per sweep (mg_tuning.sweep, tile and tail_level are ignored; persistent applies) and
+                            batches take RBGS only. */
+    double omega;        /* MG_SMOOTH_WJAC: the weight, 0 < omega <= 1 (default 0.8) */
 } mg_options;
 
 enum { MG_CYCLE_V = 0, MG_CYCLE_W = 1, MG_CYCLE_F = 2 };
+enum { MG_SMOOTH_RBGS = 0, MG_SMOOTH_WJAC = 1 };
 
 typedef struct {
     int cycles;          /* V-cycles run (MIXED: total FP32 cycles) */
@@ -104,7 +112,8 @@ typedef struct {
 
 typedef struct mg_handle mg_handle;
 
-/* Fills defaults: V(2,2), FP64, rtol 1e-10, 50 cycles, coarse_min 4, 1 inner cycle. */
+/* Fills defaults: V(2,2), FP64, rtol 1e-10, 50 cycles, coarse_min 4, 1 inner cycle, red-black block
+ * Gauss-Seidel (omega 0.8 for weighted block Jacobi). */
 MG_API mg_status mg_default_options(mg_options *opt);
 
 /* Device bytes a handle of this grid and these options needs (hierarchy,
@@ -142,9 +151,10 @@ MG_API mg_status mg_solve(mg_handle *h, const double *rhs, double *x, int on_dev
  * given side.  A building block for residual checks: res = b - L(x). */
 MG_API mg_status mg_apply(mg_handle *h, const double *x, double *y, int on_device);
 
-/* In place: `sweeps` red-black block Gauss-Seidel sweeps on the finest level
- * (red = even i+j+k first; each cell's two equations solved exactly for
- * (T_i, p_i)) of L(x) = rhs. */
+/* In place: `sweeps` sweeps of the handle's smoother on the finest level of
+ * L(x) = rhs: red-black block Gauss-Seidel (red = even i+j+k first; each
+ * cell's two equations solved exactly for (T_i, p_i)), or weighted block
+ * Jacobi (every cell from the previous iterate, damped by omega). */
 MG_API mg_status mg_smooth(mg_handle *h, const double *rhs, double *x, int sweeps, int on_device);
 
 /* Per-field stopping norms ||D^-1 r||_2 (out[2], host) of x for rhs, where
@@ -483,24 +493,35 @@ MG_API mg_status mg_provisional_async(const mg_grid *grid, double dt, const doub
  * device memory is owned by another allocator, or their time loop must not
  * call cudaMalloc/cudaFree, which can synchronise the whole device - and so
  * cannot create an mg_handle: computes the same per-field norms
- * ||D^-1 r||_2 as mg_residual_norms, r = rhs - L(x) of Eqs. 27-28, straight
- * from the caller's arrays.
+ * ||D^-1 r||_2 as mg_residual_norms, with r = rhs - L(x) for the operator
+ * that mg_apply applies, straight from the caller's arrays.
+ *   grid: checked by the same rules as in mg_create.
  *   lambda [N][4], face_alpha[a] / face_k[a] (a < dim), rhs [N][2], x [N][2]:
  *     device pointers in the layouts described at the top of this file.
  *   out: device pointer to 2 doubles, receives (norm_T, norm_p).
- *   stream: cudaStream_t for the work; the call returns after it completed.
+ *   stream: cudaStream_t for the work; the call waits for it to finish
+ *     before returning.
  * Allocates nothing: partial sums go to a static device array of 65536
- * entries (1 MiB per GPU that loads the library, kept until exit), so grids
- * of more than 65536 blocks of 32 x 8 cells (beyond 16,777,216 cells, e.g.
- * 256^3 or 4096^2) are rejected with MG_ERR_INVALID_ARG.  Its device address
- * is looked up the first time this is called on each device; make that first
- * call before any stream capture.  Each call rewrites every partial it later
- * reads, so no state carries over from the previous call, but all calls share
- * the array: calls that overlap on the GPU (other streams, other threads)
- * race and must be serialised by the caller. */
+ * entries (1 MiB on each device that runs it, kept until exit), so grids of
+ * more than 65536 blocks of 32 x 8 cells (beyond 16,777,216 cells, e.g. 256^3
+ * or 4096^2) are rejected with MG_ERR_INVALID_ARG.  The first call on each
+ * device sets the scratch up (looks up its device address; with lazy module
+ * loading, loads it and the kernels): make that first call before any stream
+ * capture begins.  Each call rewrites every partial it later reads, so no
+ * state carries over from the previous call, but all calls share the array:
+ * calls that overlap on the GPU (other streams, other threads) race and must
+ * be serialised by the caller. */
 MG_API mg_status mg_residual_norms_noalloc(const mg_grid *grid, const double *lambda,
                                            const double *const face_alpha[3], const double *const face_k[3],
                                            const double *rhs, const double *x, double *out, void *stream);
+
+/* The current device's FP64 FMA issue rate in G FMA instructions per second
+ * (no counterpart in the paper: the roofline denominator of the kernels bound
+ * by the FP64 pipe).  A kernel of independent register-resident FMA chains
+ * (4 blocks of 256 threads per SM, 8 chains per thread, no memory traffic)
+ * runs once untimed and `repeats` (1..100) times timed with CUDA events on
+ * `stream`; the fastest launch gives the rate.  Synchronous. */
+MG_API mg_status mg_fp64_fma_rate(void *stream, int repeats, double *g_fma_per_s);
 
 /* Moves all later work of the handle to another stream (cudaStream_t on the
  * handle's device).  Waits for the handle's work on its current stream. */

@@ -34,7 +34,8 @@ EXPORTS = ["mg_default_options", "mg_workspace_size", "mg_create", "mg_set_coeff
            "mg_batch_set_coeffs", "mg_get_tuning", "mg_set_tuning", "mg_autotune", "mg_batch_get_tuning",
            "mg_batch_set_tuning", "mg_batch_autotune", "mg_assemble_async", "mg_correct_async",
            "mg_energy_async", "mg_momentum_create", "mg_momentum_set_coeffs", "mg_momentum_apply",
-           "mg_momentum_solve", "mg_momentum_destroy", "mg_momentum_rhs_async", "mg_provisional_async"]
+           "mg_momentum_solve", "mg_momentum_destroy", "mg_momentum_rhs_async", "mg_provisional_async",
+           "mg_fp64_fma_rate"]
 
 MG_MAX_LEVELS = 32
 MG_SWEEP_COLOUR, MG_SWEEP_FUSED, MG_SWEEP_ASYNC, MG_SWEEP_COLOUR2 = 1, 2, 3, 4
@@ -58,7 +59,8 @@ class MgGrid(C.Structure):
 
 class MgOptions(C.Structure):
     _fields_ = [("nu1", C.c_int), ("nu2", C.c_int), ("precision", C.c_int), ("rtol", C.c_double),
-                ("max_cycles", C.c_int), ("coarse_min", C.c_int), ("inner_cycles", C.c_int), ("cycle", C.c_int)]
+                ("max_cycles", C.c_int), ("coarse_min", C.c_int), ("inner_cycles", C.c_int), ("cycle", C.c_int),
+                ("smoother", C.c_int), ("omega", C.c_double)]
 
 
 class MgStats(C.Structure):
@@ -199,6 +201,7 @@ def load(path: str = LIB_PATH):
             "mg_momentum_destroy": ([P], C.c_int),
             "mg_momentum_rhs_async": ([C.POINTER(MgGrid), C.c_double, C.c_double, pa3, P, P, P, pa3, P], C.c_int),
             "mg_provisional_async": ([C.POINTER(MgGrid), C.c_double, P, P, pa3, pa3, P], C.c_int),
+            "mg_fp64_fma_rate": ([P, C.c_int, dp], C.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -239,16 +242,19 @@ def make_grid(g) -> MgGrid:
 
 
 CYCLES = {"V": 0, "W": 1, "F": 2}
+SMOOTHERS = {"rbgs": 0, "wjac": 1}
 
 
 def make_options(precision="fp64", rtol=1e-10, max_cycles=50, nu1=2, nu2=2, coarse_min=4,
-                 inner_cycles=1, cycle="V") -> MgOptions:
+                 inner_cycles=1, cycle="V", smoother="rbgs", omega=0.8) -> MgOptions:
     o = MgOptions()
     check(load().mg_default_options(C.byref(o)))
     o.precision = MG_MIXED if precision in ("mixed", MG_MIXED) else MG_FP64
     o.rtol, o.max_cycles, o.nu1, o.nu2 = float(rtol), int(max_cycles), int(nu1), int(nu2)
     o.coarse_min, o.inner_cycles = int(coarse_min), int(inner_cycles)
     o.cycle = CYCLES[cycle] if isinstance(cycle, str) else int(cycle)
+    o.smoother = SMOOTHERS[smoother] if isinstance(smoother, str) else int(smoother)
+    o.omega = float(omega)
     return o
 
 
@@ -294,6 +300,16 @@ def residual_norms_noalloc(grid, lam, fa, fk, b, x, out, stream=None) -> None:
         stream = torch.cuda.current_stream()
     check(load().mg_residual_norms_noalloc(C.byref(g), _ptr(lam, True)[0], pa, pk, _ptr(b, True)[0],
                                            _ptr(x, True)[0], _ptr(out, True)[0], C.c_void_p(stream.cuda_stream)))
+
+
+def fp64_fma_rate(repeats: int = 5, stream=None) -> float:
+    """mg_fp64_fma_rate: the current device's measured FP64 FMA rate, G instructions per second."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    out = C.c_double()
+    check(load().mg_fp64_fma_rate(C.c_void_p(stream.cuda_stream), int(repeats), C.byref(out)))
+    return out.value
 
 
 def make_phase(ph) -> MgPhase:
@@ -378,12 +394,13 @@ class Solver:
 
     def __init__(self, grid, precision="fp64", rtol=1e-10, max_cycles=50, nu1=2, nu2=2, coarse_min=4,
                  inner_cycles=1, device: Optional[int] = None, stream=None, torch_workspace: bool = True,
-                 cycle="V"):
+                 cycle="V", smoother="rbgs", omega=0.8):
         import torch
         lib = load()
         self._lib = lib
         self.grid = make_grid(grid)
-        self.options = make_options(precision, rtol, max_cycles, nu1, nu2, coarse_min, inner_cycles, cycle)
+        self.options = make_options(precision, rtol, max_cycles, nu1, nu2, coarse_min, inner_cycles, cycle,
+                                    smoother, omega)
         dev = torch.cuda.current_device() if device is None else int(device)
         self.device = dev
         check(lib.mg_set_device(dev))

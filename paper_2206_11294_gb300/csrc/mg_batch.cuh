@@ -687,7 +687,8 @@ void b_step(mg_batch *b, cudaStream_t s) {
 
 bool same_options(const mg_options &a, const mg_options &c) {
     return a.nu1 == c.nu1 && a.nu2 == c.nu2 && a.precision == c.precision && a.rtol == c.rtol &&
-           a.max_cycles == c.max_cycles && a.inner_cycles == c.inner_cycles && a.cycle == c.cycle;
+           a.max_cycles == c.max_cycles && a.inner_cycles == c.inner_cycles && a.cycle == c.cycle &&
+           a.smoother == c.smoother;
 }
 
 void add_blocks(std::vector<int2> &t, int level_index, long long blocks) {
@@ -711,6 +712,8 @@ mg_status mg_batch_create(int count, mg_handle *const *handles, mg_batch **out) 
                         "max_cycles, inner_cycles), stream and device");
     }
     if (handles[0]->opt.cycle != MG_CYCLE_V) return fail(MG_ERR_INVALID_ARG, "mg_batch_create: batches run V-cycles");
+    if (handles[0]->opt.smoother != MG_SMOOTH_RBGS)
+        return fail(MG_ERR_INVALID_ARG, "mg_batch_create: batches smooth by red-black block Gauss-Seidel");
     mg_batch *b = new (std::nothrow) mg_batch();
     if (!b) return fail(MG_ERR_OOM, "host allocation failed");
     b->count = count;

@@ -55,7 +55,7 @@ struct LevelBuf {
     long long N;
     long long nf[3];
     double2 *x, *b;
-    double2 *xalt;          // ping-pong partner of x for fused sweeps (2D)
+    double2 *xalt;          // ping-pong partner of x for fused sweeps (2D) and Jacobi sweeps
     double2 *G[3];
     dq *S;                  // scaled local terms s [[l1, l2], [0, l3]] (set-up)
     dq *D, *Dinv, *W;
@@ -75,6 +75,35 @@ struct LevelBuf {
 mg_status cmg::set_error(mg_status s, const char *msg) {
     g_err = msg ? msg : "";
     return s;
+}
+
+// The grid alone: dimensions, spacing, boundary kinds and values.
+mg_status cmg::check_grid_geom(const mg_grid *g) {
+    if (!g) return fail(MG_ERR_INVALID_ARG, "grid must not be NULL");
+    if (g->dim != 2 && g->dim != 3) return fail(MG_ERR_INVALID_ARG, "dim must be 2 or 3");
+    if (g->axisym && g->dim != 2) return fail(MG_ERR_INVALID_ARG, "axisymmetric grids are 2D (r, z)");
+    for (int a = 0; a < 3; a++) {
+        if (g->n[a] < 1) return fail(MG_ERR_INVALID_ARG, "every n[a] must be >= 1");
+        if (a >= g->dim && g->n[a] != 1) return fail(MG_ERR_INVALID_ARG, "n[2] must be 1 for a 2D grid");
+    }
+    if (g->n[0] > (1 << 28) || g->n[1] > 8 * 65535 || g->n[2] > 65535)
+        return fail(MG_ERR_INVALID_ARG, "grid too large for the launch geometry (n1 <= 524280, n2 <= 65535)");
+    if (!(g->h > 0.0) || !std::isfinite(g->h)) return fail(MG_ERR_INVALID_ARG, "h must be positive and finite");
+    if (g->axisym && (!(g->r0 >= 0.0) || !std::isfinite(g->r0)))
+        return fail(MG_ERR_INVALID_ARG, "r0 must be >= 0 and finite");
+    for (int a = 0; a < g->dim; a++)
+        for (int s = 0; s < 2; s++) {
+            const int k = g->bc[a][s];
+            if (k != MG_BC_WALL && k != MG_BC_DIRICHLET && k != MG_BC_AXIS)
+                return fail(MG_ERR_INVALID_ARG, "unknown boundary kind");
+            if (k == MG_BC_AXIS && !(g->axisym && a == 0 && s == 0 && g->r0 == 0.0))
+                return fail(MG_ERR_INVALID_ARG, "MG_BC_AXIS only on the low-r side of an axisymmetric grid with r0 = 0");
+            if (k == MG_BC_DIRICHLET && (!std::isfinite(g->bc_T[a][s]) || !std::isfinite(g->bc_p[a][s])))
+                return fail(MG_ERR_INVALID_ARG, "Dirichlet values must be finite");
+        }
+    if (g->axisym && g->r0 == 0.0 && g->bc[0][0] == MG_BC_DIRICHLET)
+        return fail(MG_ERR_INVALID_ARG, "the symmetry axis (r0 = 0) cannot carry a Dirichlet condition");
+    return MG_OK;
 }
 
 struct mg_handle {
@@ -143,35 +172,6 @@ bool can_coarsen(const int n[3], int dim, int coarse_min) {
     return true;
 }
 
-// The grid alone: dimensions, spacing, boundary kinds and values.
-mg_status check_grid_geom(const mg_grid *g) {
-    if (!g) return fail(MG_ERR_INVALID_ARG, "grid must not be NULL");
-    if (g->dim != 2 && g->dim != 3) return fail(MG_ERR_INVALID_ARG, "dim must be 2 or 3");
-    if (g->axisym && g->dim != 2) return fail(MG_ERR_INVALID_ARG, "axisymmetric grids are 2D (r, z)");
-    for (int a = 0; a < 3; a++) {
-        if (g->n[a] < 1) return fail(MG_ERR_INVALID_ARG, "every n[a] must be >= 1");
-        if (a >= g->dim && g->n[a] != 1) return fail(MG_ERR_INVALID_ARG, "n[2] must be 1 for a 2D grid");
-    }
-    if (g->n[0] > (1 << 28) || g->n[1] > 8 * 65535 || g->n[2] > 65535)
-        return fail(MG_ERR_INVALID_ARG, "grid too large for the launch geometry (n1 <= 524280, n2 <= 65535)");
-    if (!(g->h > 0.0) || !std::isfinite(g->h)) return fail(MG_ERR_INVALID_ARG, "h must be positive and finite");
-    if (g->axisym && (!(g->r0 >= 0.0) || !std::isfinite(g->r0)))
-        return fail(MG_ERR_INVALID_ARG, "r0 must be >= 0 and finite");
-    for (int a = 0; a < g->dim; a++)
-        for (int s = 0; s < 2; s++) {
-            const int k = g->bc[a][s];
-            if (k != MG_BC_WALL && k != MG_BC_DIRICHLET && k != MG_BC_AXIS)
-                return fail(MG_ERR_INVALID_ARG, "unknown boundary kind");
-            if (k == MG_BC_AXIS && !(g->axisym && a == 0 && s == 0 && g->r0 == 0.0))
-                return fail(MG_ERR_INVALID_ARG, "MG_BC_AXIS only on the low-r side of an axisymmetric grid with r0 = 0");
-            if (k == MG_BC_DIRICHLET && (!std::isfinite(g->bc_T[a][s]) || !std::isfinite(g->bc_p[a][s])))
-                return fail(MG_ERR_INVALID_ARG, "Dirichlet values must be finite");
-        }
-    if (g->axisym && g->r0 == 0.0 && g->bc[0][0] == MG_BC_DIRICHLET)
-        return fail(MG_ERR_INVALID_ARG, "the symmetry axis (r0 = 0) cannot carry a Dirichlet condition");
-    return MG_OK;
-}
-
 mg_status check_grid(const mg_grid *g, const mg_options *o) {
     if (!g || !o) return fail(MG_ERR_INVALID_ARG, "grid and options must not be NULL");
     const mg_status st = check_grid_geom(g);
@@ -184,6 +184,10 @@ mg_status check_grid(const mg_grid *g, const mg_options *o) {
     if (!std::isfinite(o->rtol)) return fail(MG_ERR_INVALID_ARG, "rtol must be finite");
     if (o->cycle != MG_CYCLE_V && o->cycle != MG_CYCLE_W && o->cycle != MG_CYCLE_F)
         return fail(MG_ERR_INVALID_ARG, "cycle must be MG_CYCLE_V, MG_CYCLE_W or MG_CYCLE_F");
+    if (o->smoother != MG_SMOOTH_RBGS && o->smoother != MG_SMOOTH_WJAC)
+        return fail(MG_ERR_INVALID_ARG, "smoother must be MG_SMOOTH_RBGS or MG_SMOOTH_WJAC");
+    if (o->smoother == MG_SMOOTH_WJAC && !(o->omega > 0.0 && o->omega <= 1.0))
+        return fail(MG_ERR_INVALID_ARG, "omega must be in (0, 1] for weighted block Jacobi");
     int n[3] = {g->n[0], g->n[1], g->n[2]}, lev = 1;
     while (can_coarsen(n, g->dim, o->coarse_min) && lev < kMaxLevels) {
         for (int a = 0; a < g->dim; a++) n[a] /= 2;
@@ -237,7 +241,8 @@ void plan(mg_handle *h, char *base, size_t *bytes) {
         }
         l.x = P.take<double2>(l.N);
         l.b = P.take<double2>(l.N);
-        if (g.dim == 2) l.xalt = P.take<double2>(l.N);
+        const bool pingpong = g.dim == 2 || h->opt.smoother == MG_SMOOTH_WJAC;
+        if (pingpong) l.xalt = P.take<double2>(l.N);
         for (int a = 0; a < g.dim; a++) l.G[a] = P.take<double2>(l.nf[a]);
         l.S = P.take<dq>(l.N);
         l.D = P.take<dq>(l.N);
@@ -248,7 +253,7 @@ void plan(mg_handle *h, char *base, size_t *bytes) {
         if (mixed) {
             l.x32 = P.take<float2>(l.N);
             l.b32 = P.take<float2>(l.N);
-            if (g.dim == 2) l.xalt32 = P.take<float2>(l.N);
+            if (pingpong) l.xalt32 = P.take<float2>(l.N);
             for (int a = 0; a < g.dim; a++) l.G32[a] = P.take<float2>(l.nf[a]);
             if (g.dim == 2) {
                 l.p0 = (n[0] + 2) & ~1;
@@ -270,7 +275,7 @@ void plan(mg_handle *h, char *base, size_t *bytes) {
     // The cluster tail takes the levels below the finest whose cells fit
     // kTailCells, when there are at least two of them.
     h->tail_lev = h->nlev;
-    for (int l = 1; l < h->nlev; l++)
+    for (int l = 1; l < h->nlev && h->opt.smoother == MG_SMOOTH_RBGS; l++)
         if (h->L[l].N <= kTailCells) { h->tail_lev = l; break; }
     if (h->nlev - h->tail_lev < 2 || h->nlev - h->tail_lev > kTailMaxLevels) h->tail_lev = h->nlev;
     h->tail_ctas = kTailCtas;
@@ -566,10 +571,40 @@ void enqueue_sweeps(const mg_handle *h, cudaStream_t s, int l, int sweeps, int k
     }
 }
 
+// `sweeps` weighted block Jacobi sweeps on level l, alternating x -> xalt ->
+// x; after an odd number the result is copied back into x.
+template <typename R, int DIM>
+void enqueue_wjac(const mg_handle *h, cudaStream_t s, int l, int sweeps) {
+    using V2 = typename Vec<R>::v2;
+    const LevelBuf &lb = h->L[l];
+    Level<R> v = view<R>(lb);
+    V2 *a = v.x, *b = xalt_of<R>(lb);
+    const R omega = (R)h->opt.omega;
+    const dim3 gr = cell_grid(lb, DIM, lb.n[0]);
+    for (int q = 0; q < sweeps; q++) {
+        if (h->persistent)
+            k_wjac<R, DIM, true><<<wave((const void *)k_wjac<R, DIM, true>, tiles_of(gr)), kBlock, 0, s>>>(v, a, b, omega);
+        else
+            k_wjac<R, DIM, false><<<gr, kBlock, 0, s>>>(v, a, b, omega);
+        counted(h);
+        std::swap(a, b);
+    }
+    if (a != v.x) cudaMemcpyAsync(v.x, a, sizeof(V2) * lb.N, cudaMemcpyDeviceToDevice, s);
+}
+
 template <typename R, int DIM>
 void enqueue_smooth(const mg_handle *h, cudaStream_t s, int l, int sweeps) {
-    enqueue_sweeps<R, DIM>(h, s, l, sweeps, h->sweep[l], h->tile[l]);
+    if (h->opt.smoother == MG_SMOOTH_WJAC) enqueue_wjac<R, DIM>(h, s, l, sweeps);
+    else enqueue_sweeps<R, DIM>(h, s, l, sweeps, h->sweep[l], h->tile[l]);
 }
+
+// Red-black Gauss-Seidel leaves the residual of the colour swept last at zero,
+// so the restriction after pre-smoothing evaluates the red children only and
+// the norm after post-smoothing the red cells only; Jacobi leaves no such zeros.
+bool red_only_after_sweeps(const mg_handle *h) { return h->opt.smoother == MG_SMOOTH_RBGS; }
+
+// The tail kernel runs red-black V-cycles.
+bool tail_runs(const mg_handle *h) { return h->opt.cycle == MG_CYCLE_V && h->opt.smoother == MG_SMOOTH_RBGS; }
 
 // Kernel launches and sweeps of one call of enqueue_smooth.
 void smooth_launches(bool fused, int sweeps, long long *launches, long long *sweeps_out) {
@@ -635,7 +670,7 @@ template <typename R, int DIM>
 // level.  The tail kernel runs V-cycles only, so W and F cycles never use it.
 void enqueue_vcycle(const mg_handle *h, cudaStream_t s, int l, int type) {
     const LevelBuf &lb = h->L[l];
-    if (l == h->tail_lev && h->opt.cycle == MG_CYCLE_V) {
+    if (l == h->tail_lev && tail_runs(h)) {
         // the coarsest inverse is computed on the aux stream after each set-up
         cudaStreamWaitEvent(s, h->ev_inv, cudaEventWaitExternal);
         enqueue_tail<R, DIM>(h, s);
@@ -663,7 +698,7 @@ void enqueue_vcycle(const mg_handle *h, cudaStream_t s, int l, int type) {
     enqueue_smooth<R, DIM>(h, s, l, h->opt.nu1);
     if (tm_pre) cudaEventRecordWithFlags(h->ev[1], s, cudaEventRecordExternal);
     const dim3 rg = cell_grid(cb, DIM, cb.n[0]);
-    if (h->opt.nu1 > 0) {
+    if (h->opt.nu1 > 0 && red_only_after_sweeps(h)) {
         if (h->persistent)
             k_residual_restrict<R, DIM, true, true>
                 <<<wave((const void *)k_residual_restrict<R, DIM, true, true>, tiles_of(rg)), kBlock, 0, s>>>(view<R>(lb),
@@ -766,7 +801,7 @@ void warm_waves() {
 template <int DIM>
 void enqueue_cycle64(const mg_handle *h, cudaStream_t s) {
     enqueue_vcycle<double, DIM>(h, s, 0, h->opt.cycle);
-    enqueue_norm<DIM>(h, s, h->opt.nu2 > 0);
+    enqueue_norm<DIM>(h, s, h->opt.nu2 > 0 && red_only_after_sweeps(h));
     cudaMemcpyAsync(h->norms_h, h->norms_d, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
 }
 
@@ -880,7 +915,13 @@ mg_status accumulate_timing(mg_handle *h) {
     h->smooth_ms += (double)a;
     long long l1, s1;
     const bool fused = h->grid.dim == 2 && (h->sweep[0] == MG_SWEEP_FUSED || h->sweep[0] == MG_SWEEP_ASYNC);
-    smooth_launches(fused, h->opt.nu1 > 0 ? h->opt.nu1 : h->opt.nu2, &l1, &s1);
+    const int sw = h->opt.nu1 > 0 ? h->opt.nu1 : h->opt.nu2;
+    if (h->opt.smoother == MG_SMOOTH_WJAC) {
+        l1 = sw;                 // one Jacobi kernel per sweep
+        s1 = sw;
+    } else {
+        smooth_launches(fused, sw, &l1, &s1);
+    }
     h->smooth_launches += l1;
     h->smooth_sweeps += s1;
     return MG_OK;
@@ -1283,8 +1324,9 @@ mg_status time_graph(mg_handle *h, int launches, double *ms, F &&body) {
 template <typename R, int DIM>
 mg_status autotune_impl(mg_handle *h, int reps, double *vcycle_ms) {
     mg_status st;
-    // sweeps, level by level (the coarsest level is solved, not smoothed)
-    for (int l = 0; l + 1 < h->nlev; l++) {
+    // sweeps, level by level (the coarsest level is solved, not smoothed);
+    // the Jacobi smoother has a single kernel
+    for (int l = 0; l + 1 < h->nlev && h->opt.smoother == MG_SMOOTH_RBGS; l++) {
         // candidates: colour, colour with two rows per thread, then (2D) fused and TMA-fed fused per tile
         const int ncand = DIM == 2 ? 2 + 2 * kTileShapes : 2;
         double best = 1e30;
@@ -1307,7 +1349,7 @@ mg_status autotune_impl(mg_handle *h, int reps, double *vcycle_ms) {
     // the cluster tail: none, or each allowed first level and cluster size
     std::vector<std::pair<int, int>> cand{{h->nlev, kTailCtas}};
     const bool wide = tail_ctas_allowed<R, DIM>(16);
-    for (int l = 1; l < h->nlev && h->opt.cycle == MG_CYCLE_V; l++) {     // the tail runs V-cycles only
+    for (int l = 1; l < h->nlev && tail_runs(h); l++) {     // the tail runs red-black V-cycles only
         if (tail_level_ok(h, l, 1)) cand.push_back({l, 1});
         if (tail_level_ok(h, l, kTailCtas)) cand.push_back({l, kTailCtas});
         if (wide && tail_level_ok(h, l, 16)) cand.push_back({l, 16});
@@ -1360,6 +1402,8 @@ mg_status mg_default_options(mg_options *o) {
     o->coarse_min = 4;
     o->inner_cycles = 1;
     o->cycle = MG_CYCLE_V;
+    o->smoother = MG_SMOOTH_RBGS;
+    o->omega = 0.8;
     return MG_OK;
 }
 

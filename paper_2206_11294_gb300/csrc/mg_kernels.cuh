@@ -152,6 +152,34 @@ __global__ void __launch_bounds__(kBX * kBY, 8) k_rbgs_colour(Level<R> L, int co
 }
 
 // ---------------------------------------------------------------------------
+// Weighted block Jacobi (the other smoother): every cell solves its two rows
+// against the previous iterate xin, z_i = bt_i - W_i (sT, sp) with sT, sp the
+// neighbour sums of xin, and moves a fraction omega of the way:
+// xout_i = xin_i + omega (z_i - xin_i).  xin and xout are distinct buffers.
+// ---------------------------------------------------------------------------
+template <typename R, int DIM>
+__device__ __forceinline__ void wjac_block(const Level<R> &L, const typename Vec<R>::v2 *__restrict__ xin,
+                                           typename Vec<R>::v2 *__restrict__ xout, R omega, int bx, int by, int bz) {
+    const int i = bx * kBX + (int)threadIdx.x;
+    const int j = by * kBY + (int)threadIdx.y;
+    const int k = DIM == 3 ? bz : 0;
+    if (i >= L.n0 || j >= L.n1) return;
+    const long long c = cell_id(i, j, k, L.n0, L.n1);
+    R sT, sp;
+    offdiag<R, DIM, false>(L, xin, i, j, k, c, sT, sp);
+    const auto z = gs_update<R>(L, c, sT, sp);
+    const auto xo = ldg2(xin + c);
+    xout[c] = mk2<R>(xo.x + omega * (z.x - xo.x), xo.y + omega * (z.y - xo.y));
+}
+
+template <typename R, int DIM, bool P>
+__global__ void __launch_bounds__(kBX * kBY, 8) k_wjac(Level<R> L, const typename Vec<R>::v2 *__restrict__ xin,
+                                                      typename Vec<R>::v2 *__restrict__ xout, R omega) {
+    CMG_TILES(P, (L.n0 + kBX - 1) / kBX, (L.n1 + kBY - 1) / kBY, DIM == 3 ? L.n2 : 1,
+              (wjac_block<R, DIM>(L, xin, xout, omega, bx, by, bz)));
+}
+
+// ---------------------------------------------------------------------------
 // Fused 2D sweep: one launch does a whole red-black sweep (red, then black)
 // from xin to xout.  A CTA owns a TX x TY tile.  It stages xin with a
 // halo of 2 in shared memory, updates the red cells of the tile and of a

@@ -9,11 +9,11 @@
 // hierarchy is device memory) just to monitor a residual.
 //
 // Scratch: the per-block partial sums live in the file-scope array below
-// (1 MiB per GPU that loads the library, held until the process exits).  Host
-// code must not pass the array's name to a kernel (in host code it is only a
-// stand-in symbol); its device address is looked up with
-// cudaGetSymbolAddress once per device, on the first call made while that
-// device is current.
+// (1 MiB on each device, held until the process exits; with lazy module
+// loading the array and the kernels are loaded on the first call on that
+// device).  Host code must not pass the array's name to a kernel (in host
+// code it is only a stand-in symbol); its device address is looked up with
+// cudaGetSymbolAddress by the first call made while that device is current.
 #include <mutex>
 #include <string>
 
@@ -193,12 +193,10 @@ extern "C" mg_status mg_residual_norms_noalloc(const mg_grid *grid, const double
                                                const double *rhs, const double *x, double *out, void *stream) {
     if (!grid || !lambda || !face_alpha || !face_k || !rhs || !x || !out)
         return set_error(MG_ERR_INVALID_ARG, "NULL argument");
+    // the grid rules of mg_create: dimensions, spacing, boundary kinds and values
+    const mg_status gst = check_grid_geom(grid);
+    if (gst) return gst;
     const int dim = grid->dim;
-    if (dim != 2 && dim != 3) return set_error(MG_ERR_INVALID_ARG, "dim must be 2 or 3");
-    if (grid->axisym && dim != 2) return set_error(MG_ERR_INVALID_ARG, "axisymmetric grids are 2D (r, z)");
-    for (int a = 0; a < 3; a++)
-        if (grid->n[a] < 1 || (a >= dim && grid->n[a] != 1)) return set_error(MG_ERR_INVALID_ARG, "bad n[]");
-    if (!(grid->h > 0.0)) return set_error(MG_ERR_INVALID_ARG, "h must be positive");
     for (int a = 0; a < dim; a++)
         if (!face_alpha[a] || !face_k[a]) return set_error(MG_ERR_INVALID_ARG, "NULL face array");
     if (misaligned(rhs, 16) || misaligned(x, 16) || misaligned(lambda, 8) || misaligned(out, 8))

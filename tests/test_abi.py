@@ -131,3 +131,23 @@ def test_momentum_and_side_steps_validate_on_the_host(lib):
         assert lib.mg_energy_async(C.byref(g), ph, dt, None, None, None, None, pa, None, None, None, None,
                                    None) == B.MG_ERR_INVALID_ARG
     assert "dt" in B.last_error()
+
+
+@pytest.mark.parametrize("bad", [
+    dict(bc=((7, 0), (0, 0), (0, 0))),                           # unknown boundary kind
+    dict(bc=((0, 2), (0, 0), (0, 0))),                           # the axis on the high side
+    dict(axisym=1, r0=0.1, bc=((2, 0), (0, 0), (0, 0))),         # the axis where r0 != 0
+    dict(axisym=1, r0=float("nan")),
+    dict(h=float("inf")),
+])
+def test_noalloc_checks_grids_like_mg_create(lib, bad):
+    """The allocation-free norm applies mg_create's grid rules: a bad grid gets
+    the same status from both, before any device work (dummy host pointers)."""
+    from paper_2206_11294_gb300 import binding as B
+    g = _grid(**bad)
+    st_create, _ = _size(lib, g)
+    dummy = (C.c_double * 8)()
+    p = C.cast(dummy, C.c_void_p)
+    pa = (C.c_void_p * 3)(p, p, p)
+    st = lib.mg_residual_norms_noalloc(C.byref(g), p, pa, pa, p, p, p, None)
+    assert st_create == st == B.MG_ERR_INVALID_ARG, (st_create, st, B.last_error())

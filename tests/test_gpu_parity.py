@@ -145,6 +145,35 @@ def test_converged_fp64_same_cycles_as_oracle(torch_cuda, orc, name):
     s.close()
 
 
+def _background_free(orc, p):
+    """The problem restated for its deviation from the initial guess: x0 = 0,
+    homogeneous Dirichlet values, and b the residual of the original initial
+    guess (evaluated by the oracle).  Its solution is the original solution
+    minus the background, so no 1e5 Pa offset enters the rounding."""
+    import dataclasses
+    b = p.b - orc.apply_paper(p.grid.as_dict(), p.lam, p.fa, p.fk, p.x0)
+    g = dataclasses.replace(p.grid, bcT=((0.0, 0.0),) * 3, bcp=((0.0, 0.0),) * 3)
+    return dataclasses.replace(p, grid=g, b=b, x0=np.zeros_like(p.x0))
+
+
+@pytest.mark.parametrize("name", [n for n in CASES if n.startswith("stiff")])
+@pytest.mark.parametrize("cycles", [1, 4])
+def test_fixed_cycles_fp64_stiff_background_free(torch_cuda, orc, name, cycles):
+    """Stiff regime with the background removed: where the coarse levels carry
+    the convergence, the FP64 path matches the oracle after the same number of
+    cycles to 1e-12, as in the literal regime.  (With the background, each
+    side's rounding of terms of size sum_f G_f |p| ~ 1e13 bounds the agreement;
+    without it, the same rounding is relative to the deviation itself.)"""
+    p = _background_free(orc, CASES[name][0])
+    s = _solver(p, rtol=0.0, max_cycles=cycles)
+    x = p.x0.copy()
+    st = s.solve(p.b, x)
+    ref, cyc, _ = orc.mg_solve(p.grid.as_dict(), p.lam, p.fa, p.fk, p.b, p.x0, max_cycles=cycles, rtol=0.0)
+    assert st["cycles"] == cycles == cyc
+    assert rel_dev(x, ref, p.x0) <= 1e-12
+    s.close()
+
+
 @pytest.mark.parametrize("cycle", ["W", "F"])
 @pytest.mark.parametrize("name", ["literal_2d_ragged_walls", "stiff_axi_axis", "literal_3d_wall_dirichlet",
                                   "stiff_3d_walls_odd"])
@@ -343,23 +372,38 @@ def test_full_size_2d_vs_oracle(torch_cuda, orc, name):
     s.close()
 
 
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-9), ("mixed", 1e-9)])
-def test_full_size_3d_sampled_residual(torch_cuda, orc, precision, tol):
-    """256^3 bubble near a wall: the oracle evaluates the residual of the GPU
-    solution at sampled cells (too large for a full oracle solve); the
-    residual must be tiny against the right-hand side's scale there."""
+@pytest.fixture(scope="module")
+def wall3d_oracle(orc):
+    """The 256^3 bubble near a wall (Dirichlet on five faces, a wall at z = 0)
+    and the oracle's solve of it to 1e-10 (about 20 s on one host core)."""
     p = _full_case("wall3d")
-    s = _solver(p, precision=precision, rtol=1e-10, max_cycles=50)
+    ref, cyc, hist = orc.mg_solve(p.grid.as_dict(), p.lam, p.fa, p.fk, p.b, p.x0, max_cycles=50, rtol=1e-10)
+    return p, ref, cyc, hist
+
+
+def test_full_size_3d_fp64_vs_oracle(torch_cuda, wall3d_oracle):
+    """256^3, FP64, in the benchmark's launch configuration: the oracle's cycle
+    count and the whole field to 1e-12."""
+    p, ref, cyc, hist = wall3d_oracle
+    s = _solver(p, rtol=1e-10, max_cycles=50)
     x = p.x0.copy()
     st = s.solve(p.b, x)
-    rng = np.random.default_rng(0)
-    ids = rng.choice(p.grid.N, 4000, replace=False)
-    Lx = orc.apply_rows(p.grid.as_dict(), p.lam, p.fa, p.fk, x, ids)
-    Lx0 = orc.apply_rows(p.grid.as_dict(), p.lam, p.fa, p.fk, p.x0, ids)
-    r = p.b[ids] - Lx
-    r0 = p.b[ids] - Lx0
-    for f in range(2):
-        assert np.linalg.norm(r[:, f]) <= tol * np.linalg.norm(r0[:, f]) * 10, (f, st)
+    assert st["cycles"] == cyc
+    assert np.allclose(st["r0"], hist[0], rtol=1e-12)
+    assert rel_dev(x, ref, p.x0) <= 1e-12
+    s.close()
+
+
+def test_full_size_3d_mixed_vs_oracle(torch_cuda, wall3d_oracle):
+    """256^3, mixed precision stopped at the same 1e-10 reduction: the whole
+    field against the FP64 oracle's solution to 1e-8."""
+    p, ref, cyc, hist = wall3d_oracle
+    s = _solver(p, precision="mixed", rtol=1e-10, max_cycles=50)
+    x = p.x0.copy()
+    st = s.solve(p.b, x)
+    assert st["status"] == "MG_OK"
+    assert max(st["rfinal"][f] / st["r0"][f] for f in range(2)) <= 1e-10
+    assert rel_dev(x, ref, p.x0) <= 1e-8
     s.close()
 
 

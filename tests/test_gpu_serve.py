@@ -1,7 +1,14 @@
 """Serving loop on the GPU: requests of different sizes (2D and 3D, literal
 and stiff) arrive while others run; each result must be the one a lone
 mg_solve gives (same cycles, values within 1e-13 relative: the batch and the
-single path run the same device code), and the HBM budget must hold."""
+single path run the same device code), and the HBM budget must hold.
+
+Every request shape is also checked against the FP64 CPU oracle solving the
+same system with the same stopping rule (1e-10 reduction of both per-field
+norms): FP64 results with the oracle's cycle count, to 1e-12 in the literal
+regime and 1e-9 in the stiff one (whose 1e5 Pa background bounds the
+agreement of any two FP64 implementations, as in the parity tests); mixed
+precision to 1e-8."""
 import numpy as np
 import pytest
 
@@ -28,14 +35,24 @@ def _pool():
     return out
 
 
+@pytest.fixture(scope="module")
+def pool_oracle(orc):
+    pool = _pool()
+    ref = {}
+    for p in pool:
+        x, cyc, _ = orc.mg_solve(p.grid.as_dict(), p.lam, p.fa, p.fk, p.b, p.x0, max_cycles=60, rtol=1e-10)
+        ref[p.name] = (x, cyc)
+    return pool, ref
+
+
 @pytest.mark.parametrize("precision,tune", [("mixed", False), ("fp64", False), ("mixed", True)])
-def test_served_results_equal_solo(precision, tune):
+def test_served_results_equal_solo(precision, tune, pool_oracle):
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     from paper_2206_11294_gb300.binding import Solver
     from paper_2206_11294_gb300.serve import Engine, Server
-    pool = _pool()
+    pool, oref = pool_oracle
     solo = {}
     for p in pool:
         s = Solver(p.grid, precision=precision, rtol=1e-10, max_cycles=60)
@@ -56,6 +73,12 @@ def test_served_results_equal_solo(precision, tune):
         xr, sr = solo[p.name]
         assert st["cycles"] == sr["cycles"], p.name
         assert rel_dev(x, xr, p.x0) <= 1e-13, p.name
+        xo, co = oref[p.name]
+        if precision == "fp64":
+            assert st["cycles"] == co, p.name
+            assert rel_dev(x, xo, p.x0) <= (1e-9 if p.name.startswith("stiff") else 1e-12), p.name
+        else:
+            assert rel_dev(x, xo, p.x0) <= 1e-8, p.name
     stats = srv.stats()
     srv.close()
     assert stats["requests"] == 30

@@ -5,7 +5,10 @@ owned by another allocator, or their loop must not call cudaMalloc/cudaFree).
 Checked through the C ABI against the handle-based mg_residual_norms on the
 same device arrays, on two calls in a row (the second with a different state,
 so a stale partial sum from the first call would show), at the tolerance the
-other norm tests use (1e-12 relative).  This file is collected last.
+other norm tests use (1e-12 relative), and against the CPU oracle's norms.
+After a first call (which sets the scratch up), a call must leave the device's
+free memory and torch's allocated bytes unchanged: it allocates nothing.
+This file is collected last.
 """
 import numpy as np
 import pytest
@@ -32,7 +35,7 @@ def _problems():
 
 
 @pytest.mark.parametrize("q", [0, 1, 2])
-def test_noalloc_norms_match_handle_norms_twice(q):
+def test_noalloc_norms_match_handle_norms_twice(q, orc):
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
@@ -51,6 +54,15 @@ def test_noalloc_norms_match_handle_norms_twice(q):
         B.residual_norms_noalloc(p.grid, lam, fa, fk, b, xd, out)
         got = out.cpu().numpy()
         assert np.allclose(got, ref, rtol=1e-12, atol=0), (got, ref)
+        oref = orc.residual_norms(p.grid.as_dict(), p.lam, p.fa, p.fk, p.b, x)
+        assert np.allclose(got, oref, rtol=1e-12, atol=0), (got, oref)
+    # the entry point's reason to exist: a call allocates no device memory
+    torch.cuda.synchronize()
+    free0, alloc0 = torch.cuda.mem_get_info()[0], torch.cuda.memory_allocated()
+    B.residual_norms_noalloc(p.grid, lam, fa, fk, b, xd, out)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert torch.cuda.memory_allocated() == alloc0
     s.close()
 
 
