@@ -96,14 +96,21 @@ def test_apply(torch_cuda, orc, name):
     s.close()
 
 
+@pytest.mark.parametrize("smoother", ["rbgs", "wjac"])
 @pytest.mark.parametrize("name", list(CASES))
 @pytest.mark.parametrize("sweeps", [1, 3])
-def test_smooth(torch_cuda, orc, name, sweeps):
+def test_smooth(torch_cuda, orc, name, sweeps, smoother):
+    """One and three sweeps of either smoother: red-black block Gauss-Seidel,
+    or weighted block Jacobi (omega 0.8; three sweeps end in the ping-pong
+    partner and are copied back)."""
     p, _ = CASES[name]
-    s = _solver(p)
+    s = _solver(p, smoother=smoother, omega=0.8)
     x = p.x0.copy()
     s.smooth(p.b, x, sweeps)
-    ref = orc.rbgs_sweeps(p.grid.as_dict(), p.lam, p.fa, p.fk, p.b, p.x0, sweeps)
+    if smoother == "rbgs":
+        ref = orc.rbgs_sweeps(p.grid.as_dict(), p.lam, p.fa, p.fk, p.b, p.x0, sweeps)
+    else:
+        ref = orc.wjac_sweeps(p.grid.as_dict(), p.lam, p.fa, p.fk, p.b, p.x0, sweeps, omega=0.8)
     assert rel_dev(x, ref, p.x0) <= 1e-12
     s.close()
 
@@ -118,14 +125,16 @@ def test_residual_norms(torch_cuda, orc, name):
     s.close()
 
 
+@pytest.mark.parametrize("smoother", ["rbgs", "wjac"])
 @pytest.mark.parametrize("name", list(CASES))
 @pytest.mark.parametrize("cycles", [1, 4])
-def test_fixed_cycles_fp64(torch_cuda, orc, name, cycles):
+def test_fixed_cycles_fp64(torch_cuda, orc, name, cycles, smoother):
     p, tol = CASES[name]
-    s = _solver(p, rtol=0.0, max_cycles=cycles)
+    s = _solver(p, rtol=0.0, max_cycles=cycles, smoother=smoother)
     x = p.x0.copy()
     st = s.solve(p.b, x)
-    ref, cyc, _ = orc.mg_solve(p.grid.as_dict(), p.lam, p.fa, p.fk, p.b, p.x0, max_cycles=cycles, rtol=0.0)
+    ref, cyc, _ = orc.mg_solve(p.grid.as_dict(), p.lam, p.fa, p.fk, p.b, p.x0, max_cycles=cycles, rtol=0.0,
+                               smoother=smoother)
     assert st["cycles"] == cycles == cyc
     assert rel_dev(x, ref, p.x0) <= tol
     assert st["levels"] == orc.num_levels(p.grid.as_dict())
@@ -203,6 +212,58 @@ def test_w_f_cycles_vs_oracle(torch_cuda, orc, name, cycle):
     assert st["status"] == "MG_OK"
     assert rel_dev(xm, ref, p.x0) <= 1e-8
     s.close()
+
+
+@pytest.mark.parametrize("name", ["literal_2d_dirichlet_mix", "stiff_axi_axis", "stiff_3d_wall_dirichlet",
+                                  "stiff_2d_ragged_walls"])
+def test_wjac_converged_and_mixed_vs_oracle(torch_cuda, orc, name):
+    """Weighted block Jacobi (omega 0.8 and 0.6): converged FP64 solves take
+    the oracle's cycle count and match its result; mixed precision with the
+    same smoother reaches the converged oracle to 1e-8 (stiff cases run to
+    1e-12, as in test_mixed_precision); background-free stiff cases match after
+    fixed cycles to 1e-12."""
+    p, tol = CASES[name]
+    g = p.grid.as_dict()
+    for omega in (0.8, 0.6):
+        s = _solver(p, rtol=1e-10, max_cycles=120, smoother="wjac", omega=omega)
+        x = p.x0.copy()
+        st = s.solve(p.b, x)
+        ref, cyc, _ = orc.mg_solve(g, p.lam, p.fa, p.fk, p.b, p.x0, max_cycles=120, rtol=1e-10,
+                                   smoother="wjac", omega=omega)
+        assert st["cycles"] == cyc
+        assert rel_dev(x, ref, p.x0) <= tol
+        s.close()
+    rtol = 1e-10 if name.startswith("literal") else 1e-12
+    s = _solver(p, precision="mixed", rtol=rtol, max_cycles=120, smoother="wjac")
+    xm = p.x0.copy()
+    st = s.solve(p.b, xm)
+    conv, _, _ = orc.mg_solve(g, p.lam, p.fa, p.fk, p.b, p.x0, max_cycles=80, rtol=1e-13)
+    assert st["status"] == "MG_OK"
+    assert rel_dev(xm, conv, p.x0) <= 1e-8
+    s.close()
+    if name.startswith("stiff"):
+        q = _background_free(orc, p)
+        s = _solver(q, rtol=0.0, max_cycles=3, smoother="wjac")
+        x = q.x0.copy()
+        s.solve(q.b, x)
+        ref, _, _ = orc.mg_solve(q.grid.as_dict(), q.lam, q.fa, q.fk, q.b, q.x0, max_cycles=3, rtol=0.0,
+                                 smoother="wjac")
+        assert rel_dev(x, ref, q.x0) <= 1e-12
+        s.close()
+
+
+def test_wjac_refused_by_batches_and_validated(torch_cuda):
+    from paper_2206_11294_gb300.binding import Batch, MgError, MG_ERR_INVALID_ARG
+    p, _ = CASES["literal_2d_ragged_walls"]
+    s = _solver(p, smoother="wjac")
+    with pytest.raises(MgError) as e:
+        Batch([s])
+    assert e.value.status == MG_ERR_INVALID_ARG and "Gauss-Seidel" in str(e.value)
+    s.close()
+    for omega in (0.0, 1.5, float("nan")):
+        with pytest.raises(MgError) as e:
+            _solver(p, smoother="wjac", omega=omega)
+        assert e.value.status == MG_ERR_INVALID_ARG
 
 
 def test_w_f_cycles_refused_by_batches(torch_cuda):
