@@ -33,8 +33,10 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "coupled_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "libcoupled_oracle.so")
+_LIB_OMP = os.path.join(_BUILD, "libcoupled_oracle_omp.so")
 _lock = threading.Lock()
 _lib = None
+_lib_omp = None
 
 BC_WALL, BC_DIRICHLET, BC_AXIS = 0, 1, 2
 
@@ -61,6 +63,18 @@ def build(force: bool = False) -> str:
                                "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
+
+
+def build_threaded(force: bool = False) -> str:
+    """The same source with -fopenmp, for timing the oracle on every host core
+    (comparisons use the single-thread build)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB_OMP) or os.path.getmtime(_LIB_OMP) < os.path.getmtime(_SRC):
+        tmp = _LIB_OMP + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-std=c99", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
+                               "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB_OMP)
+    return _LIB_OMP
 
 
 def configure(lib):
@@ -92,6 +106,8 @@ def configure(lib):
     lib.orc_restrict.restype = C.c_int
     lib.orc_prolong_add.argtypes = [gp, dp, dp]
     lib.orc_prolong_add.restype = C.c_int
+    lib.orc_threads.argtypes = []
+    lib.orc_threads.restype = C.c_int
     return lib
 
 
@@ -177,11 +193,25 @@ CYCLES = {"V": 0, "W": 1, "F": 2}
 SMOOTHERS = {"rbgs": 0, "wjac": 1}
 
 
+def _load_threaded():
+    global _lib_omp
+    with _lock:
+        if _lib_omp is None:
+            _lib_omp = configure(C.CDLL(build_threaded()))
+    return _lib_omp
+
+
+def threads(threaded: bool = False) -> int:
+    """Threads the oracle's loops run on (the threaded build: OMP_NUM_THREADS or every core)."""
+    return int((_load_threaded() if threaded else _load()).orc_threads())
+
+
 def mg_solve(g, lam, fa, fk, b, x0, nu1=2, nu2=2, coarse_min=4, max_cycles=50, rtol=1e-10, cycle="V",
-             smoother="rbgs", omega=0.8):
+             smoother="rbgs", omega=0.8, threaded=False):
     """Returns (x, cycles, history) where history[k] = per-field norms before cycle k.  cycle: V, W or F;
-    smoother: rbgs (red-black block Gauss-Seidel) or wjac (weighted block Jacobi with weight omega)."""
-    lib = _load()
+    smoother: rbgs (red-black block Gauss-Seidel) or wjac (weighted block Jacobi with weight omega).
+    threaded: run the OpenMP build (timing only; its norms are summed in another order)."""
+    lib = _load_threaded() if threaded else _load()
     gs = _grid(g)
     lam, b = _c64(lam), _c64(b)
     x = _c64(x0).copy()

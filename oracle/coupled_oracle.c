@@ -11,7 +11,12 @@
  * plainly, in the physical (un-scaled) finite-volume form.
  *
  * Build: gcc -O2 -ffp-contract=off -fPIC -shared (no fast-math, no FMA
- * contraction, single thread), so every operation rounds as written.
+ * contraction, single thread), so every operation rounds as written.  That is
+ * the build every comparison uses.  A second build adds -fopenmp only to time
+ * the oracle on all host cores: the pragmas below split the loops over the
+ * cells of one level (of one colour in a red-black sweep, whose cells do not
+ * read each other), so each cell's arithmetic is unchanged; only the order in
+ * which the stopping norm's squares are summed differs.
  *
  * What is computed
  * ----------------
@@ -62,6 +67,19 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Threads the loops below run on: 1 in the comparison build. */
+int orc_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
 
 enum { BC_WALL = 0, BC_DIRICHLET = 1, BC_AXIS = 2 };
 
@@ -197,6 +215,7 @@ void orc_apply_paper(const orc_grid *g, const double *lam, double *const fa[3],
     long N = ncells(g);
     double (*vT)[2] = homogeneous ? NULL : (double (*)[2])g->bcT;
     double (*vp)[2] = homogeneous ? NULL : (double (*)[2])g->bcp;
+#pragma omp parallel for schedule(static)
     for (long i = 0; i < N; i++) {
         int c[3];
         cell_of(g, i, c);
@@ -313,6 +332,7 @@ static void solve2(const double D[4], const double s[2], double z[2])
 /* r = rhs - L(u) on a level (homogeneous boundary values). */
 static void level_residual(level *L)
 {
+#pragma omp parallel for schedule(static)
     for (long i = 0; i < L->N; i++) {
         int c[3];
         cell_of(&L->g, i, c);
@@ -329,6 +349,7 @@ static void level_residual(level *L)
 static void rbgs_sweep(level *L, double *const bcT2, double *const bcp2)
 {
     for (int colour = 0; colour < 2; colour++) {
+#pragma omp parallel for schedule(static)
         for (long i = 0; i < L->N; i++) {
             int c[3];
             cell_of(&L->g, i, c);
@@ -354,6 +375,7 @@ static int wjac_sweep(level *L, double *const bcT2, double *const bcp2, double o
 {
     double *z = malloc(sizeof(double) * 2 * L->N);
     if (!z) return -2;
+#pragma omp parallel for schedule(static)
     for (long i = 0; i < L->N; i++) {
         int c[3];
         cell_of(&L->g, i, c);
@@ -364,6 +386,7 @@ static int wjac_sweep(level *L, double *const bcT2, double *const bcp2, double o
         s[1] = L->rhs[2 * i + 1] - (e[1] - (D[2] * L->u[2 * i] + D[3] * L->u[2 * i + 1]));
         solve2(D, s, z + 2 * i);
     }
+#pragma omp parallel for schedule(static)
     for (long i = 0; i < 2 * L->N; i++) L->u[i] = L->u[i] + omega * (z[i] - L->u[i]);
     free(z);
     return 0;
@@ -431,6 +454,7 @@ static int coarsen(const level *F, level *C)
     if (alloc_level(C, &g)) return -2;
 
     int nchild = 1 << g.dim;
+#pragma omp parallel for schedule(static)
     for (long I = 0; I < C->N; I++) {
         int cc[3];
         cell_of(&C->g, I, cc);
@@ -450,6 +474,7 @@ static int coarsen(const level *F, level *C)
         long m = nfaces(&C->g, a);
         int dims[3] = {C->g.n[0], C->g.n[1], C->g.n[2]};
         dims[a] += 1;
+#pragma omp parallel for schedule(static)
         for (long id = 0; id < m; id++) {
             int Fp[3] = {(int)(id % dims[0]), (int)((id / dims[0]) % dims[1]),
                          (int)(id / ((long)dims[0] * dims[1]))};
@@ -488,6 +513,7 @@ static int coarsen(const level *F, level *C)
 static void restrict_residual(const level *F, level *C)
 {
     int nchild = 1 << C->g.dim;
+#pragma omp parallel for schedule(static)
     for (long I = 0; I < C->N; I++) {
         int cc[3];
         cell_of(&C->g, I, cc);
@@ -512,6 +538,7 @@ static void restrict_residual(const level *F, level *C)
 static void prolong_add(const level *C, level *F)
 {
     int dim = F->g.dim;
+#pragma omp parallel for schedule(static)
     for (long i = 0; i < F->N; i++) {
         int c[3];
         cell_of(&F->g, i, c);
@@ -617,6 +644,7 @@ static void fill_level0(level *L, const double *lam, double *const fa[3], double
 static void scaled_norms(const level *L0, const double *res, double out[2])
 {
     double s0 = 0.0, s1 = 0.0;
+#pragma omp parallel for schedule(static) reduction(+ : s0, s1)
     for (long i = 0; i < L0->N; i++) {
         int c[3];
         cell_of(&L0->g, i, c);
@@ -680,6 +708,7 @@ int orc_mg_solve(const orc_grid *g, const double *lam, double *const fa[3], doub
     for (int k = 0;; k++) {
         /* step 1: res = b - L(x) */
         orc_apply_paper(g, lam, fa, fk, x, res, 0);
+#pragma omp parallel for schedule(static)
         for (long i = 0; i < 2 * N; i++) res[i] = b[i] - res[i];
         double nk[2];
         scaled_norms(&Ls[0], res, nk);
@@ -698,6 +727,7 @@ int orc_mg_solve(const orc_grid *g, const double *lam, double *const fa[3], doub
         rc = mgcycle(Ls, 0, nlev, nu1, nu2, cycle_type, &sm);
         if (rc) goto done;
         /* step 4: a += da */
+#pragma omp parallel for schedule(static)
         for (long i = 0; i < 2 * N; i++) x[i] += Ls[0].u[i];
         cycles = k + 1;
     }
