@@ -12,9 +12,16 @@ step, per second of device time), plus solves per second.
 
 Arms:
   default            the CUDA library through its C ABI (inputs resident in HBM);
-                     `e2e` repeats the step from host buffers (copies timed).
-  --impl reference   the FP64 CPU oracle on the host cores, a bounded sample
-                     of the same workload per step (one V-cycle per problem).
+                     `e2e` repeats the step through the library's host-buffer
+                     path (mg_set_coeffs / mg_solve with on_device = 0: every
+                     copy inside the timed region).  With one GPU the same run
+                     adds `sub_results`: the workload in mixed precision, its
+                     stiff variant at the paper's bubble scale (cycles per solve,
+                     convergence factor), the 256-problem batch (batched and
+                     looped, FP64 and mixed) and one serving rate (p50 / p99).
+  --impl reference   the FP64 CPU oracle on the host cores (OpenMP over
+                     same-colour cells, every core), a bounded sample of the
+                     same workload per step (one V-cycle per problem).
 
 Multi-GPU (torchrun): replicas only.  Each rank solves its own copy of the
 workload; value = units of all ranks / max-over-ranks time (weak scaling).
@@ -56,8 +63,20 @@ SWEEP_BYTES_PER_CELL = {("fp64", 2): 112.0, ("fp64", 3): 128.0, ("mixed", 2): 56
 # x = bt - W (sT, sp) as 4 FMAs
 SWEEP_FP64_INST_PER_CELL = {2: 12.0, 3: 16.0}
 # GB300 FP64 pipe: 1.25 TFLOP/s nominal = 2 FP64 FMA per clock per SM
-# (1.25e12 / (2 * 152 * 2.07e9) = 1.99); 152 SMs at 2.07 GHz
+# (1.25e12 / (2 * 152 * 2.07e9) = 1.99); 152 SMs at 2.07 GHz.  Used only when
+# the measurement below fails; the run measures the rate with the library's
+# register-FMA kernel (mg_fp64_fma_rate).
 FP64_INST_PEAK_G = 152 * 2 * 2.07
+
+
+def fp64_peak():
+    """(G FP64 instructions/s, source): measured on this device in this run."""
+    try:
+        from paper_2206_11294_gb300 import binding as B
+        return B.fp64_fma_rate(10), "measured in this run: independent register FMA chains (mg_fp64_fma_rate), " \
+                                    "fastest of 10 launches"
+    except Exception as e:        # noqa: BLE001
+        return FP64_INST_PEAK_G, f"derived (measurement failed: {e}): 152 SMs x 2 FP64 inst/clk/SM x 2.07 GHz"
 
 
 def env_int(k, d):
@@ -235,6 +254,7 @@ def run_ours(args, rank, world):
     # roofline of the dominant kernel, from its live event timings
     c0 = counters[0]
     peak, peak_kind = measured_peak()
+    fpeak, fpeak_src = fp64_peak()
     dim0 = probs[0].grid.dim
     sweeps_per_launch = c0["smooth_sweeps"] / max(1, c0["smooth_launches"])
     per_launch = SWEEP_BYTES_PER_CELL[(args.precision, dim0)] * c0["smooth_cells"] * sweeps_per_launch
@@ -258,9 +278,9 @@ def run_ours(args, rank, world):
     if args.precision == "fp64":
         inst = SWEEP_FP64_INST_PER_CELL[dim0] * c0["smooth_cells"] * sweeps_per_launch
         ach_i = inst / avg_s / 1e9 if avg_s > 0 else None
-        roofline = {"bound": "alu", "kernel": kernel, "achieved": ach_i, "peak": FP64_INST_PEAK_G,
-                    "unit": "G FP64 inst/s", "frac": (ach_i / FP64_INST_PEAK_G) if ach_i else None,
-                    "peak_source": "derived: 152 SMs x 2 FP64 inst/clk/SM x 2.07 GHz (1.25 TFLOP/s FP64 nominal)",
+        roofline = {"bound": "alu", "kernel": kernel, "achieved": ach_i, "peak": fpeak,
+                    "unit": "G FP64 inst/s", "frac": (ach_i / fpeak) if ach_i else None,
+                    "peak_source": fpeak_src,
                     "algorithmic_fp64_inst_per_launch": inst, "avg_launch_us": avg_s * 1e6,
                     "launches_timed": c0["smooth_launches"], "traffic": traffic, "traffic_ncu": traffic_note,
                     "hbm": hbm}
@@ -268,58 +288,32 @@ def run_ours(args, rank, world):
         roofline = hbm
     cycles = [st["cycles"] for st in stats[: len(probs)]]
 
-    # end to end through the C ABI from host buffers (copies inside the timed region)
+    # end to end through the library's host-buffer path: mg_set_coeffs and
+    # mg_solve with on_device = 0 take pinned host arrays and copy them in
+    # inside the call, and mg_solve copies the result back; every copy is in
+    # the timed region.  Each step starts from its own host copy of the
+    # initial guess (prepared before timing), since the solve overwrites it.
     e2e = None
     if not args.no_e2e:
-        # every step copies lambda, the face arrays, rhs and x0 of every problem
-        # from pinned host memory and reads x back into pinned host memory.  The
-        # copies run on their own streams into two sets of device buffers: the
-        # inputs of step k+1 are copied while step k sets up and solves, and a
-        # result leaves the device while the next problem solves.
-        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
-        host = [dict(lam=pin(p.lam), fa=[pin(f) for f in p.fa], fk=[pin(f) for f in p.fk], b=pin(p.b),
-                     x0=pin(p.x0), xout=pin(p.x0)) for p in probs]
-        dv = lambda t: torch.empty_like(t, device=f"cuda:{dev}")
-        sets = [[dict(lam=dv(h["lam"]), fa=[dv(f) for f in h["fa"]], fk=[dv(f) for f in h["fk"]], b=dv(h["b"]),
-                      x=dv(h["x0"])) for h in host] for _ in range(2)]
-        cin, cout = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
-
-        def copy_in(bufs):
-            """Queues one step's input copies on the copy stream; returns an event per problem."""
-            ready = []
-            cin.wait_stream(cout)              # results of this buffer set's last use have left
-            with torch.cuda.stream(cin):
-                for hd, db in zip(host, bufs):
-                    db["lam"].copy_(hd["lam"], non_blocking=True)
-                    for a, b in zip(db["fa"] + db["fk"], hd["fa"] + hd["fk"]):
-                        a.copy_(b, non_blocking=True)
-                    db["b"].copy_(hd["b"], non_blocking=True)
-                    db["x"].copy_(hd["x0"], non_blocking=True)
-                    ev = torch.cuda.Event()
-                    ev.record(cin)
-                    ready.append(ev)
-            return ready
-
         for s, d in zip(solvers, dev_in):
             s.set_timing(False)
             d["x"].copy_(d["x0"])
             s.solve(d["b"], d["x"])            # graphs re-captured without event nodes, untimed
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+        host = [dict(lam=pin(p.lam), fa=[pin(f) for f in p.fa], fk=[pin(f) for f in p.fk], b=pin(p.b))
+                for p in probs]
+        xs = [[pin(p.x0) for p in probs] for _ in range(args.steps)]
+        for p, s, hd in zip(probs, solvers, host):     # untimed: the set-up graph of the staging inputs
+            s.set_coeffs(hd["lam"], hd["fa"], hd["fk"])
+            s.solve(hd["b"], pin(p.x0))
         torch.cuda.synchronize()
         e_units = 0.0
         w0 = time.perf_counter()
-        ready = copy_in(sets[0])
         for k in range(args.steps):
-            bufs = sets[k % 2]
-            nxt = copy_in(sets[(k + 1) % 2]) if k + 1 < args.steps else None
-            for p, s, hd, db, ev in zip(probs, solvers, host, bufs, ready):
-                stream.wait_event(ev)
-                s.set_coeffs(db["lam"], db["fa"], db["fk"])
-                st = s.solve(db["b"], db["x"])
+            for p, s, hd, xh in zip(probs, solvers, host, xs[k]):
+                s.set_coeffs(hd["lam"], hd["fa"], hd["fk"])
+                st = s.solve(hd["b"], xh)
                 e_units += p.grid.N * st["cycles"] / 1e6
-                cout.wait_stream(stream)
-                with torch.cuda.stream(cout):
-                    hd["xout"].copy_(db["x"], non_blocking=True)
-            ready = nxt
         torch.cuda.synchronize()
         e_wall = time.perf_counter() - w0
         tt = torch.tensor([e_wall], dtype=torch.float64, device=f"cuda:{dev}")
@@ -329,12 +323,18 @@ def run_ours(args, rank, world):
         d2h = sum(16 * p.grid.N for p in probs)
         e2e = {"value": e_units * world / float(tt.item()), "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "seconds": float(tt.item()),
-               "copies": "pinned host <-> device on two copy streams into two buffer sets: a step's inputs arrive "
-                         "while the previous step solves, results leave while the next problem solves"}
+               "copies": "through the C ABI with on_device = 0: pinned host lambda, faces, rhs and x in, x out, "
+                         "inside mg_set_coeffs / mg_solve (synchronous calls, no overlap between steps)",
+               "check": bool(all(np.array_equal(xs[-1][q].numpy(), dev_in[q]["x"].cpu().numpy())
+                                 for q in range(len(probs))))}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(probs)
+
+    subs = None
+    if rank == 0 and world == 1 and not args.no_sub:
+        subs = sub_results(args, dev, stream, flush, fp64_result=[d["x"].cpu().numpy() for d in dev_in])
 
     if rank != 0:
         return None
@@ -353,6 +353,7 @@ def run_ours(args, rank, world):
         "roofline": roofline,
         "cpu_baseline": cpu,
         "e2e": e2e,
+        "sub_results": subs,
         "gpu_launches": int(sum(c["launches"] for c in counters)),
         "clocks": clk,
         "wall_s": wall,
@@ -360,11 +361,105 @@ def run_ours(args, rank, world):
     return out
 
 
+# ----------------------------------------------------------------- sub-results
+def time_arm(probs, precision, steps, warmup, dev, stream, flush, tune=True, tune_reps=5, max_cycles=50):
+    """Set-up + solve to 1e-10 of every problem per step, inputs resident in
+    HBM, L2 flushed between steps, device events around each step.  Returns
+    the figures and the final solutions."""
+    import numpy as np
+    import torch
+    from paper_2206_11294_gb300.binding import Solver
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda(dev)
+    solvers, din = [], []
+    for p in probs:
+        s = Solver(p.grid, precision=precision, rtol=1e-10, max_cycles=max_cycles, device=dev, stream=stream)
+        d = dict(lam=T(p.lam), fa=[T(f) for f in p.fa], fk=[T(f) for f in p.fk], b=T(p.b), x0=T(p.x0), x=T(p.x0))
+        s.set_coeffs(d["lam"], d["fa"], d["fk"])
+        if tune:
+            s.autotune(tune_reps)
+        solvers.append(s)
+        din.append(d)
+    stats = []
+
+    def step(out):
+        for s, d in zip(solvers, din):
+            d["x"].copy_(d["x0"])
+            s.set_coeffs(d["lam"], d["fa"], d["fk"])
+            out.append(s.solve(d["b"], d["x"], allow_not_converged=True))
+
+    for _ in range(warmup):
+        step([])
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for k in range(steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        step(stats)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    secs = sum(a.elapsed_time(b) for a, b in ev) / 1e3
+    units = sum(p.grid.N * st["cycles"] for p, st in zip(probs * steps, stats)) / 1e6
+    first = stats[: len(probs)]
+    out = {"mcell_vcycles_per_s": units / secs, "solves_per_s": len(stats) / secs, "ms_per_step": secs * 1e3 / steps,
+           "cycles_per_solve": [st["cycles"] for st in first], "outer_steps": [st["outer"] for st in first],
+           "status": [st["status"] for st in first],
+           "convergence_factor": [[(st["rfinal"][f] / st["r0"][f]) ** (1.0 / max(1, st["cycles"]))
+                                   if st["r0"][f] > 0 else 0.0 for f in range(2)] for st in first]}
+    xs = [d["x"].cpu().numpy() for d in din]
+    for s in solvers:
+        s.close()
+    return out, xs
+
+
+def rel_dev(x, ref, x0):
+    import numpy as np
+    return max(float(np.linalg.norm(x[:, f] - ref[:, f]) / max(np.linalg.norm(ref[:, f] - x0[:, f]), 1e-300))
+               for f in range(2))
+
+
+def sub_results(args, dev, stream, flush, fp64_result):
+    """Figures beside the headline in the same run (one GPU): mixed precision
+    on the headline workload (and its distance to the FP64 result), the stiff
+    variant at the paper's bubble scale in FP64 and mixed, the 256-problem
+    batch in four arms, and one serving rate."""
+    from paper_2206_11294_gb300 import inputs as I
+    out = {}
+    t0 = time.perf_counter()
+    probs = workload_problems()
+    mixed, xm = time_arm(probs, "mixed", args.steps, args.warmup, dev, stream, flush, tune=not args.no_tune,
+                         tune_reps=args.tune_reps)
+    mixed["vs_fp64_rel_l2_of_deviation"] = max(rel_dev(a, b, p.x0) for a, b, p in zip(xm, fp64_result, probs))
+    mixed["workload"] = "bubbles16_1024x1024 + axi_512x1024, mixed precision (FP32 cycles, FP64 residual and update)"
+    out["mixed"] = mixed
+    stiff = {"workload": "the same two geometries at the paper's bubble scale (domain 6.4 mm = 64 R0 with "
+                         "R0 = 0.1 mm, dt = 1e-5): Laplacian-dominated p-row, density ratio 1000",
+             "max_cycles": 200}
+    sp = [I.stiff(I.bubbles_1024), I.stiff(I.bubble_axi)]
+    for prec in ("fp64", "mixed"):
+        stiff[prec], _ = time_arm(sp, prec, max(2, args.steps // 4), 1, dev, stream, flush, tune=not args.no_tune,
+                                  tune_reps=args.tune_reps, max_cycles=200)
+    out["stiff"] = stiff
+    if not args.no_batch:
+        bargs = argparse.Namespace(**vars(args))
+        bargs.steps, bargs.warmup = args.batch_steps, 1
+        out["batch"] = run_batch(bargs, modes=("batched_mixed", "batched_fp64", "loop_fp64", "loop_mixed"))
+    if not args.no_serve:
+        sargs = argparse.Namespace(**vars(args))
+        sargs.serve_rates = [args.sub_serve_rate]
+        sargs.serve_seconds = args.sub_serve_seconds
+        out["serve"] = run_serve(sargs)
+    out["seconds"] = time.perf_counter() - t0
+    return out
+
+
 # ----------------------------------------------------------------- other workloads
-def run_batch(args):
-    """256 independent 2D problems (sizes log-uniform 64..1024, multiples of 32,
-    1-8 bubbles, density ratio 1000): mixed precision through one mg_batch per
-    step versus looping the plain FP64 solver over them, both to 1e-10."""
+def run_batch(args, modes=("batched_mixed", "loop_fp64")):
+    """256 independent 2D problems (sizes log-uniform 64..1024, multiples of 64,
+    1-8 bubbles, density ratio 1000), each step set-up + solve to 1e-10 of all
+    of them, in the given arms: batched_* through one mg_batch per step,
+    loop_* looping the single-problem solver; *_mixed / *_fp64 the precision.
+    batched_mixed against loop_fp64 is the headline speed-up; the other two
+    arms separate the gain from batching from the gain from precision."""
     import numpy as np
     import torch
     from paper_2206_11294_gb300 import inputs as I
@@ -377,10 +472,10 @@ def run_batch(args):
                 x=T(p.x0)) for p in probs]
     cells = sum(p.grid.N for p in probs)
     out = {"workload": f"batch of {len(probs)} 2D problems, {cells} cells", "metric": "solves/s at 1e-10"}
-    for mode in ("batched_mixed", "loop_fp64"):
-        prec = "mixed" if mode == "batched_mixed" else "fp64"
+    for mode in modes:
+        prec = "mixed" if mode.endswith("mixed") else "fp64"
         solvers = [Solver(p.grid, precision=prec, rtol=1e-10, max_cycles=60, stream=stream) for p in probs]
-        batch = Batch(solvers) if mode == "batched_mixed" else None
+        batch = Batch(solvers) if mode.startswith("batched") else None
         # kernel choices from the library's autotuner (untimed): the batch's own
         # search, or the per-hierarchy table (equal shapes measured once)
         tuned = None
@@ -430,7 +525,12 @@ def run_batch(args):
             batch.close()
         for s in solvers:
             s.close()
-    out["speedup_batched_mixed_vs_loop_fp64"] = out["batched_mixed"]["solves_per_s"] / out["loop_fp64"]["solves_per_s"]
+    sp = lambda a, b: out[a]["solves_per_s"] / out[b]["solves_per_s"] if a in out and b in out else None
+    out["speedup_batched_mixed_vs_loop_fp64"] = sp("batched_mixed", "loop_fp64")
+    out["speedup_batching_fp64"] = sp("batched_fp64", "loop_fp64")
+    out["speedup_batching_mixed"] = sp("batched_mixed", "loop_mixed")
+    out["speedup_mixed_looped"] = sp("loop_mixed", "loop_fp64")
+    out["speedup_mixed_batched"] = sp("batched_mixed", "batched_fp64")
     return out
 
 
@@ -726,20 +826,37 @@ def run_serve(args):
     return out
 
 
-def cpu_baseline(probs):
-    """The oracle as it stands (one thread), one V-cycle per problem with its
-    hierarchy set-up: a bounded sample of the workload."""
+def _oracle_cycle_sample(probs, threaded):
+    """One oracle V-cycle (with its hierarchy set-up and the residuals around
+    it) on each problem: (Mcell-V-cycles, seconds)."""
     import oracle
-    oracle.build()
     units = 0.0
     t0 = time.perf_counter()
     for p in probs:
-        x, cyc, _ = oracle.mg_solve(p.grid.as_dict(), p.lam, p.fa, p.fk, p.b, p.x0, max_cycles=1, rtol=0.0)
+        x, cyc, _ = oracle.mg_solve(p.grid.as_dict(), p.lam, p.fa, p.fk, p.b, p.x0, max_cycles=1, rtol=0.0,
+                                    threaded=threaded)
         units += p.grid.N * cyc / 1e6
-    dt = time.perf_counter() - t0
-    return {"value": units / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "1 V-cycle (with hierarchy set-up and residuals) on each of the 2 problems",
-            "seconds": dt}
+    return units, time.perf_counter() - t0
+
+
+def cpu_baseline(probs, seconds: float = 10.0):
+    """The oracle on every host core (OpenMP build), one V-cycle per problem
+    repeated until about `seconds` of CPU time have passed: a bounded sample of
+    the workload.  The single-thread build's figure for one such sample is
+    reported beside it."""
+    import oracle
+    oracle.build()
+    oracle.build_threaded()
+    units = secs = 0.0
+    reps = 0
+    while reps == 0 or secs < seconds:
+        u, t = _oracle_cycle_sample(probs, True)
+        units, secs, reps = units + u, secs + t, reps + 1
+    u1, t1 = _oracle_cycle_sample(probs, False)
+    return {"value": units / secs, "unit": UNIT, "cores": oracle.threads(True), "kind": "oracle",
+            "sample": f"{reps} x (1 V-cycle with hierarchy set-up and residuals on each of the {len(probs)} problems), "
+                      "OpenMP over the cells of each level / colour",
+            "seconds": secs, "single_thread_value": u1 / t1}
 
 
 def run_reference(args, rank, world):
@@ -747,23 +864,21 @@ def run_reference(args, rank, world):
         return None
     probs = workload_problems()
     import oracle
-    oracle.build()
-    for _ in range(args.warmup):
-        pass   # the oracle has no warm-up state; its build is outside the timing
-    units = 0.0
-    t0 = time.perf_counter()
+    oracle.build_threaded()
+    cores = oracle.threads(True)
+    for _ in range(min(args.warmup, 1)):
+        _oracle_cycle_sample(probs[:1], True)       # page in the library and the inputs
+    units = secs = 0.0
     for _ in range(args.steps):
-        for p in probs:
-            x, cyc, _ = oracle.mg_solve(p.grid.as_dict(), p.lam, p.fa, p.fk, p.b, p.x0, max_cycles=1, rtol=0.0)
-            units += p.grid.N * cyc / 1e6
-    dt = time.perf_counter() - t0
-    v = units / dt
+        u, t = _oracle_cycle_sample(probs, True)
+        units, secs = units + u, secs + t
+    v = units / secs
+    sample = f"1 V-cycle (with set-up) on each of the {len(probs)} problems per step, OpenMP on {cores} cores"
     return {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": secs * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded bubble fields)", "impl": "reference",
             "config": {"workload": "bubbles16_1024x1024 + axi_512x1024, one oracle V-cycle each per step"},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": "1 V-cycle (with set-up) on each of the 2 problems per step"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
@@ -776,6 +891,12 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-sub", action="store_true", help="headline only: no mixed / stiff / batch / serve sub-results")
+    ap.add_argument("--no-batch", action="store_true", help="sub-results without the batch")
+    ap.add_argument("--no-serve", action="store_true", help="sub-results without the serving rate")
+    ap.add_argument("--batch-steps", type=int, default=3)
+    ap.add_argument("--sub-serve-rate", type=float, default=100.0)
+    ap.add_argument("--sub-serve-seconds", type=float, default=5.0)
     ap.add_argument("--no-tune", action="store_true", help="library default kernel choices, no autotuning")
     ap.add_argument("--tune-reps", type=int, default=5)
     ap.add_argument("--tuning-table", default=None, help="JSON table of autotuned choices to apply (and extend)")

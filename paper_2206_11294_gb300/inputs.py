@@ -311,9 +311,9 @@ def batch_problems(count: int = 256, seed: int = 5, lo: int = 64, hi: int = 1024
     return out
 
 
-def bubbles_1024(n: int = 1024, seed: int = 2) -> Problem:
-    """2D n x n grid with 16 seeded bubbles, radii uniform in [0.02, 0.08]."""
-    return bubble_2d(n=n, seed=seed, n_bubbles=16, rmin=0.02, rmax=0.08, centred=False,
+def bubbles_1024(n: int = 1024, seed: int = 2, length: float = 1.0, dt: float = 1e-7) -> Problem:
+    """2D n x n grid with 16 seeded bubbles, radii uniform in [0.02, 0.08] of the domain."""
+    return bubble_2d(n=n, seed=seed, n_bubbles=16, rmin=0.02, rmax=0.08, centred=False, length=length, dt=dt,
                      name=f"bubbles16_{n}x{n}")
 
 
