@@ -95,6 +95,12 @@ typedef struct {
                             per sweep (mg_tuning.sweep, tile and tail_level are ignored; persistent applies) and
                             batches take RBGS only. */
     double omega;        /* MG_SMOOTH_WJAC: the weight, 0 < omega <= 1 (default 0.8) */
+    double fp64_jump_ratio; /* MIXED: a finest-level cell whose interior faces' k or 1/rho differ by more than this
+                            ratio (a cell at the bubble interface) has its 2x2 block applied in FP64 inside the
+                            FP32 cycles (the FP64 W and Dinv r of the cell; every other cell stays FP32).
+                            0: off; otherwise >= 1 (default 2: the interface the volume fraction smooths over
+                            about two cells changes the coefficients by up to ~5x per cell there).  Ignored in
+                            FP64. */
 } mg_options;
 
 enum { MG_CYCLE_V = 0, MG_CYCLE_W = 1, MG_CYCLE_F = 2 };
@@ -108,12 +114,14 @@ typedef struct {
     double seconds;      /* wall time of the call */
     int status;          /* mg_status of the solve */
     int levels;          /* multigrid levels of the hierarchy */
+    long long fp64_cells; /* MIXED: finest-level cells whose 2x2 block the FP32 cycles apply in FP64 */
 } mg_stats;
 
 typedef struct mg_handle mg_handle;
 
 /* Fills defaults: V(2,2), FP64, rtol 1e-10, 50 cycles, coarse_min 4, 1 inner cycle, red-black block
- * Gauss-Seidel (omega 0.8 for weighted block Jacobi). */
+ * Gauss-Seidel (omega 0.8 for weighted block Jacobi), FP64 blocks at face-coefficient jumps above 2:1
+ * in mixed precision. */
 MG_API mg_status mg_default_options(mg_options *opt);
 
 /* Device bytes a handle of this grid and these options needs (hierarchy,
@@ -146,6 +154,28 @@ MG_API mg_status mg_set_coeffs(mg_handle *h, const double *lambda, const double 
  * NULL.  Returns MG_OK on convergence, MG_ERR_NOT_CONVERGED (x written)
  * after max_cycles. */
 MG_API mg_status mg_solve(mg_handle *h, const double *rhs, double *x, int on_device, mg_stats *stats);
+
+/* The solve of mg_solve (Sec. 3, the defect-correction loop after Eq. 34),
+ * enqueued on the handle's stream without waiting for it: the stop test runs
+ * on the device, between the cycles of one CUDA graph (a loop node whose
+ * condition a one-thread kernel sets after each cycle's norms), so the host
+ * takes no part until the end.  rhs, x: device pointers (16-byte aligned),
+ * as for mg_solve with on_device = 1; x holds the result once the work has
+ * completed.  The result and statistics equal mg_solve's bit for bit (the
+ * same kernels in the same order).  event: NULL, or a cudaEvent_t recorded on
+ * the stream after the solve, so later work on other streams can wait for the
+ * result on the device.  Arguments are checked before anything is enqueued;
+ * errors found on the device (a singular coarsest matrix, a bounded wait that
+ * gave up) are reported by mg_solve_async_stats.  The first call on a handle
+ * (and the first after mg_set_tuning, mg_autotune or mg_set_timing) captures
+ * the graph.  The caller's rhs must stay valid until the work has completed;
+ * the handle is not thread-safe. */
+MG_API mg_status mg_solve_async(mg_handle *h, const double *rhs, double *x, void *event);
+
+/* Waits for the handle's last mg_solve_async and reports it as mg_solve would:
+ * stats (nullable; seconds = device time of the solve), MG_ERR_NOT_CONVERGED
+ * after max_cycles, MG_ERR_STATE when no asynchronous solve is pending. */
+MG_API mg_status mg_solve_async_stats(mg_handle *h, mg_stats *stats);
 
 /* y = L(x) (Eqs. 27-28 with the grid's Dirichlet values), all pointers on the
  * given side.  A building block for residual checks: res = b - L(x). */

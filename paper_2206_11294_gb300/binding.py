@@ -35,7 +35,7 @@ EXPORTS = ["mg_default_options", "mg_workspace_size", "mg_create", "mg_set_coeff
            "mg_batch_set_tuning", "mg_batch_autotune", "mg_assemble_async", "mg_correct_async",
            "mg_energy_async", "mg_momentum_create", "mg_momentum_set_coeffs", "mg_momentum_apply",
            "mg_momentum_solve", "mg_momentum_destroy", "mg_momentum_rhs_async", "mg_provisional_async",
-           "mg_fp64_fma_rate"]
+           "mg_fp64_fma_rate", "mg_solve_async", "mg_solve_async_stats"]
 
 MG_MAX_LEVELS = 32
 MG_SWEEP_COLOUR, MG_SWEEP_FUSED, MG_SWEEP_ASYNC, MG_SWEEP_COLOUR2 = 1, 2, 3, 4
@@ -60,18 +60,18 @@ class MgGrid(C.Structure):
 class MgOptions(C.Structure):
     _fields_ = [("nu1", C.c_int), ("nu2", C.c_int), ("precision", C.c_int), ("rtol", C.c_double),
                 ("max_cycles", C.c_int), ("coarse_min", C.c_int), ("inner_cycles", C.c_int), ("cycle", C.c_int),
-                ("smoother", C.c_int), ("omega", C.c_double)]
+                ("smoother", C.c_int), ("omega", C.c_double), ("fp64_jump_ratio", C.c_double)]
 
 
 class MgStats(C.Structure):
     _fields_ = [("cycles", C.c_int), ("outer", C.c_int), ("r0", C.c_double * 2),
                 ("rfinal", C.c_double * 2), ("seconds", C.c_double), ("status", C.c_int),
-                ("levels", C.c_int)]
+                ("levels", C.c_int), ("fp64_cells", C.c_longlong)]
 
     def as_dict(self) -> dict:
         return dict(cycles=self.cycles, outer=self.outer, r0=list(self.r0), rfinal=list(self.rfinal),
                     seconds=self.seconds, status=STATUS_NAMES.get(self.status, self.status),
-                    levels=self.levels)
+                    levels=self.levels, fp64_cells=int(self.fp64_cells))
 
 
 class MgTuning(C.Structure):
@@ -202,6 +202,8 @@ def load(path: str = LIB_PATH):
             "mg_momentum_rhs_async": ([C.POINTER(MgGrid), C.c_double, C.c_double, pa3, P, P, P, pa3, P], C.c_int),
             "mg_provisional_async": ([C.POINTER(MgGrid), C.c_double, P, P, pa3, pa3, P], C.c_int),
             "mg_fp64_fma_rate": ([P, C.c_int, dp], C.c_int),
+            "mg_solve_async": ([P, P, P, P], C.c_int),
+            "mg_solve_async_stats": ([P, C.POINTER(MgStats)], C.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -246,7 +248,7 @@ SMOOTHERS = {"rbgs": 0, "wjac": 1}
 
 
 def make_options(precision="fp64", rtol=1e-10, max_cycles=50, nu1=2, nu2=2, coarse_min=4,
-                 inner_cycles=1, cycle="V", smoother="rbgs", omega=0.8) -> MgOptions:
+                 inner_cycles=1, cycle="V", smoother="rbgs", omega=0.8, fp64_jump_ratio=2.0) -> MgOptions:
     o = MgOptions()
     check(load().mg_default_options(C.byref(o)))
     o.precision = MG_MIXED if precision in ("mixed", MG_MIXED) else MG_FP64
@@ -255,6 +257,7 @@ def make_options(precision="fp64", rtol=1e-10, max_cycles=50, nu1=2, nu2=2, coar
     o.cycle = CYCLES[cycle] if isinstance(cycle, str) else int(cycle)
     o.smoother = SMOOTHERS[smoother] if isinstance(smoother, str) else int(smoother)
     o.omega = float(omega)
+    o.fp64_jump_ratio = float(fp64_jump_ratio)
     return o
 
 
@@ -394,13 +397,13 @@ class Solver:
 
     def __init__(self, grid, precision="fp64", rtol=1e-10, max_cycles=50, nu1=2, nu2=2, coarse_min=4,
                  inner_cycles=1, device: Optional[int] = None, stream=None, torch_workspace: bool = True,
-                 cycle="V", smoother="rbgs", omega=0.8):
+                 cycle="V", smoother="rbgs", omega=0.8, fp64_jump_ratio=2.0):
         import torch
         lib = load()
         self._lib = lib
         self.grid = make_grid(grid)
         self.options = make_options(precision, rtol, max_cycles, nu1, nu2, coarse_min, inner_cycles, cycle,
-                                    smoother, omega)
+                                    smoother, omega, fp64_jump_ratio)
         dev = torch.cuda.current_device() if device is None else int(device)
         self.device = dev
         check(lib.mg_set_device(dev))
@@ -469,6 +472,29 @@ class Solver:
         st = MgStats()
         allow = (MG_OK, MG_ERR_NOT_CONVERGED) if allow_not_converged else (MG_OK,)
         check(self._lib.mg_solve(self._h, bp, xp, int(dev), C.byref(st)), allow)
+        return st.as_dict()
+
+    def solve_async(self, b, x, event=None) -> None:
+        """mg_solve_async: b and x contiguous float64 CUDA tensors; the solve is
+        enqueued on the handle's stream and x holds the result once it has run.
+        event: None or a torch.cuda.Event, recorded after the solve (keep b alive
+        until then)."""
+        self._need(b, 2 * self.N, "rhs")
+        self._need(x, 2 * self.N, "x")
+        bp, _ = _ptr(b, True)
+        xp, _ = _ptr(x, True)
+        ev = None
+        if event is not None:
+            if not event.cuda_event:           # torch creates the CUDA event on its first record
+                event.record(self.stream)
+            ev = C.c_void_p(event.cuda_event)
+        check(self._lib.mg_solve_async(self._h, bp, xp, ev))
+
+    def async_stats(self, allow_not_converged: bool = False) -> dict:
+        """mg_solve_async_stats: waits for the last solve_async and returns its stats."""
+        st = MgStats()
+        allow = (MG_OK, MG_ERR_NOT_CONVERGED) if allow_not_converged else (MG_OK,)
+        check(self._lib.mg_solve_async_stats(self._h, C.byref(st)), allow)
         return st.as_dict()
 
     def apply(self, x):

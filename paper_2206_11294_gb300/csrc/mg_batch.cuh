@@ -310,12 +310,20 @@ __global__ void __launch_bounds__(kBatchThreads) kb_prep(const BLevel *__restric
     }
 }
 
+// A problem's flags: err[0] set-up errors, err[2] its finest-level cells marked
+// for FP64 block updates (mixed precision).
 __global__ void kb_zero_err(const BCoarse *__restrict__ co, int count) {
-    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < count; p += gridDim.x * blockDim.x) *co[p].err = 0;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < count; p += gridDim.x * blockDim.x) {
+        co[p].err[0] = 0;
+        co[p].err[2] = 0;
+    }
 }
 
 __global__ void kb_gather_err(const BCoarse *__restrict__ co, int count, int *__restrict__ out) {
-    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < count; p += gridDim.x * blockDim.x) out[p] = *co[p].err;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < count; p += gridDim.x * blockDim.x) {
+        out[p] = co[p].err[0];
+        out[count + p] = co[p].err[2];
+    }
 }
 
 // Results of all problems to the callers' device arrays.
@@ -688,7 +696,7 @@ void b_step(mg_batch *b, cudaStream_t s) {
 bool same_options(const mg_options &a, const mg_options &c) {
     return a.nu1 == c.nu1 && a.nu2 == c.nu2 && a.precision == c.precision && a.rtol == c.rtol &&
            a.max_cycles == c.max_cycles && a.inner_cycles == c.inner_cycles && a.cycle == c.cycle &&
-           a.smoother == c.smoother;
+           a.smoother == c.smoother && a.fp64_jump_ratio == c.fp64_jump_ratio;
 }
 
 void add_blocks(std::vector<int2> &t, int level_index, long long blocks) {
@@ -887,7 +895,7 @@ mg_status mg_batch_create(int count, mg_handle *const *handles, mg_batch **out) 
                  o_tab = take(sizeof(int2) * std::max<size_t>(1, tabs.size())),
                  o_sl = take(sizeof(BSetupLevel) * sl.size()), o_sin = take(sizeof(SetupIn) * count),
                  o_co = take(sizeof(BCoarse) * count), o_io = take(sizeof(BIo) * count),
-                 o_ids = take(sizeof(int) * std::max<size_t>(1, inv_ids.size())), o_err = take(sizeof(int) * count),
+                 o_ids = take(sizeof(int) * std::max<size_t>(1, inv_ids.size())), o_err = take(sizeof(int) * 2 * count),
                  o_big = take(sizeof(int) * std::max<size_t>(1, b->big_coarse.size()));
     cudaError_t e = cudaMalloc(&b->mem, off);
     if (e != cudaSuccess) {
@@ -919,7 +927,7 @@ mg_status mg_batch_create(int count, mg_handle *const *handles, mg_batch **out) 
                                             cudaMemcpyHostToDevice) != cudaSuccess) ||
         cudaMemset(b->st, 0, sizeof(BState) * count) != cudaSuccess ||
         cudaMallocHost(&b->host_io, std::max(sizeof(SetupIn), sizeof(BIo)) * count) != cudaSuccess ||
-        cudaMallocHost(&b->err_h, sizeof(int) * count) != cudaSuccess ||
+        cudaMallocHost(&b->err_h, sizeof(int) * 2 * count) != cudaSuccess ||
         cudaMallocHost(&b->active_h, sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
         mg_batch_destroy(b);
@@ -1044,6 +1052,7 @@ mg_status mg_batch_solve(mg_batch *b, const double *const *rhs, double *const *x
             o.seconds = secs;
             o.status = ok ? MG_OK : MG_ERR_NOT_CONVERGED;
             o.levels = h->nlev;
+            o.fp64_cells = h->jcells;
         }
     }
     if (!all_ok) return fail(MG_ERR_NOT_CONVERGED, "at least one problem did not converge in max_cycles");
@@ -1126,8 +1135,9 @@ mg_status mg_batch_set_coeffs(mg_batch *b, const double *const *lambda, const do
     kb_gather_err<<<(b->count + 255) / 256, 256, 0, s>>>(b->co, b->count, b->err_d);
     b->launches++;
     CK(cudaGetLastError());
-    CK(cudaMemcpyAsync(b->err_h, b->err_d, sizeof(int) * b->count, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(b->err_h, b->err_d, sizeof(int) * 2 * b->count, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    for (int p = 0; p < b->count; p++) b->h[p]->jcells = b->h[p]->L[0].jflag ? b->err_h[b->count + p] : 0;
     for (int p = 0; p < b->count; p++) {
         const int e = b->err_h[p];
         if (e & 1) return fail(MG_ERR_INVALID_COEFF, "problem " + std::to_string(p) + ": non-finite coefficient");

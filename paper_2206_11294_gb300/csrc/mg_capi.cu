@@ -31,7 +31,7 @@ using namespace cmg;
 namespace {
 
 constexpr int kMaxLevels = 32;
-constexpr int kMaxCoarseUnknowns = 1024;
+constexpr int kMaxCoarseUnknowns = 2048;
 constexpr int kSetupGraphs = 4;
 constexpr size_t kAlign = 256;
 constexpr size_t kTailSmemMax = 200 * 1024;   // shared memory a tail CTA may use
@@ -68,6 +68,9 @@ struct LevelBuf {
     int p0;
     fq *D32, *Dinv32, *W32;
     float *l4_32;
+    unsigned char *jflag;   // finest level, mixed: cells whose 2x2 block the FP32 cycles apply in FP64
+    int *jcount;            // their count (device)
+    double jratio;          // the face-coefficient ratio that marks them
 };
 
 }  // namespace
@@ -116,6 +119,7 @@ struct mg_handle {
     cudaEvent_t ev_asm;    // coarsest matrix assembled (main stream)
     cudaEvent_t ev_inv;    // coarsest inverse ready (aux stream); cycle graphs wait on it
     int *errh;             // pinned host copy of err_d
+    long long jcells;      // finest-level cells whose 2x2 block the FP32 cycles apply in FP64 (last set-up)
     int nlev;
     LevelBuf L[kMaxLevels];
     char *arena;
@@ -146,6 +150,15 @@ struct mg_handle {
     bool coeffs_set;
     cudaGraphExec_t g64, g32;   // FP64 cycle+norm; mixed inner cycles+update+residual
     cudaGraphExec_t gcorr;      // fixed FP64 cycles without norms (correction solves of the momentum predictor)
+    cudaGraphExec_t gasync;     // a whole solve with the stop test on the device (mg_solve_async)
+    long long async_kernels_pre;   // its kernels outside the loop, and per loop iteration
+    long long async_kernels_body;
+    cudaStream_t cap2;          // private stream: captures the loop body of gasync
+    AsyncStat *astat_d;         // device: the async solve's norms and cycle count
+    AsyncStat *astat_h;         // pinned host copy, written at the end of the async solve
+    cudaEvent_t ev_a0, ev_a1;   // bracket the last async solve (device time)
+    bool async_pending;         // an async solve was enqueued and its statistics not yet read
+    bool cond_body;             // capturing a conditional body: no event nodes
     long long graph_kernels_corr;
     struct SetupGraph {         // set-up of the levels for the input pointers in key
         cudaGraphExec_t exec;
@@ -188,6 +201,8 @@ mg_status check_grid(const mg_grid *g, const mg_options *o) {
         return fail(MG_ERR_INVALID_ARG, "smoother must be MG_SMOOTH_RBGS or MG_SMOOTH_WJAC");
     if (o->smoother == MG_SMOOTH_WJAC && !(o->omega > 0.0 && o->omega <= 1.0))
         return fail(MG_ERR_INVALID_ARG, "omega must be in (0, 1] for weighted block Jacobi");
+    if (!(o->fp64_jump_ratio == 0.0 || (o->fp64_jump_ratio >= 1.0 && std::isfinite(o->fp64_jump_ratio))))
+        return fail(MG_ERR_INVALID_ARG, "fp64_jump_ratio must be 0 (off) or a finite ratio >= 1");
     int n[3] = {g->n[0], g->n[1], g->n[2]}, lev = 1;
     while (can_coarsen(n, g->dim, o->coarse_min) && lev < kMaxLevels) {
         for (int a = 0; a < g->dim; a++) n[a] /= 2;
@@ -264,6 +279,10 @@ void plan(mg_handle *h, char *base, size_t *bytes) {
             l.W32 = P.take<fq>(l.N);
             l.l4_32 = P.take<float>(l.N);
             l.bt32 = P.take<float2>(l.N);
+            if (h->nlev == 0 && h->opt.fp64_jump_ratio > 0.0) {
+                l.jflag = P.take<unsigned char>(l.N);
+                l.jratio = h->opt.fp64_jump_ratio;
+            }
         }
         h->nlev++;
         if (!can_coarsen(n, g.dim, h->opt.coarse_min) || h->nlev == kMaxLevels) break;
@@ -305,17 +324,20 @@ void plan(mg_handle *h, char *base, size_t *bytes) {
     h->partial = P.take<double2>(h->npartial);
     h->norms_d = P.take<double>(8);
     h->ticket = P.take<unsigned int>(1);
-    h->err_d = P.take<int>(2);            // [0] set-up flags, [1] bounded waits that gave up (per solve)
+    h->err_d = P.take<int>(4);            // [0] set-up flags, [1] bounded waits that gave up (per solve), [2] jump cells
+    if (h->L[0].jflag) h->L[0].jcount = h->err_d + 2;
+    h->astat_d = P.take<AsyncStat>(1);
     *bytes = P.off + kAlign;
 }
 
 template <typename R> Level<R> view(const LevelBuf &l);
 template <> Level<double> view<double>(const LevelBuf &l) {
-    return Level<double>{l.n[0], l.n[1], l.n[2], l.N, l.x, l.b, l.G[0], l.G[1], l.G[2], l.D, l.Dinv, l.l4, l.W, l.bt};
+    return Level<double>{l.n[0], l.n[1], l.n[2], l.N, l.x, l.b, l.G[0], l.G[1], l.G[2], l.D, l.Dinv, l.l4, l.W, l.bt,
+                         l.W, l.bt, l.jflag};
 }
 template <> Level<float> view<float>(const LevelBuf &l) {
     return Level<float>{l.n[0], l.n[1], l.n[2], l.N, l.x32, l.b32, l.G32[0], l.G32[1], l.G32[2], l.D32, l.Dinv32,
-                        l.l4_32, l.W32, l.bt32};
+                        l.l4_32, l.W32, l.bt32, l.W, l.bt, nullptr};
 }
 
 BcFlags bc_flags(const mg_grid &g) {
@@ -425,6 +447,7 @@ template <typename R>
 bool async_ok(const mg_handle *h, int l, int tile) {
     if (h->grid.dim != 2 || async_smem<R>(tile) > kSmemOptInMax) return false;
     if (sizeof(R) == 4 && ((h->L[l].n[0] & 1) || !h->L[l].G32p0)) return false;   // FP32 rows: 8 n0 bytes
+    if (sizeof(R) == 4 && h->L[l].jflag) return false;   // its staged W has no FP64 branch for marked cells
     return true;
 }
 
@@ -672,7 +695,8 @@ void enqueue_vcycle(const mg_handle *h, cudaStream_t s, int l, int type) {
     const LevelBuf &lb = h->L[l];
     if (l == h->tail_lev && tail_runs(h)) {
         // the coarsest inverse is computed on the aux stream after each set-up
-        cudaStreamWaitEvent(s, h->ev_inv, cudaEventWaitExternal);
+        // (a conditional body may hold no event node: the async solve waits first)
+        if (!h->cond_body) cudaStreamWaitEvent(s, h->ev_inv, cudaEventWaitExternal);
         enqueue_tail<R, DIM>(h, s);
         counted(h);
         return;
@@ -680,7 +704,7 @@ void enqueue_vcycle(const mg_handle *h, cudaStream_t s, int l, int type) {
     if (l == h->nlev - 1) {
         const Level<R> v = view<R>(lb);
         // the coarsest inverse is computed on the aux stream after each set-up
-        cudaStreamWaitEvent(s, h->ev_inv, cudaEventWaitExternal);
+        if (!h->cond_body) cudaStreamWaitEvent(s, h->ev_inv, cudaEventWaitExternal);
         const int threads = 256;
         const unsigned blocks = (unsigned)((h->nc * 32LL + threads - 1) / threads);
         k_coarse_matvec<R><<<blocks, threads, 0, s>>>(coarse_inverse<R>(h), reinterpret_cast<const R *>(v.b),
@@ -692,8 +716,8 @@ void enqueue_vcycle(const mg_handle *h, cudaStream_t s, int l, int type) {
     // timing brackets one smoothing pass of the finest level per cycle: the
     // pre-smoothing, or the post-smoothing when there is none (two event nodes
     // per cycle, not four: each costs the step a little)
-    const bool tm_pre = h->timing && l == 0 && h->opt.nu1 > 0;
-    const bool tm_post = h->timing && l == 0 && h->opt.nu1 == 0;
+    const bool tm_pre = h->timing && !h->cond_body && l == 0 && h->opt.nu1 > 0;
+    const bool tm_post = h->timing && !h->cond_body && l == 0 && h->opt.nu1 == 0;
     if (tm_pre) cudaEventRecordWithFlags(h->ev[0], s, cudaEventRecordExternal);
     enqueue_smooth<R, DIM>(h, s, l, h->opt.nu1);
     if (tm_pre) cudaEventRecordWithFlags(h->ev[1], s, cudaEventRecordExternal);
@@ -957,6 +981,9 @@ SetupOut setup_out(const LevelBuf &l, bool mixed) {
         o.G0p = l.G32p0;
         o.p0 = l.p0;
         o.n0 = l.n[0];
+        o.jflag = l.jflag;
+        o.jcount = l.jcount;
+        o.jratio = l.jratio;
     }
     return o;
 }
@@ -979,6 +1006,7 @@ void enqueue_setup_levels(mg_handle *h, cudaStream_t s, const SetupGeom &gm, con
     const bool mixed = h->opt.precision == MG_MIXED;
     const LevelBuf &f = h->L[0];
     cudaMemsetAsync(h->err_d, 0, sizeof(int), s);
+    if (f.jflag) cudaMemsetAsync(h->err_d + 2, 0, sizeof(int), s);
     k_setup_fine<DIM><<<cell_grid(f, DIM, f.n[0]), kBlock, 0, s>>>(gm, in, setup_out(f, mixed), h->err_d);
     counted(h);
     double hl = h->grid.h;
@@ -1110,7 +1138,9 @@ mg_status setup_hierarchy(mg_handle *h, const double *lam, const double *const f
     // flags 1 and 2 come from the level kernels, which precede this copy on
     // the stream (the inverse on the private stream keeps running)
     CK(cudaMemcpyAsync(h->errh, h->err_d, sizeof(int), cudaMemcpyDeviceToHost, s));
+    if (f.jflag) CK(cudaMemcpyAsync(h->errh + 2, h->err_d + 2, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    h->jcells = f.jflag ? h->errh[2] : 0;
     const int err = *h->errh;
     if (err & 1) return fail(MG_ERR_INVALID_COEFF, "non-finite coefficient in lambda or the face arrays");
     if (err & 2) return fail(MG_ERR_INVALID_COEFF, "a local 2x2 block is singular or not finite");
@@ -1219,6 +1249,99 @@ mg_status correction_cycles(mg_handle *h, const double2 *rhs) {
     return MG_OK;
 }
 
+// A whole solve as one graph, for mg_solve_async: the initial norms and a
+// first stop test, then a WHILE node whose body is one iteration of the
+// solve (FP64: a cycle and its norms; mixed: the FP32 cycles, the update and
+// the FP64 residual with its norms) ending in the stop test, then (mixed) x =
+// x0 + delta and the copy of the statistics to pinned host memory.  The same
+// kernels in the same order as mg_solve, so the result is the same bit for
+// bit.  The body holds no event node (graph rules): the caller's stream waits
+// for the coarsest inverse before launching the graph.
+template <int DIM>
+mg_status capture_async(mg_handle *h) {
+    const bool mixed = h->opt.precision == MG_MIXED;
+    cudaGraph_t graph = nullptr;
+    CK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
+    const long long before = h->enq;
+    cudaError_t e = cudaSuccess;
+    cudaGraph_t cg = nullptr;
+    cudaGraphConditionalHandle cond = 0;
+    cudaGraphNode_t node = nullptr;
+    cudaGraph_t body = nullptr;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t ndeps = 0;
+    cudaStreamCaptureStatus cs;
+    if (mixed) enqueue_residual_to32<DIM>(h, h->cap, true);
+    else enqueue_norm<DIM>(h, h->cap, false);
+    long long pre = h->enq - before;
+    e = cudaStreamGetCaptureInfo(h->cap, &cs, nullptr, &cg, nullptr, nullptr, nullptr);
+    // the condition starts at 0 on every launch (the loop runs only if the
+    // first stop test below asks for it); the body's stop test ends the loop
+    // after max_cycles iterations at the latest
+    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&cond, cg, 0, cudaGraphCondAssignDefault);
+    if (e == cudaSuccess) {
+        k_async_stop<<<1, 32, 0, h->cap>>>(h->norms_d, h->astat_d, h->opt.max_cycles, h->opt.rtol, cond, 1);
+        pre++;
+        e = cudaStreamGetCaptureInfo(h->cap, &cs, nullptr, &cg, &deps, nullptr, &ndeps);
+    }
+    if (e == cudaSuccess) {
+        cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};   // the rest zero-initialised
+        np.conditional.handle = cond;
+        np.conditional.type = cudaGraphCondTypeWhile;
+        np.conditional.size = 1;
+        e = cudaGraphAddNode(&node, cg, deps, nullptr, ndeps, &np);
+        if (e == cudaSuccess) body = np.conditional.phGraph_out[0];
+    }
+    if (e == cudaSuccess) e = cudaStreamUpdateCaptureDependencies(h->cap, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+    long long per = 0;
+    if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(h->cap2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        const long long b0 = h->enq;
+        h->cond_body = true;
+        if (mixed) {
+            for (int q = 0; q < h->opt.inner_cycles; q++) enqueue_vcycle<float, DIM>(h, h->cap2, 0, h->opt.cycle);
+            const LevelBuf &f = h->L[0];
+            k_add_correction<<<lin_blocks(f.N), 256, 0, h->cap2>>>(mixed_delta(h), f.x32, f.N);
+            counted(h);
+            enqueue_residual_to32<DIM>(h, h->cap2);
+        } else {
+            enqueue_vcycle<double, DIM>(h, h->cap2, 0, h->opt.cycle);
+            enqueue_norm<DIM>(h, h->cap2, h->opt.nu2 > 0 && red_only_after_sweeps(h));
+        }
+        k_async_stop<<<1, 32, 0, h->cap2>>>(h->norms_d, h->astat_d, h->opt.max_cycles, h->opt.rtol, cond, 0);
+        counted(h);
+        h->cond_body = false;
+        per = h->enq - b0;
+        const cudaError_t le = cudaGetLastError();
+        cudaGraph_t out = nullptr;
+        e = cudaStreamEndCapture(h->cap2, &out);
+        if (e == cudaSuccess && le != cudaSuccess) e = le;
+    }
+    long long post = 0;
+    if (e == cudaSuccess) {
+        if (mixed) {
+            const LevelBuf &f = h->L[0];
+            k_add_pairs<<<lin_blocks(f.N), 256, 0, h->cap>>>(f.x, mixed_delta(h), f.N);
+            post++;
+        }
+        e = cudaMemcpyAsync(h->astat_h, h->astat_d, sizeof(AsyncStat), cudaMemcpyDeviceToHost, h->cap);
+    }
+    h->enq = before;
+    const cudaError_t le = cudaGetLastError();
+    const cudaError_t ee = cudaStreamEndCapture(h->cap, &graph);
+    if (e == cudaSuccess) e = le != cudaSuccess ? le : ee;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&h->gasync, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        h->gasync = nullptr;
+        h->cond_body = false;
+        return fail(MG_ERR_CUDA, std::string("async solve graph: ") + cudaGetErrorString(e));
+    }
+    h->async_kernels_pre = pre + post;
+    h->async_kernels_body = per;
+    return MG_OK;
+}
+
 // The device error flags a solve reports (singular coarsest matrix, a bounded wait that gave up); one host wait.
 mg_status handle_errors(mg_handle *h) {
     CK(cudaStreamWaitEvent(h->stream, h->ev_inv, 0));
@@ -1282,6 +1405,7 @@ bool tail_ctas_ok(const mg_handle *h, int ctas) {
 
 void drop_graphs(mg_handle *h) {
     if (h->g64) { cudaGraphExecDestroy(h->g64); h->g64 = nullptr; }
+    if (h->gasync) { cudaGraphExecDestroy(h->gasync); h->gasync = nullptr; }
     if (h->gcorr) { cudaGraphExecDestroy(h->gcorr); h->gcorr = nullptr; }
     if (h->g32) { cudaGraphExecDestroy(h->g32); h->g32 = nullptr; }
 }
@@ -1404,6 +1528,7 @@ mg_status mg_default_options(mg_options *o) {
     o->cycle = MG_CYCLE_V;
     o->smoother = MG_SMOOTH_RBGS;
     o->omega = 0.8;
+    o->fp64_jump_ratio = 2.0;
     return MG_OK;
 }
 
@@ -1457,10 +1582,13 @@ mg_status mg_create(const mg_grid *grid, const mg_options *opt, void *workspace,
     size_t dummy;
     plan(h, aligned, &dummy);
     if (cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&h->cap2, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreate(&h->ev_a0) != cudaSuccess || cudaEventCreate(&h->ev_a1) != cudaSuccess ||
+        cudaMallocHost(&h->astat_h, sizeof(AsyncStat)) != cudaSuccess ||
         cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&h->ev_asm, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&h->ev_inv, cudaEventDisableTiming) != cudaSuccess ||
-        cudaMallocHost(&h->errh, 2 * sizeof(int)) != cudaSuccess ||
+        cudaMallocHost(&h->errh, 4 * sizeof(int)) != cudaSuccess ||
         cudaMallocHost(&h->norms_h, 8 * sizeof(double)) != cudaSuccess ||
         cudaMemsetAsync(h->ticket, 0, sizeof(unsigned int), h->stream) != cudaSuccess ||
         cudaStreamSynchronize(h->stream) != cudaSuccess) {
@@ -1508,6 +1636,7 @@ mg_status mg_solve(mg_handle *h, const double *rhs, double *x, int on_device, mg
     mg_stats s;
     std::memset(&s, 0, sizeof(s));
     s.levels = h->nlev;
+    s.fp64_cells = h->jcells;
     const int dim = h->grid.dim;
     if (h->opt.precision == MG_FP64) st = dim == 2 ? solve64<2>(h, &s) : solve64<3>(h, &s);
     else st = dim == 2 ? solve_mixed<2>(h, &s) : solve_mixed<3>(h, &s);
@@ -1519,6 +1648,64 @@ mg_status mg_solve(mg_handle *h, const double *rhs, double *x, int on_device, mg
     if (h->errh[0] & 4) return fail(MG_ERR_INVALID_COEFF, "the coarsest-level matrix is singular");
     if (h->errh[1] & kErrAsyncTimeout) return fail(MG_ERR_TIMEOUT, "an asynchronous copy did not complete in time");
     s.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (stats) *stats = s;
+    if (s.status != MG_OK) {
+        g_err = "not converged after " + std::to_string(h->opt.max_cycles) + " cycles";
+        return (mg_status)s.status;
+    }
+    return MG_OK;
+}
+
+mg_status mg_solve_async(mg_handle *h, const double *rhs, double *x, void *event) {
+    mg_status st = check_handle(h, true);
+    if (st) return st;
+    if (!rhs || !x) return fail(MG_ERR_INVALID_ARG, "rhs and x must not be NULL");
+    if (!aligned16(rhs) || !aligned16(x)) return fail(MG_ERR_INVALID_ARG, "device pair arrays must be 16-byte aligned");
+    DeviceGuard dg(h->device);
+    if (!h->gasync) {
+        st = h->grid.dim == 2 ? capture_async<2>(h) : capture_async<3>(h);
+        if (st) return st;
+    }
+    CK(cudaMemsetAsync(h->err_d + 1, 0, sizeof(int), h->stream));
+    h->x_stale = false;
+    if ((st = prep(h, rhs, x, 1))) return st;
+    CK(cudaStreamWaitEvent(h->stream, h->ev_inv, 0));
+    CK(cudaEventRecord(h->ev_a0, h->stream));
+    CK(cudaGraphLaunch(h->gasync, h->stream));
+    if ((st = x_out(h, x, 1))) return st;
+    CK(cudaMemcpyAsync(h->errh, h->err_d, 2 * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaEventRecord(h->ev_a1, h->stream));
+    if (event) CK(cudaEventRecord(reinterpret_cast<cudaEvent_t>(event), h->stream));
+    h->async_pending = true;
+    return MG_OK;
+}
+
+mg_status mg_solve_async_stats(mg_handle *h, mg_stats *stats) {
+    mg_status st = check_handle(h, false);
+    if (st) return st;
+    if (!h->async_pending) return fail(MG_ERR_STATE, "no mg_solve_async to report on");
+    DeviceGuard dg(h->device);
+    CK(cudaEventSynchronize(h->ev_a1));
+    h->async_pending = false;
+    const AsyncStat a = *h->astat_h;
+    h->enq += h->async_kernels_pre + (long long)a.it * h->async_kernels_body + 1;   // + the right-hand side's prep
+    mg_stats s;
+    std::memset(&s, 0, sizeof(s));
+    s.levels = h->nlev;
+    s.fp64_cells = h->jcells;
+    const int per = h->opt.precision == MG_MIXED ? h->opt.inner_cycles : 1;
+    s.cycles = a.it * per;
+    s.outer = a.it;
+    for (int f = 0; f < 2; f++) {
+        s.r0[f] = a.n0[f];
+        s.rfinal[f] = a.nk[f];
+    }
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, h->ev_a0, h->ev_a1));
+    s.seconds = ms * 1e-3;
+    s.status = (a.ok || !(h->opt.rtol > 0.0)) ? MG_OK : MG_ERR_NOT_CONVERGED;
+    if (h->errh[0] & 4) return fail(MG_ERR_INVALID_COEFF, "the coarsest-level matrix is singular");
+    if (h->errh[1] & kErrAsyncTimeout) return fail(MG_ERR_TIMEOUT, "an asynchronous copy did not complete in time");
     if (stats) *stats = s;
     if (s.status != MG_OK) {
         g_err = "not converged after " + std::to_string(h->opt.max_cycles) + " cycles";
@@ -1909,13 +2096,18 @@ mg_status mg_destroy(mg_handle *h) {
     DeviceGuard dg(h->device);
     if (h->stream) cudaStreamSynchronize(h->stream);
     if (h->g64) cudaGraphExecDestroy(h->g64);
+    if (h->gasync) cudaGraphExecDestroy(h->gasync);
     if (h->gcorr) cudaGraphExecDestroy(h->gcorr);
     for (auto &sg : h->gsetup)
         if (sg.exec) cudaGraphExecDestroy(sg.exec);
     if (h->g32) cudaGraphExecDestroy(h->g32);
     if (h->aux) cudaStreamSynchronize(h->aux);
     if (h->cap) cudaStreamDestroy(h->cap);
+    if (h->cap2) cudaStreamDestroy(h->cap2);
     if (h->aux) cudaStreamDestroy(h->aux);
+    if (h->ev_a0) cudaEventDestroy(h->ev_a0);
+    if (h->ev_a1) cudaEventDestroy(h->ev_a1);
+    if (h->astat_h) cudaFreeHost(h->astat_h);
     if (h->ev_asm) cudaEventDestroy(h->ev_asm);
     if (h->ev_inv) cudaEventDestroy(h->ev_inv);
     if (h->errh) cudaFreeHost(h->errh);

@@ -85,11 +85,23 @@ __device__ __forceinline__ void offdiag(const Level<R> &L, const typename Vec<R>
     if (WITH_L4) sp += __ldg(L.l4 + c) * sT;
 }
 
-// Gauss-Seidel update of one cell from its plain neighbour sums.
+// Gauss-Seidel update of one cell from its plain neighbour sums.  In the FP32
+// cycles a cell next to a large coefficient jump (its FP32 W marked with a NaN
+// first entry at set-up) applies its 2x2 block in FP64 instead: the FP64 W
+// and Dinv b of the same level, the neighbour sums promoted.
+template <typename R>
+__device__ __noinline__ typename Vec<R>::v2 gs_update_fp64(const Level<R> &L, long long c, R sT, R sp) {
+    const dq W = ldgq(L.W64 + c);
+    const double2 bt = __ldcg(L.bt64 + c);
+    const double t = (double)sT, p = (double)sp;
+    return mk2<R>((R)(bt.x - W.a * t - W.b * p), (R)(bt.y - W.c * t - W.d * p));
+}
+
 template <typename R, bool NC = true>
 __device__ __forceinline__ typename Vec<R>::v2 gs_update(const Level<R> &L, long long c, R sT, R sp) {
     const auto bt = ldv<NC>(L.bt + c);
     const auto W = ldgq(L.W + c);
+    if (sizeof(R) == 4 && W.a != W.a) return gs_update_fp64<R>(L, c, sT, sp);
     return mk2<R>(bt.x - W.a * sT - W.b * sp, bt.y - W.c * sT - W.d * sp);
 }
 
@@ -149,6 +161,49 @@ template <typename R, int DIM, bool P>
 __global__ void __launch_bounds__(kBX * kBY, 8) k_rbgs_colour(Level<R> L, int colour) {
     CMG_TILES(P, ((L.n0 + 1) / 2 + kBX - 1) / kBX, (L.n1 + kBY - 1) / kBY, DIM == 3 ? L.n2 : 1,
               (rbgs_colour_block<R, DIM>(L, colour, bx, by, bz)));
+}
+
+// ---------------------------------------------------------------------------
+// The stop test of a solve run as one graph (mg_solve_async): the V-cycles
+// repeat inside a WHILE graph node whose condition this one-thread kernel
+// sets.  init: the initial norms n0 (norms[0..1]), no cycle yet; otherwise a
+// cycle has run and norms holds its norms.  The rule is mg_solve's: stop when
+// both fields fell by rtol (rtol <= 0: never), or at the start when both
+// initial norms are zero; the loop ends at max_it cycles whatever the norms
+// (so a non-finite norm still ends it).
+// ---------------------------------------------------------------------------
+struct AsyncStat {
+    double n0[2], nk[2];
+    int it;        // cycles (outer steps) run
+    int ok;        // the stop test was met
+};
+
+__device__ __forceinline__ bool async_converged(const double n0[2], const double nk[2], double rtol) {
+    if (!(rtol > 0.0)) return false;
+    for (int f = 0; f < 2; f++) {
+        const double q = n0[f] > 0.0 ? nk[f] / n0[f] : 0.0;
+        if (!(q <= rtol)) return false;
+    }
+    return true;
+}
+
+__global__ void k_async_stop(const double *__restrict__ norms, AsyncStat *__restrict__ st, int max_it, double rtol,
+                             cudaGraphConditionalHandle cond, int init) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    bool ok;
+    if (init) {
+        st->n0[0] = st->nk[0] = norms[0];
+        st->n0[1] = st->nk[1] = norms[1];
+        st->it = 0;
+        ok = async_converged(st->n0, st->nk, rtol) || (st->n0[0] == 0.0 && st->n0[1] == 0.0);
+    } else {
+        st->it += 1;
+        st->nk[0] = norms[0];
+        st->nk[1] = norms[1];
+        ok = async_converged(st->n0, st->nk, rtol);
+    }
+    st->ok = ok ? 1 : 0;
+    cudaGraphSetConditional(cond, (!ok && st->it < max_it) ? 1u : 0u);
 }
 
 // ---------------------------------------------------------------------------
@@ -552,6 +607,7 @@ __device__ __forceinline__ void residual64_to32_cell(const Level<double> &L, flo
     zp2 = fma(zp, zp, zp2);
     b32[c] = make_float2((float)rT, (float)rp);
     bt32[c] = make_float2((float)zT, (float)zp);     // Dinv r for the FP32 sweeps
+    if (L.jflag && L.jflag[c]) L.bt[c] = make_double2(zT, zp);   // and in FP64 where they apply the block in FP64
     e32[c] = make_float2(0.f, 0.f);
     if (r_out) {                                     // the initial residual of the defect correction:
         r_out[c] = make_double2(rT, rp);             // r0 over b (only this thread reads b[c], before this store),
@@ -763,6 +819,11 @@ struct SetupOut {                 // one level's outputs
     float *l432;
     float2 *G0p;                  // 2D mixed: FP32 axis-0 faces again, row pitch p0 (even), or NULL
     int p0, n0;
+    // finest level of mixed precision with jump marking on: per-cell mark,
+    // count of marked cells, and the face-coefficient ratio that marks a cell
+    unsigned char *jflag;
+    int *jcount;
+    double jratio;
 };
 
 struct SetupGeom {
@@ -891,6 +952,32 @@ __device__ __forceinline__ void setup_fine_cells(const SetupGeom &gm, const Setu
     if (bad) atomicOr(err, 1);
     const dq S = AXI ? dq{s * l1, s * l2, 0.0, s * l3} : dq{l1, l2, 0.0, l3};
     finish_cell<DIM>(o, c, fid, own, g, S, l4, err);
+    if (o.jflag) {
+        // a coefficient jump at this cell: its interior faces' k or 1/rho
+        // differ by more than the ratio; its 2x2 block is then applied in FP64
+        // by the FP32 cycles (marked by a NaN first entry of its FP32 W)
+        double kmin = 0.0, kmax = 0.0, amin = 0.0, amax = 0.0;
+        bool any = false;
+#pragma unroll
+        for (int a = 0; a < DIM; a++)
+#pragma unroll
+            for (int sd = 0; sd < 2; sd++) {
+                const int fpos = pos[a] + sd;
+                if (fpos == 0 || fpos == gm.n[a]) continue;
+                const double kk = kf[a][sd], al = af[a][sd];
+                kmin = any ? fmin(kmin, kk) : kk;
+                kmax = any ? fmax(kmax, kk) : kk;
+                amin = any ? fmin(amin, al) : al;
+                amax = any ? fmax(amax, al) : al;
+                any = true;
+            }
+        const bool jump = any && (kmax > o.jratio * kmin || amax > o.jratio * amin);
+        o.jflag[c] = jump ? 1 : 0;
+        if (jump) {
+            reinterpret_cast<float *>(o.W32 + c)[0] = __int_as_float(0x7fc00000);
+            atomicAdd(o.jcount, 1);
+        }
+    }
 }
 
 template <int DIM>

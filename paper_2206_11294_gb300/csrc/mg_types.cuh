@@ -49,6 +49,14 @@ struct Level {
     const R *l4;
     const typename Vec<R>::q4 *W;   // Dinv [[1, 0], [l4, 1]]
     typename Vec<R>::v2 *bt;        // Dinv b
+    // FP32 levels of mixed precision: the same level's FP64 W and Dinv b.  A
+    // cell whose FP32 W has a NaN first entry (set at set-up for cells at a
+    // large coefficient jump) is updated with these, in FP64.
+    const dq *W64;
+    double2 *bt64;
+    // Finest level of mixed precision: 1 for those cells (the FP64 residual
+    // then stores their Dinv r in FP64); NULL elsewhere.
+    const unsigned char *jflag;
 };
 
 // Dirichlet flags per axis and side (prolongation ghost signs).

@@ -86,6 +86,26 @@ class HierarchyCache:
         self.created += 1
         return obj
 
+    def acquire_new(self, key: Tuple, nbytes: int, evict: bool = True):
+        """A newly created hierarchy of that key (never an idle one), or None
+        when the budget does not allow it (after evicting idle ones, if
+        `evict`)."""
+        if nbytes > self.budget:
+            raise MemoryError(f"request needs {nbytes} bytes, budget is {self.budget}")
+        while evict and self.used + nbytes > self.budget and self.idle:
+            oid, (k, obj, nb) = self.idle.popitem(last=False)
+            self.free(obj)
+            self.used -= nb
+            self.evictions += 1
+        if self.used + nbytes > self.budget:
+            return None
+        obj = self.make(key)
+        self.used += nbytes
+        self.peak = max(self.peak, self.used)
+        self.busy[id(obj)] = (key, obj, nbytes)
+        self.created += 1
+        return obj
+
     def release(self, obj):
         k, o, nb = self.busy.pop(id(obj))
         self.idle[id(obj)] = (k, o, nb)
@@ -124,6 +144,8 @@ class Engine:
         self.table = tuning_table
         self._tuned = set()
         self._tune_lock = threading.Lock()
+        self._pinned = {}                 # id(problem) -> (problem, pinned host copies of its inputs)
+        self._pin_lock = threading.Lock()
         if tune and self.table is None:
             from .autotune import TuningTable
             self.table = TuningTable(None)
@@ -154,23 +176,43 @@ class Engine:
         self._tuned.discard(id(solver))
         solver.close()
 
+    def pinned(self, problem) -> dict:
+        """Page-locked host copies of a problem's inputs, made once per problem
+        object (a request's arrays as a client would hand them over), so that
+        each request's host-to-device copies run at full link speed."""
+        import numpy as np
+        torch = self.torch
+        with self._pin_lock:
+            hit = self._pinned.get(id(problem))
+            if hit is not None and hit[0] is problem:
+                return hit[1]
+            pin = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).pin_memory()
+            d = dict(lam=pin(problem.lam), fa=[pin(f) for f in problem.fa], fk=[pin(f) for f in problem.fk],
+                     b=pin(problem.b), x0=pin(problem.x0))
+            self._pinned[id(problem)] = (problem, d)
+            return d
+
     def run(self, solvers: List, problems: List, stream) -> List[Tuple[Any, dict]]:
-        """Coefficients and one solve per problem (batched when several)."""
+        """Coefficients and one solve per problem (batched when several).  The
+        inputs go to the device and the result comes back through page-locked
+        host memory, on the slot's stream; the returned x is a host array."""
         torch = self.torch
         for s in solvers:
             if s.stream is not stream:
                 s.set_stream(stream)      # a cached hierarchy moves to this slot's stream
         with torch.cuda.stream(stream):
-            T = lambda a: torch.from_numpy(a).to(f"cuda:{self.device}", non_blocking=False)
+            dev = f"cuda:{self.device}"
+            T = lambda a: a.to(dev, non_blocking=True)
             bs, xs = [], []
             for s, p in zip(solvers, problems):
-                s.set_coeffs(T(p.lam), [T(f) for f in p.fa], [T(f) for f in p.fk])
+                h = self.pinned(p)
+                s.set_coeffs(T(h["lam"]), [T(f) for f in h["fa"]], [T(f) for f in h["fk"]])
                 if self.tune and id(s) not in self._tuned:
                     with self._tune_lock:            # one measurement at a time on the device
                         self.table.tune(s)
                         self._tuned.add(id(s))
-                bs.append(T(p.b))
-                xs.append(T(p.x0.copy()))
+                bs.append(T(h["b"]))
+                xs.append(T(h["x0"]))
             if len(solvers) == 1:
                 stats = [solvers[0].solve(bs[0], xs[0], allow_not_converged=True)]
             else:
@@ -179,9 +221,11 @@ class Engine:
                     stats = batch.solve(bs, xs, allow_not_converged=True)
                 finally:
                     batch.close()
-            out = [x.cpu().numpy() for x in xs]
+            outs = [torch.empty(x.shape, dtype=x.dtype, pin_memory=True) for x in xs]
+            for o, x in zip(outs, xs):
+                o.copy_(x, non_blocking=True)
             stream.synchronize()
-        return list(zip(out, stats))
+        return list(zip([o.numpy() for o in outs], stats))
 
 
 class Server:
@@ -207,6 +251,39 @@ class Server:
     def _make(self, key):
         problem, stream = self._make_stream
         return self.engine.make(problem, stream)
+
+    def prewarm(self, problems: List, per_shape: int = 1) -> int:
+        """Builds up to `per_shape` hierarchies for each distinct grid among
+        `problems` before any request arrives (as far as the HBM budget allows),
+        runs one solve on each (its graphs are captured and, with tuning, its
+        kernel choices measured) and leaves them idle in the cache, so that
+        requests find resident hierarchies instead of creating them.  Returns
+        the number built."""
+        stream = self.engine.new_stream()
+        seen, built = set(), 0
+        for p in problems:
+            key = (self.engine.key(p),)
+            if key in seen:
+                continue
+            seen.add(key)
+            got = []
+            with self.lock:
+                for _ in range(per_shape):
+                    self._make_stream = (p, stream)
+                    try:
+                        s = self.cache.acquire_new(key, self.engine.size(p), evict=False)
+                    except MemoryError:
+                        s = None
+                    if s is None:
+                        break
+                    got.append(s)
+            for s in got:
+                self.engine.run([s], [p], stream)
+            with self.lock:
+                for s in got:
+                    self.cache.release(s)
+            built += len(got)
+        return built
 
     def submit(self, problem) -> cf.Future:
         fut: cf.Future = cf.Future()

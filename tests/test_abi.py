@@ -42,6 +42,7 @@ def test_default_options(lib):
     assert (o.nu1, o.nu2, o.precision, o.max_cycles, o.coarse_min, o.inner_cycles) == (2, 2, 0, 50, 4, 1)
     assert o.rtol == 1e-10
     assert o.cycle == B.CYCLES["V"] == 0 and B.CYCLES == {"V": 0, "W": 1, "F": 2}
+    assert o.smoother == B.SMOOTHERS["rbgs"] == 0 and o.omega == 0.8 and o.fp64_jump_ratio == 2.0
 
 
 def test_cycle_option_validated(lib):
@@ -87,6 +88,10 @@ def test_workspace_size_scales_with_levels(lib):
     (dict(n=(1000, 1000, 1)), {}),                                # coarsest 125 x 125: too large
     ({}, dict(nu1=0, nu2=0)),
     ({}, dict(max_cycles=-1)),
+    ({}, dict(smoother=2)),
+    ({}, dict(smoother="wjac", omega=1.5)),
+    ({}, dict(fp64_jump_ratio=0.5)),
+    ({}, dict(fp64_jump_ratio=float("inf"))),
 ])
 def test_argument_validation(lib, kw, okw):
     st, _ = _size(lib, _grid(**kw), **okw)

@@ -168,13 +168,26 @@ def test_table_reuses_measurement(torch_cuda):
 def test_tma_sweep_on_ragged_grid(torch_cuda, precision):
     """The TMA-fed sweep on a grid that no tile shape divides (200 x 72: tiles
     hang over the right and top edges, where the boxes are zero-filled): same
-    result, bit for bit, as colour sweeps; a level it cannot run is refused."""
+    result, bit for bit, as colour sweeps; a level it cannot run is refused.
+    Mixed precision runs it with the FP64 blocks at jumps off: the TMA sweep
+    stages the FP32 W in shared memory and has no FP64 branch, so with them on
+    the finest level refuses it."""
     from paper_2206_11294_gb300.binding import MgError, MG_ERR_INVALID_ARG
     W, D = I.BC_WALL, I.BC_DIRICHLET
     p = I.random_coeff_problem(I.Grid(dim=2, axisym=0, n=(200, 72, 1), h=1e-4, bc=((D, W), (W, D), (0, 0)),
                                       bcT=((300, 0), (0, 300), (0, 0)), bcp=((1e5, 0), (0, 1e5), (0, 0))),
                                seed=73, dt=1e-5)
-    s0, x0, st0 = _solve(p, precision=precision)
+    if precision == "mixed":
+        sj, _, stj = _solve(p, precision="mixed")
+        assert stj["fp64_cells"] > 0
+        bad = sj.tuning()
+        bad["sweep"][0], bad["tile"][0] = "async", 1
+        with pytest.raises(MgError) as e:
+            sj.set_tuning(bad)
+        assert e.value.status == MG_ERR_INVALID_ARG
+        sj.close()
+    kw = dict(precision=precision) if precision == "fp64" else dict(precision="mixed", fp64_jump_ratio=0.0)
+    s0, x0, st0 = _solve(p, **kw)
     base = s0.tuning()
     n = base["levels"]
     sizes = s0.levels()
@@ -185,7 +198,7 @@ def test_tma_sweep_on_ragged_grid(torch_cuda, precision):
         for l in range(n - 1):
             if allowed(l, t):
                 v["sweep"][l], v["tile"][l] = "async", t
-        s, x, st = _solve(p, tuning=v, precision=precision)
+        s, x, st = _solve(p, tuning=v, **kw)
         assert st["cycles"] == st0["cycles"]
         assert np.array_equal(x, x0), t
         s.close()

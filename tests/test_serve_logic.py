@@ -111,3 +111,22 @@ def test_poisson_stream_rate():
     st = run_stream(srv, [prob("a", 4, 10), prob("b", 6, 20)], rate=2000.0, count=200)
     srv.close()
     assert st["requests"] == 200 and st["throughput_rps"] > 0
+
+
+def test_prewarm_builds_resident_hierarchies_within_budget():
+    """prewarm builds per_shape hierarchies per distinct grid without evicting
+    any, stops at the budget, runs one solve on each, and later requests reuse
+    them instead of creating new ones."""
+    eng = FakeEngine()
+    srv = Server(eng, hbm_budget=250, slots=2, max_batch=1)
+    pool = [prob("a", 8, 50), prob("a2", 8, 50), prob("b", 16, 60), prob("c", 32, 100)]
+    built = srv.prewarm(pool, per_shape=2)
+    # a: 2 x 50, b: 2 x 60 -> 220 used; c (100) does not fit without evicting
+    assert built == 4 and srv.cache.used == 220 and srv.cache.evictions == 0
+    assert eng.groups == [1, 1, 1, 1]
+    created = srv.cache.created
+    futs = [srv.submit(p) for p in pool[:3] * 3]
+    for f in futs:
+        f.result(timeout=10)
+    assert srv.cache.created == created          # every request found a resident hierarchy
+    srv.close()
