@@ -317,6 +317,57 @@ def bubbles_1024(n: int = 1024, seed: int = 2, length: float = 1.0, dt: float = 
                      name=f"bubbles16_{n}x{n}")
 
 
+def composite_bubble(n: int = 64, box=None, seed: int = 9, n_bubbles: int = 2, rmin: float = 0.06,
+                     rmax: float = 0.12, length: float = 1.0, dt: float = 1e-7, bc=None, bcT=None, bcp=None,
+                     name: str = ""):
+    """A refined-patch (adaptive) grid around bubbles: (base, patch, box).
+
+    base: the n x n grid of spacing length / n over the whole domain, its
+    coefficients and right-hand side assembled at that spacing; box = ((i0,
+    i1), (j0, j1)) the base cells refined 2:1 (by default the bubbles'
+    bounding box, one base cell wider); patch: the fine cells of the box,
+    cut from the same field assembled on the 2n x 2n grid of the whole domain
+    (its grid's origin at the box's corner).  The bubbles stay inside the box,
+    so the base cells outside it are pure liquid, as on a grid coarsened away
+    from the bubble."""
+    rng = np.random.default_rng(seed)
+    bc = bc or _walls(2)
+    bcT = bcT or ((0.0, 0.0),) * 3
+    bcp = bcp or ((0.0, 0.0),) * 3
+    H = length / n
+    gb = Grid(dim=2, axisym=0, n=(n, n, 1), h=H, bc=bc, bcT=bcT, bcp=bcp)
+    gf = Grid(dim=2, axisym=0, n=(2 * n, 2 * n, 1), h=H / 2, bc=bc, bcT=bcT, bcp=bcp)
+    centres, radii = _place_bubbles(rng, n_bubbles, rmin * length, rmax * length, 2, (length, length))
+    if box is None:
+        lo = [min(c[a] - r for c, r in zip(centres, radii)) for a in range(2)]
+        hi = [max(c[a] + r for c, r in zip(centres, radii)) for a in range(2)]
+        box = tuple((max(0, int(math.floor(lo[a] / H)) - 1), min(n, int(math.ceil(hi[a] / H)) + 1)) for a in range(2))
+    base = assemble(name or f"composite_base_{n}", gb, volume_fraction(gb, centres, radii), liquid(), gas(), dt, rng)
+    full = assemble(f"composite_fine_{2 * n}", gf, volume_fraction(gf, centres, radii), liquid(), gas(), dt, rng)
+    (i0, i1), (j0, j1) = box
+    m0, m1 = 2 * (i1 - i0), 2 * (j1 - j0)
+    pbc = [list(s) for s in bc]
+    pT = [list(s) for s in bcT]
+    pP = [list(s) for s in bcp]
+    for a, (lo_, hi_) in enumerate(box):
+        if lo_ > 0:
+            pbc[a][0], pT[a][0], pP[a][0] = BC_WALL, 0.0, 0.0
+        if hi_ < n:
+            pbc[a][1], pT[a][1], pP[a][1] = BC_WALL, 0.0, 0.0
+    gp = Grid(dim=2, axisym=0, n=(m0, m1, 1), h=H / 2, origin=(i0 * H, j0 * H, 0.0),
+              bc=tuple(map(tuple, pbc)), bcT=tuple(map(tuple, pT)), bcp=tuple(map(tuple, pP)))
+    cells = lambda arr, k: arr.reshape(2 * n, 2 * n, k)[2 * j0: 2 * j1, 2 * i0: 2 * i1].reshape(-1, k)
+    fa = [full.fa[0].reshape(2 * n, 2 * n + 1)[2 * j0: 2 * j1, 2 * i0: 2 * i1 + 1].reshape(-1),
+          full.fa[1].reshape(2 * n + 1, 2 * n)[2 * j0: 2 * j1 + 1, 2 * i0: 2 * i1].reshape(-1)]
+    fk = [full.fk[0].reshape(2 * n, 2 * n + 1)[2 * j0: 2 * j1, 2 * i0: 2 * i1 + 1].reshape(-1),
+          full.fk[1].reshape(2 * n + 1, 2 * n)[2 * j0: 2 * j1 + 1, 2 * i0: 2 * i1].reshape(-1)]
+    patch = Problem(name=f"composite_patch_{m0}x{m1}", grid=gp, lam=np.ascontiguousarray(cells(full.lam, 4)),
+                    fa=[np.ascontiguousarray(f) for f in fa], fk=[np.ascontiguousarray(f) for f in fk],
+                    b=np.ascontiguousarray(cells(full.b, 2)), x0=np.ascontiguousarray(cells(full.x0, 2)),
+                    meta=dict(dt=dt))
+    return base, patch, box
+
+
 def random_coeff_problem(g: Grid, seed: int, jump: float = 1000.0, dt: float = 1e-7,
                          couple: bool = True) -> Problem:
     """Small problem with random bubble placement on an arbitrary grid (tests)."""

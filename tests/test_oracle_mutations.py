@@ -226,3 +226,69 @@ def test_wjac_mutant_fails_the_pin(orc, name):
             assert not _wjac_pins_pass(orc), name
     finally:
         del MUTATIONS[name]
+
+
+# Planted mistakes in the refined-patch oracle (composite_oracle.c), against its pins.
+COMPOSITE_MUTATIONS = {
+    # the interface flux seen from the fine cell over h instead of the 1.5 h to the coarse centre
+    "cf_interface_distance": ("sum += cf * (gu - u) / (1.5 * h * h);", "sum += cf * (gu - u) / (h * h);"),
+    # the coarse field's tangential slope taken the wrong way
+    "cf_tangential_sign": ("return uc + sgn * (up - um) / 8.0;", "return uc - sgn * (up - um) / 8.0;"),
+    # the tangential offset taken as half a coarse cell instead of a quarter
+    "cf_tangential_offset": ("return uc + sgn * (up - um) / 8.0;", "return uc + sgn * (up - um) / 4.0;"),
+    # the base cell's interface flux with the wrong distance: no longer the fine faces' flux
+    "cf_reflux_distance": ("sum += (0.5 * H) * cf * (uf - gu) / (1.5 * 0.5 * H) / (H * H);",
+                           "sum += (0.5 * H) * cf * (uf - gu) / (0.5 * H) / (H * H);"),
+    # the FAC cycle without the base correction's prolongation onto the patch
+    "cf_fac_no_prolongation": ("        prolong_to_patch(cg, &P, Ls[0].u, P.u);\n", "\n"),
+}
+
+
+@contextlib.contextmanager
+def composite_mutant(name):
+    from oracle import composite as cf
+    old, new = COMPOSITE_MUTATIONS[name]
+    here = os.path.dirname(cf.__file__)
+    src = open(os.path.join(here, "composite_oracle.c")).read()
+    assert src.count(old) >= 1, name
+    d = tempfile.mkdtemp()
+    try:
+        shutil.copy(os.path.join(here, "coupled_oracle.c"), os.path.join(d, "coupled_oracle.c"))
+        path = os.path.join(d, "m.c")
+        open(path, "w").write(src.replace(old, new))
+        import subprocess
+        subprocess.check_call(["gcc", "-std=c99", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+                               "-I", d, "-o", os.path.join(d, "m.so"), path, "-lm"])
+        lib = cf.configure(C.CDLL(os.path.join(d, "m.so")))
+        cf._load()
+        saved = cf._lib
+        cf._lib = lib
+        try:
+            yield
+        finally:
+            cf._lib = saved
+    finally:
+        shutil.rmtree(d, ignore_errors=True)
+
+
+def _composite_pins_pass() -> bool:
+    import test_oracle_composite as P
+    try:
+        for axis in (0, 1):
+            for box in (((3, 8), (2, 7)), ((0, 6), (3, 9))):
+                P.test_linear_fields_have_zero_laplacian(axis, box)
+        P.test_conservation_with_walls(((3, 8), (2, 7)))
+        P.test_fac_converges_to_the_dense_solution(True, None)
+    except (AssertionError, RuntimeError):
+        return False
+    return True
+
+
+def test_unmutated_oracle_passes_the_composite_pins():
+    assert _composite_pins_pass()
+
+
+@pytest.mark.parametrize("name", list(COMPOSITE_MUTATIONS))
+def test_composite_mutant_fails_a_pin(name):
+    with composite_mutant(name):
+        assert not _composite_pins_pass(), name
