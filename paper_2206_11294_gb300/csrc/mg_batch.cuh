@@ -279,6 +279,23 @@ __global__ void __launch_bounds__(kBatchThreads) kb_coarse_assemble(const BCoars
     }
 }
 
+// Windowed path of the coarsest inverses (window_path): one block per problem
+// factors (the factors in the problem's work array: Lb, then Uc); a 2D grid
+// of warp groups (x: column groups, y: problem) computes the inverse.
+__global__ void __launch_bounds__(kWinThreads) kb_band_lu_window(const BCoarse *__restrict__ co,
+                                                                  const int *__restrict__ ids) {
+    const BCoarse &C = co[ids[blockIdx.x]];
+    band_lu_window_block(C.M, C.nc, C.kl, C.kl, C.piv, C.dinv, C.Mwork, C.Mwork + (long long)C.nc * C.kl, C.err);
+}
+
+__global__ void __launch_bounds__(256) kb_band_inv_block(const BCoarse *__restrict__ co, const int *__restrict__ ids) {
+    const BCoarse &C = co[ids[blockIdx.y]];
+    const int j0 = blockIdx.x * (blockDim.x >> 5);
+    if (j0 >= C.nc) return;
+    band_inv_block(C.Mwork, C.Mwork + (long long)C.nc * C.kl, C.piv, C.dinv, C.nc, C.kl, C.kl, C.Minv, C.Minv32,
+                   C.err, j0);
+}
+
 // Coarsest inverses of the problems listed in ids (nc <= kBandSmemMax): the
 // single-warp LU, one block per problem; then the columns, one warp per 32.
 __global__ void __launch_bounds__(kLUThreads) kb_band_lu_warp(const BCoarse *__restrict__ co,
@@ -503,6 +520,11 @@ struct mg_batch {
     BIo *io;
     int *inv_ids;
     int *big_ids;                     // problems on the banded path (device)
+    int *win_ids;                     // problems on the windowed banded path (device)
+    std::vector<int> win_coarse;      // their indices
+    int max_nc_win = 0;
+    size_t win_smem = 0, win_inv_smem = 0;
+    int win_warps = 8;
     int max_nc_big;
     int n_inv_smem;
     size_t inv_smem_bytes;
@@ -876,11 +898,19 @@ mg_status mg_batch_create(int count, mg_handle *const *handles, mg_batch **out) 
             b->inv_cols_smem_bytes = std::max(b->inv_cols_smem_bytes,
                                               sizeof(double) * (size_t)inv_smem_doubles(h->nc, C.kl, C.kl));
             b->max_nc_small = std::max(b->max_nc_small, h->nc);
+        } else if (window_path(h->nc, C.kl)) {
+            b->win_coarse.push_back(p);
+            b->max_nc_win = std::max(b->max_nc_win, h->nc);
+            b->win_smem = std::max(b->win_smem, (size_t)band_window_smem(C.kl, C.kl));
+            b->win_warps = std::min(b->win_warps, inv_block_warps(h->nc, C.kl));
         } else {
             b->big_coarse.push_back(p);
             b->max_nc_big = std::max(b->max_nc_big, h->nc);
         }
     }
+    for (int p : b->win_coarse)          // the staging of the common warp count
+        b->win_inv_smem = std::max(b->win_inv_smem, (size_t)band_inv_block_smem(co[p].nc, co[p].kl, co[p].kl,
+                                                                                 b->win_warps));
     b->n_inv_smem = (int)inv_ids.size();
     // one device allocation for the tables
     size_t off = 0;
@@ -896,7 +926,8 @@ mg_status mg_batch_create(int count, mg_handle *const *handles, mg_batch **out) 
                  o_sl = take(sizeof(BSetupLevel) * sl.size()), o_sin = take(sizeof(SetupIn) * count),
                  o_co = take(sizeof(BCoarse) * count), o_io = take(sizeof(BIo) * count),
                  o_ids = take(sizeof(int) * std::max<size_t>(1, inv_ids.size())), o_err = take(sizeof(int) * 2 * count),
-                 o_big = take(sizeof(int) * std::max<size_t>(1, b->big_coarse.size()));
+                 o_big = take(sizeof(int) * std::max<size_t>(1, b->big_coarse.size())),
+                 o_win = take(sizeof(int) * std::max<size_t>(1, b->win_coarse.size()));
     cudaError_t e = cudaMalloc(&b->mem, off);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -914,6 +945,7 @@ mg_status mg_batch_create(int count, mg_handle *const *handles, mg_batch **out) 
     b->io = reinterpret_cast<BIo *>(b->mem + o_io);
     b->inv_ids = reinterpret_cast<int *>(b->mem + o_ids);
     b->big_ids = reinterpret_cast<int *>(b->mem + o_big);
+    b->win_ids = reinterpret_cast<int *>(b->mem + o_win);
     b->err_d = reinterpret_cast<int *>(b->mem + o_err);
     if (cudaMemcpy(b->lv, lv.data(), sizeof(BLevel) * lv.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(b->pr, pr.data(), sizeof(BProb) * count, cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -923,6 +955,8 @@ mg_status mg_batch_create(int count, mg_handle *const *handles, mg_batch **out) 
         cudaMemcpy(b->co, co.data(), sizeof(BCoarse) * count, cudaMemcpyHostToDevice) != cudaSuccess ||
         (inv_ids.size() && cudaMemcpy(b->inv_ids, inv_ids.data(), sizeof(int) * inv_ids.size(),
                                       cudaMemcpyHostToDevice) != cudaSuccess) ||
+        (b->win_coarse.size() && cudaMemcpy(b->win_ids, b->win_coarse.data(), sizeof(int) * b->win_coarse.size(),
+                                            cudaMemcpyHostToDevice) != cudaSuccess) ||
         (b->big_coarse.size() && cudaMemcpy(b->big_ids, b->big_coarse.data(), sizeof(int) * b->big_coarse.size(),
                                             cudaMemcpyHostToDevice) != cudaSuccess) ||
         cudaMemset(b->st, 0, sizeof(BState) * count) != cudaSuccess ||
@@ -1123,6 +1157,15 @@ mg_status mg_batch_set_coeffs(mg_batch *b, const double *const *lambda, const do
         CK(raise_smem_limit((const void *)kb_band_inv_cols_warp, (int)b->inv_cols_smem_bytes));
         kb_band_inv_cols_warp<<<dim3((b->max_nc_small + 31) / 32, b->n_inv_smem), dim3(32, kInvRows),
                                 b->inv_cols_smem_bytes, s>>>(b->co, b->inv_ids);
+        b->launches += 2;
+    }
+    if (!b->win_coarse.empty()) {           // the windowed LU, a block per problem, then the inverse's columns
+        const unsigned nw = (unsigned)b->win_coarse.size();
+        CK(raise_smem_limit((const void *)kb_band_lu_window, (int)b->win_smem));
+        CK(raise_smem_limit((const void *)kb_band_inv_block, (int)b->win_inv_smem));
+        kb_band_lu_window<<<nw, kWinThreads, b->win_smem, s>>>(b->co, b->win_ids);
+        kb_band_inv_block<<<dim3((unsigned)((b->max_nc_win + b->win_warps - 1) / b->win_warps), nw), 32 * b->win_warps,
+                            b->win_inv_smem, s>>>(b->co, b->win_ids);
         b->launches += 2;
     }
     if (!b->big_coarse.empty()) {           // medium coarsest levels: the banded path, all at once

@@ -1454,4 +1454,258 @@ __global__ void k_transpose(const double *__restrict__ W, double *__restrict__ M
     }
 }
 
+// ---------------------------------------------------------------------------
+// Coarsest inverse for kBandSmemMax < n (the coarsest grids of sizes with an
+// odd factor of 9 or more, up to 31 x 31 cells) in two kernels, both exact in
+// FP64 with the same banded partial pivoting as k_band_lu:
+//
+// 1. k_band_lu_window: one block.  Only the active window of the band, rows
+//    k..k+kl and columns k..k+kl+ku, is live at step k; it sits in shared
+//    memory, circular in both directions, and the row that enters after the
+//    step is loaded from global memory while the step computes.  The factors
+//    leave in compact band layouts: Lb[k][q] = l_{k+1+q,k} (q < kl) and
+//    Uc[c][o] = u_{c-o,c} (1 <= o <= kl+ku, column c of U), with piv[k] and
+//    dinv[k] = 1 / u_kk.
+// 2. k_band_inv_block: each warp of a block computes one column j of the
+//    inverse, y = U^-1 L^-1 P e_j (the row swaps and multipliers in the order
+//    the factorisation applied them, then U from the last row up), with y in
+//    shared memory; the block's warps walk the same steps together, so each
+//    chunk of kInvChunk rows of Lb / Uc is staged in shared memory once for
+//    all of them.  The columns are written back as row segments of Minv (and
+//    of the FP32 copy).
+// ---------------------------------------------------------------------------
+constexpr int kWinThreads = 1024;
+constexpr int kLuAhead = 8;           // steps by which the windowed LU loads the rows entering it ahead
+constexpr int kInvChunk = 32;
+constexpr long long kWinSmemMax = 200 * 1024;
+
+// Shared memory of k_band_lu_window for bandwidths kl, ku (bytes).
+inline long long band_window_smem(int kl, int ku) {
+    const long long R = kl + 1, C = kl + ku + 1;
+    return 8LL * (R * C + C + R);
+}
+
+// Shared memory of k_band_inv_block with `warps` warps per block (bytes).
+inline long long band_inv_block_smem(int n, int kl, int ku, int warps) {
+    const long long C = kl + ku + 1;
+    return 8LL * ((long long)warps * n + (long long)kInvChunk * (kl + C + 1)) + 4LL * kInvChunk;
+}
+
+// Slot arithmetic without divisions: a window row or column index moves by
+// at most one period, so one conditional subtraction wraps it.
+__device__ __forceinline__ int wrap(int v, int m) { return v >= m ? v - m : v; }
+
+// One pivot step of the windowed LU (see band_lu_window_block).  `pre` holds
+// column k + 1 + tid of the row that enters the window after this step, and
+// receives the one that enters kLuAhead steps later.  Returns false on a zero
+// pivot.
+__device__ __forceinline__ bool band_lu_window_step(const double *__restrict__ M, int n, int kl, int R, int C, int ur,
+                                                    int k, int ks, int kc, double *W, double *urow, double *lmul,
+                                                    int *__restrict__ piv, double *__restrict__ dinv,
+                                                    double *__restrict__ Lb, double *__restrict__ Uc, double &pre,
+                                                    int &s_piv, int &s_bad, double &s_pinv) {
+    const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5, nty = blockDim.x >> 5;
+    const int rlast = min(n - 1, k + kl), clast = min(n - 1, k + ur);
+    if (tid < 32) {
+        // pivot: largest |a_rk|, the first such row on ties.  |a| is compared
+        // as its bit pattern with the sign cleared (monotone for non-negative
+        // doubles), on the integer pipe instead of GB300's scarce FP64 one.
+        long long best = -1;
+        int br = k;
+        for (int r = k + tid, rs = wrap(ks + tid, R); r <= rlast; r += 32, rs = wrap(rs + 32 - (32 / R) * R, R)) {
+            const long long v = __double_as_longlong(W[rs * C + kc]) & 0x7fffffffffffffffLL;
+            if (v > best) { best = v; br = r; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const long long ov = __shfl_down_sync(0xffffffffu, best, o);
+            const int orr = __shfl_down_sync(0xffffffffu, br, o);
+            if (ov > best || (ov == best && orr < br)) { best = ov; br = orr; }
+        }
+        if (tid == 0) {
+            s_piv = br;
+            piv[k] = br;
+            if (best <= 0) s_bad = 1;               // an exactly zero column below the diagonal
+        }
+    }
+    __syncthreads();
+    if (s_bad) return false;
+    const int p = s_piv;
+    if (tid <= clast - k) {                        // swap rows k and p; keep row k of U
+        const int cs = wrap(kc + tid, C);
+        const double a = W[ks * C + cs];
+        double b = a;
+        if (p != k) {
+            const int ps = wrap(ks + (p - k), R) * C + cs;
+            b = W[ps];
+            W[ps] = a;
+            W[ks * C + cs] = b;
+        }
+        urow[tid] = b;
+        // one reciprocal per step: GB300's FP64 pipe issues ~2 operations per clock per SM,
+        // and a division in every thread of the block would cost more than the step's update
+        if (tid == 0) s_pinv = 1.0 / b;
+    }
+    __syncthreads();
+    const double pinv = s_pinv;
+    if (tid >= 1 && tid <= clast - k) Uc[(long long)(k + tid) * C + tid] = urow[tid];
+    if (tid == 0) dinv[k] = pinv;
+    if (tid < rlast - k) {                         // multipliers of rows k+1..rlast; column k leaves the window
+        const int rs = wrap(ks + 1 + tid, R) * C + kc;
+        const double l = W[rs] * pinv;
+        lmul[tid] = l;
+        Lb[(long long)k * kl + tid] = l;
+        W[rs] = 0.0;
+    }
+    __syncthreads();
+    const int nr = rlast - k, ncl = clast - k;
+    for (int i = ty; i < nr; i += nty) {           // rows k+1..rlast by warp, columns k+1..clast by lane
+        const double l = lmul[i];
+        double *row = W + wrap(ks + 1 + i, R) * C;
+        for (int jj = tx; jj < ncl; jj += 32) row[wrap(kc + 1 + jj, C)] -= l * urow[1 + jj];
+    }
+    if (tid < C) W[ks * C + wrap(kc + 1 + tid, C)] = pre;   // row k + R enters the retired slot (zeros beyond n)
+    {
+        const int r = k + R + kLuAhead, c = k + kLuAhead + 1 + tid;
+        pre = (tid < C && r < n && c < n) ? M[(long long)r * n + c] : 0.0;
+    }
+    __syncthreads();
+    return true;
+}
+
+__device__ __forceinline__ void band_lu_window_block(const double *__restrict__ M, int n, int kl, int ku,
+                                                     int *__restrict__ piv, double *__restrict__ dinv,
+                                                     double *__restrict__ Lb, double *__restrict__ Uc,
+                                                     int *__restrict__ err) {
+    extern __shared__ double wsm[];
+    __shared__ int s_piv, s_bad;
+    __shared__ double s_pinv;
+    const int R = kl + 1, ur = kl + ku, C = ur + 1;
+    double *W = wsm;                  // R x C window: entry (r, c) at (r mod R) * C + (c mod C)
+    double *urow = W + R * C;         // row k of U after the swap (columns k..k+ur)
+    double *lmul = urow + C;          // multipliers of rows k+1..k+kl
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    for (int q = tid; q < R * C; q += nthr) {
+        const int r = q / C, c = q - r * C;
+        W[q] = (r < n && c < n) ? M[(long long)r * n + c] : 0.0;
+    }
+    if (tid == 0) s_bad = 0;
+    // the rows entering the window, kLuAhead steps ahead: pre[a] serves the
+    // steps k = a (mod kLuAhead); the step loop is unrolled by kLuAhead so
+    // every slot is a register that its load has kLuAhead steps to fill
+    double pre[kLuAhead];
+#pragma unroll
+    for (int a = 0; a < kLuAhead; a++) {
+        const int r = R + a, c = a + 1 + tid;
+        pre[a] = (tid < C && r < n && c < n) ? M[(long long)r * n + c] : 0.0;
+    }
+    __syncthreads();
+    int k = 0, ks = 0, kc = 0;        // k mod R, k mod C
+    bool ok = true;
+    for (; k < n && ok;) {
+#pragma unroll
+        for (int a = 0; a < kLuAhead; a++) {
+            if (k < n && ok) {
+                ok = band_lu_window_step(M, n, kl, R, C, ur, k, ks, kc, W, urow, lmul, piv, dinv, Lb, Uc, pre[a],
+                                         s_piv, s_bad, s_pinv);
+                if (ok) {
+                    k++;
+                    ks = wrap(ks + 1, R);
+                    kc = wrap(kc + 1, C);
+                }
+            }
+        }
+    }
+    if (!ok) {
+        for (int q = k + tid; q < n; q += nthr) {
+            piv[q] = q;
+            dinv[q] = 0.0;
+        }
+        if (tid == 0) atomicOr(err, 4);
+    }
+}
+
+__global__ void __launch_bounds__(kWinThreads) k_band_lu_window(const double *__restrict__ M, int n, int kl, int ku,
+                                                                int *__restrict__ piv, double *__restrict__ dinv,
+                                                                double *__restrict__ Lb, double *__restrict__ Uc,
+                                                                int *__restrict__ err) {
+    band_lu_window_block(M, n, kl, ku, piv, dinv, Lb, Uc, err);
+}
+
+// Columns j0 .. j0 + warps - 1 of the inverse (block of warps x 32 threads).
+__device__ __forceinline__ void band_inv_block(const double *__restrict__ Lb, const double *__restrict__ Uc,
+                                               const int *__restrict__ piv, const double *__restrict__ dinv, int n,
+                                               int kl, int ku, double *__restrict__ Minv, float *__restrict__ Minv32,
+                                               const int *__restrict__ err, int j0) {
+    if (*(volatile const int *)err & 4) return;
+    extern __shared__ double ism[];
+    const int C = kl + ku + 1, ur = kl + ku;
+    const int warps = blockDim.x >> 5, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    double *y = ism + (long long)w * n;                      // this warp's column
+    double *Lc = ism + (long long)warps * n;                 // kInvChunk rows of Lb
+    double *Ucc = Lc + kInvChunk * kl;                       // kInvChunk rows of Uc
+    double *dc = Ucc + kInvChunk * C;                        // kInvChunk of dinv
+    int *pc = reinterpret_cast<int *>(dc + kInvChunk);       // kInvChunk of piv
+    const int j = j0 + w;
+    const bool live = j < n;
+    for (int i = lane; i < n; i += 32) y[i] = (live && i == j) ? 1.0 : 0.0;
+    // forward: P and L; columns j < n start at max(0, j - kl): earlier steps only swap and scale zeros
+    const int kstart = max(0, j0 - kl);
+    for (int kb = kstart; kb < n; kb += kInvChunk) {
+        const int cnt = min(kInvChunk, n - kb);
+        __syncthreads();
+        for (int q = tid; q < cnt * kl; q += nthr) Lc[q] = Lb[(long long)kb * kl + q];
+        for (int q = tid; q < cnt; q += nthr) pc[q] = piv[kb + q];
+        __syncthreads();
+        for (int t = 0; t < cnt; t++) {
+            const int k = kb + t;
+            const int p = pc[t];
+            if (p != k && lane == 0) {
+                const double a = y[k];
+                y[k] = y[p];
+                y[p] = a;
+            }
+            __syncwarp();
+            const double yk = y[k];
+            const int m = min(kl, n - 1 - k);
+            for (int q = lane; q < m; q += 32) y[k + 1 + q] -= Lc[t * kl + q] * yk;
+            __syncwarp();
+        }
+    }
+    // backward: U, from the last row up, column-wise: y_i = y_i / u_ii, then
+    // y_{i-o} -= u_{i-o,i} y_i
+    for (int ib = n - 1; ib >= 0; ib -= kInvChunk) {
+        const int cnt = min(kInvChunk, ib + 1);
+        __syncthreads();
+        for (int q = tid; q < cnt * C; q += nthr) Ucc[q] = Uc[(long long)(ib - cnt + 1) * C + q];
+        for (int q = tid; q < cnt; q += nthr) dc[q] = dinv[ib - cnt + 1 + q];
+        __syncthreads();
+        for (int t = cnt - 1; t >= 0; t--) {
+            const int i = ib - cnt + 1 + t;
+            const double yi = y[i] * dc[t];
+            __syncwarp();
+            if (lane == 0) y[i] = yi;
+            const int m = min(ur, i);
+            for (int o = 1 + lane; o <= m; o += 32) y[i - o] -= Ucc[t * C + o] * yi;
+            __syncwarp();
+        }
+    }
+    __syncthreads();
+    for (int q = tid; q < n * warps; q += nthr) {            // row segments Minv[i][j0 .. j0 + warps)
+        const int i = q / warps, ww = q - i * warps;
+        if (j0 + ww < n) {
+            const double v = ism[(long long)ww * n + i];
+            Minv[(long long)i * n + j0 + ww] = v;
+            if (Minv32) Minv32[(long long)i * n + j0 + ww] = (float)v;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_band_inv_block(const double *__restrict__ Lb, const double *__restrict__ Uc,
+                                                        const int *__restrict__ piv, const double *__restrict__ dinv,
+                                                        int n, int kl, int ku, double *__restrict__ Minv,
+                                                        float *__restrict__ Minv32, const int *__restrict__ err) {
+    band_inv_block(Lb, Uc, piv, dinv, n, kl, ku, Minv, Minv32, err, blockIdx.x * (blockDim.x >> 5));
+}
+
 }  // namespace cmg

@@ -586,3 +586,44 @@ def test_no_cycle_when_stop_test_met_at_start(torch_cuda, precision, on_device):
         assert st["cycles"] == stf["cycles"] and np.array_equal(x, xf)
         s.close()
         f.close()
+
+
+def _large_coarse_cases():
+    return {
+        # 736 = 23 x 32: the coarsest level is 23 x 23 cells (1058 unknowns)
+        "2d_736_bubbles": I.bubble_2d(736, seed=95, n_bubbles=5, rmin=0.03, rmax=0.1, centred=False),
+        # coarsest 9 x 13 (234 unknowns), stiff, Dirichlet and wall sides
+        "2d_stiff_9x13": I.random_coeff_problem(I.Grid(dim=2, axisym=0, n=(144, 208, 1), h=1e-4,
+                                                       bc=((D, W), (W, D), (0, 0)), bcT=((310, 0), (0, 290), (0, 0)),
+                                                       bcp=((1.1e5, 0), (0, 0.9e5), (0, 0))), seed=96, dt=1e-5),
+        # coarsest 5 x 7 x 3 (210 unknowns, band 71)
+        "3d_5x7x3": I.random_coeff_problem(I.Grid(dim=3, axisym=0, n=(40, 56, 24), h=1e-4, bc=((W, D), (W, W), (D, W)),
+                                                  bcT=((0, 300), (0, 0), (300, 0)), bcp=((0, 1e5), (0, 0), (1e5, 0))),
+                                           seed=97, dt=1e-5),
+    }
+
+
+@pytest.mark.parametrize("name", ["2d_736_bubbles", "2d_stiff_9x13", "3d_5x7x3"])
+def test_large_coarsest_levels_vs_oracle(torch_cuda, orc, name):
+    """Coarsest levels above 128 unknowns take the windowed banded LU and the
+    block-column inverse: FP64 solves after fixed cycles match the oracle
+    (whose coarsest solve is Gaussian elimination) at the usual tolerance, and
+    mixed precision reaches the converged oracle."""
+    p = _large_coarse_cases()[name]
+    g = p.grid.as_dict()
+    tol = 1e-9 if "stiff" in name or "3d" in name else 1e-12
+    s = _solver(p, rtol=0.0, max_cycles=2)
+    lv = s.levels()
+    assert 2 * int(np.prod(lv[-1])) > 128
+    x = p.x0.copy()
+    st = s.solve(p.b, x)
+    ref, cyc, _ = orc.mg_solve(g, p.lam, p.fa, p.fk, p.b, p.x0, max_cycles=2, rtol=0.0)
+    assert st["cycles"] == 2 == cyc
+    assert rel_dev(x, ref, p.x0) <= tol
+    s.close()
+    s = _solver(p, precision="mixed", rtol=1e-12 if tol > 1e-12 else 1e-10, max_cycles=80)
+    xm = p.x0.copy()
+    s.solve(p.b, xm)
+    conv, _, _ = orc.mg_solve(g, p.lam, p.fa, p.fk, p.b, p.x0, max_cycles=80, rtol=1e-13)
+    assert rel_dev(xm, conv, p.x0) <= 1e-8
+    s.close()
