@@ -553,6 +553,69 @@ MG_API mg_status mg_residual_norms_noalloc(const mg_grid *grid, const double *la
  * `stream`; the fastest launch gives the rate.  Synchronous. */
 MG_API mg_status mg_fp64_fma_rate(void *stream, int repeats, double *g_fma_per_s);
 
+/* ---------------------------------------------------------------------
+ * Refined-patch (adaptive) grids.  The paper's production grids are coarsened
+ * away from the bubble (Sec. 5.2, the rigid-wall collapse runs); here in its
+ * two-level, block-structured form on 2D Cartesian grids: a uniform base grid
+ * (spacing H, the grid's boundary conditions) and one box of base cells,
+ * box[a][0] <= i < box[a][1] on axis a, refined 2:1 into a patch of spacing
+ * H/2 ((2 * box width) cells per axis).  The unknowns are the patch's cells and
+ * the base cells outside the box; each carries Eqs. 27-28 with its finite-volume
+ * divergence:
+ *   - between two cells of one level, and at the domain boundary: as on a
+ *     uniform grid (walls: no flux; Dirichlet: the value half a cell away);
+ *   - at the coarse-fine interface (a patch side inside the domain), seen from
+ *     a patch cell: c_f (u~ - u_f) / (1.5 h), u~ = u_C + s (u_{C+t} - u_{C-t}) / 8
+ *     the base field at the patch cell's tangential position (C the adjacent
+ *     base cell, t along the interface, s = -1 for the lower, +1 for the upper
+ *     of the two patch cells beside C; outside the domain the base cell's
+ *     wall or Dirichlet ghost), 1.5 h being the distance between the two
+ *     centres;
+ *   - seen from the base cell C: the sum of its two patch faces' fluxes, with
+ *     opposite sign (conservative).
+ * Arrays: base [N_b][..] on the base grid's cells and faces, patch [N_f][..]
+ * on the patch's (cells x-fastest, faces as for mg_set_coeffs), all device
+ * pointers, pairs 16-byte aligned; a base cell under the box is ignored on
+ * input and receives the mean of its four children on output.  FP64; the
+ * calls wait for their work.
+ * ------------------------------------------------------------------------- */
+typedef struct mg_composite mg_composite;
+
+/* grid: the base grid (dim 2, not axisymmetric; walls and Dirichlet sides);
+ * box: base-cell range per axis, non-empty; opt: nu1, nu2 and coarse_min of
+ * the cycles (precision must be MG_FP64; NULL: defaults); stream: cudaStream_t.
+ * Allocates the base grid's hierarchy and the work arrays. */
+MG_API mg_status mg_composite_create(const mg_grid *grid, const int box[2][2], const mg_options *opt, void *stream,
+                                     mg_composite **out);
+
+/* Coefficients (Eqs. 29-32 and face 1/rho, k) of both levels, copied.  The base
+ * hierarchy of the FAC cycle takes the base arrays outside the box and, under
+ * it, the patch's coarsened: a covered cell's l1..l4 the mean of its children's,
+ * each of its faces the mean of its two patch faces. */
+MG_API mg_status mg_composite_set_coeffs(mg_composite *m, const double *lam_b, const double *const fa_b[3],
+                                         const double *const fk_b[3], const double *lam_f,
+                                         const double *const fa_f[3], const double *const fk_f[3]);
+
+/* y = L(x) on the composite grid (with the grid's Dirichlet values); yb of the
+ * covered base cells is 0. */
+MG_API mg_status mg_composite_apply(mg_composite *m, const double *xb, const double *xf, double *yb, double *yf);
+
+/* The paper's defect-correction loop (Sec. 3, after Eq. 34) for L(x) = b,
+ * `cycles` steps, each correction one FAC cycle: nu1 red-black block
+ * Gauss-Seidel sweeps on the patch rows (interface values of the base
+ * correction zero), the patch residual averaged onto the covered base cells
+ * and the valid base cells' residual corrected for the patch's interface
+ * fluxes, one V-cycle of the base hierarchy from zero, its result prolonged
+ * onto the patch (cell-centred bilinear) and added, nu2 sweeps on the patch
+ * rows with the base correction's interface values; then x += the correction
+ * on the valid cells.  norms (nullable, host, 4 * (cycles + 1)): before each
+ * step and after the last, the L2 norms of the T and p residuals over the
+ * valid base cells, then over the patch. */
+MG_API mg_status mg_composite_solve(mg_composite *m, const double *bb, const double *bf, double *xb, double *xf,
+                                    int cycles, double *norms);
+
+MG_API mg_status mg_composite_destroy(mg_composite *m);
+
 /* Moves all later work of the handle to another stream (cudaStream_t on the
  * handle's device).  Waits for the handle's work on its current stream. */
 MG_API mg_status mg_set_stream(mg_handle *h, void *stream);

@@ -78,18 +78,23 @@ static int covered(const orc_cgrid *cg, int I, int J)
 
 /* Value of field `fld` (0 = T, 1 = p) of base cell (I, J), or across the
  * domain boundary its ghost: mirror at a wall, 2 g - u at a Dirichlet side
- * (g = 0 when homogeneous).  (I, J) may be one cell outside along one axis. */
+ * (g = 0 when homogeneous).  (I, J) may be one cell outside along either axis
+ * or both (a corner: the rule of each side in turn, x first). */
 static double base_value(const orc_grid *g, const double *xb, int I, int J, int fld, int homogeneous)
 {
-    int c[3] = {I, J, 0}, ax = -1, side = 0;
-    if (I < 0) { c[0] = 0; ax = 0; side = 0; }
-    if (I >= g->n[0]) { c[0] = g->n[0] - 1; ax = 0; side = 1; }
-    if (J < 0) { c[1] = 0; ax = 1; side = 0; }
-    if (J >= g->n[1]) { c[1] = g->n[1] - 1; ax = 1; side = 1; }
+    int c[3] = {I, J, 0}, out[2] = {-1, -1};
+    if (I < 0) { c[0] = 0; out[0] = 0; }
+    if (I >= g->n[0]) { c[0] = g->n[0] - 1; out[0] = 1; }
+    if (J < 0) { c[1] = 0; out[1] = 0; }
+    if (J >= g->n[1]) { c[1] = g->n[1] - 1; out[1] = 1; }
     double u = xb[2 * cell_id(g, c) + fld];
-    if (ax < 0 || g->bc[ax][side] != BC_DIRICHLET) return u;
-    double gv = homogeneous ? 0.0 : (fld == 0 ? g->bcT[ax][side] : g->bcp[ax][side]);
-    return 2.0 * gv - u;
+    for (int ax = 0; ax < 2; ax++) {
+        int side = out[ax];
+        if (side < 0 || g->bc[ax][side] != BC_DIRICHLET) continue;
+        double gv = homogeneous ? 0.0 : (fld == 0 ? g->bcT[ax][side] : g->bcp[ax][side]);
+        u = 2.0 * gv - u;
+    }
+    return u;
 }
 
 /* u~ of the fine cell (fi, fj) of the patch across its interface side (a, s):

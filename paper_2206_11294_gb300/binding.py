@@ -35,7 +35,8 @@ EXPORTS = ["mg_default_options", "mg_workspace_size", "mg_create", "mg_set_coeff
            "mg_batch_set_tuning", "mg_batch_autotune", "mg_assemble_async", "mg_correct_async",
            "mg_energy_async", "mg_momentum_create", "mg_momentum_set_coeffs", "mg_momentum_apply",
            "mg_momentum_solve", "mg_momentum_destroy", "mg_momentum_rhs_async", "mg_provisional_async",
-           "mg_fp64_fma_rate", "mg_solve_async", "mg_solve_async_stats"]
+           "mg_fp64_fma_rate", "mg_solve_async", "mg_solve_async_stats", "mg_composite_create",
+           "mg_composite_set_coeffs", "mg_composite_apply", "mg_composite_solve", "mg_composite_destroy"]
 
 MG_MAX_LEVELS = 32
 MG_SWEEP_COLOUR, MG_SWEEP_FUSED, MG_SWEEP_ASYNC, MG_SWEEP_COLOUR2 = 1, 2, 3, 4
@@ -204,6 +205,12 @@ def load(path: str = LIB_PATH):
             "mg_fp64_fma_rate": ([P, C.c_int, dp], C.c_int),
             "mg_solve_async": ([P, P, P, P], C.c_int),
             "mg_solve_async_stats": ([P, C.POINTER(MgStats)], C.c_int),
+            "mg_composite_create": ([C.POINTER(MgGrid), (C.c_int * 2) * 2, C.POINTER(MgOptions), P, C.POINTER(P)],
+                                    C.c_int),
+            "mg_composite_set_coeffs": ([P, P, pa3, pa3, P, pa3, pa3], C.c_int),
+            "mg_composite_apply": ([P, P, P, P, P], C.c_int),
+            "mg_composite_solve": ([P, P, P, P, P, C.c_int, dp], C.c_int),
+            "mg_composite_destroy": ([P], C.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -767,3 +774,74 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+class Composite:
+    """mg_composite: a refined-patch (adaptive) grid, base grid plus one 2:1 box."""
+
+    def __init__(self, grid, box, nu1=2, nu2=2, coarse_min=4, device: Optional[int] = None, stream=None):
+        import torch
+        lib = load()
+        self._lib = lib
+        self.grid = make_grid(grid)
+        self.box = tuple(tuple(int(v) for v in box[a]) for a in range(2))
+        dev = torch.cuda.current_device() if device is None else int(device)
+        self.device = dev
+        check(lib.mg_set_device(dev))
+        if stream is None:
+            stream = torch.cuda.current_stream(dev)
+        self.stream = stream
+        o = make_options("fp64", 0.0, 1, nu1, nu2, coarse_min)
+        b = ((C.c_int * 2) * 2)(*[(C.c_int * 2)(*self.box[a]) for a in range(2)])
+        h = C.c_void_p()
+        check(lib.mg_composite_create(C.byref(self.grid), b, C.byref(o), C.c_void_p(stream.cuda_stream), C.byref(h)))
+        self._h = h
+        self.Nb = self.grid.n[0] * self.grid.n[1]
+        self.m = (2 * (self.box[0][1] - self.box[0][0]), 2 * (self.box[1][1] - self.box[1][0]))
+        self.Nf = self.m[0] * self.m[1]
+
+    @staticmethod
+    def _dev(a):
+        import torch
+        if _is_torch(a) and a.is_cuda:
+            return a
+        return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+    def set_coeffs(self, lam_b, fa_b, fk_b, lam_f, fa_f, fk_f):
+        d = self._dev
+        self._keep = [d(lam_b), [d(f) for f in fa_b], [d(f) for f in fk_b], d(lam_f), [d(f) for f in fa_f],
+                      [d(f) for f in fk_f]]
+        lb, fab, fkb, lf, faf, fkf = self._keep
+        arr = lambda fs: (C.c_void_p * 3)(*[C.c_void_p(f.data_ptr()) for f in fs], None)
+        check(self._lib.mg_composite_set_coeffs(self._h, C.c_void_p(lb.data_ptr()), arr(fab), arr(fkb),
+                                                C.c_void_p(lf.data_ptr()), arr(faf), arr(fkf)))
+
+    def apply(self, xb, xf):
+        import torch
+        xb, xf = self._dev(xb), self._dev(xf)
+        yb, yf = torch.empty_like(xb), torch.empty_like(xf)
+        check(self._lib.mg_composite_apply(self._h, C.c_void_p(xb.data_ptr()), C.c_void_p(xf.data_ptr()),
+                                           C.c_void_p(yb.data_ptr()), C.c_void_p(yf.data_ptr())))
+        return yb, yf
+
+    def solve(self, bb, bf, xb, xf, cycles: int, norms: bool = True):
+        """xb, xf: CUDA tensors solved in place (numpy arrays: copies returned).
+        Returns (xb, xf, norms [cycles + 1, 4] or None)."""
+        bb, bf, xb, xf = self._dev(bb), self._dev(bf), self._dev(xb), self._dev(xf)
+        h = np.zeros(4 * (cycles + 1)) if norms else None
+        check(self._lib.mg_composite_solve(self._h, C.c_void_p(bb.data_ptr()), C.c_void_p(bf.data_ptr()),
+                                           C.c_void_p(xb.data_ptr()), C.c_void_p(xf.data_ptr()), int(cycles),
+                                           h.ctypes.data_as(C.POINTER(C.c_double)) if norms else None))
+        return xb, xf, (h.reshape(-1, 4) if norms else None)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.mg_composite_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+

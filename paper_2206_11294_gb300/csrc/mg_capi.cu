@@ -960,6 +960,22 @@ bool converged(const double n0[2], const double nk[2], double rtol) {
     return true;
 }
 
+// The coarsest inverse above kBandSmemMax unknowns takes the windowed LU and
+// the block-column inverse when the band's window and the inverse's staging
+// fit a block's shared memory and the factors fit the n x n work array;
+// otherwise the three global-memory kernels.
+int inv_block_warps(int n, int kl) {
+    for (int w = 8; w > 1; w /= 2)
+        if (band_inv_block_smem(n, kl, kl, w) <= kWinSmemMax) return w;
+    return 1;
+}
+
+bool window_path(int n, int kl) {
+    return n > kBandSmemMax && band_window_smem(kl, kl) <= kWinSmemMax &&
+           band_inv_block_smem(n, kl, kl, inv_block_warps(n, kl)) <= kWinSmemMax &&
+           (long long)n * (kl + 2LL * kl + 1) <= (long long)n * n;
+}
+
 // ---------------------------------------------------------------- set-up
 SetupOut setup_out(const LevelBuf &l, bool mixed) {
     SetupOut o;
@@ -1123,6 +1139,18 @@ mg_status setup_hierarchy(mg_handle *h, const double *lam, const double *const f
         k_band_inv_cols_warp<<<(h->nc + 31) / 32, dim3(32, kInvRows), smem_inv,
                                a>>>(h->Mtmp, h->piv, h->dinv, h->nc, kl, kl, h->Minv, mixed ? h->Minv32 : nullptr,
                                     h->err_d);
+    } else if (window_path(h->nc, kl)) {
+        // the band's active window in shared memory, then the columns of the inverse, a warp each
+        const long long wsm = band_window_smem(kl, kl);
+        const int warps = inv_block_warps(h->nc, kl);
+        const long long ism = band_inv_block_smem(h->nc, kl, kl, warps);
+        CK(raise_smem_limit((const void *)k_band_lu_window, (int)wsm));
+        CK(raise_smem_limit((const void *)k_band_inv_block, (int)ism));
+        double *Lb = h->Mwork, *Uc = h->Mwork + (long long)h->nc * kl;
+        k_band_lu_window<<<1, kWinThreads, (size_t)wsm, a>>>(h->Mtmp, h->nc, kl, kl, h->piv, h->dinv, Lb, Uc,
+                                                             h->err_d);
+        k_band_inv_block<<<(h->nc + warps - 1) / warps, 32 * warps, (size_t)ism, a>>>(
+            Lb, Uc, h->piv, h->dinv, h->nc, kl, kl, h->Minv, mixed ? h->Minv32 : nullptr, h->err_d);
     } else {
         k_band_lu<<<1, dim3(32, 32, 1), 0, a>>>(h->Mtmp, h->nc, kl, kl, h->piv, h->dinv, h->err_d);
         k_band_inv_cols<<<(h->nc + 127) / 128, 128, 0, a>>>(h->Mtmp, h->piv, h->dinv, h->nc, kl, kl, h->Mwork,
@@ -1134,7 +1162,7 @@ mg_status setup_hierarchy(mg_handle *h, const double *lam, const double *const f
     }
     CK(cudaGetLastError());
     CK(cudaEventRecord(h->ev_inv, a));
-    counted(h, h->nc <= kBandSmemMax ? 2 : 4);
+    counted(h, h->nc <= kBandSmemMax || window_path(h->nc, kl) ? 2 : 4);
     // flags 1 and 2 come from the level kernels, which precede this copy on
     // the stream (the inverse on the private stream keeps running)
     CK(cudaMemcpyAsync(h->errh, h->err_d, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -2122,6 +2150,7 @@ mg_status mg_destroy(mg_handle *h) {
 }
 
 #include "mg_momentum_api.cuh"
+#include "mg_composite_api.cuh"
 
 const char *mg_last_error(void) { return g_err.c_str(); }
 

@@ -214,3 +214,22 @@ def test_second_order_convergence():
         errs.append(max(np.abs(xb[~cov] - ub[~cov]).max(), np.abs(xf - uf).max()))
     order = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
     assert np.all(order >= 1.8), (errs, order)
+
+
+def test_fac_with_the_patch_in_a_dirichlet_corner():
+    """The patch in the corner of two Dirichlet sides: the prolongation's
+    stencil reaches across both (odd ghosts in turn); FAC still reaches the
+    dense solution."""
+    bc = ((D, W), (D, W), (0, 0))
+    bcT = ((305.0, 0.0), (295.0, 0.0), (0.0, 0.0))
+    bcp = ((1.05e5, 0.0), (0.98e5, 0.0), (0.0, 0.0))
+    b, p, box = I.composite_bubble(16, box=((0, 8), (0, 10)), seed=12, n_bubbles=1, rmin=0.1, rmax=0.15,
+                                   length=6.4e-3, dt=1e-5, bc=bc, bcT=bcT, bcp=bcp)
+    assert p.grid.bc[0][0] == D and p.grid.bc[1][0] == D
+    gd = b.grid.as_dict()
+    xd_b, xd_f = cf.dense_solve(gd, box, b.lam, b.fa, b.fk, p.lam, p.fa, p.fk, b.b, p.b)
+    xb, xf, hist = cf.fac_solve(gd, box, b.lam, b.fa, b.fk, p.lam, p.fa, p.fk, b.b, p.b, b.x0, p.x0, 40,
+                                coarse_min=2)
+    for f in range(2):
+        dev = np.abs(xd_f[:, f] - p.x0[:, f]).max()
+        assert np.abs(xf[:, f] - xd_f[:, f]).max() <= 1e-9 * dev
