@@ -131,7 +131,7 @@ class Engine:
     that shape through a shared autotune.TuningTable (optionally a file)."""
 
     def __init__(self, device: int = 0, precision: str = "mixed", rtol: float = 1e-10, max_cycles: int = 60,
-                 tune: bool = False, tuning_table=None):
+                 tune: bool = False, tuning_table=None, batch_min: int = 4):
         import torch
         from . import binding
         self.torch = torch
@@ -141,6 +141,9 @@ class Engine:
         self.rtol = rtol
         self.max_cycles = max_cycles
         self.tune = tune
+        # a group of fewer requests runs as solo solves: building an mg_batch
+        # (its tables, its cycle graph) costs more than it saves for a few
+        self.batch_min = max(2, int(batch_min))
         self.table = tuning_table
         self._tuned = set()
         self._tune_lock = threading.Lock()
@@ -213,8 +216,8 @@ class Engine:
                         self._tuned.add(id(s))
                 bs.append(T(h["b"]))
                 xs.append(T(h["x0"]))
-            if len(solvers) == 1:
-                stats = [solvers[0].solve(bs[0], xs[0], allow_not_converged=True)]
+            if len(solvers) < self.batch_min:
+                stats = [s.solve(b, x, allow_not_converged=True) for s, b, x in zip(solvers, bs, xs)]
             else:
                 batch = self.binding.Batch(solvers)
                 try:
@@ -352,7 +355,7 @@ class Server:
                 for q, r in enumerate(taken):
                     self.log.append(dict(rid=r.rid, latency=done - r.arrival, queued=r.admitted - r.arrival,
                                          batch=len(taken), slot=slot, ok=err is None,
-                                         cells=int(r.problem.grid.N)))
+                                         cells=int(r.problem.grid.N), dim=int(r.problem.grid.dim)))
                 self.lock.notify_all()
             for q, r in enumerate(taken):
                 if err is None:
@@ -375,11 +378,15 @@ class Server:
             lat = sorted(e["latency"] for e in self.log if e["ok"])
             if not lat:
                 return {}
-            pick = lambda q: lat[min(len(lat) - 1, int(round(q * (len(lat) - 1))))]
-            return dict(requests=len(lat), p50_ms=pick(0.5) * 1e3, p99_ms=pick(0.99) * 1e3,
-                        mean_batch=sum(e["batch"] for e in self.log) / len(self.log),
-                        peak_bytes=self.cache.peak, evictions=self.cache.evictions,
-                        hierarchies_created=self.cache.created, hierarchies_reused=self.cache.reused)
+            pick = lambda v, q: v[min(len(v) - 1, int(round(q * (len(v) - 1))))]
+            out = dict(requests=len(lat), p50_ms=pick(lat, 0.5) * 1e3, p99_ms=pick(lat, 0.99) * 1e3,
+                       mean_batch=sum(e["batch"] for e in self.log) / len(self.log),
+                       peak_bytes=self.cache.peak, evictions=self.cache.evictions,
+                       hierarchies_created=self.cache.created, hierarchies_reused=self.cache.reused)
+            for d in sorted({e.get("dim") for e in self.log if e["ok"] and e.get("dim")}):
+                v = sorted(e["latency"] for e in self.log if e["ok"] and e.get("dim") == d)
+                out[f"by_dim_{d}"] = dict(requests=len(v), p50_ms=pick(v, 0.5) * 1e3, p99_ms=pick(v, 0.99) * 1e3)
+            return out
 
 
 def poisson_arrivals(rate: float, count: int, seed: int) -> List[float]:

@@ -61,7 +61,7 @@ def test_served_results_equal_solo(precision, tune, pool_oracle):
         st = s.solve(p.b, x)
         solo[p.name] = (x, st)
         s.close()
-    eng = Engine(device=0, precision=precision, rtol=1e-10, max_cycles=60, tune=tune)
+    eng = Engine(device=0, precision=precision, rtol=1e-10, max_cycles=60, tune=tune, batch_min=2)
     sizes = {p.name: eng.size(p) for p in pool}
     budget = int(0.6 * sum(sizes.values()))          # forces waiting and eviction
     srv = Server(eng, hbm_budget=budget, slots=3, max_batch=4)
