@@ -319,7 +319,7 @@ def bubbles_1024(n: int = 1024, seed: int = 2, length: float = 1.0, dt: float = 
 
 def composite_bubble(n: int = 64, box=None, seed: int = 9, n_bubbles: int = 2, rmin: float = 0.06,
                      rmax: float = 0.12, length: float = 1.0, dt: float = 1e-7, bc=None, bcT=None, bcp=None,
-                     name: str = ""):
+                     name: str = "", centres=None, radii=None):
     """A refined-patch (adaptive) grid around bubbles: (base, patch, box).
 
     base: the n x n grid of spacing length / n over the whole domain, its
@@ -329,7 +329,8 @@ def composite_bubble(n: int = 64, box=None, seed: int = 9, n_bubbles: int = 2, r
     cut from the same field assembled on the 2n x 2n grid of the whole domain
     (its grid's origin at the box's corner).  The bubbles stay inside the box,
     so the base cells outside it are pure liquid, as on a grid coarsened away
-    from the bubble."""
+    from the bubble.  centres, radii (fractions of the domain): given bubbles
+    instead of seeded ones."""
     rng = np.random.default_rng(seed)
     bc = bc or _walls(2)
     bcT = bcT or ((0.0, 0.0),) * 3
@@ -337,7 +338,11 @@ def composite_bubble(n: int = 64, box=None, seed: int = 9, n_bubbles: int = 2, r
     H = length / n
     gb = Grid(dim=2, axisym=0, n=(n, n, 1), h=H, bc=bc, bcT=bcT, bcp=bcp)
     gf = Grid(dim=2, axisym=0, n=(2 * n, 2 * n, 1), h=H / 2, bc=bc, bcT=bcT, bcp=bcp)
-    centres, radii = _place_bubbles(rng, n_bubbles, rmin * length, rmax * length, 2, (length, length))
+    if centres is None:
+        centres, radii = _place_bubbles(rng, n_bubbles, rmin * length, rmax * length, 2, (length, length))
+    else:
+        centres = [[c[0] * length, c[1] * length] for c in centres]
+        radii = [r * length for r in radii]
     if box is None:
         lo = [min(c[a] - r for c, r in zip(centres, radii)) for a in range(2)]
         hi = [max(c[a] + r for c, r in zip(centres, radii)) for a in range(2)]
