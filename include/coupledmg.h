@@ -614,10 +614,20 @@ MG_API mg_status mg_composite_apply(mg_composite *m, const double *xb, const dou
 MG_API mg_status mg_composite_solve(mg_composite *m, const double *bb, const double *bf, double *xb, double *xf,
                                     int cycles, double *norms);
 
+/* Measures and applies the kernel choices of the base grid's hierarchy, as
+ * mg_autotune does for a handle (every choice runs the same arithmetic, so
+ * later solves give the same result bit for bit).  Needs coefficients.
+ * vcycle_ms (nullable, host): the chosen V-cycle's time.  Waits for its
+ * work. */
+MG_API mg_status mg_composite_autotune(mg_composite *m, int reps, double *vcycle_ms);
+
 MG_API mg_status mg_composite_destroy(mg_composite *m);
 
 /* Moves all later work of the handle to another stream (cudaStream_t on the
- * handle's device).  Waits for the handle's work on its current stream. */
+ * handle's device).  The new stream waits, on the device, for the work that
+ * the handle's last mg_set_coeffs or mg_solve_async left running (the other
+ * calls finish theirs before returning); the call does not block the host and
+ * does not wait for later work of other handles on the old stream. */
 MG_API mg_status mg_set_stream(mg_handle *h, void *stream);
 
 /* Makes `device` the CUDA device this thread's later mg_create calls use

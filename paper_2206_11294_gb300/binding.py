@@ -36,7 +36,8 @@ EXPORTS = ["mg_default_options", "mg_workspace_size", "mg_create", "mg_set_coeff
            "mg_energy_async", "mg_momentum_create", "mg_momentum_set_coeffs", "mg_momentum_apply",
            "mg_momentum_solve", "mg_momentum_destroy", "mg_momentum_rhs_async", "mg_provisional_async",
            "mg_fp64_fma_rate", "mg_solve_async", "mg_solve_async_stats", "mg_composite_create",
-           "mg_composite_set_coeffs", "mg_composite_apply", "mg_composite_solve", "mg_composite_destroy"]
+           "mg_composite_set_coeffs", "mg_composite_apply", "mg_composite_solve", "mg_composite_autotune",
+           "mg_composite_destroy"]
 
 MG_MAX_LEVELS = 32
 MG_SWEEP_COLOUR, MG_SWEEP_FUSED, MG_SWEEP_ASYNC, MG_SWEEP_COLOUR2 = 1, 2, 3, 4
@@ -210,6 +211,7 @@ def load(path: str = LIB_PATH):
             "mg_composite_set_coeffs": ([P, P, pa3, pa3, P, pa3, pa3], C.c_int),
             "mg_composite_apply": ([P, P, P, P, P], C.c_int),
             "mg_composite_solve": ([P, P, P, P, P, C.c_int, dp], C.c_int),
+            "mg_composite_autotune": ([P, C.c_int, dp], C.c_int),
             "mg_composite_destroy": ([P], C.c_int),
         }
         for name, (args, res) in sig.items():
@@ -833,6 +835,12 @@ class Composite:
                                            C.c_void_p(xb.data_ptr()), C.c_void_p(xf.data_ptr()), int(cycles),
                                            h.ctypes.data_as(C.POINTER(C.c_double)) if norms else None))
         return xb, xf, (h.reshape(-1, 4) if norms else None)
+
+    def autotune(self, reps: int = 5) -> float:
+        """Kernel choices of the base hierarchy (mg_composite_autotune); returns the V-cycle's ms."""
+        ms = C.c_double(0.0)
+        check(self._lib.mg_composite_autotune(self._h, int(reps), C.byref(ms)))
+        return ms.value
 
     def close(self):
         if getattr(self, "_h", None):

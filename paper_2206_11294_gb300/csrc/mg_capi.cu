@@ -118,6 +118,7 @@ struct mg_handle {
     cudaStream_t aux;      // private stream: the coarsest inverse, overlapping the solve's start
     cudaEvent_t ev_asm;    // coarsest matrix assembled (main stream)
     cudaEvent_t ev_inv;    // coarsest inverse ready (aux stream); cycle graphs wait on it
+    cudaEvent_t ev_last;   // end of the last call that returned with work pending on the stream
     int *errh;             // pinned host copy of err_d
     long long jcells;      // finest-level cells whose 2x2 block the FP32 cycles apply in FP64 (last set-up)
     int nlev;
@@ -906,9 +907,9 @@ mg_status x_out(mg_handle *h, double *x, int on_device) {
 }
 
 template <int DIM>
-void enqueue_prep(mg_handle *h, const double2 *rhs) {
+void enqueue_prep(mg_handle *h, const double2 *rhs, cudaStream_t s) {
     const LevelBuf &f = h->L[0];
-    k_prep_rhs<DIM><<<cell_grid(f, DIM, f.n[0]), kBlock, 0, h->stream>>>(view<double>(f), rhs, bc_vals(h->grid),
+    k_prep_rhs<DIM><<<cell_grid(f, DIM, f.n[0]), kBlock, 0, s>>>(view<double>(f), rhs, bc_vals(h->grid),
                                                                           h->grid.axisym, h->grid.r0, h->grid.h);
     counted(h);
 }
@@ -918,8 +919,8 @@ mg_status prep(mg_handle *h, const double *rhs, const double *x, int on_device) 
     mg_status st = pair_in(h, rhs, on_device, &r);
     if (st) return st;
     if ((st = x_in(h, x, on_device))) return st;
-    if (h->grid.dim == 2) enqueue_prep<2>(h, r);
-    else enqueue_prep<3>(h, r);
+    if (h->grid.dim == 2) enqueue_prep<2>(h, r, h->stream);
+    else enqueue_prep<3>(h, r, h->stream);
     CK(cudaGetLastError());
     return MG_OK;
 }
@@ -1270,10 +1271,23 @@ mg_status correction_cycles(mg_handle *h, const double2 *rhs) {
     }
     const LevelBuf &f = h->L[0];
     CK(cudaMemsetAsync(f.x, 0, sizeof(double2) * f.N, h->stream));
-    enqueue_prep<DIM>(h, rhs);
+    enqueue_prep<DIM>(h, rhs, h->stream);
     CK(cudaGetLastError());
     CK(cudaGraphLaunch(h->gcorr, h->stream));
     h->enq += h->graph_kernels_corr;
+    return MG_OK;
+}
+
+// The same correction enqueued on stream s without a graph of its own (for
+// a caller that captures it into its graph): x = 0, the prepared right-hand
+// side rhs, max_cycles FP64 cycles without norms.
+template <int DIM>
+mg_status enqueue_correction(mg_handle *h, cudaStream_t s, const double2 *rhs) {
+    const LevelBuf &f = h->L[0];
+    CK(cudaMemsetAsync(f.x, 0, sizeof(double2) * f.N, s));
+    enqueue_prep<DIM>(h, rhs, s);
+    for (int q = 0; q < h->opt.max_cycles; q++) enqueue_vcycle<double, DIM>(h, s, 0, h->opt.cycle);
+    CK(cudaGetLastError());
     return MG_OK;
 }
 
@@ -1616,6 +1630,7 @@ mg_status mg_create(const mg_grid *grid, const mg_options *opt, void *workspace,
         cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&h->ev_asm, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&h->ev_inv, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_last, cudaEventDisableTiming) != cudaSuccess ||
         cudaMallocHost(&h->errh, 4 * sizeof(int)) != cudaSuccess ||
         cudaMallocHost(&h->norms_h, 8 * sizeof(double)) != cudaSuccess ||
         cudaMemsetAsync(h->ticket, 0, sizeof(unsigned int), h->stream) != cudaSuccess ||
@@ -1648,6 +1663,9 @@ mg_status mg_set_coeffs(mg_handle *h, const double *lambda, const double *const 
     h->coeffs_set = false;
     st = h->grid.dim == 2 ? setup_hierarchy<2>(h, lambda, face_alpha, face_k, on_device)
                           : setup_hierarchy<3>(h, lambda, face_alpha, face_k, on_device);
+    // the set-up is still running: mg_set_stream orders the next stream after it
+    const cudaError_t e = cudaEventRecord(h->ev_last, h->stream);
+    if (st == MG_OK && e != cudaSuccess) return fail(MG_ERR_CUDA, std::string("set-up: ") + cudaGetErrorString(e));
     if (st == MG_OK) h->coeffs_set = true;
     return st;
 }
@@ -1704,6 +1722,7 @@ mg_status mg_solve_async(mg_handle *h, const double *rhs, double *x, void *event
     CK(cudaMemcpyAsync(h->errh, h->err_d, 2 * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaEventRecord(h->ev_a1, h->stream));
     if (event) CK(cudaEventRecord(reinterpret_cast<cudaEvent_t>(event), h->stream));
+    CK(cudaEventRecord(h->ev_last, h->stream));
     h->async_pending = true;
     return MG_OK;
 }
@@ -2099,8 +2118,13 @@ mg_status mg_set_stream(mg_handle *h, void *stream) {
     mg_status st = check_handle(h, false);
     if (st) return st;
     DeviceGuard dg(h->device);
-    CK(cudaStreamSynchronize(h->stream));
-    h->stream = reinterpret_cast<cudaStream_t>(stream);
+    // Only mg_set_coeffs and mg_solve_async return with the handle's work
+    // still running; the new stream waits (on the device) for the end of the
+    // last of them.  The old stream's later work, another handle's, is not
+    // waited for, and the host does not block.
+    const cudaStream_t next = reinterpret_cast<cudaStream_t>(stream);
+    CK(cudaStreamWaitEvent(next, h->ev_last, 0));
+    h->stream = next;
     return MG_OK;
 }
 
@@ -2138,6 +2162,7 @@ mg_status mg_destroy(mg_handle *h) {
     if (h->astat_h) cudaFreeHost(h->astat_h);
     if (h->ev_asm) cudaEventDestroy(h->ev_asm);
     if (h->ev_inv) cudaEventDestroy(h->ev_inv);
+    if (h->ev_last) cudaEventDestroy(h->ev_last);
     if (h->errh) cudaFreeHost(h->errh);
     for (int q = 0; q < 2; q++)
         if (h->ev[q]) cudaEventDestroy(h->ev[q]);

@@ -35,6 +35,12 @@ struct CfGeom {
     int dir[2][2];         // Dirichlet side (1) or wall (0), per axis and side
     double gT[2][2], gp[2][2];   // Dirichlet values (zero for the correction problems)
     int iface[2][2];       // patch side inside the domain (1): a coarse-fine interface
+    // the flux factors, as reciprocals (the kernels multiply; FP64 division
+    // is a long instruction sequence on this GPU): patch faces between two
+    // patch cells 1/h^2, at the interface 1/(1.5 h^2), at a Dirichlet side
+    // 1/(0.5 h^2); base faces 1/H^2, 1/(0.5 H^2), and the base side of the
+    // interface 1/(1.5 H^2) (two fine faces of length h over the area H^2)
+    double rh2, rif, rdf, rH2, rdb, rbif;
 };
 
 struct CfCoef {            // physical coefficients of both levels
@@ -89,13 +95,12 @@ __device__ __forceinline__ double2 cf_ghost(const CfGeom &g, const double2 *__re
     const double2 uc = cf_base_value(g, xb, C[0], C[1]);
     const double2 up = cf_base_value(g, xb, Cp[0], Cp[1]);
     const double2 um = cf_base_value(g, xb, Cm[0], Cm[1]);
-    return make_double2(uc.x + sgn * (up.x - um.x) / 8.0, uc.y + sgn * (up.y - um.y) / 8.0);
+    return make_double2(uc.x + sgn * (up.x - um.x) * 0.125, uc.y + sgn * (up.y - um.y) * 0.125);
 }
 
 // div(k grad T), div((1/rho) grad p) of valid base cell (I, J).
 __device__ __forceinline__ void cf_base_div(const CfGeom &g, const CfCoef &k, const double2 *__restrict__ xb,
                                             const double2 *__restrict__ xf, int I, int J, double &lapT, double &lapp) {
-    const double H = g.H;
     const double2 u = xb[I + (long long)g.n0 * J];
     lapT = 0.0;
     lapp = 0.0;
@@ -121,18 +126,18 @@ __device__ __forceinline__ void cf_base_div(const CfGeom &g, const CfCoef &k, co
                     const long long fid = cf_fface(g, a, fface[0], fface[1]);
                     const double2 uf = xf[ff[0] + (long long)g.m0 * ff[1]];
                     const double2 gu = cf_ghost(g, xb, a, side, ff[0], ff[1]);
-                    lapT += (0.5 * H) * k.fkf[a][fid] * (uf.x - gu.x) / (1.5 * 0.5 * H) / (H * H);
-                    lapp += (0.5 * H) * k.faf[a][fid] * (uf.y - gu.y) / (1.5 * 0.5 * H) / (H * H);
+                    lapT += k.fkf[a][fid] * (uf.x - gu.x) * g.rbif;
+                    lapp += k.faf[a][fid] * (uf.y - gu.y) * g.rbif;
                 }
             } else if (inside) {
                 const long long fid = cf_bface(g, a, I + (a == 0 ? s : 0), J + (a == 1 ? s : 0));
                 const double2 un = xb[nb[0] + (long long)g.n0 * nb[1]];
-                lapT += k.fkb[a][fid] * (un.x - u.x) / (H * H);
-                lapp += k.fab[a][fid] * (un.y - u.y) / (H * H);
+                lapT += k.fkb[a][fid] * (un.x - u.x) * g.rH2;
+                lapp += k.fab[a][fid] * (un.y - u.y) * g.rH2;
             } else if (g.dir[a][s]) {
                 const long long fid = cf_bface(g, a, I + (a == 0 ? s : 0), J + (a == 1 ? s : 0));
-                lapT += k.fkb[a][fid] * (g.gT[a][s] - u.x) / (0.5 * H * H);
-                lapp += k.fab[a][fid] * (g.gp[a][s] - u.y) / (0.5 * H * H);
+                lapT += k.fkb[a][fid] * (g.gT[a][s] - u.x) * g.rdb;
+                lapp += k.fab[a][fid] * (g.gp[a][s] - u.y) * g.rdb;
             }
         }
 }
@@ -142,7 +147,6 @@ __device__ __forceinline__ void cf_base_div(const CfGeom &g, const CfCoef &k, co
 __device__ __forceinline__ void cf_fine_div(const CfGeom &g, const CfCoef &k, const double2 *__restrict__ xb,
                                             const double2 *__restrict__ xf, int i, int j, double &lapT, double &lapp,
                                             double &sk, double &sa) {
-    const double h = g.h;
     const double2 u = xf[i + (long long)g.m0 * j];
     lapT = lapp = sk = sa = 0.0;
 #pragma unroll
@@ -156,21 +160,21 @@ __device__ __forceinline__ void cf_fine_div(const CfGeom &g, const CfCoef &k, co
             const double ck = k.fkf[a][fid], ca = k.faf[a][fid];
             if (nb[a] >= 0 && nb[a] < ma) {
                 const double2 un = xf[nb[0] + (long long)g.m0 * nb[1]];
-                lapT += ck * (un.x - u.x) / (h * h);
-                lapp += ca * (un.y - u.y) / (h * h);
-                sk += ck / (h * h);
-                sa += ca / (h * h);
+                lapT += ck * (un.x - u.x) * g.rh2;
+                lapp += ca * (un.y - u.y) * g.rh2;
+                sk += ck * g.rh2;
+                sa += ca * g.rh2;
             } else if (g.iface[a][s]) {
                 const double2 gu = cf_ghost(g, xb, a, s, i, j);
-                lapT += ck * (gu.x - u.x) / (1.5 * h * h);
-                lapp += ca * (gu.y - u.y) / (1.5 * h * h);
-                sk += ck / (1.5 * h * h);
-                sa += ca / (1.5 * h * h);
+                lapT += ck * (gu.x - u.x) * g.rif;
+                lapp += ca * (gu.y - u.y) * g.rif;
+                sk += ck * g.rif;
+                sa += ca * g.rif;
             } else if (g.dir[a][s]) {
-                lapT += ck * (g.gT[a][s] - u.x) / (0.5 * h * h);
-                lapp += ca * (g.gp[a][s] - u.y) / (0.5 * h * h);
-                sk += ck / (0.5 * h * h);
-                sa += ca / (0.5 * h * h);
+                lapT += ck * (g.gT[a][s] - u.x) * g.rdf;
+                lapp += ca * (g.gp[a][s] - u.y) * g.rdf;
+                sk += ck * g.rdf;
+                sa += ca * g.rdf;
             }
         }
 }
@@ -230,8 +234,8 @@ __global__ void __launch_bounds__(256) k_cf_rbgs_fine(CfGeom g, CfCoef k, const 
     const double D0 = l[0] - sk, D1 = l[1], D2 = -l[3] * sk, D3 = l[2] - sa;
     const double s0 = rhs[c].x - (e0 - (D0 * u.x + D1 * u.y));
     const double s1 = rhs[c].y - (e1 - (D2 * u.x + D3 * u.y));
-    const double det = D0 * D3 - D1 * D2;
-    xf[c] = make_double2((D3 * s0 - D1 * s1) / det, (D0 * s1 - D2 * s0) / det);
+    const double rdet = 1.0 / (D0 * D3 - D1 * D2);
+    xf[c] = make_double2((D3 * s0 - D1 * s1) * rdet, (D0 * s1 - D2 * s0) * rdet);
 }
 
 // The base correction problem's right-hand side: valid cells the composite
@@ -244,7 +248,6 @@ __global__ void __launch_bounds__(256) k_cf_base_rhs(CfGeom g, CfCoef k, const d
     const int I = blockIdx.x * blockDim.x + threadIdx.x, J = blockIdx.y * blockDim.y + threadIdx.y;
     if (I >= g.n0 || J >= g.n1) return;
     const long long c = I + (long long)g.n0 * J;
-    const double H = g.H;
     if (cf_covered(g, I, J)) {
         double s0 = 0.0, s1 = 0.0;
 #pragma unroll
@@ -253,7 +256,7 @@ __global__ void __launch_bounds__(256) k_cf_base_rhs(CfGeom g, CfCoef k, const d
             s0 += sf[f].x;
             s1 += sf[f].y;
         }
-        sb[c] = make_double2(s0 / 4.0, s1 / 4.0);
+        sb[c] = make_double2(s0 * 0.25, s1 * 0.25);
         return;
     }
     double tT = 0.0, tp = 0.0;
@@ -277,20 +280,24 @@ __global__ void __launch_bounds__(256) k_cf_base_rhs(CfGeom g, CfCoef k, const d
                 fface[a] += side;
                 const long long fid = cf_fface(g, a, fface[0], fface[1]);
                 const double2 d = df[ff[0] + (long long)g.m0 * ff[1]];
-                tT += (0.5 * H) * k.fkf[a][fid] * d.x / (1.5 * 0.5 * H) / (H * H);
-                tp += (0.5 * H) * k.faf[a][fid] * d.y / (1.5 * 0.5 * H) / (H * H);
+                tT += k.fkf[a][fid] * d.x * g.rbif;
+                tp += k.faf[a][fid] * d.y * g.rbif;
             }
         }
     const double oT = tT, op = tp + k.lamb[4 * c + 3] * tT;
     sb[c] = make_double2(rb[c].x - oT, rb[c].y - op);
 }
 
-// Patch correction += bilinear prolongation of the base correction db (the
-// fine cells' positions in the whole domain; homogeneous ghosts outside it).
-__global__ void __launch_bounds__(256) k_cf_prolong(CfGeom g, const double2 *__restrict__ db,
-                                                    double2 *__restrict__ df) {
+// After the base correction db: the patch correction df += its bilinear
+// prolongation (the fine cells' positions in the whole domain; homogeneous
+// ghosts outside it), and out = rf minus what db adds to the patch rows
+// through the interface ghosts (the p-row's l4 div(k grad T) included).
+__global__ void __launch_bounds__(256) k_cf_prolong_ghost(CfGeom g, CfCoef k, const double2 *__restrict__ db,
+                                                          const double2 *__restrict__ rf, double2 *__restrict__ df,
+                                                          double2 *__restrict__ out) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
     if (i >= g.m0 || j >= g.m1) return;
+    const long long c = i + (long long)g.m0 * j;
     const int gi = 2 * g.b0[0] + i, gj = 2 * g.b0[1] + j;
     const int P[2] = {gi / 2, gj / 2};
     const int sg[2] = {(gi & 1) ? 1 : -1, (gj & 1) ? 1 : -1};
@@ -312,18 +319,7 @@ __global__ void __launch_bounds__(256) k_cf_prolong(CfGeom g, const double2 *__r
         aT += w * v.x;
         ap += w * v.y;
     }
-    const long long c = i + (long long)g.m0 * j;
     df[c] = make_double2(df[c].x + aT, df[c].y + ap);
-}
-
-// out = rf minus what the base correction db adds to the patch rows through
-// the interface ghosts (the p-row's l4 div(k grad T) included).
-__global__ void __launch_bounds__(256) k_cf_ghost_rhs(CfGeom g, CfCoef k, const double2 *__restrict__ rf,
-                                                      const double2 *__restrict__ db, double2 *__restrict__ out) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
-    if (i >= g.m0 || j >= g.m1) return;
-    const long long c = i + (long long)g.m0 * j;
-    const double h = g.h;
     double gT = 0.0, gp = 0.0;
     const int pos[2] = {i, j};
 #pragma unroll
@@ -335,11 +331,10 @@ __global__ void __launch_bounds__(256) k_cf_ghost_rhs(CfGeom g, CfCoef k, const 
             if ((s == 0 && pos[a] != 0) || (s == 1 && pos[a] != ma - 1)) continue;
             const long long fid = cf_fface(g, a, i + (a == 0 ? s : 0), j + (a == 1 ? s : 0));
             const double2 gu = cf_ghost(g, db, a, s, i, j);
-            gT += k.fkf[a][fid] * gu.x / (1.5 * h * h);
-            gp += k.faf[a][fid] * gu.y / (1.5 * h * h);
+            gT += k.fkf[a][fid] * gu.x * g.rif;
+            gp += k.faf[a][fid] * gu.y * g.rif;
         }
-    const double oT = gT, op = gp + k.lamf[4 * c + 3] * gT;
-    out[c] = make_double2(rf[c].x - oT, rf[c].y - op);
+    out[c] = make_double2(rf[c].x - gT, rf[c].y - (gp + k.lamf[4 * c + 3] * gT));
 }
 
 // x += correction on the valid base cells and the patch.
@@ -368,7 +363,7 @@ __global__ void __launch_bounds__(256) k_cf_covered_mean(CfGeom g, double2 *__re
         s0 += xf[f].x;
         s1 += xf[f].y;
     }
-    xb[I + (long long)g.n0 * J] = make_double2(s0 / 4.0, s1 / 4.0);
+    xb[I + (long long)g.n0 * J] = make_double2(s0 * 0.25, s1 * 0.25);
 }
 
 // The base hierarchy's coefficients: the caller's base arrays, with the
@@ -389,7 +384,7 @@ __global__ void __launch_bounds__(256) k_cf_cover(CfGeom g, CfCoef k, double *__
             const long long f = (2 * (I - g.b0[0]) + (q & 1)) + (long long)g.m0 * (2 * (J - g.b0[1]) + (q >> 1));
             acc += k.lamf[4 * f + t];
         }
-        lam[4 * c + t] = acc / 4.0;
+        lam[4 * c + t] = acc * 0.25;
     }
     double *fa[2] = {fa0, fa1}, *fk[2] = {fk0, fk1};
 #pragma unroll
@@ -407,8 +402,8 @@ __global__ void __launch_bounds__(256) k_cf_cover(CfGeom g, CfCoef k, double *__
                 sk += k.fkf[a][fid];
             }
             const long long bid = cf_bface(g, a, F0, F1);
-            fa[a][bid] = sa / 2.0;
-            fk[a][bid] = sk / 2.0;
+            fa[a][bid] = sa * 0.5;
+            fk[a][bid] = sk * 0.5;
         }
 }
 

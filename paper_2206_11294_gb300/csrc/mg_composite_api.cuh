@@ -21,6 +21,7 @@ struct mg_composite {
     unsigned int *ticket;
     int nblk;
     bool coeffs_set;
+    cudaGraphExec_t gcyc;      // one FAC cycle and the new residuals (captured at the first solve)
 };
 
 namespace {
@@ -47,40 +48,63 @@ void cf_enqueue_norms(mg_composite *m) {
 }
 
 // The composite residuals r = b - L(x) of the current x.
-void cf_enqueue_residual(mg_composite *m) {
+void cf_enqueue_residual(mg_composite *m, cudaStream_t s) {
     const CfCoef k = cf_coef(m);
-    k_cf_rows_base<<<cf_grid2(m->g.n0, m->g.n1), dim3(32, 8), 0, m->stream>>>(m->g, k, m->xb, m->xf, m->bb, m->rb);
-    k_cf_rows_fine<<<cf_grid2(m->g.m0, m->g.m1), dim3(32, 8), 0, m->stream>>>(m->g, k, m->xb, m->xf, m->bf, m->rf);
+    k_cf_rows_base<<<cf_grid2(m->g.n0, m->g.n1), dim3(32, 8), 0, s>>>(m->g, k, m->xb, m->xf, m->bb, m->rb);
+    k_cf_rows_fine<<<cf_grid2(m->g.m0, m->g.m1), dim3(32, 8), 0, s>>>(m->g, k, m->xb, m->xf, m->bf, m->rf);
 }
 
-void cf_enqueue_sweeps(mg_composite *m, const double2 *rhs, int sweeps) {
+void cf_enqueue_sweeps(mg_composite *m, cudaStream_t s, const double2 *rhs, int sweeps) {
     const CfCoef k = cf_coef(m);
     const dim3 gr = cf_grid2((m->g.m0 + 1) / 2, m->g.m1);
     for (int q = 0; q < sweeps; q++)
         for (int colour = 0; colour < 2; colour++)
-            k_cf_rbgs_fine<<<gr, dim3(32, 8), 0, m->stream>>>(m->g0, k, m->zb, rhs, m->df, colour);
+            k_cf_rbgs_fine<<<gr, dim3(32, 8), 0, s>>>(m->g0, k, m->zb, rhs, m->df, colour);
 }
 
-// One FAC cycle on the residuals rb, rf, then x += the correction.
-mg_status cf_fac_cycle(mg_composite *m) {
+// One FAC cycle on the residuals rb, rf, x += the correction, and the
+// residuals of the new x.
+mg_status cf_enqueue_fac_cycle(mg_composite *m, cudaStream_t s) {
     const CfCoef k = cf_coef(m);
-    cudaStream_t s = m->stream;
     CK(cudaMemsetAsync(m->df, 0, sizeof(double2) * m->Nf, s));
-    cf_enqueue_sweeps(m, m->rf, m->opt.nu1);
+    cf_enqueue_sweeps(m, s, m->rf, m->opt.nu1);
     // the patch residual of the correction (zero base values), then the base right-hand side
     k_cf_rows_fine<<<cf_grid2(m->g.m0, m->g.m1), dim3(32, 8), 0, s>>>(m->g0, k, m->zb, m->df, m->rf, m->sf);
     k_cf_base_rhs<<<cf_grid2(m->g.n0, m->g.n1), dim3(32, 8), 0, s>>>(m->g0, k, m->rb, m->df, m->sf, m->sb);
-    CK(cudaGetLastError());
     // one V-cycle of the base hierarchy from zero; the result is in its finest level's x
-    mg_status st = correction_cycles<2>(m->hb, m->sb);
+    mg_status st = enqueue_correction<2>(m->hb, s, m->sb);
     if (st) return st;
     const double2 *db = m->hb->L[0].x;
-    k_cf_prolong<<<cf_grid2(m->g.m0, m->g.m1), dim3(32, 8), 0, s>>>(m->g0, db, m->df);
-    k_cf_ghost_rhs<<<cf_grid2(m->g.m0, m->g.m1), dim3(32, 8), 0, s>>>(m->g0, k, m->rf, db, m->sf);
-    cf_enqueue_sweeps(m, m->sf, m->opt.nu2);
+    k_cf_prolong_ghost<<<cf_grid2(m->g.m0, m->g.m1), dim3(32, 8), 0, s>>>(m->g0, k, db, m->rf, m->df, m->sf);
+    cf_enqueue_sweeps(m, s, m->sf, m->opt.nu2);
     const dim3 ug = cf_grid2(std::max(m->g.n0, m->g.m0), std::max(m->g.n1, m->g.m1));
     k_cf_update<<<ug, dim3(32, 8), 0, s>>>(m->g, m->xb, m->xf, db, m->df);
+    cf_enqueue_residual(m, s);
     CK(cudaGetLastError());
+    return MG_OK;
+}
+
+// The FAC cycle as one graph, captured on the base handle's private capture
+// stream (the caller's stream may be the legacy default stream, which cannot
+// be captured).  Every pointer it uses is fixed for the handle's life.
+mg_status cf_capture(mg_composite *m) {
+    cudaStream_t cs = m->hb->cap;
+    cudaGraph_t graph = nullptr;
+    CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    const mg_status st = cf_enqueue_fac_cycle(m, cs);
+    const cudaError_t le = cudaGetLastError();
+    cudaError_t e = cudaStreamEndCapture(cs, &graph);
+    if (st || le != cudaSuccess || e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        if (st) return st;
+        return fail(MG_ERR_CUDA, std::string("FAC cycle capture: ") + cudaGetErrorString(le ? le : e));
+    }
+    e = cudaGraphInstantiate(&m->gcyc, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        m->gcyc = nullptr;
+        return fail(MG_ERR_CUDA, std::string("FAC cycle graph instantiate: ") + cudaGetErrorString(e));
+    }
     return MG_OK;
 }
 
@@ -139,6 +163,12 @@ mg_status mg_composite_create(const mg_grid *grid, const int box[2][2], const mg
     g.m1 = 2 * (box[1][1] - box[1][0]);
     g.H = grid->h;
     g.h = 0.5 * grid->h;
+    g.rh2 = 1.0 / (g.h * g.h);
+    g.rif = 1.0 / (1.5 * g.h * g.h);
+    g.rdf = 1.0 / (0.5 * g.h * g.h);
+    g.rH2 = 1.0 / (g.H * g.H);
+    g.rdb = 1.0 / (0.5 * g.H * g.H);
+    g.rbif = 1.0 / (1.5 * g.H * g.H);
     m->g0 = g;
     std::memset(m->g0.gT, 0, sizeof(m->g0.gT));
     std::memset(m->g0.gp, 0, sizeof(m->g0.gp));
@@ -285,15 +315,16 @@ mg_status mg_composite_solve(mg_composite *m, const double *bb, const double *bf
     CK(cudaMemcpyAsync(m->bf, bf, 16 * m->Nf, cudaMemcpyDeviceToDevice, s));
     CK(cudaMemcpyAsync(m->xb, xb, 16 * m->Nb, cudaMemcpyDeviceToDevice, s));
     CK(cudaMemcpyAsync(m->xf, xf, 16 * m->Nf, cudaMemcpyDeviceToDevice, s));
+    if (cycles > 0 && !m->gcyc && (st = cf_capture(m))) return st;
+    cf_enqueue_residual(m, s);
     for (int k = 0;; k++) {
-        cf_enqueue_residual(m);
         if (norms) {
             cf_enqueue_norms(m);
             CK(cudaStreamSynchronize(s));
             for (int q = 0; q < 4; q++) norms[4 * k + q] = m->norms_h[q];
         }
         if (k == cycles) break;
-        if ((st = cf_fac_cycle(m))) return st;
+        CK(cudaGraphLaunch(m->gcyc, s));
     }
     const int bx = m->g.b1[0] - m->g.b0[0], by = m->g.b1[1] - m->g.b0[1];
     k_cf_covered_mean<<<cf_grid2(bx, by), dim3(32, 8), 0, s>>>(m->g, m->xb, m->xf);
@@ -307,10 +338,24 @@ mg_status mg_composite_solve(mg_composite *m, const double *bb, const double *bf
     return MG_OK;
 }
 
+mg_status mg_composite_autotune(mg_composite *m, int reps, double *vcycle_ms) {
+    if (!m) return fail(MG_ERR_INVALID_ARG, "NULL handle");
+    if (!m->coeffs_set) return fail(MG_ERR_STATE, "mg_composite_set_coeffs has not succeeded");
+    DeviceGuard dg(m->device);
+    const mg_status st = mg_autotune(m->hb, reps, nullptr, vcycle_ms);
+    // the FAC cycle graph holds the base hierarchy's former kernel choices
+    if (m->gcyc) {
+        cudaGraphExecDestroy(m->gcyc);
+        m->gcyc = nullptr;
+    }
+    return st;
+}
+
 mg_status mg_composite_destroy(mg_composite *m) {
     if (!m) return MG_OK;
     DeviceGuard dg(m->device);
     if (m->stream) cudaStreamSynchronize(m->stream);
+    if (m->gcyc) cudaGraphExecDestroy(m->gcyc);
     if (m->hb) mg_destroy(m->hb);
     if (m->arena) cudaFree(m->arena);
     if (m->norms_h) cudaFreeHost(m->norms_h);

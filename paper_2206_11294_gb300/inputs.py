@@ -290,9 +290,10 @@ def round_to(v: float, m: int) -> int:
     return max(m, int(round(v / m)) * m)
 
 
-def batch_sizes(count: int = 256, seed: int = 5, lo: int = 64, hi: int = 1024, multiple: int = 64):
-    """Log-uniform sizes in [lo, hi], rounded to a multiple (64: every size then
-    coarsens to at most 15 x 15 cells, within the exact coarsest solve)."""
+def batch_sizes(count: int = 256, seed: int = 5, lo: int = 64, hi: int = 1024, multiple: int = 32):
+    """Log-uniform sizes in [lo, hi], rounded to a multiple (32: every size then
+    coarsens to at most 31 x 31 cells, 1922 unknowns of the exact coarsest
+    solve)."""
     rng = np.random.default_rng(seed)
     return [min(hi, round_to(math.exp(rng.uniform(math.log(lo), math.log(hi))), multiple))
             for _ in range(count)]

@@ -154,8 +154,10 @@ class Engine:
             self.table = TuningTable(None)
         torch.cuda.set_device(device)
 
-    def new_stream(self):
-        return self.torch.cuda.Stream(device=self.device)
+    def new_stream(self, high: bool = False):
+        """A stream of this device; high: of the highest priority, whose
+        blocks the GPU schedules ahead of waiting blocks of normal streams."""
+        return self.torch.cuda.Stream(device=self.device, priority=-1 if high else 0)
 
     def key(self, problem) -> Tuple:
         g = problem.grid
@@ -234,10 +236,14 @@ class Engine:
 class Server:
     """Continuous-batching loop: submit() returns a future of (x, stats)."""
 
-    def __init__(self, engine, hbm_budget: int, slots: int = 4, max_batch: int = 8):
+    def __init__(self, engine, hbm_budget: int, slots: int = 4, max_batch: int = 8, small_cells: int = 1 << 20):
         self.engine = engine
         self.slots = slots
         self.max_batch = max_batch
+        # groups of at most this many cells per problem run on a slot's
+        # high-priority stream: a short request's kernels then start as SMs
+        # free up, instead of queueing behind every block of a large solve
+        self.small_cells = small_cells
         self.lock = threading.Condition()
         self.queue: "collections.deque[Request]" = collections.deque()
         self.cache = HierarchyCache(hbm_budget, make=self._make, free=engine.free)
@@ -331,6 +337,7 @@ class Server:
 
     def _worker(self, slot: int):
         stream = self.engine.new_stream()
+        fast = self.engine.new_stream(high=True)
         while True:
             with self.lock:
                 while True:
@@ -340,8 +347,9 @@ class Server:
                     if taken:
                         break
                     self.lock.wait(timeout=0.05)
+            small = max(int(r.problem.grid.N) for r in taken) <= self.small_cells
             try:
-                results = self.engine.run(solvers, [r.problem for r in taken], stream)
+                results = self.engine.run(solvers, [r.problem for r in taken], fast if small else stream)
                 err = None
             except Exception as e:       # a failed group fails its own requests only
                 results, err = None, e

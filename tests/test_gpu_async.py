@@ -158,3 +158,34 @@ def test_degenerate_stops(torch_cuda, precision):
             assert sa[k] == st[k], (kw, k)
         assert torch.equal(xa, xs), kw
         s.close()
+
+
+def test_set_stream_orders_after_the_running_set_up(torch_cuda):
+    """mg_set_coeffs returns with its set-up still running; mg_set_stream then
+    makes the new stream wait for it on the device, not for the old stream's
+    later work and not on the host.  The old stream is held back by a bounded
+    spin kernel enqueued before the set-up, so a solve on the new stream that
+    did not wait would read the previous coefficients (a different problem's)
+    and give another result."""
+    torch = torch_cuda
+    from paper_2206_11294_gb300.binding import Solver
+    p, q = CASES["2d_stiff"], I.random_coeff_problem(CASES["2d_stiff"].grid, seed=91, dt=1e-5)
+    d, e = _dev(torch, p), _dev(torch, q)
+    ref = Solver(p.grid, precision="fp64", rtol=1e-10, max_cycles=120)
+    ref.set_coeffs(d["lam"], d["fa"], d["fk"])
+    x_ref = d["x0"].clone()
+    st_ref = ref.solve(d["b"], x_ref)
+    ref.close()
+    sa, sb = torch.cuda.Stream(), torch.cuda.Stream()
+    s = Solver(p.grid, precision="fp64", rtol=1e-10, max_cycles=120, stream=sa)
+    x = d["x0"].clone()
+    s.set_coeffs(e["lam"], e["fa"], e["fk"])         # another problem's coefficients first
+    torch.cuda.synchronize()
+    with torch.cuda.stream(sa):
+        torch.cuda._sleep(20_000_000)                # about 10 ms of spinning on sa
+    s.set_coeffs(d["lam"], d["fa"], d["fk"])         # on sa, queued behind the spin
+    s.set_stream(sb)
+    st = s.solve(d["b"], x)                          # on sb, at once
+    assert st["cycles"] == st_ref["cycles"]
+    assert np.array_equal(x.cpu().numpy(), x_ref.cpu().numpy())
+    s.close()

@@ -95,6 +95,21 @@ def test_composite_fac_fixed_cycles(torch_cuda, name, cycles):
     c.close()
 
 
+def test_composite_autotune_keeps_results(torch_cuda):
+    """The base hierarchy's kernel choices change no arithmetic: after
+    mg_composite_autotune (which also drops the captured FAC-cycle graph) the
+    same solve gives the same result bit for bit."""
+    b, p, box = CASES["stiff_bubbles_64"]
+    c = _composite(b, p, box)
+    xb0, xf0, h0 = c.solve(b.b, p.b, b.x0.copy(), p.x0.copy(), 4)
+    assert c.autotune(reps=2) > 0
+    xb1, xf1, h1 = c.solve(b.b, p.b, b.x0.copy(), p.x0.copy(), 4)
+    assert np.array_equal(xb0.cpu().numpy(), xb1.cpu().numpy())
+    assert np.array_equal(xf0.cpu().numpy(), xf1.cpu().numpy())
+    assert np.array_equal(h0, h1)
+    c.close()
+
+
 def test_composite_converges_to_the_dense_solution(torch_cuda):
     from oracle import composite as cf
     b, p, box = I.composite_bubble(16, seed=25, n_bubbles=1, rmin=0.15, rmax=0.2, length=6.4e-3, dt=1e-5)

@@ -18,9 +18,10 @@ class FakeEngine:
         self.max_live = 0
         self.lock = threading.Lock()
         self.groups = []
+        self.streams = []
 
-    def new_stream(self):
-        return object()
+    def new_stream(self, high=False):
+        return ("high" if high else "normal", object())
 
     def key(self, p):
         return (p.grid.n,)
@@ -40,6 +41,7 @@ class FakeEngine:
 
     def run(self, solvers, problems, stream):
         self.groups.append(len(problems))
+        self.streams.append((stream[0], max(p.grid.N for p in problems)))
         time.sleep(self.delay)
         if any(p.name == self.fail_name for p in problems):
             raise RuntimeError("bad coefficients")
@@ -130,3 +132,14 @@ def test_prewarm_builds_resident_hierarchies_within_budget():
         f.result(timeout=10)
     assert srv.cache.created == created          # every request found a resident hierarchy
     srv.close()
+
+
+def test_small_groups_run_on_the_high_priority_stream():
+    eng = FakeEngine(delay=0.0)
+    srv = Server(eng, hbm_budget=10_000, slots=2, max_batch=1, small_cells=100)
+    futs = [srv.submit(prob(f"p{i}", n, 10)) for i, n in enumerate([50, 100, 101, 4000])]
+    for f in futs:
+        f.result(timeout=10)
+    srv.close()
+    assert sorted(eng.streams, key=lambda t: t[1]) == [("high", 50), ("high", 100), ("normal", 101),
+                                                        ("normal", 4000)]
