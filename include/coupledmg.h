@@ -553,6 +553,18 @@ MG_API mg_status mg_residual_norms_noalloc(const mg_grid *grid, const double *la
  * `stream`; the fastest launch gives the rate.  Synchronous. */
 MG_API mg_status mg_fp64_fma_rate(void *stream, int repeats, double *g_fma_per_s);
 
+/* Copies `bytes` from page-locked host memory (mapped for the device, as
+ * cudaHostAlloc / cudaMallocHost memory is) to device memory with a kernel on
+ * `stream` (no counterpart in the paper: request transfers of the serving
+ * loop).  The SMs load the source over the CPU-GPU link, so the copy does not
+ * wait in the copy engines' queue behind a large transfer enqueued on another
+ * stream; on a high-priority stream it runs beside that transfer.  Both
+ * pointers 16-byte aligned; any size.  MG_ERR_INVALID_ARG (nothing launched)
+ * for a source that is not page-locked host memory, a destination that is not
+ * device memory of the current device, or misaligned pointers.  Asynchronous:
+ * the source must stay valid and unchanged until the stream has run the copy. */
+MG_API mg_status mg_copy_h2d_async(void *dst, const void *src, size_t bytes, void *stream);
+
 /* ---------------------------------------------------------------------
  * Refined-patch (adaptive) grids.  The paper's production grids are coarsened
  * away from the bubble (Sec. 5.2, the rigid-wall collapse runs); here in its

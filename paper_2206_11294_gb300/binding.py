@@ -35,7 +35,7 @@ EXPORTS = ["mg_default_options", "mg_workspace_size", "mg_create", "mg_set_coeff
            "mg_batch_set_tuning", "mg_batch_autotune", "mg_assemble_async", "mg_correct_async",
            "mg_energy_async", "mg_momentum_create", "mg_momentum_set_coeffs", "mg_momentum_apply",
            "mg_momentum_solve", "mg_momentum_destroy", "mg_momentum_rhs_async", "mg_provisional_async",
-           "mg_fp64_fma_rate", "mg_solve_async", "mg_solve_async_stats", "mg_composite_create",
+           "mg_fp64_fma_rate", "mg_copy_h2d_async", "mg_solve_async", "mg_solve_async_stats", "mg_composite_create",
            "mg_composite_set_coeffs", "mg_composite_apply", "mg_composite_solve", "mg_composite_autotune",
            "mg_composite_destroy"]
 
@@ -204,6 +204,7 @@ def load(path: str = LIB_PATH):
             "mg_momentum_rhs_async": ([C.POINTER(MgGrid), C.c_double, C.c_double, pa3, P, P, P, pa3, P], C.c_int),
             "mg_provisional_async": ([C.POINTER(MgGrid), C.c_double, P, P, pa3, pa3, P], C.c_int),
             "mg_fp64_fma_rate": ([P, C.c_int, dp], C.c_int),
+            "mg_copy_h2d_async": ([P, P, C.c_size_t, P], C.c_int),
             "mg_solve_async": ([P, P, P, P], C.c_int),
             "mg_solve_async_stats": ([P, C.POINTER(MgStats)], C.c_int),
             "mg_composite_create": ([C.POINTER(MgGrid), (C.c_int * 2) * 2, C.POINTER(MgOptions), P, C.POINTER(P)],
@@ -312,6 +313,21 @@ def residual_norms_noalloc(grid, lam, fa, fk, b, x, out, stream=None) -> None:
         stream = torch.cuda.current_stream()
     check(load().mg_residual_norms_noalloc(C.byref(g), _ptr(lam, True)[0], pa, pk, _ptr(b, True)[0],
                                            _ptr(x, True)[0], _ptr(out, True)[0], C.c_void_p(stream.cuda_stream)))
+
+
+def copy_h2d(dst, src, stream=None):
+    """mg_copy_h2d_async: dst (CUDA tensor) <- src (page-locked CPU tensor of the
+    same size in bytes), copied by a kernel on `stream` (default: the current
+    one); returns dst.  Asynchronous, like a non-blocking copy."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    nbytes = src.numel() * src.element_size()
+    if dst.numel() * dst.element_size() != nbytes or not dst.is_contiguous() or not src.is_contiguous():
+        raise ValueError("copy_h2d: contiguous tensors of the same size in bytes")
+    check(load().mg_copy_h2d_async(C.c_void_p(dst.data_ptr()), C.c_void_p(src.data_ptr()), C.c_size_t(nbytes),
+                                   C.c_void_p(stream.cuda_stream)))
+    return dst
 
 
 def fp64_fma_rate(repeats: int = 5, stream=None) -> float:

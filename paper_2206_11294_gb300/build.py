@@ -17,7 +17,7 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libcoupledmg.so")
 INCLUDE = os.path.join(ROOT, "include")
 
-SOURCES = ["mg_capi.cu", "mg_noalloc.cu", "mg_peak.cu"]
+SOURCES = ["mg_capi.cu", "mg_noalloc.cu", "mg_peak.cu", "mg_transfer.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]

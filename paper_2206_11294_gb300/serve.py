@@ -131,7 +131,7 @@ class Engine:
     that shape through a shared autotune.TuningTable (optionally a file)."""
 
     def __init__(self, device: int = 0, precision: str = "mixed", rtol: float = 1e-10, max_cycles: int = 60,
-                 tune: bool = False, tuning_table=None, batch_min: int = 4):
+                 tune: bool = False, tuning_table=None, batch_min: int = 4, kernel_copy_cells: int = 1 << 20):
         import torch
         from . import binding
         self.torch = torch
@@ -144,6 +144,10 @@ class Engine:
         # a group of fewer requests runs as solo solves: building an mg_batch
         # (its tables, its cycle graph) costs more than it saves for a few
         self.batch_min = max(2, int(batch_min))
+        # inputs of problems up to this many cells go to the device through
+        # mg_copy_h2d_async (a kernel) rather than the copy engines, whose queue
+        # would hold them behind a large request's transfer
+        self.kernel_copy_cells = kernel_copy_cells
         self.table = tuning_table
         self._tuned = set()
         self._tune_lock = threading.Lock()
@@ -207,10 +211,13 @@ class Engine:
                 s.set_stream(stream)      # a cached hierarchy moves to this slot's stream
         with torch.cuda.stream(stream):
             dev = f"cuda:{self.device}"
-            T = lambda a: a.to(dev, non_blocking=True)
             bs, xs = [], []
             for s, p in zip(solvers, problems):
                 h = self.pinned(p)
+                if int(p.grid.N) <= self.kernel_copy_cells:
+                    T = lambda a: self.binding.copy_h2d(torch.empty(a.shape, dtype=a.dtype, device=dev), a, stream)
+                else:
+                    T = lambda a: a.to(dev, non_blocking=True)
                 s.set_coeffs(T(h["lam"]), [T(f) for f in h["fa"]], [T(f) for f in h["fk"]])
                 if self.tune and id(s) not in self._tuned:
                     with self._tune_lock:            # one measurement at a time on the device
