@@ -101,10 +101,20 @@ typedef struct {
                             0: off; otherwise >= 1 (default 2: the interface the volume fraction smooths over
                             about two cells changes the coefficients by up to ~5x per cell there).  Ignored in
                             FP64. */
+    int coarse_solve;    /* The exact coarsest solve (Sec. 3 names a direct solve there).  Both factor the
+                            coarsest matrix once per mg_set_coeffs (banded LU with partial pivoting, FP64).
+                            MG_COARSE_AUTO (default): coarsest systems above 128 unknowns (odd grid factors of 9
+                            or more, e.g. 31 x 31 cells for n = 992) keep the factors and each cycle runs the two
+                            triangular solves, one warp, 2n dependent steps; smaller ones form the inverse and
+                            each cycle multiplies by it.  MG_COARSE_INVERSE: always form the inverse (its n^2
+                            (kl + ku) set-up work pays back only over many cycles).  A hierarchy that solves
+                            from the factors runs without the V-cycle tail kernel (mg_tuning.tail_level must be
+                            >= levels).  Batches need one value for all their handles. */
 } mg_options;
 
 enum { MG_CYCLE_V = 0, MG_CYCLE_W = 1, MG_CYCLE_F = 2 };
 enum { MG_SMOOTH_RBGS = 0, MG_SMOOTH_WJAC = 1 };
+enum { MG_COARSE_AUTO = 0, MG_COARSE_INVERSE = 1 };
 
 typedef struct {
     int cycles;          /* V-cycles run (MIXED: total FP32 cycles) */
@@ -121,7 +131,7 @@ typedef struct mg_handle mg_handle;
 
 /* Fills defaults: V(2,2), FP64, rtol 1e-10, 50 cycles, coarse_min 4, 1 inner cycle, red-black block
  * Gauss-Seidel (omega 0.8 for weighted block Jacobi), FP64 blocks at face-coefficient jumps above 2:1
- * in mixed precision. */
+ * in mixed precision, MG_COARSE_AUTO. */
 MG_API mg_status mg_default_options(mg_options *opt);
 
 /* Device bytes a handle of this grid and these options needs (hierarchy,

@@ -62,7 +62,8 @@ class MgGrid(C.Structure):
 class MgOptions(C.Structure):
     _fields_ = [("nu1", C.c_int), ("nu2", C.c_int), ("precision", C.c_int), ("rtol", C.c_double),
                 ("max_cycles", C.c_int), ("coarse_min", C.c_int), ("inner_cycles", C.c_int), ("cycle", C.c_int),
-                ("smoother", C.c_int), ("omega", C.c_double), ("fp64_jump_ratio", C.c_double)]
+                ("smoother", C.c_int), ("omega", C.c_double), ("fp64_jump_ratio", C.c_double),
+                ("coarse_solve", C.c_int)]
 
 
 class MgStats(C.Structure):
@@ -255,10 +256,12 @@ def make_grid(g) -> MgGrid:
 
 CYCLES = {"V": 0, "W": 1, "F": 2}
 SMOOTHERS = {"rbgs": 0, "wjac": 1}
+COARSE = {"auto": 0, "inverse": 1}
 
 
 def make_options(precision="fp64", rtol=1e-10, max_cycles=50, nu1=2, nu2=2, coarse_min=4,
-                 inner_cycles=1, cycle="V", smoother="rbgs", omega=0.8, fp64_jump_ratio=2.0) -> MgOptions:
+                 inner_cycles=1, cycle="V", smoother="rbgs", omega=0.8, fp64_jump_ratio=2.0,
+                 coarse="auto") -> MgOptions:
     o = MgOptions()
     check(load().mg_default_options(C.byref(o)))
     o.precision = MG_MIXED if precision in ("mixed", MG_MIXED) else MG_FP64
@@ -268,6 +271,7 @@ def make_options(precision="fp64", rtol=1e-10, max_cycles=50, nu1=2, nu2=2, coar
     o.smoother = SMOOTHERS[smoother] if isinstance(smoother, str) else int(smoother)
     o.omega = float(omega)
     o.fp64_jump_ratio = float(fp64_jump_ratio)
+    o.coarse_solve = COARSE[coarse] if isinstance(coarse, str) else int(coarse)
     return o
 
 
@@ -422,13 +426,13 @@ class Solver:
 
     def __init__(self, grid, precision="fp64", rtol=1e-10, max_cycles=50, nu1=2, nu2=2, coarse_min=4,
                  inner_cycles=1, device: Optional[int] = None, stream=None, torch_workspace: bool = True,
-                 cycle="V", smoother="rbgs", omega=0.8, fp64_jump_ratio=2.0):
+                 cycle="V", smoother="rbgs", omega=0.8, fp64_jump_ratio=2.0, coarse="auto"):
         import torch
         lib = load()
         self._lib = lib
         self.grid = make_grid(grid)
         self.options = make_options(precision, rtol, max_cycles, nu1, nu2, coarse_min, inner_cycles, cycle,
-                                    smoother, omega, fp64_jump_ratio)
+                                    smoother, omega, fp64_jump_ratio, coarse)
         dev = torch.cuda.current_device() if device is None else int(device)
         self.device = dev
         check(lib.mg_set_device(dev))

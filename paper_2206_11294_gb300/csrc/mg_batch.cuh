@@ -33,6 +33,11 @@ struct BProb {                  // one problem, device side
     unsigned int *ticket;
     const double *Minv;
     const float *Minv32;
+    const double *Lb, *Uc;      // the coarsest level's factors, when its solve uses them (k_coarse_lu)
+    const int *piv;
+    const double *dinv;
+    const int *err;
+    int kl;
     int nc;
     int coarse;                 // index of its coarsest level in the BLevel table
     int npartial;
@@ -166,6 +171,22 @@ __global__ void __launch_bounds__(kBatchThreads) kb_coarse(const BLevel *__restr
     }
 }
 
+// Coarsest solves of the problems that keep the factors (ids): one block each.
+template <typename R>
+__global__ void __launch_bounds__(kLuSolveThreads) kb_coarse_lu(const BLevel *__restrict__ lv,
+                                                                const BProb *__restrict__ pr,
+                                                                const BState *__restrict__ st,
+                                                                const int *__restrict__ ids) {
+    extern __shared__ double blusm[];
+    const int p = ids[blockIdx.x];
+    if (!st[p].active) return;
+    const BProb &P = pr[p];
+    const Level<R> C = pick<R>(lv[P.coarse]);
+    coarse_lu_solve_block<R>(P.Lb, P.Uc, P.piv, P.dinv, P.nc, P.kl, P.kl, reinterpret_cast<const R *>(C.b),
+                             reinterpret_cast<R *>(C.x), P.err, blusm);
+}
+
+
 template <int DIM>
 __global__ void __launch_bounds__(kBatchThreads) kb_setup_fine(const BSetupLevel *__restrict__ sl,
                                                                const SetupIn *__restrict__ in,
@@ -286,6 +307,14 @@ __global__ void __launch_bounds__(kWinThreads) kb_band_lu_window(const BCoarse *
                                                                   const int *__restrict__ ids) {
     const BCoarse &C = co[ids[blockIdx.x]];
     band_lu_window_block(C.M, C.nc, C.kl, C.kl, C.piv, C.dinv, C.Mwork, C.Mwork + (long long)C.nc * C.kl, C.err);
+}
+
+// Columns of U over their pivots (scale_uc), for the problems that keep the factors: a 2D grid (x: chunks of a
+// problem's entries, y: problem).
+__global__ void __launch_bounds__(256) kb_scale_uc(const BCoarse *__restrict__ co, const int *__restrict__ ids) {
+    const BCoarse &C = co[ids[blockIdx.y]];
+    scale_uc(C.Mwork + (long long)C.nc * C.kl, C.dinv, C.nc, C.kl, C.kl, C.err,
+             blockIdx.x * (long long)blockDim.x + threadIdx.x, (long long)gridDim.x * blockDim.x);
 }
 
 __global__ void __launch_bounds__(256) kb_band_inv_block(const BCoarse *__restrict__ co, const int *__restrict__ ids) {
@@ -522,6 +551,8 @@ struct mg_batch {
     int *big_ids;                     // problems on the banded path (device)
     int *win_ids;                     // problems on the windowed banded path (device)
     std::vector<int> win_coarse;      // their indices
+    bool win_factors = false;         // the windowed-path problems solve from their factors (no inverse)
+    size_t lu_smem = 0;               // shared memory of kb_coarse_lu
     int max_nc_win = 0;
     size_t win_smem = 0, win_inv_smem = 0;
     int win_warps = 8;
@@ -585,8 +616,16 @@ void b_vcycle(mg_batch *b, cudaStream_t s) {
         b->launches++;
     }
     const int ncs = b->coarse.second;
-    kb_coarse<R><<<batch_grid(b, ncs), kBatchThreads, 0, s>>>(b->lv, b->pr, b->st, b->tabs + b->coarse.first, ncs);
-    b->launches++;
+    if (ncs > 0) {
+        kb_coarse<R><<<batch_grid(b, ncs), kBatchThreads, 0, s>>>(b->lv, b->pr, b->st, b->tabs + b->coarse.first, ncs);
+        b->launches++;
+    }
+    if (b->win_factors) {
+        raise_smem_limit((const void *)kb_coarse_lu<R>, (int)b->lu_smem);
+        kb_coarse_lu<R><<<(unsigned)b->win_coarse.size(), kLuSolveThreads, b->lu_smem, s>>>(b->lv, b->pr, b->st,
+                                                                                            b->win_ids);
+        b->launches++;
+    }
     for (int d = b->dmax - 2; d >= 0; d--) {
         if (b->colour[d].second == 0) continue;
         const int np = b->prolong[d].second;
@@ -718,7 +757,7 @@ void b_step(mg_batch *b, cudaStream_t s) {
 bool same_options(const mg_options &a, const mg_options &c) {
     return a.nu1 == c.nu1 && a.nu2 == c.nu2 && a.precision == c.precision && a.rtol == c.rtol &&
            a.max_cycles == c.max_cycles && a.inner_cycles == c.inner_cycles && a.cycle == c.cycle &&
-           a.smoother == c.smoother && a.fp64_jump_ratio == c.fp64_jump_ratio;
+           a.smoother == c.smoother && a.fp64_jump_ratio == c.fp64_jump_ratio && a.coarse_solve == c.coarse_solve;
 }
 
 void add_blocks(std::vector<int2> &t, int level_index, long long blocks) {
@@ -788,6 +827,12 @@ mg_status mg_batch_create(int count, mg_handle *const *handles, mg_batch **out) 
         pr[p].ticket = h->ticket;
         pr[p].Minv = h->Minv;
         pr[p].Minv32 = h->Minv32;
+        pr[p].Lb = h->coarse_factors ? h->Mwork : nullptr;
+        pr[p].Uc = h->coarse_factors ? h->Mwork + (long long)h->nc * h->coarse_kl : nullptr;
+        pr[p].piv = h->piv;
+        pr[p].dinv = h->dinv;
+        pr[p].err = h->err_d;
+        pr[p].kl = h->coarse_kl;
         pr[p].nc = h->nc;
         pr[p].coarse = base[p] + h->nlev - 1;
         pr[p].npartial = h->npartial;
@@ -830,7 +875,8 @@ mg_status mg_batch_create(int count, mg_handle *const *handles, mg_batch **out) 
         add_blocks(tn, base[p], (long long)g0.x * g0.y * g0.z);
         const dim3 gn = norm_grid(h->L[0], dim);
         add_blocks(tnorm, base[p], (long long)gn.x * gn.y * gn.z);
-        for (int r = 0; r < (h->nc + 7) / 8; r++) tco.push_back(make_int2(p, r));
+        if (!h->coarse_factors)
+            for (int r = 0; r < (h->nc + 7) / 8; r++) tco.push_back(make_int2(p, r));
         add_blocks(tcell, base[p], (h->L[0].N + kBatchThreads - 1) / kBatchThreads);
     }
     b->cells0g = slice(tn);
@@ -900,6 +946,8 @@ mg_status mg_batch_create(int count, mg_handle *const *handles, mg_batch **out) 
             b->max_nc_small = std::max(b->max_nc_small, h->nc);
         } else if (window_path(h->nc, C.kl)) {
             b->win_coarse.push_back(p);
+            b->win_factors = h->coarse_factors;      // one coarse_solve option for the whole batch
+            b->lu_smem = std::max(b->lu_smem, (size_t)coarse_lu_smem(h->nc, C.kl, C.kl));
             b->max_nc_win = std::max(b->max_nc_win, h->nc);
             b->win_smem = std::max(b->win_smem, (size_t)band_window_smem(C.kl, C.kl));
             b->win_warps = std::min(b->win_warps, inv_block_warps(h->nc, C.kl));
@@ -1164,9 +1212,13 @@ mg_status mg_batch_set_coeffs(mg_batch *b, const double *const *lambda, const do
         CK(raise_smem_limit((const void *)kb_band_lu_window, (int)b->win_smem));
         CK(raise_smem_limit((const void *)kb_band_inv_block, (int)b->win_inv_smem));
         kb_band_lu_window<<<nw, kWinThreads, b->win_smem, s>>>(b->co, b->win_ids);
-        kb_band_inv_block<<<dim3((unsigned)((b->max_nc_win + b->win_warps - 1) / b->win_warps), nw), 32 * b->win_warps,
-                            b->win_inv_smem, s>>>(b->co, b->win_ids);
-        b->launches += 2;
+        b->launches++;
+        if (b->win_factors)                 // the cycles solve from Lb and the scaled Uc (kb_coarse_lu)
+            kb_scale_uc<<<dim3(64, nw), 256, 0, s>>>(b->co, b->win_ids);
+        else
+            kb_band_inv_block<<<dim3((unsigned)((b->max_nc_win + b->win_warps - 1) / b->win_warps), nw),
+                                32 * b->win_warps, b->win_inv_smem, s>>>(b->co, b->win_ids);
+        b->launches++;
     }
     if (!b->big_coarse.empty()) {           // medium coarsest levels: the banded path, all at once
         const unsigned nb = (unsigned)b->big_coarse.size();

@@ -136,8 +136,10 @@ struct mg_handle {
     int persistent;        // colour sweeps, restriction, prolongation: one persistent wave (1) or a block per tile (0)
     TmaLevel *tmaps;       // tensor maps per (level, precision, tile), built on first use (host memory)
     unsigned char *tmap_ok;
-    double *Minv, *Mtmp;
-    double *Mwork;         // coarse inverse: columns before the transpose (banded path)
+    double *Minv, *Mtmp;   // coarse inverse (NULL when the cycles solve from the factors); assembled matrix
+    bool coarse_factors;   // the cycles solve the coarsest level from its LU factors (k_coarse_lu)
+    int coarse_kl;         // the coarsest matrix's lower (= upper) bandwidth
+    double *Mwork;         // coarse inverse: columns before the transpose (banded path); the window path's factors
     int *piv;              // coarse inverse: pivot rows (banded path)
     double *dinv;          // coarse inverse: reciprocal pivots (banded path)
     float *Minv32;
@@ -204,6 +206,8 @@ mg_status check_grid(const mg_grid *g, const mg_options *o) {
         return fail(MG_ERR_INVALID_ARG, "omega must be in (0, 1] for weighted block Jacobi");
     if (!(o->fp64_jump_ratio == 0.0 || (o->fp64_jump_ratio >= 1.0 && std::isfinite(o->fp64_jump_ratio))))
         return fail(MG_ERR_INVALID_ARG, "fp64_jump_ratio must be 0 (off) or a finite ratio >= 1");
+    if (o->coarse_solve != MG_COARSE_AUTO && o->coarse_solve != MG_COARSE_INVERSE)
+        return fail(MG_ERR_INVALID_ARG, "coarse_solve must be MG_COARSE_AUTO or MG_COARSE_INVERSE");
     int n[3] = {g->n[0], g->n[1], g->n[2]}, lev = 1;
     while (can_coarsen(n, g->dim, o->coarse_min) && lev < kMaxLevels) {
         for (int a = 0; a < g->dim; a++) n[a] /= 2;
@@ -238,6 +242,8 @@ dim3 cell_grid(const LevelBuf &l, int dim, int xthreads) {
 dim3 norm_grid(const LevelBuf &l, int dim) {
     return dim3((unsigned)norm_gx(l.n[0]), (unsigned)norm_gy(l.n[1]), (unsigned)(dim == 3 ? l.n[2] : 1));
 }
+
+bool window_path(int n, int kl);
 
 // Lays out every buffer; with base == NULL only computes the size.
 void plan(mg_handle *h, char *base, size_t *bytes) {
@@ -292,12 +298,18 @@ void plan(mg_handle *h, char *base, size_t *bytes) {
     const LevelBuf &f = h->L[0];
     const LevelBuf &c = h->L[h->nlev - 1];
     h->nc = (int)(2 * c.N);
+    // band of the coarsest matrix: the farthest neighbour cell is n0 (2D) or
+    // n0*n1 (3D) cells away, two unknowns per cell
+    h->coarse_kl = std::min(h->nc - 1, 2 * (g.dim == 3 ? c.n[0] * c.n[1] : c.n[0]) + 1);
+    h->coarse_factors = h->opt.coarse_solve == MG_COARSE_AUTO && window_path(h->nc, h->coarse_kl);
     // The cluster tail takes the levels below the finest whose cells fit
-    // kTailCells, when there are at least two of them.
+    // kTailCells, when there are at least two of them (and the coarsest
+    // level has an inverse: the tail multiplies by it).
     h->tail_lev = h->nlev;
     for (int l = 1; l < h->nlev && h->opt.smoother == MG_SMOOTH_RBGS; l++)
         if (h->L[l].N <= kTailCells) { h->tail_lev = l; break; }
-    if (h->nlev - h->tail_lev < 2 || h->nlev - h->tail_lev > kTailMaxLevels) h->tail_lev = h->nlev;
+    if (h->nlev - h->tail_lev < 2 || h->nlev - h->tail_lev > kTailMaxLevels || h->coarse_factors)
+        h->tail_lev = h->nlev;
     h->tail_ctas = kTailCtas;
     h->persistent = 0;
     // Default kernel choices until mg_autotune / mg_set_tuning: FP32 cycles
@@ -313,13 +325,13 @@ void plan(mg_handle *h, char *base, size_t *bytes) {
     // lambda, then 1/rho and k of every axis (host-side coefficient intake)
     h->stage_bytes = (size_t)(32 * f.N + 16 * sumnf);
     h->stage = P.take<char>((long long)h->stage_bytes);
-    h->Minv = P.take<double>((long long)h->nc * h->nc);
+    h->Minv = h->coarse_factors ? nullptr : P.take<double>((long long)h->nc * h->nc);
     h->Mtmp = P.take<double>((long long)h->nc * h->nc);
     const bool big = h->nc > kBandSmemMax;
     h->Mwork = big ? P.take<double>((long long)h->nc * h->nc) : nullptr;
     h->piv = P.take<int>(h->nc);
     h->dinv = P.take<double>(h->nc);
-    h->Minv32 = mixed ? P.take<float>((long long)h->nc * h->nc) : nullptr;
+    h->Minv32 = mixed && !h->coarse_factors ? P.take<float>((long long)h->nc * h->nc) : nullptr;
     const dim3 gg = norm_grid(f, g.dim);
     h->npartial = (int)(gg.x * gg.y * gg.z);
     h->partial = P.take<double2>(h->npartial);
@@ -704,8 +716,18 @@ void enqueue_vcycle(const mg_handle *h, cudaStream_t s, int l, int type) {
     }
     if (l == h->nlev - 1) {
         const Level<R> v = view<R>(lb);
-        // the coarsest inverse is computed on the aux stream after each set-up
+        // the coarsest inverse (or factors) is computed on the aux stream after each set-up
         if (!h->cond_body) cudaStreamWaitEvent(s, h->ev_inv, cudaEventWaitExternal);
+        if (h->coarse_factors) {
+            const long long sm = coarse_lu_smem(h->nc, h->coarse_kl, h->coarse_kl);
+            raise_smem_limit((const void *)k_coarse_lu<R>, (int)sm);
+            k_coarse_lu<R><<<1, kLuSolveThreads, (size_t)sm, s>>>(h->Mwork, h->Mwork + (long long)h->nc * h->coarse_kl, h->piv,
+                                                     h->dinv, h->nc, h->coarse_kl, h->coarse_kl,
+                                                     reinterpret_cast<const R *>(v.b), reinterpret_cast<R *>(v.x),
+                                                     h->err_d);
+            counted(h);
+            return;
+        }
         const int threads = 256;
         const unsigned blocks = (unsigned)((h->nc * 32LL + threads - 1) / threads);
         k_coarse_matvec<R><<<blocks, threads, 0, s>>>(coarse_inverse<R>(h), reinterpret_cast<const R *>(v.b),
@@ -1150,8 +1172,11 @@ mg_status setup_hierarchy(mg_handle *h, const double *lam, const double *const f
         double *Lb = h->Mwork, *Uc = h->Mwork + (long long)h->nc * kl;
         k_band_lu_window<<<1, kWinThreads, (size_t)wsm, a>>>(h->Mtmp, h->nc, kl, kl, h->piv, h->dinv, Lb, Uc,
                                                              h->err_d);
-        k_band_inv_block<<<(h->nc + warps - 1) / warps, 32 * warps, (size_t)ism, a>>>(
-            Lb, Uc, h->piv, h->dinv, h->nc, kl, kl, h->Minv, mixed ? h->Minv32 : nullptr, h->err_d);
+        if (h->coarse_factors)           // the cycles solve from Lb and the scaled Uc (k_coarse_lu)
+            k_scale_uc<<<lin_blocks((long long)h->nc * 2 * kl), 256, 0, a>>>(Uc, h->dinv, h->nc, kl, kl, h->err_d);
+        else
+            k_band_inv_block<<<(h->nc + warps - 1) / warps, 32 * warps, (size_t)ism, a>>>(
+                Lb, Uc, h->piv, h->dinv, h->nc, kl, kl, h->Minv, mixed ? h->Minv32 : nullptr, h->err_d);
     } else {
         k_band_lu<<<1, dim3(32, 32, 1), 0, a>>>(h->Mtmp, h->nc, kl, kl, h->piv, h->dinv, h->err_d);
         k_band_inv_cols<<<(h->nc + 127) / 128, 128, 0, a>>>(h->Mtmp, h->piv, h->dinv, h->nc, kl, kl, h->Mwork,
@@ -1402,6 +1427,7 @@ mg_status check_handle(const mg_handle *h, bool need_coeffs) {
 
 // ---------------------------------------------------------------- tuning
 bool tail_level_ok(const mg_handle *h, int l, int ctas = kTailCtas) {
+    if (h->coarse_factors) return false;     // the tail multiplies by the coarsest inverse
     if (!(l >= 1 && h->nlev - l >= 2 && h->nlev - l <= kTailMaxLevels && h->L[l].N <= kTailMaxCells)) return false;
     size_t smem = 0;
     if (h->opt.precision == MG_MIXED) tail_args<float>(h, l, ctas, &smem);
@@ -1571,6 +1597,7 @@ mg_status mg_default_options(mg_options *o) {
     o->smoother = MG_SMOOTH_RBGS;
     o->omega = 0.8;
     o->fp64_jump_ratio = 2.0;
+    o->coarse_solve = MG_COARSE_AUTO;
     return MG_OK;
 }
 

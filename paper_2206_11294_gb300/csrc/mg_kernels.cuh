@@ -1708,4 +1708,171 @@ __global__ void __launch_bounds__(256) k_band_inv_block(const double *__restrict
     band_inv_block(Lb, Uc, piv, dinv, n, kl, ku, Minv, Minv32, err, blockIdx.x * (blockDim.x >> 5));
 }
 
+// ---------------------------------------------------------------------------
+// The coarsest solve from the factors (mg_options.coarse_solve AUTO on the
+// windowed path): x = U^-1 L^-1 P b with the factors k_band_lu_window leaves
+// (Lb, piv; Uc with each column scaled by its reciprocal pivot, see
+// k_scale_uc), one block of kLuSolveThreads per system, in FP64 whatever R
+// is.  The steps are those of one column of k_band_inv_block with b in place
+// of e_j: the row swaps and multipliers in the order the factorisation
+// applied them, then U from the last row up.  A step's multiply-adds are
+// spread over the block's four warps, one per SM sub-partition: GB300's FP64
+// pipe issues a warp's FMA over many cycles, so one warp would take four
+// times as long per step.  One barrier per step, two for a forward step that
+// swaps rows: every thread reads the pivot row's value itself (and, for a
+// swap, y_k, before thread 0 overwrites it); the thread that updates the
+// pivot row starts from the value swapped out of row k.  In the backward
+// step the scaled column puts no division on the chain (x = dinv y at the
+// end, all threads).  y sits in
+// shared memory; the rows of Lb (and piv) or Uc the next kLuSolveRows steps
+// use are staged by asynchronous 8-byte copies one chunk ahead,
+// double-buffered.  With the coarsest matrix singular (err & 4, reported by
+// the solve) x is set to 0.
+// ---------------------------------------------------------------------------
+constexpr int kLuSolveRows = 16;
+constexpr int kLuSolveThreads = 128;
+
+// Shared memory of k_coarse_lu (bytes): y, then two chunks each of Lb rows,
+// Uc rows and piv.
+inline long long coarse_lu_smem(int n, int kl, int ku) {
+    const long long C = kl + ku + 1;
+    return 8LL * (n + 2LL * kLuSolveRows * (kl + C)) + 4LL * 2 * kLuSolveRows;
+}
+
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"((unsigned)__cvta_generic_to_shared(smem)),
+                 "l"(gmem)
+                 : "memory");
+}
+
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"((unsigned)__cvta_generic_to_shared(smem)),
+                 "l"(gmem)
+                 : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Uc[i][o] *= dinv[i] (1 <= o <= kl + ku): column i of U over its pivot, so
+// that the backward step updates with y_i itself (one system, grid-stride).
+__device__ __forceinline__ void scale_uc(double *__restrict__ Uc, const double *__restrict__ dinv, int n, int kl,
+                                         int ku, const int *__restrict__ err, long long start, long long stride) {
+    if (*(volatile const int *)err & 4) return;
+    const int ur = kl + ku, C = ur + 1;
+    for (long long q = start; q < (long long)n * ur; q += stride) {
+        const int i = (int)(q / ur), o = 1 + (int)(q - (long long)i * ur);
+        Uc[(long long)i * C + o] *= dinv[i];
+    }
+}
+
+__global__ void k_scale_uc(double *__restrict__ Uc, const double *__restrict__ dinv, int n, int kl, int ku,
+                           const int *__restrict__ err) {
+    scale_uc(Uc, dinv, n, kl, ku, err, blockIdx.x * (long long)blockDim.x + threadIdx.x,
+             (long long)gridDim.x * blockDim.x);
+}
+
+template <typename R>
+__device__ void coarse_lu_solve_block(const double *__restrict__ Lb, const double *__restrict__ Uc,
+                                      const int *__restrict__ piv, const double *__restrict__ dinv, int n, int kl,
+                                      int ku, const R *__restrict__ b, R *__restrict__ x,
+                                      const int *__restrict__ err, double *sm) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    if (*(volatile const int *)err & 4) {
+        for (int i = tid; i < n; i += nt) x[i] = R(0);
+        return;
+    }
+    const int C = kl + ku + 1, ur = kl + ku;
+    double *y = sm;
+    double *Lbuf = y + n;                                      // 2 x kLuSolveRows x kl
+    double *Ubuf = Lbuf + 2 * kLuSolveRows * kl;                // 2 x kLuSolveRows x C
+    int *pbuf = reinterpret_cast<int *>(Ubuf + 2 * kLuSolveRows * C);   // 2 x kLuSolveRows
+    const int nch = (n + kLuSolveRows - 1) / kLuSolveRows;
+    for (int i = tid; i < n; i += nt) y[i] = (double)b[i];
+    // forward: rows k0 .. k0 + cnt - 1 of Lb and piv per chunk
+    auto stage_l = [&](int k0, int buf) {
+        const int cnt = min(kLuSolveRows, n - k0);
+        const double *src = Lb + (long long)k0 * kl;
+        double *dst = Lbuf + buf * kLuSolveRows * kl;
+        for (int q = tid; q < cnt * kl; q += nt) cp_async8(dst + q, src + q);
+        for (int q = tid; q < cnt; q += nt) cp_async4(pbuf + buf * kLuSolveRows + q, piv + k0 + q);
+        cp_async_commit();
+    };
+    stage_l(0, 0);
+    for (int c = 0; c < nch; c++) {
+        const int k0 = c * kLuSolveRows, cnt = min(kLuSolveRows, n - k0), buf = c & 1;
+        __syncthreads();                        // chunk c - 1, in the other buffer, is done with
+        if (c + 1 < nch) {
+            stage_l(k0 + kLuSolveRows, buf ^ 1);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncthreads();
+        const double *Lc = Lbuf + buf * kLuSolveRows * kl;
+        const int *pc = pbuf + buf * kLuSolveRows;
+        for (int t = 0; t < cnt; t++) {
+            const int k = k0 + t, p = pc[t];
+            const double yk = y[p];                // y_k after the swap (p == k: no swap)
+            double a = 0.0;
+            if (p != k) {                          // the same branch in every thread
+                a = y[k];
+                __syncthreads();                   // both read everywhere before either changes
+                if (tid == 0) y[k] = yk;
+            }
+            const int m = min(kl, n - 1 - k);
+            for (int q = tid; q < m; q += nt) {
+                const int r = k + 1 + q;
+                const double v = r == p ? a : y[r];
+                y[r] = v - Lc[t * kl + q] * yk;
+            }
+            __syncthreads();
+        }
+    }
+    // backward: rows hi - cnt + 1 .. hi of the scaled Uc per chunk, from the last row up
+    auto stage_u = [&](int hi, int buf) {
+        const int cnt = min(kLuSolveRows, hi + 1), lo = hi - cnt + 1;
+        const double *src = Uc + (long long)lo * C;
+        double *dst = Ubuf + buf * kLuSolveRows * C;
+        for (int q = tid; q < cnt * C; q += nt) cp_async8(dst + q, src + q);
+        cp_async_commit();
+    };
+    stage_u(n - 1, 0);
+    for (int c = 0; c < nch; c++) {
+        const int hi = n - 1 - c * kLuSolveRows, cnt = min(kLuSolveRows, hi + 1), lo = hi - cnt + 1, buf = c & 1;
+        __syncthreads();
+        if (c + 1 < nch) {
+            stage_u(hi - kLuSolveRows, buf ^ 1);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncthreads();
+        const double *Ucc = Ubuf + buf * kLuSolveRows * C;
+        for (int t = cnt - 1; t >= 0; t--) {
+            const int i = lo + t;
+            const double yi = y[i];
+            const int m = min(ur, i);
+            for (int o = 1 + tid; o <= m; o += nt) y[i - o] -= Ucc[t * C + o] * yi;
+            __syncthreads();
+        }
+    }
+    for (int i = tid; i < n; i += nt) x[i] = (R)(y[i] * dinv[i]);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kLuSolveThreads) k_coarse_lu(const double *__restrict__ Lb,
+                                                               const double *__restrict__ Uc,
+                                                               const int *__restrict__ piv,
+                                                               const double *__restrict__ dinv, int n, int kl, int ku,
+                                                               const R *__restrict__ b, R *__restrict__ x,
+                                                               const int *__restrict__ err) {
+    extern __shared__ double lusm[];
+    coarse_lu_solve_block<R>(Lb, Uc, piv, dinv, n, kl, ku, b, x, err, lusm);
+}
+
 }  // namespace cmg

@@ -43,6 +43,7 @@ def test_default_options(lib):
     assert o.rtol == 1e-10
     assert o.cycle == B.CYCLES["V"] == 0 and B.CYCLES == {"V": 0, "W": 1, "F": 2}
     assert o.smoother == B.SMOOTHERS["rbgs"] == 0 and o.omega == 0.8 and o.fp64_jump_ratio == 2.0
+    assert o.coarse_solve == B.COARSE["auto"] == 0 and B.COARSE == {"auto": 0, "inverse": 1}
 
 
 def test_cycle_option_validated(lib):
@@ -92,6 +93,8 @@ def test_workspace_size_scales_with_levels(lib):
     ({}, dict(smoother="wjac", omega=1.5)),
     ({}, dict(fp64_jump_ratio=0.5)),
     ({}, dict(fp64_jump_ratio=float("inf"))),
+    ({}, dict(coarse=2)),
+    ({}, dict(coarse=-1)),
 ])
 def test_argument_validation(lib, kw, okw):
     st, _ = _size(lib, _grid(**kw), **okw)
@@ -156,3 +159,20 @@ def test_noalloc_checks_grids_like_mg_create(lib, bad):
     pa = (C.c_void_p * 3)(p, p, p)
     st = lib.mg_residual_norms_noalloc(C.byref(g), p, pa, pa, p, p, p, None)
     assert st_create == st == B.MG_ERR_INVALID_ARG, (st_create, st, B.last_error())
+
+
+def test_factored_coarse_solve_needs_no_inverse(lib):
+    """With the default coarse solve a 31 x 31 coarsest level (n = 992: 1922
+    unknowns, the windowed path) keeps its LU factors and no dense inverse:
+    the workspace is smaller by the FP64 inverse (and its FP32 copy in mixed
+    precision) than with MG_COARSE_INVERSE.  Small coarsest levels are the
+    same either way."""
+    nc = 2 * 31 * 31
+    for prec, per in (("fp64", 8), ("mixed", 12)):
+        st, auto = _size(lib, _grid(n=(992, 992, 1), h=1 / 992), precision=prec)
+        st2, inv = _size(lib, _grid(n=(992, 992, 1), h=1 / 992), precision=prec, coarse="inverse")
+        assert st == st2 == 0
+        assert 0 <= (inv - auto) - per * nc * nc <= 4096
+    st, a = _size(lib, _grid(n=(1024, 1024, 1), h=1 / 1024))
+    st2, b = _size(lib, _grid(n=(1024, 1024, 1), h=1 / 1024), coarse="inverse")
+    assert st == st2 == 0 and a == b

@@ -288,16 +288,18 @@ def test_batch_3d_rejects_fused(torch_cuda):
         s.close()
 
 
+@pytest.mark.parametrize("coarse", ["auto", "inverse"])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_batch_banded_coarsest_path(torch_cuda, precision):
-    """Problems whose coarsest level has more than 128 unknowns (15 x 15 and
-    13 x 13 cells) take the banded inverse, batched over problems: same
-    results as the per-handle set-up, bit for bit."""
+def test_batch_banded_coarsest_path(torch_cuda, precision, coarse):
+    """Problems whose coarsest level has more than 128 unknowns (31 x 31, 15 x
+    15 and 13 x 13 cells) take the windowed banded LU, batched over problems,
+    and either solve from the factors in each cycle (auto) or form the
+    inverse: same results as the per-handle set-up, bit for bit."""
     from paper_2206_11294_gb300.binding import Batch, Solver
     torch = torch_cuda
     probs = [I.bubble_2d(n=n, seed=300 + q, n_bubbles=2, rmin=0.05, rmax=0.15, centred=False, gas_rho=1.0,
-                         name=f"m{q}") for q, n in enumerate([480, 416, 64, 480])]
-    kw = dict(precision=precision, rtol=1e-10, max_cycles=60)
+                         name=f"m{q}") for q, n in enumerate([480, 416, 64, 480, 992])]
+    kw = dict(precision=precision, rtol=1e-10, max_cycles=60, coarse=coarse)
     ref = _solvers(probs, **kw)
     assert all(len(s.levels()) >= 3 for s in ref)
     xs_ref = []

@@ -603,16 +603,18 @@ def _large_coarse_cases():
     }
 
 
+@pytest.mark.parametrize("coarse", ["auto", "inverse"])
 @pytest.mark.parametrize("name", ["2d_736_bubbles", "2d_stiff_9x13", "3d_5x7x3"])
-def test_large_coarsest_levels_vs_oracle(torch_cuda, orc, name):
-    """Coarsest levels above 128 unknowns take the windowed banded LU and the
-    block-column inverse: FP64 solves after fixed cycles match the oracle
-    (whose coarsest solve is Gaussian elimination) at the usual tolerance, and
-    mixed precision reaches the converged oracle."""
+def test_large_coarsest_levels_vs_oracle(torch_cuda, orc, name, coarse):
+    """Coarsest levels above 128 unknowns take the windowed banded LU; each
+    cycle then solves from the factors (auto) or multiplies by the
+    block-column inverse (inverse): FP64 solves after fixed cycles match the
+    oracle (whose coarsest solve is Gaussian elimination) at the usual
+    tolerance, and mixed precision reaches the converged oracle."""
     p = _large_coarse_cases()[name]
     g = p.grid.as_dict()
     tol = 1e-9 if "stiff" in name or "3d" in name else 1e-12
-    s = _solver(p, rtol=0.0, max_cycles=2)
+    s = _solver(p, rtol=0.0, max_cycles=2, coarse=coarse)
     lv = s.levels()
     assert 2 * int(np.prod(lv[-1])) > 128
     x = p.x0.copy()
@@ -621,9 +623,47 @@ def test_large_coarsest_levels_vs_oracle(torch_cuda, orc, name):
     assert st["cycles"] == 2 == cyc
     assert rel_dev(x, ref, p.x0) <= tol
     s.close()
-    s = _solver(p, precision="mixed", rtol=1e-12 if tol > 1e-12 else 1e-10, max_cycles=80)
+    s = _solver(p, precision="mixed", rtol=1e-12 if tol > 1e-12 else 1e-10, max_cycles=80, coarse=coarse)
     xm = p.x0.copy()
     s.solve(p.b, xm)
     conv, _, _ = orc.mg_solve(g, p.lam, p.fa, p.fk, p.b, p.x0, max_cycles=80, rtol=1e-13)
     assert rel_dev(xm, conv, p.x0) <= 1e-8
     s.close()
+
+
+@pytest.mark.parametrize("name", ["2d_736_bubbles", "2d_stiff_9x13", "3d_5x7x3"])
+def test_factored_coarse_solve_equals_inverse(torch_cuda, name):
+    """The two coarsest solves are exact up to rounding: the same cycle count
+    and results within 1e-13 of the deviation, FP64 and mixed (1e-11 on the
+    stiff and 3D cases, whose rows carry the 1e5 Pa background: a rounding
+    difference anywhere is amplified there as in the oracle comparisons).
+    The factored one forms no inverse (smaller workspace) and refuses the
+    tail kernel, which multiplies by the inverse; its autotuner picks no
+    tail.  The 5 x 7 x 3 coarsest level (210 unknowns, band 71) is too wide
+    for the windowed LU and keeps the inverse either way."""
+    from paper_2206_11294_gb300.binding import MgError, MG_ERR_INVALID_ARG
+    p = _large_coarse_cases()[name]
+    tol = 1e-11 if "stiff" in name or "3d" in name else 1e-13
+    factored = "3d" not in name
+    for prec, rtol in (("fp64", 1e-10), ("mixed", 1e-10)):
+        a = _solver(p, precision=prec, rtol=rtol, max_cycles=80)
+        b = _solver(p, precision=prec, rtol=rtol, max_cycles=80, coarse="inverse")
+        assert (a.workspace_bytes < b.workspace_bytes) if factored else (a.workspace_bytes == b.workspace_bytes)
+        xa, xb = p.x0.copy(), p.x0.copy()
+        sa, sb = a.solve(p.b, xa), b.solve(p.b, xb)
+        assert sa["cycles"] == sb["cycles"] and sa["outer"] == sb["outer"]
+        assert rel_dev(xa, xb, p.x0) <= tol
+        if factored:
+            t = a.tuning()
+            n = t["levels"]
+            assert t["tail_level"] >= n
+            for lvl in range(1, n - 1):
+                with pytest.raises(MgError) as e:
+                    a.set_tuning(dict(t, tail_level=lvl))
+                assert e.value.status == MG_ERR_INVALID_ARG
+            tuned, _ = a.autotune(reps=1)
+            assert tuned["tail_level"] >= n
+            x2 = p.x0.copy()
+            assert a.solve(p.b, x2)["cycles"] == sa["cycles"] and np.array_equal(x2, xa)
+        a.close()
+        b.close()

@@ -37,8 +37,11 @@ PROBS = _problems()
 
 
 def _solve(p, tuning=None, **kw):
+    """The coarsest solve by the inverse: the tail kernel, one of the choices
+    under test, multiplies by it (the 3D problem's 8 x 4 x 4 coarsest level
+    would otherwise solve from its factors and refuse every tail)."""
     from paper_2206_11294_gb300.binding import Solver
-    s = Solver(p.grid, rtol=1e-10, max_cycles=60, **kw)
+    s = Solver(p.grid, rtol=1e-10, max_cycles=60, coarse="inverse", **kw)
     s.set_coeffs(p.lam, p.fa, p.fk)
     if tuning is not None:
         s.set_tuning(tuning)
