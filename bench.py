@@ -999,7 +999,7 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=30.0)
     ap.add_argument("--serve-max", type=int, default=2000)
     ap.add_argument("--serve-budget", type=int, default=120 << 30)
-    ap.add_argument("--serve-per-shape", type=int, default=2, help="hierarchies per shape in the warm pool")
+    ap.add_argument("--serve-per-shape", type=int, default=4, help="hierarchies per shape in the warm pool")
     ap.add_argument("--cycle", default="V", choices=["V", "W", "F"], help="cycle of the correction solve")
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per launch of the dominant kernel from an ncu capture")
