@@ -591,6 +591,71 @@ def run_wall3d(args):
     return out
 
 
+class nvtx_range:
+    """An NVTX range around a timed loop, so that a profiler can take its
+    kernels alone (ncu --nvtx --nvtx-include "<name>/")."""
+
+    def __init__(self, name: str):
+        self.name = name
+
+    def __enter__(self):
+        import torch
+        torch.cuda.nvtx.range_push(self.name)
+
+    def __exit__(self, *exc):
+        import torch
+        torch.cuda.nvtx.range_pop()
+
+
+def run_coarse(args):
+    """Grids whose coarsest level is large (an odd factor of 9 or more: 2D n =
+    480, 736, 992, coarsest 15^2, 23^2, 31^2; 3D n = 96, 160, 224, coarsest
+    6^3, 5^3, 7^3), set-up + solve to 1e-10 per step, FP64 and mixed, with the
+    coarsest level solved from its LU factors (coarse_solve AUTO) and through
+    the inverse formed at set-up (INVERSE); literal units, autotuned."""
+    import numpy as np
+    import torch
+    from paper_2206_11294_gb300 import inputs as I
+    from paper_2206_11294_gb300.binding import Solver
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    probs = [I.bubble_2d(n=n, seed=5, n_bubbles=4, rmin=0.02, rmax=0.08, centred=False) for n in (480, 736, 992)]
+    probs += [I.bubble_wall_3d(n=n, seed=700) for n in (96, 160, 224)]
+    out = {"workload": "large coarsest levels: set-up + solve to 1e-10 per step", "cases": []}
+    for p in probs:
+        d = dict(lam=T(p.lam), fa=[T(f) for f in p.fa], fk=[T(f) for f in p.fk], b=T(p.b), x0=T(p.x0), x=T(p.x0))
+        case = {"grid": "x".join(str(v) for v in p.grid.n[:p.grid.dim]), "cells": p.grid.N}
+        for prec in ("fp64", "mixed"):
+            for coarse in ("auto", "inverse"):
+                s = Solver(p.grid, precision=prec, rtol=1e-10, max_cycles=60, stream=stream, coarse=coarse)
+                case["coarsest"] = "x".join(str(v) for v in s.levels()[-1][:p.grid.dim])
+                s.set_coeffs(d["lam"], d["fa"], d["fk"])
+                if not args.no_tune:
+                    s.autotune(args.tune_reps)
+                for _ in range(args.warmup):
+                    d["x"].copy_(d["x0"])
+                    s.set_coeffs(d["lam"], d["fa"], d["fk"])
+                    s.solve(d["b"], d["x"])
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                with nvtx_range(f"coarse_{case['grid']}_{prec}_{coarse}"):
+                    for _ in range(args.steps):
+                        d["x"].copy_(d["x0"])
+                        s.set_coeffs(d["lam"], d["fa"], d["fk"])
+                        st = s.solve(d["b"], d["x"])
+                e1.record(stream)
+                torch.cuda.synchronize()
+                case[f"{prec}_{coarse}"] = {"ms_per_step": e0.elapsed_time(e1) / args.steps, "cycles": st["cycles"],
+                                            "workspace_mb": s.workspace_bytes / 1e6}
+                s.close()
+        out["cases"].append(case)
+    out["l2"] = "not flushed (one problem resident)"
+    out["data"] = "synthetic (seeded bubble fields)"
+    return out
+
+
 def run_adaptive(args):
     """A refined-patch (adaptive) grid against the uniform grid of its finest
     spacing: one bubble of radius 0.1 at the centre of the unit square, walls;
@@ -636,10 +701,11 @@ def run_adaptive(args):
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        for _ in range(args.steps):
-            xb.copy_(d["xb0"]); xf.copy_(d["xf0"])
-            c.set_coeffs(d["lb"], d["fab"], d["fkb"], d["lf"], d["faf"], d["fkf"])
-            c.solve(d["bb"], d["bf"], xb, xf, need, norms=False)
+        with nvtx_range(f"adaptive_{label}"):
+            for _ in range(args.steps):
+                xb.copy_(d["xb0"]); xf.copy_(d["xf0"])
+                c.set_coeffs(d["lb"], d["fab"], d["fkb"], d["lf"], d["faf"], d["fkf"])
+                c.solve(d["bb"], d["bf"], xb, xf, need, norms=False)
         e1.record(stream)
         torch.cuda.synchronize()
         ms_c = e0.elapsed_time(e1) / args.steps
@@ -992,7 +1058,7 @@ def main():
     ap.add_argument("--tune-reps", type=int, default=5)
     ap.add_argument("--tuning-table", default=None, help="JSON table of autotuned choices to apply (and extend)")
     ap.add_argument("--workload", default="bubbles",
-                    choices=["bubbles", "batch", "serve", "wall3d", "timestep", "momentum", "adaptive"])
+                    choices=["bubbles", "batch", "serve", "wall3d", "timestep", "momentum", "adaptive", "coarse"])
     ap.add_argument("--n3d", type=int, default=256)
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--serve-rates", type=float, nargs="+", default=[10, 30, 100, 300, 1000, 2000])
@@ -1009,7 +1075,7 @@ def main():
     if args.workload != "bubbles":
         if rank == 0:
             out = {"batch": run_batch, "serve": run_serve, "wall3d": run_wall3d, "timestep": run_timestep,
-                   "momentum": run_momentum, "adaptive": run_adaptive}[args.workload](args)
+                   "momentum": run_momentum, "adaptive": run_adaptive, "coarse": run_coarse}[args.workload](args)
             print(json.dumps(out), flush=True)
         return
     if args.impl == "ours" and world > 1:
