@@ -317,6 +317,15 @@ __global__ void __launch_bounds__(256) kb_scale_uc(const BCoarse *__restrict__ c
              blockIdx.x * (long long)blockDim.x + threadIdx.x, (long long)gridDim.x * blockDim.x);
 }
 
+// The blocked LU on one cluster per problem (band_lu_blocked_block): cluster c factors problem ids[c].
+__global__ void __launch_bounds__(kLuBlockedThreads) kb_band_lu_blocked(const BCoarse *__restrict__ co,
+                                                                        const int *__restrict__ ids) {
+    extern __shared__ double bbsm[];
+    const BCoarse &C = co[ids[blockIdx.x / kLuClusterCtas]];
+    band_lu_blocked_block(C.M, C.nc, C.kl, C.kl, C.piv, C.dinv, C.Mwork, C.Mwork + (long long)C.nc * C.kl, C.err,
+                          bbsm);
+}
+
 __global__ void __launch_bounds__(256) kb_band_inv_block(const BCoarse *__restrict__ co, const int *__restrict__ ids) {
     const BCoarse &C = co[ids[blockIdx.y]];
     const int j0 = blockIdx.x * (blockDim.x >> 5);
@@ -1211,7 +1220,20 @@ mg_status mg_batch_set_coeffs(mg_batch *b, const double *const *lambda, const do
         const unsigned nw = (unsigned)b->win_coarse.size();
         CK(raise_smem_limit((const void *)kb_band_lu_window, (int)b->win_smem));
         CK(raise_smem_limit((const void *)kb_band_inv_block, (int)b->win_inv_smem));
-        kb_band_lu_window<<<nw, kWinThreads, b->win_smem, s>>>(b->co, b->win_ids);
+        {   // blocked over one cluster per problem where every problem's shared memory fits, else one block each
+            size_t bsm = 0;
+            bool blocked = true;
+            for (int p : b->win_coarse) {
+                const mg_handle *hp = b->h[p];
+                blocked = blocked && lu_blocked_ok(hp->nc, hp->coarse_kl);
+                bsm = std::max(bsm, (size_t)band_blocked_smem(hp->nc, hp->coarse_kl, hp->coarse_kl));
+            }
+            if (blocked)
+                CK(launch_cluster(kb_band_lu_blocked, s, (int)nw, kLuBlockedThreads, bsm, (const BCoarse *)b->co,
+                                  (const int *)b->win_ids));
+            else
+                kb_band_lu_window<<<nw, kWinThreads, b->win_smem, s>>>(b->co, b->win_ids);
+        }
         b->launches++;
         if (b->win_factors)                 // the cycles solve from Lb and the scaled Uc (kb_coarse_lu)
             kb_scale_uc<<<dim3(64, nw), 256, 0, s>>>(b->co, b->win_ids);

@@ -999,6 +999,39 @@ bool window_path(int n, int kl) {
            (long long)n * (kl + 2LL * kl + 1) <= (long long)n * n;
 }
 
+// The windowed path's LU blocked over one cluster per coarsest matrix
+// (k_band_lu_blocked; the same factors as k_band_lu_window) where its shared
+// memory fits.
+bool lu_blocked_ok(int n, int kl) { return band_blocked_smem(n, kl, kl) <= kWinSmemMax; }
+
+// Launches kern on `clusters` clusters of kLuClusterCtas CTAs of `threads` threads.
+template <typename... Args>
+cudaError_t launch_cluster(void (*kern)(Args...), cudaStream_t s, int clusters, int threads, size_t smem,
+                           Args... args) {
+    cudaError_t e = raise_smem_limit((const void *)kern, (int)smem);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg;
+    std::memset(&cfg, 0, sizeof(cfg));
+    cfg.gridDim = dim3((unsigned)(kLuClusterCtas * clusters), 1, 1);
+    cfg.blockDim = dim3((unsigned)threads, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = kLuClusterCtas;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
+cudaError_t launch_lu_blocked(cudaStream_t s, const double *M, int n, int kl, int *piv, double *dinv, double *Lb,
+                              double *Uc, int *err) {
+    return launch_cluster(k_band_lu_blocked, s, 1, kLuBlockedThreads, (size_t)band_blocked_smem(n, kl, kl), M, n, kl,
+                          kl, piv, dinv, Lb, Uc, err);
+}
+
 // ---------------------------------------------------------------- set-up
 SetupOut setup_out(const LevelBuf &l, bool mixed) {
     SetupOut o;
@@ -1170,8 +1203,11 @@ mg_status setup_hierarchy(mg_handle *h, const double *lam, const double *const f
         CK(raise_smem_limit((const void *)k_band_lu_window, (int)wsm));
         CK(raise_smem_limit((const void *)k_band_inv_block, (int)ism));
         double *Lb = h->Mwork, *Uc = h->Mwork + (long long)h->nc * kl;
-        k_band_lu_window<<<1, kWinThreads, (size_t)wsm, a>>>(h->Mtmp, h->nc, kl, kl, h->piv, h->dinv, Lb, Uc,
-                                                             h->err_d);
+        if (lu_blocked_ok(h->nc, kl))
+            CK(launch_lu_blocked(a, h->Mtmp, h->nc, kl, h->piv, h->dinv, Lb, Uc, h->err_d));
+        else
+            k_band_lu_window<<<1, kWinThreads, (size_t)wsm, a>>>(h->Mtmp, h->nc, kl, kl, h->piv, h->dinv, Lb, Uc,
+                                                                 h->err_d);
         if (h->coarse_factors)           // the cycles solve from Lb and the scaled Uc (k_coarse_lu)
             k_scale_uc<<<lin_blocks((long long)h->nc * 2 * kl), 256, 0, a>>>(Uc, h->dinv, h->nc, kl, kl, h->err_d);
         else

@@ -1631,6 +1631,216 @@ __global__ void __launch_bounds__(kWinThreads) k_band_lu_window(const double *__
     band_lu_window_block(M, n, kl, ku, piv, dinv, Lb, Uc, err);
 }
 
+// ---------------------------------------------------------------------------
+// The windowed LU blocked over a thread-block cluster (k_band_lu_blocked).
+// The single-block kernel runs every step's rank-1 update of the whole window
+// on one SM, whose FP64 pipe bounds it.  Here the columns are grouped in
+// panels of kLuNb; panel b belongs to CTA b mod kLuClusterCtas, which keeps
+// each of its columns j as the vector of rows j - (kl + ku) .. j + kl (every
+// row a step can reach it in).  For panel b the owner runs the panel's steps
+// on the panel's own columns only (pivot, swap, multipliers, row of U,
+// update), then publishes the pivots and multipliers; after one cluster
+// barrier every CTA applies those steps, in order, to each of its columns
+// after the panel that they reach (swap, row of U, update), one warp per
+// column.  Every entry receives the same multiply-adds in the same order as
+// in the unblocked factorisation, so the factors are the single-block
+// kernel's bit for bit.  A panel becomes resident kLuNb + kl + ku columns
+// before its first step, in a slot freed long before.  A zero pivot stops
+// every CTA after the same barrier; a last barrier keeps each CTA's shared
+// memory alive until no other CTA reads it.
+// ---------------------------------------------------------------------------
+constexpr int kLuClusterCtas = 8;
+constexpr int kLuNb = 16;
+constexpr int kLuBlockedThreads = 512;
+
+struct LuBlockedShape {
+    int ur, C, Lc, NP, S, npan, bsz;
+};
+
+__host__ __device__ inline LuBlockedShape lu_blocked_shape(int n, int kl, int ku) {
+    LuBlockedShape g;
+    g.ur = kl + ku;
+    g.C = g.ur + 1;
+    g.Lc = g.ur + kl + 1;                                   // rows j - ur .. j + kl of column j
+    g.NP = (kLuNb + g.ur + kLuNb - 1) / kLuNb;              // panels a panel's steps reach
+    g.S = (g.NP + kLuClusterCtas - 1) / kLuClusterCtas + 1; // resident panels per CTA
+    g.npan = (n + kLuNb - 1) / kLuNb;
+    g.bsz = kLuNb * kl + kLuNb + 1;                         // multipliers, pivots, stop flag
+    return g;
+}
+
+// Shared memory of k_band_lu_blocked (bytes), at least 116 KB: more than half
+// of an SM's, so that no two CTAs of a cluster share an SM's FP64 pipe.
+inline long long band_blocked_smem(int n, int kl, int ku) {
+    const LuBlockedShape g = lu_blocked_shape(n, kl, ku);
+    const long long need = 8LL * ((long long)g.S * kLuNb * g.Lc + 3LL * g.bsz + kLuNb);
+    return need > 116LL * 1024 ? need : 116LL * 1024;
+}
+
+__device__ __forceinline__ void band_lu_blocked_block(const double *__restrict__ M, int n, int kl, int ku,
+                                                      int *__restrict__ piv, double *__restrict__ dinv,
+                                                      double *__restrict__ Lb, double *__restrict__ Uc,
+                                                      int *__restrict__ err, double *sm) {
+    namespace cg = cooperative_groups;
+    constexpr int P = kLuClusterCtas, NB = kLuNb;
+    cg::cluster_group cl = cg::this_cluster();
+    __shared__ long long s_best;
+    __shared__ int s_p;
+    __shared__ double s_pinv;
+    const int rank = (int)cl.block_rank();
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+    const LuBlockedShape g = lu_blocked_shape(n, kl, ku);
+    const int ur = g.ur, C = g.C, Lc = g.Lc;
+    double *store = sm;                                     // S x NB x Lc
+    double *bc = store + (long long)g.S * NB * Lc;          // 2 x bsz: this CTA's broadcasts
+    double *loc = bc + 2 * g.bsz;                           // bsz: the panel owner's, copied
+    double *urow = loc + g.bsz;                             // NB: row p of U in the panel's columns
+    // column j of a panel this CTA owns
+    auto colp = [&](int j) {
+        const int b = j / NB;
+        return store + ((long long)((b / P) % g.S) * NB + (j - b * NB)) * Lc;
+    };
+    auto load_panel = [&](int b) {
+        if (b >= g.npan || b % P != rank) return;
+        double *base = colp(b * NB);
+        for (int q = tid; q < NB * Lc; q += nt) {
+            const int c = q / Lc, idx = q - c * Lc, j = b * NB + c, r = j - ur + idx;
+            base[q] = (j < n && r >= 0 && r < n) ? M[(long long)r * n + j] : 0.0;
+        }
+    };
+    for (int b = 0; b < g.NP && b < g.npan; b++) load_panel(b);
+    __syncthreads();
+    int kfail = n;
+    for (int b = 0; b < g.npan; b++) {
+        const int o = b % P, k0 = b * NB, k1 = min(n, k0 + NB);
+        double *bs = bc + (b & 1) * g.bsz;
+        if (rank == o) {                                    // the same branch in every thread of this CTA
+            if (tid == 0) bs[NB * kl + NB] = -1.0;
+            for (int p = k0; p < k1; p++) {
+                double *cp = colp(p);
+                const int rl = min(n - 1, p + kl), nr = rl - p;
+                if (tid < 32) {                             // pivot: largest |a|, first row on ties
+                    long long best = -1;
+                    int br = p;
+                    for (int r = p + tid; r <= rl; r += 32) {
+                        const long long v = __double_as_longlong(cp[r - p + ur]) & 0x7fffffffffffffffLL;
+                        if (v > best) { best = v; br = r; }
+                    }
+                    for (int off = 16; off > 0; off >>= 1) {
+                        const long long ov = __shfl_down_sync(0xffffffffu, best, off);
+                        const int orr = __shfl_down_sync(0xffffffffu, br, off);
+                        if (ov > best || (ov == best && orr < br)) { best = ov; br = orr; }
+                    }
+                    if (tid == 0) {
+                        s_best = best;
+                        s_p = br;
+                    }
+                }
+                __syncthreads();
+                if (s_best <= 0) {                          // a zero column: stop here, every CTA at this panel
+                    if (tid == 0) bs[NB * kl + NB] = (double)p;
+                    __syncthreads();
+                    break;
+                }
+                const int pp = s_p;
+                if (tid < k1 - p) {                         // swap rows p and pp in the panel's columns p..k1-1
+                    const int j = p + tid;
+                    double *cj = colp(j);
+                    const int ia = p - j + ur, ib = pp - j + ur;
+                    const double a = cj[ia];
+                    cj[ia] = cj[ib];
+                    cj[ib] = a;
+                }
+                __syncthreads();
+                if (tid == 0) {
+                    s_pinv = 1.0 / cp[ur];
+                    piv[p] = pp;
+                    dinv[p] = s_pinv;
+                    bs[NB * kl + (p - k0)] = (double)pp;
+                }
+                __syncthreads();
+                const double pinv = s_pinv;
+                for (int q = tid; q < nr; q += nt) {
+                    const double l = cp[ur + 1 + q] * pinv;
+                    bs[(p - k0) * kl + q] = l;
+                    Lb[(long long)p * kl + q] = l;
+                }
+                if (tid < k1 - p - 1) {                     // row p of U in the panel's columns p+1..k1-1
+                    const int j = p + 1 + tid;
+                    const double u = colp(j)[p - j + ur];
+                    urow[tid] = u;
+                    Uc[(long long)j * C + (j - p)] = u;
+                }
+                __syncthreads();
+                for (int c = warp; c < k1 - p - 1; c += nw) {   // the panel's columns by warp, rows by lane
+                    const int j = p + 1 + c;
+                    double *cj = colp(j);
+                    const double u = urow[c];
+                    for (int q = lane; q < nr; q += 32) cj[p + 1 + q - j + ur] -= bs[(p - k0) * kl + q] * u;
+                }
+                __syncthreads();
+            }
+        }
+        cl.sync();                                          // panel b's broadcast is visible cluster-wide
+        const double *ob = cl.map_shared_rank(bs, o);
+        for (int q = tid; q < g.bsz; q += nt) loc[q] = ob[q];
+        __syncthreads();
+        const int stop = (int)loc[NB * kl + NB];            // read by every thread of every CTA
+        const int kend = stop >= 0 ? stop : k1;             // the panel's steps that ran
+        // this CTA's columns k1 .. min(n - 1, kend - 1 + ur), a warp each: panel b's steps, in order
+        const int hi = min(n - 1, kend - 1 + ur);
+        if (stop < 0 && k1 <= hi) {
+            const int pb = k1 / NB;                         // first panel after b
+            const int b1 = pb + ((rank - pb) % P + P) % P;  // this CTA's first panel >= pb
+            for (int c = warp; c < g.S * NB; c += nw) {
+                const int j = (b1 + (c / NB) * P) * NB + (c % NB);
+                if (j > hi) continue;
+                double *cj = colp(j);
+                for (int p = max(k0, j - ur); p < kend; p++) {
+                    const int pp = (int)loc[NB * kl + (p - k0)];
+                    const int ia = p - j + ur, ib = pp - j + ur;
+                    if (lane == 0 && pp != p) {
+                        const double a = cj[ia];
+                        cj[ia] = cj[ib];
+                        cj[ib] = a;
+                    }
+                    __syncwarp();
+                    const double u = cj[ia];
+                    if (lane == 0) Uc[(long long)j * C + (j - p)] = u;
+                    const int nr = min(n - 1, p + kl) - p;
+                    for (int q = lane; q < nr; q += 32) cj[p + 1 + q - j + ur] -= loc[(p - k0) * kl + q] * u;
+                    __syncwarp();
+                }
+            }
+        }
+        if (stop >= 0) {
+            kfail = stop;
+            break;
+        }
+        __syncthreads();
+        load_panel(b + g.NP);
+        __syncthreads();
+    }
+    if (kfail < n && rank == 0) {
+        for (int q = kfail + tid; q < n; q += nt) {
+            piv[q] = q;
+            dinv[q] = 0.0;
+        }
+        if (tid == 0) atomicOr(err, 4);
+    }
+    cl.sync();                                              // no CTA leaves while another may still read it
+}
+
+__global__ void __launch_bounds__(kLuBlockedThreads) k_band_lu_blocked(const double *__restrict__ M, int n, int kl,
+                                                                       int ku, int *__restrict__ piv,
+                                                                       double *__restrict__ dinv,
+                                                                       double *__restrict__ Lb,
+                                                                       double *__restrict__ Uc,
+                                                                       int *__restrict__ err) {
+    extern __shared__ double lbsm[];
+    band_lu_blocked_block(M, n, kl, ku, piv, dinv, Lb, Uc, err, lbsm);
+}
+
 // Columns j0 .. j0 + warps - 1 of the inverse (block of warps x 32 threads).
 __device__ __forceinline__ void band_inv_block(const double *__restrict__ Lb, const double *__restrict__ Uc,
                                                const int *__restrict__ piv, const double *__restrict__ dinv, int n,
