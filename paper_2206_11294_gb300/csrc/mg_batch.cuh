@@ -1220,9 +1220,11 @@ mg_status mg_batch_set_coeffs(mg_batch *b, const double *const *lambda, const do
         const unsigned nw = (unsigned)b->win_coarse.size();
         CK(raise_smem_limit((const void *)kb_band_lu_window, (int)b->win_smem));
         CK(raise_smem_limit((const void *)kb_band_inv_block, (int)b->win_inv_smem));
-        {   // blocked over one cluster per problem where every problem's shared memory fits, else one block each
+        {   // blocked over one cluster per problem where every problem's shared memory fits and all the clusters
+            // run at once (one SM per CTA), else one block each: a second wave of clusters would cost more than
+            // the blocked LU saves over all problems factoring side by side
             size_t bsm = 0;
-            bool blocked = true;
+            bool blocked = (long long)nw * kLuClusterCtas <= (long long)b->sms;
             for (int p : b->win_coarse) {
                 const mg_handle *hp = b->h[p];
                 blocked = blocked && lu_blocked_ok(hp->nc, hp->coarse_kl);

@@ -317,3 +317,34 @@ def test_batch_banded_coarsest_path(torch_cuda, precision, coarse):
     b.close()
     for s in ref + fresh:
         s.close()
+
+
+def test_window_and_blocked_lu_give_the_same_factors(torch_cuda):
+    """Twenty problems on the windowed coarse path (288^2: 9 x 9 coarsest
+    cells, 162 unknowns) are more than one wave of 8-CTA clusters, so the
+    batch factors them with the single-block windowed LU, while each solo
+    handle uses the LU blocked over a cluster.  The two factorisations do the
+    same multiply-adds per entry in the same order: batch and solo results
+    must agree bit for bit, in both precisions."""
+    from paper_2206_11294_gb300.binding import Batch, Solver
+    probs = [I.bubble_2d(n=288, seed=400 + q, n_bubbles=1 + q % 3, rmin=0.05, rmax=0.15, centred=False,
+                         gas_rho=1.0, name=f"w{q}") for q in range(20)]
+    for precision in ("fp64", "mixed"):
+        kw = dict(precision=precision, rtol=1e-10, max_cycles=60)
+        ref = _solvers(probs, **kw)
+        assert 2 * int(np.prod(ref[0].levels()[-1])) > 128
+        xs_ref = []
+        for s, p in zip(ref, probs):
+            x = p.x0.copy()
+            s.solve(p.b, x)
+            xs_ref.append(x)
+        fresh = [Solver(p.grid, **kw) for p in probs]
+        b = Batch(fresh)
+        b.set_coeffs([p.lam for p in probs], [p.fa for p in probs], [p.fk for p in probs])
+        xs = [p.x0.copy() for p in probs]
+        b.solve([p.b for p in probs], xs)
+        for q in range(len(probs)):
+            assert np.array_equal(xs[q], xs_ref[q]), (precision, q)
+        b.close()
+        for s in ref + fresh:
+            s.close()
