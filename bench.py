@@ -246,7 +246,8 @@ def run_ours(args, rank, world):
     if world > 1:
         dist.barrier()
     clk = clocks.stop() if clocks else None
-    dev_ms = sum(a.elapsed_time(b) for a, b in zip(starts, ends))
+    step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+    dev_ms = sum(step_ms)
     counters = [s.counters() for s in solvers]
     units = sum(p.grid.N * st["cycles"] for p, st in zip(probs * args.steps, stats)) / 1e6
     solves = len(stats)
@@ -330,7 +331,7 @@ def run_ours(args, rank, world):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        cpu = cpu_baseline(probs)
+        cpu = cpu_baseline(probs, batch_sample=not args.no_sub and not args.no_batch)
 
     subs = None
     if rank == 0 and world == 1 and not args.no_sub:
@@ -346,6 +347,7 @@ def run_ours(args, rank, world):
         "config": {"workload": "bubbles16_1024x1024 + axi_512x1024, set-up + solve to 1e-10 per step",
                    "cells_per_step": sum(p.grid.N for p in probs), "cycles_per_solve": cycles,
                    "solves_per_s": solves * world / tmax, "precision": args.precision,
+                   "step_ms_p10_p50_p90": [float(np.percentile(step_ms, q)) for q in (10, 50, 90)],
                    "cycle": f"{args.cycle}(2,2) red-black block GS, exact coarsest solve",
                    "l2": "flushed between steps",
                    "parallelism": f"replicas x{world}",
@@ -996,7 +998,7 @@ def _oracle_cycle_sample(probs, threaded):
     return units, time.perf_counter() - t0
 
 
-def cpu_baseline(probs, seconds: float = 10.0):
+def cpu_baseline(probs, seconds: float = 10.0, batch_sample: bool = False):
     """The oracle on every host core (OpenMP build), one V-cycle per problem
     repeated until about `seconds` of CPU time have passed: a bounded sample of
     the workload.  The single-thread build's figure for one such sample is
@@ -1010,10 +1012,19 @@ def cpu_baseline(probs, seconds: float = 10.0):
         u, t = _oracle_cycle_sample(probs, True)
         units, secs, reps = units + u, secs + t, reps + 1
     u1, t1 = _oracle_cycle_sample(probs, False)
-    return {"value": units / secs, "unit": UNIT, "cores": oracle.threads(True), "kind": "oracle",
-            "sample": f"{reps} x (1 V-cycle with hierarchy set-up and residuals on each of the {len(probs)} problems), "
-                      "OpenMP over the cells of each level / colour",
-            "seconds": secs, "single_thread_value": u1 / t1}
+    out = {"value": units / secs, "unit": UNIT, "cores": oracle.threads(True), "kind": "oracle",
+           "sample": f"{reps} x (1 V-cycle with hierarchy set-up and residuals on each of the {len(probs)} problems), "
+                     "OpenMP over the cells of each level / colour",
+           "seconds": secs, "single_thread_value": u1 / t1}
+    if batch_sample:
+        # the 256-problem batch's first 32 problems (the same seeded sizes and fields), one V-cycle each
+        from paper_2206_11294_gb300 import inputs as I
+        bp = I.batch_problems(count=32)
+        ub, tb = _oracle_cycle_sample(bp, True)
+        out["batch_sample"] = {"problems": len(bp), "cells": int(sum(p.grid.N for p in bp)),
+                               "mcell_vcycles_per_s": ub / tb, "seconds": tb,
+                               "sample": "1 V-cycle with set-up on each of the batch's first 32 problems, OpenMP"}
+    return out
 
 
 def run_reference(args, rank, world):

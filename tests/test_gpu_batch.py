@@ -348,3 +348,24 @@ def test_window_and_blocked_lu_give_the_same_factors(torch_cuda):
         b.close()
         for s in ref + fresh:
             s.close()
+
+
+def test_batch_sample_of_32_vs_oracle(torch_cuda, orc):
+    """The 256-problem batch workload's first 32 problems (the same seeded
+    sizes, 64^2 to 1024^2 in multiples of 32, and bubble fields), batched in
+    FP64 for two fixed cycles: each against the oracle's two cycles at 1e-12
+    of the deviation."""
+    from paper_2206_11294_gb300.binding import Batch
+    probs = I.batch_problems(count=32)
+    assert len({p.grid.n for p in probs}) > 10
+    solvers = _solvers(probs, rtol=0.0, max_cycles=2)
+    b = Batch(solvers)
+    xs = [p.x0.copy() for p in probs]
+    st = b.solve([p.b for p in probs], xs)
+    for q, p in enumerate(probs):
+        ref, cyc, _ = orc.mg_solve(p.grid.as_dict(), p.lam, p.fa, p.fk, p.b, p.x0, max_cycles=2, rtol=0.0)
+        assert st[q]["cycles"] == 2 == cyc
+        assert rel_dev(xs[q], ref, p.x0) <= 1e-12, (q, p.grid.n)
+    b.close()
+    for s in solvers:
+        s.close()
