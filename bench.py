@@ -663,11 +663,13 @@ def run_adaptive(args):
     spacing: one bubble of radius 0.1 at the centre of the unit square, walls;
     the composite grid is a 512^2 base grid whose box around the bubble is
     refined 2:1 (finest spacing 1/1024 there), the uniform one 1024^2.  Each
-    is set up and solved to a 1e-10 reduction of its residual norms (the
-    composite solve's cycle count found by a first solve with norms, then
-    timed without them; a composite norm that rounding stops above 1e-10
-    counts as converged within twice its floor), in the workloads' units and
-    at the paper's bubble scale."""
+    is set up and solved to a 1e-10 reduction of its residual norms, in the
+    workloads' units and at the paper's bubble scale, in FP64 and in mixed
+    precision (the composite's base correction in FP32; the uniform solve's
+    cycles in FP32 inside FP64 refinement).  The composite solve's cycle count
+    is found by a first solve with norms, then timed without them; a
+    composite norm that rounding stops above 1e-10 counts as converged within
+    twice its floor."""
     import numpy as np
     import torch
     from paper_2206_11294_gb300 import inputs as I
@@ -678,11 +680,13 @@ def run_adaptive(args):
     out = {"workload": "one bubble R = 0.1 at the centre: refined-patch grid (512^2 base, 2:1 box around the bubble) "
                        "against the uniform 1024^2 grid, set-up + solve to 1e-10 per step",
            "regimes": []}
-    for label, kw in (("literal", {}), ("stiff", dict(length=6.4e-3, dt=1e-5))):
+    cases = [(label, kw, prec) for prec in ("fp64", "mixed")
+             for label, kw in (("literal", {}), ("stiff", dict(length=6.4e-3, dt=1e-5)))]
+    for label, kw, prec in cases:
         b, p, box = I.composite_bubble(512, seed=31, centres=[[0.5, 0.5]], radii=[0.1], **kw)
         u = I.bubble_2d(1024, seed=31, rmin=0.1, rmax=0.1, **kw)        # centred: the same bubble
         cells = b.grid.N - (box[0][1] - box[0][0]) * (box[1][1] - box[1][0]) + p.grid.N
-        c = Composite(b.grid, box)
+        c = Composite(b.grid, box, precision=prec)
         d = dict(lb=T(b.lam), fab=[T(f) for f in b.fa], fkb=[T(f) for f in b.fk], lf=T(p.lam),
                  faf=[T(f) for f in p.fa], fkf=[T(f) for f in p.fk], bb=T(b.b), bf=T(p.b), xb0=T(b.x0), xf0=T(p.x0))
         c.set_coeffs(d["lb"], d["fab"], d["fkb"], d["lf"], d["faf"], d["fkf"])
@@ -703,7 +707,7 @@ def run_adaptive(args):
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        with nvtx_range(f"adaptive_{label}"):
+        with nvtx_range(f"adaptive_{label}_{prec}"):
             for _ in range(args.steps):
                 xb.copy_(d["xb0"]); xf.copy_(d["xf0"])
                 c.set_coeffs(d["lb"], d["fab"], d["fkb"], d["lf"], d["faf"], d["fkf"])
@@ -712,7 +716,7 @@ def run_adaptive(args):
         torch.cuda.synchronize()
         ms_c = e0.elapsed_time(e1) / args.steps
         c.close()
-        s = Solver(u.grid, rtol=1e-10, max_cycles=200)
+        s = Solver(u.grid, rtol=1e-10, max_cycles=200, precision=prec)
         du = dict(lam=T(u.lam), fa=[T(f) for f in u.fa], fk=[T(f) for f in u.fk], b=T(u.b), x0=T(u.x0))
         s.set_coeffs(du["lam"], du["fa"], du["fk"])
         if not args.no_tune:
@@ -728,7 +732,8 @@ def run_adaptive(args):
         torch.cuda.synchronize()
         ms_u = e0.elapsed_time(e1) / args.steps
         s.close()
-        out["regimes"].append({"regime": label, "composite_cells": cells, "uniform_cells": u.grid.N, "box": box,
+        out["regimes"].append({"regime": label, "precision": prec, "composite_cells": cells,
+                               "uniform_cells": u.grid.N, "box": box,
                                "composite_cycles": need, "composite_ms": ms_c,
                                "composite_reduction": [float(v) for v in red[need]],
                                "composite_floor": [float(v) for v in red.min(axis=0)],

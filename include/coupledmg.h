@@ -604,9 +604,13 @@ MG_API mg_status mg_copy_h2d_async(void *dst, const void *src, size_t bytes, voi
 typedef struct mg_composite mg_composite;
 
 /* grid: the base grid (dim 2, not axisymmetric; walls and Dirichlet sides);
- * box: base-cell range per axis, non-empty; opt: nu1, nu2 and coarse_min of
- * the cycles (precision must be MG_FP64; NULL: defaults); stream: cudaStream_t.
- * Allocates the base grid's hierarchy and the work arrays. */
+ * box: base-cell range per axis, non-empty; opt: nu1, nu2, coarse_min and
+ * coarse_solve of the cycles, and the precision: MG_FP64, or MG_MIXED, where
+ * the FAC cycle's base correction runs its V-cycle in FP32 (with FP64 2x2
+ * blocks at coefficient jumps, fp64_jump_ratio) while the composite
+ * residuals, the patch sweeps and the update stay FP64 (NULL: defaults);
+ * stream: cudaStream_t.  Allocates the base grid's hierarchy and the work
+ * arrays. */
 MG_API mg_status mg_composite_create(const mg_grid *grid, const int box[2][2], const mg_options *opt, void *stream,
                                      mg_composite **out);
 

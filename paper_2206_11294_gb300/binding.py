@@ -801,7 +801,8 @@ class Batch:
 class Composite:
     """mg_composite: a refined-patch (adaptive) grid, base grid plus one 2:1 box."""
 
-    def __init__(self, grid, box, nu1=2, nu2=2, coarse_min=4, device: Optional[int] = None, stream=None):
+    def __init__(self, grid, box, nu1=2, nu2=2, coarse_min=4, device: Optional[int] = None, stream=None,
+                 precision="fp64"):
         import torch
         lib = load()
         self._lib = lib
@@ -813,7 +814,7 @@ class Composite:
         if stream is None:
             stream = torch.cuda.current_stream(dev)
         self.stream = stream
-        o = make_options("fp64", 0.0, 1, nu1, nu2, coarse_min)
+        o = make_options(precision, 0.0, 1, nu1, nu2, coarse_min)
         b = ((C.c_int * 2) * 2)(*[(C.c_int * 2)(*self.box[a]) for a in range(2)])
         h = C.c_void_p()
         check(lib.mg_composite_create(C.byref(self.grid), b, C.byref(o), C.c_void_p(stream.cuda_stream), C.byref(h)))

@@ -1341,13 +1341,22 @@ mg_status correction_cycles(mg_handle *h, const double2 *rhs) {
 
 // The same correction enqueued on stream s without a graph of its own (for
 // a caller that captures it into its graph): x = 0, the prepared right-hand
-// side rhs, max_cycles FP64 cycles without norms.
+// side rhs, max_cycles cycles without norms.  A mixed-precision handle runs
+// them in FP32 (right-hand side rounded from the FP64 one, as for an outer
+// step of its solves) and leaves the correction, widened, in the FP64 x.
 template <int DIM>
 mg_status enqueue_correction(mg_handle *h, cudaStream_t s, const double2 *rhs) {
     const LevelBuf &f = h->L[0];
     CK(cudaMemsetAsync(f.x, 0, sizeof(double2) * f.N, s));
     enqueue_prep<DIM>(h, rhs, s);
-    for (int q = 0; q < h->opt.max_cycles; q++) enqueue_vcycle<double, DIM>(h, s, 0, h->opt.cycle);
+    if (h->opt.precision == MG_MIXED) {
+        enqueue_residual_to32<DIM>(h, s, true);        // x = 0: b32 = b, bt32 = Dinv b, e32 = 0
+        for (int q = 0; q < h->opt.max_cycles; q++) enqueue_vcycle<float, DIM>(h, s, 0, h->opt.cycle);
+        k_add_correction<<<lin_blocks(f.N), 256, 0, s>>>(f.x, f.x32, f.N);
+        counted(h);
+    } else {
+        for (int q = 0; q < h->opt.max_cycles; q++) enqueue_vcycle<double, DIM>(h, s, 0, h->opt.cycle);
+    }
     CK(cudaGetLastError());
     return MG_OK;
 }

@@ -134,7 +134,8 @@ mg_status mg_composite_create(const mg_grid *grid, const int box[2][2], const mg
     mg_options o;
     if (opt) o = *opt;
     else mg_default_options(&o);
-    if (o.precision != MG_FP64) return fail(MG_ERR_INVALID_ARG, "refined-patch solves run in FP64");
+    if (o.precision != MG_FP64 && o.precision != MG_MIXED)
+        return fail(MG_ERR_INVALID_ARG, "precision must be MG_FP64 or MG_MIXED");
     if (o.nu1 < 0 || o.nu2 < 0 || o.nu1 > 16 || o.nu2 > 16 || o.nu1 + o.nu2 == 0)
         return fail(MG_ERR_INVALID_ARG, "nu1, nu2 must be in 0..16 and not both zero");
     mg_composite *m = new (std::nothrow) mg_composite();

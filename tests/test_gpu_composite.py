@@ -120,6 +120,31 @@ def test_composite_converges_to_the_dense_solution(torch_cuda):
     c.close()
 
 
+@pytest.mark.parametrize("name", ["stiff_bubbles_64", "stiff_dirichlet_corner", "literal_edge_box"])
+def test_composite_mixed_base_correction(torch_cuda, name):
+    """MG_MIXED: the base correction's V-cycle in FP32, the composite
+    residual, the patch sweeps and the update in FP64.  The defect
+    correction reaches the FP64 composite solve's fixed point: against the
+    FP64 solve run to its rounding floor, 1e-8 of the deviation, in at most a
+    few more steps."""
+    from paper_2206_11294_gb300.binding import Composite
+    b, p, box = CASES[name]
+    ref = _composite(b, p, box)
+    xb64, xf64, h64 = ref.solve(b.b, p.b, b.x0.copy(), p.x0.copy(), 40)
+    ref.close()
+    c = Composite(b.grid, box, precision="mixed")
+    c.set_coeffs(b.lam, b.fa, b.fk, p.lam, p.fa, p.fk)
+    xb, xf, h = c.solve(b.b, p.b, b.x0.copy(), p.x0.copy(), 40)
+    xb, xf = xb.cpu().numpy(), xf.cpu().numpy()
+    assert _rel(xf, xf64.cpu().numpy(), p.x0) <= 1e-8
+    assert _rel(xb, xb64.cpu().numpy(), b.x0) <= 1e-8
+    # the same contraction until the floors: within a factor 2 after 3 steps
+    for q in range(4):
+        if h64[3, q] > 1e-6 * h64[0, q]:
+            assert h[3, q] <= 2.0 * h64[3, q] + 1e-30
+    c.close()
+
+
 def test_composite_rejects_bad_arguments(torch_cuda):
     from paper_2206_11294_gb300.binding import Composite, MgError, MG_ERR_INVALID_ARG
     b, p, box = CASES["literal_bubbles_64"]
