@@ -364,10 +364,13 @@ def run_ours(args, rank, world):
 
 
 # ----------------------------------------------------------------- sub-results
-def time_arm(probs, precision, steps, warmup, dev, stream, flush, tune=True, tune_reps=5, max_cycles=50):
+def time_arm(probs, precision, steps, warmup, dev, stream, flush, tune=True, tune_reps=5, max_cycles=50,
+             sweep_roofline=False):
     """Set-up + solve to 1e-10 of every problem per step, inputs resident in
     HBM, L2 flushed between steps, device events around each step.  Returns
-    the figures and the final solutions."""
+    the figures and the final solutions.  sweep_roofline: also the finest-level
+    sweeps of problem 0 timed live (event hooks) against the measured HBM
+    bandwidth."""
     import numpy as np
     import torch
     from paper_2206_11294_gb300.binding import Solver
@@ -389,9 +392,13 @@ def time_arm(probs, precision, steps, warmup, dev, stream, flush, tune=True, tun
             s.set_coeffs(d["lam"], d["fa"], d["fk"])
             out.append(s.solve(d["b"], d["x"], allow_not_converged=True))
 
+    if sweep_roofline:
+        solvers[0].set_timing(True)
     for _ in range(warmup):
         step([])
     torch.cuda.synchronize()
+    if sweep_roofline:
+        solvers[0].set_timing(True)          # counters from the timed steps only
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     for k in range(steps):
         flush.zero_()
@@ -407,6 +414,20 @@ def time_arm(probs, precision, steps, warmup, dev, stream, flush, tune=True, tun
            "status": [st["status"] for st in first],
            "convergence_factor": [[(st["rfinal"][f] / st["r0"][f]) ** (1.0 / max(1, st["cycles"]))
                                    if st["r0"][f] > 0 else 0.0 for f in range(2)] for st in first]}
+    if sweep_roofline:
+        c0 = solvers[0].counters()
+        dim0 = probs[0].grid.dim
+        spl = c0["smooth_sweeps"] / max(1, c0["smooth_launches"])
+        per_launch = SWEEP_BYTES_PER_CELL[(precision, dim0)] * c0["smooth_cells"] * spl
+        avg_s = c0["smooth_ms"] / 1e3 / max(1, c0["smooth_launches"])
+        peak, peak_kind = measured_peak()
+        ach = per_launch / avg_s / 1e9 if avg_s > 0 else None
+        t0 = solvers[0].tuning()
+        out["sweep_roofline"] = {"bound": "hbm", "kernel": f"finest-level {t0['sweep'][0]} sweep of {probs[0].name}",
+                                 "achieved": ach, "peak": peak, "unit": "GB/s",
+                                 "frac": (ach / peak) if ach else None, "peak_source": peak_kind,
+                                 "algorithmic_bytes_per_launch": per_launch, "avg_launch_us": avg_s * 1e6,
+                                 "launches_timed": c0["smooth_launches"]}
     xs = [d["x"].cpu().numpy() for d in din]
     for s in solvers:
         s.close()
@@ -429,6 +450,7 @@ def sub_results(args, dev, stream, flush, fp64_result):
     t0 = time.perf_counter()
     probs = workload_problems()
     mixed, xm = time_arm(probs, "mixed", args.steps, args.warmup, dev, stream, flush, tune=not args.no_tune,
+                         sweep_roofline=True,
                          tune_reps=args.tune_reps)
     mixed["vs_fp64_rel_l2_of_deviation"] = max(rel_dev(a, b, p.x0) for a, b, p in zip(xm, fp64_result, probs))
     mixed["workload"] = "bubbles16_1024x1024 + axi_512x1024, mixed precision (FP32 cycles, FP64 residual and update)"
