@@ -596,15 +596,19 @@ def _large_coarse_cases():
         "2d_stiff_9x13": I.random_coeff_problem(I.Grid(dim=2, axisym=0, n=(144, 208, 1), h=1e-4,
                                                        bc=((D, W), (W, D), (0, 0)), bcT=((310, 0), (0, 290), (0, 0)),
                                                        bcp=((1.1e5, 0), (0, 0.9e5), (0, 0))), seed=96, dt=1e-5),
-        # coarsest 5 x 7 x 3 (210 unknowns, band 71)
+        # coarsest 5 x 7 x 3 (210 unknowns, band 71): too wide for the windowed LU
         "3d_5x7x3": I.random_coeff_problem(I.Grid(dim=3, axisym=0, n=(40, 56, 24), h=1e-4, bc=((W, D), (W, W), (D, W)),
                                                   bcT=((0, 300), (0, 0), (300, 0)), bcp=((0, 1e5), (0, 0), (1e5, 0))),
                                            seed=97, dt=1e-5),
+        # coarsest 6 x 6 x 6 (432 unknowns, band 73): the LU blocked over a cluster, 3D
+        "3d_6x6x6": I.random_coeff_problem(I.Grid(dim=3, axisym=0, n=(48, 48, 48), h=1e-4, bc=((D, W), (W, W), (W, D)),
+                                                  bcT=((300, 0), (0, 0), (0, 300)), bcp=((1e5, 0), (0, 0), (0, 1e5))),
+                                           seed=98, dt=1e-5),
     }
 
 
 @pytest.mark.parametrize("coarse", ["auto", "inverse"])
-@pytest.mark.parametrize("name", ["2d_736_bubbles", "2d_stiff_9x13", "3d_5x7x3"])
+@pytest.mark.parametrize("name", ["2d_736_bubbles", "2d_stiff_9x13", "3d_5x7x3", "3d_6x6x6"])
 def test_large_coarsest_levels_vs_oracle(torch_cuda, orc, name, coarse):
     """Coarsest levels above 128 unknowns take the windowed banded LU; each
     cycle then solves from the factors (auto) or multiplies by the
@@ -631,7 +635,7 @@ def test_large_coarsest_levels_vs_oracle(torch_cuda, orc, name, coarse):
     s.close()
 
 
-@pytest.mark.parametrize("name", ["2d_736_bubbles", "2d_stiff_9x13", "3d_5x7x3"])
+@pytest.mark.parametrize("name", ["2d_736_bubbles", "2d_stiff_9x13", "3d_5x7x3", "3d_6x6x6"])
 def test_factored_coarse_solve_equals_inverse(torch_cuda, name):
     """The two coarsest solves are exact up to rounding: the same cycle count
     and results within 1e-13 of the deviation, FP64 and mixed (1e-11 on the
@@ -644,7 +648,7 @@ def test_factored_coarse_solve_equals_inverse(torch_cuda, name):
     from paper_2206_11294_gb300.binding import MgError, MG_ERR_INVALID_ARG
     p = _large_coarse_cases()[name]
     tol = 1e-11 if "stiff" in name or "3d" in name else 1e-13
-    factored = "3d" not in name
+    factored = name != "3d_5x7x3"
     for prec, rtol in (("fp64", 1e-10), ("mixed", 1e-10)):
         a = _solver(p, precision=prec, rtol=rtol, max_cycles=80)
         b = _solver(p, precision=prec, rtol=rtol, max_cycles=80, coarse="inverse")
