@@ -16,7 +16,11 @@ on the GPU:
   of launches per V-cycle stage for all of them); a single request runs
   mg_solve on its hierarchy;
 - every request's result is the one a lone mg_solve would give: the batch
-  runs the same per-block device code and stops each problem on its own.
+  runs the same per-block device code and stops each problem on its own;
+- small groups (every problem at most `small_cells` cells) run on the slot's
+  high-priority stream, their inputs copied to the device by a kernel
+  (mg_copy_h2d_async): they wait neither in the copy engines' queue behind a
+  large request's transfer nor behind a large solve's waiting blocks.
 
 The GPU work goes through the C ABI (binding.Solver / binding.Batch); this
 module only schedules.  The engine is pluggable so the scheduling logic can
