@@ -10,6 +10,16 @@ FP64 solve (mg_solve: V(2,2) cycles, red-black block Gauss-Seidel, stop at
 Metric: Mcell * V-cycles per second (finest cells times cycles, summed over the
 step, per second of device time), plus solves per second.
 
+Schedule (--schedule): "concurrent" (default) gives each problem its own
+handle and stream and runs them at once, problem 0 through mg_solve (its
+cycle graphs carry the timing hooks of the dominant kernel) and the others
+through mg_solve_async; the problems are independent, so the kernels of one
+fill the SMs that the other's coarse levels and host waits leave idle, and
+every result is bit for bit that of a solve alone.  "serial" solves them one
+after the other on one stream.  In the concurrent step the timed sweep shares
+the SMs with the other problem's kernels, so the roofline also reports the
+same kernel timed in serial steps after the timed region ("isolated").
+
 Arms:
   default            the CUDA library through its C ABI (inputs resident in HBM);
                      `e2e` repeats the step through the library's host-buffer
@@ -173,6 +183,72 @@ def gpu_identity(torch, dev):
         return None
 
 
+def solve_concurrently(solvers, data, main, allow=False):
+    """One set-up + solve of every problem, each handle on its own stream,
+    forked from and joined back into `main`.  Problems 1.. are enqueued first
+    with mg_solve_async (the stop test runs on the device, the host does not
+    wait); problem 0 then runs mg_solve, whose per-cycle graphs carry the
+    timing hooks; then the others' statistics are collected.  The problems are
+    independent, so their kernels overlap on the device; every result is bit
+    for bit the one of a solve alone."""
+    import torch
+    fork = torch.cuda.Event()
+    fork.record(main)
+    for s in solvers:
+        s.stream.wait_event(fork)
+    for s, d in list(zip(solvers, data))[1:]:
+        s.set_coeffs(d["lam"], d["fa"], d["fk"])
+        s.solve_async(d["b"], d["x"])
+    s0, d0 = solvers[0], data[0]
+    s0.set_coeffs(d0["lam"], d0["fa"], d0["fk"])
+    out = [s0.solve(d0["b"], d0["x"], allow_not_converged=allow)]
+    out += [s.async_stats(allow_not_converged=allow) for s in solvers[1:]]
+    for s in solvers:
+        e = torch.cuda.Event()
+        e.record(s.stream)
+        main.wait_event(e)
+    return out
+
+
+def solve_serially(solvers, data, allow=False):
+    """The same step with the problems one after the other (mg_solve each)."""
+    return [(s.set_coeffs(d["lam"], d["fa"], d["fk"]), s.solve(d["b"], d["x"], allow_not_converged=allow))[1]
+            for s, d in zip(solvers, data)]
+
+
+def in_threads(fns):
+    """Runs the callables in one host thread each (the library's calls release
+    the interpreter lock) and returns their results in order."""
+    import threading
+    out, err = [None] * len(fns), []
+
+    def run(i):
+        try:
+            out[i] = fns[i]()
+        except BaseException as e:        # noqa: BLE001
+            err.append(e)
+    th = [threading.Thread(target=run, args=(i,)) for i in range(len(fns))]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    if err:
+        raise err[0]
+    return out
+
+
+def sweep_timing(solver, precision, dim):
+    """Launch count and average duration of the finest-level smoothing pass
+    timed by the handle's hooks, with its algorithmic bytes and FP64
+    instructions per launch."""
+    c = solver.counters()
+    spl = c["smooth_sweeps"] / max(1, c["smooth_launches"])
+    avg_s = c["smooth_ms"] / 1e3 / max(1, c["smooth_launches"])
+    return {"launches": c["smooth_launches"], "avg_s": avg_s,
+            "bytes": SWEEP_BYTES_PER_CELL[(precision, dim)] * c["smooth_cells"] * spl,
+            "fp64_inst": SWEEP_FP64_INST_PER_CELL[dim] * c["smooth_cells"] * spl}
+
+
 def face_bytes(p):
     return sum(8 * (a.size + b.size) for a, b in zip(p.fa, p.fk))
 
@@ -192,8 +268,9 @@ def run_ours(args, rank, world):
     dev_in = []
     solvers = []
     for p in probs:
-        s = Solver(p.grid, precision=args.precision, rtol=1e-10, max_cycles=50, device=dev, stream=stream,
-                   cycle=args.cycle)
+        # one stream per handle: independent problems overlap on the device
+        s = Solver(p.grid, precision=args.precision, rtol=1e-10, max_cycles=50, device=dev,
+                   stream=torch.cuda.Stream(dev), cycle=args.cycle)
         dev_in.append(dict(lam=T(p.lam), fa=[T(f) for f in p.fa], fk=[T(f) for f in p.fk], b=T(p.b),
                            x0=T(p.x0), x=T(p.x0)))
         solvers.append(s)
@@ -207,12 +284,24 @@ def run_ours(args, rank, world):
             s.set_coeffs(d["lam"], d["fa"], d["fk"])
             tunings[p.name] = describe(table.tune(s, reps=args.tune_reps))
         table.save()
+    torch.cuda.synchronize()
 
-    def step(collect):
-        for s, d in zip(solvers, dev_in):
-            s.set_coeffs(d["lam"], d["fa"], d["fk"])
-            st = s.solve(d["b"], d["x"])
-            collect.append(st)
+    def step(collect, schedule=args.schedule):
+        if schedule == "concurrent":
+            collect += solve_concurrently(solvers, dev_in, stream)
+        else:
+            collect += solve_serially(solvers, dev_in)
+
+    def timed_steps(n, collect, schedule=args.schedule):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+        for k in range(n):
+            flush.zero_()                           # L2 flushed between timed steps
+            for d in dev_in:
+                d["x"].copy_(d["x0"])
+            ev[k][0].record(stream)
+            step(collect, schedule)
+            ev[k][1].record(stream)
+        return ev
 
     # timing hooks of the dominant kernel: one finest-level smoothing pass per
     # cycle of problem 0 only (the hooks cost the step ~1%; every handle's
@@ -226,41 +315,40 @@ def run_ours(args, rank, world):
     solvers[0].set_timing(True)      # reset counters after warm-up
     for s in solvers[1:]:
         s.set_timing(False)          # (also resets their launch counters)
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     stats = []
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
     clocks = ClockSampler(gpu_identity(torch, dev)) if rank == 0 else None
     wall0 = time.perf_counter()
-    for k in range(args.steps):
-        flush.zero_()                           # L2 flushed between timed steps
-        for d in dev_in:
-            d["x"].copy_(d["x0"])
-        starts[k].record(stream)
-        step(stats)
-        ends[k].record(stream)
+    ev = timed_steps(args.steps, stats)
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
     if world > 1:
         dist.barrier()
     clk = clocks.stop() if clocks else None
-    step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+    step_ms = [a.elapsed_time(b) for a, b in ev]
     dev_ms = sum(step_ms)
     counters = [s.counters() for s in solvers]
+    live = sweep_timing(solvers[0], args.precision, probs[0].grid.dim)
     units = sum(p.grid.N * st["cycles"] for p, st in zip(probs * args.steps, stats)) / 1e6
     solves = len(stats)
     value, tmax = replica_value(units, dev_ms / 1e3, world, device=f"cuda:{dev}")
+    # the same kernel with the problems one after the other (steps after the
+    # timed region): in the concurrent step its launches share the SMs with
+    # the other problem's kernels, so their duration there is the share it got
+    isolated = None
+    if args.schedule == "concurrent":
+        for s in solvers[1:]:
+            s.set_timing(False)
+        solvers[0].set_timing(True)
+        timed_steps(max(3, args.steps // 2), [], "serial")
+        torch.cuda.synchronize()
+        isolated = sweep_timing(solvers[0], args.precision, probs[0].grid.dim)
     # roofline of the dominant kernel, from its live event timings
-    c0 = counters[0]
     peak, peak_kind = measured_peak()
     fpeak, fpeak_src = fp64_peak()
     dim0 = probs[0].grid.dim
-    sweeps_per_launch = c0["smooth_sweeps"] / max(1, c0["smooth_launches"])
-    per_launch = SWEEP_BYTES_PER_CELL[(args.precision, dim0)] * c0["smooth_cells"] * sweeps_per_launch
-    avg_s = c0["smooth_ms"] / 1e3 / max(1, c0["smooth_launches"])
-    achieved = per_launch / avg_s / 1e9 if avg_s > 0 else None
     t0 = solvers[0].tuning()
     rname = "double" if args.precision == "fp64" else "float"
     if t0["sweep"][0] == "fused":
@@ -272,21 +360,33 @@ def run_ours(args, rank, world):
     tr = TRAFFIC.get(kernel)
     traffic = args.traffic if args.traffic is not None else (tr["cold"] if tr else None)
     traffic_note = None if args.traffic is not None or not tr else dict(tr)
-    hbm = {"bound": "hbm", "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "GB/s",
-           "frac": (achieved / peak) if achieved else None, "peak_source": peak_kind,
-           "algorithmic_bytes_per_launch": per_launch, "avg_launch_us": avg_s * 1e6,
-           "launches_timed": c0["smooth_launches"], "traffic": traffic, "traffic_ncu": traffic_note}
-    if args.precision == "fp64":
-        inst = SWEEP_FP64_INST_PER_CELL[dim0] * c0["smooth_cells"] * sweeps_per_launch
-        ach_i = inst / avg_s / 1e9 if avg_s > 0 else None
-        roofline = {"bound": "alu", "kernel": kernel, "achieved": ach_i, "peak": fpeak,
-                    "unit": "G FP64 inst/s", "frac": (ach_i / fpeak) if ach_i else None,
-                    "peak_source": fpeak_src,
-                    "algorithmic_fp64_inst_per_launch": inst, "avg_launch_us": avg_s * 1e6,
-                    "launches_timed": c0["smooth_launches"], "traffic": traffic, "traffic_ncu": traffic_note,
-                    "hbm": hbm}
-    else:
-        roofline = hbm
+
+    def roofline_of(t):
+        avg_s = t["avg_s"]
+        achieved = t["bytes"] / avg_s / 1e9 if avg_s > 0 else None
+        hbm = {"bound": "hbm", "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "GB/s",
+               "frac": (achieved / peak) if achieved else None, "peak_source": peak_kind,
+               "algorithmic_bytes_per_launch": t["bytes"], "avg_launch_us": avg_s * 1e6,
+               "launches_timed": t["launches"], "traffic": traffic, "traffic_ncu": traffic_note}
+        if args.precision != "fp64":
+            return hbm
+        ach_i = t["fp64_inst"] / avg_s / 1e9 if avg_s > 0 else None
+        return {"bound": "alu", "kernel": kernel, "achieved": ach_i, "peak": fpeak,
+                "unit": "G FP64 inst/s", "frac": (ach_i / fpeak) if ach_i else None,
+                "peak_source": fpeak_src,
+                "algorithmic_fp64_inst_per_launch": t["fp64_inst"], "avg_launch_us": avg_s * 1e6,
+                "launches_timed": t["launches"], "traffic": traffic, "traffic_ncu": traffic_note,
+                "hbm": hbm}
+
+    roofline = roofline_of(live)
+    if isolated is not None:
+        roofline["timed_in"] = "the concurrent step (the other problem's kernels share the SMs)"
+        iso = roofline_of(isolated)
+        iso["timed_in"] = "serial steps after the timed region (the problems one after the other)"
+        roofline["isolated"] = {k: iso[k] for k in ("achieved", "frac", "avg_launch_us", "launches_timed",
+                                                    "timed_in")}
+        if "hbm" in iso:
+            roofline["isolated"]["hbm_frac"] = iso["hbm"]["frac"]
     cycles = [st["cycles"] for st in stats[: len(probs)]]
 
     # end to end through the library's host-buffer path: mg_set_coeffs and
@@ -308,13 +408,17 @@ def run_ours(args, rank, world):
             s.set_coeffs(hd["lam"], hd["fa"], hd["fk"])
             s.solve(hd["b"], pin(p.x0))
         torch.cuda.synchronize()
+        def one(s, hd, xh):
+            s.set_coeffs(hd["lam"], hd["fa"], hd["fk"])
+            return s.solve(hd["b"], xh)
+
         e_units = 0.0
         w0 = time.perf_counter()
         for k in range(args.steps):
-            for p, s, hd, xh in zip(probs, solvers, host, xs[k]):
-                s.set_coeffs(hd["lam"], hd["fa"], hd["fk"])
-                st = s.solve(hd["b"], xh)
-                e_units += p.grid.N * st["cycles"] / 1e6
+            work = [lambda s=s, hd=hd, xh=xh: one(s, hd, xh) for s, hd, xh in zip(solvers, host, xs[k])]
+            # concurrent: one host thread per handle, each on its own stream
+            sts = in_threads(work) if args.schedule == "concurrent" else [w() for w in work]
+            e_units += sum(p.grid.N * st["cycles"] for p, st in zip(probs, sts)) / 1e6
         torch.cuda.synchronize()
         e_wall = time.perf_counter() - w0
         tt = torch.tensor([e_wall], dtype=torch.float64, device=f"cuda:{dev}")
@@ -326,6 +430,8 @@ def run_ours(args, rank, world):
                "d2h_bytes_per_step": d2h, "seconds": float(tt.item()),
                "copies": "through the C ABI with on_device = 0: pinned host lambda, faces, rhs and x in, x out, "
                          "inside mg_set_coeffs / mg_solve (synchronous calls, no overlap between steps)",
+               "schedule": ("one host thread per problem, each handle on its own stream"
+                            if args.schedule == "concurrent" else "the problems one after the other"),
                "check": bool(all(np.array_equal(xs[-1][q].numpy(), dev_in[q]["x"].cpu().numpy())
                                  for q in range(len(probs))))}
 
@@ -351,6 +457,9 @@ def run_ours(args, rank, world):
                    "cycle": f"{args.cycle}(2,2) red-black block GS, exact coarsest solve",
                    "l2": "flushed between steps",
                    "parallelism": f"replicas x{world}",
+                   "schedule": ("concurrent: each problem on its own handle and stream, problem 0 by mg_solve, "
+                                "the others by mg_solve_async" if args.schedule == "concurrent"
+                                else "serial: mg_solve of each problem in turn, one stream"),
                    "tuning": tunings or "library defaults (--no-tune)"},
         "roofline": roofline,
         "cpu_baseline": cpu,
@@ -365,32 +474,47 @@ def run_ours(args, rank, world):
 
 # ----------------------------------------------------------------- sub-results
 def time_arm(probs, precision, steps, warmup, dev, stream, flush, tune=True, tune_reps=5, max_cycles=50,
-             sweep_roofline=False):
+             sweep_roofline=False, schedule="concurrent"):
     """Set-up + solve to 1e-10 of every problem per step, inputs resident in
-    HBM, L2 flushed between steps, device events around each step.  Returns
-    the figures and the final solutions.  sweep_roofline: also the finest-level
-    sweeps of problem 0 timed live (event hooks) against the measured HBM
-    bandwidth."""
+    HBM, L2 flushed between steps, device events around each step, the
+    problems scheduled as the headline's (`schedule`).  Returns the figures
+    and the final solutions.  sweep_roofline: also the finest-level sweeps of
+    problem 0 timed live (event hooks) against the measured HBM bandwidth, in
+    the step and (concurrent schedule) in serial steps after it."""
     import numpy as np
     import torch
     from paper_2206_11294_gb300.binding import Solver
     T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda(dev)
     solvers, din = [], []
     for p in probs:
-        s = Solver(p.grid, precision=precision, rtol=1e-10, max_cycles=max_cycles, device=dev, stream=stream)
+        s = Solver(p.grid, precision=precision, rtol=1e-10, max_cycles=max_cycles, device=dev,
+                   stream=torch.cuda.Stream(dev))
         d = dict(lam=T(p.lam), fa=[T(f) for f in p.fa], fk=[T(f) for f in p.fk], b=T(p.b), x0=T(p.x0), x=T(p.x0))
         s.set_coeffs(d["lam"], d["fa"], d["fk"])
         if tune:
             s.autotune(tune_reps)
         solvers.append(s)
         din.append(d)
+    torch.cuda.synchronize()
     stats = []
 
-    def step(out):
-        for s, d in zip(solvers, din):
+    def step(out, how=schedule):
+        for d in din:
             d["x"].copy_(d["x0"])
-            s.set_coeffs(d["lam"], d["fa"], d["fk"])
-            out.append(s.solve(d["b"], d["x"], allow_not_converged=True))
+        if how == "concurrent":
+            out += solve_concurrently(solvers, din, stream, allow=True)
+        else:
+            out += solve_serially(solvers, din, allow=True)
+
+    def timed(n, out, how=schedule):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+        for k in range(n):
+            flush.zero_()
+            ev[k][0].record(stream)
+            step(out, how)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        return ev
 
     if sweep_roofline:
         solvers[0].set_timing(True)
@@ -399,35 +523,41 @@ def time_arm(probs, precision, steps, warmup, dev, stream, flush, tune=True, tun
     torch.cuda.synchronize()
     if sweep_roofline:
         solvers[0].set_timing(True)          # counters from the timed steps only
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-    for k in range(steps):
-        flush.zero_()
-        ev[k][0].record(stream)
-        step(stats)
-        ev[k][1].record(stream)
-    torch.cuda.synchronize()
+    ev = timed(steps, stats)
     secs = sum(a.elapsed_time(b) for a, b in ev) / 1e3
     units = sum(p.grid.N * st["cycles"] for p, st in zip(probs * steps, stats)) / 1e6
     first = stats[: len(probs)]
     out = {"mcell_vcycles_per_s": units / secs, "solves_per_s": len(stats) / secs, "ms_per_step": secs * 1e3 / steps,
            "cycles_per_solve": [st["cycles"] for st in first], "outer_steps": [st["outer"] for st in first],
-           "status": [st["status"] for st in first],
+           "status": [st["status"] for st in first], "schedule": schedule,
            "convergence_factor": [[(st["rfinal"][f] / st["r0"][f]) ** (1.0 / max(1, st["cycles"]))
                                    if st["r0"][f] > 0 else 0.0 for f in range(2)] for st in first]}
     if sweep_roofline:
-        c0 = solvers[0].counters()
         dim0 = probs[0].grid.dim
-        spl = c0["smooth_sweeps"] / max(1, c0["smooth_launches"])
-        per_launch = SWEEP_BYTES_PER_CELL[(precision, dim0)] * c0["smooth_cells"] * spl
-        avg_s = c0["smooth_ms"] / 1e3 / max(1, c0["smooth_launches"])
         peak, peak_kind = measured_peak()
-        ach = per_launch / avg_s / 1e9 if avg_s > 0 else None
         t0 = solvers[0].tuning()
+
+        def hbm_of(t):
+            ach = t["bytes"] / t["avg_s"] / 1e9 if t["avg_s"] > 0 else None
+            return ach, (ach / peak) if ach else None
+
+        live = sweep_timing(solvers[0], precision, dim0)
+        ach, frac = hbm_of(live)
         out["sweep_roofline"] = {"bound": "hbm", "kernel": f"finest-level {t0['sweep'][0]} sweep of {probs[0].name}",
                                  "achieved": ach, "peak": peak, "unit": "GB/s",
-                                 "frac": (ach / peak) if ach else None, "peak_source": peak_kind,
-                                 "algorithmic_bytes_per_launch": per_launch, "avg_launch_us": avg_s * 1e6,
-                                 "launches_timed": c0["smooth_launches"]}
+                                 "frac": frac, "peak_source": peak_kind,
+                                 "algorithmic_bytes_per_launch": live["bytes"], "avg_launch_us": live["avg_s"] * 1e6,
+                                 "launches_timed": live["launches"]}
+        if schedule == "concurrent":
+            solvers[0].set_timing(True)
+            timed(max(3, steps // 2), [], "serial")
+            iso = sweep_timing(solvers[0], precision, dim0)
+            ach_i, frac_i = hbm_of(iso)
+            out["sweep_roofline"]["timed_in"] = "the concurrent step"
+            out["sweep_roofline"]["isolated"] = {"achieved": ach_i, "frac": frac_i,
+                                                 "avg_launch_us": iso["avg_s"] * 1e6,
+                                                 "launches_timed": iso["launches"],
+                                                 "timed_in": "serial steps after the timed region"}
     xs = [d["x"].cpu().numpy() for d in din]
     for s in solvers:
         s.close()
@@ -450,8 +580,7 @@ def sub_results(args, dev, stream, flush, fp64_result):
     t0 = time.perf_counter()
     probs = workload_problems()
     mixed, xm = time_arm(probs, "mixed", args.steps, args.warmup, dev, stream, flush, tune=not args.no_tune,
-                         sweep_roofline=True,
-                         tune_reps=args.tune_reps)
+                         sweep_roofline=True, tune_reps=args.tune_reps, schedule=args.schedule)
     mixed["vs_fp64_rel_l2_of_deviation"] = max(rel_dev(a, b, p.x0) for a, b, p in zip(xm, fp64_result, probs))
     mixed["workload"] = "bubbles16_1024x1024 + axi_512x1024, mixed precision (FP32 cycles, FP64 residual and update)"
     out["mixed"] = mixed
@@ -461,7 +590,7 @@ def sub_results(args, dev, stream, flush, fp64_result):
     sp = [I.stiff(I.bubbles_1024), I.stiff(I.bubble_axi)]
     for prec in ("fp64", "mixed"):
         stiff[prec], _ = time_arm(sp, prec, max(2, args.steps // 4), 1, dev, stream, flush, tune=not args.no_tune,
-                                  tune_reps=args.tune_reps, max_cycles=200)
+                                  tune_reps=args.tune_reps, max_cycles=200, schedule=args.schedule)
     out["stiff"] = stiff
     if not args.no_batch:
         bargs = argparse.Namespace(**vars(args))
@@ -1084,6 +1213,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--schedule", default="concurrent", choices=["concurrent", "serial"],
+                    help="the step's problems on their own streams at once, or one after the other")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-sub", action="store_true", help="headline only: no mixed / stiff / batch / serve sub-results")
