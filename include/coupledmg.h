@@ -244,10 +244,14 @@ MG_API mg_status mg_counters(const mg_handle *h, long long *launches, double *sm
  *   persistent  colour sweeps, restriction and prolongation launch one block
  *               per tile (0) or one persistent wave of blocks (SMs x resident
  *               blocks) that walk the tiles (1).
+ *   overlap     the kernels of a cycle and of the set-up launch as
+ *               programmatic dependents of the kernel before them (1): each
+ *               is set up while that kernel drains and waits for it on the
+ *               device before it touches memory; 0: plain stream order.
  * Defaults after mg_create: colour sweeps for FP64 cycles, fused 64 x 16 for
  * the FP32 cycles of mixed precision on 2D grids; the tail from the first
- * level below the finest with at most 4096 cells, 8 CTAs.  mg_autotune also
- * tries one block. */
+ * level below the finest with at most 4096 cells, 8 CTAs; overlap 1.
+ * mg_autotune also tries one block, and keeps the handle's overlap. */
 #define MG_MAX_LEVELS 32
 enum { MG_SWEEP_COLOUR = 1, MG_SWEEP_FUSED = 2, MG_SWEEP_ASYNC = 3, MG_SWEEP_COLOUR2 = 4 };
 typedef struct {
@@ -257,6 +261,7 @@ typedef struct {
     int tail_level;
     int tail_ctas;
     int persistent;
+    int overlap;
 } mg_tuning;
 
 MG_API mg_status mg_get_tuning(const mg_handle *h, mg_tuning *out);

@@ -79,13 +79,13 @@ class MgStats(C.Structure):
 
 class MgTuning(C.Structure):
     _fields_ = [("levels", C.c_int), ("sweep", C.c_int * MG_MAX_LEVELS), ("tile", C.c_int * MG_MAX_LEVELS),
-                ("tail_level", C.c_int), ("tail_ctas", C.c_int), ("persistent", C.c_int)]
+                ("tail_level", C.c_int), ("tail_ctas", C.c_int), ("persistent", C.c_int), ("overlap", C.c_int)]
 
     def as_dict(self) -> dict:
         n = self.levels
         return dict(levels=n, sweep=[_SWEEP_NAMES.get(int(self.sweep[l]), "colour") for l in range(n)],
                     tile=[int(self.tile[l]) for l in range(n)], tail_level=int(self.tail_level),
-                    tail_ctas=int(self.tail_ctas), persistent=int(self.persistent))
+                    tail_ctas=int(self.tail_ctas), persistent=int(self.persistent), overlap=int(self.overlap))
 
     @staticmethod
     def from_dict(d: dict) -> "MgTuning":
@@ -98,6 +98,7 @@ class MgTuning(C.Structure):
         t.tail_level = int(d["tail_level"])
         t.tail_ctas = int(d["tail_ctas"])
         t.persistent = int(d.get("persistent", 0))
+        t.overlap = int(d.get("overlap", 1))      # the library's default where an entry predates the field
         return t
 
 

@@ -125,6 +125,7 @@ __global__ void __launch_bounds__(256, 1)
                        const __grid_constant__ CUtensorMap mg1, const __grid_constant__ CUtensorMap mbt,
                        const __grid_constant__ CUtensorMap mw, const __grid_constant__ Level<R> L,
                        typename Vec<R>::v2 *__restrict__ xout, int *__restrict__ err) {
+    pdl_entry();
     using T = TmaTile<R, TX, TY>;
     using V2 = typename Vec<R>::v2;
     using Q4 = typename Vec<R>::q4;

@@ -16,6 +16,7 @@
 #include <map>
 #include <mutex>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "coupledmg.h"
@@ -134,6 +135,7 @@ struct mg_handle {
     int sweep[kMaxLevels]; // per level: MG_SWEEP_COLOUR or MG_SWEEP_FUSED
     int tile[kMaxLevels];  // per level: fused tile shape (index into kTileX / kTileY)
     int persistent;        // colour sweeps, restriction, prolongation: one persistent wave (1) or a block per tile (0)
+    int overlap;           // cycle and set-up kernels as programmatic dependent launches (1) or in plain order (0)
     TmaLevel *tmaps;       // tensor maps per (level, precision, tile), built on first use (host memory)
     unsigned char *tmap_ok;
     double *Minv, *Mtmp;   // coarse inverse (NULL when the cycles solve from the factors); assembled matrix
@@ -312,6 +314,7 @@ void plan(mg_handle *h, char *base, size_t *bytes) {
         h->tail_lev = h->nlev;
     h->tail_ctas = kTailCtas;
     h->persistent = 0;
+    h->overlap = 1;
     // Default kernel choices until mg_autotune / mg_set_tuning: FP32 cycles
     // (mixed precision) sweep fused in 2D; FP64 sweeps are bound by GB300's
     // FP64 pipe, where the fused kernel's recomputed ring costs more than the
@@ -431,16 +434,48 @@ unsigned lin_blocks(long long n) {
 // ---------------------------------------------------------------- V-cycle
 inline void counted(const mg_handle *h, long long n = 1) { const_cast<mg_handle *>(h)->enq += n; }
 
+// Launches one kernel of a cycle or a set-up in stream s.  With the handle's
+// overlap on, as a programmatic dependent of the kernel before it (each of
+// these kernels starts with pdl_entry): it is set up while that kernel
+// drains.  `cluster` > 0: thread-block clusters of that size.
+template <typename... KArgs, typename... Args>
+void launch_k(const mg_handle *h, void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+              int cluster, Args &&...args) {
+    cudaLaunchConfig_t cfg;
+    std::memset(&cfg, 0, sizeof(cfg));
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[2];
+    int na = 0;
+    if (cluster > 0) {
+        attr[na].id = cudaLaunchAttributeClusterDimension;
+        attr[na].val.clusterDim.x = (unsigned)cluster;
+        attr[na].val.clusterDim.y = 1;
+        attr[na].val.clusterDim.z = 1;
+        na++;
+    }
+    if (h->overlap) {
+        attr[na].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[na].val.programmaticStreamSerializationAllowed = 1;
+        na++;
+    }
+    cfg.attrs = attr;
+    cfg.numAttrs = (unsigned)na;
+    cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
+
 template <typename R> typename Vec<R>::v2 *xalt_of(const LevelBuf &l);
 template <> double2 *xalt_of<double>(const LevelBuf &l) { return l.xalt; }
 template <> float2 *xalt_of<float>(const LevelBuf &l) { return l.xalt32; }
 
 template <typename R, int TX, int TY>
-void launch_fused(const LevelBuf &lb, const Level<R> &v, cudaStream_t s) {
+void launch_fused(const mg_handle *h, const LevelBuf &lb, const Level<R> &v, cudaStream_t s) {
     const dim3 gf((unsigned)((lb.n[0] + TX - 1) / TX), (unsigned)((lb.n[1] + TY - 1) / TY), 1);
     typename Vec<R>::v2 *xa = xalt_of<R>(lb);
-    k_rbgs_fused2d<R, TX, TY><<<gf, kBlock, 0, s>>>(v, v.x, xa);
-    k_rbgs_fused2d<R, TX, TY><<<gf, kBlock, 0, s>>>(v, xa, v.x);
+    launch_k(h, k_rbgs_fused2d<R, TX, TY>, gf, kBlock, 0, s, 0, v, v.x, xa);
+    launch_k(h, k_rbgs_fused2d<R, TX, TY>, gf, kBlock, 0, s, 0, v, xa, v.x);
 }
 
 // ---------------------------------------------------------------- TMA sweeps
@@ -556,8 +591,8 @@ void launch_fused_tma(const mg_handle *h, int l, int tile, const Level<R> &v, cu
     const long long tiles = (long long)((lb.n[0] + TX - 1) / TX) * ((lb.n[1] + TY - 1) / TY);
     const unsigned grid = wave(fn, tiles, smem);
     typename Vec<R>::v2 *xa = xalt_of<R>(lb);
-    k_rbgs_fused2d_tma<R, TX, TY><<<grid, kBlock, smem, s>>>(m->x[0], m->g0, m->g1, m->bt, m->w, v, xa, h->err_d + 1);
-    k_rbgs_fused2d_tma<R, TX, TY><<<grid, kBlock, smem, s>>>(m->x[1], m->g0, m->g1, m->bt, m->w, v, v.x, h->err_d + 1);
+    launch_k(h, k_rbgs_fused2d_tma<R, TX, TY>, grid, kBlock, smem, s, 0, m->x[0], m->g0, m->g1, m->bt, m->w, v, xa, h->err_d + 1);
+    launch_k(h, k_rbgs_fused2d_tma<R, TX, TY>, grid, kBlock, smem, s, 0, m->x[1], m->g0, m->g1, m->bt, m->w, v, v.x, h->err_d + 1);
 }
 
 // `sweeps` red-black sweeps on level l with the given kernel choice.  Fused
@@ -571,9 +606,9 @@ void enqueue_sweeps(const mg_handle *h, cudaStream_t s, int l, int sweeps, int k
     int q = 0;
     if (DIM == 2 && kind == MG_SWEEP_FUSED) {
         for (; q + 1 < sweeps; q += 2) {
-            if (tile == 1) launch_fused<R, kTileX[1], kTileY[1]>(lb, v, s);
-            else if (tile == 2) launch_fused<R, kTileX[2], kTileY[2]>(lb, v, s);
-            else launch_fused<R, kTileX[0], kTileY[0]>(lb, v, s);
+            if (tile == 1) launch_fused<R, kTileX[1], kTileY[1]>(h, lb, v, s);
+            else if (tile == 2) launch_fused<R, kTileX[2], kTileY[2]>(h, lb, v, s);
+            else launch_fused<R, kTileX[0], kTileY[0]>(h, lb, v, s);
             counted(h, 2);
         }
     }
@@ -589,19 +624,19 @@ void enqueue_sweeps(const mg_handle *h, cudaStream_t s, int l, int sweeps, int k
     if (kind == MG_SWEEP_COLOUR2) {
         const dim3 g2(gr.x, (unsigned)((lb.n[1] + 2 * kBY - 1) / (2 * kBY)), gr.z);
         for (; q < sweeps; q++) {
-            k_rbgs_colour2<R, DIM><<<g2, kBlock, 0, s>>>(v, 0);
-            k_rbgs_colour2<R, DIM><<<g2, kBlock, 0, s>>>(v, 1);
+            launch_k(h, k_rbgs_colour2<R, DIM>, g2, kBlock, 0, s, 0, v, 0);
+            launch_k(h, k_rbgs_colour2<R, DIM>, g2, kBlock, 0, s, 0, v, 1);
             counted(h, 2);
         }
     }
     for (; q < sweeps; q++) {
         if (h->persistent) {
             const unsigned gw = wave((const void *)k_rbgs_colour<R, DIM, true>, tiles_of(gr));
-            k_rbgs_colour<R, DIM, true><<<gw, kBlock, 0, s>>>(v, 0);
-            k_rbgs_colour<R, DIM, true><<<gw, kBlock, 0, s>>>(v, 1);
+            launch_k(h, k_rbgs_colour<R, DIM, true>, gw, kBlock, 0, s, 0, v, 0);
+            launch_k(h, k_rbgs_colour<R, DIM, true>, gw, kBlock, 0, s, 0, v, 1);
         } else {
-            k_rbgs_colour<R, DIM, false><<<gr, kBlock, 0, s>>>(v, 0);
-            k_rbgs_colour<R, DIM, false><<<gr, kBlock, 0, s>>>(v, 1);
+            launch_k(h, k_rbgs_colour<R, DIM, false>, gr, kBlock, 0, s, 0, v, 0);
+            launch_k(h, k_rbgs_colour<R, DIM, false>, gr, kBlock, 0, s, 0, v, 1);
         }
         counted(h, 2);
     }
@@ -619,9 +654,9 @@ void enqueue_wjac(const mg_handle *h, cudaStream_t s, int l, int sweeps) {
     const dim3 gr = cell_grid(lb, DIM, lb.n[0]);
     for (int q = 0; q < sweeps; q++) {
         if (h->persistent)
-            k_wjac<R, DIM, true><<<wave((const void *)k_wjac<R, DIM, true>, tiles_of(gr)), kBlock, 0, s>>>(v, a, b, omega);
+            launch_k(h, k_wjac<R, DIM, true>, wave((const void *)k_wjac<R, DIM, true>, tiles_of(gr)), kBlock, 0, s, 0, v, a, b, omega);
         else
-            k_wjac<R, DIM, false><<<gr, kBlock, 0, s>>>(v, a, b, omega);
+            launch_k(h, k_wjac<R, DIM, false>, gr, kBlock, 0, s, 0, v, a, b, omega);
         counted(h);
         std::swap(a, b);
     }
@@ -676,24 +711,11 @@ void enqueue_tail(const mg_handle *h, cudaStream_t s) {
     TailArgs<R> A = tail_args<R>(h, h->tail_lev, h->tail_ctas, &smem);
     if (h->tail_ctas == 1) {                  // one CTA, no cluster
         raise_smem_limit((const void *)k_vcycle_tail<R, DIM, false>, (int)kTailSmemMax);
-        k_vcycle_tail<R, DIM, false><<<1, kBlock, smem, s>>>(A);
+        launch_k(h, k_vcycle_tail<R, DIM, false>, 1, kBlock, smem, s, 0, A);
         return;
     }
     raise_smem_limit((const void *)k_vcycle_tail<R, DIM, true>, (int)kTailSmemMax);
-    cudaLaunchConfig_t cfg;
-    std::memset(&cfg, 0, sizeof(cfg));
-    cfg.gridDim = dim3((unsigned)h->tail_ctas, 1, 1);
-    cfg.blockDim = kBlock;
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = (unsigned)h->tail_ctas;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    cudaLaunchKernelEx(&cfg, k_vcycle_tail<R, DIM, true>, A);
+    launch_k(h, k_vcycle_tail<R, DIM, true>, dim3((unsigned)h->tail_ctas, 1, 1), kBlock, smem, s, h->tail_ctas, A);
 }
 
 template <typename R, int DIM>
@@ -721,7 +743,7 @@ void enqueue_vcycle(const mg_handle *h, cudaStream_t s, int l, int type) {
         if (h->coarse_factors) {
             const long long sm = coarse_lu_smem(h->nc, h->coarse_kl, h->coarse_kl);
             raise_smem_limit((const void *)k_coarse_lu<R>, (int)sm);
-            k_coarse_lu<R><<<1, kLuSolveThreads, (size_t)sm, s>>>(h->Mwork, h->Mwork + (long long)h->nc * h->coarse_kl, h->piv,
+            launch_k(h, k_coarse_lu<R>, 1, kLuSolveThreads, (size_t)sm, s, 0, h->Mwork, h->Mwork + (long long)h->nc * h->coarse_kl, h->piv,
                                                      h->dinv, h->nc, h->coarse_kl, h->coarse_kl,
                                                      reinterpret_cast<const R *>(v.b), reinterpret_cast<R *>(v.x),
                                                      h->err_d);
@@ -730,7 +752,7 @@ void enqueue_vcycle(const mg_handle *h, cudaStream_t s, int l, int type) {
         }
         const int threads = 256;
         const unsigned blocks = (unsigned)((h->nc * 32LL + threads - 1) / threads);
-        k_coarse_matvec<R><<<blocks, threads, 0, s>>>(coarse_inverse<R>(h), reinterpret_cast<const R *>(v.b),
+        launch_k(h, k_coarse_matvec<R>, blocks, threads, 0, s, 0, coarse_inverse<R>(h), reinterpret_cast<const R *>(v.b),
                                                       reinterpret_cast<R *>(v.x), h->nc);
         counted(h);
         return;
@@ -747,18 +769,16 @@ void enqueue_vcycle(const mg_handle *h, cudaStream_t s, int l, int type) {
     const dim3 rg = cell_grid(cb, DIM, cb.n[0]);
     if (h->opt.nu1 > 0 && red_only_after_sweeps(h)) {
         if (h->persistent)
-            k_residual_restrict<R, DIM, true, true>
-                <<<wave((const void *)k_residual_restrict<R, DIM, true, true>, tiles_of(rg)), kBlock, 0, s>>>(view<R>(lb),
+            launch_k(h, k_residual_restrict<R, DIM, true, true>, wave((const void *)k_residual_restrict<R, DIM, true, true>, tiles_of(rg)), kBlock, 0, s, 0, view<R>(lb),
                                                                                                           view<R>(cb));
         else
-            k_residual_restrict<R, DIM, true, false><<<rg, kBlock, 0, s>>>(view<R>(lb), view<R>(cb));
+            launch_k(h, k_residual_restrict<R, DIM, true, false>, rg, kBlock, 0, s, 0, view<R>(lb), view<R>(cb));
     } else {
         if (h->persistent)
-            k_residual_restrict<R, DIM, false, true>
-                <<<wave((const void *)k_residual_restrict<R, DIM, false, true>, tiles_of(rg)), kBlock, 0, s>>>(
+            launch_k(h, k_residual_restrict<R, DIM, false, true>, wave((const void *)k_residual_restrict<R, DIM, false, true>, tiles_of(rg)), kBlock, 0, s, 0, 
                     view<R>(lb), view<R>(cb));
         else
-            k_residual_restrict<R, DIM, false, false><<<rg, kBlock, 0, s>>>(view<R>(lb), view<R>(cb));
+            launch_k(h, k_residual_restrict<R, DIM, false, false>, rg, kBlock, 0, s, 0, view<R>(lb), view<R>(cb));
     }
     counted(h);
     enqueue_vcycle<R, DIM>(h, s, l + 1, type);
@@ -766,10 +786,10 @@ void enqueue_vcycle(const mg_handle *h, cudaStream_t s, int l, int type) {
         enqueue_vcycle<R, DIM>(h, s, l + 1, type == MG_CYCLE_W ? MG_CYCLE_W : MG_CYCLE_V);
     const dim3 pg = cell_grid(lb, DIM, lb.n[0]);
     if (h->persistent)
-        k_prolong_add<R, DIM, true><<<wave((const void *)k_prolong_add<R, DIM, true>, tiles_of(pg)), kBlock, 0, s>>>(
+        launch_k(h, k_prolong_add<R, DIM, true>, wave((const void *)k_prolong_add<R, DIM, true>, tiles_of(pg)), kBlock, 0, s, 0, 
             view<R>(cb), view<R>(lb), bc_flags(h->grid));
     else
-        k_prolong_add<R, DIM, false><<<pg, kBlock, 0, s>>>(view<R>(cb), view<R>(lb), bc_flags(h->grid));
+        launch_k(h, k_prolong_add<R, DIM, false>, pg, kBlock, 0, s, 0, view<R>(cb), view<R>(lb), bc_flags(h->grid));
     counted(h);
     if (tm_post) cudaEventRecordWithFlags(h->ev[0], s, cudaEventRecordExternal);
     enqueue_smooth<R, DIM>(h, s, l, h->opt.nu2);
@@ -783,16 +803,14 @@ void enqueue_norm(const mg_handle *h, cudaStream_t s, bool after_sweep) {
     const dim3 ng = norm_grid(f, DIM);
     if (after_sweep) {
         if (h->persistent)
-            k_norm_partials<DIM, true, true><<<wave((const void *)k_norm_partials<DIM, true, true>, tiles_of(ng)), kBlock,
-                                               0, s>>>(view<double>(f), h->partial, h->ticket, h->norms_d);
+            launch_k(h, k_norm_partials<DIM, true, true>, wave((const void *)k_norm_partials<DIM, true, true>, tiles_of(ng)), kBlock, 0, s, 0, view<double>(f), h->partial, h->ticket, h->norms_d);
         else
-            k_norm_partials<DIM, true, false><<<ng, kBlock, 0, s>>>(view<double>(f), h->partial, h->ticket, h->norms_d);
+            launch_k(h, k_norm_partials<DIM, true, false>, ng, kBlock, 0, s, 0, view<double>(f), h->partial, h->ticket, h->norms_d);
     } else {
         if (h->persistent)
-            k_norm_partials<DIM, false, true><<<wave((const void *)k_norm_partials<DIM, false, true>, tiles_of(ng)),
-                                                kBlock, 0, s>>>(view<double>(f), h->partial, h->ticket, h->norms_d);
+            launch_k(h, k_norm_partials<DIM, false, true>, wave((const void *)k_norm_partials<DIM, false, true>, tiles_of(ng)), kBlock, 0, s, 0, view<double>(f), h->partial, h->ticket, h->norms_d);
         else
-            k_norm_partials<DIM, false, false><<<ng, kBlock, 0, s>>>(view<double>(f), h->partial, h->ticket, h->norms_d);
+            launch_k(h, k_norm_partials<DIM, false, false>, ng, kBlock, 0, s, 0, view<double>(f), h->partial, h->ticket, h->norms_d);
     }
     counted(h);
 }
@@ -818,10 +836,10 @@ void enqueue_residual_to32(const mg_handle *h, cudaStream_t s, bool initial = fa
     double2 *r_out = initial ? f.b : nullptr;
     double2 *r_out2 = initial ? delta : nullptr;
     if (h->persistent)
-        k_residual64_to32<DIM, true><<<wave((const void *)k_residual64_to32<DIM, true>, tiles_of(ng)), kBlock, 0, s>>>(
+        launch_k(h, k_residual64_to32<DIM, true>, wave((const void *)k_residual64_to32<DIM, true>, tiles_of(ng)), kBlock, 0, s, 0, 
             v, f.b32, f.bt32, f.x32, r_out, r_out2, h->partial, h->ticket, h->norms_d);
     else
-        k_residual64_to32<DIM, false><<<ng, kBlock, 0, s>>>(v, f.b32, f.bt32, f.x32, r_out, r_out2, h->partial,
+        launch_k(h, k_residual64_to32<DIM, false>, ng, kBlock, 0, s, 0, v, f.b32, f.bt32, f.x32, r_out, r_out2, h->partial,
                                                              h->ticket, h->norms_d);
     counted(h);
 }
@@ -857,7 +875,7 @@ template <int DIM>
 void enqueue_step32(const mg_handle *h, cudaStream_t s) {
     for (int q = 0; q < h->opt.inner_cycles; q++) enqueue_vcycle<float, DIM>(h, s, 0, h->opt.cycle);
     const LevelBuf &f = h->L[0];
-    k_add_correction<<<lin_blocks(f.N), 256, 0, s>>>(mixed_delta(h), f.x32, f.N);
+    launch_k(h, k_add_correction, lin_blocks(f.N), 256, 0, s, 0, mixed_delta(h), f.x32, f.N);
     counted(h);
     enqueue_residual_to32<DIM>(h, s);
     cudaMemcpyAsync(h->norms_h, h->norms_d, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
@@ -931,7 +949,7 @@ mg_status x_out(mg_handle *h, double *x, int on_device) {
 template <int DIM>
 void enqueue_prep(mg_handle *h, const double2 *rhs, cudaStream_t s) {
     const LevelBuf &f = h->L[0];
-    k_prep_rhs<DIM><<<cell_grid(f, DIM, f.n[0]), kBlock, 0, s>>>(view<double>(f), rhs, bc_vals(h->grid),
+    launch_k(h, k_prep_rhs<DIM>, cell_grid(f, DIM, f.n[0]), kBlock, 0, s, 0, view<double>(f), rhs, bc_vals(h->grid),
                                                                           h->grid.axisym, h->grid.r0, h->grid.h);
     counted(h);
 }
@@ -1079,7 +1097,7 @@ void enqueue_setup_levels(mg_handle *h, cudaStream_t s, const SetupGeom &gm, con
     const LevelBuf &f = h->L[0];
     cudaMemsetAsync(h->err_d, 0, sizeof(int), s);
     if (f.jflag) cudaMemsetAsync(h->err_d + 2, 0, sizeof(int), s);
-    k_setup_fine<DIM><<<cell_grid(f, DIM, f.n[0]), kBlock, 0, s>>>(gm, in, setup_out(f, mixed), h->err_d);
+    launch_k(h, k_setup_fine<DIM>, cell_grid(f, DIM, f.n[0]), kBlock, 0, s, 0, gm, in, setup_out(f, mixed), h->err_d);
     counted(h);
     double hl = h->grid.h;
     for (int l = 1; l < h->nlev; l++) {
@@ -1088,15 +1106,15 @@ void enqueue_setup_levels(mg_handle *h, cudaStream_t s, const SetupGeom &gm, con
         SetupGeom cg = gm;
         for (int a = 0; a < 3; a++) cg.n[a] = C.n[a];
         cg.h = 2.0 * hl;
-        k_setup_coarse<DIM><<<cell_grid(C, DIM, C.n[0]), kBlock, 0, s>>>(cg, setup_fine_of(F, hl), setup_out(C, mixed),
-                                                                         h->err_d);
+        launch_k(h, k_setup_coarse<DIM>, cell_grid(C, DIM, C.n[0]), kBlock, 0, s, 0, cg, setup_fine_of(F, hl),
+                 setup_out(C, mixed), h->err_d);
         counted(h);
         hl *= 2.0;
     }
     const LevelBuf &c = h->L[h->nlev - 1];
     cudaMemsetAsync(h->Mtmp, 0, sizeof(double) * h->nc * h->nc, s);
-    k_coarse_assemble<DIM><<<lin_blocks(c.N), 256, 0, s>>>(c.n[0], c.n[1], c.n[2], c.G[0], c.G[1],
-                                                           DIM == 3 ? c.G[2] : nullptr, c.D, c.l4, h->Mtmp);
+    launch_k(h, k_coarse_assemble<DIM>, lin_blocks(c.N), 256, 0, s, 0, c.n[0], c.n[1], c.n[2], c.G[0], c.G[1],
+             DIM == 3 ? c.G[2] : nullptr, c.D, c.l4, h->Mtmp);
     counted(h);
 }
 
@@ -1313,7 +1331,7 @@ mg_status solve_mixed(mg_handle *h, mg_stats *st) {
                                  [&](cudaStream_t s) { enqueue_residual_to32<DIM>(h, s, true); });
     if (e) return e;
     if (!h->x_stale) {
-        k_add_pairs<<<lin_blocks(f.N), 256, 0, h->stream>>>(f.x, mixed_delta(h), f.N);
+        launch_k(h, k_add_pairs, lin_blocks(f.N), 256, 0, h->stream, 0, f.x, mixed_delta(h), f.N);
         counted(h);
         CK(cudaGetLastError());
     }
@@ -1352,7 +1370,7 @@ mg_status enqueue_correction(mg_handle *h, cudaStream_t s, const double2 *rhs) {
     if (h->opt.precision == MG_MIXED) {
         enqueue_residual_to32<DIM>(h, s, true);        // x = 0: b32 = b, bt32 = Dinv b, e32 = 0
         for (int q = 0; q < h->opt.max_cycles; q++) enqueue_vcycle<float, DIM>(h, s, 0, h->opt.cycle);
-        k_add_correction<<<lin_blocks(f.N), 256, 0, s>>>(f.x, f.x32, f.N);
+        launch_k(h, k_add_correction, lin_blocks(f.N), 256, 0, s, 0, f.x, f.x32, f.N);
         counted(h);
     } else {
         for (int q = 0; q < h->opt.max_cycles; q++) enqueue_vcycle<double, DIM>(h, s, 0, h->opt.cycle);
@@ -1392,7 +1410,7 @@ mg_status capture_async(mg_handle *h) {
     // after max_cycles iterations at the latest
     if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&cond, cg, 0, cudaGraphCondAssignDefault);
     if (e == cudaSuccess) {
-        k_async_stop<<<1, 32, 0, h->cap>>>(h->norms_d, h->astat_d, h->opt.max_cycles, h->opt.rtol, cond, 1);
+        launch_k(h, k_async_stop, 1, 32, 0, h->cap, 0, h->norms_d, h->astat_d, h->opt.max_cycles, h->opt.rtol, cond, 1);
         pre++;
         e = cudaStreamGetCaptureInfo(h->cap, &cs, nullptr, &cg, &deps, nullptr, &ndeps);
     }
@@ -1413,14 +1431,14 @@ mg_status capture_async(mg_handle *h) {
         if (mixed) {
             for (int q = 0; q < h->opt.inner_cycles; q++) enqueue_vcycle<float, DIM>(h, h->cap2, 0, h->opt.cycle);
             const LevelBuf &f = h->L[0];
-            k_add_correction<<<lin_blocks(f.N), 256, 0, h->cap2>>>(mixed_delta(h), f.x32, f.N);
+            launch_k(h, k_add_correction, lin_blocks(f.N), 256, 0, h->cap2, 0, mixed_delta(h), f.x32, f.N);
             counted(h);
             enqueue_residual_to32<DIM>(h, h->cap2);
         } else {
             enqueue_vcycle<double, DIM>(h, h->cap2, 0, h->opt.cycle);
             enqueue_norm<DIM>(h, h->cap2, h->opt.nu2 > 0 && red_only_after_sweeps(h));
         }
-        k_async_stop<<<1, 32, 0, h->cap2>>>(h->norms_d, h->astat_d, h->opt.max_cycles, h->opt.rtol, cond, 0);
+        launch_k(h, k_async_stop, 1, 32, 0, h->cap2, 0, h->norms_d, h->astat_d, h->opt.max_cycles, h->opt.rtol, cond, 0);
         counted(h);
         h->cond_body = false;
         per = h->enq - b0;
@@ -1433,7 +1451,7 @@ mg_status capture_async(mg_handle *h) {
     if (e == cudaSuccess) {
         if (mixed) {
             const LevelBuf &f = h->L[0];
-            k_add_pairs<<<lin_blocks(f.N), 256, 0, h->cap>>>(f.x, mixed_delta(h), f.N);
+            launch_k(h, k_add_pairs, lin_blocks(f.N), 256, 0, h->cap, 0, f.x, mixed_delta(h), f.N);
             post++;
         }
         e = cudaMemcpyAsync(h->astat_h, h->astat_d, sizeof(AsyncStat), cudaMemcpyDeviceToHost, h->cap);
@@ -1622,6 +1640,7 @@ void get_tuning(const mg_handle *h, mg_tuning *t) {
     t->tail_level = h->tail_lev;
     t->tail_ctas = h->tail_ctas;
     t->persistent = h->persistent;
+    t->overlap = h->overlap;
 }
 
 }  // namespace
@@ -2118,6 +2137,7 @@ mg_status mg_set_tuning(mg_handle *h, const mg_tuning *t) {
     if (!no_tail && !tail_ctas_ok(h, t->tail_ctas))
         return fail(MG_ERR_INVALID_ARG, "tail cluster size must be 1, 8, or 16 where the device allows it");
     if (t->persistent != 0 && t->persistent != 1) return fail(MG_ERR_INVALID_ARG, "persistent must be 0 or 1");
+    if (t->overlap != 0 && t->overlap != 1) return fail(MG_ERR_INVALID_ARG, "overlap must be 0 or 1");
     CK(cudaStreamSynchronize(h->stream));
     for (int l = 0; l < h->nlev; l++) {
         h->sweep[l] = t->sweep[l];
@@ -2126,6 +2146,7 @@ mg_status mg_set_tuning(mg_handle *h, const mg_tuning *t) {
     h->tail_lev = no_tail ? h->nlev : t->tail_level;
     h->tail_ctas = no_tail ? kTailCtas : t->tail_ctas;
     h->persistent = t->persistent;
+    h->overlap = t->overlap;
     drop_graphs(h);
     return MG_OK;
 }

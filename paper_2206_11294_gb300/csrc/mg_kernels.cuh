@@ -60,6 +60,19 @@ __device__ __forceinline__ fq ldgq(const fq *p) {
     return fq{u.x, u.y, u.z, u.w};
 }
 
+// Programmatic dependent launch (griddepcontrol, sm_90 and later).  A kernel
+// of a cycle launched with the programmatic-serialisation attribute is set up
+// while the kernel before it in the stream drains: its blocks are scheduled
+// as that kernel's last blocks exit, and pdl_entry() (griddepcontrol.wait)
+// returns once that kernel has completed and its writes are visible.  Every
+// such kernel calls it before it reads or writes anything.  Launched without
+// the attribute it returns at once.  No kernel triggers its dependents early
+// (griddepcontrol.launch_dependents): blocks of the next grid scheduled while
+// this one still runs land on the SMs that free first, and small FP64 grids
+// packed onto a few SMs' FP64 pipes made the FP64 step 4% slower.
+__device__ __forceinline__ void pdl_entry() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+
+
 // Off-diagonal part of the two rows: sT = sum over interior faces of G^T_f T_nb,
 // sp = sum of G^p_f p_nb + l4 * sT (the p-row's T-Laplacian term, Eq. 28).
 // Neighbours beyond the grid contribute nothing (homogeneous boundary values;
@@ -134,6 +147,7 @@ __device__ __forceinline__ void rbgs_colour_block(const Level<R> &L, int colour,
 // a partial last wave can then fit one wave).  Same per-cell arithmetic.
 template <typename R, int DIM>
 __global__ void __launch_bounds__(kBX * kBY, 7) k_rbgs_colour2(Level<R> L, int colour) {
+    pdl_entry();
     using V2 = typename Vec<R>::v2;
     const int k = DIM == 3 ? (int)blockIdx.z : 0;
     V2 out[2];
@@ -159,9 +173,11 @@ __global__ void __launch_bounds__(kBX * kBY, 7) k_rbgs_colour2(Level<R> L, int c
 
 template <typename R, int DIM, bool P>
 __global__ void __launch_bounds__(kBX * kBY, 8) k_rbgs_colour(Level<R> L, int colour) {
+    pdl_entry();
     CMG_TILES(P, ((L.n0 + 1) / 2 + kBX - 1) / kBX, (L.n1 + kBY - 1) / kBY, DIM == 3 ? L.n2 : 1,
               (rbgs_colour_block<R, DIM>(L, colour, bx, by, bz)));
 }
+
 
 // ---------------------------------------------------------------------------
 // The stop test of a solve run as one graph (mg_solve_async): the V-cycles
@@ -189,6 +205,7 @@ __device__ __forceinline__ bool async_converged(const double n0[2], const double
 
 __global__ void k_async_stop(const double *__restrict__ norms, AsyncStat *__restrict__ st, int max_it, double rtol,
                              cudaGraphConditionalHandle cond, int init) {
+    pdl_entry();
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     bool ok;
     if (init) {
@@ -230,6 +247,7 @@ __device__ __forceinline__ void wjac_block(const Level<R> &L, const typename Vec
 template <typename R, int DIM, bool P>
 __global__ void __launch_bounds__(kBX * kBY, 8) k_wjac(Level<R> L, const typename Vec<R>::v2 *__restrict__ xin,
                                                       typename Vec<R>::v2 *__restrict__ xout, R omega) {
+    pdl_entry();
     CMG_TILES(P, (L.n0 + kBX - 1) / kBX, (L.n1 + kBY - 1) / kBY, DIM == 3 ? L.n2 : 1,
               (wjac_block<R, DIM>(L, xin, xout, omega, bx, by, bz)));
 }
@@ -328,6 +346,7 @@ __device__ __forceinline__ void rbgs_fused2d_block(const Level<R> &L, const type
 template <typename R, int TX, int TY>
 __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 8 : 4)
     k_rbgs_fused2d(Level<R> L, const typename Vec<R>::v2 *__restrict__ xin, typename Vec<R>::v2 *__restrict__ xout) {
+    pdl_entry();
     rbgs_fused2d_block<R, TX, TY>(L, xin, xout, blockIdx.x, blockIdx.y);
 }
 
@@ -376,6 +395,7 @@ __device__ __forceinline__ void residual_restrict_block(const Level<R> &F, const
 
 template <typename R, int DIM, bool RED, bool P>
 __global__ void __launch_bounds__(kBX * kBY) k_residual_restrict(Level<R> F, Level<R> C) {
+    pdl_entry();
     CMG_TILES(P, (C.n0 + kBX - 1) / kBX, (C.n1 + kBY - 1) / kBY, DIM == 3 ? C.n2 : 1,
               (residual_restrict_block<R, DIM, true, RED>(F, C, bx, by, bz)));
 }
@@ -435,6 +455,7 @@ __device__ __forceinline__ void prolong_add_block(const Level<R> &C, const Level
 
 template <typename R, int DIM, bool P>
 __global__ void __launch_bounds__(kBX * kBY) k_prolong_add(Level<R> C, Level<R> F, BcFlags bc) {
+    pdl_entry();
     CMG_TILES(P, (F.n0 + kBX - 1) / kBX, (F.n1 + kBY - 1) / kBY, DIM == 3 ? F.n2 : 1,
               (prolong_add_block<R, DIM>(C, F, bc, bx, by, bz)));
 }
@@ -445,6 +466,7 @@ __global__ void __launch_bounds__(kBX * kBY) k_prolong_add(Level<R> C, Level<R> 
 // ---------------------------------------------------------------------------
 template <typename R>
 __global__ void k_coarse_matvec(const R *__restrict__ Minv, const R *__restrict__ b, R *__restrict__ x, int n) {
+    pdl_entry();
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (warp >= n) return;
@@ -577,6 +599,7 @@ __device__ __forceinline__ double2 norm_block(const Level<double> &L, int bx, in
 template <int DIM, bool RED, bool P>
 __global__ void __launch_bounds__(kBX * kBY) k_norm_partials(Level<double> L, double2 *__restrict__ partial,
                                                            unsigned int *__restrict__ ticket, double *__restrict__ out) {
+    pdl_entry();
     double zT2 = 0.0, zp2 = 0.0;     // a block's tiles accumulate, then one reduction
     CMG_TILES(P, norm_gx(L.n0), norm_gy(L.n1), DIM == 3 ? L.n2 : 1, (norm_tile<DIM, RED>(L, bx, by, bz, zT2, zp2)));
     block_sum2(zT2, zp2);
@@ -653,6 +676,7 @@ __global__ void __launch_bounds__(kBX * kBY) k_residual64_to32(Level<double> L, 
                                                              double2 *__restrict__ partial,
                                                              unsigned int *__restrict__ ticket,
                                                              double *__restrict__ out) {
+    pdl_entry();
     double zT2 = 0.0, zp2 = 0.0;
     CMG_TILES(P, norm_gx(L.n0), norm_gy(L.n1), DIM == 3 ? L.n2 : 1,
               (residual64_to32_tile<DIM>(L, b32, bt32, e32, r_out, r_out2, bx, by, bz, zT2, zp2)));
@@ -664,6 +688,7 @@ __global__ void __launch_bounds__(kBX * kBY) k_residual64_to32(Level<double> L, 
 
 // x += delta: the solution from the initial guess and the accumulated correction
 __global__ void k_add_pairs(double2 *__restrict__ x, const double2 *__restrict__ delta, long long N) {
+    pdl_entry();
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
         const double2 a = x[c], d = delta[c];
         x[c] = make_double2(a.x + d.x, a.y + d.y);
@@ -672,6 +697,7 @@ __global__ void k_add_pairs(double2 *__restrict__ x, const double2 *__restrict__
 
 // x64 += e32 (the refinement update; mixed solves pass the correction delta as x64)
 __global__ void k_add_correction(double2 *__restrict__ x, const float2 *__restrict__ e, long long N) {
+    pdl_entry();
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
         const float2 d = e[c];
         double2 v = x[c];
@@ -774,6 +800,7 @@ template <int DIM>
 __global__ void __launch_bounds__(kBX * kBY) k_prep_rhs(const __grid_constant__ Level<double> L,
                                                       const double2 *__restrict__ rhs, const __grid_constant__ BcVals bv,
                                                       int axisym, double r0, double h) {
+    pdl_entry();
     CMG_TILES(false, (L.n0 + kBX - 1) / kBX, (L.n1 + kBY - 1) / kBY, DIM == 3 ? L.n2 : 1,
               (prep_rhs_block<DIM>(L, rhs, nullptr, bv, axisym, r0, h, bx, by, bz)));
 }
@@ -989,6 +1016,7 @@ __device__ __forceinline__ void setup_fine_block(const SetupGeom &gm, const Setu
 
 template <int DIM>
 __global__ void __launch_bounds__(kBX * kBY) k_setup_fine(SetupGeom gm, SetupIn in, SetupOut o, int *__restrict__ err) {
+    pdl_entry();
     CMG_TILES(false, (gm.n[0] + kBX - 1) / kBX, (gm.n[1] + kBY - 1) / kBY, DIM == 3 ? gm.n[2] : 1,
               (setup_fine_block<DIM>(gm, in, o, err, bx, by, bz)));
 }
@@ -1084,6 +1112,7 @@ __device__ __forceinline__ void setup_coarse_block(const SetupGeom &cg, const Se
 template <int DIM>
 __global__ void __launch_bounds__(kBX * kBY) k_setup_coarse(SetupGeom cg, SetupFine F, SetupOut o,
                                                           int *__restrict__ err) {
+    pdl_entry();
     CMG_TILES(false, (cg.n[0] + kBX - 1) / kBX, (cg.n[1] + kBY - 1) / kBY, DIM == 3 ? cg.n[2] : 1,
               (setup_coarse_block<DIM>(cg, F, o, err, bx, by, bz)));
 }
@@ -1101,6 +1130,7 @@ template <int DIM>
 __global__ void k_coarse_assemble(int n0, int n1, int n2, const double2 *__restrict__ G0,
                                   const double2 *__restrict__ G1, const double2 *__restrict__ G2,
                                   const dq *__restrict__ D, const double *__restrict__ l4, double *__restrict__ M) {
+    pdl_entry();
     const long long N = (long long)n0 * n1 * n2;
     const long long n = 2 * N;
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
@@ -2081,6 +2111,7 @@ __global__ void __launch_bounds__(kLuSolveThreads) k_coarse_lu(const double *__r
                                                                const double *__restrict__ dinv, int n, int kl, int ku,
                                                                const R *__restrict__ b, R *__restrict__ x,
                                                                const int *__restrict__ err) {
+    pdl_entry();
     extern __shared__ double lusm[];
     coarse_lu_solve_block<R>(Lb, Uc, piv, dinv, n, kl, ku, b, x, err, lusm);
 }

@@ -249,6 +249,7 @@ __device__ __forceinline__ void tail_prolong(const TailCta<R> &C, const TailLeve
 // CL: launched as a cluster of CTAs (distributed shared memory); else one CTA.
 template <typename R, int DIM, bool CL>
 __global__ void __launch_bounds__(kTailThreads) k_vcycle_tail(const __grid_constant__ TailArgs<R> A) {
+    pdl_entry();
     namespace cg = cooperative_groups;
     using V2 = typename Vec<R>::v2;
     extern __shared__ __align__(16) unsigned char tail_smem[];

@@ -12,7 +12,7 @@ from paper_2206_11294_gb300 import binding as B
 
 def _tuning(levels=5):
     return dict(levels=levels, sweep=["colour", "fused", "fused", "colour", "colour"][:levels],
-                tile=[0, 1, 2, 0, 0][:levels], tail_level=3, tail_ctas=8, persistent=1)
+                tile=[0, 1, 2, 0, 0][:levels], tail_level=3, tail_ctas=8, persistent=1, overlap=0)
 
 
 def test_key_depends_on_shape_precision_and_cycle_not_on_spacing():
@@ -61,10 +61,15 @@ def test_ctypes_mirror_roundtrip():
     t = B.MgTuning.from_dict(_tuning())
     assert t.sweep[1] == B.MG_SWEEP_FUSED and t.sweep[0] == B.MG_SWEEP_COLOUR
     assert t.as_dict() == _tuning()
-    # layout of the C struct: levels, sweep[32], tile[32], tail_level, tail_ctas, persistent (all int)
-    assert C.sizeof(B.MgTuning) == 4 * (1 + 2 * B.MG_MAX_LEVELS + 3)
+    # layout of the C struct: levels, sweep[32], tile[32], tail_level, tail_ctas, persistent, overlap (all int)
+    assert C.sizeof(B.MgTuning) == 4 * (1 + 2 * B.MG_MAX_LEVELS + 4)
     assert B.MgTuning.tail_ctas.offset == 4 * (1 + 2 * B.MG_MAX_LEVELS + 1)
     assert B.MgTuning.persistent.offset == 4 * (1 + 2 * B.MG_MAX_LEVELS + 2)
+    assert B.MgTuning.overlap.offset == 4 * (1 + 2 * B.MG_MAX_LEVELS + 3)
+    # an entry stored before the overlap field existed reads as the library's default, 1
+    d = _tuning()
+    del d["overlap"]
+    assert B.MgTuning.from_dict(d).overlap == 1
 
 
 def test_sweep_names_roundtrip():

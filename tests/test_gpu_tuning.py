@@ -59,6 +59,8 @@ def _variants(s):
     colour = dict(base, sweep=["colour"] * n, tile=[0] * n, tail_level=n, tail_ctas=8, persistent=0)
     out.append(colour)
     out.append(dict(colour, persistent=1))
+    out.append(dict(colour, overlap=0))                     # plain stream order instead of dependent launches
+    out.append(dict(colour, overlap=0, persistent=1))
     out.append(dict(colour, sweep=["colour2"] * n))
     if dim == 2:
         for t in range(3):
@@ -136,6 +138,7 @@ def test_set_tuning_rejects_bad_choices(torch_cuda):
                       (s2, lambda t: t.update(tail_level=1, tail_ctas=1)),   # 6144 FP64 cells: > 200 KB
                       # a valid sweep change with an invalid flag: nothing of it may be applied
                       (s2, lambda t: t.update(persistent=2, sweep=["fused"] + t["sweep"][1:])),
+                      (s2, lambda t: t.update(overlap=2, sweep=["fused"] + t["sweep"][1:])),
                       (s2, lambda t: t.update(tail_level=1))]:      # level 1 of 192x128 has 6144 cells: allowed
         before = s.tuning()
         t = dict(before, sweep=list(before["sweep"]), tile=list(before["tile"]))
