@@ -59,9 +59,9 @@ FALLBACK_HBM_GBS = 6800.0
 # 16 finest-level launches of one solve sequence).
 TRAFFIC = {
     "k_rbgs_colour<double,2> on the finest level of bubbles16_1024x1024": {
-        "cold": 103.8e6, "warm": 33.8e6,
-        "source": "ncu capture of k_rbgs_colour<double,2> on the 1024^2 level: --set full (cold), "
-                  "--cache-control none over one solve sequence (warm)"},
+        "cold": 103.9e6, "warm": 32.4e6,
+        "source": "ncu capture of k_rbgs_colour<double,2> on the 1024^2 level: --set full (cold, mean of the "
+                  "first two launches), --cache-control none over two solve sequences (warm, median of 16)"},
 }
 L2_FLUSH_BYTES = 256 << 20
 # algorithmic bytes per finest cell of one full red-black sweep: read x 16 +
