@@ -1045,15 +1045,17 @@ __device__ __forceinline__ void setup_coarse_cells(const SetupGeom &cg, const Se
     const double *l4f = F.l4;
     const double hf = F.h;
     const long long cc = cell_id(I, J, K, cg.n[0], cg.n[1]);
-    double a0 = 0, a1 = 0, a2 = 0, a3 = 0, v4 = 0, vs = 0;
+    // S = s [[l1, l2], [0, l3]] on every level: its lower-left entry is zero
+    // by construction and is neither summed nor scaled
+    double a0 = 0, a1 = 0, a3 = 0, v4 = 0, vs = 0;
 #pragma unroll
     for (int q = 0; q < (1 << DIM); q++) {
         const int i = 2 * I + (q & 1);
         const long long f = cell_id(i, 2 * J + ((q >> 1) & 1), DIM == 3 ? 2 * K + (q >> 2) : 0, fn0, fn1);
         const dq sf = Sf[f];
         // sums start from the first child: an addition to 0.0 would still take an FP64 issue slot
-        if (q == 0) { a0 = sf.a; a1 = sf.b; a2 = sf.c; a3 = sf.d; }
-        else { a0 += sf.a; a1 += sf.b; a2 += sf.c; a3 += sf.d; }
+        if (q == 0) { a0 = sf.a; a1 = sf.b; a3 = sf.d; }
+        else { a0 += sf.a; a1 += sf.b; a3 += sf.d; }
         if (AXI) {
             const double sc = cg.r0 + (i + 0.5) * hf;
             if (q == 0) { v4 = sc * l4f[f]; vs = sc; }
@@ -1063,7 +1065,7 @@ __device__ __forceinline__ void setup_coarse_cells(const SetupGeom &cg, const Se
         }
     }
     const double wb = 1.0 / (1 << DIM);
-    const dq S{a0 * wb, a1 * wb, a2 * wb, a3 * wb};
+    const dq S{a0 * wb, a1 * wb, 0.0, a3 * wb};
     const double l4 = AXI ? v4 / vs : v4 * wb;   // volume-weighted mean (a power-of-two mean is exact as a product)
     const int P[3] = {I, J, K};
     const int fm[3][2] = {{fn0 + 1, fn1}, {fn0, fn1 + 1}, {fn0, fn1}};   // fine face array dims (x, y) per axis
