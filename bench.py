@@ -704,6 +704,12 @@ def run_wall3d(args):
     results = {}
     for prec in ("fp64", "mixed"):
         s = Solver(p.grid, precision=prec, rtol=1e-10, max_cycles=60, stream=stream)
+        tuned = "library defaults (--no-tune)"
+        if not args.no_tune:                   # the library's autotuner, before the warm-up (untimed)
+            from paper_2206_11294_gb300.autotune import describe
+            s.set_coeffs(d["lam"], d["fa"], d["fk"])
+            t, _ = s.autotune(args.tune_reps)
+            tuned = describe(t)
         s.set_timing(True)
         for _ in range(args.warmup):
             d["x"].copy_(d["x0"])
@@ -727,7 +733,7 @@ def run_wall3d(args):
         byts = SWEEP_BYTES_PER_CELL[(prec, 3)] * c["smooth_cells"] * spl
         ent = {"mcell_vcycles_per_s": sum(p.grid.N * x["cycles"] for x in st) / secs / 1e6,
                "solves_per_s": len(st) / secs, "ms_per_step": secs * 1e3 / args.steps, "cycles": st[0]["cycles"],
-               "outer": st[0]["outer"], "sweep_us": avg * 1e6,
+               "outer": st[0]["outer"], "sweep_us": avg * 1e6, "tuning": tuned,
                "sweep_hbm": {"achieved_GBs": byts / avg / 1e9, "frac": byts / avg / 1e9 / peak, "peak": peak,
                              "peak_source": peak_kind}}
         if prec == "fp64":

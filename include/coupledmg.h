@@ -251,7 +251,7 @@ MG_API mg_status mg_counters(const mg_handle *h, long long *launches, double *sm
  * Defaults after mg_create: colour sweeps for FP64 cycles, fused 64 x 16 for
  * the FP32 cycles of mixed precision on 2D grids; the tail from the first
  * level below the finest with at most 4096 cells, 8 CTAs; overlap 1.
- * mg_autotune also tries one block, and keeps the handle's overlap. */
+ * mg_autotune also tries one block. */
 #define MG_MAX_LEVELS 32
 enum { MG_SWEEP_COLOUR = 1, MG_SWEEP_FUSED = 2, MG_SWEEP_ASYNC = 3, MG_SWEEP_COLOUR2 = 4 };
 typedef struct {
@@ -272,7 +272,9 @@ MG_API mg_status mg_set_tuning(mg_handle *h, const mg_tuning *t);
  * per level, each sweep kernel (and tile shape) as one CUDA graph of `reps`
  * pairs of sweeps (median of five replays); then each allowed tail (none,
  * every allowed first level on 1, 8 or 16 CTAs), with and without persistent
- * waves, as a graph of one V-cycle
+ * waves, then the chosen kernels with and without dependent launches (plain
+ * order kept only where it is more than 1% faster), each as a graph of one
+ * V-cycle
  * launched 4 * reps + 1 times, each launch timed with CUDA events on the
  * handle's stream and waited for, as the solve does per cycle (median), so
  * the per-launch cost of the graph counts.

@@ -96,10 +96,12 @@ class TuningTable:
 
 def describe(tuning: dict) -> str:
     """Short text form: per level C (colour), C2 (colour, two rows per thread), F<tile> (fused) or
-    A<tile> (TMA-fed fused), then the tail."""
+    A<tile> (TMA-fed fused), then the tail; "plain stream order" where the kernels do not launch as
+    programmatic dependents."""
     code = {"colour": lambda t: "C", "colour2": lambda t: "C2", "async": lambda t: f"A{t}", "fused": lambda t: f"F{t}"}
     lv = ",".join(code[s](t) for s, t in zip(tuning["sweep"], tuning["tile"]))
     tail = "none" if tuning["tail_level"] >= tuning["levels"] else \
         f"from L{tuning['tail_level']} on {tuning['tail_ctas']} CTAs"
     waves = ", persistent waves" if tuning.get("persistent") else ""
-    return f"sweeps [{lv}], tail {tail}{waves}"
+    order = ", plain stream order" if tuning.get("overlap", 1) == 0 else ""
+    return f"sweeps [{lv}], tail {tail}{waves}{order}"

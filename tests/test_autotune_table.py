@@ -80,8 +80,9 @@ def test_sweep_names_roundtrip():
 
 
 def test_describe():
-    assert describe(_tuning()) == "sweeps [C,F1,F2,C,C], tail from L3 on 8 CTAs, persistent waves"
-    d = _tuning()
+    assert describe(_tuning()) == "sweeps [C,F1,F2,C,C], tail from L3 on 8 CTAs, persistent waves, plain stream order"
+    assert describe(dict(_tuning(), overlap=1)) == "sweeps [C,F1,F2,C,C], tail from L3 on 8 CTAs, persistent waves"
+    d = dict(_tuning(), overlap=1)
     d["tail_level"] = 5
     d["persistent"] = 0
     assert describe(d).endswith("tail none")

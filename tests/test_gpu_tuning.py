@@ -117,6 +117,7 @@ def test_autotune_picks_valid_choice_and_keeps_results(torch_cuda, name, precisi
         assert set(tuning["sweep"]) <= {"colour", "colour2"}
     assert tuning["tail_level"] >= n or 1 <= tuning["tail_level"] <= n - 2
     assert tuning["tail_ctas"] in (1, 8, 16)
+    assert tuning["overlap"] in (0, 1)
     assert s0.tuning() == tuning
     x = p.x0.copy()
     st = s0.solve(p.b, x)                     # scratch overwritten by the tuner: same solve
