@@ -351,9 +351,9 @@ def run_ours(args, rank, world):
     dim0 = probs[0].grid.dim
     t0 = solvers[0].tuning()
     rname = "double" if args.precision == "fp64" else "float"
-    if t0["sweep"][0] == "fused":
+    if t0["sweep"][0] in ("fused", "fused2"):
         tx, ty = TILE_SHAPES[t0["tile"][0]]
-        kernel = f"k_rbgs_fused2d<{rname},{tx},{ty}>"
+        kernel = f"k_rbgs_fused2d{'_x2' if t0['sweep'][0] == 'fused2' else ''}<{rname},{tx},{ty}>"
     else:
         kernel = f"k_rbgs_colour<{rname},{dim0}>"
     kernel += " on the finest level of " + probs[0].name

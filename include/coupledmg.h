@@ -231,6 +231,12 @@ MG_API mg_status mg_counters(const mg_handle *h, long long *launches, double *sm
  *               mbarrier, persistent blocks, the next tiles' copies in flight
  *               while a tile is computed; a tile whose two stages exceed one
  *               block's 227 KB of shared memory is refused, e.g. 64 x 16 FP64);
+ *               or MG_SWEEP_FUSED2 (2D only, red-black smoothing with
+ *               nu1 / 2 + nu2 / 2 even: each pair of sweeps as one launch on
+ *               tiles staged with a 4-cell halo, the red and black values of
+ *               shrinking rings recomputed per tile; the level's values move
+ *               between its two buffers and are back in place at the end of
+ *               each cycle);
  *   tile[l]     fused tile shape, cells: 0 = 64 x 16, 1 = 32 x 16, 2 = 32 x 8;
  *   tail_level  the levels from this one to the coarsest run as one kernel
  *               (smoothing, restriction, coarsest solve, prolongation as
@@ -253,7 +259,7 @@ MG_API mg_status mg_counters(const mg_handle *h, long long *launches, double *sm
  * level below the finest with at most 4096 cells, 8 CTAs; overlap 1.
  * mg_autotune also tries one block. */
 #define MG_MAX_LEVELS 32
-enum { MG_SWEEP_COLOUR = 1, MG_SWEEP_FUSED = 2, MG_SWEEP_ASYNC = 3, MG_SWEEP_COLOUR2 = 4 };
+enum { MG_SWEEP_COLOUR = 1, MG_SWEEP_FUSED = 2, MG_SWEEP_ASYNC = 3, MG_SWEEP_COLOUR2 = 4, MG_SWEEP_FUSED2 = 5 };
 typedef struct {
     int levels;                 /* mg_get_tuning: the hierarchy's levels (ignored by mg_set_tuning) */
     int sweep[MG_MAX_LEVELS];

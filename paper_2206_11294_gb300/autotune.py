@@ -95,10 +95,11 @@ class TuningTable:
 
 
 def describe(tuning: dict) -> str:
-    """Short text form: per level C (colour), C2 (colour, two rows per thread), F<tile> (fused) or
-    A<tile> (TMA-fed fused), then the tail; "plain stream order" where the kernels do not launch as
-    programmatic dependents."""
-    code = {"colour": lambda t: "C", "colour2": lambda t: "C2", "async": lambda t: f"A{t}", "fused": lambda t: f"F{t}"}
+    """Short text form: per level C (colour), C2 (colour, two rows per thread), F<tile> (fused),
+    A<tile> (TMA-fed fused) or P<tile> (fused pairs of sweeps), then the tail; "plain stream order"
+    where the kernels do not launch as programmatic dependents."""
+    code = {"colour": lambda t: "C", "colour2": lambda t: "C2", "async": lambda t: f"A{t}", "fused": lambda t: f"F{t}",
+            "fused2": lambda t: f"P{t}"}
     lv = ",".join(code[s](t) for s, t in zip(tuning["sweep"], tuning["tile"]))
     tail = "none" if tuning["tail_level"] >= tuning["levels"] else \
         f"from L{tuning['tail_level']} on {tuning['tail_ctas']} CTAs"

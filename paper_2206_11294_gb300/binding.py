@@ -40,9 +40,9 @@ EXPORTS = ["mg_default_options", "mg_workspace_size", "mg_create", "mg_set_coeff
            "mg_composite_destroy"]
 
 MG_MAX_LEVELS = 32
-MG_SWEEP_COLOUR, MG_SWEEP_FUSED, MG_SWEEP_ASYNC, MG_SWEEP_COLOUR2 = 1, 2, 3, 4
+MG_SWEEP_COLOUR, MG_SWEEP_FUSED, MG_SWEEP_ASYNC, MG_SWEEP_COLOUR2, MG_SWEEP_FUSED2 = 1, 2, 3, 4, 5
 _SWEEP_NAMES = {MG_SWEEP_COLOUR: "colour", MG_SWEEP_FUSED: "fused", MG_SWEEP_ASYNC: "async",
-                MG_SWEEP_COLOUR2: "colour2"}
+                MG_SWEEP_COLOUR2: "colour2", MG_SWEEP_FUSED2: "fused2"}
 _SWEEP_CODES = {v: k for k, v in _SWEEP_NAMES.items()}
 TILE_SHAPES = [(64, 16), (32, 16), (32, 8)]      # fused tile shapes by index (cells x, y)
 

@@ -478,6 +478,14 @@ void launch_fused(const mg_handle *h, const LevelBuf &lb, const Level<R> &v, cud
     launch_k(h, k_rbgs_fused2d<R, TX, TY>, gf, kBlock, 0, s, 0, v, xa, v.x);
 }
 
+// Two sweeps in one launch (k_rbgs_fused2d_x2): src -> dst.
+template <typename R, int TX, int TY>
+void launch_fused_x2(const mg_handle *h, const LevelBuf &lb, const Level<R> &v, const typename Vec<R>::v2 *src,
+                     typename Vec<R>::v2 *dst, cudaStream_t s) {
+    const dim3 gf((unsigned)((lb.n[0] + TX - 1) / TX), (unsigned)((lb.n[1] + TY - 1) / TY), 1);
+    launch_k(h, k_rbgs_fused2d_x2<R, TX, TY>, gf, kBlock, 0, s, 0, v, src, dst);
+}
+
 // ---------------------------------------------------------------- TMA sweeps
 // Shared memory of the TMA fused sweep with tile `tile`.
 template <typename R>
@@ -596,14 +604,30 @@ void launch_fused_tma(const mg_handle *h, int l, int tile, const Level<R> &v, cu
 }
 
 // `sweeps` red-black sweeps on level l with the given kernel choice.  Fused
-// (2D only): pairs of sweeps run as fused launches x -> xalt -> x; a leftover
-// odd sweep (and every non-fused sweep) runs as two colour launches in place.
-// The result always ends in x and is the same, bit for bit, for every choice.
+// (2D only): pairs of sweeps run as fused launches x -> xalt -> x.  Fused
+// pairs (MG_SWEEP_FUSED2, 2D only): each pair of sweeps is one launch from
+// the buffer that holds the level's values to the other one.  A leftover odd
+// sweep (and every non-fused sweep) runs as two colour launches in place.
+// alt: the values start in xalt (only after fused pairs).  Returns whether
+// they end in xalt.  The values are the same, bit for bit, for every choice.
 template <typename R, int DIM>
-void enqueue_sweeps(const mg_handle *h, cudaStream_t s, int l, int sweeps, int kind, int tile) {
+bool enqueue_sweeps(const mg_handle *h, cudaStream_t s, int l, int sweeps, int kind, int tile, bool alt = false) {
+    using V2 = typename Vec<R>::v2;
     const LevelBuf &lb = h->L[l];
     Level<R> v = view<R>(lb);
+    V2 *const xm = v.x, *const xa = xalt_of<R>(lb);
+    if (alt) v.x = xa;
     int q = 0;
+    if (DIM == 2 && kind == MG_SWEEP_FUSED2) {
+        for (; q + 1 < sweeps; q += 2) {
+            V2 *dst = v.x == xm ? xa : xm;
+            if (tile == 1) launch_fused_x2<R, kTileX[1], kTileY[1]>(h, lb, v, v.x, dst, s);
+            else if (tile == 2) launch_fused_x2<R, kTileX[2], kTileY[2]>(h, lb, v, v.x, dst, s);
+            else launch_fused_x2<R, kTileX[0], kTileY[0]>(h, lb, v, v.x, dst, s);
+            v.x = dst;
+            counted(h);
+        }
+    }
     if (DIM == 2 && kind == MG_SWEEP_FUSED) {
         for (; q + 1 < sweeps; q += 2) {
             if (tile == 1) launch_fused<R, kTileX[1], kTileY[1]>(h, lb, v, s);
@@ -640,6 +664,7 @@ void enqueue_sweeps(const mg_handle *h, cudaStream_t s, int l, int sweeps, int k
         }
         counted(h, 2);
     }
+    return v.x != xm;
 }
 
 // `sweeps` weighted block Jacobi sweeps on level l, alternating x -> xalt ->
@@ -663,10 +688,21 @@ void enqueue_wjac(const mg_handle *h, cudaStream_t s, int l, int sweeps) {
     if (a != v.x) cudaMemcpyAsync(v.x, a, sizeof(V2) * lb.N, cudaMemcpyDeviceToDevice, s);
 }
 
+// Returns whether the level's values end in xalt (fused pairs only; alt:
+// they start there).
 template <typename R, int DIM>
-void enqueue_smooth(const mg_handle *h, cudaStream_t s, int l, int sweeps) {
-    if (h->opt.smoother == MG_SMOOTH_WJAC) enqueue_wjac<R, DIM>(h, s, l, sweeps);
-    else enqueue_sweeps<R, DIM>(h, s, l, sweeps, h->sweep[l], h->tile[l]);
+bool enqueue_smooth(const mg_handle *h, cudaStream_t s, int l, int sweeps, bool alt = false) {
+    if (h->opt.smoother == MG_SMOOTH_WJAC) {
+        enqueue_wjac<R, DIM>(h, s, l, sweeps);
+        return false;
+    }
+    return enqueue_sweeps<R, DIM>(h, s, l, sweeps, h->sweep[l], h->tile[l], alt);
+}
+
+// Fused pairs leave a level's values in xalt after an odd number of pairs;
+// a V-cycle needs them back in x at its end: nu1 / 2 + nu2 / 2 even.
+bool fused2_ok(const mg_options &o, int dim) {
+    return dim == 2 && o.smoother == MG_SMOOTH_RBGS && (o.nu1 / 2 + o.nu2 / 2) % 2 == 0;
 }
 
 // Red-black Gauss-Seidel leaves the residual of the colour swept last at zero,
@@ -678,9 +714,10 @@ bool red_only_after_sweeps(const mg_handle *h) { return h->opt.smoother == MG_SM
 bool tail_runs(const mg_handle *h) { return h->opt.cycle == MG_CYCLE_V && h->opt.smoother == MG_SMOOTH_RBGS; }
 
 // Kernel launches and sweeps of one call of enqueue_smooth.
-void smooth_launches(bool fused, int sweeps, long long *launches, long long *sweeps_out) {
+void smooth_launches(int kind, bool dim2, int sweeps, long long *launches, long long *sweeps_out) {
+    const bool fused = dim2 && (kind == MG_SWEEP_FUSED || kind == MG_SWEEP_ASYNC || kind == MG_SWEEP_FUSED2);
     const int fused_pairs = fused ? sweeps / 2 : 0;
-    *launches = 2LL * fused_pairs + 2LL * (sweeps - 2 * fused_pairs);
+    *launches = (kind == MG_SWEEP_FUSED2 ? 1LL : 2LL) * fused_pairs + 2LL * (sweeps - 2 * fused_pairs);
     *sweeps_out = sweeps;
 }
 
@@ -764,21 +801,24 @@ void enqueue_vcycle(const mg_handle *h, cudaStream_t s, int l, int type) {
     const bool tm_pre = h->timing && !h->cond_body && l == 0 && h->opt.nu1 > 0;
     const bool tm_post = h->timing && !h->cond_body && l == 0 && h->opt.nu1 == 0;
     if (tm_pre) cudaEventRecordWithFlags(h->ev[0], s, cudaEventRecordExternal);
-    enqueue_smooth<R, DIM>(h, s, l, h->opt.nu1);
+    const bool alt = enqueue_smooth<R, DIM>(h, s, l, h->opt.nu1);
     if (tm_pre) cudaEventRecordWithFlags(h->ev[1], s, cudaEventRecordExternal);
+    // the level's values, where the smoothing left them
+    Level<R> vl = view<R>(lb);
+    if (alt) vl.x = xalt_of<R>(lb);
     const dim3 rg = cell_grid(cb, DIM, cb.n[0]);
     if (h->opt.nu1 > 0 && red_only_after_sweeps(h)) {
         if (h->persistent)
-            launch_k(h, k_residual_restrict<R, DIM, true, true>, wave((const void *)k_residual_restrict<R, DIM, true, true>, tiles_of(rg)), kBlock, 0, s, 0, view<R>(lb),
+            launch_k(h, k_residual_restrict<R, DIM, true, true>, wave((const void *)k_residual_restrict<R, DIM, true, true>, tiles_of(rg)), kBlock, 0, s, 0, vl,
                                                                                                           view<R>(cb));
         else
-            launch_k(h, k_residual_restrict<R, DIM, true, false>, rg, kBlock, 0, s, 0, view<R>(lb), view<R>(cb));
+            launch_k(h, k_residual_restrict<R, DIM, true, false>, rg, kBlock, 0, s, 0, vl, view<R>(cb));
     } else {
         if (h->persistent)
             launch_k(h, k_residual_restrict<R, DIM, false, true>, wave((const void *)k_residual_restrict<R, DIM, false, true>, tiles_of(rg)), kBlock, 0, s, 0, 
-                    view<R>(lb), view<R>(cb));
+                    vl, view<R>(cb));
         else
-            launch_k(h, k_residual_restrict<R, DIM, false, false>, rg, kBlock, 0, s, 0, view<R>(lb), view<R>(cb));
+            launch_k(h, k_residual_restrict<R, DIM, false, false>, rg, kBlock, 0, s, 0, vl, view<R>(cb));
     }
     counted(h);
     enqueue_vcycle<R, DIM>(h, s, l + 1, type);
@@ -787,13 +827,17 @@ void enqueue_vcycle(const mg_handle *h, cudaStream_t s, int l, int type) {
     const dim3 pg = cell_grid(lb, DIM, lb.n[0]);
     if (h->persistent)
         launch_k(h, k_prolong_add<R, DIM, true>, wave((const void *)k_prolong_add<R, DIM, true>, tiles_of(pg)), kBlock, 0, s, 0, 
-            view<R>(cb), view<R>(lb), bc_flags(h->grid));
+            view<R>(cb), vl, bc_flags(h->grid));
     else
-        launch_k(h, k_prolong_add<R, DIM, false>, pg, kBlock, 0, s, 0, view<R>(cb), view<R>(lb), bc_flags(h->grid));
+        launch_k(h, k_prolong_add<R, DIM, false>, pg, kBlock, 0, s, 0, view<R>(cb), vl, bc_flags(h->grid));
     counted(h);
     if (tm_post) cudaEventRecordWithFlags(h->ev[0], s, cudaEventRecordExternal);
-    enqueue_smooth<R, DIM>(h, s, l, h->opt.nu2);
+    const bool alt_end = enqueue_smooth<R, DIM>(h, s, l, h->opt.nu2, alt);
     if (tm_post) cudaEventRecordWithFlags(h->ev[1], s, cudaEventRecordExternal);
+    // (fused pairs are allowed only where the pairs of a cycle are even in number)
+    if (alt_end)
+        cudaMemcpyAsync(view<R>(lb).x, xalt_of<R>(lb), sizeof(typename Vec<R>::v2) * lb.N, cudaMemcpyDeviceToDevice,
+                        s);
 }
 
 // after_sweep: x has just come out of a red-black sweep (red cells only).
@@ -979,13 +1023,12 @@ mg_status accumulate_timing(mg_handle *h) {
     CK(cudaEventElapsedTime(&a, h->ev[0], h->ev[1]));
     h->smooth_ms += (double)a;
     long long l1, s1;
-    const bool fused = h->grid.dim == 2 && (h->sweep[0] == MG_SWEEP_FUSED || h->sweep[0] == MG_SWEEP_ASYNC);
     const int sw = h->opt.nu1 > 0 ? h->opt.nu1 : h->opt.nu2;
     if (h->opt.smoother == MG_SMOOTH_WJAC) {
         l1 = sw;                 // one Jacobi kernel per sweep
         s1 = sw;
     } else {
-        smooth_launches(fused, sw, &l1, &s1);
+        smooth_launches(h->sweep[0], h->grid.dim == 2, sw, &l1, &s1);
     }
     h->smooth_launches += l1;
     h->smooth_sweeps += s1;
@@ -1582,15 +1625,19 @@ mg_status autotune_impl(mg_handle *h, int reps, double *vcycle_ms) {
     // sweeps, level by level (the coarsest level is solved, not smoothed);
     // the Jacobi smoother has a single kernel
     for (int l = 0; l + 1 < h->nlev && h->opt.smoother == MG_SMOOTH_RBGS; l++) {
-        // candidates: colour, colour with two rows per thread, then (2D) fused and TMA-fed fused per tile
-        const int ncand = DIM == 2 ? 2 + 2 * kTileShapes : 2;
+        // candidates: colour, colour with two rows per thread, then (2D) fused, TMA-fed fused and fused pairs
+        // per tile
+        const int ncand = DIM == 2 ? 2 + 3 * kTileShapes : 2;
         double best = 1e30;
         int kind = MG_SWEEP_COLOUR, tile = 0;
         for (int c = 0; c < ncand; c++) {
-            const int ck = c == 0 ? MG_SWEEP_COLOUR
-                                  : (c == 1 ? MG_SWEEP_COLOUR2 : (c < 2 + kTileShapes ? MG_SWEEP_FUSED : MG_SWEEP_ASYNC));
+            const int ck = c == 0   ? MG_SWEEP_COLOUR
+                           : c == 1 ? MG_SWEEP_COLOUR2
+                           : c < 2 + kTileShapes ? MG_SWEEP_FUSED
+                           : c < 2 + 2 * kTileShapes ? MG_SWEEP_ASYNC : MG_SWEEP_FUSED2;
             const int ct = c < 2 ? 0 : (c - 2) % kTileShapes;
             if (ck == MG_SWEEP_ASYNC && !async_ok<R>(h, l, ct)) continue;
+            if (ck == MG_SWEEP_FUSED2 && !fused2_ok(h->opt, DIM)) continue;
             double ms = 0.0;
             st = time_graph(h, 5, &ms, [&](cudaStream_t s) {
                 for (int r = 0; r < reps; r++) enqueue_sweeps<R, DIM>(h, s, l, 2, ck, ct);
@@ -1894,8 +1941,11 @@ mg_status mg_smooth(mg_handle *h, const double *rhs, double *x, int sweeps, int 
     if (!rhs || !x || sweeps < 0) return fail(MG_ERR_INVALID_ARG, "bad arguments to mg_smooth");
     DeviceGuard dg(h->device);
     if ((st = prep(h, rhs, x, on_device))) return st;
-    if (h->grid.dim == 2) enqueue_smooth<double, 2>(h, h->stream, 0, sweeps);
-    else enqueue_smooth<double, 3>(h, h->stream, 0, sweeps);
+    const bool alt = h->grid.dim == 2 ? enqueue_smooth<double, 2>(h, h->stream, 0, sweeps)
+                                      : enqueue_smooth<double, 3>(h, h->stream, 0, sweeps);
+    if (alt)          // an odd number of fused pairs: the values are in xalt
+        CK(cudaMemcpyAsync(h->L[0].x, h->L[0].xalt, sizeof(double2) * h->L[0].N, cudaMemcpyDeviceToDevice,
+                           h->stream));
     CK(cudaGetLastError());
     if ((st = x_out(h, x, on_device))) return st;
     CK(cudaStreamSynchronize(h->stream));
@@ -2130,11 +2180,14 @@ mg_status mg_set_tuning(mg_handle *h, const mg_tuning *t) {
     if (!t) return fail(MG_ERR_INVALID_ARG, "tuning is NULL");
     for (int l = 0; l < h->nlev; l++) {
         if (t->sweep[l] != MG_SWEEP_COLOUR && t->sweep[l] != MG_SWEEP_FUSED && t->sweep[l] != MG_SWEEP_ASYNC &&
-            t->sweep[l] != MG_SWEEP_COLOUR2)
-            return fail(MG_ERR_INVALID_ARG, "sweep kind must be MG_SWEEP_COLOUR, MG_SWEEP_COLOUR2, MG_SWEEP_FUSED or "
-                                            "MG_SWEEP_ASYNC");
-        if ((t->sweep[l] == MG_SWEEP_FUSED || t->sweep[l] == MG_SWEEP_ASYNC) && h->grid.dim != 2)
+            t->sweep[l] != MG_SWEEP_COLOUR2 && t->sweep[l] != MG_SWEEP_FUSED2)
+            return fail(MG_ERR_INVALID_ARG, "sweep kind must be MG_SWEEP_COLOUR, MG_SWEEP_COLOUR2, MG_SWEEP_FUSED, "
+                                            "MG_SWEEP_ASYNC or MG_SWEEP_FUSED2");
+        if ((t->sweep[l] == MG_SWEEP_FUSED || t->sweep[l] == MG_SWEEP_ASYNC || t->sweep[l] == MG_SWEEP_FUSED2) &&
+            h->grid.dim != 2)
             return fail(MG_ERR_INVALID_ARG, "fused sweeps are for 2D grids");
+        if (t->sweep[l] == MG_SWEEP_FUSED2 && l + 1 < h->nlev && !fused2_ok(h->opt, h->grid.dim))
+            return fail(MG_ERR_INVALID_ARG, "fused sweep pairs need red-black smoothing with nu1 / 2 + nu2 / 2 even");
         if (t->tile[l] < 0 || t->tile[l] >= kTileShapes) return fail(MG_ERR_INVALID_ARG, "tile shape out of range");
         if (t->sweep[l] == MG_SWEEP_ASYNC && l + 1 < h->nlev &&
             !(h->opt.precision == MG_MIXED ? async_ok<float>(h, l, t->tile[l]) : async_ok<double>(h, l, t->tile[l])))

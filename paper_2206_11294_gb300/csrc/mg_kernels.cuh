@@ -350,6 +350,62 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 8 : 4)
     rbgs_fused2d_block<R, TX, TY>(L, xin, xout, blockIdx.x, blockIdx.y);
 }
 
+// Two red-black sweeps on one tile (temporal blocking): x staged with a halo
+// of 4, then the red cells of the tile and a 3-cell ring, the black cells of
+// a 2-cell ring, the red cells of a 1-cell ring, the black cells of the tile.
+// Each phase reads only values the phase before it left in its ring (or the
+// staged x), so every cell of the tile ends as after two full sweeps, with
+// the same update in the same order: the result is the other kernels' bit
+// for bit.  Faces, W and bt of the ring are read once from DRAM and the
+// second time from L1; xin -> xout.
+template <typename R, int TX, int TY>
+__device__ __forceinline__ void rbgs_fused2d_x2_block(const Level<R> &L, const typename Vec<R>::v2 *__restrict__ xin,
+                                                      typename Vec<R>::v2 *__restrict__ xout, int bx, int by) {
+    using V2 = typename Vec<R>::v2;
+    constexpr int H = 4, SX = TX + 2 * H, SY = TY + 2 * H;
+    __shared__ V2 xs[SY][SX];
+    const int n0 = L.n0, n1 = L.n1;
+    const int i0 = bx * TX, j0 = by * TY;
+    const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+    for (int q = tid; q < SY * SX; q += 256) {
+        const int ly = q / SX, lx = q - ly * SX;
+        const int gi = i0 + lx - H, gj = j0 + ly - H;
+        if (gi >= 0 && gi < n0 && gj >= 0 && gj < n1) xs[ly][lx] = ldg2(xin + (long long)gj * n0 + gi);
+    }
+    __syncthreads();
+    // phase p = 0..3: colour (p even: red), ring width 3 - p
+#pragma unroll 1
+    for (int p = 0; p < 4; p++) {
+        const int ring = 3 - p, par = p & 1;            // par 0: red ((i + j) even), 1: black
+        const int w = TX + 2 * ring, hgt = TY + 2 * ring;
+        const int per_row = w / 2;                      // TX even: each row holds w / 2 cells of a colour
+        for (int q = tid; q < hgt * per_row; q += 256) {
+            const int ry = q / per_row, rx = q - ry * per_row;
+            const int gj = j0 - ring + ry;
+            const int gi = i0 - ring + 2 * rx + ((i0 - ring + gj + par) & 1);
+            if (gi < 0 || gi >= n0 || gj < 0 || gj >= n1) continue;
+            const int lx = gi - i0 + H, ly = gj - j0 + H;
+            const long long c = (long long)gj * n0 + gi;
+            R sT, sp;
+            offdiag_tile2d<R, SX - 4>(L, xs, lx, ly, gi, gj, c, sT, sp);
+            xs[ly][lx] = gs_update<R>(L, c, sT, sp);
+        }
+        __syncthreads();
+    }
+    for (int q = tid; q < TY * TX; q += 256) {
+        const int ty = q / TX, tx = q - ty * TX;
+        const int gi = i0 + tx, gj = j0 + ty;
+        if (gi < n0 && gj < n1) xout[(long long)gj * n0 + gi] = xs[ty + H][tx + H];
+    }
+}
+
+template <typename R, int TX, int TY>
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 6 : 4)
+    k_rbgs_fused2d_x2(Level<R> L, const typename Vec<R>::v2 *__restrict__ xin, typename Vec<R>::v2 *__restrict__ xout) {
+    pdl_entry();
+    rbgs_fused2d_x2_block<R, TX, TY>(L, xin, xout, blockIdx.x, blockIdx.y);
+}
+
 // ---------------------------------------------------------------------------
 // Residual of the children, restricted: coarse b = mean of the 2^DIM
 // children's residuals (plain mean in the row-scaled form = volume-weighted

@@ -74,9 +74,9 @@ def test_ctypes_mirror_roundtrip():
 
 def test_sweep_names_roundtrip():
     d = _tuning()
-    d["sweep"] = ["async", "fused", "colour", "async", "colour"]
+    d["sweep"] = ["async", "fused", "colour", "fused2", "colour"]
     assert B.MgTuning.from_dict(d).as_dict() == d
-    assert describe(d).startswith("sweeps [A0,F1,C,A0,C]")
+    assert describe(d).startswith("sweeps [A0,F1,C,P0,C]")
 
 
 def test_describe():

@@ -67,6 +67,10 @@ def _variants(s):
             out.append(dict(colour, sweep=["fused"] * n, tile=[t] * n))
         for t in range(3):
             out.append(dict(colour, sweep=["async"] * n, tile=[t] * n))
+        for t in range(3):
+            out.append(dict(colour, sweep=["fused2"] * n, tile=[t] * n))
+        out.append(dict(colour, sweep=["fused2" if l % 2 == 0 else "fused" for l in range(n)],
+                        tile=[(l + 1) % 3 for l in range(n)]))
         out.append(dict(colour, sweep=["fused" if l % 2 else "colour" for l in range(n)],
                         tile=[l % 3 for l in range(n)]))
     sizes = s.levels()
@@ -155,6 +159,37 @@ def test_set_tuning_rejects_bad_choices(torch_cuda):
         assert s.tuning() == before
     s2.close()
     s3.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_fused_pairs_in_w_cycles_and_smoothing(torch_cuda, precision):
+    """Fused sweep pairs move a level's values to its second buffer and back
+    within each cycle: W-cycles (two visits of each coarse level) and the
+    public smoother (one pair: the values come back by a copy) give the colour
+    sweeps' results bit for bit; a cycle shape whose pairs are odd in number
+    (V(2,0)) is refused."""
+    from paper_2206_11294_gb300.binding import MgError, MG_ERR_INVALID_ARG
+    p = PROBS["2d"]
+    s0, x0, st0 = _solve(p, precision=precision, cycle="W")
+    n = s0.tuning()["levels"]
+    pairs = dict(s0.tuning(), sweep=["fused2"] * n, tile=[0] * n, tail_level=n)
+    s1, x1, st1 = _solve(p, tuning=pairs, precision=precision, cycle="W")
+    assert st1["cycles"] == st0["cycles"] and np.array_equal(x1, x0)
+    if precision == "fp64":
+        a, b = p.x0.copy(), p.x0.copy()
+        s0.set_tuning(dict(s0.tuning(), sweep=["colour"] * n))
+        s0.smooth(p.b, a, sweeps=2)
+        s1.smooth(p.b, b, sweeps=2)
+        assert np.array_equal(a, b)
+        s0.smooth(p.b, a, sweeps=3)
+        s1.smooth(p.b, b, sweeps=3)
+        assert np.array_equal(a, b)
+    s2, _, _ = _solve(p, precision=precision, nu2=0)
+    with pytest.raises(MgError) as e:
+        s2.set_tuning(dict(s2.tuning(), sweep=["fused2"] * n, tile=[0] * n))
+    assert e.value.status == MG_ERR_INVALID_ARG
+    for s in (s0, s1, s2):
+        s.close()
 
 
 def test_table_reuses_measurement(torch_cuda):
