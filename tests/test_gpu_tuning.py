@@ -1,7 +1,8 @@
 """Kernel choices (mg_set_tuning) and the native autotuner (mg_autotune).
 
-Every choice -- colour or fused sweeps with any tile shape per level, the
-cluster tail from any allowed level on 8 or 16 CTAs, or none -- runs the same
+Every choice -- colour, fused, TMA-fed fused or fused-pair sweeps with any
+tile shape per level, the cluster tail from any allowed level on 1, 8 or 16
+CTAs, or none, dependent launches on or off -- runs the same
 per-cell arithmetic in the same order, so solves must agree bit for bit and
 stop after the same number of cycles."""
 import numpy as np
@@ -116,7 +117,7 @@ def test_autotune_picks_valid_choice_and_keeps_results(torch_cuda, name, precisi
     assert ms > 0
     n = len(s0.levels())
     assert tuning["levels"] == n
-    assert all(k in ("colour", "colour2", "fused", "async") for k in tuning["sweep"])
+    assert all(k in ("colour", "colour2", "fused", "async", "fused2") for k in tuning["sweep"])
     if p.grid.dim == 3:
         assert set(tuning["sweep"]) <= {"colour", "colour2"}
     assert tuning["tail_level"] >= n or 1 <= tuning["tail_level"] <= n - 2
