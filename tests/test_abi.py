@@ -176,3 +176,21 @@ def test_factored_coarse_solve_needs_no_inverse(lib):
     st, a = _size(lib, _grid(n=(1024, 1024, 1), h=1 / 1024))
     st2, b = _size(lib, _grid(n=(1024, 1024, 1), h=1 / 1024), coarse="inverse")
     assert st == st2 == 0 and a == b
+
+
+def test_binding_constants_match_the_header():
+    """Every MG_* enum value the binding defines equals the header's, and the
+    header's sweep kinds, status codes and flags all have a binding name."""
+    from paper_2206_11294_gb300 import binding as B
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    text = open(os.path.join(root, "include", "coupledmg.h")).read()
+    header = {m.group(1): int(m.group(2)) for m in re.finditer(r"\b(MG_[A-Z0-9_]+)\s*=\s*(-?\d+)", text)}
+    assert header["MG_SWEEP_FUSED2"] == 5 and header["MG_ERR_STATE"] == 8
+    bound = {k: getattr(B, k) for k in dir(B) if k.startswith("MG_") and isinstance(getattr(B, k), int)}
+    for k, v in bound.items():
+        if k in header:
+            assert header[k] == v, k
+    for k in header:
+        named = k.startswith(("MG_SWEEP_", "MG_ERR_", "MG_ASSEMBLE_", "MG_MOMENTUM_"))
+        if named or k in ("MG_OK", "MG_FP64", "MG_MIXED"):
+            assert k in bound, k
