@@ -141,6 +141,32 @@ def test_fixed_cycles_fp64(torch_cuda, orc, name, cycles, smoother):
     s.close()
 
 
+@pytest.mark.parametrize("tile", [0, 2])
+@pytest.mark.parametrize("name", [n for n in CASES if CASES[n][0].grid.dim == 2])
+def test_fixed_cycles_fused_pairs_vs_oracle(torch_cuda, orc, name, tile):
+    """Two sweeps per launch on tiles with a 4-cell halo (MG_SWEEP_FUSED2) on
+    every smoothed level, no tail: 1 and 3 fixed V(2,2) cycles against the
+    oracle's, at the tolerance of the plain kernels, and the colour sweeps'
+    results bit for bit."""
+    p, tol = CASES[name]
+    for cycles in (1, 3):
+        s = _solver(p, rtol=0.0, max_cycles=cycles)
+        n = s.tuning()["levels"]
+        s.set_tuning(dict(s.tuning(), sweep=["fused2"] * n, tile=[tile] * n, tail_level=n))
+        x = p.x0.copy()
+        st = s.solve(p.b, x)
+        ref, cyc, _ = orc.mg_solve(p.grid.as_dict(), p.lam, p.fa, p.fk, p.b, p.x0, max_cycles=cycles, rtol=0.0)
+        assert st["cycles"] == cycles == cyc
+        assert rel_dev(x, ref, p.x0) <= tol
+        c = _solver(p, rtol=0.0, max_cycles=cycles)
+        c.set_tuning(dict(c.tuning(), sweep=["colour"] * n, tile=[0] * n, tail_level=n))
+        xc = p.x0.copy()
+        c.solve(p.b, xc)
+        assert np.array_equal(x, xc)
+        s.close()
+        c.close()
+
+
 @pytest.mark.parametrize("name", list(CASES))
 def test_converged_fp64_same_cycles_as_oracle(torch_cuda, orc, name):
     p, tol = CASES[name]
